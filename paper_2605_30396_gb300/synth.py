@@ -1,0 +1,122 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle tests and the bench.
+
+This module holds only input generation (random draws and their packing); none of
+the codec's arithmetic (sparse coding, dictionary update, SH evaluation) lives
+here, so both sides of every parity test can take their inputs from it.
+
+Signal model (stand-in for the 45 non-DC SH coefficients per Gaussian of a
+trained 3DGS model, Sec. 2.2): a hidden unit-norm dictionary of K atoms whose
+entries have per-SH-degree standard deviations 0.15 / 0.08 / 0.04 (degree 1, 2,
+3), optionally with correlation rho between the R, G, B entries of the same
+basis function; each signal is s distinct hidden atoms with Laplace(b=1)
+coefficients plus N(0, sigma_noise^2) noise.  Layout is channel-major:
+x[c*15 + b], c in {R, G, B}, b = SH basis index 0..14 (degree 1..3).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+D_SH = 45
+N_BASIS = 15
+# SH degree of basis b (0-based over degrees 1..3): 3 of degree 1, 5 of 2, 7 of 3.
+BASIS_DEGREE = np.array([1] * 3 + [2] * 5 + [3] * 7)
+DEGREE_STD = {1: 0.15, 2: 0.08, 3: 0.04}
+
+
+def hidden_dictionary(K: int, seed: int, rho: float = 0.0, dtype=np.float64) -> np.ndarray:
+    """Hidden unit-norm atoms, shape (K, 45), row j = atom j (channel-major)."""
+    rng = np.random.default_rng(seed)
+    std_b = np.array([DEGREE_STD[int(l)] for l in BASIS_DEGREE])  # (15,)
+    # (R,G,B) triple of each basis entry ~ N(0, Sigma), Sigma = (1-rho) I + rho 11^T
+    cov = (1.0 - rho) * np.eye(3) + rho * np.ones((3, 3))
+    chol = np.linalg.cholesky(cov)
+    z = rng.standard_normal((K, N_BASIS, 3)) @ chol.T  # (K, 15, 3)
+    z = z * std_b[None, :, None]
+    atoms = np.transpose(z, (0, 2, 1)).reshape(K, D_SH)  # channel-major
+    atoms /= np.linalg.norm(atoms, axis=1, keepdims=True)
+    return atoms.astype(dtype)
+
+
+def distinct_supports(rng: np.random.Generator, N: int, K: int, s: int) -> np.ndarray:
+    """(N, s) int64 array of s distinct atom indices per row, uniform."""
+    sup = rng.integers(0, K, size=(N, s))
+    while True:
+        srt = np.sort(sup, axis=1)
+        bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+        if bad.size == 0:
+            return sup
+        sup[bad] = rng.integers(0, K, size=(bad.size, s))
+
+
+def signals(N: int, atoms: np.ndarray, s: int, seed: int, noise_std: float = 1e-3,
+            dtype=np.float32, chunk: int = 1 << 18) -> np.ndarray:
+    """(N, 45) signals: s-sparse Laplace(1) combinations of hidden atoms + noise."""
+    rng = np.random.default_rng(seed)
+    K = atoms.shape[0]
+    out = np.empty((N, D_SH), dtype=dtype)
+    for lo in range(0, N, chunk):
+        n = min(chunk, N - lo)
+        sup = distinct_supports(rng, n, K, s)
+        coef = rng.laplace(0.0, 1.0, size=(n, s))
+        x = np.einsum("ns,nsd->nd", coef, atoms[sup])
+        x += noise_std * rng.standard_normal((n, D_SH))
+        out[lo:lo + n] = x
+    return out
+
+
+def unit_directions(N: int, seed: int, dtype=np.float32) -> np.ndarray:
+    """(N, 3) uniform unit vectors (normalised N(0, I3))."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((N, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    return v.astype(dtype)
+
+
+def camera_and_means(N: int, cam_seed: int, mean_seed: int, radius: float = 4.0,
+                     dtype=np.float32):
+    """Camera position radius*u (u uniform on S^2) and Gaussian means ~ U[-1,1]^3."""
+    cam = radius * unit_directions(1, cam_seed, dtype=np.float64)[0]
+    rng = np.random.default_rng(mean_seed)
+    mu = rng.uniform(-1.0, 1.0, size=(N, 3))
+    return cam.astype(dtype), mu.astype(dtype)
+
+
+def init_atom_indices(N: int, K: int, seed: int) -> np.ndarray:
+    """K distinct signal indices whose (normalised) signals seed the dictionary."""
+    return np.random.default_rng(seed).choice(N, K, replace=False)
+
+
+def erc_dictionary(n: int) -> np.ndarray:
+    """[I | H/sqrt(n)] (2n atoms of dimension n, rows = atoms), mutual coherence 1/sqrt(n).
+
+    H is the Sylvester Hadamard matrix, so n must be a power of two.
+    """
+    H = np.array([[1.0]])
+    while H.shape[0] < n:
+        H = np.block([[H, H], [H, -H]])
+    assert H.shape[0] == n
+    return np.concatenate([np.eye(n), H.T / np.sqrt(n)], axis=0)
+
+
+def planted_sparse(rng: np.random.Generator, atoms: np.ndarray, N: int, s: int,
+                   min_abs: float = 0.5):
+    """Exactly s-sparse signals (no noise) with coefficient magnitudes >= min_abs."""
+    K = atoms.shape[0]
+    sup = distinct_supports(rng, N, K, s)
+    mag = min_abs + rng.exponential(1.0, size=(N, s))
+    sign = rng.choice([-1.0, 1.0], size=(N, s))
+    coef = mag * sign
+    x = np.einsum("ns,nsd->nd", coef, atoms[sup])
+    return x, sup, coef
+
+
+def mlp_params(K: int, seed: int, d_in: int = D_SH, hidden: int = 256):
+    """He-style random init for the 45->256->256->K support-proposal network."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.standard_normal((hidden, d_in)) * np.sqrt(2.0 / d_in)
+    W2 = rng.standard_normal((hidden, hidden)) * np.sqrt(2.0 / hidden)
+    W3 = rng.standard_normal((K, hidden)) * np.sqrt(1.0 / hidden)
+    b1 = np.zeros(hidden)
+    b2 = np.zeros(hidden)
+    b3 = np.full(K, -np.log(K / 16.0))
+    return {"W1": W1, "b1": b1, "W2": W2, "b2": b2, "W3": W3, "b3": b3}
