@@ -1,0 +1,179 @@
+/*
+ * dlsh.h - C ABI of the GB300 sparse spherical-harmonic codec for 3D Gaussian
+ * Splatting ("Smaller and Faster 3DGS via Post-Training Dictionary Learning").
+ *
+ * The codec replaces the 45 non-DC SH coefficients of every Gaussian (15 basis
+ * functions of degree 1..3, times R, G, B) by a shared dictionary D and a sparse
+ * code per Gaussian (Sec. 2.2).  D is learned by alternating minimisation of
+ * Eq. 1 (codes by OMP, then the dictionary with the codes fixed, Sec. 2.1), and
+ * radiance is evaluated straight from the sparse codes (Sec. 2.2).
+ *
+ * Conventions shared by every call
+ *   - Signals x_i are d = 45 floats, channel-major: x[c*15 + b], c in {R,G,B},
+ *     b = SH basis index 0..14 (l*l + l + m - 1 for degree l = 1..3, m = -l..l,
+ *     real SH with the Condon-Shortley phase).
+ *   - X is N x d row-major FP32.  The dictionary is passed as K x d row-major
+ *     FP32: row j is atom j (the paper's D is its transpose, d x K).
+ *   - Sparse codes use a padded ELL layout: idx[N*s] (uint16, atom indices in
+ *     selection order, pad 0), coef[N*s] (FP32, pad 0), nnz[N] (uint8).
+ *   - Every array argument is a caller-owned DEVICE pointer unless stated
+ *     otherwise.  Pointers must be 16-byte aligned where the call says so.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = the legacy default stream) and returns a status code.  Argument
+ *     errors are found on the host before anything is launched.  Device-side
+ *     failures (a bounded wait that ran out, a bad value found by a kernel) are
+ *     recorded in a status word inside the workspace; with DLSH_FLAG_SYNC the
+ *     call synchronises the stream and turns that word into its return code.
+ *   - Scratch memory: calls that need scratch take a caller-allocated workspace
+ *     (`ws`, `ws_bytes`, 256-byte aligned) whose size the matching
+ *     *_workspace_size() function returns.  The library itself never calls
+ *     cudaMalloc.
+ *   - On error, dlsh_last_error() returns a message for the calling thread.
+ */
+#ifndef DLSH_H
+#define DLSH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define DLSH_OK               0
+#define DLSH_ERR_INVALID_ARG (-1) /* null/misaligned pointer, bad size        */
+#define DLSH_ERR_UNSUPPORTED (-2) /* d != 45, K > 65535, s > 32, ...          */
+#define DLSH_ERR_CUDA        (-3) /* a CUDA runtime call failed               */
+#define DLSH_ERR_TIMEOUT     (-4) /* a device-side bounded wait ran out       */
+#define DLSH_ERR_WORKSPACE   (-5) /* workspace missing or too small           */
+#define DLSH_ERR_DEVICE      (-6) /* a kernel flagged invalid data            */
+
+/* ---- correlation precision of the OMP atom selection (D^T r) --------- */
+#define DLSH_PREC_FP32 0 /* "plain FP32": 3xTF32 split on tcgen05, FP32 accumulate */
+#define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate, top-4 FP32 re-score    */
+#define DLSH_PREC_FP8  2 /* E4M3, per-atom and per-row scales, top-4 FP32 re-score */
+
+/* ---- flags ------------------------------------------------------------ */
+#define DLSH_FLAG_SYNC 1 /* synchronise the stream and report device status */
+
+/* ---- limits ----------------------------------------------------------- */
+#define DLSH_D      45    /* signal length (15 SH basis functions x RGB)      */
+#define DLSH_MAX_K  65535 /* atom indices are stored as uint16                */
+#define DLSH_MAX_S  32    /* maximum nonzeros per code                        */
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char* dlsh_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int dlsh_version(void);
+
+/* Number of streaming multiprocessors of the current device (0 on failure). */
+int dlsh_num_sms(void);
+
+/* Running count of kernels this library has enqueued in this process (kernels
+ * captured into a CUDA graph are counted once, at capture). */
+unsigned long long dlsh_kernel_launches(void);
+
+/*
+ * Sparse coding by OMP (Sec. 2.1): for every signal x_i, greedily select up to s
+ * atoms, each time the one of largest |d_j^T r| over atoms not yet selected
+ * (ties: smallest j), then re-fit all selected coefficients by least squares,
+ * r = x - D_I gamma.  Stops early when ||r||_2 <= eps (checked before each
+ * selection), when max |d_j^T r| <= 1e-7 ||x||, or when the new atom is
+ * numerically dependent on the selected ones (Cholesky pivot^2 <= 1e-6).
+ *
+ * D [K*d] FP32, X [N*d] FP32 (16-byte aligned), d must be 45, 1 <= K <= 65535,
+ * 1 <= s <= 32 (s <= 16 for DLSH_PREC_FP32), N >= 0.
+ * Outputs: idx [N*s], coef [N*s], nnz [N], resid_sq [N] (||r||^2; may be NULL).
+ * Workspace: dlsh_encode_workspace_size(K, d, s, precision) bytes.
+ */
+size_t dlsh_encode_workspace_size(int K, int d, int s, int precision);
+int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
+                float eps, int precision, uint16_t* idx, float* coef,
+                uint8_t* nnz, float* resid_sq, void* ws, size_t ws_bytes,
+                void* stream, int flags);
+
+/*
+ * Correlation step alone (the D^T r of every OMP iteration, Sec. 2.1) on the
+ * same tensor-core path the encoder uses: C [M*K] = R [M*d] * D^T, FP32 result,
+ * computed at `precision` (FP32 = 3xTF32; BF16; FP8 returns the scaled value
+ * rho_i sigma_j (q_r . q_d)).  M >= 0.  Workspace: dlsh_encode_workspace_size.
+ */
+int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M,
+                   int precision, float* C, void* ws, size_t ws_bytes,
+                   void* stream, int flags);
+
+/*
+ * Radiance straight from the sparse codes (Sec. 2.2): for Gaussian i with view
+ * direction v_i,  rgb_c = sum_{b} Y_b(v_i) * sum_{t < nnz_i} coef[i,t] * D[idx[i,t], c*15+b].
+ * If cam_pos (HOST pointer to 3 floats) is NULL, dirs_or_means [N*3] holds unit
+ * view directions; otherwise it holds Gaussian means mu_i and
+ * v_i = (mu_i - cam) / ||mu_i - cam||.  Output rgb [N*3] FP32 (view-dependent
+ * part only; the DC term is not part of the dictionary).  No workspace.
+ */
+int dlsh_decode(const float* D, int K, int d, const uint16_t* idx,
+                const float* coef, const uint8_t* nnz, int s, int64_t N,
+                const float* dirs_or_means, const float* cam_pos, float* rgb,
+                void* stream, int flags);
+
+/*
+ * Dictionary update with the codes fixed (the second half of the alternating
+ * minimisation of Eq. 1), read as MOD:
+ *   G = A A^T, B = X A^T, lambda = 1e-6 trace(G)/K (1e-6 if trace is 0),
+ *   D~ = (B + lambda D_old)(G + lambda I)^-1  (FP64 Cholesky on the device),
+ *   d_j = d~_j / ||d~_j||; atoms with no nonzero in A (or d~_j = 0) are
+ *   refilled in increasing j with the normalised signals of largest resid_sq
+ *   (decreasing order, ties to the smallest index, zero signals skipped).
+ * D_old, D_new [K*d]; resid_sq [N] (needed only when an atom is unused; may be
+ * NULL, then unused atoms keep D_old).  Accumulation order is fixed: results
+ * are bitwise reproducible.  Workspace: dlsh_mod_workspace_size(K, d, s, N).
+ */
+size_t dlsh_mod_workspace_size(int K, int d, int s, int64_t N);
+int dlsh_mod_update(const float* X, int64_t N, int d, int K,
+                    const uint16_t* idx, const float* coef, const uint8_t* nnz,
+                    int s, const float* D_old, const float* resid_sq,
+                    float* D_new, void* ws, size_t ws_bytes, void* stream,
+                    int flags);
+
+/*
+ * Alternating minimisation of Eq. 1 (Sec. 2.1): D_0 = normalised X rows at
+ * init_idx [K] (int64, distinct, device), then `iters` times
+ * {codes = OMP(D, X); D = MOD(D, codes)} and a final OMP pass.  Writes the final
+ * dictionary D_out [K*d], the final codes, and rmse [iters+1] (device FP32,
+ * sqrt(sum ||r||^2 / (N d)) after every coding pass).  The whole loop is
+ * captured once into a CUDA graph and replayed; no host synchronisation happens
+ * inside it.  Workspace: dlsh_learn_workspace_size(...).
+ */
+/*
+ * First step of the learning loop alone: D_out row j = X[init_idx[j]] /
+ * ||X[init_idx[j]]||, init_idx [K] int64 on the device (the random choice of
+ * signals is an input).  Rows whose index is out of range or whose signal is
+ * zero are left unwritten.  No workspace.
+ */
+int dlsh_init_dictionary(const float* X, int64_t N, int d, const int64_t* init_idx,
+                         int K, float* D_out, void* stream, int flags);
+
+size_t dlsh_learn_workspace_size(int K, int d, int s, int64_t N, int precision);
+int dlsh_learn_dictionary(const float* X, int64_t N, int d, int K, int s,
+                          float eps, int iters, const int64_t* init_idx,
+                          int precision, float* D_out, uint16_t* idx,
+                          float* coef, uint8_t* nnz, float* rmse, void* ws,
+                          size_t ws_bytes, void* stream, int flags);
+
+/*
+ * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in
+ * Compressed Sparse Column form, one column per Gaussian.  col_ptr [N+1]
+ * (int64), row_idx and val have room for N*s entries; col_ptr[N] = total nnz.
+ * Workspace: dlsh_csc_workspace_size(N).
+ */
+size_t dlsh_csc_workspace_size(int64_t N);
+int dlsh_csc_from_ell(const uint16_t* idx, const float* coef,
+                      const uint8_t* nnz, int64_t N, int s, int64_t* col_ptr,
+                      uint16_t* row_idx, float* val, void* ws, size_t ws_bytes,
+                      void* stream, int flags);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DLSH_H */

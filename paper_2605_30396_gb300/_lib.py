@@ -1,0 +1,66 @@
+"""ctypes loader for libdlsh.so: argument types of every C-ABI entry point.
+
+Importing this module never falls back to anything: if the library is missing
+or stale, `lib()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+_LIB = None
+
+c_int, c_int64, c_float, c_size_t = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
+P = ctypes.c_void_p
+
+SIGNATURES = {
+    "dlsh_last_error": (ctypes.c_char_p, []),
+    "dlsh_version": (c_int, []),
+    "dlsh_num_sms": (c_int, []),
+    "dlsh_kernel_launches": (ctypes.c_ulonglong, []),
+    "dlsh_encode_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "dlsh_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P, P,
+                            c_size_t, P, c_int]),
+    "dlsh_correlate": (c_int, [P, c_int, c_int, P, c_int64, c_int, P, P, c_size_t, P, c_int]),
+    "dlsh_decode": (c_int, [P, c_int, c_int, P, P, P, c_int, c_int64, P, P, P, P, c_int]),
+    "dlsh_mod_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
+    "dlsh_mod_update": (c_int, [P, c_int64, c_int, c_int, P, P, P, c_int, P, P, P, P, c_size_t,
+                                P, c_int]),
+    "dlsh_learn_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64, c_int]),
+    "dlsh_learn_dictionary": (c_int, [P, c_int64, c_int, c_int, c_int, c_float, c_int, P, c_int,
+                                      P, P, P, P, P, P, c_size_t, P, c_int]),
+    "dlsh_init_dictionary": (c_int, [P, c_int64, c_int, P, c_int, P, P, c_int]),
+    "dlsh_csc_workspace_size": (c_size_t, [c_int64]),
+    "dlsh_csc_from_ell": (c_int, [P, P, P, c_int64, c_int, P, P, P, P, c_size_t, P, c_int]),
+}
+
+
+def lib_path() -> str:
+    return _build.SO_PATH
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library (built in-tree by `build()`); raises if unavailable."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    if not _build.is_current():
+        raise RuntimeError(f"{path} is stale or built for another machine: rebuild it")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name, None)
+        if fn is None:
+            continue
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def last_error() -> str:
+    return lib().dlsh_last_error().decode()

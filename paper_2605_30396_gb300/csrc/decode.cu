@@ -1,0 +1,291 @@
+// Radiance straight from the sparse codes (Sec. 2.2): the renderer's SH step
+// reads the shared dictionary and each Gaussian's nonzeros instead of its 45 SH
+// coefficients.  For Gaussian i and unit view direction v_i,
+//   rgb_c = sum_b Y_b(v_i) * sum_{t < nnz_i} coef[i,t] * D[idx[i,t], c*15 + b].
+//
+// Memory-bound design: the dictionary is staged once per CTA in shared memory
+// (rows padded to 3 x 16 floats: R0..R14,0, G0..G14,0, B0..B14,0) and every
+// nonzero costs three conflict-light 16-lane row reads.  A warp works on
+// batches of 32 Gaussians: first one lane per Gaussian computes its direction
+// and 15 basis values into shared memory; then each half-warp takes one
+// Gaussian, lane b owning basis b of all three channels, accumulates
+// sum_t coef * D[j_t, c*15+b], multiplies by Y_b and reduces across the half
+// with shuffles.  Results are staged and written back coalesced.
+#include <math.h>
+
+#include "common.cuh"
+#include "host.hpp"
+
+namespace dlsh {
+namespace dec {
+
+constexpr int ROW = 48;         // padded dictionary row in shared memory
+constexpr int YS = 17;          // basis values per Gaussian slot (15 used, padded)
+constexpr int WARP_SMEM = (32 * YS + 96) * 4;  // basis slots + staged rgb per warp
+constexpr int SMEM_LIMIT = 232448;
+
+// Real-SH constants of the Cartesian forms below, computed on the host from
+// N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) and the associated Legendre
+// polynomials' leading factors.
+struct ShConst {
+  float c[15];
+};
+__constant__ ShConst g_sh;
+
+// Y_b(v) for unit v, basis order b = l*l + l + m - 1 (l = 1..3, m = -l..l),
+// Condon-Shortley phase included in the constants' signs.
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[15]) {
+  const float* c = g_sh.c;
+  const float xx = x * x, yy = y * y, zz = z * z;
+  Y[0] = c[0] * y;
+  Y[1] = c[1] * z;
+  Y[2] = c[2] * x;
+  Y[3] = c[3] * x * y;
+  Y[4] = c[4] * y * z;
+  Y[5] = c[5] * (3.f * zz - 1.f);
+  Y[6] = c[6] * x * z;
+  Y[7] = c[7] * (xx - yy);
+  Y[8] = c[8] * y * (3.f * xx - yy);
+  Y[9] = c[9] * x * y * z;
+  Y[10] = c[10] * y * (5.f * zz - 1.f);
+  Y[11] = c[11] * z * (5.f * zz - 3.f);
+  Y[12] = c[12] * x * (5.f * zz - 1.f);
+  Y[13] = c[13] * z * (xx - yy);
+  Y[14] = c[14] * x * (xx - 3.f * yy);
+}
+
+template <bool SMEM_D>
+__global__ void __launch_bounds__(512) decode_kernel(
+    const float* __restrict__ D, int K, const uint16_t* __restrict__ idx,
+    const float* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int64_t N,
+    const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
+    float* __restrict__ rgb, uint32_t* status) {
+  extern __shared__ __align__(16) float sm[];
+  const int nwarps = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* Ds = sm;
+  float* wsm = sm + (SMEM_D ? K * ROW : 0) + warp * (WARP_SMEM / 4);
+  float* Ys = wsm;
+  float* outs = wsm + 32 * YS;
+  if (SMEM_D) {
+    for (int f = threadIdx.x; f < K * ROW; f += blockDim.x) {
+      const int j = f / ROW, q = f - j * ROW, c = q >> 4, b = q & 15;
+      Ds[f] = b < 15 ? D[static_cast<size_t>(j) * DLSH_D + c * 15 + b] : 0.f;
+    }
+    __syncthreads();
+  }
+  const int hl = lane & 15, h = lane >> 4;
+  const unsigned FULL = 0xffffffffu;
+  const int64_t nbatch = (N + 31) / 32;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
+  bool bad = false;
+  for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
+    const int64_t base = bt * 32;
+    // ---- phase A: one lane per Gaussian, direction + 15 basis values
+    {
+      const int64_t g = base + lane;
+      float vx = 0.f, vy = 0.f, vz = 1.f;
+      int nz = 0;
+      if (g < N) {
+        vx = dm[g * 3 + 0];
+        vy = dm[g * 3 + 1];
+        vz = dm[g * 3 + 2];
+        if (use_cam) {
+          vx -= cx;
+          vy -= cy;
+          vz -= cz;
+          const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+          vx *= inv;
+          vy *= inv;
+          vz *= inv;
+        }
+        nz = nnz[g];
+      }
+      float Y[15];
+      sh_basis(vx, vy, vz, Y);
+#pragma unroll
+      for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
+      Ys[lane * YS + 15] = __int_as_float(nz);
+    }
+    __syncwarp();
+    // ---- phase B: a half-warp per Gaussian, lane hl owns basis hl
+    for (int pp = 0; pp < 16; ++pp) {
+      const int gl = 2 * pp + h;
+      const int64_t g = base + gl;
+      const bool valid = g < N;
+      int nz = __float_as_int(Ys[gl * YS + 15]);
+      if (nz > s) {
+        bad = true;
+        nz = s;
+      }
+      uint32_t j0 = 0, j1 = 0;
+      float a0 = 0.f, a1 = 0.f;
+      if (valid && hl < s) {
+        j0 = idx[g * s + hl];
+        a0 = coef[g * s + hl];
+      }
+      if (valid && hl + 16 < s) {
+        j1 = idx[g * s + hl + 16];
+        a1 = coef[g * s + hl + 16];
+      }
+      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+      for (int t = 0; t < s; ++t) {
+        uint32_t j = __shfl_sync(FULL, t < 16 ? j0 : j1, t & 15, 16);
+        float a = __shfl_sync(FULL, t < 16 ? a0 : a1, t & 15, 16);
+        if (t >= nz) a = 0.f;
+        if (j >= static_cast<uint32_t>(K)) {
+          if (a != 0.f) bad = true;
+          j = 0;
+          a = 0.f;
+        }
+        if (SMEM_D) {
+          const float* row = Ds + j * ROW;
+          acc0 = fmaf(a, row[hl], acc0);
+          acc1 = fmaf(a, row[16 + hl], acc1);
+          acc2 = fmaf(a, row[32 + hl], acc2);
+        } else if (hl < 15) {
+          const float* row = D + static_cast<size_t>(j) * DLSH_D;
+          acc0 = fmaf(a, __ldg(row + hl), acc0);
+          acc1 = fmaf(a, __ldg(row + 15 + hl), acc1);
+          acc2 = fmaf(a, __ldg(row + 30 + hl), acc2);
+        }
+      }
+      const float yb = hl < 15 ? Ys[gl * YS + hl] : 0.f;
+      float p0 = acc0 * yb, p1 = acc1 * yb, p2 = acc2 * yb;
+#pragma unroll
+      for (int off = 8; off > 0; off >>= 1) {
+        p0 += __shfl_xor_sync(FULL, p0, off);
+        p1 += __shfl_xor_sync(FULL, p1, off);
+        p2 += __shfl_xor_sync(FULL, p2, off);
+      }
+      if (hl == 0) {
+        outs[gl * 3 + 0] = p0;
+        outs[gl * 3 + 1] = p1;
+        outs[gl * 3 + 2] = p2;
+      }
+    }
+    __syncwarp();
+    // ---- coalesced store of the batch's 32 x 3 outputs
+    const int64_t lim = (N - base) * 3;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int e = lane + 32 * q;
+      if (e < lim) rgb[base * 3 + e] = outs[e];
+    }
+    __syncwarp();
+  }
+  if (bad) flag_status(status, ST_BAD_INPUT);
+}
+
+static double factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= k;
+  return f;
+}
+
+static double nlm(int l, int m) {
+  const int am = m < 0 ? -m : m;
+  return sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * factorial(l - am) / factorial(l + am));
+}
+
+// Constants of the Cartesian forms used by sh_basis.  With P_l^m carrying the
+// Condon-Shortley phase: P_1^1 = -sin, P_2^1 = -3z sin, P_2^2 = 3 sin^2,
+// P_3^1 = -1.5 (5z^2-1) sin, P_3^2 = 15 z sin^2, P_3^3 = -15 sin^3, and
+// sin^m(theta) {cos,sin}(m phi) expands to the x/y polynomials of sh_basis.
+static ShConst make_constants() {
+  const double r2 = sqrt(2.0);
+  ShConst k;
+  k.c[0] = static_cast<float>(-r2 * nlm(1, -1));          // y
+  k.c[1] = static_cast<float>(nlm(1, 0));                 // z
+  k.c[2] = static_cast<float>(-r2 * nlm(1, 1));           // x
+  k.c[3] = static_cast<float>(r2 * nlm(2, -2) * 3.0 * 2.0);  // xy   (sin^2 sin 2phi = 2xy)
+  k.c[4] = static_cast<float>(-r2 * nlm(2, -1) * 3.0);    // yz
+  k.c[5] = static_cast<float>(nlm(2, 0) * 0.5);           // 3z^2 - 1
+  k.c[6] = static_cast<float>(-r2 * nlm(2, 1) * 3.0);     // xz
+  k.c[7] = static_cast<float>(r2 * nlm(2, 2) * 3.0);      // x^2 - y^2
+  k.c[8] = static_cast<float>(-r2 * nlm(3, -3) * 15.0);   // y(3x^2 - y^2)
+  k.c[9] = static_cast<float>(r2 * nlm(3, -2) * 15.0 * 2.0);  // xyz
+  k.c[10] = static_cast<float>(-r2 * nlm(3, -1) * 1.5);   // y(5z^2 - 1)
+  k.c[11] = static_cast<float>(nlm(3, 0) * 0.5);          // z(5z^2 - 3)
+  k.c[12] = static_cast<float>(-r2 * nlm(3, 1) * 1.5);    // x(5z^2 - 1)
+  k.c[13] = static_cast<float>(r2 * nlm(3, 2) * 15.0);    // z(x^2 - y^2)
+  k.c[14] = static_cast<float>(-r2 * nlm(3, 3) * 15.0);   // x(x^2 - 3y^2)
+  return k;
+}
+
+static int upload_constants(cudaStream_t st) {
+  static thread_local int uploaded_dev = -1;
+  int dev = 0;
+  DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_decode: cudaGetDevice");
+  if (uploaded_dev == dev) return DLSH_OK;
+  const ShConst k = make_constants();
+  DLSH_CUDA_TRY(cudaMemcpyToSymbolAsync(g_sh, &k, sizeof(k), 0, cudaMemcpyHostToDevice, st),
+                "dlsh_decode: constants");
+  DLSH_CUDA_TRY(cudaStreamSynchronize(st), "dlsh_decode: constants");
+  uploaded_dev = dev;
+  return DLSH_OK;
+}
+
+}  // namespace dec
+
+// Shared with the bench / learn paths: enqueue one decode.
+int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef,
+                   const uint8_t* nnz, int s, int64_t N, const float* dm, const float* cam,
+                   float* rgb, uint32_t* status, cudaStream_t st) {
+  using namespace dec;
+  int rc = upload_constants(st);
+  if (rc) return rc;
+  if (N == 0) return DLSH_OK;
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 1;
+  const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
+  const int64_t nbatch = (N + 31) / 32;
+  const size_t dbytes = static_cast<size_t>(K) * ROW * 4;
+  int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / WARP_SMEM);
+  if (nwarps > 16) nwarps = 16;
+  if (nwarps >= 8) {
+    const size_t smem = dbytes + static_cast<size_t>(nwarps) * WARP_SMEM;
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
+                  "dlsh_decode: attribute");
+    int per_sm = static_cast<int>(SMEM_LIMIT / smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = static_cast<int64_t>(sms) * per_sm;
+    const int64_t need = (nbatch + nwarps - 1) / nwarps;
+    if (grid > need) grid = need;
+    decode_kernel<true><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
+        D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
+  } else {
+    const int nw = 8;
+    const size_t smem = static_cast<size_t>(nw) * WARP_SMEM;
+    int64_t grid = static_cast<int64_t>(sms) * 8;
+    const int64_t need = (nbatch + nw - 1) / nw;
+    if (grid > need) grid = need;
+    decode_kernel<false><<<static_cast<int>(grid), nw * 32, smem, st>>>(
+        D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
+  }
+  count_launches(1);
+  return check_launch("dlsh_decode: launch");
+}
+
+}  // namespace dlsh
+
+extern "C" int dlsh_decode(const float* D, int K, int d, const uint16_t* idx, const float* coef,
+                           const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
+                           const float* cam_pos, float* rgb, void* stream, int flags) {
+  using namespace dlsh;
+  clear_error();
+  if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_decode: d must be 45, got %d", d);
+  if (K < 1 || K > DLSH_MAX_K)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_decode: K must be in [1, 65535], got %d", K);
+  if (s < 1 || s > DLSH_MAX_S)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_decode: s must be in [1, 32], got %d", s);
+  if (N < 0) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_decode: N < 0");
+  if (!D) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_decode: D is NULL");
+  if (N > 0 && (!idx || !coef || !nnz || !dirs_or_means || !rgb))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_decode: NULL array");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = decode_enqueue(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, rgb, nullptr, st);
+  if (rc) return rc;
+  return finish(st, nullptr, flags, "dlsh_decode");
+}
