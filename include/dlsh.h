@@ -95,6 +95,29 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                 void* stream, int flags);
 
 /*
+ * dlsh_encode without a workspace and without any allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory, such
+ * as plugins whose host application owns every device allocation through its
+ * own pool, or real-time loops where a cudaMalloc (which may synchronise the
+ * device) is not allowed.  Same arguments, outputs and stop rules as
+ * dlsh_encode, minus `ws`/`ws_bytes`.
+ *
+ * Scratch lives in one fixed device array of dlsh_encode_noalloc_max_bytes()
+ * bytes (8 MiB), which every GPU that loads the library holds until the process
+ * exits; that covers K <= 1024 at every precision and s.  A configuration that
+ * needs more returns DLSH_ERR_UNSUPPORTED before anything is launched.  The
+ * first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array: calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race on it and must be serialised by the caller.
+ */
+size_t dlsh_encode_noalloc_max_bytes(void);
+int dlsh_encode_noalloc(const float* D, int K, int d, const float* X, int64_t N,
+                        int s, float eps, int precision, uint16_t* idx,
+                        float* coef, uint8_t* nnz, float* resid_sq,
+                        void* stream, int flags);
+
+/*
  * Correlation step alone (the D^T r of every OMP iteration, Sec. 2.1) on the
  * same tensor-core path the encoder uses: C [M*K] = R [M*d] * D^T, FP32 result,
  * computed at `precision` (FP32 = 3xTF32; BF16; FP8 returns the scaled value

@@ -23,6 +23,9 @@ SIGNATURES = {
     "dlsh_encode_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),
     "dlsh_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P, P,
                             c_size_t, P, c_int]),
+    "dlsh_encode_noalloc_max_bytes": (c_size_t, []),
+    "dlsh_encode_noalloc": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P,
+                                    P, P, c_int]),
     "dlsh_correlate": (c_int, [P, c_int, c_int, P, c_int64, c_int, P, P, c_size_t, P, c_int]),
     "dlsh_decode": (c_int, [P, c_int, c_int, P, P, P, c_int, c_int64, P, P, P, P, c_int]),
     "dlsh_mod_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),

@@ -1,0 +1,88 @@
+// Encoder entry point that allocates nothing and needs no caller workspace.
+//
+// Some callers cannot allocate device memory: plugins whose host application
+// owns every device allocation through its own pool, and real-time loops where
+// a cudaMalloc (which can synchronise the device) is not allowed.  For them the
+// encoder's scratch (padded FP32 dictionary, Gram matrix, packed tensor-core
+// operand image, status word) lives in one file-scope device array of fixed
+// size, reserved on every GPU that loads this library until the process exits.
+#include <mutex>
+
+#include "host.hpp"
+
+namespace dlsh {
+
+int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, float eps, int prec,
+                   uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq, void* ws,
+                   cudaStream_t st, uint32_t** status_out);
+size_t encode_ws_bytes(int K, int s, int prec);
+
+namespace noalloc {
+
+constexpr size_t kScratchBytes = size_t(8) << 20;  // 8 MiB: K <= 1024 at any precision and s
+constexpr int kMaxDevices = 64;
+
+// Host code must not use this name as a device address: it is a host-side
+// stand-in.  The device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+static std::mutex g_mu;
+static void* g_addr[kMaxDevices] = {};
+
+// Looks up (once per device, with that device current) the device address of
+// g_scratch.
+static int scratch_address(void** out) {
+  int dev = 0;
+  DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_encode_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_addr[dev]) {
+    void* p = nullptr;
+    DLSH_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch), "dlsh_encode_noalloc: cudaGetSymbolAddress");
+    if (!p) return set_error(DLSH_ERR_CUDA, "dlsh_encode_noalloc: null scratch address");
+    g_addr[dev] = p;
+  }
+  *out = g_addr[dev];
+  return DLSH_OK;
+}
+
+}  // namespace noalloc
+}  // namespace dlsh
+
+extern "C" size_t dlsh_encode_noalloc_max_bytes(void) { return dlsh::noalloc::kScratchBytes; }
+
+extern "C" int dlsh_encode_noalloc(const float* D, int K, int d, const float* X, int64_t N, int s,
+                                   float eps, int precision, uint16_t* idx, float* coef,
+                                   uint8_t* nnz, float* resid_sq, void* stream, int flags) {
+  using namespace dlsh;
+  clear_error();
+  if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: d must be 45");
+  if (K < 1 || K > DLSH_MAX_K)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: K must be in [1, 65535]");
+  if (s < 1 || s > 16)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: s must be in [1, 16]");
+  if (precision < 0 || precision > 2)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: unknown precision %d", precision);
+  if (!D) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: D is NULL");
+  if (N < 0) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: N < 0");
+  if (N > 0 && (!X || !idx || !coef || !nnz))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: NULL X/idx/coef/nnz");
+  if (!(eps >= 0.f)) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: eps < 0");
+  const size_t need = encode_ws_bytes(K, s, precision);
+  if (need == 0)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: K=%d s=%d does not fit", K, s);
+  if (need > noalloc::kScratchBytes)
+    return set_error(DLSH_ERR_UNSUPPORTED,
+                     "dlsh_encode_noalloc: K=%d s=%d precision=%d needs %zu bytes of scratch, "
+                     "more than the fixed %zu (use dlsh_encode with a workspace)",
+                     K, s, precision, need, noalloc::kScratchBytes);
+  void* ws = nullptr;
+  int rc = noalloc::scratch_address(&ws);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* status = nullptr;
+  rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status);
+  if (rc) return rc;
+  return finish(st, status, flags, "dlsh_encode_noalloc");
+}
