@@ -3,14 +3,14 @@
 // coefficients.  For Gaussian i and unit view direction v_i,
 //   rgb_c = sum_b Y_b(v_i) * sum_{t < nnz_i} coef[i,t] * D[idx[i,t], c*15 + b].
 //
-// Memory-bound design: the dictionary is staged once per CTA in shared memory
-// (rows padded to 3 x 16 floats: R0..R14,0, G0..G14,0, B0..B14,0) and every
-// nonzero costs three conflict-light 16-lane row reads.  A warp works on
-// batches of 32 Gaussians: first one lane per Gaussian computes its direction
-// and 15 basis values into shared memory; then each half-warp takes one
-// Gaussian, lane b owning basis b of all three channels, accumulates
-// sum_t coef * D[j_t, c*15+b], multiplies by Y_b and reduces across the half
-// with shuffles.  Results are staged and written back coalesced.
+// Memory-bound design: the FP32 dictionary is staged once per CTA in shared
+// memory and every nonzero costs three 16-lane reads of one dictionary row.  A
+// warp works on batches of 32 Gaussians: first all of the batch's codes are
+// loaded (coalesced) into shared memory while one lane per Gaussian computes its
+// direction and 15 basis values; then each half-warp takes one Gaussian, lane b
+// owning basis b of all three channels, accumulates sum_t coef * D[j_t, c*15+b],
+// multiplies by Y_b and reduces across the half with shuffles.  Results are
+// staged and written back coalesced.
 #include <math.h>
 
 #include "common.cuh"
@@ -19,10 +19,12 @@
 namespace dlsh {
 namespace dec {
 
-constexpr int ROW = 48;         // padded dictionary row in shared memory
-constexpr int YS = 17;          // basis values per Gaussian slot (15 used, padded)
-constexpr int WARP_SMEM = (32 * YS + 96) * 4;  // basis slots + staged rgb per warp
+constexpr int ROW = 45;         // dictionary row in shared memory (plus 16 zero words at the end)
+constexpr int YS = 17;          // basis values per Gaussian slot (15 used, slot 15 holds nnz)
 constexpr int SMEM_LIMIT = 232448;
+
+// Per-warp shared memory: basis slots, staged rgb, and the batch's codes.
+__host__ __device__ constexpr int warp_floats(int s) { return 32 * YS + 96 + 32 * s * 2; }
 
 // Real-SH constants of the Cartesian forms below, computed on the host from
 // N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) and the associated Legendre
@@ -64,14 +66,14 @@ __global__ void __launch_bounds__(512) decode_kernel(
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float* Ds = sm;
-  float* wsm = sm + (SMEM_D ? K * ROW : 0) + warp * (WARP_SMEM / 4);
+  const int dwords = SMEM_D ? K * ROW + 16 : 0;
+  float* wsm = sm + dwords + warp * warp_floats(s);
   float* Ys = wsm;
   float* outs = wsm + 32 * YS;
+  float* ccoef = outs + 96;
+  uint32_t* cidx = reinterpret_cast<uint32_t*>(ccoef + 32 * s);
   if (SMEM_D) {
-    for (int f = threadIdx.x; f < K * ROW; f += blockDim.x) {
-      const int j = f / ROW, q = f - j * ROW, c = q >> 4, b = q & 15;
-      Ds[f] = b < 15 ? D[static_cast<size_t>(j) * DLSH_D + c * 15 + b] : 0.f;
-    }
+    for (int f = threadIdx.x; f < dwords; f += blockDim.x) Ds[f] = f < K * ROW ? D[f] : 0.f;
     __syncthreads();
   }
   const int hl = lane & 15, h = lane >> 4;
@@ -81,15 +83,22 @@ __global__ void __launch_bounds__(512) decode_kernel(
   bool bad = false;
   for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
     const int64_t base = bt * 32;
-    // ---- phase A: one lane per Gaussian, direction + 15 basis values
+    const int nb = N - base < 32 ? static_cast<int>(N - base) : 32;
+    // ---- phase A: every load of the batch is issued here, then one lane per
+    // Gaussian computes its direction and 15 basis values
+    for (int f = lane; f < nb * s; f += 32) {
+      cidx[f] = idx[base * s + f];
+      ccoef[f] = coef[base * s + f];
+    }
     {
       const int64_t g = base + lane;
       float vx = 0.f, vy = 0.f, vz = 1.f;
       int nz = 0;
-      if (g < N) {
+      if (lane < nb) {
         vx = dm[g * 3 + 0];
         vy = dm[g * 3 + 1];
         vz = dm[g * 3 + 2];
+        nz = nnz[g];
         if (use_cam) {
           vx -= cx;
           vy -= cy;
@@ -99,7 +108,6 @@ __global__ void __launch_bounds__(512) decode_kernel(
           vy *= inv;
           vz *= inv;
         }
-        nz = nnz[g];
       }
       float Y[15];
       sh_basis(vx, vy, vz, Y);
@@ -108,48 +116,40 @@ __global__ void __launch_bounds__(512) decode_kernel(
       Ys[lane * YS + 15] = __int_as_float(nz);
     }
     __syncwarp();
-    // ---- phase B: a half-warp per Gaussian, lane hl owns basis hl
+    // ---- phase B: a half-warp per Gaussian, lane hl owns basis hl of R, G, B
     for (int pp = 0; pp < 16; ++pp) {
       const int gl = 2 * pp + h;
-      const int64_t g = base + gl;
-      const bool valid = g < N;
-      int nz = __float_as_int(Ys[gl * YS + 15]);
+      int nz = gl < nb ? __float_as_int(Ys[gl * YS + 15]) : 0;
       if (nz > s) {
         bad = true;
         nz = s;
       }
-      uint32_t j0 = 0, j1 = 0;
-      float a0 = 0.f, a1 = 0.f;
-      if (valid && hl < s) {
-        j0 = idx[g * s + hl];
-        a0 = coef[g * s + hl];
-      }
-      if (valid && hl + 16 < s) {
-        j1 = idx[g * s + hl + 16];
-        a1 = coef[g * s + hl + 16];
-      }
       float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
       for (int t = 0; t < s; ++t) {
-        uint32_t j = __shfl_sync(FULL, t < 16 ? j0 : j1, t & 15, 16);
-        float a = __shfl_sync(FULL, t < 16 ? a0 : a1, t & 15, 16);
-        if (t >= nz) a = 0.f;
+        uint32_t j = 0;
+        float a = 0.f;
+        if (t < nz) {
+          j = cidx[gl * s + t];
+          a = ccoef[gl * s + t];
+        }
         if (j >= static_cast<uint32_t>(K)) {
-          if (a != 0.f) bad = true;
+          bad = true;
           j = 0;
           a = 0.f;
         }
         if (SMEM_D) {
-          const float* row = Ds + j * ROW;
-          acc0 = fmaf(a, row[hl], acc0);
-          acc1 = fmaf(a, row[16 + hl], acc1);
-          acc2 = fmaf(a, row[32 + hl], acc2);
+          const float* row = Ds + j * ROW + hl;
+          acc0 = fmaf(a, row[0], acc0);
+          acc1 = fmaf(a, row[15], acc1);
+          acc2 = fmaf(a, row[30], acc2);
         } else if (hl < 15) {
-          const float* row = D + static_cast<size_t>(j) * DLSH_D;
-          acc0 = fmaf(a, __ldg(row + hl), acc0);
-          acc1 = fmaf(a, __ldg(row + 15 + hl), acc1);
-          acc2 = fmaf(a, __ldg(row + 30 + hl), acc2);
+          const float* row = D + static_cast<size_t>(j) * DLSH_D + hl;
+          acc0 = fmaf(a, __ldg(row), acc0);
+          acc1 = fmaf(a, __ldg(row + 15), acc1);
+          acc2 = fmaf(a, __ldg(row + 30), acc2);
         }
       }
+      // lane 15 read a neighbouring word (finite) times Y = 0
       const float yb = hl < 15 ? Ys[gl * YS + hl] : 0.f;
       float p0 = acc0 * yb, p1 = acc1 * yb, p2 = acc2 * yb;
 #pragma unroll
@@ -165,12 +165,11 @@ __global__ void __launch_bounds__(512) decode_kernel(
       }
     }
     __syncwarp();
-    // ---- coalesced store of the batch's 32 x 3 outputs
-    const int64_t lim = (N - base) * 3;
+    // ---- coalesced store of the batch's outputs
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int e = lane + 32 * q;
-      if (e < lim) rgb[base * 3 + e] = outs[e];
+      if (e < nb * 3) rgb[base * 3 + e] = outs[e];
     }
     __syncwarp();
   }
@@ -240,11 +239,12 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
   if (sms <= 0) sms = 1;
   const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
   const int64_t nbatch = (N + 31) / 32;
-  const size_t dbytes = static_cast<size_t>(K) * ROW * 4;
-  int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / WARP_SMEM);
+  const size_t dbytes = (static_cast<size_t>(K) * ROW + 16) * 4;
+  const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
+  int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
   if (nwarps > 16) nwarps = 16;
-  if (nwarps >= 8) {
-    const size_t smem = dbytes + static_cast<size_t>(nwarps) * WARP_SMEM;
+  if (nwarps >= 6) {
+    const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
     DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                   "dlsh_decode: attribute");
@@ -257,8 +257,11 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
         D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
   } else {
     const int nw = 8;
-    const size_t smem = static_cast<size_t>(nw) * WARP_SMEM;
-    int64_t grid = static_cast<int64_t>(sms) * 8;
+    const size_t smem = static_cast<size_t>(nw) * wbytes;
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
+                  "dlsh_decode: attribute");
+    int64_t grid = static_cast<int64_t>(sms) * 4;
     const int64_t need = (nbatch + nw - 1) / nw;
     if (grid > need) grid = need;
     decode_kernel<false><<<static_cast<int>(grid), nw * 32, smem, st>>>(
