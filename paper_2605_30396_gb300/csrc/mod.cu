@@ -6,17 +6,23 @@
 //   unused atoms refilled with the worst-fit signals.
 //
 // GPU design (deterministic, no floating-point atomics):
-//   1. count_kernel   per-tile atom histograms (integer counts)
-//   2. scan_kernel    exclusive scan, atom-major, tile-minor
-//   3. scatter_kernel one warp per signal tile writes (signal, coef) into the
-//                     atom-major list in signal order (a counting sort)
-//   4. accum_kernel   one CTA per atom: row j of G and column j of B in FP64,
-//                     each warp over a fixed slice, slices summed in order
-//   5. FP64 blocked Cholesky of G + lambda I (diagonal factor, panel solve,
-//      trailing update), forward and backward substitution for the d RHS
+//   1. count_kernel     per-tile atom histograms (integer counts)
+//   2. scan kernels     per-atom totals, atom offsets, per-(atom, tile) offsets
+//   3. scatter_kernel   one warp per signal tile writes (signal, coef, nnz) into
+//                       the atom-major list in signal order (a counting sort)
+//   4. accum_kernel     one CTA per atom: row j of G and column j of B.  Each
+//                       warp owns a fixed slice of the atom's list; batches are
+//                       staged with cp.async (double-buffered) and summed in
+//                       float-float arithmetic (exact FMA products, two-sum
+//                       accumulation: about FP64 accuracy on the FP32 pipe,
+//                       since GB300's FP64 units are slow); slices are added
+//                       in a fixed order in FP64
+//   5. FP64 blocked Cholesky of G + lambda I (diagonal factor with its inverse,
+//      panel solve, trailing update), then blocked forward and backward
+//      substitution for the 45 right-hand sides using the diagonal inverses
 //   6. normalise, then refill unused atoms (argmax passes over resid_sq)
-// GB300's FP64 rate is low but K^3/3 at K <= 2048 is a few GFLOP; the solve
-// stays in FP64 because G + lambda I can have condition numbers near 1e6+.
+// The factorisation stays in FP64 because G + lambda I can have condition
+// numbers near 1e6 and beyond.
 #include <math.h>
 
 #include "common.cuh"
@@ -28,18 +34,24 @@ namespace mod {
 constexpr int TS = 2048;       // signals per counting-sort tile
 constexpr int NB = 32;         // Cholesky block
 constexpr int RW = 48;         // padded RHS width (45 used)
-constexpr int MAX_K = 4096;    // shared-memory G-row partials and FP64 G size limit
+constexpr int MAX_K = 4096;    // shared-memory G-row partials limit
+constexpr int SMEM_LIMIT = 232448;
 constexpr double RIDGE_REL = 1e-6;
 
 struct Ws {
   uint32_t* status;
-  int* cnt;        // K x T
-  int* off;        // K x T
+  int* cnt;        // K x T per-(atom, tile) counts
+  int* off;        // K x T offsets
+  int* atom_total; // K
   int* atom_start; // K + 1
   int* list_sig;   // N*s
   float* list_coef;
+  uint8_t* list_nnz;
   double* M;       // K x K (G, then G + lambda I, then its Cholesky factor)
-  double* Z;       // K x RW (B^T + lambda D_old, then the solution)
+  double* Linv;    // nblk x 32 x 32 inverses of the diagonal blocks
+  double* Z;       // K x RW right-hand sides (B^T + lambda D_old)
+  double* Yb;      // K x RW forward-substitution result
+  double* Xb;      // K x RW solution D~^T
   double* lam;     // [0] lambda
   int* dead;       // K
 };
@@ -47,17 +59,45 @@ struct Ws {
 static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   Carver c(base);
   const int64_t T = (N + TS - 1) / TS > 0 ? (N + TS - 1) / TS : 1;
+  const int nblk = (K + NB - 1) / NB;
   w.status = c.take<uint32_t>(64);
   w.cnt = c.take<int>(static_cast<size_t>(K) * T);
   w.off = c.take<int>(static_cast<size_t>(K) * T);
+  w.atom_total = c.take<int>(K);
   w.atom_start = c.take<int>(K + 1);
   w.list_sig = c.take<int>(static_cast<size_t>(N) * s + 1);
   w.list_coef = c.take<float>(static_cast<size_t>(N) * s + 1);
+  w.list_nnz = c.take<uint8_t>(static_cast<size_t>(N) * s + 1);
   w.M = c.take<double>(static_cast<size_t>(K) * K);
+  w.Linv = c.take<double>(static_cast<size_t>(nblk) * NB * NB);
   w.Z = c.take<double>(static_cast<size_t>(K) * RW);
+  w.Yb = c.take<double>(static_cast<size_t>(K) * RW);
+  w.Xb = c.take<double>(static_cast<size_t>(K) * RW);
   w.lam = c.take<double>(4);
   w.dead = c.take<int>(K);
   return c.size();
+}
+
+// ---- cp.async (4-byte global -> shared copies, no registers) -----------------
+__device__ __forceinline__ void cp_async4(void* smem, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// ---- float-float accumulation: (hi, lo) += a * b, product exact via FMA ------
+__device__ __forceinline__ void ff_fma(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fadd_rn(s, -hi);
+  float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -v)), __fadd_rn(p, -v));
+  e = __fadd_rn(e, __fadd_rn(lo, pe));
+  hi = __fadd_rn(s, e);
+  lo = __fadd_rn(e, -__fadd_rn(hi, -s));
 }
 
 // ---- 1. per-tile histograms ------------------------------------------------
@@ -91,145 +131,268 @@ __global__ void count_kernel(const uint16_t* __restrict__ idx, const uint8_t* __
   if (bad) flag_status(status, ST_BAD_INPUT);
 }
 
-// ---- 2. exclusive scan of cnt (atom-major) -----------------------------------
-__global__ void scan_kernel(const int* __restrict__ cnt, int64_t total, int K, int T,
-                            int* __restrict__ off, int* __restrict__ atom_start) {
-  __shared__ long long part[1024];
+// ---- 2. offsets: per-atom totals, atom starts, per-(atom, tile) offsets -------
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sm, int* total) {
+  // Hillis-Steele over blockDim.x (<= 1024) values; returns the exclusive prefix
   const int tid = threadIdx.x;
-  const int64_t per = (total + blockDim.x - 1) / blockDim.x;
-  const int64_t a = tid * per, b = a + per < total ? a + per : total;
-  long long sum = 0;
-  for (int64_t e = a; e < b; ++e) sum += cnt[e];
-  part[tid] = sum;
+  sm[tid] = v;
   __syncthreads();
-  if (tid == 0) {
-    long long run = 0;
-    for (int q = 0; q < static_cast<int>(blockDim.x); ++q) {
-      const long long v = part[q];
-      part[q] = run;
-      run += v;
-    }
+  for (int o = 1; o < static_cast<int>(blockDim.x); o <<= 1) {
+    const int u = tid >= o ? sm[tid - o] : 0;
+    __syncthreads();
+    sm[tid] += u;
+    __syncthreads();
   }
+  const int incl = sm[tid];
+  if (total) *total = sm[blockDim.x - 1];
   __syncthreads();
-  long long run = part[tid];
-  for (int64_t e = a; e < b; ++e) {
-    off[e] = static_cast<int>(run);
-    if (e % T == 0) atom_start[e / T] = static_cast<int>(run);
-    run += cnt[e];
+  return incl - v;
+}
+
+__global__ void atom_total_kernel(const int* __restrict__ cnt, int T, int* __restrict__ atom_total) {
+  __shared__ int red[256];
+  const int j = blockIdx.x;
+  int acc = 0;
+  for (int b = threadIdx.x; b < T; b += blockDim.x) acc += cnt[static_cast<size_t>(j) * T + b];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
   }
-  if (tid == static_cast<int>(blockDim.x) - 1) atom_start[K] = static_cast<int>(run);
+  if (threadIdx.x == 0) atom_total[j] = red[0];
+}
+
+__global__ void atom_scan_kernel(const int* __restrict__ atom_total, int K,
+                                 int* __restrict__ atom_start) {
+  __shared__ int sm[1024];
+  __shared__ int carry_s;
+  int carry = 0;
+  for (int base = 0; base < K; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int v = j < K ? atom_total[j] : 0;
+    int tot = 0;
+    const int ex = block_exclusive_scan(v, sm, &tot);
+    if (j < K) atom_start[j] = carry + ex;
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+    carry = carry_s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atom_start[K] = carry;
+}
+
+__global__ void tile_offsets_kernel(const int* __restrict__ cnt, int T,
+                                    const int* __restrict__ atom_start, int* __restrict__ off) {
+  __shared__ int sm[256];
+  const int j = blockIdx.x;
+  const int per = (T + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per, b1 = b0 + per < T ? b0 + per : T;
+  int sum = 0;
+  for (int b = b0; b < b1; ++b) sum += cnt[static_cast<size_t>(j) * T + b];
+  int run = atom_start[j] + block_exclusive_scan(sum, sm, nullptr);
+  for (int b = b0; b < b1; ++b) {
+    off[static_cast<size_t>(j) * T + b] = run;
+    run += cnt[static_cast<size_t>(j) * T + b];
+  }
 }
 
 // ---- 3. counting-sort scatter, one warp per tile, signal order ---------------
+// The warp loads 32/s signals per step (one lane per code slot) one step ahead,
+// then commits them to the atom-major list one signal at a time; a signal's
+// atoms are distinct, so the shared-memory cursors see no contention and the
+// list order is the signal order.
 __global__ void scatter_kernel(const uint16_t* __restrict__ idx, const float* __restrict__ coef,
                                const uint8_t* __restrict__ nnz, int s, int64_t N, int K, int T,
                                const int* __restrict__ off, int* __restrict__ list_sig,
-                               float* __restrict__ list_coef) {
+                               float* __restrict__ list_coef, uint8_t* __restrict__ list_nnz) {
   extern __shared__ int cursor[];
   const int lane = threadIdx.x;
   const int b = blockIdx.x;
   for (int j = lane; j < K; j += 32) cursor[j] = off[static_cast<size_t>(j) * T + b];
   __syncwarp();
+  const int P = 32 / s;  // signals per step
+  const int q = lane / s, t = lane - q * s;
+  const bool slot = lane < P * s;
   const int64_t i0 = static_cast<int64_t>(b) * TS;
   const int64_t i1 = i0 + TS < N ? i0 + TS : N;
-  for (int64_t i = i0; i < i1; ++i) {
-    int nz = nnz[i];
-    nz = nz > s ? s : nz;
-    if (lane < nz) {
-      const int j = idx[i * s + lane];
-      if (j < K) {
-        const int pos = atomicAdd(&cursor[j], 1);  // distinct atoms per signal: no contention
-        list_sig[pos] = static_cast<int>(i);
-        list_coef[pos] = coef[i * s + lane];
+  auto load = [&](int64_t base, int& j, float& c, int& nz) {
+    const int64_t i = base + q;
+    j = -1;
+    c = 0.f;
+    nz = 0;
+    if (slot && i < i1) {
+      nz = nnz[i];
+      nz = nz > s ? s : nz;
+      if (t < nz) {
+        j = idx[i * s + t];
+        c = coef[i * s + t];
       }
     }
-    __syncwarp();
-  }
-}
-
-// ---- 4. G row j and B column j in FP64 ----------------------------------------
-// 4 warps; warp w takes the w-th contiguous quarter of atom j's list; within a
-// warp entries are processed in list order.  Partials are summed in warp order.
-constexpr int ACC_WARPS = 4;
-constexpr int BATCH = 32;
-
-__global__ void __launch_bounds__(ACC_WARPS * 32)
-    accum_kernel(const float* __restrict__ X, const uint16_t* __restrict__ idx,
-                 const float* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int K,
-                 const int* __restrict__ atom_start, const int* __restrict__ list_sig,
-                 const float* __restrict__ list_coef, double* __restrict__ M,
-                 double* __restrict__ Z) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  const int j = blockIdx.x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double* grow = reinterpret_cast<double*>(smraw) + static_cast<size_t>(warp) * K;
-  double* bpart = reinterpret_cast<double*>(smraw) + static_cast<size_t>(ACC_WARPS) * K +
-                  warp * RW;
-  float* xst = reinterpret_cast<float*>(reinterpret_cast<double*>(smraw) +
-                                        static_cast<size_t>(ACC_WARPS) * K + ACC_WARPS * RW) +
-               warp * (BATCH * DLSH_D + BATCH * 32 * 2 + BATCH * 2);
-  uint32_t* cst_i = reinterpret_cast<uint32_t*>(xst + BATCH * DLSH_D);
-  float* cst_c = reinterpret_cast<float*>(cst_i + BATCH * 32);
-  int* est_i = reinterpret_cast<int*>(cst_c + BATCH * 32);
-  float* est_a = reinterpret_cast<float*>(est_i + BATCH);
-  for (int k = lane; k < K; k += 32) grow[k] = 0.0;
-  double b0 = 0.0, b1 = 0.0;
-  const int e0 = atom_start[j], e1 = atom_start[j + 1];
-  const int len = e1 - e0;
-  const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / ACC_WARPS);
-  const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / ACC_WARPS);
-  __syncwarp();
-  for (int qb = q0; qb < q1; qb += BATCH) {
-    const int nb = q1 - qb < BATCH ? q1 - qb : BATCH;
-    if (lane < nb) {
-      est_i[lane] = list_sig[qb + lane];
-      est_a[lane] = list_coef[qb + lane];
-    }
-    __syncwarp();
-    // stage the batch's signals and codes
-    for (int f = lane; f < nb * DLSH_D; f += 32) {
-      const int e = f / DLSH_D, dd = f - e * DLSH_D;
-      xst[f] = X[static_cast<int64_t>(est_i[e]) * DLSH_D + dd];
-    }
-    for (int f = lane; f < nb * s; f += 32) {
-      const int e = f / s, t = f - e * s;
-      const int64_t i = est_i[e];
-      const int nz = nnz[i];
-      cst_i[e * 32 + t] = t < nz ? idx[i * s + t] : 0xFFFFFFFFu;
-      cst_c[e * 32 + t] = coef[i * s + t];
-    }
-    __syncwarp();
-    for (int e = 0; e < nb; ++e) {
-      const double a = est_a[e];
-      if (lane < s) {
-        const uint32_t k = cst_i[e * 32 + lane];
-        if (k < static_cast<uint32_t>(K)) grow[k] += a * static_cast<double>(cst_c[e * 32 + lane]);
+  };
+  int jn, nzn;
+  float cn;
+  load(i0, jn, cn, nzn);
+  for (int64_t base = i0; base < i1; base += P) {
+    const int jc = jn, nzc = nzn;
+    const float cc = cn;
+    if (base + P < i1) load(base + P, jn, cn, nzn);
+    for (int qq = 0; qq < P; ++qq) {
+      if (q == qq && slot && jc >= 0 && jc < K) {
+        const int pos = atomicAdd(&cursor[jc], 1);
+        list_sig[pos] = static_cast<int>(base + q);
+        list_coef[pos] = cc;
+        list_nnz[pos] = static_cast<uint8_t>(nzc);
       }
-      b0 += a * static_cast<double>(xst[e * DLSH_D + lane]);
-      if (lane < DLSH_D - 32) b1 += a * static_cast<double>(xst[e * DLSH_D + 32 + lane]);
       __syncwarp();
     }
   }
-  bpart[lane] = b0;
-  if (lane < RW - 32) bpart[32 + lane] = lane < DLSH_D - 32 ? b1 : 0.0;
+}
+
+// ---- 4. G row j and B column j ---------------------------------------------------
+constexpr int AB = 32;  // list entries per batch
+__host__ __device__ constexpr int acc_buf_words(int s) {
+  return 3 * AB + AB * DLSH_D + AB * s + AB * (s / 2 + 1);
+}
+
+__global__ void __launch_bounds__(128)
+    accum_kernel(const float* __restrict__ X, const uint32_t* __restrict__ idxw,
+                 const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
+                 const int* __restrict__ list_sig, const float* __restrict__ list_coef,
+                 const uint8_t* __restrict__ list_nnz, double* __restrict__ M,
+                 double* __restrict__ Z) {
+  extern __shared__ __align__(16) float smf[];
+  const int j = blockIdx.x;
+  const int nw = blockDim.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sw = s / 2 + 1;
+  const int bw = acc_buf_words(s);
+  float* ghi = smf + static_cast<size_t>(warp) * 2 * K;
+  float* glo = ghi + K;
+  float* wbuf = smf + static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(warp) * 2 * bw;
+  for (int k = lane; k < K; k += 32) {
+    ghi[k] = 0.f;
+    glo[k] = 0.f;
+  }
+  float b0h = 0.f, b0l = 0.f, b1h = 0.f, b1l = 0.f;
+  const int e0 = atom_start[j], e1 = atom_start[j + 1];
+  const int len = e1 - e0;
+  const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
+  const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
+  const int nbt = (q1 - q0 + AB - 1) / AB;
+  auto bptr = [&](int buf) { return wbuf + buf * bw; };
+  auto load_list = [&](int bt, int& li, float& la, int& ln) {
+    const int e = q0 + bt * AB + lane;
+    li = 0;
+    la = 0.f;
+    ln = 0;
+    if (e < q1) {
+      li = list_sig[e];
+      la = list_coef[e];
+      ln = list_nnz[e];
+    }
+  };
+  auto stage = [&](int buf, int cnt, int li, float la, int ln) {
+    float* B = bptr(buf);
+    int* ei = reinterpret_cast<int*>(B);
+    int* en = ei + 2 * AB;
+    B[AB + lane] = la;
+    ei[lane] = li;
+    en[lane] = ln;
+    __syncwarp();
+    float* xb = B + 3 * AB;
+    float* cf = xb + AB * DLSH_D;
+    uint32_t* cw = reinterpret_cast<uint32_t*>(cf + AB * s);
+    for (int f = lane; f < cnt * DLSH_D; f += 32) {
+      const int e = f / DLSH_D, d = f - e * DLSH_D;
+      cp_async4(xb + f, X + static_cast<int64_t>(ei[e]) * DLSH_D + d);
+    }
+    for (int f = lane; f < cnt * s; f += 32) {
+      const int e = f / s, t = f - e * s;
+      cp_async4(cf + f, coef + static_cast<int64_t>(ei[e]) * s + t);
+    }
+    for (int f = lane; f < cnt * sw; f += 32) {
+      const int e = f / sw, w = f - e * sw;
+      const int64_t base = static_cast<int64_t>(ei[e]) * s;
+      const int64_t w0 = base >> 1, wl = (base + s - 1) >> 1;
+      if (w0 + w <= wl) cp_async4(cw + f, idxw + w0 + w);
+    }
+    cp_async_commit();
+  };
+  int li = 0, ln = 0;
+  float la = 0.f;
+  if (nbt > 0) {
+    load_list(0, li, la, ln);
+    stage(0, q1 - q0 < AB ? q1 - q0 : AB, li, la, ln);
+  }
+  if (nbt > 1) load_list(1, li, la, ln);
+  for (int bt = 0; bt < nbt; ++bt) {
+    const int cnt = q1 - q0 - bt * AB < AB ? q1 - q0 - bt * AB : AB;
+    if (bt + 1 < nbt) {
+      const int cn = q1 - q0 - (bt + 1) * AB < AB ? q1 - q0 - (bt + 1) * AB : AB;
+      stage((bt + 1) & 1, cn, li, la, ln);
+      if (bt + 2 < nbt) load_list(bt + 2, li, la, ln);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    const float* B = bptr(bt & 1);
+    const int* ei = reinterpret_cast<const int*>(B);
+    const float* ea = B + AB;
+    const int* en = ei + 2 * AB;
+    const float* xb = B + 3 * AB;
+    const float* cf = xb + AB * DLSH_D;
+    const uint32_t* cw = reinterpret_cast<const uint32_t*>(cf + AB * s);
+    for (int e = 0; e < cnt; ++e) {
+      const float a = ea[e];
+      ff_fma(b0h, b0l, a, xb[e * DLSH_D + lane]);
+      if (lane < DLSH_D - 32) ff_fma(b1h, b1l, a, xb[e * DLSH_D + 32 + lane]);
+      const int nz = en[e];
+      if (lane < nz) {
+        const int o = ((ei[e] * s) & 1) + lane;
+        const uint32_t wv = cw[e * sw + (o >> 1)];
+        const int k = (o & 1) ? static_cast<int>(wv >> 16) : static_cast<int>(wv & 0xFFFFu);
+        if (k < K) ff_fma(ghi[k], glo[k], a, cf[e * s + lane]);
+      }
+    }
+    __syncwarp();
+  }
+  // publish this warp's B partial next to its G partial, then sum the warps in order
   __syncthreads();
-  double* gw = reinterpret_cast<double*>(smraw);
+  double* bpart = reinterpret_cast<double*>(wbuf);  // the warp's staging area is free now
+  bpart[lane] = static_cast<double>(b0h) + static_cast<double>(b0l);
+  if (lane < RW - 32)
+    bpart[32 + lane] = lane < DLSH_D - 32 ? static_cast<double>(b1h) + static_cast<double>(b1l) : 0.0;
+  __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
-    for (int w = 0; w < ACC_WARPS; ++w) acc += gw[static_cast<size_t>(w) * K + k];
+    for (int w = 0; w < nw; ++w) {
+      const float* gh = smf + static_cast<size_t>(w) * 2 * K;
+      acc += static_cast<double>(gh[k]) + static_cast<double>(gh[K + k]);
+    }
     M[static_cast<size_t>(j) * K + k] = acc;
   }
-  double* bw = reinterpret_cast<double*>(smraw) + static_cast<size_t>(ACC_WARPS) * K;
   for (int q = threadIdx.x; q < RW; q += blockDim.x) {
     double acc = 0.0;
-    for (int w = 0; w < ACC_WARPS; ++w) acc += bw[w * RW + q];
+    for (int w = 0; w < nw; ++w) {
+      const double* bp = reinterpret_cast<const double*>(smf + static_cast<size_t>(nw) * 2 * K +
+                                                         static_cast<size_t>(w) * 2 * bw);
+      acc += bp[q];
+    }
     Z[static_cast<size_t>(j) * RW + q] = acc;
   }
 }
 
-static size_t accum_smem(int K) {
-  return static_cast<size_t>(ACC_WARPS) * K * 8 + ACC_WARPS * RW * 8 +
-         static_cast<size_t>(ACC_WARPS) * (BATCH * DLSH_D + BATCH * 32 * 2 + BATCH * 2) * 4;
+static int accum_warps(int K, int s, size_t* smem) {
+  for (int nw = 4; nw >= 1; --nw) {
+    const size_t b = (static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(nw) * 2 * acc_buf_words(s)) * 4;
+    if (b <= static_cast<size_t>(SMEM_LIMIT)) {
+      *smem = b;
+      return nw;
+    }
+  }
+  return 0;
 }
 
 // ---- 5a. lambda = 1e-6 trace(G)/K; M += lambda I; Z += lambda D_old -----------
@@ -257,7 +420,8 @@ __global__ void ridge_kernel(double* __restrict__ M, double* __restrict__ Z,
 }
 
 // ---- 5b. blocked Cholesky (lower, in place, row-major M[r*K + c]) -------------
-__global__ void potrf_diag_kernel(double* __restrict__ M, int K, int k0, uint32_t* status) {
+__global__ void potrf_diag_kernel(double* __restrict__ M, int K, int k0, double* __restrict__ Linv,
+                                  uint32_t* status) {
   __shared__ double A[NB][NB + 1];
   const int nb = K - k0 < NB ? K - k0 : NB;
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
@@ -279,6 +443,23 @@ __global__ void potrf_diag_kernel(double* __restrict__ M, int K, int k0, uint32_
     __syncthreads();
   }
   if (tx < nb && ty < nb) M[static_cast<size_t>(k0 + ty) * K + k0 + tx] = tx <= ty ? A[ty][tx] : 0.0;
+  // inverse of the factored block, one column per thread of the first row:
+  // X[r][c] = (delta_rc - sum_{c<=k<r} L[r][k] X[k][c]) / L[r][r]
+  __shared__ double Xi[NB][NB + 1];
+  if (ty == 0) {
+    const int c = tx;
+    for (int r = 0; r < NB; ++r) {
+      double v = 0.0;
+      if (r < nb && c < nb && r >= c) {
+        double acc = r == c ? 1.0 : 0.0;
+        for (int k = c; k < r; ++k) acc -= A[r][k] * Xi[k][c];
+        v = acc / A[r][r];
+      }
+      Xi[r][c] = v;
+    }
+  }
+  __syncthreads();
+  Linv[(static_cast<size_t>(k0 / NB) * NB + ty) * NB + tx] = Xi[ty][tx];
 }
 
 // Rows below the diagonal block: L21 = A21 L11^-T, one thread per row.
@@ -335,53 +516,59 @@ __global__ void syrk_kernel(double* __restrict__ M, int K, int k0) {
   }
 }
 
-// ---- 5c. forward solve L y = Z, block kb (left-looking), one CTA per column ---
-__global__ void fwd_block_kernel(const double* __restrict__ M, double* __restrict__ Z, int K,
-                                 int k0) {
-  __shared__ double y[NB];
-  const int col = blockIdx.x, q = threadIdx.x;  // 32 threads
-  const int nb = K - k0 < NB ? K - k0 : NB;
-  if (q < nb) {
-    double acc = Z[static_cast<size_t>(k0 + q) * RW + col];
-    const double* lr = M + static_cast<size_t>(k0 + q) * K;
-    for (int r = 0; r < k0; ++r) acc -= lr[r] * Z[static_cast<size_t>(r) * RW + col];
-    y[q] = acc;
+// ---- 5c. forward substitution L Y = Z, block kb (right-looking) -------------
+// grid (nblk - kb, 3): x = target row block offset, y = group of 15 columns.
+// Every CTA recomputes Y_kb = Linv_kb Z_kb in shared memory; CTA x = 0 stores
+// it, CTAs x > 0 subtract L[row block][kb] Y_kb from their (later) rows of Z.
+__global__ void fwd_step_kernel(const double* __restrict__ M, const double* __restrict__ Linv,
+                                double* __restrict__ Z, double* __restrict__ Yb, int K, int kb) {
+  __shared__ double Yk[NB][16];
+  const int k0 = kb * NB, nb = K - k0 < NB ? K - k0 : NB;
+  const int r = threadIdx.y, c = threadIdx.x;  // 32 x 15
+  const int col = blockIdx.y * 15 + c;
+  const double* Li = Linv + static_cast<size_t>(kb) * NB * NB;
+  double y = 0.0;
+  if (r < nb) {
+    for (int k = 0; k <= r; ++k) y += Li[r * NB + k] * Z[static_cast<size_t>(k0 + k) * RW + col];
   }
+  Yk[r][c] = y;
   __syncthreads();
-  if (q == 0) {
-    for (int c = 0; c < nb; ++c) {
-      double acc = y[c];
-      const double* lr = M + static_cast<size_t>(k0 + c) * K + k0;
-      for (int p = 0; p < c; ++p) acc -= lr[p] * y[p];
-      y[c] = acc / lr[c];
-    }
+  if (blockIdx.x == 0) {
+    if (r < nb) Yb[static_cast<size_t>(k0 + r) * RW + col] = y;
+    return;
   }
-  __syncthreads();
-  if (q < nb) Z[static_cast<size_t>(k0 + q) * RW + col] = y[q];
+  const int row = k0 + static_cast<int>(blockIdx.x) * NB + r;
+  if (row >= K) return;
+  const double* lr = M + static_cast<size_t>(row) * K + k0;
+  double acc = 0.0;
+  for (int k = 0; k < nb; ++k) acc += lr[k] * Yk[k][c];
+  Z[static_cast<size_t>(row) * RW + col] -= acc;
 }
 
-// ---- 5d. backward solve L^T x = y, block kb (from the last), per column -------
-__global__ void bwd_block_kernel(const double* __restrict__ M, double* __restrict__ Z, int K,
-                                 int k0) {
-  __shared__ double x[NB];
-  const int col = blockIdx.x, q = threadIdx.x;
-  const int nb = K - k0 < NB ? K - k0 : NB;
-  if (q < nb) {
-    double acc = Z[static_cast<size_t>(k0 + q) * RW + col];
-    for (int r = k0 + nb; r < K; ++r)
-      acc -= M[static_cast<size_t>(r) * K + k0 + q] * Z[static_cast<size_t>(r) * RW + col];
-    x[q] = acc;
+// ---- 5d. backward substitution L^T X = Y, block kb (right-looking, last first) --
+// grid (kb + 1, 3): CTA x = 0 stores X_kb = Linv_kb^T Y_kb; CTA x > 0 subtracts
+// L[kb][row block]^T X_kb from the rows of block kb - x.
+__global__ void bwd_step_kernel(const double* __restrict__ M, const double* __restrict__ Linv,
+                                double* __restrict__ Yb, double* __restrict__ Xb, int K, int kb) {
+  __shared__ double Xk[NB][16];
+  const int k0 = kb * NB, nb = K - k0 < NB ? K - k0 : NB;
+  const int r = threadIdx.y, c = threadIdx.x;
+  const int col = blockIdx.y * 15 + c;
+  const double* Li = Linv + static_cast<size_t>(kb) * NB * NB;
+  double x = 0.0;
+  if (r < nb) {
+    for (int k = r; k < nb; ++k) x += Li[k * NB + r] * Yb[static_cast<size_t>(k0 + k) * RW + col];
   }
+  Xk[r][c] = x;
   __syncthreads();
-  if (q == 0) {
-    for (int c = nb - 1; c >= 0; --c) {
-      double acc = x[c];
-      for (int p = c + 1; p < nb; ++p) acc -= M[static_cast<size_t>(k0 + p) * K + k0 + c] * x[p];
-      x[c] = acc / M[static_cast<size_t>(k0 + c) * K + k0 + c];
-    }
+  if (blockIdx.x == 0) {
+    if (r < nb) Xb[static_cast<size_t>(k0 + r) * RW + col] = x;
+    return;
   }
-  __syncthreads();
-  if (q < nb) Z[static_cast<size_t>(k0 + q) * RW + col] = x[q];
+  const int row = (kb - static_cast<int>(blockIdx.x)) * NB + r;  // a full earlier block
+  double acc = 0.0;
+  for (int k = 0; k < nb; ++k) acc += M[static_cast<size_t>(k0 + k) * K + row] * Xk[k][c];
+  Yb[static_cast<size_t>(row) * RW + col] -= acc;
 }
 
 // ---- 6a. normalise; mark dead atoms ----------------------------------------------
@@ -497,40 +684,59 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   Ws w;
   carve(ws, K, s, N, w);
   if (status_out) *status_out = w.status;
+  size_t acc_smem = 0;
+  const int acc_nw = accum_warps(K, s, &acc_smem);
+  if (acc_nw == 0)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mod_update: K=%d s=%d does not fit", K, s);
   DLSH_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(uint32_t), st), "dlsh_mod_update: reset");
   const int T = static_cast<int>((N + TS - 1) / TS > 0 ? (N + TS - 1) / TS : 1);
+  int launches = 0;
   if (N > 0) {
     count_kernel<<<T, 256, K * sizeof(int), st>>>(idx, nnz, s, N, K, T, w.cnt, w.status);
   } else {
     DLSH_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(int) * K * T, st), "dlsh_mod_update: cnt");
   }
-  scan_kernel<<<1, 1024, 0, st>>>(w.cnt, static_cast<int64_t>(K) * T, K, T, w.off, w.atom_start);
-  if (N > 0)
+  atom_total_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_total);
+  atom_scan_kernel<<<1, 1024, 0, st>>>(w.atom_total, K, w.atom_start);
+  tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
+  launches += (N > 0 ? 1 : 0) + 3;
+  if (N > 0) {
     scatter_kernel<<<T, 32, K * sizeof(int), st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list_sig,
-                                                  w.list_coef);
-  const size_t asm_bytes = accum_smem(K);
+                                                  w.list_coef, w.list_nnz);
+    ++launches;
+  }
   DLSH_CUDA_TRY(cudaFuncSetAttribute(accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(asm_bytes)),
+                                     static_cast<int>(acc_smem)),
                 "dlsh_mod_update: attribute");
-  accum_kernel<<<K, ACC_WARPS * 32, asm_bytes, st>>>(X, idx, coef, nnz, s, K, w.atom_start,
-                                                     w.list_sig, w.list_coef, w.M, w.Z);
+  accum_kernel<<<K, acc_nw * 32, acc_smem, st>>>(X, reinterpret_cast<const uint32_t*>(idx), coef, s,
+                                                 K, w.atom_start, w.list_sig, w.list_coef,
+                                                 w.list_nnz, w.M, w.Z);
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
-  for (int k0 = 0; k0 < K; k0 += NB) {
-    potrf_diag_kernel<<<1, dim3(32, 32), 0, st>>>(w.M, K, k0, w.status);
+  launches += 2;
+  const int nblk = (K + NB - 1) / NB;
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k0 = kb * NB;
+    potrf_diag_kernel<<<1, dim3(32, 32), 0, st>>>(w.M, K, k0, w.Linv, w.status);
+    ++launches;
     const int rest = K - k0 - NB;
     if (rest > 0) {
       trsm_panel_kernel<<<(rest + 127) / 128, 128, 0, st>>>(w.M, K, k0);
       const int tiles = (rest + 31) / 32;
       syrk_kernel<<<dim3(tiles, tiles), dim3(32, 8), 0, st>>>(w.M, K, k0);
+      launches += 2;
     }
   }
-  for (int k0 = 0; k0 < K; k0 += NB) fwd_block_kernel<<<DLSH_D, 32, 0, st>>>(w.M, w.Z, K, k0);
-  for (int k0 = ((K - 1) / NB) * NB; k0 >= 0; k0 -= NB)
-    bwd_block_kernel<<<DLSH_D, 32, 0, st>>>(w.M, w.Z, K, k0);
-  normalise_kernel<<<(K + 7) / 8, 256, 0, st>>>(w.Z, w.atom_start, K, D_new, D_old, w.dead);
-  if (resid && N > 0) refill_kernel<<<1, 1024, 0, st>>>(X, resid, N, K, w.dead, D_new);
-  const int nblk = (K + NB - 1) / NB;
-  count_launches((N > 0 ? 3 : 1) + 3 + (3 * nblk - 2) + 2 * nblk + 1 + ((resid && N > 0) ? 1 : 0));
+  for (int kb = 0; kb < nblk; ++kb)
+    fwd_step_kernel<<<dim3(nblk - kb, 3), dim3(15, NB), 0, st>>>(w.M, w.Linv, w.Z, w.Yb, K, kb);
+  for (int kb = nblk - 1; kb >= 0; --kb)
+    bwd_step_kernel<<<dim3(kb + 1, 3), dim3(15, NB), 0, st>>>(w.M, w.Linv, w.Yb, w.Xb, K, kb);
+  normalise_kernel<<<(K + 7) / 8, 256, 0, st>>>(w.Xb, w.atom_start, K, D_new, D_old, w.dead);
+  launches += 2 * nblk + 1;
+  if (resid && N > 0) {
+    refill_kernel<<<1, 1024, 0, st>>>(X, resid, N, K, w.dead, D_new);
+    ++launches;
+  }
+  count_launches(launches);
   return check_launch("dlsh_mod_update: launch");
 }
 
@@ -557,6 +763,8 @@ int dlsh_mod_update(const float* X, int64_t N, int d, int K, const uint16_t* idx
   if (N < 0 || N * s >= (1LL << 31))
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mod_update: N*s must be < 2^31");
   if (!D_old || !D_new) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_mod_update: NULL D");
+  if (reinterpret_cast<uintptr_t>(idx) % 4 != 0)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_mod_update: idx must be 4-byte aligned");
   if (N > 0 && (!X || !idx || !coef || !nnz))
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_mod_update: NULL array");
   int rc = check_workspace(ws, ws_bytes, mod_ws_bytes(K, s, N), "dlsh_mod_update");
