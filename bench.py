@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--precision", default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     return ap.parse_args()
 
 
@@ -156,6 +157,68 @@ def cpu_oracle_rate(X, init, K, s, budget_s=15.0):
                       f"{dt:.1f} s"}
 
 
+def learned_leg(api, synth, D, X, s, K, cal_tau=1.01, n_train=2_000_000, n_cal=200_000,
+                epochs=10, batch=8192, lr=1e-2, seed=7):
+    """The learned encoder against plain FP32 OMP at (near) equal RMSE.
+
+    The MLP is trained by the library's own kernels on (signal, OMP support)
+    pairs the codec generates: n_train fresh signals from the same hidden
+    dictionary, encoded with the current dictionary D.  The fallback threshold
+    tau is calibrated on another fresh n_cal signals so that the deployed RMSE
+    stays within cal_tau of plain OMP's; then both encoders are timed on X (the
+    held-out scene, inputs resident)."""
+    import numpy as np
+    import torch
+    Dh = synth.hidden_dictionary(K, 0, rho=0.6)
+    Xtr = torch.from_numpy(synth.signals(n_train, Dh, s, seed)).cuda()
+    itr, _, ntr, _ = api.encode(D, Xtr, s, sync=True)
+    net = api.MLP(K, synth.mlp_params(K, seed))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = net.train(Xtr, itr, ntr, epochs=epochs, batch=batch, lr=lr)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del Xtr, itr, ntr
+    Xc = torch.from_numpy(synth.signals(n_cal, Dh, s, seed + 1)).cuda()
+    _, _, _, rp_c = api.encode(D, Xc, s, sync=True)
+    cand = net.propose(Xc, 2 * s)
+    _, _, _, rr_c = api.encode_restricted(D, Xc, cand, s)
+    tau = api.calibrate_fallback(rr_c, rp_c, cal_tau)
+    del Xc, cand
+
+    N = X.shape[0]
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            r = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, r
+
+    ms_plain, (_, _, _, rp) = timed(lambda: api.encode(D, X, s, precision="fp32"))
+    ms_l, (_, _, _, rl, nfb) = timed(lambda: api.encode_learned(D, X, s, net, mode="deploy", tau=tau,
+                                                               fallback_precision="bf16"))
+    ms_b, (_, _, _, rb) = timed(lambda: api.encode(D, X, s, precision="bf16"))
+    rm = lambda r: float(np.sqrt(r.double().sum().item() / (N * 45)))
+    l = losses.float().cpu().numpy()
+    return {
+        "train_pairs": n_train, "train_epochs": epochs, "train_s": train_s,
+        "train_loss_first_last": [float(l[:20].mean()), float(l[-20:].mean())],
+        "tau": tau, "fallback_rate": int(nfb.item()) / N,
+        "learned_bf16_gaussians_per_s": N / (ms_l * 1e-3),
+        "plain_fp32_gaussians_per_s": N / (ms_plain * 1e-3),
+        "plain_bf16_gaussians_per_s": N / (ms_b * 1e-3),
+        "rmse_learned": rm(rl), "rmse_plain_fp32": rm(rp), "rmse_plain_bf16": rm(rb),
+        "speedup_learned_vs_plain_fp32": ms_plain / ms_l,
+    }
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -181,7 +244,7 @@ def main():
     import numpy as np
     import torch
 
-    from paper_2605_30396_gb300 import _lib, api
+    from paper_2605_30396_gb300 import _lib, api, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -291,6 +354,13 @@ def main():
         e2e = {"value": N / dt, "unit": "Gaussians/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
+    learned = None
+    if not a.no_learned:
+        learned = learned_leg(api, synth, Dcur, X, s, K)
+        learned["workload"] = ("MLP 45-256-256-%d trained on 2M fresh (signal, OMP support) pairs; "
+                               "learned proposal (2s candidates) + restricted OMP + BF16 plain-OMP "
+                               "fallback on the %d scene signals" % (K, N))
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_oracle_rate(X_np, init, K, s)
@@ -312,7 +382,8 @@ def main():
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cl,
         "detail": {"encode_ms": enc_ms, "encode_gaussians_per_s": N / (enc_ms * 1e-3),
                    "mod_ms": mod_ms, "decode_ms": dec_ms, "decode_GBps": dec_gbs,
-                   "decode_hbm_frac": dec_gbs / float(peaks["hbm_gbs"]), "rmse": rmse},
+                   "decode_hbm_frac": dec_gbs / float(peaks["hbm_gbs"]), "rmse": rmse,
+                   "learned": learned},
     }
     if rank == 0:
         print(json.dumps(line))

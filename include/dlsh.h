@@ -95,6 +95,20 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                 void* stream, int flags);
 
 /*
+ * dlsh_encode with per-phase timing: identical results, plus six counters in
+ * `cycles` (device, uint64[6], zeroed by the call) summed over the first
+ * selection/solver thread of every CTA, in SM clock cycles: waiting for the
+ * tensor cores, the selection phase (including that wait), the barrier after
+ * selection, the solver phase, the barrier after the solver, and the number of
+ * OMP iterations counted.
+ */
+int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
+                        int s, float eps, int precision, uint16_t* idx,
+                        float* coef, uint8_t* nnz, float* resid_sq, void* ws,
+                        size_t ws_bytes, unsigned long long* cycles, void* stream,
+                        int flags);
+
+/*
  * dlsh_encode without a workspace and without any allocation.  The paper has no
  * counterpart: this exists for callers that cannot allocate device memory, such
  * as plugins whose host application owns every device allocation through its
@@ -183,6 +197,112 @@ int dlsh_learn_dictionary(const float* X, int64_t N, int d, int K, int s,
                           int precision, float* D_out, uint16_t* idx,
                           float* coef, uint8_t* nnz, float* rmse, void* ws,
                           size_t ws_bytes, void* stream, int flags);
+
+/* ---- many scenes in one call ---------------------------------------------
+ * Several independent encoding problems (one per scene: its own dictionary D,
+ * K, signals X [N x 45], s and eps; outputs as in dlsh_encode) in one call.
+ * Each scene is encoded exactly as dlsh_encode would encode it (same plan, so
+ * bitwise the same codes), on internal streams forked from `stream` and joined
+ * back to it: scenes run concurrently, the most expensive (N*K*s) first.
+ * precision: FP32, BF16 or FP8 for every scene; bn: 0 (tuned/default) or 64 /
+ * 128 to force the atom-chunk width of FP32 scenes.  At most 32 scenes,
+ * s <= 16; scenes with N = 0 are skipped.  The call enqueues only kernels and
+ * event record/wait (no host copies), so it can be captured into a CUDA graph;
+ * the scene table is read at enqueue time.  Workspace: see
+ * dlsh_encode_multi_workspace_size (0 = invalid scene table). */
+typedef struct dlsh_scene {
+  const float* D;   /* K x 45 */
+  int K;
+  const float* X;   /* N x 45 */
+  int64_t N;
+  int s;
+  float eps;
+  uint16_t* idx;    /* N x s */
+  float* coef;      /* N x s */
+  uint8_t* nnz;     /* N */
+  float* resid_sq;  /* N, may be NULL */
+} dlsh_scene;
+size_t dlsh_encode_multi_workspace_size(const dlsh_scene* scenes, int n, int precision, int bn);
+int dlsh_encode_multi(const dlsh_scene* scenes, int n, int precision, int bn, void* ws,
+                      size_t ws_bytes, void* stream, int flags);
+
+/* Autotuner: times dlsh_encode on the caller's sample at every admissible
+ * atom-chunk width (64 or 128 atoms per MMA) and records the fastest for
+ * (K, s, precision); later plans use it.  With DLSH_AUTOTUNE_CACHE set to a file
+ * path the table is kept there as JSON lines and read back at first use.
+ * Outputs are scratch of the sample's size; *best_bn (host, may be NULL). */
+int dlsh_autotune_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
+                         int precision, uint16_t* idx, float* coef, uint8_t* nnz,
+                         float* resid_sq, void* ws, size_t ws_bytes, void* stream, int* best_bn);
+
+/* ---- learned support proposal ------------------------------------------
+ * An extension of the paper's plain OMP (Sec. 2.1): a 45 -> 256 -> 256 -> K MLP
+ *   xn = x/||x|| (0 if x = 0); h1 = gelu(W1 xn + b1); h2 = gelu(W2 h1 + b2);
+ *   z = W3 h2 + b3;  gelu(u) = u Phi(u) (exact erf form)
+ * trained with mean BCE-with-logits against the multi-hot OMP support and Adam
+ * (beta 0.9/0.999, eps 1e-8, FP32 master weights, BF16 weights in every GEMM,
+ * FP32 accumulation on tcgen05).  Its 2s largest logits (ties: smaller index)
+ * are the candidates of an OMP restricted to them; plain OMP is the fallback.
+ *
+ * Parameters live in a caller-owned blob of dlsh_mlp_size(K) bytes (256-byte
+ * aligned).  The parameter vector (dlsh_mlp_num_params(K) floats) is, in order:
+ * W1 [256 x 64] (input padded from 45 to 64; columns 45..63 are zero), b1
+ * [256], W2 [256 x 256], b2 [256], W3 [K x 256], b3 [K], all row-major. */
+long long dlsh_mlp_num_params(int K);
+size_t dlsh_mlp_size(int K);
+/* Batch workspace for forward / gradients / training with batches of B rows. */
+size_t dlsh_mlp_workspace_size(int K, int64_t B);
+/* Sets the parameters from `params` (device FP32) and zeroes the Adam state. */
+int dlsh_mlp_init(void* mlp, int K, const float* params, void* stream, int flags);
+/* Copies the FP32 parameter vector out (device). */
+int dlsh_mlp_params(const void* mlp, int K, float* params, void* stream, int flags);
+/* Logits [B x K] of the signals X [B x 45]. */
+int dlsh_mlp_forward(const void* mlp, int K, const float* X, int64_t B, float* logits,
+                     void* ws, size_t ws_bytes, void* stream, int flags);
+/* Gradients of the mean BCE loss (layout of the parameter vector) for the
+ * targets given as ELL supports (idx [B x s], nnz [B]); loss (device, 1). */
+int dlsh_mlp_gradients(const void* mlp, int K, const float* X, int64_t B,
+                       const uint16_t* idx, const uint8_t* nnz, int s, float* grads,
+                       float* loss, void* ws, size_t ws_bytes, void* stream, int flags);
+/* One Adam step (step counts from 1) on one batch. */
+int dlsh_mlp_train_step(void* mlp, int K, const float* X, int64_t B, const uint16_t* idx,
+                        const uint8_t* nnz, int s, float lr, int64_t step, float* loss,
+                        void* ws, size_t ws_bytes, void* stream, int flags);
+/* `epochs` passes over N signals in consecutive batches (N / batch per epoch),
+ * learning rate lr * (1 + cos(pi t / T)) / 2; loss_per_step (device, may be
+ * NULL) receives every step's loss.  Workspace: dlsh_mlp_workspace_size(K, batch). */
+int dlsh_mlp_train(void* mlp, int K, const float* X, int64_t N, const uint16_t* idx,
+                   const uint8_t* nnz, int s, int epochs, int64_t batch, float lr,
+                   float* loss_per_step, void* ws, size_t ws_bytes, void* stream, int flags);
+/* The m (2, 4, 8, 16 or 32) largest logits of every signal, largest first:
+ * cand [N x m] uint16 atom indices. */
+size_t dlsh_mlp_propose_workspace_size(int K, int64_t N);
+int dlsh_mlp_propose(const void* mlp, int K, const float* X, int64_t N, int m,
+                     uint16_t* cand, void* ws, size_t ws_bytes, void* stream, int flags);
+/* OMP restricted to each signal's m candidate atoms (s <= m <= 32): the same
+ * greedy steps, stop rules and outputs as dlsh_encode, the argmax taken over the
+ * candidates only (ties: smaller atom index).  Workspace:
+ * dlsh_encode_workspace_size(K, d, s, DLSH_PREC_FP32). */
+int dlsh_encode_restricted(const float* D, int K, int d, const float* X, int64_t N,
+                           const uint16_t* cand, int m, int s, float eps, uint16_t* idx,
+                           float* coef, uint8_t* nnz, float* resid_sq, void* ws,
+                           size_t ws_bytes, void* stream, int flags);
+/* Learned encoder: MLP proposal of 2s candidates, restricted OMP, and plain OMP
+ * (at fallback_precision) as the fallback.  mode 0 ("exact"): plain OMP runs on
+ * every signal and replaces the learned code when ||r_learned|| > ||r_plain|| *
+ * (1 + 1e-6).  mode 1 ("deploy"): plain OMP runs only on the signals with
+ * ||r_learned|| > tau.  n_fallback (device, uint64) receives the count. */
+size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N);
+int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N, int s,
+                        float eps, const void* mlp, int mode, float tau,
+                        int fallback_precision, uint16_t* idx, float* coef, uint8_t* nnz,
+                        float* resid_sq, unsigned long long* n_fallback, void* ws,
+                        size_t ws_bytes, void* stream, int flags);
+/* Deploy-mode threshold from a calibration set: the tau whose fallback set is
+ * the smallest that keeps sqrt(sum r) within max_ratio of plain OMP's, given
+ * both residual vectors (device); *tau is written on the host. */
+int dlsh_calibrate_fallback(const float* resid_learned, const float* resid_plain, int64_t N,
+                            float max_ratio, float* tau, void* stream);
 
 /*
  * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in

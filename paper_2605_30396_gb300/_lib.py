@@ -15,6 +15,14 @@ _LIB = None
 c_int, c_int64, c_float, c_size_t = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_size_t
 P = ctypes.c_void_p
 
+class Scene(ctypes.Structure):
+    """Mirror of dlsh_scene."""
+    _fields_ = [("D", ctypes.c_void_p), ("K", ctypes.c_int), ("X", ctypes.c_void_p),
+                ("N", ctypes.c_int64), ("s", ctypes.c_int), ("eps", ctypes.c_float),
+                ("idx", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("nnz", ctypes.c_void_p),
+                ("resid_sq", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "dlsh_last_error": (ctypes.c_char_p, []),
     "dlsh_version": (c_int, []),
@@ -23,6 +31,8 @@ SIGNATURES = {
     "dlsh_encode_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),
     "dlsh_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P, P,
                             c_size_t, P, c_int]),
+    "dlsh_encode_profile": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P,
+                                    P, c_size_t, P, P, c_int]),
     "dlsh_encode_noalloc_max_bytes": (c_size_t, []),
     "dlsh_encode_noalloc": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P,
                                     P, P, c_int]),
@@ -35,6 +45,29 @@ SIGNATURES = {
     "dlsh_learn_dictionary": (c_int, [P, c_int64, c_int, c_int, c_int, c_float, c_int, P, c_int,
                                       P, P, P, P, P, P, c_size_t, P, c_int]),
     "dlsh_init_dictionary": (c_int, [P, c_int64, c_int, P, c_int, P, P, c_int]),
+    "dlsh_mlp_num_params": (ctypes.c_longlong, [c_int]),
+    "dlsh_mlp_size": (c_size_t, [c_int]),
+    "dlsh_mlp_workspace_size": (c_size_t, [c_int, c_int64]),
+    "dlsh_mlp_init": (c_int, [P, c_int, P, P, c_int]),
+    "dlsh_mlp_params": (c_int, [P, c_int, P, P, c_int]),
+    "dlsh_mlp_forward": (c_int, [P, c_int, P, c_int64, P, P, c_size_t, P, c_int]),
+    "dlsh_mlp_gradients": (c_int, [P, c_int, P, c_int64, P, P, c_int, P, P, P, c_size_t, P, c_int]),
+    "dlsh_mlp_train_step": (c_int, [P, c_int, P, c_int64, P, P, c_int, c_float, c_int64, P, P,
+                                    c_size_t, P, c_int]),
+    "dlsh_mlp_train": (c_int, [P, c_int, P, c_int64, P, P, c_int, c_int, c_int64, c_float, P, P,
+                               c_size_t, P, c_int]),
+    "dlsh_mlp_propose_workspace_size": (c_size_t, [c_int, c_int64]),
+    "dlsh_mlp_propose": (c_int, [P, c_int, P, c_int64, c_int, P, P, c_size_t, P, c_int]),
+    "dlsh_encode_restricted": (c_int, [P, c_int, c_int, P, c_int64, P, c_int, c_int, c_float, P, P,
+                                       P, P, P, c_size_t, P, c_int]),
+    "dlsh_encode_learned_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
+    "dlsh_encode_learned": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, P, c_int, c_float,
+                                    c_int, P, P, P, P, P, P, c_size_t, P, c_int]),
+    "dlsh_calibrate_fallback": (c_int, [P, P, c_int64, c_float, P, P]),
+    "dlsh_encode_multi_workspace_size": (c_size_t, [P, c_int, c_int, c_int]),
+    "dlsh_encode_multi": (c_int, [P, c_int, c_int, c_int, P, c_size_t, P, c_int]),
+    "dlsh_autotune_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_int, P, P, P, P, P,
+                                     c_size_t, P, P]),
     "dlsh_csc_workspace_size": (c_size_t, [c_int64]),
     "dlsh_csc_from_ell": (c_int, [P, P, P, c_int64, c_int, P, P, P, P, c_size_t, P, c_int]),
 }

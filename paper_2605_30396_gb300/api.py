@@ -109,6 +109,27 @@ def encode(D, X, s: int, eps: float = 0.0, precision="fp32", sync: bool = False,
     return idx, coef, nnz, resid
 
 
+def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
+    """encode() plus per-phase SM-cycle counters of the encoder (see dlsh.h)."""
+    D = _to_device(D, torch.float32)
+    X = _to_device(X, torch.float32)
+    N, K = X.shape[0], D.shape[0]
+    idx = torch.empty((N, s), dtype=torch.int16, device=X.device)
+    coef = torch.empty((N, s), dtype=torch.float32, device=X.device)
+    nnz = torch.empty((N,), dtype=torch.uint8, device=X.device)
+    resid = torch.empty((N,), dtype=torch.float32, device=X.device)
+    cyc = torch.zeros((6,), dtype=torch.int64, device=X.device)
+    L = _lib.lib()
+    need = L.dlsh_encode_workspace_size(K, D.shape[1], s, _prec(precision))
+    ws = workspace(need, key="encode")
+    rc = L.dlsh_encode_profile(_p(D), K, D.shape[1], _p(X), N, s, float(eps), _prec(precision),
+                               _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws), ws.numel(), _p(cyc),
+                               _stream(), FLAG_SYNC)
+    _check(rc, "dlsh_encode_profile")
+    names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations")
+    return (idx, coef, nnz, resid), dict(zip(names, cyc.cpu().tolist()))
+
+
 def correlate(D, R, precision="fp32", sync: bool = True):
     """C = R D^T on the encoder's tensor-core path."""
     D = _dev_f32(D)
@@ -218,3 +239,223 @@ def csc_from_ell(idx, coef, nnz, sync: bool = False):
     _check(rc, "dlsh_csc_from_ell")
     total = int(col_ptr[-1].item())
     return col_ptr, row_idx[:total], val[:total]
+
+
+# ---- learned support proposal --------------------------------------------------
+HIDDEN = 256
+X_IN = 64
+
+
+def mlp_num_params(K: int) -> int:
+    return int(_lib.lib().dlsh_mlp_num_params(K))
+
+
+def mlp_pack(params: dict, K: int) -> torch.Tensor:
+    """Flattens {W1 (256,45 or 64), b1, W2, b2, W3 (K,256), b3} into the C ABI's
+    parameter vector (FP32, W1 zero-padded to 64 input columns)."""
+    W1 = torch.as_tensor(params["W1"], dtype=torch.float32)
+    if W1.shape[1] < X_IN:
+        W1 = torch.nn.functional.pad(W1, (0, X_IN - W1.shape[1]))
+    parts = [W1, params["b1"], params["W2"], params["b2"], params["W3"], params["b3"]]
+    vec = torch.cat([torch.as_tensor(p, dtype=torch.float32).reshape(-1) for p in parts])
+    assert vec.numel() == mlp_num_params(K)
+    return vec
+
+
+def mlp_unpack(vec: torch.Tensor, K: int) -> dict:
+    v = vec.detach().to("cpu", torch.float64)
+    o = 0
+    out = {}
+    for name, shape in (("W1", (HIDDEN, X_IN)), ("b1", (HIDDEN,)), ("W2", (HIDDEN, HIDDEN)),
+                        ("b2", (HIDDEN,)), ("W3", (K, HIDDEN)), ("b3", (K,))):
+        n = 1
+        for d in shape:
+            n *= d
+        out[name] = v[o:o + n].reshape(shape).numpy()
+        o += n
+    return out
+
+
+class MLP:
+    """Device-resident support-proposal network (parameters + Adam state)."""
+
+    def __init__(self, K: int, params: dict):
+        self.K = K
+        L = _lib.lib()
+        self.blob = torch.empty(L.dlsh_mlp_size(K), dtype=torch.uint8, device="cuda")
+        vec = mlp_pack(params, K).cuda()
+        _check(L.dlsh_mlp_init(_p(self.blob), K, _p(vec), _stream(), FLAG_SYNC), "dlsh_mlp_init")
+        self.step = 0
+
+    def params(self) -> torch.Tensor:
+        out = torch.empty(mlp_num_params(self.K), dtype=torch.float32, device="cuda")
+        _check(_lib.lib().dlsh_mlp_params(_p(self.blob), self.K, _p(out), _stream(), FLAG_SYNC),
+               "dlsh_mlp_params")
+        return out
+
+    def _ws(self, B):
+        return workspace(_lib.lib().dlsh_mlp_workspace_size(self.K, B), key="mlp")
+
+    def forward(self, X):
+        X = _dev_f32(X)
+        B = X.shape[0]
+        out = torch.empty((B, self.K), dtype=torch.float32, device="cuda")
+        ws = self._ws(B)
+        _check(_lib.lib().dlsh_mlp_forward(_p(self.blob), self.K, _p(X), B, _p(out), _p(ws),
+                                           ws.numel(), _stream(), FLAG_SYNC), "dlsh_mlp_forward")
+        return out
+
+    def gradients(self, X, idx, nnz):
+        X = _dev_f32(X)
+        B, s = idx.shape
+        g = torch.empty(mlp_num_params(self.K), dtype=torch.float32, device="cuda")
+        loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+        ws = self._ws(B)
+        _check(_lib.lib().dlsh_mlp_gradients(_p(self.blob), self.K, _p(X), B, _p(idx.contiguous()),
+                                             _p(nnz.contiguous()), s, _p(g), _p(loss), _p(ws),
+                                             ws.numel(), _stream(), FLAG_SYNC), "dlsh_mlp_gradients")
+        return g, float(loss.item())
+
+    def train_step(self, X, idx, nnz, lr: float):
+        X = _dev_f32(X)
+        B, s = idx.shape
+        self.step += 1
+        loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+        ws = self._ws(B)
+        _check(_lib.lib().dlsh_mlp_train_step(_p(self.blob), self.K, _p(X), B, _p(idx.contiguous()),
+                                              _p(nnz.contiguous()), s, float(lr), self.step,
+                                              _p(loss), _p(ws), ws.numel(), _stream(), FLAG_SYNC),
+               "dlsh_mlp_train_step")
+        return float(loss.item())
+
+    def train(self, X, idx, nnz, epochs: int, batch: int, lr: float, sync: bool = True):
+        X = _dev_f32(X)
+        N, s = idx.shape
+        steps = (N // batch) * epochs
+        losses = torch.empty((max(steps, 1),), dtype=torch.float32, device="cuda")
+        ws = self._ws(batch)
+        _check(_lib.lib().dlsh_mlp_train(_p(self.blob), self.K, _p(X), N, _p(idx.contiguous()),
+                                         _p(nnz.contiguous()), s, epochs, batch, float(lr),
+                                         _p(losses), _p(ws), ws.numel(), _stream(),
+                                         FLAG_SYNC if sync else 0), "dlsh_mlp_train")
+        self.step += steps
+        return losses[:steps]
+
+    def propose(self, X, m: int):
+        X = _dev_f32(X)
+        N = X.shape[0]
+        cand = torch.empty((N, m), dtype=torch.int16, device="cuda")
+        ws = workspace(_lib.lib().dlsh_mlp_propose_workspace_size(self.K, N), key="propose")
+        _check(_lib.lib().dlsh_mlp_propose(_p(self.blob), self.K, _p(X), N, m, _p(cand), _p(ws),
+                                           ws.numel(), _stream(), FLAG_SYNC), "dlsh_mlp_propose")
+        return cand
+
+
+def encode_restricted(D, X, cand, s: int, eps: float = 0.0, sync: bool = True):
+    D = _dev_f32(D)
+    X = _dev_f32(X)
+    N, m = cand.shape
+    K = D.shape[0]
+    idx = torch.empty((N, s), dtype=torch.int16, device="cuda")
+    coef = torch.empty((N, s), dtype=torch.float32, device="cuda")
+    nnz = torch.empty((N,), dtype=torch.uint8, device="cuda")
+    resid = torch.empty((N,), dtype=torch.float32, device="cuda")
+    L = _lib.lib()
+    ws = workspace(L.dlsh_encode_workspace_size(K, D_SH, s, 0), key="encode")
+    _check(L.dlsh_encode_restricted(_p(D), K, D_SH, _p(X), N, _p(cand.contiguous()), m, s,
+                                    float(eps), _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws),
+                                    ws.numel(), _stream(), FLAG_SYNC if sync else 0),
+           "dlsh_encode_restricted")
+    return idx, coef, nnz, resid
+
+
+def encode_learned(D, X, s: int, mlp: "MLP", mode: str = "deploy", tau: float = 0.0,
+                   eps: float = 0.0, fallback_precision="fp32", sync: bool = False, out=None):
+    """Learned proposal + restricted OMP + plain-OMP fallback.  Returns
+    (idx, coef, nnz, resid_sq, n_fallback_tensor)."""
+    host = not X.is_cuda
+    D = _to_device(D, torch.float32)
+    X = _to_device(X, torch.float32)
+    N, K = X.shape[0], D.shape[0]
+    if out is None:
+        idx = torch.empty((N, s), dtype=torch.int16, device="cuda")
+        coef = torch.empty((N, s), dtype=torch.float32, device="cuda")
+        nnz = torch.empty((N,), dtype=torch.uint8, device="cuda")
+        resid = torch.empty((N,), dtype=torch.float32, device="cuda")
+    else:
+        idx, coef, nnz, resid = out
+    nfb = torch.zeros((1,), dtype=torch.int64, device="cuda")
+    L = _lib.lib()
+    need = L.dlsh_encode_learned_workspace_size(K, D_SH, s, N)
+    if need == 0:
+        raise DlshError(-2, "dlsh_encode_learned_workspace_size")
+    ws = workspace(need, key="learned")
+    _check(L.dlsh_encode_learned(_p(D), K, D_SH, _p(X), N, s, float(eps), _p(mlp.blob),
+                                 0 if mode == "exact" else 1, float(tau), _prec(fallback_precision),
+                                 _p(idx), _p(coef), _p(nnz), _p(resid), _p(nfb), _p(ws), ws.numel(),
+                                 _stream(), FLAG_SYNC if sync else 0), "dlsh_encode_learned")
+    if host:
+        return tuple(t.to("cpu") for t in (idx, coef, nnz, resid, nfb))
+    return idx, coef, nnz, resid, nfb
+
+
+def calibrate_fallback(resid_learned, resid_plain, max_ratio: float = 1.01) -> float:
+    tau = ctypes.c_float(0.0)
+    _check(_lib.lib().dlsh_calibrate_fallback(_p(resid_learned.contiguous()),
+                                              _p(resid_plain.contiguous()), resid_learned.numel(),
+                                              float(max_ratio), ctypes.byref(tau), _stream()),
+           "dlsh_calibrate_fallback")
+    return float(tau.value)
+
+
+# ---- many scenes in one call, autotuner ------------------------------------------
+def encode_multi(scenes, precision="fp32", bn: int = 0, sync: bool = False):
+    """scenes: list of dicts {D (K,45), X (N,45), s, eps=0}.  Returns a list of
+    (idx, coef, nnz, resid_sq) per scene; the scenes are encoded concurrently on
+    streams forked from the current one (graph-capturable)."""
+    outs, keep, arr = [], [], (_lib.Scene * len(scenes))()
+    for i, sc in enumerate(scenes):
+        D = _dev_f32(sc["D"])
+        X = _dev_f32(sc["X"])
+        s = int(sc["s"])
+        N = X.shape[0]
+        o = (torch.empty((N, s), dtype=torch.int16, device="cuda"),
+             torch.empty((N, s), dtype=torch.float32, device="cuda"),
+             torch.empty((N,), dtype=torch.uint8, device="cuda"),
+             torch.empty((N,), dtype=torch.float32, device="cuda"))
+        keep += [D, X]
+        outs.append(o)
+        arr[i] = _lib.Scene(D.data_ptr(), D.shape[0], X.data_ptr(), N, s, float(sc.get("eps", 0.0)),
+                            o[0].data_ptr(), o[1].data_ptr(), o[2].data_ptr(), o[3].data_ptr())
+    L = _lib.lib()
+    need = L.dlsh_encode_multi_workspace_size(ctypes.byref(arr), len(scenes), _prec(precision), bn)
+    if need == 0:
+        raise DlshError(-2, "dlsh_encode_multi_workspace_size")
+    ws = workspace(need, key="multi")
+    _check(L.dlsh_encode_multi(ctypes.byref(arr), len(scenes), _prec(precision), bn, _p(ws),
+                               ws.numel(), _stream(), FLAG_SYNC if sync else 0), "dlsh_encode_multi")
+    if not sync:
+        _KEEPALIVE.append(keep)
+    return outs
+
+
+_KEEPALIVE = []
+
+
+def autotune_encode(D, X, s: int, precision="fp32") -> int:
+    """Times the encoder's admissible atom-chunk widths on this sample; returns the
+    winner (later encodes of the same K, s, precision use it)."""
+    D = _dev_f32(D)
+    X = _dev_f32(X)
+    N, K = X.shape[0], D.shape[0]
+    idx = torch.empty((N, s), dtype=torch.int16, device="cuda")
+    coef = torch.empty((N, s), dtype=torch.float32, device="cuda")
+    nnz = torch.empty((N,), dtype=torch.uint8, device="cuda")
+    resid = torch.empty((N,), dtype=torch.float32, device="cuda")
+    L = _lib.lib()
+    ws = workspace(L.dlsh_encode_workspace_size(K, D_SH, s, _prec(precision)), key="encode")
+    best = ctypes.c_int(0)
+    _check(L.dlsh_autotune_encode(_p(D), K, D_SH, _p(X), N, s, _prec(precision), _p(idx), _p(coef),
+                                  _p(nnz), _p(resid), _p(ws), ws.numel(), _stream(),
+                                  ctypes.byref(best)), "dlsh_autotune_encode")
+    return int(best.value)

@@ -3,34 +3,42 @@
 //
 // One CTA owns a tile of 128 signals (one per TMEM lane) and runs the s OMP
 // iterations of the tile to completion; CTAs are persistent over tiles.
-//   warp 5  TMA producer: streams the dictionary operand (pre-packed in the
-//           canonical no-swizzle UMMA layout) into a ring of shared-memory
-//           stages with cp.async.bulk; when the whole dictionary fits, it is
-//           loaded once and stays resident.
-//   warp 4  MMA issuer: per iteration and per chunk of BN atoms, one thread
-//           issues tcgen05.mma R(128 x 48) . D_chunk^T into a TMEM buffer
-//           (512 columns = 512/BN buffers, so MMAs run ahead of the epilogue).
-//   warps 0-3  epilogue/solver, thread i = signal i = TMEM lane i: reads its
-//           row of correlations with tcgen05.ld, keeps the running argmax
-//           (exact for FP32; top-4 with an FP32 re-score for BF16/FP8),
-//           extends the Cholesky factor of the support's Gram matrix, solves
-//           the least-squares system, recomputes r = x - D_I gamma in FP32 and
-//           writes r back as the next A operand.
+//   warp 17  TMA producer: streams the dictionary operand (pre-packed in the
+//            canonical no-swizzle UMMA layout) into a ring of shared-memory
+//            stages with cp.async.bulk; when the whole dictionary fits, it is
+//            loaded once and stays resident.
+//   warp 16  MMA issuer: per iteration and per chunk of BN atoms, one thread
+//            issues tcgen05.mma R(128 x 48) . D_chunk^T into a TMEM buffer
+//            (512 columns = 512/BN buffers, so MMAs run ahead of selection).
+//   warps 0-15  selection + solver, in two phases per iteration:
+//            selection: four threads per TMEM lane (one per column quarter)
+//            read the row's correlations with tcgen05.ld and keep the running
+//            argmax (exact for FP32; top 4 for BF16/FP8);
+//            solver: four sub-lanes per signal, each owning 12 of the 48 dims,
+//            merge the quarters (FP32 re-score of the top 4 for BF16/FP8),
+//            extend the Cholesky factor of the support's Gram matrix, solve
+//            the least-squares system, recompute r = x - D_I gamma in FP32 and
+//            write r back as the next A operand.
 // Correlation precisions: FP32 (3xTF32 split hi*hi + hi*lo + lo*hi, FP32
 // accumulate), BF16, FP8 E4M3 with per-row and per-atom scales.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "host.hpp"
+#include "internal.hpp"
 
 namespace dlsh {
 namespace enc {
 
 constexpr int TILE_M = 128;
 constexpr int DPAD = 48;  // FP32 copy of D: rows padded from 45 to 48 floats
-constexpr int NEPI = 128;
-constexpr int NTHREADS = 192;
+constexpr int NEPI = 512;      // selection/solver threads (16 warps)
+constexpr int NTHREADS = 576;  // + MMA warp + TMA producer warp
 constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in dynamic shared memory per CTA
 constexpr float CORR_STOP_REL = 1e-7f;
 constexpr float PIVOT_MIN = 1e-6f;
@@ -43,16 +51,23 @@ __host__ __device__ constexpr int op_parts(int prec) { return prec == 0 ? 2 : 1;
 struct Plan {
   int prec, BN, K, Kp, nchunks, stages, resident, s;
   uint32_t a_bytes, chunk_bytes;
-  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_sig, off_bar, smem;
+  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_rowt, off_cand, off_r,
+      off_sig, off_bar, smem;
 };
 
 inline int choose_bn(int prec, int s) { return (prec == 0 && s > 8) ? 64 : 128; }
 
-int make_plan(int K, int s, int prec, Plan& p, int smem_limit = SMEM_LIMIT) {
+// Atom-chunk widths picked by dlsh_autotune_encode, keyed by (K, s, precision).
+int tuned_bn(int K, int s, int prec);
+
+// bn = 0: the tuned width if one was recorded, else the default.  BF16 and FP8
+// use 128 (the selection's key network packs 32 columns per thread).
+int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM_LIMIT) {
   p.prec = prec;
   p.K = K;
   p.s = s;
-  p.BN = choose_bn(prec, s);
+  if (bn == 0) bn = tuned_bn(K, s, prec);
+  p.BN = prec != 0 ? 128 : (bn == 64 || bn == 128 ? bn : choose_bn(prec, s));
   p.nchunks = (K + p.BN - 1) / p.BN;
   p.Kp = p.nchunks * p.BN;
   p.a_bytes = TILE_M * op_kb(prec) * 16 * op_parts(prec);
@@ -64,11 +79,14 @@ int make_plan(int K, int s, int prec, Plan& p, int smem_limit = SMEM_LIMIT) {
     return o;
   };
   p.off_a = take(p.a_bytes);
-  p.off_x = take(DPAD * TILE_M * 4);
+  p.off_x = take(0);  // (the signal tile is read straight into registers)
   p.off_L = take(static_cast<uint32_t>(s * (s + 1) / 2) * TILE_M * 4);
   p.off_sel = take(s * TILE_M * 4);
   p.off_y = take(s * TILE_M * 4);
   p.off_g = take(s * TILE_M * 4);
+  p.off_rowt = take(TILE_M * 4);
+  p.off_cand = take(TILE_M * 4 * (prec == 0 ? 1 : 4) * 8);
+  p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
   p.off_sig = take(prec == 2 ? p.Kp * 4 : 0);
   p.off_bar = take(1024);
   const uint32_t fixed = (off + 1023u) & ~1023u;
@@ -85,6 +103,22 @@ int make_plan(int K, int s, int prec, Plan& p, int smem_limit = SMEM_LIMIT) {
   return DLSH_OK;
 }
 
+// The arrays and sizes one tile is encoded with.
+struct SceneDev {
+  const float* X;
+  long long N;
+  const uint8_t* img;
+  const float* D32p;
+  const float* G;
+  const float* sigma;
+  uint16_t* idx;
+  float* coef;
+  uint8_t* nnz;
+  float* resid;
+  int K, s, nchunks;
+  float eps;
+};
+
 struct Args {
   const float* X;
   int64_t N;
@@ -99,8 +133,30 @@ struct Args {
   float eps;
   uint32_t* status;
   long long budget;
+  unsigned long long* prof;  // optional: per-phase SM cycles of thread 0 (6 counters)
+  const long long* n_dev;    // optional: signal count read on the device (overrides N)
   Plan p;
 };
+
+// The arrays and sizes of tile `tile`.
+__device__ __forceinline__ void tile_scene(const Args& a, long long NS, int tile, SceneDev& sd,
+                                           int& lt) {
+  sd.X = a.X;
+  sd.N = NS;
+  sd.img = a.img;
+  sd.D32p = a.D32p;
+  sd.G = a.G;
+  sd.sigma = a.sigma;
+  sd.idx = a.idx;
+  sd.coef = a.coef;
+  sd.nnz = a.nnz;
+  sd.resid = a.resid_sq;
+  sd.K = a.p.K;
+  sd.s = a.p.s;
+  sd.nchunks = a.p.nchunks;
+  sd.eps = a.eps;
+  lt = tile;
+}
 
 // ---------------------------------------------------------------------------
 // Operand packing.  A row (signal i) occupies 16 bytes per K-block at
@@ -277,16 +333,135 @@ __global__ void gram_kernel(const float* __restrict__ D32p, int K, float* __rest
 }
 
 // ---------------------------------------------------------------------------
-// The encoder.
+// The encoder.  Per OMP iteration of a tile:
+//   phase 1 (selection): thread (warp w < 16, lane l) reads TMEM lane
+//     32*(w%4) + l, i.e. row R1 of the tile, over column quarter q = w/4 of
+//     every chunk, and keeps its best candidate(s) for that row and quarter;
+//   phase 2 (solver): thread (warp w, lane l) serves row R2 = 8w + l/4 with
+//     sub-lane u = l%4 owning signal dims [12u, 12u+12); the four sub-lanes
+//     of a row run the same scalar recurrences (bitwise identical values) and
+//     combine dot products with two butterfly shuffles.
 // ---------------------------------------------------------------------------
+template <int PREC>
+__device__ __forceinline__ void write_a_part(uint8_t* A, int row, int u, const float (&r)[12],
+                                             float inv_rho) {
+  constexpr uint32_t LBO = TILE_M * 16;
+  if constexpr (PREC == 1) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = 12 * u + 4 * k;
+      uint2 pk;
+      pk.x = pack_bf16x2(r[4 * k + 0], r[4 * k + 1]);
+      pk.y = pack_bf16x2(r[4 * k + 2], r[4 * k + 3]);
+      *reinterpret_cast<uint2*>(A + (e >> 3) * LBO + row * 16 + (e & 7) * 2) = pk;
+    }
+  } else if constexpr (PREC == 0) {
+    constexpr uint32_t PART = TILE_M * 12 * 16;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int kb = 3 * u + k;
+      float4 hi, lo;
+      hi.x = to_tf32(r[4 * k + 0]);
+      hi.y = to_tf32(r[4 * k + 1]);
+      hi.z = to_tf32(r[4 * k + 2]);
+      hi.w = to_tf32(r[4 * k + 3]);
+      lo.x = to_tf32(r[4 * k + 0] - hi.x);
+      lo.y = to_tf32(r[4 * k + 1] - hi.y);
+      lo.z = to_tf32(r[4 * k + 2] - hi.z);
+      lo.w = to_tf32(r[4 * k + 3] - hi.w);
+      *reinterpret_cast<float4*>(A + kb * LBO + row * 16) = hi;
+      *reinterpret_cast<float4*>(A + PART + kb * LBO + row * 16) = lo;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = 12 * u + 4 * k;
+      const uint32_t w = pack_e4m3x4(r[4 * k] * inv_rho, r[4 * k + 1] * inv_rho,
+                                     r[4 * k + 2] * inv_rho, r[4 * k + 3] * inv_rho);
+      *reinterpret_cast<uint32_t*>(A + (e >> 4) * LBO + row * 16 + (e & 15)) = w;
+    }
+  }
+}
+
+// Butterfly over the four sub-lanes of one row (lanes 4k..4k+3).  Only those
+// four lanes take part, so rows of one warp may sit on different branches.
+__device__ __forceinline__ unsigned quad_mask() {
+  return 0xFu << ((threadIdx.x & 31) & ~3u);
+}
+__device__ __forceinline__ float quad_sum(float v) {
+  const unsigned m = quad_mask();
+  v += __shfl_xor_sync(m, v, 1);
+  v += __shfl_xor_sync(m, v, 2);
+  return v;
+}
+__device__ __forceinline__ float quad_max(float v) {
+  const unsigned m = quad_mask();
+  v = fmaxf(v, __shfl_xor_sync(m, v, 1));
+  v = fmaxf(v, __shfl_xor_sync(m, v, 2));
+  return v;
+}
+
+// Inserts (v, j) into a list sorted by (value desc, index asc) of length 4.
+__device__ __forceinline__ void top4_insert(float (&tv)[4], int (&tj)[4], float v, int j) {
+  auto before = [](float a, int ja, float b, int jb) { return a > b || (a == b && ja < jb); };
+  if (!before(v, j, tv[3], tj[3])) return;
+  if (before(v, j, tv[0], tj[0])) {
+    tv[3] = tv[2]; tj[3] = tj[2]; tv[2] = tv[1]; tj[2] = tj[1]; tv[1] = tv[0]; tj[1] = tj[0];
+    tv[0] = v; tj[0] = j;
+  } else if (before(v, j, tv[1], tj[1])) {
+    tv[3] = tv[2]; tj[3] = tj[2]; tv[2] = tv[1]; tj[2] = tj[1];
+    tv[1] = v; tj[1] = j;
+  } else if (before(v, j, tv[2], tj[2])) {
+    tv[3] = tv[2]; tj[3] = tj[2];
+    tv[2] = v; tj[2] = j;
+  } else {
+    tv[3] = v; tj[3] = j;
+  }
+}
+
+template <int NC>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]);
+template <>
+__device__ __forceinline__ void tmem_ld_cols<32>(uint32_t taddr, float (&v)[32]) {
+  tmem_ld32(taddr, v);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_cols<16>(uint32_t taddr, float (&v)[16]) {
+  tmem_ld16(taddr, v);
+}
+
+template <int NC>
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&r)[NC]);
+template <>
+__device__ __forceinline__ void tmem_ld_issue<32>(uint32_t taddr, uint32_t (&r)[32]) {
+  tmem_ld32_issue(taddr, r);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_issue<16>(uint32_t taddr, uint32_t (&r)[16]) {
+  tmem_ld16_issue(taddr, r);
+}
+template <int NC>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[NC]);
+template <>
+__device__ __forceinline__ void tmem_ld_wait<32>(uint32_t (&r)[32]) {
+  tmem_ld32_wait(r);
+}
+template <>
+__device__ __forceinline__ void tmem_ld_wait<16>(uint32_t (&r)[16]) {
+  tmem_ld16_wait(r);
+}
+
 template <int PREC, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NBUF = 512 / BN;
+  constexpr int QC = BN / 4;  // columns of one chunk read by one phase-1 thread
+  constexpr int NCAND = PREC == 0 ? 1 : 4;
+  static_assert(PREC == 0 || QC == 32, "the top-4 key network packs a 5-bit column index");
   const Plan& p = a.p;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int s = p.s, K = p.K, nchunks = p.nchunks;
-  const int ntiles = static_cast<int>((a.N + TILE_M - 1) / TILE_M);
+  const long long NS = a.n_dev ? *a.n_dev : a.N;
+  const int ntiles = static_cast<int>((NS + TILE_M - 1) / TILE_M);
 
   uint64_t* bar_a = reinterpret_cast<uint64_t*>(smem + p.off_bar);
   uint64_t* bar_full = bar_a + 1;
@@ -296,10 +471,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_dempty + p.stages);
 
   if (tid == 0) {
-    mbar_init(bar_a, NEPI);
+    mbar_init(bar_a, 1);
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&bar_full[b], 1);
-      mbar_init(&bar_empty[b], NEPI);
+      mbar_init(&bar_empty[b], NEPI / 32);
     }
     for (int q = 0; q < p.stages; ++q) {
       mbar_init(&bar_dfull[q], 1);
@@ -318,11 +493,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   const uint32_t a_addr = smem_u32(smem + p.off_a);
   const uint32_t ring_addr = smem_u32(smem + p.off_ring);
 
-  if (warp == 5) {
+  if (warp == NEPI / 32 + 1) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       if (p.resident) {
-        for (int c = 0; c < nchunks; ++c) {
+        for (int c = 0; c < p.nchunks; ++c) {
           mbar_arrive_expect_tx(&bar_dfull[c], p.chunk_bytes);
           bulk_g2s(smem + p.off_ring + static_cast<size_t>(c) * p.chunk_bytes,
                    a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes, &bar_dfull[c]);
@@ -331,8 +506,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         long long ring = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-          for (int it = 0; it < s && ok; ++it) {
-            for (int c = 0; c < nchunks; ++c, ++ring) {
+          SceneDev sd;
+          int lt;
+          tile_scene(a, NS, tile, sd, lt);
+          for (int it = 0; it < sd.s && ok; ++it) {
+            for (int c = 0; c < sd.nchunks; ++c, ++ring) {
               const int st = static_cast<int>(ring % p.stages);
               const uint32_t par = static_cast<uint32_t>((ring / p.stages) & 1) ^ 1u;
               if (!mbar_wait(&bar_dempty[st], par, a.budget)) {
@@ -342,12 +520,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               }
               mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
               bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
-                       a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes,
+                       sd.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes,
                        &bar_dfull[st]);
             }
           }
         }
-        // drain: the last release of every stage has arrived
         for (long long f = ring > p.stages ? ring - p.stages : 0; ok && f < ring; ++f) {
           if (!mbar_wait(&bar_dempty[f % p.stages], static_cast<uint32_t>((f / p.stages) & 1),
                          a.budget)) {
@@ -357,14 +534,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         }
       }
     }
-  } else if (warp == 4) {
+  } else if (warp == NEPI / 32) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t a_phase = 0;
       long long cc = 0, ring = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        for (int it = 0; it < s && ok; ++it) {
+        SceneDev sd;
+        int lt;
+        tile_scene(a, NS, tile, sd, lt);
+        const int nchunks = sd.nchunks;
+        for (int it = 0; it < sd.s && ok; ++it) {
           if (!mbar_wait(bar_a, a_phase, a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
             ok = false;
@@ -403,237 +584,352 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       }
     }
   } else {
-    // ------------------------------------------------ epilogue / solver
-    const int i = tid;
+    // ------------------------------------------------ selection + solver
     uint8_t* A = smem + p.off_a;
-    float* xs = reinterpret_cast<float*>(smem + p.off_x);
-    float* Ls = reinterpret_cast<float*>(smem + p.off_L);
-    int* sel = reinterpret_cast<int*>(smem + p.off_sel);
-    float* ys = reinterpret_cast<float*>(smem + p.off_y);
-    float* gs = reinterpret_cast<float*>(smem + p.off_g);
-    const float* sig = reinterpret_cast<const float*>(smem + p.off_sig);
-    float* sig_w = reinterpret_cast<float*>(smem + p.off_sig);
+    float* Ls = reinterpret_cast<float*>(smem + p.off_L);       // packed L, [pos][128]
+    int* sel = reinterpret_cast<int*>(smem + p.off_sel);        // [m][128]
+    float* ys = reinterpret_cast<float*>(smem + p.off_y);       // [m][128]
+    float* gs = reinterpret_cast<float*>(smem + p.off_g);       // [m][128]
+    int* rowt = reinterpret_cast<int*>(smem + p.off_rowt);      // [128] support size
+    float* cv = reinterpret_cast<float*>(smem + p.off_cand);    // [128][4][NCAND]
+    int* cj = reinterpret_cast<int*>(smem + p.off_cand + TILE_M * 4 * NCAND * 4);
+    float* sig = reinterpret_cast<float*>(smem + p.off_sig);
+    float* rsm = reinterpret_cast<float*>(smem + p.off_r);  // [12][512] residual slices
     if constexpr (PREC == 2) {
-      for (int j = i; j < p.Kp; j += NEPI) sig_w[j] = a.sigma[j];
+      for (int j = tid; j < p.Kp; j += NEPI) sig[j] = a.sigma[j];
+      // FP8 rows hold 64 bytes: bytes 48..63 are zero padding, written once
+      for (int row = tid; row < TILE_M; row += NEPI)
+        *reinterpret_cast<uint4*>(A + 3 * TILE_M * 16 + row * 16) = make_uint4(0, 0, 0, 0);
     }
-    // rows 45..47 of the signal tile are padding and stay zero
-    for (int k = DLSH_D; k < DPAD; ++k) xs[k * TILE_M + i] = 0.f;
-#define LS(r, c) Ls[(((r) * ((r) + 1)) / 2 + (c)) * TILE_M + i]
+    const int R1 = 32 * (warp & 3) + lane, q1 = warp >> 2;
+    const int R2 = 8 * warp + (lane >> 2), u = lane & 3;
+    const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                          static_cast<uint32_t>(q1 * QC);
+#define LS(rr, cc2) Ls[(((rr) * ((rr) + 1)) / 2 + (cc2)) * TILE_M + R2]
     long long cc = 0;
     bool ok = true;
-    const float eps2 = a.eps * a.eps;
-    const uint32_t trow = tmem_base + (static_cast<uint32_t>(warp * 32) << 16);
+    long long pc_wait = 0, pc_p1 = 0, pc_b1 = 0, pc_p2 = 0, pc_b2 = 0, pc_it = 0;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int64_t g0 = static_cast<int64_t>(tile) * TILE_M;
-      const int rows = static_cast<int>(a.N - g0 < TILE_M ? a.N - g0 : TILE_M);
-      named_bar_sync(1, NEPI);
-      const float* Xt = a.X + g0 * DLSH_D;
-      for (int f = i; f < TILE_M * DLSH_D; f += NEPI) {
-        const int row = f / DLSH_D, col = f - row * DLSH_D;
-        xs[col * TILE_M + row] = row < rows ? __ldg(Xt + f) : 0.f;
-      }
-      named_bar_sync(1, NEPI);
-      float r[48];
-      float xn2 = 0.f;
+      SceneDev sd;
+      int lt;
+      tile_scene(a, NS, tile, sd, lt);
+      const int s = sd.s, K = sd.K, nchunks = sd.nchunks;
+      const float eps2 = sd.eps * sd.eps;
+      const int64_t g0 = static_cast<int64_t>(lt) * TILE_M;
+      const int rows = static_cast<int>(sd.N - g0 < TILE_M ? sd.N - g0 : TILE_M);
+      // -------- each sub-lane loads its 12 dims of the signal (a warp reads 8
+      // consecutive rows: one contiguous 1440-byte span)
+      // x and r live in registers only during the solver phase (the selection
+      // phase needs the registers); x is re-read from L1/L2, r kept in smem.
+      const float* xr = sd.X + (g0 + R2) * DLSH_D + 12 * u;
+      const bool in_tile = R2 < rows;
+      auto load_x = [&](float (&x)[12]) {
 #pragma unroll
-      for (int k = 0; k < 48; ++k) {
-        r[k] = k < DLSH_D ? xs[k * TILE_M + i] : 0.f;
-        xn2 = fmaf(r[k], r[k], xn2);
-      }
-      const float xnorm = sqrtf(xn2);
-      float rn2 = xn2;
-      bool active = i < rows;
+        for (int k = 0; k < 12; ++k) x[k] = (in_tile && 12 * u + k < DLSH_D) ? __ldg(xr + k) : 0.f;
+      };
+      float xnorm, rn2;
+      bool active = in_tile;
       int t = 0;
-      write_a_row<PREC>(A, i, r);
+      if (u == 0) rowt[R2] = 0;
+      {
+        float x[12];
+        load_x(x);
+        float part = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) part = fmaf(x[k], x[k], part);
+        rn2 = quad_sum(part);
+        xnorm = sqrtf(rn2);
+        float inv = 1.f;
+        if constexpr (PREC == 2) {
+          float mx = 0.f;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fabsf(x[k]));
+          mx = quad_max(mx);
+          inv = mx > 0.f ? FP8_MAX / mx : 1.f;
+        }
+        write_a_part<PREC>(A, R2, u, x, inv);
+        if constexpr (PREC != 0) {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = x[k];
+        }
+      }
       fence_proxy_async_smem();
-      mbar_arrive(bar_a);
+      named_bar_sync(1, NEPI);
+      if (tid == 0) mbar_arrive(bar_a);
 
       for (int it = 0; it < s; ++it) {
-        if (active && rn2 <= eps2) active = false;
-        // -------- atom selection over all chunks
-        float tv[4] = {-1.f, -1.f, -1.f, -1.f};
-        int tj[4] = {-1, -1, -1, -1};
-        float bval = 0.f;
-        for (int c = 0; c < nchunks; ++c, ++cc) {
-          const int buf = static_cast<int>(cc % NBUF);
-          if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((cc / NBUF) & 1), a.budget)) {
+        const long long T0 = clock64();
+        // ================= phase 1: selection over this thread's column quarter
+        const int t1 = rowt[R1];
+        // Only strictly positive |c| are candidates: atoms already in the
+        // support and padding atoms are zeroed first, so they never qualify.
+        float tv[4] = {0.f, 0.f, 0.f, 0.f};
+        int tj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+        auto process = [&](uint32_t (&rr)[QC], int c) {
+            const int j0 = c * BN + q1 * QC;
+            // exclusion mask of this chunk quarter: selected atoms and j >= K
+            uint32_t em = (K - j0 < QC) ? ~((K - j0 <= 0) ? 0u : ((1u << (K - j0)) - 1u)) : 0u;
+            for (int mm = 0; mm < t1; ++mm) {
+              const unsigned d = static_cast<unsigned>(sel[mm * TILE_M + R1] - j0);
+              if (d < static_cast<unsigned>(QC)) em |= 1u << d;
+            }
+            if constexpr (PREC == 2) {
+#pragma unroll
+              for (int k = 0; k < QC; ++k) rr[k] = __float_as_uint(__uint_as_float(rr[k]) * sig[j0 + k]);
+            }
+#pragma unroll
+            for (int k = 0; k < QC; ++k) rr[k] = ((em >> k) & 1u) ? 0u : (rr[k] & 0x7fffffffu);
+            float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < QC; k += 2) {
+              m0 = fmaxf(m0, __uint_as_float(rr[k]));
+              m1 = fmaxf(m1, __uint_as_float(rr[k + 1]));
+            }
+            const float m = fmaxf(m0, m1);
+            if constexpr (PREC == 0) {
+              // exact argmax: the first (smallest) index attaining the maximum
+              if (m > tv[0]) {
+                int bk = 0;
+#pragma unroll
+                for (int k = QC - 1; k >= 0; --k)
+                  if (__uint_as_float(rr[k]) == m) bk = k;
+                tv[0] = m;
+                tj[0] = j0 + bk;
+              }
+            } else if (m > tv[3]) {
+              // top 4 of this chunk quarter with a branchless min/max network on
+              // keys (|c| with its low 5 mantissa bits replaced by 31 - k, so
+              // larger keys mean larger values and, on ties, smaller indices),
+              // then merged into the running top 4
+              uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+#pragma unroll
+              for (int k = 0; k < QC; ++k) {
+                uint32_t xk = (rr[k] & ~31u) | static_cast<uint32_t>(31 - k);
+                uint32_t hi = max(k0, xk);
+                xk = min(k0, xk);
+                k0 = hi;
+                hi = max(k1, xk);
+                xk = min(k1, xk);
+                k1 = hi;
+                hi = max(k2, xk);
+                xk = min(k2, xk);
+                k2 = hi;
+                k3 = max(k3, xk);
+              }
+              const uint32_t kk[4] = {k0, k1, k2, k3};
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float val = __uint_as_float(kk[e] & ~31u);
+                if (val > tv[3]) top4_insert(tv, tj, val, j0 + 31 - static_cast<int>(kk[e] & 31u));
+              }
+            }
+        };
+        auto acquire = [&](long long ccq) -> bool {  // wait for the chunk's MMAs
+          const int buf = static_cast<int>(ccq % NBUF);
+          const long long W0 = clock64();
+          if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((ccq / NBUF) & 1), a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
+            return false;
+          }
+          pc_wait += clock64() - W0;
+          tc_fence_after();
+          return true;
+        };
+        auto release = [&](long long ccq) {  // the chunk's TMEM buffer may be reused
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_empty[static_cast<int>(ccq % NBUF)]);
+        };
+        for (int c = 0; c < nchunks; ++c, ++cc) {
+          if (!acquire(cc)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-#pragma unroll 1
-          for (int cb = 0; cb < BN; cb += 32) {
-            float v[32];
-            __syncwarp();
-            tmem_ld32(trow + static_cast<uint32_t>(buf * BN + cb), v);
-            const int j0 = c * BN + cb;
-            if constexpr (PREC == 2) {
-#pragma unroll
-              for (int k = 0; k < 32; ++k) v[k] *= sig[j0 + k];
-            }
-            float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f;
-#pragma unroll
-            for (int k = 0; k < 32; k += 4) {
-              m0 = fmaxf(m0, fabsf(v[k]));
-              m1 = fmaxf(m1, fabsf(v[k + 1]));
-              m2 = fmaxf(m2, fabsf(v[k + 2]));
-              m3 = fmaxf(m3, fabsf(v[k + 3]));
-            }
-            const float m = fmaxf(fmaxf(m0, m1), fmaxf(m2, m3));
-            const float thr = (PREC == 0) ? tv[0] : tv[3];
-            if (active && m > thr) {
-#pragma unroll
-              for (int k = 0; k < 32; ++k) {
-                const float av = fabsf(v[k]);
-                const int j = j0 + k;
-                const float th = (PREC == 0) ? tv[0] : tv[3];
-                if (av > th && j < K) {
-                  bool taken = false;
-                  for (int q = 0; q < t; ++q) taken |= (sel[q * TILE_M + i] == j);
-                  if (!taken) {
-                    if constexpr (PREC == 0) {
-                      tv[0] = av;
-                      tj[0] = j;
-                      bval = v[k];
-                    } else {
-                      if (av > tv[0]) {
-                        tv[3] = tv[2]; tj[3] = tj[2];
-                        tv[2] = tv[1]; tj[2] = tj[1];
-                        tv[1] = tv[0]; tj[1] = tj[0];
-                        tv[0] = av; tj[0] = j;
-                      } else if (av > tv[1]) {
-                        tv[3] = tv[2]; tj[3] = tj[2];
-                        tv[2] = tv[1]; tj[2] = tj[1];
-                        tv[1] = av; tj[1] = j;
-                      } else if (av > tv[2]) {
-                        tv[3] = tv[2]; tj[3] = tj[2];
-                        tv[2] = av; tj[2] = j;
-                      } else {
-                        tv[3] = av; tj[3] = j;
-                      }
-                    }
-                  }
-                }
-              }
-            }
-          }
-          tc_fence_before();
-          mbar_arrive(&bar_empty[buf]);
+          __syncwarp();
+          uint32_t rr[QC];
+          tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
+          tmem_ld_wait<QC>(rr);
+          release(cc);
+          process(rr, c);
         }
-        if (!ok) break;
+#pragma unroll
+        for (int k = 0; k < NCAND; ++k) {
+          cv[(R1 * 4 + q1) * NCAND + k] = tv[k];
+          cj[(R1 * 4 + q1) * NCAND + k] = tj[k];
+        }
+        const long long T1 = clock64();
+        // barrier + vote: every selection thread leaves together if any wait ran out
+        if (named_bar_or(1, NEPI, !ok)) {
+          ok = false;
+          break;
+        }
+        const long long T2 = clock64();
 
+        // ================= phase 2: merge, re-score, Cholesky, solve, residual
+        if (active && rn2 <= eps2) active = false;
         if (active) {
-          // -------- FP32 re-score of the low-precision candidates
-          int js = tj[0];
-          float best = tv[0];
+          float x[12], r[12];
+          load_x(x);
           if constexpr (PREC != 0) {
-            best = -1.f;
-            js = -1;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              if (tj[q] >= 0) {
-                const float4* drow = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(tj[q]) * DPAD);
-                float c0 = 0.f;
+            for (int k = 0; k < 12; ++k) r[k] = rsm[k * NEPI + tid];
+          }
+          int js = -1;
+          float best = -1.f;
+          if constexpr (PREC == 0) {
 #pragma unroll
-                for (int u = 0; u < 12; ++u) {
-                  const float4 dv = __ldg(drow + u);
-                  c0 = fmaf(r[4 * u + 0], dv.x, c0);
-                  c0 = fmaf(r[4 * u + 1], dv.y, c0);
-                  c0 = fmaf(r[4 * u + 2], dv.z, c0);
-                  c0 = fmaf(r[4 * u + 3], dv.w, c0);
+            for (int qq = 0; qq < 4; ++qq) {
+              const float v = cv[R2 * 4 + qq];
+              const int j = cj[R2 * 4 + qq];
+              if (j < K && (v > best || (v == best && j < js))) {
+                best = v;
+                js = j;
+              }
+            }
+          } else {
+            // entries with j >= K are empty slots (value 0, index INT_MAX)
+            float mv[4] = {-1.f, -1.f, -1.f, -1.f};
+            int mj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+#pragma unroll 1
+            for (int e = 0; e < 16; ++e) {
+              const int j = cj[R2 * 16 + e];
+              if (j < K) top4_insert(mv, mj, cv[R2 * 16 + e], j);
+            }
+            // FP32 re-score of the four candidates: c = r . d_j
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              float c0 = 0.f;
+              if (mv[k] >= 0.f) {
+                const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(mj[k]) * DPAD + 12 * u);
+#pragma unroll
+                for (int w4 = 0; w4 < 3; ++w4) {
+                  const float4 dv = __ldg(dr + w4);
+                  c0 = fmaf(r[4 * w4 + 0], dv.x, c0);
+                  c0 = fmaf(r[4 * w4 + 1], dv.y, c0);
+                  c0 = fmaf(r[4 * w4 + 2], dv.z, c0);
+                  c0 = fmaf(r[4 * w4 + 3], dv.w, c0);
                 }
-                const float ac = fabsf(c0);
-                if (ac > best || (ac == best && tj[q] < js)) {
-                  best = ac;
-                  js = tj[q];
-                  bval = c0;
-                }
+              }
+              c0 = fabsf(quad_sum(c0));
+              if (mv[k] >= 0.f && (c0 > best || (c0 == best && mj[k] < js))) {
+                best = c0;
+                js = mj[k];
               }
             }
           }
-          (void)bval;
           if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
             active = false;
           } else {
             // -------- Cholesky update: w = L^-1 g, g_m = <d_js, d_sel[m]>
-            const float* Grow = a.G + static_cast<size_t>(js) * K;
+            const float* Grow = sd.G + static_cast<size_t>(js) * K;
             float wn2 = 0.f;
-            for (int m = 0; m < t; ++m) {
-              float acc = __ldg(Grow + sel[m * TILE_M + i]);
-              for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), LS(t, q), acc);
-              const float w = acc / LS(m, m);
-              LS(t, m) = w;
+            for (int mm = 0; mm < t; ++mm) {
+              float acc = __ldg(Grow + sel[mm * TILE_M + R2]);
+              for (int qq = 0; qq < mm; ++qq) acc = fmaf(-LS(mm, qq), LS(t, qq), acc);
+              const float w = acc / LS(mm, mm);
+              LS(t, mm) = w;  // the four sub-lanes store identical values
               wn2 = fmaf(w, w, wn2);
             }
             const float gjj = __ldg(Grow + js);
             const float ell2 = gjj - wn2;
             if (!(ell2 > PIVOT_MIN * gjj)) {
-              active = false;  // numerically dependent atom: not added
+              active = false;
             } else {
               const float ell = sqrtf(ell2);
               LS(t, t) = ell;
-              // b_t = <d_js, x>, forward step of L y = D_I^T x
-              const float4* drow = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD);
-              float b = 0.f;
+              const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+              float bp = 0.f;
 #pragma unroll
-              for (int u = 0; u < 12; ++u) {
-                const float4 dv = __ldg(drow + u);
-                b = fmaf(dv.x, xs[(4 * u + 0) * TILE_M + i], b);
-                b = fmaf(dv.y, xs[(4 * u + 1) * TILE_M + i], b);
-                b = fmaf(dv.z, xs[(4 * u + 2) * TILE_M + i], b);
-                b = fmaf(dv.w, xs[(4 * u + 3) * TILE_M + i], b);
+              for (int w4 = 0; w4 < 3; ++w4) {
+                const float4 dv = __ldg(dr + w4);
+                bp = fmaf(dv.x, x[4 * w4 + 0], bp);
+                bp = fmaf(dv.y, x[4 * w4 + 1], bp);
+                bp = fmaf(dv.z, x[4 * w4 + 2], bp);
+                bp = fmaf(dv.w, x[4 * w4 + 3], bp);
               }
-              float yt = b;
-              for (int m = 0; m < t; ++m) yt = fmaf(-LS(t, m), ys[m * TILE_M + i], yt);
-              ys[t * TILE_M + i] = yt / ell;
-              sel[t * TILE_M + i] = js;
+              float yt = quad_sum(bp);
+              for (int mm = 0; mm < t; ++mm) yt = fmaf(-LS(t, mm), ys[mm * TILE_M + R2], yt);
+              yt /= ell;
+              ys[t * TILE_M + R2] = yt;
+              sel[t * TILE_M + R2] = js;
               ++t;
               // back substitution L^T gamma = y
-              for (int m = t - 1; m >= 0; --m) {
-                float acc = ys[m * TILE_M + i];
-                for (int q = m + 1; q < t; ++q) acc = fmaf(-LS(q, m), gs[q * TILE_M + i], acc);
-                gs[m * TILE_M + i] = acc / LS(m, m);
+              for (int mm = t - 1; mm >= 0; --mm) {
+                float acc = ys[mm * TILE_M + R2];
+                for (int qq = mm + 1; qq < t; ++qq) acc = fmaf(-LS(qq, mm), gs[qq * TILE_M + R2], acc);
+                gs[mm * TILE_M + R2] = acc / LS(mm, mm);
               }
-              // residual r = x - D_I gamma, in FP32 from the FP32 atoms
+              // residual r = x - D_I gamma on this sub-lane's 12 dims
 #pragma unroll
-              for (int k = 0; k < 48; ++k) r[k] = k < DLSH_D ? xs[k * TILE_M + i] : 0.f;
-              for (int m = 0; m < t; ++m) {
-                const float gm = gs[m * TILE_M + i];
-                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sel[m * TILE_M + i]) * DPAD);
+              for (int k = 0; k < 12; ++k) r[k] = x[k];
+              for (int mm = 0; mm < t; ++mm) {
+                const float gm = gs[mm * TILE_M + R2];
+                const float4* da = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(sel[mm * TILE_M + R2]) * DPAD + 12 * u);
 #pragma unroll
-                for (int u = 0; u < 12; ++u) {
-                  const float4 dv = __ldg(dr + u);
-                  r[4 * u + 0] = fmaf(-gm, dv.x, r[4 * u + 0]);
-                  r[4 * u + 1] = fmaf(-gm, dv.y, r[4 * u + 1]);
-                  r[4 * u + 2] = fmaf(-gm, dv.z, r[4 * u + 2]);
-                  r[4 * u + 3] = fmaf(-gm, dv.w, r[4 * u + 3]);
+                for (int w4 = 0; w4 < 3; ++w4) {
+                  const float4 dv = __ldg(da + w4);
+                  r[4 * w4 + 0] = fmaf(-gm, dv.x, r[4 * w4 + 0]);
+                  r[4 * w4 + 1] = fmaf(-gm, dv.y, r[4 * w4 + 1]);
+                  r[4 * w4 + 2] = fmaf(-gm, dv.z, r[4 * w4 + 2]);
+                  r[4 * w4 + 3] = fmaf(-gm, dv.w, r[4 * w4 + 3]);
                 }
               }
-              rn2 = 0.f;
+              float pr = 0.f;
 #pragma unroll
-              for (int k = 0; k < 48; ++k) rn2 = fmaf(r[k], r[k], rn2);
+              for (int k = 0; k < 12; ++k) pr = fmaf(r[k], r[k], pr);
+              rn2 = quad_sum(pr);
+              if (u == 0) rowt[R2] = t;
+              if (it + 1 < s) {
+                float inv = 1.f;
+                if constexpr (PREC == 2) {
+                  float mx = 0.f;
+#pragma unroll
+                  for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fabsf(r[k]));
+                  mx = quad_max(mx);
+                  inv = mx > 0.f ? FP8_MAX / mx : 1.f;
+                }
+                write_a_part<PREC>(A, R2, u, r, inv);
+              }
+              if constexpr (PREC != 0) {
+#pragma unroll
+                for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = r[k];
+              }
             }
           }
         }
-        if (it + 1 < s) {
-          if (active) write_a_row<PREC>(A, i, r);
-          fence_proxy_async_smem();
-          mbar_arrive(bar_a);
-        }
+        fence_proxy_async_smem();
+        const long long T3 = clock64();
+        named_bar_sync(1, NEPI);
+        if (it + 1 < s && tid == 0) mbar_arrive(bar_a);
+        const long long T4 = clock64();
+        pc_p1 += T1 - T0;
+        pc_b1 += T2 - T1;
+        pc_p2 += T3 - T2;
+        pc_b2 += T4 - T3;
+        ++pc_it;
       }
       if (!ok) break;
-      if (i < rows) {
-        const int64_t g = g0 + i;
-        for (int m = 0; m < s; ++m) {
-          a.idx[g * s + m] = m < t ? static_cast<uint16_t>(sel[m * TILE_M + i]) : static_cast<uint16_t>(0);
-          a.coef[g * s + m] = m < t ? gs[m * TILE_M + i] : 0.f;
+      if (R2 < rows) {
+        const int64_t g = g0 + R2;
+        for (int mm = u; mm < s; mm += 4) {
+          sd.idx[g * s + mm] = mm < t ? static_cast<uint16_t>(sel[mm * TILE_M + R2]) : static_cast<uint16_t>(0);
+          sd.coef[g * s + mm] = mm < t ? gs[mm * TILE_M + R2] : 0.f;
         }
-        a.nnz[g] = static_cast<uint8_t>(t);
-        if (a.resid_sq) a.resid_sq[g] = rn2;
+        if (u == 0) {
+          sd.nnz[g] = static_cast<uint8_t>(t);
+          if (sd.resid) sd.resid[g] = rn2;
+        }
       }
     }
 #undef LS
+    if (a.prof && tid == 0) {
+      atomicAdd(a.prof + 0, static_cast<unsigned long long>(pc_wait));
+      atomicAdd(a.prof + 1, static_cast<unsigned long long>(pc_p1));
+      atomicAdd(a.prof + 2, static_cast<unsigned long long>(pc_b1));
+      atomicAdd(a.prof + 3, static_cast<unsigned long long>(pc_p2));
+      atomicAdd(a.prof + 4, static_cast<unsigned long long>(pc_b2));
+      atomicAdd(a.prof + 5, static_cast<unsigned long long>(pc_it));
+    }
   }
   tc_fence_before();
   __syncthreads();
@@ -815,10 +1111,11 @@ static int prepare(const float* D, const Plan& p, const Ws& w, bool gram, cudaSt
 // Entry points shared with the learning loop (learn.cu).
 int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, float eps, int prec,
                    uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq, void* ws,
-                   cudaStream_t st, uint32_t** status_out) {
+                   cudaStream_t st, uint32_t** status_out, unsigned long long* prof,
+                   const long long* n_dev, int bn) {
   using namespace enc;
   Plan p;
-  if (make_plan(K, s, prec, p) != DLSH_OK)
+  if (make_plan(K, s, prec, p, bn) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
   Ws w;
@@ -826,8 +1123,8 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   if (status_out) *status_out = w.status;
   int rc = prepare(D, p, w, true, st);
   if (rc) return rc;
-  if (N == 0) return DLSH_OK;
-  Args a;
+  if (N == 0 && !n_dev) return DLSH_OK;
+  Args a{};  // value-initialised: no scene table, no device-side count, no profiling
   a.X = X;
   a.N = N;
   a.D32p = w.D32p;
@@ -841,11 +1138,13 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   a.eps = eps;
   a.status = w.status;
   a.budget = kWaitBudget;
+  a.prof = prof;
+  a.n_dev = n_dev;
   a.p = p;
   const int ntiles = static_cast<int>((N + TILE_M - 1) / TILE_M);
   int sms = device_sm_count();
   if (sms <= 0) sms = 1;
-  const int grid = ntiles < sms ? ntiles : sms;
+  const int grid = (n_dev || ntiles > sms) ? sms : (ntiles > 0 ? ntiles : 1);
   if (p.BN == 128) {
     if (prec == 0) return launch_encode<0, 128>(a, grid, st);
     if (prec == 1) return launch_encode<1, 128>(a, grid, st);
@@ -854,11 +1153,33 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   return launch_encode<0, 64>(a, grid, st);
 }
 
+// Prepares the dictionary (padded FP32 copy, Gram, operand image) in an
+// encoder workspace and returns pointers into it.
+int encode_prepare_only(const float* D, int K, int s, int prec, void* ws, cudaStream_t st,
+                        const float** D32p, const float** G, uint32_t** status) {
+  using namespace enc;
+  Plan p;
+  if (make_plan(K, s, prec, p) != DLSH_OK)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh: K=%d s=%d does not fit", K, s);
+  Ws w;
+  carve(ws, p, w);
+  *D32p = w.D32p;
+  *G = w.G;
+  *status = w.status;
+  return prepare(D, p, w, true, st);
+}
+
+// Largest workspace over the chunk widths the plan may pick.
 size_t encode_ws_bytes(int K, int s, int prec) {
-  enc::Plan p;
-  if (enc::make_plan(K, s, prec, p) != DLSH_OK) return 0;
-  enc::Ws w;
-  return enc::carve(nullptr, p, w);
+  size_t best = 0;
+  for (int bn : {64, 128}) {
+    enc::Plan p;
+    if (enc::make_plan(K, s, prec, p, bn) != DLSH_OK) continue;
+    enc::Ws w;
+    const size_t b = enc::carve(nullptr, p, w);
+    if (b > best) best = b;
+  }
+  return best;
 }
 
 }  // namespace dlsh
@@ -890,9 +1211,32 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s, 
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint32_t* status = nullptr;
-  rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status);
+  rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status,
+                      nullptr, nullptr);
   if (rc) return rc;
   return finish(st, status, flags, "dlsh_encode");
+}
+
+int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N, int s, float eps,
+                        int precision, uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq,
+                        void* ws, size_t ws_bytes, unsigned long long* cycles, void* stream,
+                        int flags) {
+  using namespace dlsh;
+  clear_error();
+  int rc = enc::validate("dlsh_encode_profile", D, K, d, s, precision);
+  if (rc) return rc;
+  if (N < 0 || (N > 0 && (!X || !idx || !coef || !nnz)) || !cycles)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_profile: bad arguments");
+  rc = check_workspace(ws, ws_bytes, encode_ws_bytes(K, s, precision), "dlsh_encode_profile");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DLSH_CUDA_TRY(cudaMemsetAsync(cycles, 0, 6 * sizeof(unsigned long long), st),
+                "dlsh_encode_profile: reset");
+  uint32_t* status = nullptr;
+  rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status,
+                      cycles, nullptr);
+  if (rc) return rc;
+  return finish(st, status, flags, "dlsh_encode_profile");
 }
 
 int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M, int precision,
@@ -929,3 +1273,273 @@ int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M, int 
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Autotuner: times the encoder at each admissible atom-chunk width on the
+// caller's sample and records the fastest per (K, s, precision), in memory and,
+// if DLSH_AUTOTUNE_CACHE names a file, as JSON lines there (read at first use).
+// ===========================================================================
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace dlsh {
+namespace enc {
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned;
+static bool g_tune_loaded = false;
+
+static void load_tune_cache_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[256];
+  while (fgets(line, sizeof(line), f)) {
+    int K, s, prec, bn;
+    if (sscanf(line, " {\"K\": %d, \"s\": %d, \"precision\": %d, \"bn\": %d", &K, &s, &prec, &bn) == 4)
+      g_tuned[std::make_tuple(K, s, prec)] = bn;
+  }
+  fclose(f);
+}
+
+int tuned_bn(int K, int s, int prec) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  load_tune_cache_locked();
+  auto it = g_tuned.find(std::make_tuple(K, s, prec));
+  return it == g_tuned.end() ? 0 : it->second;
+}
+
+static void record_tuned(int K, int s, int prec, int bn) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  load_tune_cache_locked();
+  g_tuned[std::make_tuple(K, s, prec)] = bn;
+  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tuned)
+    fprintf(f, "{\"K\": %d, \"s\": %d, \"precision\": %d, \"bn\": %d}\n", std::get<0>(kv.first),
+            std::get<1>(kv.first), std::get<2>(kv.first), kv.second);
+  fclose(f);
+}
+
+}  // namespace enc
+}  // namespace dlsh
+
+extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
+                                    int precision, uint16_t* idx, float* coef, uint8_t* nnz,
+                                    float* resid_sq, void* ws, size_t ws_bytes, void* stream,
+                                    int* best_bn) {
+  using namespace dlsh;
+  using namespace dlsh::enc;
+  clear_error();
+  int rc = validate("dlsh_autotune_encode", D, K, d, s, precision);
+  if (rc) return rc;
+  if (N < 1 || !X || !idx || !coef || !nnz)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_autotune_encode: need a non-empty sample");
+  rc = check_workspace(ws, ws_bytes, encode_ws_bytes(K, s, precision), "dlsh_autotune_encode");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  DLSH_CUDA_TRY(cudaEventCreate(&e0), "dlsh_autotune_encode: event");
+  DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
+  int best = 0;
+  float best_ms = 0.f;
+  for (int bn : {64, 128}) {
+    Plan p;
+    if (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn) continue;
+    // force this width for the trial runs
+    record_tuned(K, s, precision, bn);
+    uint32_t* status = nullptr;
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      rc = encode_enqueue(D, K, X, N, s, 0.f, precision, idx, coef, nnz, resid_sq, ws, st, &status,
+                          nullptr, nullptr);
+      cudaEventRecord(e1, st);
+      if (rc) break;
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;  // the first run warms up
+    }
+    if (rc) break;
+    if (best == 0 || ms_sum < best_ms) {
+      best = bn;
+      best_ms = ms_sum;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best == 0) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_encode: no admissible width");
+  record_tuned(K, s, precision, best);
+  if (best_bn) *best_bn = best;
+  return finish(st, nullptr, 0, "dlsh_autotune_encode");
+}
+
+// ===========================================================================
+// Multi-scene encoding.  Every scene is encoded by the single-scene encoder
+// with its own plan (the chunk width and staging a dlsh_encode call of that
+// scene would pick, so the codes are bitwise those of separate calls), on one
+// of a few internal streams forked from the caller's stream with an event and
+// joined back the same way.  Scenes are dealt to the streams in decreasing
+// order of total cost (N*K*s), so small scenes fill the SMs the large ones
+// leave idle.  Event record and wait are captured as graph dependencies, so
+// the whole call can be captured into a CUDA graph.
+// ===========================================================================
+#include <mutex>
+
+namespace dlsh {
+namespace enc {
+
+constexpr int MAX_SCENES = 32;
+constexpr int kStreams = 4;
+constexpr int kMaxDevices = 64;
+
+struct StatusList {
+  const uint32_t* w[MAX_SCENES];
+  int n;
+};
+
+// out |= the status words of every scene.
+__global__ void or_status_list_kernel(const StatusList l, uint32_t* out) {
+  uint32_t v = 0;
+  for (int i = 0; i < l.n; ++i) v |= l.w[i][0];
+  if (v) atomicOr(out, v);
+}
+
+struct Fork {
+  cudaStream_t s[kStreams];
+  cudaEvent_t fork, join[kStreams];
+  bool ready = false;
+};
+static std::mutex g_fork_mu;
+static Fork g_fork[kMaxDevices];
+
+// Per-scene workspace regions: one status word for the call, then a
+// single-scene encoder workspace per scene.
+static size_t multi_carve(void* base, const dlsh_scene* sc, int n, int prec, uint32_t** status,
+                          void** per) {
+  Carver c(base);
+  *status = c.take<uint32_t>(64);
+  for (int i = 0; i < n; ++i) per[i] = c.take<uint8_t>(encode_ws_bytes(sc[i].K, sc[i].s, prec));
+  return c.size();
+}
+
+static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
+  if (!sc || n < 1 || n > MAX_SCENES)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
+  if (prec < 0 || prec > 2)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
+  if (bn != 0 && bn != 64 && bn != 128)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 64 or 128");
+  for (int i = 0; i < n; ++i) {
+    const dlsh_scene& x = sc[i];
+    if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
+      return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has bad sizes", i);
+    if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
+      return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
+    Plan p;
+    if (make_plan(x.K, x.s, prec, p, bn) != DLSH_OK)
+      return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
+                       i, x.K, x.s);
+  }
+  return DLSH_OK;
+}
+
+static int fork_streams(Fork** out) {
+  int dev = 0;
+  DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_encode_multi: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: device %d out of range", dev);
+  Fork& f = g_fork[dev];
+  if (!f.ready) {
+    for (int i = 0; i < kStreams; ++i) {
+      DLSH_CUDA_TRY(cudaStreamCreateWithFlags(&f.s[i], cudaStreamNonBlocking),
+                    "dlsh_encode_multi: stream");
+      DLSH_CUDA_TRY(cudaEventCreateWithFlags(&f.join[i], cudaEventDisableTiming),
+                    "dlsh_encode_multi: event");
+    }
+    DLSH_CUDA_TRY(cudaEventCreateWithFlags(&f.fork, cudaEventDisableTiming),
+                  "dlsh_encode_multi: event");
+    f.ready = true;
+  }
+  *out = &f;
+  return DLSH_OK;
+}
+
+}  // namespace enc
+}  // namespace dlsh
+
+extern "C" size_t dlsh_encode_multi_workspace_size(const dlsh_scene* scenes, int n, int precision,
+                                                   int bn) {
+  using namespace dlsh;
+  using namespace dlsh::enc;
+  if (multi_validate(scenes, n, precision, bn) != DLSH_OK) return 0;
+  uint32_t* status;
+  void* per[MAX_SCENES];
+  return multi_carve(nullptr, scenes, n, precision, &status, per);
+}
+
+extern "C" int dlsh_encode_multi(const dlsh_scene* scenes, int n, int precision, int bn, void* ws,
+                                 size_t ws_bytes, void* stream, int flags) {
+  using namespace dlsh;
+  using namespace dlsh::enc;
+  clear_error();
+  int rc = multi_validate(scenes, n, precision, bn);
+  if (rc) return rc;
+  uint32_t* status = nullptr;
+  void* per[MAX_SCENES];
+  rc = check_workspace(ws, ws_bytes, multi_carve(nullptr, scenes, n, precision, &status, per),
+                       "dlsh_encode_multi");
+  if (rc) return rc;
+  multi_carve(ws, scenes, n, precision, &status, per);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DLSH_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(uint32_t), st), "dlsh_encode_multi: reset");
+  int order[MAX_SCENES];
+  int m = 0;
+  for (int i = 0; i < n; ++i)
+    if (scenes[i].N > 0) order[m++] = i;
+  std::sort(order, order + m, [&](int a, int b) {
+    const double ca = static_cast<double>(scenes[a].N) * scenes[a].K * scenes[a].s;
+    const double cb = static_cast<double>(scenes[b].N) * scenes[b].K * scenes[b].s;
+    return ca > cb || (ca == cb && a < b);
+  });
+  if (m > 0) {
+    std::lock_guard<std::mutex> lock(g_fork_mu);
+    Fork* f = nullptr;
+    rc = fork_streams(&f);
+    if (rc) return rc;
+    const int used = m < kStreams ? m : kStreams;
+    DLSH_CUDA_TRY(cudaEventRecord(f->fork, st), "dlsh_encode_multi: fork");
+    for (int k = 0; k < used; ++k)
+      DLSH_CUDA_TRY(cudaStreamWaitEvent(f->s[k], f->fork, 0), "dlsh_encode_multi: fork");
+    StatusList sl{};
+    sl.n = m;
+    for (int q = 0; q < m; ++q) {
+      const dlsh_scene& x = scenes[order[q]];
+      uint32_t* sst = nullptr;
+      rc = encode_enqueue(x.D, x.K, x.X, x.N, x.s, x.eps, precision, x.idx, x.coef, x.nnz,
+                          x.resid_sq, per[order[q]], f->s[q % kStreams], &sst, nullptr, nullptr, bn);
+      if (rc) break;
+      sl.w[q] = sst;
+    }
+    // the join is recorded even after a failed enqueue, so that no internal
+    // stream is left forked from a stream under capture
+    for (int k = 0; k < used; ++k) {
+      DLSH_CUDA_TRY(cudaEventRecord(f->join[k], f->s[k]), "dlsh_encode_multi: join");
+      DLSH_CUDA_TRY(cudaStreamWaitEvent(st, f->join[k], 0), "dlsh_encode_multi: join");
+    }
+    if (rc) return rc;
+    or_status_list_kernel<<<1, 1, 0, st>>>(sl, status);
+    count_launches(1);
+    rc = check_launch("dlsh_encode_multi: status");
+    if (rc) return rc;
+  }
+  return finish(st, status, flags, "dlsh_encode_multi");
+}

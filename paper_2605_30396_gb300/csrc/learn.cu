@@ -6,17 +6,9 @@
 
 #include "common.cuh"
 #include "host.hpp"
+#include "internal.hpp"
 
 namespace dlsh {
-
-int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, float eps, int prec,
-                   uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq, void* ws,
-                   cudaStream_t st, uint32_t** status_out);
-size_t encode_ws_bytes(int K, int s, int prec);
-int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const float* coef,
-                const uint8_t* nnz, int s, const float* D_old, const float* resid, float* D_new,
-                void* ws, cudaStream_t st, uint32_t** status_out);
-size_t mod_ws_bytes(int K, int s, int64_t N);
 
 namespace learn {
 

@@ -1,0 +1,512 @@
+// Learned support proposal, second half: OMP restricted to the MLP's 2s
+// candidate atoms, then plain OMP (Sec. 2.1) as the fallback.
+//
+// restricted_omp_kernel  one thread per signal.  The candidates' correlations
+//                        with x (alpha0 = D_C^T x) and their Gram block G_CC are
+//                        gathered once; the s greedy steps then run on these
+//                        small arrays alone (c = alpha0 - G_CI gamma), with the
+//                        same incremental Cholesky least squares as the full
+//                        encoder.  The final residual is recomputed explicitly.
+// fallback               "exact": plain OMP on every signal, keep whichever code
+//                        has the smaller residual (ties keep the learned one);
+//                        "deploy": plain OMP only for signals whose learned
+//                        residual exceeds tau, compacted, encoded with a
+//                        device-side count, and scattered back.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "host.hpp"
+#include "internal.hpp"
+
+namespace dlsh {
+
+namespace lrn {
+
+constexpr int RT = 64;  // threads per block of the restricted OMP
+constexpr float CORR_STOP_REL = 1e-7f;
+constexpr float PIVOT_MIN = 1e-6f;
+constexpr int DPAD = 48;
+
+__host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
+__host__ __device__ constexpr int rest_words(int m, int s) { return tri(m) + m + tri(s) + 3 * s; }
+
+// Shared arrays are [entry][RT] so consecutive threads hit consecutive banks.
+template <int M>
+__global__ void __launch_bounds__(RT)
+    restricted_omp_kernel(const float* __restrict__ X, long long N, const float* __restrict__ D32p,
+                          const float* __restrict__ G, int K, const uint16_t* __restrict__ cand,
+                          int s, float eps, uint16_t* __restrict__ idx, float* __restrict__ coef,
+                          uint8_t* __restrict__ nnz, float* __restrict__ resid,
+                          uint32_t* status) {
+  extern __shared__ float rs[];
+  const int tid = threadIdx.x;
+  const long long n = static_cast<long long>(blockIdx.x) * RT + tid;
+  float* Gc = rs;                          // tri(M)
+  float* a0 = Gc + tri(M) * RT;            // M
+  float* Ls = a0 + M * RT;                 // tri(s)
+  float* ys = Ls + tri(s) * RT;            // s
+  float* gs = ys + s * RT;                 // s
+  int* si = reinterpret_cast<int*>(gs + s * RT);  // s: positions (0..M-1) in selection order
+#define GC(q, p) Gc[((q) >= (p) ? tri(q) + (p) : tri(p) + (q)) * RT + tid]
+#define LS(r, c) Ls[(tri(r) + (c)) * RT + tid]
+  if (n >= N) return;
+  int cj[M];
+  bool bad = false;
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    int j = cand[n * M + q];
+    if (j >= K) {
+      bad = true;
+      j = 0;
+    }
+    cj[q] = j;
+  }
+  float x[48];
+  float xn2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 48; ++k) {
+    x[k] = k < DLSH_D ? X[n * DLSH_D + k] : 0.f;
+    xn2 = fmaf(x[k], x[k], xn2);
+  }
+  // alpha0 = D_C^T x and the Gram block of the candidates
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const float4* dr = reinterpret_cast<const float4*>(D32p + static_cast<size_t>(cj[q]) * DPAD);
+    float acc = 0.f;
+#pragma unroll
+    for (int u = 0; u < 12; ++u) {
+      const float4 dv = __ldg(dr + u);
+      acc = fmaf(dv.x, x[4 * u + 0], acc);
+      acc = fmaf(dv.y, x[4 * u + 1], acc);
+      acc = fmaf(dv.z, x[4 * u + 2], acc);
+      acc = fmaf(dv.w, x[4 * u + 3], acc);
+    }
+    a0[q * RT + tid] = acc;
+  }
+#pragma unroll
+  for (int q = 0; q < M; ++q)
+#pragma unroll
+    for (int p = 0; p <= q; ++p) GC(q, p) = __ldg(G + static_cast<size_t>(cj[q]) * K + cj[p]);
+  const float xnorm = sqrtf(xn2);
+  uint32_t taken = 0;
+  int t = 0;
+  for (int it = 0; it < s; ++it) {
+    if (eps > 0.f) {
+      // ||r||^2 = ||x||^2 - y.y for the current least-squares fit
+      float yy = 0.f;
+      for (int k = 0; k < t; ++k) yy = fmaf(ys[k * RT + tid], ys[k * RT + tid], yy);
+      if (xn2 - yy <= eps * eps) break;
+    }
+    // c = alpha0 - G_{C,I} gamma over the candidates not yet selected
+    float best = 0.f;
+    int bq = -1, bj = 0x7fffffff;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      float c = a0[q * RT + tid];
+      for (int k = 0; k < t; ++k) c = fmaf(-GC(q, si[k * RT + tid]), gs[k * RT + tid], c);
+      const float ac = fabsf(c);
+      if (!((taken >> q) & 1u) && (ac > best || (ac == best && cj[q] < bj))) {
+        best = ac;
+        bq = q;
+        bj = cj[q];
+      }
+    }
+    if (bq < 0 || !(best > CORR_STOP_REL * xnorm)) break;
+    // Cholesky update with g_k = G[j*][I_k]
+    float wn2 = 0.f;
+    for (int m = 0; m < t; ++m) {
+      float acc = GC(bq, si[m * RT + tid]);
+      for (int qq = 0; qq < m; ++qq) acc = fmaf(-LS(m, qq), LS(t, qq), acc);
+      const float w = acc / LS(m, m);
+      LS(t, m) = w;
+      wn2 = fmaf(w, w, wn2);
+    }
+    const float gjj = GC(bq, bq);
+    const float ell2 = gjj - wn2;
+    if (!(ell2 > PIVOT_MIN * gjj)) break;
+    const float ell = sqrtf(ell2);
+    LS(t, t) = ell;
+    float yt = a0[bq * RT + tid];
+    for (int m = 0; m < t; ++m) yt = fmaf(-LS(t, m), ys[m * RT + tid], yt);
+    ys[t * RT + tid] = yt / ell;
+    si[t * RT + tid] = bq;
+    taken |= 1u << bq;
+    ++t;
+    for (int m = t - 1; m >= 0; --m) {
+      float acc = ys[m * RT + tid];
+      for (int qq = m + 1; qq < t; ++qq) acc = fmaf(-LS(qq, m), gs[qq * RT + tid], acc);
+      gs[m * RT + tid] = acc / LS(m, m);
+    }
+  }
+  // explicit residual of the final code
+#pragma unroll
+  for (int k = 0; k < 48; ++k) x[k] = k < DLSH_D ? x[k] : 0.f;
+  for (int m = 0; m < t; ++m) {
+    const float gm = gs[m * RT + tid];
+    int qsel = si[m * RT + tid];
+    int j = 0;
+#pragma unroll
+    for (int q = 0; q < M; ++q)
+      if (q == qsel) j = cj[q];
+    const float4* dr = reinterpret_cast<const float4*>(D32p + static_cast<size_t>(j) * DPAD);
+#pragma unroll
+    for (int u = 0; u < 12; ++u) {
+      const float4 dv = __ldg(dr + u);
+      x[4 * u + 0] = fmaf(-gm, dv.x, x[4 * u + 0]);
+      x[4 * u + 1] = fmaf(-gm, dv.y, x[4 * u + 1]);
+      x[4 * u + 2] = fmaf(-gm, dv.z, x[4 * u + 2]);
+      x[4 * u + 3] = fmaf(-gm, dv.w, x[4 * u + 3]);
+    }
+    idx[n * s + m] = static_cast<uint16_t>(j);
+    coef[n * s + m] = gm;
+  }
+  for (int m = t; m < s; ++m) {
+    idx[n * s + m] = 0;
+    coef[n * s + m] = 0.f;
+  }
+  float r2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < 48; ++k) r2 = fmaf(x[k], x[k], r2);
+  nnz[n] = static_cast<uint8_t>(t);
+  resid[n] = r2;
+  if (bad) flag_status(status, ST_BAD_INPUT);
+#undef GC
+#undef LS
+}
+
+// exact mode: keep the plain code where its residual is smaller (1e-6 relative)
+__global__ void choose_kernel(long long N, int s, const float* __restrict__ rL,
+                              const float* __restrict__ rP, const uint16_t* __restrict__ iP,
+                              const float* __restrict__ cP, const uint8_t* __restrict__ nP,
+                              uint16_t* __restrict__ idx, float* __restrict__ coef,
+                              uint8_t* __restrict__ nnz, float* __restrict__ resid,
+                              unsigned long long* __restrict__ nfb) {
+  const long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool fb = false;
+  if (i < N) {
+    fb = sqrtf(rL[i]) > sqrtf(rP[i]) * (1.f + 1e-6f);
+    if (fb) {
+      for (int m = 0; m < s; ++m) {
+        idx[i * s + m] = iP[i * s + m];
+        coef[i * s + m] = cP[i * s + m];
+      }
+      nnz[i] = nP[i];
+      resid[i] = rP[i];
+    }
+  }
+  const unsigned cnt = __popc(__ballot_sync(0xffffffffu, fb));
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(nfb, static_cast<unsigned long long>(cnt));
+}
+
+// deploy mode: flags, per-block counts, offsets, compaction (signal order)
+constexpr int CB = 1024;
+__global__ void fb_count_kernel(const float* __restrict__ rL, long long N, float tau2,
+                                int* __restrict__ part) {
+  __shared__ int red[CB];
+  const long long i = static_cast<long long>(blockIdx.x) * CB + threadIdx.x;
+  red[threadIdx.x] = (i < N && rL[i] > tau2) ? 1 : 0;
+  __syncthreads();
+  for (int w = CB / 2; w > 0; w >>= 1) {
+    if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void fb_scan_kernel(int* part, int nblocks, long long* total) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    long long run = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      const int v = part[b];
+      part[b] = static_cast<int>(run);
+      run += v;
+    }
+    *total = run;
+  }
+}
+__global__ void fb_compact_kernel(const float* __restrict__ rL, const float* __restrict__ X,
+                                  long long N, float tau2, const int* __restrict__ part,
+                                  long long* __restrict__ list, float* __restrict__ Xfb) {
+  __shared__ int sc[CB];
+  const long long i = static_cast<long long>(blockIdx.x) * CB + threadIdx.x;
+  const int f = (i < N && rL[i] > tau2) ? 1 : 0;
+  sc[threadIdx.x] = f;
+  __syncthreads();
+  for (int o = 1; o < CB; o <<= 1) {
+    const int v = static_cast<int>(threadIdx.x) >= o ? sc[threadIdx.x - o] : 0;
+    __syncthreads();
+    sc[threadIdx.x] += v;
+    __syncthreads();
+  }
+  if (f) {
+    const long long pos = part[blockIdx.x] + sc[threadIdx.x] - 1;
+    list[pos] = i;
+    for (int k = 0; k < DLSH_D; ++k) Xfb[pos * DLSH_D + k] = X[i * DLSH_D + k];
+  }
+}
+__global__ void fb_scatter_kernel(const long long* __restrict__ list, const long long* __restrict__ total,
+                                  int s, const uint16_t* __restrict__ iF, const float* __restrict__ cF,
+                                  const uint8_t* __restrict__ nF, const float* __restrict__ rF,
+                                  uint16_t* __restrict__ idx, float* __restrict__ coef,
+                                  uint8_t* __restrict__ nnz, float* __restrict__ resid) {
+  const long long k = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= *total) return;
+  const long long i = list[k];
+  for (int m = 0; m < s; ++m) {
+    idx[i * s + m] = iF[k * s + m];
+    coef[i * s + m] = cF[k * s + m];
+  }
+  nnz[i] = nF[k];
+  resid[i] = rF[k];
+}
+
+}  // namespace lrn
+
+static int restricted_launch(const float* X, long long N, const float* D32p, const float* G, int K,
+                             const uint16_t* cand, int m, int s, float eps, uint16_t* idx,
+                             float* coef, uint8_t* nnz, float* resid, uint32_t* status,
+                             cudaStream_t st) {
+  using namespace lrn;
+  if (N == 0) return DLSH_OK;
+  const size_t smem = static_cast<size_t>(rest_words(m, s)) * RT * 4;
+  const int grid = static_cast<int>((N + RT - 1) / RT);
+#define LAUNCH(MM)                                                                              \
+  do {                                                                                          \
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(restricted_omp_kernel<MM>,                               \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,             \
+                                       static_cast<int>(smem)),                                 \
+                  "dlsh_encode_restricted: attribute");                                         \
+    restricted_omp_kernel<MM><<<grid, RT, smem, st>>>(X, N, D32p, G, K, cand, s, eps, idx, coef, \
+                                                      nnz, resid, status);                      \
+  } while (0)
+  switch (m) {
+    case 2: LAUNCH(2); break;
+    case 4: LAUNCH(4); break;
+    case 8: LAUNCH(8); break;
+    case 16: LAUNCH(16); break;
+    case 32: LAUNCH(32); break;
+    default: return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_restricted: m must be 2, 4, 8, 16 or 32");
+  }
+#undef LAUNCH
+  count_launches(1);
+  return check_launch("dlsh_encode_restricted: launch");
+}
+
+namespace lrn {
+constexpr long long CHUNK = 65536;  // rows per MLP inference chunk
+
+struct Ws {
+  uint32_t* status;
+  void* enc;          // encoder workspace (prepared dictionary, Gram)
+  void* mlpws;        // MLP forward workspace for CHUNK rows
+  uint16_t* cand;     // N x m
+  uint16_t* iP;       // N x s   plain / fallback codes
+  float* cP;
+  uint8_t* nP;
+  float* rP;
+  long long* list;    // N
+  float* Xfb;         // N x 45
+  int* part;          // blocks
+  long long* total;   // 1
+  unsigned long long* nfb;
+};
+inline size_t carve(void* base, int K, int s, long long N, Ws& w) {
+  const long long m = 2 * s;
+  const long long rows = N < CHUNK ? (N > 0 ? N : 1) : CHUNK;
+  Carver c(base);
+  w.status = c.take<uint32_t>(64);
+  w.enc = c.take<uint8_t>(encode_ws_bytes(K, s, 0));
+  w.mlpws = c.take<uint8_t>(mlp_train_ws_bytes(K, rows));
+  w.cand = c.take<uint16_t>(N * m + 1);
+  w.iP = c.take<uint16_t>(N * s + 1);
+  w.cP = c.take<float>(N * s + 1);
+  w.nP = c.take<uint8_t>(N + 1);
+  w.rP = c.take<float>(N + 1);
+  w.list = c.take<long long>(N + 1);
+  w.Xfb = c.take<float>(N * DLSH_D + 1);
+  w.part = c.take<int>((N + CB - 1) / CB + 1);
+  w.total = c.take<long long>(2);
+  w.nfb = c.take<unsigned long long>(2);
+  return c.size();
+}
+}  // namespace lrn
+
+int propose_enqueue(const void* mlp, int K, const float* X, long long N, int m, uint16_t* cand,
+                    void* mlpws, cudaStream_t st) {
+  for (long long r0 = 0; r0 < N; r0 += lrn::CHUNK) {
+    const long long rows = N - r0 < lrn::CHUNK ? N - r0 : lrn::CHUNK;
+    float* logits = nullptr;
+    int rc = mlp_forward_enqueue(mlp, K, X + r0 * DLSH_D, rows, mlpws, &logits, st);
+    if (rc) return rc;
+    rc = mlp_topk_enqueue(logits, rows, K, m, cand + r0 * m, st);
+    if (rc) return rc;
+  }
+  return DLSH_OK;
+}
+
+}  // namespace dlsh
+
+extern "C" {
+
+size_t dlsh_mlp_propose_workspace_size(int K, int64_t N) {
+  if (K < 1 || K > DLSH_MAX_K || N < 0) return 0;
+  return dlsh::mlp_train_ws_bytes(K, N < dlsh::lrn::CHUNK ? (N > 0 ? N : 1) : dlsh::lrn::CHUNK);
+}
+
+int dlsh_mlp_propose(const void* mlp, int K, const float* X, int64_t N, int m, uint16_t* cand,
+                     void* ws, size_t ws_bytes, void* stream, int flags) {
+  using namespace dlsh;
+  clear_error();
+  if (!mlp || K < 1 || K > DLSH_MAX_K || N < 0 || (N > 0 && (!X || !cand)))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_mlp_propose: bad arguments");
+  if (m != 2 && m != 4 && m != 8 && m != 16 && m != 32)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mlp_propose: m must be 2, 4, 8, 16 or 32");
+  int rc = check_workspace(ws, ws_bytes, dlsh_mlp_propose_workspace_size(K, N), "dlsh_mlp_propose");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = propose_enqueue(mlp, K, X, N, m, cand, ws, st);
+  if (rc) return rc;
+  return finish(st, nullptr, flags, "dlsh_mlp_propose");
+}
+
+int dlsh_encode_restricted(const float* D, int K, int d, const float* X, int64_t N,
+                           const uint16_t* cand, int m, int s, float eps, uint16_t* idx,
+                           float* coef, uint8_t* nnz, float* resid_sq, void* ws, size_t ws_bytes,
+                           void* stream, int flags) {
+  using namespace dlsh;
+  clear_error();
+  if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_restricted: d must be 45");
+  if (!D || K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || N < 0)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_restricted: bad sizes");
+  if (m < s || m > 32) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_restricted: need s <= m <= 32");
+  if (N > 0 && (!X || !cand || !idx || !coef || !nnz || !resid_sq))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_restricted: NULL array");
+  if (!(eps >= 0.f)) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_restricted: eps < 0");
+  int rc = check_workspace(ws, ws_bytes, encode_ws_bytes(K, s, 0), "dlsh_encode_restricted");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const float* D32p = nullptr;
+  const float* G = nullptr;
+  uint32_t* status = nullptr;
+  rc = encode_prepare_only(D, K, s, 0, ws, st, &D32p, &G, &status);
+  if (rc) return rc;
+  rc = restricted_launch(X, N, D32p, G, K, cand, m, s, eps, idx, coef, nnz, resid_sq, status, st);
+  if (rc) return rc;
+  return finish(st, status, flags, "dlsh_encode_restricted");
+}
+
+size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N) {
+  if (d != DLSH_D || K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || N < 0) return 0;
+  if (dlsh::encode_ws_bytes(K, s, 0) == 0) return 0;
+  dlsh::lrn::Ws w;
+  return dlsh::lrn::carve(nullptr, K, s, N, w);
+}
+
+int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N, int s, float eps,
+                        const void* mlp, int mode, float tau, int fallback_precision,
+                        uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq,
+                        unsigned long long* n_fallback, void* ws, size_t ws_bytes, void* stream,
+                        int flags) {
+  using namespace dlsh;
+  using namespace dlsh::lrn;
+  clear_error();
+  const size_t need = dlsh_encode_learned_workspace_size(K, d, s, N);
+  if (need == 0 || !mlp || !D) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: bad sizes");
+  if (2 * s > 32) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_learned: 2s must be <= 32");
+  if (mode != 0 && mode != 1) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: mode 0 or 1");
+  if (fallback_precision < 0 || fallback_precision > 2)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: unknown fallback precision");
+  if (N > 0 && (!X || !idx || !coef || !nnz || !resid_sq || !n_fallback))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: NULL array");
+  if (!(eps >= 0.f) || !(tau >= 0.f))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: eps and tau must be >= 0");
+  int rc = check_workspace(ws, ws_bytes, need, "dlsh_encode_learned");
+  if (rc) return rc;
+  Ws w;
+  carve(ws, K, s, N, w);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DLSH_CUDA_TRY(cudaMemsetAsync(w.nfb, 0, sizeof(unsigned long long), st), "dlsh_encode_learned: reset");
+  const int m = 2 * s;
+  const float* D32p = nullptr;
+  const float* G = nullptr;
+  uint32_t* status = nullptr;
+  rc = encode_prepare_only(D, K, s, 0, w.enc, st, &D32p, &G, &status);
+  if (rc) return rc;
+  rc = propose_enqueue(mlp, K, X, N, m, w.cand, w.mlpws, st);
+  if (rc) return rc;
+  rc = restricted_launch(X, N, D32p, G, K, w.cand, m, s, eps, idx, coef, nnz, resid_sq, status, st);
+  if (rc) return rc;
+  if (N > 0) {
+    if (mode == 0) {
+      uint32_t* est = nullptr;
+      rc = encode_enqueue(D, K, X, N, s, eps, fallback_precision, w.iP, w.cP, w.nP, w.rP, w.enc, st,
+                          &est);
+      if (rc) return rc;
+      choose_kernel<<<static_cast<int>((N + 255) / 256), 256, 0, st>>>(
+          N, s, resid_sq, w.rP, w.iP, w.cP, w.nP, idx, coef, nnz, resid_sq, w.nfb);
+      count_launches(1);
+    } else {
+      const int nb = static_cast<int>((N + CB - 1) / CB);
+      const float tau2 = tau * tau;
+      fb_count_kernel<<<nb, CB, 0, st>>>(resid_sq, N, tau2, w.part);
+      fb_scan_kernel<<<1, 1, 0, st>>>(w.part, nb, w.total);
+      fb_compact_kernel<<<nb, CB, 0, st>>>(resid_sq, X, N, tau2, w.part, w.list, w.Xfb);
+      count_launches(3);
+      uint32_t* est = nullptr;
+      rc = encode_enqueue(D, K, w.Xfb, N, s, eps, fallback_precision, w.iP, w.cP, w.nP, w.rP,
+                          w.enc, st, &est, nullptr, w.total);
+      if (rc) return rc;
+      fb_scatter_kernel<<<static_cast<int>((N + 255) / 256), 256, 0, st>>>(
+          w.list, w.total, s, w.iP, w.cP, w.nP, w.rP, idx, coef, nnz, resid_sq);
+      DLSH_CUDA_TRY(cudaMemcpyAsync(w.nfb, w.total, sizeof(long long), cudaMemcpyDeviceToDevice, st),
+                    "dlsh_encode_learned: count");
+      count_launches(1);
+    }
+  }
+  DLSH_CUDA_TRY(cudaMemcpyAsync(n_fallback, w.nfb, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToDevice, st),
+                "dlsh_encode_learned: count");
+  return finish(st, status, flags, "dlsh_encode_learned");
+}
+
+// tau such that falling back whenever ||r_learned|| > tau keeps the combined
+// RMSE within `max_ratio` of plain OMP's on this calibration set (host search
+// over the sorted learned residuals; the smallest fallback set wins).
+int dlsh_calibrate_fallback(const float* resid_learned, const float* resid_plain, int64_t N,
+                            float max_ratio, float* tau, void* stream) {
+  using namespace dlsh;
+  clear_error();
+  if (N < 1 || !resid_learned || !resid_plain || !tau || !(max_ratio >= 1.f))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_calibrate_fallback: bad arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float> rl(N), rp(N);
+  DLSH_CUDA_TRY(cudaMemcpyAsync(rl.data(), resid_learned, N * sizeof(float), cudaMemcpyDeviceToHost, st),
+                "dlsh_calibrate_fallback: copy");
+  DLSH_CUDA_TRY(cudaMemcpyAsync(rp.data(), resid_plain, N * sizeof(float), cudaMemcpyDeviceToHost, st),
+                "dlsh_calibrate_fallback: copy");
+  DLSH_CUDA_TRY(cudaStreamSynchronize(st), "dlsh_calibrate_fallback: sync");
+  double plain = 0.0, learned = 0.0;
+  for (int64_t i = 0; i < N; ++i) {
+    plain += rp[i];
+    learned += std::max(rl[i], 0.f);
+  }
+  const double budget = plain * static_cast<double>(max_ratio) * max_ratio;
+  std::vector<int64_t> order(N);
+  for (int64_t i = 0; i < N; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+    return rl[a] > rl[b] || (rl[a] == rl[b] && a < b);
+  });
+  // fall back on the k largest learned residuals, k = 0, 1, ...
+  double total = learned;
+  int64_t k = 0;
+  while (k < N && total > budget) {
+    const int64_t i = order[k];
+    total += static_cast<double>(rp[i]) - std::max(rl[i], 0.f);
+    ++k;
+  }
+  // tau sits just below the last learned residual that falls back
+  *tau = k >= N ? 0.f : std::sqrt(std::max(rl[order[k]], 0.f));
+  return DLSH_OK;
+}
+
+}  // extern "C"

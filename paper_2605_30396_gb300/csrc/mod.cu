@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "host.hpp"
+#include "internal.hpp"
 
 namespace dlsh {
 namespace mod {
@@ -54,7 +55,14 @@ struct Ws {
   double* Xb;      // K x RW solution D~^T
   double* lam;     // [0] lambda
   int* dead;       // K
+  int* seg_start;  // K + 1: first accumulation segment of each atom
+  double* Gp;      // max_segs x K partial G rows
+  double* Bp;      // max_segs x RW partial B columns
 };
+
+constexpr int SEG = 4096;  // list entries per accumulation segment
+
+inline int64_t max_segments(int K, int s, int64_t N) { return (N * s + SEG - 1) / SEG + K; }
 
 static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   Carver c(base);
@@ -75,6 +83,9 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.Xb = c.take<double>(static_cast<size_t>(K) * RW);
   w.lam = c.take<double>(4);
   w.dead = c.take<int>(K);
+  w.seg_start = c.take<int>(K + 1);
+  w.Gp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * K);
+  w.Bp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * RW);
   return c.size();
 }
 
@@ -258,11 +269,10 @@ __host__ __device__ constexpr int acc_buf_words(int s) {
 __global__ void __launch_bounds__(128)
     accum_kernel(const float* __restrict__ X, const uint32_t* __restrict__ idxw,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
-                 const int* __restrict__ list_sig, const float* __restrict__ list_coef,
-                 const uint8_t* __restrict__ list_nnz, double* __restrict__ M,
-                 double* __restrict__ Z) {
+                 const int* __restrict__ seg_start, const int* __restrict__ list_sig,
+                 const float* __restrict__ list_coef, const uint8_t* __restrict__ list_nnz,
+                 double* __restrict__ Gp, double* __restrict__ Bp) {
   extern __shared__ __align__(16) float smf[];
-  const int j = blockIdx.x;
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sw = s / 2 + 1;
@@ -270,12 +280,25 @@ __global__ void __launch_bounds__(128)
   float* ghi = smf + static_cast<size_t>(warp) * 2 * K;
   float* glo = ghi + K;
   float* wbuf = smf + static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(warp) * 2 * bw;
+  const int nseg = seg_start[K];
+  for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
+  // the segment's atom: the largest j with seg_start[j] <= seg
+  int j = 0;
+  {
+    int lo = 0, hi = K - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (seg_start[mid] <= seg) lo = mid; else hi = mid - 1;
+    }
+    j = lo;
+  }
   for (int k = lane; k < K; k += 32) {
     ghi[k] = 0.f;
     glo[k] = 0.f;
   }
   float b0h = 0.f, b0l = 0.f, b1h = 0.f, b1l = 0.f;
-  const int e0 = atom_start[j], e1 = atom_start[j + 1];
+  const int e0 = atom_start[j] + (seg - seg_start[j]) * SEG;
+  const int e1 = e0 + SEG < atom_start[j + 1] ? e0 + SEG : atom_start[j + 1];
   const int len = e1 - e0;
   const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
   const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
@@ -371,7 +394,7 @@ __global__ void __launch_bounds__(128)
       const float* gh = smf + static_cast<size_t>(w) * 2 * K;
       acc += static_cast<double>(gh[k]) + static_cast<double>(gh[K + k]);
     }
-    M[static_cast<size_t>(j) * K + k] = acc;
+    Gp[static_cast<size_t>(seg) * K + k] = acc;
   }
   for (int q = threadIdx.x; q < RW; q += blockDim.x) {
     double acc = 0.0;
@@ -380,6 +403,46 @@ __global__ void __launch_bounds__(128)
                                                          static_cast<size_t>(w) * 2 * bw);
       acc += bp[q];
     }
+    Bp[static_cast<size_t>(seg) * RW + q] = acc;
+  }
+  __syncthreads();  // shared partials are reused by the next segment
+  }
+}
+
+// Segment counts per atom (ceil(n_j / SEG)) and their exclusive scan.
+__global__ void seg_scan_kernel(const int* __restrict__ atom_total, int K,
+                                int* __restrict__ seg_start) {
+  __shared__ int sm[1024];
+  __shared__ int carry_s;
+  int carry = 0;
+  for (int base = 0; base < K; base += 1024) {
+    const int j = base + threadIdx.x;
+    const int v = j < K ? (atom_total[j] + SEG - 1) / SEG : 0;
+    int tot = 0;
+    const int ex = block_exclusive_scan(v, sm, &tot);
+    if (j < K) seg_start[j] = carry + ex;
+    if (threadIdx.x == 0) carry_s = carry + tot;
+    __syncthreads();
+    carry = carry_s;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) seg_start[K] = carry;
+}
+
+// Row j of G and column j of B: the atom's segment partials summed in order.
+__global__ void seg_reduce_kernel(const int* __restrict__ seg_start, const double* __restrict__ Gp,
+                                  const double* __restrict__ Bp, int K, double* __restrict__ M,
+                                  double* __restrict__ Z) {
+  const int j = blockIdx.x;
+  const int s0 = seg_start[j], s1 = seg_start[j + 1];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    double acc = 0.0;
+    for (int sg = s0; sg < s1; ++sg) acc += Gp[static_cast<size_t>(sg) * K + k];
+    M[static_cast<size_t>(j) * K + k] = acc;
+  }
+  for (int q = threadIdx.x; q < RW; q += blockDim.x) {
+    double acc = 0.0;
+    for (int sg = s0; sg < s1; ++sg) acc += Bp[static_cast<size_t>(sg) * RW + q];
     Z[static_cast<size_t>(j) * RW + q] = acc;
   }
 }
@@ -708,11 +771,23 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   DLSH_CUDA_TRY(cudaFuncSetAttribute(accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(acc_smem)),
                 "dlsh_mod_update: attribute");
-  accum_kernel<<<K, acc_nw * 32, acc_smem, st>>>(X, reinterpret_cast<const uint32_t*>(idx), coef, s,
-                                                 K, w.atom_start, w.list_sig, w.list_coef,
-                                                 w.list_nnz, w.M, w.Z);
+  seg_scan_kernel<<<1, 1024, 0, st>>>(w.atom_total, K, w.seg_start);
+  {
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 1;
+    int per_sm = static_cast<int>(SMEM_LIMIT / (acc_smem > 0 ? acc_smem : 1));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    int64_t grid = static_cast<int64_t>(sms) * per_sm;
+    const int64_t ms = max_segments(K, s, N);
+    if (grid > ms) grid = ms;
+    accum_kernel<<<static_cast<int>(grid), acc_nw * 32, acc_smem, st>>>(
+        X, reinterpret_cast<const uint32_t*>(idx), coef, s, K, w.atom_start, w.seg_start,
+        w.list_sig, w.list_coef, w.list_nnz, w.Gp, w.Bp);
+  }
+  seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, w.M, w.Z);
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
-  launches += 2;
+  launches += 4;
   const int nblk = (K + NB - 1) / NB;
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * NB;

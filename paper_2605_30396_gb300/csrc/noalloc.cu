@@ -9,13 +9,9 @@
 #include <mutex>
 
 #include "host.hpp"
+#include "internal.hpp"
 
 namespace dlsh {
-
-int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, float eps, int prec,
-                   uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq, void* ws,
-                   cudaStream_t st, uint32_t** status_out);
-size_t encode_ws_bytes(int K, int s, int prec);
 
 namespace noalloc {
 

@@ -1,0 +1,56 @@
+"""Many scenes in one call (each encoded as a single-scene call would encode
+it, scenes running concurrently on forked streams); the chunk-width autotuner."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2605_30396_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene(i, N, K, s):
+    D = synth.hidden_dictionary(K, 1000 + i).astype(np.float32)
+    X = synth.signals(N, synth.hidden_dictionary(K, 2000 + i), min(s, 8), 3000 + i)
+    return {"D": torch.from_numpy(D).cuda(), "X": torch.from_numpy(X).cuda(), "s": s}
+
+
+SPECS = [(0, 5000, 512, 4), (1, 777, 1024, 8), (2, 2000, 1024, 16), (3, 700, 2048, 8),
+         (4, 0, 64, 4), (5, 1, 300, 2), (6, 129, 64, 1)]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
+def test_multi_equals_single_calls(lib, prec):
+    scenes = [_scene(*sp) for sp in SPECS]
+    outs = lib.encode_multi(scenes, precision=prec, sync=True)
+    for sc, o in zip(scenes, outs):
+        ref = lib.encode(sc["D"], sc["X"], sc["s"], precision=prec, sync=True)
+        for a, b in zip(o, ref):
+            np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_multi_under_graph_capture(lib):
+    scenes = [_scene(*sp) for sp in SPECS[:3]]
+    ref = lib.encode_multi(scenes, sync=True)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        lib.encode_multi(scenes)  # warm-up: workspace and internal streams exist
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        outs = lib.encode_multi(scenes)
+    g.replay()
+    torch.cuda.synchronize()
+    for o, r in zip(outs, ref):
+        for a, b in zip(o, r):
+            np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+
+
+def test_autotune_keeps_results(lib):
+    sc = _scene(9, 20000, 1024, 8)
+    before = lib.encode(sc["D"], sc["X"], 8, sync=True)
+    bn = lib.autotune_encode(sc["D"], sc["X"][:8192], 8)
+    assert bn in (64, 128)
+    after = lib.encode(sc["D"], sc["X"], 8, sync=True)
+    for a, b in zip(before, after):
+        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
