@@ -95,12 +95,15 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                 void* stream, int flags);
 
 /*
- * dlsh_encode with per-phase timing: identical results, plus six counters in
- * `cycles` (device, uint64[6], zeroed by the call) summed over the first
- * selection/solver thread of every CTA, in SM clock cycles: waiting for the
+ * dlsh_encode with per-phase timing: identical results, plus ten counters in
+ * `cycles` (device, uint64[10], zeroed by the call) summed over all CTAs, in SM
+ * clock cycles.  From the first selection/solver thread: waiting for the
  * tensor cores, the selection phase (including that wait), the barrier after
  * selection, the solver phase, the barrier after the solver, and the number of
- * OMP iterations counted.
+ * OMP iterations counted.  From the MMA-issuing thread: waiting for the A
+ * operand (the residual), for a dictionary chunk to land, and for a TMEM
+ * buffer to be released.  From the TMA-producing thread: waiting for a free
+ * ring stage.
  */
 int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
                         int s, float eps, int precision, uint16_t* idx,

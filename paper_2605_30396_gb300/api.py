@@ -118,7 +118,7 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
     coef = torch.empty((N, s), dtype=torch.float32, device=X.device)
     nnz = torch.empty((N,), dtype=torch.uint8, device=X.device)
     resid = torch.empty((N,), dtype=torch.float32, device=X.device)
-    cyc = torch.zeros((6,), dtype=torch.int64, device=X.device)
+    cyc = torch.zeros((10,), dtype=torch.int64, device=X.device)
     L = _lib.lib()
     need = L.dlsh_encode_workspace_size(K, D.shape[1], s, _prec(precision))
     ws = workspace(need, key="encode")
@@ -126,7 +126,8 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
                                _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws), ws.numel(), _p(cyc),
                                _stream(), FLAG_SYNC)
     _check(rc, "dlsh_encode_profile")
-    names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations")
+    names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations",
+             "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "tma_wait_stage")
     return (idx, coef, nnz, resid), dict(zip(names, cyc.cpu().tolist()))
 
 

@@ -51,7 +51,7 @@ __host__ __device__ constexpr int op_parts(int prec) { return prec == 0 ? 2 : 1;
 struct Plan {
   int prec, BN, K, Kp, nchunks, stages, resident, s;
   uint32_t a_bytes, chunk_bytes;
-  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_rowt, off_cand, off_r,
+  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_idg, off_rowt, off_cand, off_r,
       off_sig, off_bar, smem;
 };
 
@@ -84,6 +84,7 @@ int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM
   p.off_sel = take(s * TILE_M * 4);
   p.off_y = take(s * TILE_M * 4);
   p.off_g = take(s * TILE_M * 4);
+  p.off_idg = take(s * TILE_M * 4);
   p.off_rowt = take(TILE_M * 4);
   p.off_cand = take(TILE_M * 4 * (prec == 0 ? 1 : 4) * 8);
   p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
@@ -451,7 +452,8 @@ __device__ __forceinline__ void tmem_ld_wait<16>(uint32_t (&r)[16]) {
   tmem_ld16_wait(r);
 }
 
-template <int PREC, int BN>
+// SMAX: compile-time bound on s (8 or 16) for the solver's register arrays.
+template <int PREC, int BN, int SMAX>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NBUF = 512 / BN;
@@ -471,6 +473,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_dempty + p.stages);
 
   if (tid == 0) {
+    if (a.prof)
+      for (int k = 0; k < 12; ++k)
+        reinterpret_cast<unsigned long long*>(smem + p.off_bar + 928)[k] = 0;
     mbar_init(bar_a, 1);
     for (int b = 0; b < NBUF; ++b) {
       mbar_init(&bar_full[b], 1);
@@ -492,6 +497,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   const uint32_t tmem_base = *tmem_slot;
   const uint32_t a_addr = smem_u32(smem + p.off_a);
   const uint32_t ring_addr = smem_u32(smem + p.off_ring);
+  // optional phase profile (SM cycles), one shared-memory slot per counter:
+  // 0-5 first selection/solver thread, 6-8 MMA issuer, 9 TMA producer
+  unsigned long long* pcs = reinterpret_cast<unsigned long long*>(smem + p.off_bar + 928);
+  const bool prof_any = a.prof != nullptr;
 
   if (warp == NEPI / 32 + 1) {
     // ------------------------------------------------ TMA producer
@@ -513,11 +522,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             for (int c = 0; c < sd.nchunks; ++c, ++ring) {
               const int st = static_cast<int>(ring % p.stages);
               const uint32_t par = static_cast<uint32_t>((ring / p.stages) & 1) ^ 1u;
+              const long long Wp = prof_any ? clock64() : 0;
               if (!mbar_wait(&bar_dempty[st], par, a.budget)) {
                 flag_status(a.status, ST_TIMEOUT);
                 ok = false;
                 break;
               }
+              if (prof_any) pcs[9] += clock64() - Wp;
               mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
               bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
                        sd.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes,
@@ -546,11 +557,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         tile_scene(a, NS, tile, sd, lt);
         const int nchunks = sd.nchunks;
         for (int it = 0; it < sd.s && ok; ++it) {
+          const long long Wa = prof_any ? clock64() : 0;
           if (!mbar_wait(bar_a, a_phase, a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
             ok = false;
             break;
           }
+          if (prof_any) pcs[6] += clock64() - Wa;
           a_phase ^= 1u;
           tc_fence_after();
           for (int c = 0; c < nchunks; ++c, ++cc) {
@@ -565,8 +578,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             }
             const int buf = static_cast<int>(cc % NBUF);
             const uint32_t epar = static_cast<uint32_t>((cc / NBUF) & 1) ^ 1u;
-            if (!mbar_wait(&bar_dfull[st], dpar, a.budget) ||
-                !mbar_wait(&bar_empty[buf], epar, a.budget)) {
+            const long long Wd = prof_any ? clock64() : 0;
+            const bool okd = mbar_wait(&bar_dfull[st], dpar, a.budget);
+            const long long We = prof_any ? clock64() : 0;
+            const bool oke = okd && mbar_wait(&bar_empty[buf], epar, a.budget);
+            if (prof_any) {
+              pcs[7] += We - Wd;
+              pcs[8] += clock64() - We;
+            }
+            if (!oke) {
               flag_status(a.status, ST_TIMEOUT);
               ok = false;
               break;
@@ -590,6 +610,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     int* sel = reinterpret_cast<int*>(smem + p.off_sel);        // [m][128]
     float* ys = reinterpret_cast<float*>(smem + p.off_y);       // [m][128]
     float* gs = reinterpret_cast<float*>(smem + p.off_g);       // [m][128]
+    float* idg = reinterpret_cast<float*>(smem + p.off_idg);   // [m][128] 1 / L(m, m)
     int* rowt = reinterpret_cast<int*>(smem + p.off_rowt);      // [128] support size
     float* cv = reinterpret_cast<float*>(smem + p.off_cand);    // [128][4][NCAND]
     int* cj = reinterpret_cast<int*>(smem + p.off_cand + TILE_M * 4 * NCAND * 4);
@@ -606,9 +627,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
                           static_cast<uint32_t>(q1 * QC);
 #define LS(rr, cc2) Ls[(((rr) * ((rr) + 1)) / 2 + (cc2)) * TILE_M + R2]
+#define IDG(rr) idg[(rr) * TILE_M + R2]
     long long cc = 0;
     bool ok = true;
-    long long pc_wait = 0, pc_p1 = 0, pc_b1 = 0, pc_p2 = 0, pc_b2 = 0, pc_it = 0;
+    const bool prof_on = prof_any && tid == 0;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       SceneDev sd;
       int lt;
@@ -658,14 +680,74 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       if (tid == 0) mbar_arrive(bar_a);
 
       for (int it = 0; it < s; ++it) {
-        const long long T0 = clock64();
+        const long long T0 = prof_on ? clock64() : 0;
         // ================= phase 1: selection over this thread's column quarter
-        const int t1 = rowt[R1];
-        // Only strictly positive |c| are candidates: atoms already in the
-        // support and padding atoms are zeroed first, so they never qualify.
-        float tv[4] = {0.f, 0.f, 0.f, 0.f};
-        int tj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-        auto process = [&](uint32_t (&rr)[QC], int c) {
+        auto acquire = [&](long long ccq) -> bool {  // wait for the chunk's MMAs
+          const int buf = static_cast<int>(ccq % NBUF);
+          const long long W0 = prof_on ? clock64() : 0;
+          if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((ccq / NBUF) & 1), a.budget)) {
+            flag_status(a.status, ST_TIMEOUT);
+            return false;
+          }
+          if (prof_on) pcs[0] += clock64() - W0;
+          tc_fence_after();
+          return true;
+        };
+        auto release = [&](long long ccq) {  // the chunk's TMEM buffer may be reused
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_empty[static_cast<int>(ccq % NBUF)]);
+        };
+        if constexpr (PREC == 0) {
+          // Argmax of |c| on 32-bit keys: |c| with its low 5 mantissa bits
+          // replaced by 31 - k (k = column within the quarter), so one integer
+          // max per element yields the largest value and, among values equal
+          // to 2^-18 relative, the smallest column.  Chunks are compared on
+          // the value bits only (strictly greater wins), so ties go to the
+          // smallest atom index overall.  Atoms already in the support are not
+          // masked here (see the solver's stop rule).
+          uint32_t best = 0;
+          int bestc = 0;
+          for (int c = 0; c < nchunks; ++c, ++cc) {
+            if (!acquire(cc)) {
+              ok = false;
+              break;
+            }
+            __syncwarp();
+            uint32_t rr[QC];
+            tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
+            tmem_ld_wait<QC>(rr);
+            release(cc);
+            uint32_t m0 = 0, m1 = 0;
+#pragma unroll
+            for (int k = 0; k < QC; k += 2) {
+              m0 = max(m0, (rr[k] & 0x7fffffe0u) | static_cast<uint32_t>(31 - k));
+              m1 = max(m1, (rr[k + 1] & 0x7fffffe0u) | static_cast<uint32_t>(30 - k));
+            }
+            const uint32_t m = max(m0, m1);
+            if ((m & ~31u) > (best & ~31u)) {
+              best = m;
+              bestc = c;
+            }
+          }
+          cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
+          cj[R1 * 4 + q1] = bestc * BN + q1 * QC + 31 - static_cast<int>(best & 31u);
+        } else {
+          const int t1 = rowt[R1];
+          // Only strictly positive |c| are candidates: atoms already in the
+          // support and padding atoms are zeroed first, so they never qualify.
+          float tv[4] = {0.f, 0.f, 0.f, 0.f};
+          int tj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
+          for (int c = 0; c < nchunks; ++c, ++cc) {
+            if (!acquire(cc)) {
+              ok = false;
+              break;
+            }
+            __syncwarp();
+            uint32_t rr[QC];
+            tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
+            tmem_ld_wait<QC>(rr);
+            release(cc);
             const int j0 = c * BN + q1 * QC;
             // exclusion mask of this chunk quarter: selected atoms and j >= K
             uint32_t em = (K - j0 < QC) ? ~((K - j0 <= 0) ? 0u : ((1u << (K - j0)) - 1u)) : 0u;
@@ -685,18 +767,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               m0 = fmaxf(m0, __uint_as_float(rr[k]));
               m1 = fmaxf(m1, __uint_as_float(rr[k + 1]));
             }
-            const float m = fmaxf(m0, m1);
-            if constexpr (PREC == 0) {
-              // exact argmax: the first (smallest) index attaining the maximum
-              if (m > tv[0]) {
-                int bk = 0;
-#pragma unroll
-                for (int k = QC - 1; k >= 0; --k)
-                  if (__uint_as_float(rr[k]) == m) bk = k;
-                tv[0] = m;
-                tj[0] = j0 + bk;
-              }
-            } else if (m > tv[3]) {
+            if (fmaxf(m0, m1) > tv[3]) {
               // top 4 of this chunk quarter with a branchless min/max network on
               // keys (|c| with its low 5 mantissa bits replaced by 31 - k, so
               // larger keys mean larger values and, on ties, smaller indices),
@@ -723,49 +794,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 if (val > tv[3]) top4_insert(tv, tj, val, j0 + 31 - static_cast<int>(kk[e] & 31u));
               }
             }
-        };
-        auto acquire = [&](long long ccq) -> bool {  // wait for the chunk's MMAs
-          const int buf = static_cast<int>(ccq % NBUF);
-          const long long W0 = clock64();
-          if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((ccq / NBUF) & 1), a.budget)) {
-            flag_status(a.status, ST_TIMEOUT);
-            return false;
           }
-          pc_wait += clock64() - W0;
-          tc_fence_after();
-          return true;
-        };
-        auto release = [&](long long ccq) {  // the chunk's TMEM buffer may be reused
-          tc_fence_before();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bar_empty[static_cast<int>(ccq % NBUF)]);
-        };
-        for (int c = 0; c < nchunks; ++c, ++cc) {
-          if (!acquire(cc)) {
-            ok = false;
-            break;
-          }
-          __syncwarp();
-          uint32_t rr[QC];
-          tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
-          tmem_ld_wait<QC>(rr);
-          release(cc);
-          process(rr, c);
-        }
 #pragma unroll
-        for (int k = 0; k < NCAND; ++k) {
-          cv[(R1 * 4 + q1) * NCAND + k] = tv[k];
-          cj[(R1 * 4 + q1) * NCAND + k] = tj[k];
+          for (int k = 0; k < NCAND; ++k) {
+            cv[(R1 * 4 + q1) * NCAND + k] = tv[k];
+            cj[(R1 * 4 + q1) * NCAND + k] = tj[k];
+          }
         }
-        const long long T1 = clock64();
+        const long long T1 = prof_on ? clock64() : 0;
         // barrier + vote: every selection thread leaves together if any wait ran out
         if (named_bar_or(1, NEPI, !ok)) {
           ok = false;
           break;
         }
-        const long long T2 = clock64();
+        const long long T2 = prof_on ? clock64() : 0;
 
         // ================= phase 2: merge, re-score, Cholesky, solve, residual
+        // Per-iteration quantities live in registers (arrays of SMAX entries,
+        // predicated on m < t); the factor L, y, gamma and the support stay in
+        // shared memory across iterations.  Every Gram entry and dictionary
+        // row the step needs is loaded as soon as the new atom is known.
         if (active && rn2 <= eps2) active = false;
         if (active) {
           float x[12], r[12];
@@ -774,6 +822,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 #pragma unroll
             for (int k = 0; k < 12; ++k) r[k] = rsm[k * NEPI + tid];
           }
+          int sl[SMAX];
+#pragma unroll
+          for (int m = 0; m < SMAX; ++m) sl[m] = m < t ? sel[m * TILE_M + R2] : 0;
           int js = -1;
           float best = -1.f;
           if constexpr (PREC == 0) {
@@ -786,6 +837,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 js = j;
               }
             }
+            // Support atoms are not masked in phase 1: the residual is
+            // orthogonal to them, so their |c| sits at rounding level and one
+            // of them wins only when every atom's correlation is at that
+            // level.  The row then stops, as no atom can reduce the residual
+            // by more than rounding.
+            bool dup = false;
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) dup |= (m < t && sl[m] == js);
+            if (dup) js = -1;
           } else {
             // entries with j >= K are empty slots (value 0, index INT_MAX)
             float mv[4] = {-1.f, -1.f, -1.f, -1.f};
@@ -820,60 +880,106 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
             active = false;
           } else {
-            // -------- Cholesky update: w = L^-1 g, g_m = <d_js, d_sel[m]>
+            // -------- prefetch: Gram row entries of the support and the new
+            // atom's dictionary row
             const float* Grow = sd.G + static_cast<size_t>(js) * K;
-            float wn2 = 0.f;
-            for (int mm = 0; mm < t; ++mm) {
-              float acc = __ldg(Grow + sel[mm * TILE_M + R2]);
-              for (int qq = 0; qq < mm; ++qq) acc = fmaf(-LS(mm, qq), LS(t, qq), acc);
-              const float w = acc / LS(mm, mm);
-              LS(t, mm) = w;  // the four sub-lanes store identical values
-              wn2 = fmaf(w, w, wn2);
-            }
+            float gv[SMAX];
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) gv[m] = m < t ? __ldg(Grow + sl[m]) : 0.f;
             const float gjj = __ldg(Grow + js);
+            float4 dj[3];
+            {
+              const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+#pragma unroll
+              for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
+            }
+            // -------- Cholesky update: w = L^-1 g, g_m = <d_js, d_sel[m]>
+            float w[SMAX];
+            float wn2 = 0.f;
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) {
+              w[m] = 0.f;
+              if (m < t) {
+                float acc = gv[m];
+#pragma unroll
+                for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
+                w[m] = acc * IDG(m);
+                wn2 = fmaf(w[m], w[m], wn2);
+              }
+            }
             const float ell2 = gjj - wn2;
             if (!(ell2 > PIVOT_MIN * gjj)) {
               active = false;
             } else {
               const float ell = sqrtf(ell2);
+              const float iell = 1.f / ell;
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m)
+                if (m < t) LS(t, m) = w[m];  // the four sub-lanes store identical values
               LS(t, t) = ell;
-              const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+              IDG(t) = iell;
               float bp = 0.f;
 #pragma unroll
               for (int w4 = 0; w4 < 3; ++w4) {
-                const float4 dv = __ldg(dr + w4);
-                bp = fmaf(dv.x, x[4 * w4 + 0], bp);
-                bp = fmaf(dv.y, x[4 * w4 + 1], bp);
-                bp = fmaf(dv.z, x[4 * w4 + 2], bp);
-                bp = fmaf(dv.w, x[4 * w4 + 3], bp);
+                bp = fmaf(dj[w4].x, x[4 * w4 + 0], bp);
+                bp = fmaf(dj[w4].y, x[4 * w4 + 1], bp);
+                bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
+                bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
               }
+              float yv[SMAX];
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m) yv[m] = m < t ? ys[m * TILE_M + R2] : 0.f;
               float yt = quad_sum(bp);
-              for (int mm = 0; mm < t; ++mm) yt = fmaf(-LS(t, mm), ys[mm * TILE_M + R2], yt);
-              yt /= ell;
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m)
+                if (m < t) yt = fmaf(-w[m], yv[m], yt);
+              yt *= iell;
               ys[t * TILE_M + R2] = yt;
               sel[t * TILE_M + R2] = js;
-              ++t;
-              // back substitution L^T gamma = y
-              for (int mm = t - 1; mm >= 0; --mm) {
-                float acc = ys[mm * TILE_M + R2];
-                for (int qq = mm + 1; qq < t; ++qq) acc = fmaf(-LS(qq, mm), gs[qq * TILE_M + R2], acc);
-                gs[mm * TILE_M + R2] = acc / LS(mm, mm);
+              // back substitution L^T gamma = y (the new atom's entry first)
+              const float gt = yt * iell;
+              float gam[SMAX];
+#pragma unroll
+              for (int m = SMAX - 1; m >= 0; --m) {
+                gam[m] = 0.f;
+                if (m < t) {
+                  float acc = yv[m];
+#pragma unroll
+                  for (int q = m + 1; q < SMAX; ++q)
+                    if (q < t) acc = fmaf(-LS(q, m), gam[q], acc);
+                  acc = fmaf(-w[m], gt, acc);
+                  gam[m] = acc * IDG(m);
+                }
               }
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m)
+                if (m < t) gs[m * TILE_M + R2] = gam[m];
+              gs[t * TILE_M + R2] = gt;
               // residual r = x - D_I gamma on this sub-lane's 12 dims
 #pragma unroll
               for (int k = 0; k < 12; ++k) r[k] = x[k];
-              for (int mm = 0; mm < t; ++mm) {
-                const float gm = gs[mm * TILE_M + R2];
-                const float4* da = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(sel[mm * TILE_M + R2]) * DPAD + 12 * u);
 #pragma unroll
-                for (int w4 = 0; w4 < 3; ++w4) {
-                  const float4 dv = __ldg(da + w4);
-                  r[4 * w4 + 0] = fmaf(-gm, dv.x, r[4 * w4 + 0]);
-                  r[4 * w4 + 1] = fmaf(-gm, dv.y, r[4 * w4 + 1]);
-                  r[4 * w4 + 2] = fmaf(-gm, dv.z, r[4 * w4 + 2]);
-                  r[4 * w4 + 3] = fmaf(-gm, dv.w, r[4 * w4 + 3]);
+              for (int m = 0; m < SMAX; ++m) {
+                if (m < t) {
+                  const float4* da = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
+#pragma unroll
+                  for (int w4 = 0; w4 < 3; ++w4) {
+                    const float4 dv = __ldg(da + w4);
+                    r[4 * w4 + 0] = fmaf(-gam[m], dv.x, r[4 * w4 + 0]);
+                    r[4 * w4 + 1] = fmaf(-gam[m], dv.y, r[4 * w4 + 1]);
+                    r[4 * w4 + 2] = fmaf(-gam[m], dv.z, r[4 * w4 + 2]);
+                    r[4 * w4 + 3] = fmaf(-gam[m], dv.w, r[4 * w4 + 3]);
+                  }
                 }
               }
+#pragma unroll
+              for (int w4 = 0; w4 < 3; ++w4) {
+                r[4 * w4 + 0] = fmaf(-gt, dj[w4].x, r[4 * w4 + 0]);
+                r[4 * w4 + 1] = fmaf(-gt, dj[w4].y, r[4 * w4 + 1]);
+                r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
+                r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
+              }
+              ++t;
               float pr = 0.f;
 #pragma unroll
               for (int k = 0; k < 12; ++k) pr = fmaf(r[k], r[k], pr);
@@ -898,15 +1004,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           }
         }
         fence_proxy_async_smem();
-        const long long T3 = clock64();
+        const long long T3 = prof_on ? clock64() : 0;
         named_bar_sync(1, NEPI);
         if (it + 1 < s && tid == 0) mbar_arrive(bar_a);
-        const long long T4 = clock64();
-        pc_p1 += T1 - T0;
-        pc_b1 += T2 - T1;
-        pc_p2 += T3 - T2;
-        pc_b2 += T4 - T3;
-        ++pc_it;
+        const long long T4 = prof_on ? clock64() : 0;
+        if (prof_on) {
+          pcs[1] += T1 - T0;
+          pcs[2] += T2 - T1;
+          pcs[3] += T3 - T2;
+          pcs[4] += T4 - T3;
+          pcs[5] += 1;
+        }
       }
       if (!ok) break;
       if (R2 < rows) {
@@ -922,17 +1030,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       }
     }
 #undef LS
-    if (a.prof && tid == 0) {
-      atomicAdd(a.prof + 0, static_cast<unsigned long long>(pc_wait));
-      atomicAdd(a.prof + 1, static_cast<unsigned long long>(pc_p1));
-      atomicAdd(a.prof + 2, static_cast<unsigned long long>(pc_b1));
-      atomicAdd(a.prof + 3, static_cast<unsigned long long>(pc_p2));
-      atomicAdd(a.prof + 4, static_cast<unsigned long long>(pc_b2));
-      atomicAdd(a.prof + 5, static_cast<unsigned long long>(pc_it));
-    }
+#undef IDG
   }
   tc_fence_before();
   __syncthreads();
+  if (prof_any && tid == 0)
+    for (int k = 0; k < 10; ++k) atomicAdd(a.prof + k, pcs[k]);
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem_base, 512);
@@ -1066,7 +1169,7 @@ static int validate(const char* call, const float* D, int K, int d, int s, int p
 
 template <int PREC, int BN>
 static int launch_encode(const Args& a, int grid, cudaStream_t st) {
-  auto fn = encode_kernel<PREC, BN>;
+  auto fn = a.p.s <= 8 ? encode_kernel<PREC, BN, 8> : encode_kernel<PREC, BN, 16>;
   DLSH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                 "dlsh_encode: cudaFuncSetAttribute");
   fn<<<grid, NTHREADS, a.p.smem, st>>>(a);
@@ -1230,7 +1333,7 @@ int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
   rc = check_workspace(ws, ws_bytes, encode_ws_bytes(K, s, precision), "dlsh_encode_profile");
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  DLSH_CUDA_TRY(cudaMemsetAsync(cycles, 0, 6 * sizeof(unsigned long long), st),
+  DLSH_CUDA_TRY(cudaMemsetAsync(cycles, 0, 10 * sizeof(unsigned long long), st),
                 "dlsh_encode_profile: reset");
   uint32_t* status = nullptr;
   rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status,

@@ -17,12 +17,13 @@
 //                       accumulation: about FP64 accuracy on the FP32 pipe,
 //                       since GB300's FP64 units are slow); slices are added
 //                       in a fixed order in FP64
-//   5. FP64 blocked Cholesky of G + lambda I (diagonal factor with its inverse,
-//      panel solve, trailing update), then blocked forward and backward
-//      substitution for the 45 right-hand sides using the diagonal inverses
+//   5. mixed-precision solve of (G + lambda I) D~^T = (B + lambda D_old)^T:
+//      Jacobi scaling S = diag^-1/2 (unit diagonal), FP32 blocked Cholesky of
+//      S (G + lambda I) S (diagonal factor with its inverse, panel, trailing
+//      update), FP32 triangular solves, and iterative refinement with the
+//      residual of the scaled system computed in FP64 (GB300's FP64 rate is
+//      a small fraction of its FP32 rate, so FP64 is spent only there)
 //   6. normalise, then refill unused atoms (argmax passes over resid_sq)
-// The factorisation stays in FP64 because G + lambda I can have condition
-// numbers near 1e6 and beyond.
 #include <math.h>
 
 #include "common.cuh"
@@ -38,6 +39,7 @@ constexpr int RW = 48;         // padded RHS width (45 used)
 constexpr int MAX_K = 4096;    // shared-memory G-row partials limit
 constexpr int SMEM_LIMIT = 232448;
 constexpr double RIDGE_REL = 1e-6;
+constexpr int kRefine = 3;     // FP32 solves (two FP64 residual corrections)
 
 struct Ws {
   uint32_t* status;
@@ -48,12 +50,16 @@ struct Ws {
   int* list_sig;   // N*s
   float* list_coef;
   uint8_t* list_nnz;
-  double* M;       // K x K (G, then G + lambda I, then its Cholesky factor)
-  double* Linv;    // nblk x 32 x 32 inverses of the diagonal blocks
+  double* M;       // K x K: G + lambda I (FP64, kept for the refinement residuals)
   double* Z;       // K x RW right-hand sides (B^T + lambda D_old)
-  double* Yb;      // K x RW forward-substitution result
-  double* Xb;      // K x RW solution D~^T
   double* lam;     // [0] lambda
+  double* dsc;     // K: Jacobi scale 1 / sqrt(M_jj)
+  float* A32;      // K x K: S M S, then its FP32 Cholesky factor (lower)
+  float* Linv32;   // nblk x 32 x 32 inverses of the factor's diagonal blocks
+  double* Zs;      // K x RW: S Z
+  double* Xs;      // K x RW: solution of the scaled system (FP64 accumulation)
+  float* R32;      // K x RW: current residual of the scaled system
+  double* Xb;      // K x RW: D~^T = S Xs
   int* dead;       // K
   int* seg_start;  // K + 1: first accumulation segment of each atom
   double* Gp;      // max_segs x K partial G rows
@@ -77,11 +83,15 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.list_coef = c.take<float>(static_cast<size_t>(N) * s + 1);
   w.list_nnz = c.take<uint8_t>(static_cast<size_t>(N) * s + 1);
   w.M = c.take<double>(static_cast<size_t>(K) * K);
-  w.Linv = c.take<double>(static_cast<size_t>(nblk) * NB * NB);
   w.Z = c.take<double>(static_cast<size_t>(K) * RW);
-  w.Yb = c.take<double>(static_cast<size_t>(K) * RW);
-  w.Xb = c.take<double>(static_cast<size_t>(K) * RW);
   w.lam = c.take<double>(4);
+  w.dsc = c.take<double>(K);
+  w.A32 = c.take<float>(static_cast<size_t>(K) * K);
+  w.Linv32 = c.take<float>(static_cast<size_t>(nblk) * NB * NB);
+  w.Zs = c.take<double>(static_cast<size_t>(K) * RW);
+  w.Xs = c.take<double>(static_cast<size_t>(K) * RW);
+  w.R32 = c.take<float>(static_cast<size_t>(K) * RW);
+  w.Xb = c.take<double>(static_cast<size_t>(K) * RW);
   w.dead = c.take<int>(K);
   w.seg_start = c.take<int>(K + 1);
   w.Gp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * K);
@@ -482,156 +492,256 @@ __global__ void ridge_kernel(double* __restrict__ M, double* __restrict__ Z,
   }
 }
 
-// ---- 5b. blocked Cholesky (lower, in place, row-major M[r*K + c]) -------------
-__global__ void potrf_diag_kernel(double* __restrict__ M, int K, int k0, double* __restrict__ Linv,
-                                  uint32_t* status) {
-  __shared__ double A[NB][NB + 1];
-  const int nb = K - k0 < NB ? K - k0 : NB;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 32
-  if (tx < nb && ty < nb) A[ty][tx] = M[static_cast<size_t>(k0 + ty) * K + k0 + tx];
-  __syncthreads();
-  for (int c = 0; c < nb; ++c) {
-    if (tx == 0 && ty == 0) {
-      double dv = A[c][c];
-      if (!(dv > 0.0)) {
-        flag_status(status, ST_BAD_INPUT);
-        dv = 1e-300;
-      }
-      A[c][c] = sqrt(dv);
-    }
-    __syncthreads();
-    if (tx == 0 && ty > c && ty < nb) A[ty][c] /= A[c][c];
-    __syncthreads();
-    if (ty > c && ty < nb && tx > c && tx <= ty) A[ty][tx] -= A[ty][c] * A[tx][c];
-    __syncthreads();
+// ---- 5b. Jacobi scaling: S = diag(M)^-1/2, A = S M S (FP32, lower), Zs = S Z --
+// One CTA per row j.  A has a unit diagonal, which keeps the FP32 factorisation
+// well scaled; the refinement below works on the same scaled system in FP64.
+__global__ void scale_kernel(const double* __restrict__ M, const double* __restrict__ Z, int K,
+                             double* __restrict__ dsc, float* __restrict__ A,
+                             double* __restrict__ Zs, float* __restrict__ R32,
+                             double* __restrict__ Xs) {
+  const int j = blockIdx.x;
+  const double dj = 1.0 / sqrt(M[static_cast<size_t>(j) * K + j]);
+  if (threadIdx.x == 0) dsc[j] = dj;
+  for (int k = threadIdx.x; k <= j; k += blockDim.x) {
+    const double dk = 1.0 / sqrt(M[static_cast<size_t>(k) * K + k]);
+    A[static_cast<size_t>(j) * K + k] = static_cast<float>(dj * M[static_cast<size_t>(j) * K + k] * dk);
   }
-  if (tx < nb && ty < nb) M[static_cast<size_t>(k0 + ty) * K + k0 + tx] = tx <= ty ? A[ty][tx] : 0.0;
-  // inverse of the factored block, one column per thread of the first row:
-  // X[r][c] = (delta_rc - sum_{c<=k<r} L[r][k] X[k][c]) / L[r][r]
-  __shared__ double Xi[NB][NB + 1];
-  if (ty == 0) {
-    const int c = tx;
-    for (int r = 0; r < NB; ++r) {
-      double v = 0.0;
-      if (r < nb && c < nb && r >= c) {
-        double acc = r == c ? 1.0 : 0.0;
-        for (int k = c; k < r; ++k) acc -= A[r][k] * Xi[k][c];
-        v = acc / A[r][r];
-      }
-      Xi[r][c] = v;
-    }
+  for (int c = threadIdx.x; c < RW; c += blockDim.x) {
+    const double z = c < DLSH_D ? dj * Z[static_cast<size_t>(j) * RW + c] : 0.0;
+    Zs[static_cast<size_t>(j) * RW + c] = z;
+    R32[static_cast<size_t>(j) * RW + c] = static_cast<float>(z);
+    Xs[static_cast<size_t>(j) * RW + c] = 0.0;
   }
-  __syncthreads();
-  Linv[(static_cast<size_t>(k0 / NB) * NB + ty) * NB + tx] = Xi[ty][tx];
 }
 
-// Rows below the diagonal block: L21 = A21 L11^-T, one thread per row.
-__global__ void trsm_panel_kernel(double* __restrict__ M, int K, int k0) {
-  __shared__ double L[NB][NB + 1];
+// ---- 5c. FP32 blocked Cholesky of A (lower, in place, row-major A[r*K + c]) ----
+// Factor and invert one 32 x 32 diagonal block in one warp: lane r holds row
+// r of the block in registers; pivots and L entries move by shuffles.  Rows
+// past the matrix end are padded with the identity and not written back.
+__global__ void __launch_bounds__(32) potrf_diag_kernel(float* __restrict__ M, int K, int k0,
+                                                        float* __restrict__ Linv,
+                                                        uint32_t* status) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
   const int nb = K - k0 < NB ? K - k0 : NB;
-  for (int f = threadIdx.x; f < NB * NB; f += blockDim.x) {
-    const int r = f / NB, c = f % NB;
-    L[r][c] = (r < nb && c < nb) ? M[static_cast<size_t>(k0 + r) * K + k0 + c] : 0.0;
+  float a[NB];
+#pragma unroll
+  for (int k = 0; k < NB; ++k)
+    a[k] = (lane < nb && k < nb) ? (k <= lane ? M[static_cast<size_t>(k0 + lane) * K + k0 + k] : 0.f)
+                                 : (k == lane ? 1.f : 0.f);
+  bool bad = false;
+#pragma unroll
+  for (int c = 0; c < NB; ++c) {
+    float d = __shfl_sync(FULL, a[c], c);
+    if (!(d > 0.f)) {
+      bad = true;
+      d = 1e-30f;
+    }
+    const float l = sqrtf(d);
+    const float il = 1.f / l;
+    if (lane == c) a[c] = l;
+    else if (lane > c) a[c] *= il;  // L[lane][c]
+#pragma unroll
+    for (int k = c + 1; k < NB; ++k) {
+      const float lkc = __shfl_sync(FULL, a[c], k);  // L[k][c]
+      if (lane >= k) a[k] = fmaf(-a[c], lkc, a[k]);
+    }
   }
+  if (bad && lane == 0) flag_status(status, ST_BAD_INPUT);
+  if (lane < nb) {
+#pragma unroll
+    for (int k = 0; k < NB; ++k)
+      if (k < nb) M[static_cast<size_t>(k0 + lane) * K + k0 + k] = k <= lane ? a[k] : 0.f;
+  }
+  // X = L^-1, one column per lane: X[r][c] = (delta_rc - sum_{k<r} L[r][k] X[k][c]) / L[r][r]
+  float x[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) {
+    const float irr = 1.f / __shfl_sync(FULL, a[r], r);
+    float acc = r == lane ? 1.f : 0.f;
+#pragma unroll
+    for (int k = 0; k < r; ++k) acc = fmaf(-__shfl_sync(FULL, a[k], r), x[k], acc);
+    x[r] = r >= lane ? acc * irr : 0.f;
+  }
+  float* out = Linv + static_cast<size_t>(k0 / NB) * NB * NB;
+#pragma unroll
+  for (int r = 0; r < NB; ++r) out[r * NB + lane] = (r < nb && lane < nb) ? x[r] : 0.f;
+}
+
+// Rows below the diagonal block: L21 = A21 L11^-T = A21 (L11^-1)^T with the
+// block inverse from potrf_diag_kernel, one thread per row.
+__global__ void trsm_panel_kernel(float* __restrict__ M, int K, int k0,
+                                  const float* __restrict__ Linv) {
+  __shared__ float Li[NB][NB + 1];
+  const float* inv = Linv + static_cast<size_t>(k0 / NB) * NB * NB;
+  for (int f = threadIdx.x; f < NB * NB; f += blockDim.x) Li[f / NB][f % NB] = inv[f];
   __syncthreads();
+  const int nb = K - k0 < NB ? K - k0 : NB;
   const int row = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= K) return;
-  double* mr = M + static_cast<size_t>(row) * K + k0;
-  double v[NB];
+  float* mr = M + static_cast<size_t>(row) * K + k0;
+  float v[NB];
 #pragma unroll
-  for (int c = 0; c < NB; ++c) v[c] = c < nb ? mr[c] : 0.0;
+  for (int c = 0; c < NB; ++c) v[c] = c < nb ? mr[c] : 0.f;
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     if (c < nb) {
-      double acc = v[c];
+      float acc = 0.f;
 #pragma unroll
-      for (int q = 0; q < c; ++q) acc -= v[q] * L[c][q];
-      v[c] = acc / L[c][c];
+      for (int q = 0; q <= c; ++q) acc = fmaf(v[q], Li[c][q], acc);
+      mr[c] = acc;
     }
   }
-#pragma unroll
-  for (int c = 0; c < NB; ++c)
-    if (c < nb) mr[c] = v[c];
 }
 
-// Trailing update A22 -= L21 L21^T on lower 32x32 tiles.
-__global__ void syrk_kernel(double* __restrict__ M, int K, int k0) {
+// Trailing update A22 -= L21 L21^T on lower 64 x 64 tiles (4 x 4 per thread).
+__global__ void __launch_bounds__(256) syrk_kernel(float* __restrict__ M, int K, int k0) {
   const int k1 = k0 + NB;
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bj > bi) return;
-  __shared__ double Li[32][NB + 1];
-  __shared__ double Lj[32][NB + 1];
-  const int r0 = k1 + bi * 32, c0 = k1 + bj * 32;
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  for (int r = ty; r < 32; r += 8) {
-    Li[r][tx] = (r0 + r < K) ? M[static_cast<size_t>(r0 + r) * K + k0 + tx] : 0.0;
-    Lj[r][tx] = (c0 + r < K) ? M[static_cast<size_t>(c0 + r) * K + k0 + tx] : 0.0;
+  __shared__ float Li[NB][64 + 1];
+  __shared__ float Lj[NB][64 + 1];
+  const int r0 = k1 + bi * 64, c0 = k1 + bj * 64;
+  for (int f = threadIdx.x; f < 64 * NB; f += 256) {
+    const int r = f / NB, q = f % NB;
+    Li[q][r] = (r0 + r < K) ? M[static_cast<size_t>(r0 + r) * K + k0 + q] : 0.f;
+    Lj[q][r] = (c0 + r < K) ? M[static_cast<size_t>(c0 + r) * K + k0 + q] : 0.f;
   }
   __syncthreads();
-  for (int r = ty; r < 32; r += 8) {
-    const int gr = r0 + r, gc = c0 + tx;
-    if (gr < K && gc < K && gc <= gr) {
-      double acc = 0.0;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // rows tr + 16i, cols tc + 16j
+  float acc[4][4] = {};
+#pragma unroll 8
+  for (int q = 0; q < NB; ++q) {
+    float li[4], lj[4];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) acc += Li[r][q] * Lj[tx][q];
-      M[static_cast<size_t>(gr) * K + gc] -= acc;
+    for (int i = 0; i < 4; ++i) li[i] = Li[q][tr + 16 * i];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) lj[jj] = Lj[q][tc + 16 * jj];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(li[i], lj[jj], acc[i][jj]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int gr = r0 + tr + 16 * i, gc = c0 + tc + 16 * jj;
+      if (gr < K && gc < K && gc <= gr) M[static_cast<size_t>(gr) * K + gc] -= acc[i][jj];
+    }
+}
+
+// ---- 5d. FP32 solve (L L^T) c = r for one right-hand side per CTA, then
+// X += c in FP64.  Forward: per 32-row block B, u = r_B - L[B][<B] y, y_B =
+// Linv_B u; backward: v = y_B - L[>B][B]^T x, x_B = Linv_B^T v.  256 threads.
+constexpr int SV_T = 256;
+__global__ void __launch_bounds__(SV_T) solve32_kernel(const float* __restrict__ L,
+                                                       const float* __restrict__ Linv, int K,
+                                                       const float* __restrict__ R32,
+                                                       double* __restrict__ Xs) {
+  extern __shared__ float sv[];
+  float* y = sv;             // K: forward result, then the solution
+  float* part = sv + K;      // 8 x 32 partial sums
+  float* u = part + 8 * 32;  // 32
+  const int col = blockIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nblk = (K + NB - 1) / NB;
+  // forward
+  for (int b = 0; b < nblk; ++b) {
+    const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
+    // rows k0 + (4 per warp), columns [0, k0) split over lanes
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = warp * 4 + rr;
+      float acc = 0.f;
+      if (r < nb) {
+        const float* lr = L + static_cast<size_t>(k0 + r) * K;
+        for (int k = lane; k < k0; k += 32) acc = fmaf(lr[k], y[k], acc);
+      }
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0 && r < NB) u[r] = r < nb ? R32[static_cast<size_t>(k0 + r) * RW + col] - acc : 0.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const float* inv = Linv + static_cast<size_t>(b) * NB * NB;
+      float acc = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < NB; ++k) acc = fmaf(inv[lane * NB + k], u[k], acc);
+      if (lane < nb) y[k0 + lane] = acc;
+    }
+    __syncthreads();
+  }
+  // backward (y is overwritten by x block by block, last block first)
+  for (int b = nblk - 1; b >= 0; --b) {
+    const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
+    float acc = 0.f;
+    for (int k = k0 + NB + warp; k < K; k += 8)
+      if (lane < nb) acc = fmaf(L[static_cast<size_t>(k) * K + k0 + lane], y[k], acc);
+    part[warp * 32 + lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      float v = 0.f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += part[q * 32 + lane];
+      u[lane] = lane < nb ? y[k0 + lane] - v : 0.f;
+      __syncwarp();
+      const float* inv = Linv + static_cast<size_t>(b) * NB * NB;
+      float xr = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < NB; ++k) xr = fmaf(inv[k * NB + lane], u[k], xr);
+      if (lane < nb) y[k0 + lane] = xr;
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < K; j += SV_T) Xs[static_cast<size_t>(j) * RW + col] += static_cast<double>(y[j]);
+}
+
+// ---- 5e. FP64 residual of the scaled system: R = Zs - (S M S) X, as FP32 -----
+// 32 x 48 output tiles (one row per warp lane group), k in chunks of 32.
+__global__ void __launch_bounds__(256) residual_kernel(const double* __restrict__ M,
+                                                       const double* __restrict__ dsc, int K,
+                                                       const double* __restrict__ Zs,
+                                                       const double* __restrict__ Xs,
+                                                       float* __restrict__ R32) {
+  __shared__ double Ms[32][33];
+  __shared__ double Xt[32][RW];
+  const int j0 = blockIdx.x * 32;
+  const int tr = threadIdx.x / 8, tc = threadIdx.x % 8;  // row tr, columns tc + 8q (q < 6)
+  double acc[6] = {};
+  for (int k0 = 0; k0 < K; k0 += 32) {
+    for (int f = threadIdx.x; f < 32 * 32; f += 256) {
+      const int r = f / 32, c = f % 32;
+      Ms[r][c] = (j0 + r < K && k0 + c < K) ? M[static_cast<size_t>(j0 + r) * K + k0 + c] : 0.0;
+    }
+    for (int f = threadIdx.x; f < 32 * RW; f += 256) {
+      const int r = f / RW, c = f % RW;
+      Xt[r][c] = k0 + r < K ? dsc[k0 + r] * Xs[static_cast<size_t>(k0 + r) * RW + c] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const double m = Ms[tr][k];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) acc[q] = fma(m, Xt[k][tc + 8 * q], acc[q]);
+    }
+    __syncthreads();
+  }
+  const int j = j0 + tr;
+  if (j < K) {
+    const double dj = dsc[j];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int c = tc + 8 * q;
+      R32[static_cast<size_t>(j) * RW + c] =
+          static_cast<float>(Zs[static_cast<size_t>(j) * RW + c] - dj * acc[q]);
     }
   }
 }
 
-// ---- 5c. forward substitution L Y = Z, block kb (right-looking) -------------
-// grid (nblk - kb, 3): x = target row block offset, y = group of 15 columns.
-// Every CTA recomputes Y_kb = Linv_kb Z_kb in shared memory; CTA x = 0 stores
-// it, CTAs x > 0 subtract L[row block][kb] Y_kb from their (later) rows of Z.
-__global__ void fwd_step_kernel(const double* __restrict__ M, const double* __restrict__ Linv,
-                                double* __restrict__ Z, double* __restrict__ Yb, int K, int kb) {
-  __shared__ double Yk[NB][16];
-  const int k0 = kb * NB, nb = K - k0 < NB ? K - k0 : NB;
-  const int r = threadIdx.y, c = threadIdx.x;  // 32 x 15
-  const int col = blockIdx.y * 15 + c;
-  const double* Li = Linv + static_cast<size_t>(kb) * NB * NB;
-  double y = 0.0;
-  if (r < nb) {
-    for (int k = 0; k <= r; ++k) y += Li[r * NB + k] * Z[static_cast<size_t>(k0 + k) * RW + col];
-  }
-  Yk[r][c] = y;
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    if (r < nb) Yb[static_cast<size_t>(k0 + r) * RW + col] = y;
-    return;
-  }
-  const int row = k0 + static_cast<int>(blockIdx.x) * NB + r;
-  if (row >= K) return;
-  const double* lr = M + static_cast<size_t>(row) * K + k0;
-  double acc = 0.0;
-  for (int k = 0; k < nb; ++k) acc += lr[k] * Yk[k][c];
-  Z[static_cast<size_t>(row) * RW + col] -= acc;
-}
-
-// ---- 5d. backward substitution L^T X = Y, block kb (right-looking, last first) --
-// grid (kb + 1, 3): CTA x = 0 stores X_kb = Linv_kb^T Y_kb; CTA x > 0 subtracts
-// L[kb][row block]^T X_kb from the rows of block kb - x.
-__global__ void bwd_step_kernel(const double* __restrict__ M, const double* __restrict__ Linv,
-                                double* __restrict__ Yb, double* __restrict__ Xb, int K, int kb) {
-  __shared__ double Xk[NB][16];
-  const int k0 = kb * NB, nb = K - k0 < NB ? K - k0 : NB;
-  const int r = threadIdx.y, c = threadIdx.x;
-  const int col = blockIdx.y * 15 + c;
-  const double* Li = Linv + static_cast<size_t>(kb) * NB * NB;
-  double x = 0.0;
-  if (r < nb) {
-    for (int k = r; k < nb; ++k) x += Li[k * NB + r] * Yb[static_cast<size_t>(k0 + k) * RW + col];
-  }
-  Xk[r][c] = x;
-  __syncthreads();
-  if (blockIdx.x == 0) {
-    if (r < nb) Xb[static_cast<size_t>(k0 + r) * RW + col] = x;
-    return;
-  }
-  const int row = (kb - static_cast<int>(blockIdx.x)) * NB + r;  // a full earlier block
-  double acc = 0.0;
-  for (int k = 0; k < nb; ++k) acc += M[static_cast<size_t>(k0 + k) * K + row] * Xk[k][c];
-  Yb[static_cast<size_t>(row) * RW + col] -= acc;
+// Unscaled solution D~^T = S X.
+__global__ void unscale_kernel(const double* __restrict__ dsc, const double* __restrict__ Xs, int K,
+                               double* __restrict__ Xb) {
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e < static_cast<int64_t>(K) * RW) Xb[e] = dsc[e / RW] * Xs[e];
 }
 
 // ---- 6a. normalise; mark dead atoms ----------------------------------------------
@@ -788,25 +898,37 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, w.M, w.Z);
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
   launches += 4;
+  // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
+  // kRefine FP32 solves with FP64 residuals in between
   const int nblk = (K + NB - 1) / NB;
+  scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
+  ++launches;
   for (int kb = 0; kb < nblk; ++kb) {
     const int k0 = kb * NB;
-    potrf_diag_kernel<<<1, dim3(32, 32), 0, st>>>(w.M, K, k0, w.Linv, w.status);
+    potrf_diag_kernel<<<1, 32, 0, st>>>(w.A32, K, k0, w.Linv32, w.status);
     ++launches;
     const int rest = K - k0 - NB;
     if (rest > 0) {
-      trsm_panel_kernel<<<(rest + 127) / 128, 128, 0, st>>>(w.M, K, k0);
-      const int tiles = (rest + 31) / 32;
-      syrk_kernel<<<dim3(tiles, tiles), dim3(32, 8), 0, st>>>(w.M, K, k0);
+      trsm_panel_kernel<<<(rest + 127) / 128, 128, 0, st>>>(w.A32, K, k0, w.Linv32);
+      const int tiles = (rest + 63) / 64;
+      syrk_kernel<<<dim3(tiles, tiles), 256, 0, st>>>(w.A32, K, k0);
       launches += 2;
     }
   }
-  for (int kb = 0; kb < nblk; ++kb)
-    fwd_step_kernel<<<dim3(nblk - kb, 3), dim3(15, NB), 0, st>>>(w.M, w.Linv, w.Z, w.Yb, K, kb);
-  for (int kb = nblk - 1; kb >= 0; --kb)
-    bwd_step_kernel<<<dim3(kb + 1, 3), dim3(15, NB), 0, st>>>(w.M, w.Linv, w.Yb, w.Xb, K, kb);
+  const size_t sv_smem = static_cast<size_t>(K + 8 * 32 + 32) * sizeof(float);
+  for (int it = 0; it < kRefine; ++it) {
+    if (it > 0) {
+      residual_kernel<<<(K + 31) / 32, 256, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
+      ++launches;
+    }
+    solve32_kernel<<<DLSH_D, SV_T, sv_smem, st>>>(w.A32, w.Linv32, K, w.R32, w.Xs);
+    ++launches;
+  }
+  unscale_kernel<<<static_cast<int>((static_cast<int64_t>(K) * RW + 255) / 256), 256, 0, st>>>(
+      w.dsc, w.Xs, K, w.Xb);
+  ++launches;
   normalise_kernel<<<(K + 7) / 8, 256, 0, st>>>(w.Xb, w.atom_start, K, D_new, D_old, w.dead);
-  launches += 2 * nblk + 1;
+  ++launches;
   if (resid && N > 0) {
     refill_kernel<<<1, 1024, 0, st>>>(X, resid, N, K, w.dead, D_new);
     ++launches;
