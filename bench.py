@@ -27,6 +27,11 @@ sys.path.insert(0, ROOT)
 METRIC = ("OMP Gaussians/s at K=1024,s=8, learned+BF16 vs plain at equal RMSE; decode GB/s")
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
+# DRAM bytes (read + write) per signal of the encoder, from one ncu capture of
+# encode_kernel at N = 1,000,000, K = 1024, s = 8, FP32 (profiles/
+# encode_kernel_fp32_N1M_K1024_s8.md: 185.07 MB + 37.91 MB); the traffic
+# grows with the number of signals, so a launch over N signals moves N times it.
+ENCODE_TRAFFIC = {(1024, 8, "fp32"): (185.071104e6 + 37.910016e6) / 1_000_000}
 
 
 def parse():
@@ -42,6 +47,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--workload", default="scene", choices=["scene", "multi"],
+                    help="scene: the single-scene step (default); multi: 13 scenes of uneven "
+                         "size, K and s encoded by one graph-captured multi-scene call")
+    ap.add_argument("--multi-scale", type=float, default=1.0,
+                    help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step", choices=["step", "encode", "decode"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
@@ -221,6 +231,95 @@ def learned_leg(api, synth, D, X, s, K, cal_tau=1.01, n_train=2_000_000, n_cal=2
     }
 
 
+def multi_scenes(scale=1.0, n_scenes=13):
+    """Config-5 scenes: K = (512, 1024, 2048)[i % 3], s = (4, 8, 16)[(i // 3) % 3],
+    hidden dictionary of K atoms with seed 1000 + i, N log-uniform in
+    [0.5M, 6M] (drawn with seed 0), times `scale`."""
+    import numpy as np
+    from paper_2605_30396_gb300 import synth
+    rng = np.random.default_rng(0)
+    ns = np.exp(rng.uniform(np.log(0.5e6), np.log(6e6), n_scenes))
+    out = []
+    for i in range(n_scenes):
+        K = (512, 1024, 2048)[i % 3]
+        s = (4, 8, 16)[(i // 3) % 3]
+        N = max(1, int(round(ns[i] * scale)))
+        Dh = synth.hidden_dictionary(K, 1000 + i)
+        X = synth.signals(N, Dh, s, 2000 + i)
+        init = synth.init_atom_indices(N, K, 3000 + i)
+        cam, mu = synth.camera_and_means(N, 4000 + i, 5000 + i)
+        out.append({"K": K, "s": s, "N": N, "X": X, "init": init, "cam": cam, "mu": mu})
+    return out
+
+
+def run_multi(a):
+    """13 scenes encoded by one graph-captured dlsh_encode_multi call (each
+    scene's (K, s) autotuned on a sample first), then decoded from one camera
+    per scene.  A step = the graph replay plus the decodes."""
+    import torch
+
+    from paper_2605_30396_gb300 import _lib, api
+    torch.cuda.set_device(0)
+    L = _lib.lib()
+    sc = multi_scenes(a.multi_scale)
+    scenes, decs = [], []
+    tuned = {}
+    for x in sc:
+        X = torch.from_numpy(x["X"]).cuda()
+        D = api.init_dictionary(X, x["init"])
+        key = (x["K"], x["s"])
+        if key not in tuned:
+            tuned[key] = api.autotune_encode(D, X[:65536], x["s"])
+        scenes.append({"D": D, "X": X, "s": x["s"]})
+        decs.append((torch.from_numpy(x["mu"]).cuda(), x["cam"]))
+    total = sum(x["N"] for x in sc)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        api.encode_multi(scenes)  # warm-up: workspaces and internal streams exist
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        outs = api.encode_multi(scenes)
+    rgbs = [torch.empty((x["N"], 3), dtype=torch.float32, device="cuda") for x in sc]
+
+    def step():
+        g.replay()
+        for o, (mu, cam), sc_, rgb in zip(outs, decs, scenes, rgbs):
+            api.decode(sc_["D"], o[0], o[1], o[2], means=mu, cam=cam, out=rgb)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(0)
+    clocks.start()
+    launches0 = L.dlsh_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    cl = clocks.stop()
+    ms = e0.elapsed_time(e1) / a.steps
+    rm = []
+    for o, x in zip(outs, sc):
+        rm.append(float((o[3].double().sum() / (x["N"] * 45)).sqrt().item()))
+    print(json.dumps({
+        "metric": METRIC, "value": total / (ms * 1e-3), "unit": "Gaussians/s", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "multi-scene: 13 scenes, N log-uniform in [0.5M, 6M] x %g, "
+                               "K in {512,1024,2048}, s in {4,8,16}; step = one graph replay of "
+                               "the multi-scene encode + a decode per scene" % a.multi_scale,
+                   "total_N": total, "scenes": [[x["N"], x["K"], x["s"]] for x in sc],
+                   "tuned_bn": {f"{k[0]},{k[1]}": v for k, v in tuned.items()}},
+        "gpu_launches_untimed_graph": L.dlsh_kernel_launches() - launches0,
+        "clocks": cl, "detail": {"rmse_per_scene": rm},
+    }))
+
+
 def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     """One leg alone (encode or decode) for profiling: W untimed and K timed
     calls on resident inputs, CUDA events on the launching stream."""
@@ -272,6 +371,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return run_reference(a)
+    if a.workload == "multi":
+        return run_multi(a)
     import numpy as np
     import torch
 
@@ -410,7 +511,9 @@ def main():
                    "l2": "inputs larger than L2 (X = %.0f MB)" % (X_np.nbytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (ENCODE_TRAFFIC[(K, s, a.precision)] * N
+                                 if (K, s, a.precision) in ENCODE_TRAFFIC else None),
                      "kernel": "encode_kernel (prep+gram included in the timing)",
                      "peak_source": f"{src}: {peak_note}"},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cl,

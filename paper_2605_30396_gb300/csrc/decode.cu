@@ -56,152 +56,6 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[1
   Y[14] = c[14] * x * (xx - 3.f * yy);
 }
 
-// ---------------------------------------------------------------------------
-// Shared-memory dictionary path (K up to about 1100 at s = 8).
-//
-// The dictionary sits in shared memory as rows of 48 floats: three channel
-// segments of 16 (15 basis values and a zero).  A warp decodes a pair of
-// Gaussians per step, one per half-warp; lane b of a half owns basis b of the
-// three channels.  Per nonzero, each half reads three 64-byte segments of one
-// row; a segment covers one half of the banks, (3j + c) mod 2.  When the two
-// rows of a step have equal parity, the second half reads its first two
-// segments in swapped order, so two of the three reads hit disjoint bank
-// halves instead of none.  The pair's codes are staged per warp (atom index,
-// swap flag and coefficient in 8 bytes); each lane evaluates its own basis
-// value from a per-lane Cartesian form; the three channel sums are formed by
-// a transposing reduction over the half-warp (five shuffles per pair).
-// ---------------------------------------------------------------------------
-constexpr int DROW = 48;
-
-// Y_b = c_b * u_b * (al x^2 + be y^2 + ga z^2 + de), u_b a product of a subset
-// of {x, y, z} (the Cartesian forms of sh_basis).
-struct LaneBasis {
-  float c, al, be, ga, de;
-  bool ex, ey, ez;
-};
-
-__device__ __forceinline__ LaneBasis lane_basis(int b) {
-  // u flags (x, y, z) and the quadratic's coefficients, basis order as sh_basis
-  constexpr unsigned char U[16] = {2, 1, 4, 6, 3, 0, 5, 0, 2, 7, 2, 1, 4, 1, 4, 0};
-  constexpr signed char Q[16][4] = {{0, 0, 0, 1}, {0, 0, 0, 1}, {0, 0, 0, 1}, {0, 0, 0, 1},
-                                    {0, 0, 0, 1}, {0, 0, 3, -1}, {0, 0, 0, 1}, {1, -1, 0, 0},
-                                    {3, -1, 0, 0}, {0, 0, 0, 1}, {0, 0, 5, -1}, {0, 0, 5, -3},
-                                    {0, 0, 5, -1}, {1, -1, 0, 0}, {1, -3, 0, 0}, {0, 0, 0, 0}};
-  LaneBasis l;
-  l.c = b < 15 ? g_sh.c[b] : 0.f;
-  l.al = Q[b][0];
-  l.be = Q[b][1];
-  l.ga = Q[b][2];
-  l.de = Q[b][3];
-  l.ex = (U[b] & 4) != 0;
-  l.ey = (U[b] & 2) != 0;
-  l.ez = (U[b] & 1) != 0;
-  return l;
-}
-
-__global__ void __launch_bounds__(1024) decode_smem_kernel(
-    const float* __restrict__ D, int K, const uint16_t* __restrict__ idx,
-    const float* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int64_t N,
-    const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
-    float* __restrict__ rgb, uint32_t* status) {
-  extern __shared__ __align__(16) float sm[];
-  const unsigned FULL = 0xffffffffu;
-  const int nwarps = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int hl = lane & 15, h = lane >> 4;
-  float* Ds = sm;
-  uint2* codes = reinterpret_cast<uint2*>(sm + static_cast<size_t>(K) * DROW) + warp * 2 * s;
-  for (int f = threadIdx.x; f < K * DROW; f += blockDim.x) {
-    const int j = f / DROW, e = f - j * DROW, c = e >> 4, b = e & 15;
-    Ds[f] = b < 15 ? D[static_cast<size_t>(j) * DLSH_D + c * 15 + b] : 0.f;
-  }
-  __syncthreads();
-  const LaneBasis lb = lane_basis(hl);
-  const bool b8 = (hl & 8) != 0, b4 = (hl & 4) != 0;
-  const int64_t npairs = (N + 1) / 2;
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
-  bool bad = false;
-  for (int64_t pr = static_cast<int64_t>(blockIdx.x) * nwarps + warp; pr < npairs; pr += wstride) {
-    const int64_t g = 2 * pr + h;
-    const bool valid = g < N;
-    int nz = valid ? nnz[g] : 0;
-    if (nz > s) {
-      bad = true;
-      nz = s;
-    }
-    // ---- stage the pair's codes: (j | swap << 16, coefficient)
-    for (int t0 = 0; t0 < s; t0 += 16) {
-      const int t = t0 + hl;
-      uint32_t j = 0;
-      float a = 0.f;
-      if (t < nz) {
-        j = idx[g * s + t];
-        a = coef[g * s + t];
-        if (j >= static_cast<uint32_t>(K)) {
-          bad = true;
-          j = 0;
-          a = 0.f;
-        }
-      }
-      const uint32_t jo = __shfl_xor_sync(FULL, j, 16);
-      const uint32_t swap = (h == 1 && ((j ^ jo) & 1u) == 0u) ? 1u : 0u;
-      if (t < s) codes[h * s + t] = make_uint2(j | (swap << 16), __float_as_uint(a));
-    }
-    // ---- direction and this lane's basis value
-    float vx = 0.f, vy = 0.f, vz = 1.f;
-    if (valid) {
-      vx = dm[g * 3 + 0];
-      vy = dm[g * 3 + 1];
-      vz = dm[g * 3 + 2];
-      if (use_cam) {
-        vx -= cx;
-        vy -= cy;
-        vz -= cz;
-        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-        vx *= inv;
-        vy *= inv;
-        vz *= inv;
-      }
-    }
-    const float u = (lb.ex ? vx : 1.f) * (lb.ey ? vy : 1.f) * (lb.ez ? vz : 1.f);
-    const float Y = lb.c * u * fmaf(lb.al, vx * vx, fmaf(lb.be, vy * vy, fmaf(lb.ga, vz * vz, lb.de)));
-    const int nzm = max(nz, __shfl_xor_sync(FULL, nz, 16));
-    __syncwarp();
-    // ---- accumulate sum_t a_t D[j_t, c, b] for the three channels
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-#pragma unroll 4
-    for (int t = 0; t < nzm; ++t) {
-      const uint2 cw = codes[h * s + t];
-      const uint32_t j = cw.x & 0xffffu;
-      const bool sw = (cw.x >> 16) != 0u;
-      const float a = __uint_as_float(cw.y);
-      const float* row = Ds + j * DROW + hl;
-      const float v0 = row[sw ? 16 : 0];
-      const float v1 = row[sw ? 0 : 16];
-      const float v2 = row[32];
-      acc0 = fmaf(a, sw ? v1 : v0, acc0);
-      acc1 = fmaf(a, sw ? v0 : v1, acc1);
-      acc2 = fmaf(a, v2, acc2);
-    }
-    // ---- sum over the half's 16 lanes: lanes 0, 4, 8 end with R, G, B
-    const float p0 = acc0 * Y, p1 = acc1 * Y, p2 = acc2 * Y;
-    float ka = b8 ? p2 : p0, kb = b8 ? 0.f : p1;
-    ka += __shfl_xor_sync(FULL, b8 ? p0 : p2, 8);
-    kb += __shfl_xor_sync(FULL, b8 ? p1 : 0.f, 8);
-    float kc = b4 ? kb : ka;
-    kc += __shfl_xor_sync(FULL, b4 ? ka : kb, 4);
-    kc += __shfl_xor_sync(FULL, kc, 2);
-    kc += __shfl_xor_sync(FULL, kc, 1);
-    if (valid && (hl & 3) == 0 && hl < 12) rgb[g * 3 + (hl >> 2)] = kc;
-    __syncwarp();
-  }
-  if (bad) flag_status(status, ST_BAD_INPUT);
-}
-
-// ---------------------------------------------------------------------------
-// Global-memory dictionary path (large K): the layout of the first version,
-// kept for dictionaries that do not fit in shared memory.
-// ---------------------------------------------------------------------------
 template <bool SMEM_D>
 __global__ void __launch_bounds__(512) decode_kernel(
     const float* __restrict__ D, int K, const uint16_t* __restrict__ idx,
@@ -384,33 +238,33 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
   int sms = device_sm_count();
   if (sms <= 0) sms = 1;
   const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
-  const size_t dbytes = static_cast<size_t>(K) * DROW * 4;
-  const size_t wslot = static_cast<size_t>(2 * s) * 8;  // a warp's staged pair of codes
-  int nw = dbytes < static_cast<size_t>(SMEM_LIMIT) ? static_cast<int>((SMEM_LIMIT - dbytes) / wslot) : 0;
-  if (nw > 32) nw = 32;
-  if (nw >= 8) {
-    const size_t smem = dbytes + static_cast<size_t>(nw) * wslot;
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_smem_kernel,
+  const int64_t nbatch = (N + 31) / 32;
+  const size_t dbytes = (static_cast<size_t>(K) * ROW + 16) * 4;
+  const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
+  int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
+  if (nwarps > 16) nwarps = 16;
+  if (nwarps >= 6) {
+    const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                   "dlsh_decode: attribute");
-    const int64_t npairs = (N + 1) / 2;
-    int64_t grid = sms;
-    const int64_t need = (npairs + nw - 1) / nw;
+    int per_sm = static_cast<int>(SMEM_LIMIT / smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = static_cast<int64_t>(sms) * per_sm;
+    const int64_t need = (nbatch + nwarps - 1) / nwarps;
     if (grid > need) grid = need;
-    decode_smem_kernel<<<static_cast<int>(grid), nw * 32, smem, st>>>(
+    decode_kernel<true><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
         D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
   } else {
-    const int64_t nbatch = (N + 31) / 32;
-    const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
-    const int nwg = 8;
-    const size_t smem = static_cast<size_t>(nwg) * wbytes;
+    const int nw = 8;
+    const size_t smem = static_cast<size_t>(nw) * wbytes;
     DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                   "dlsh_decode: attribute");
     int64_t grid = static_cast<int64_t>(sms) * 4;
-    const int64_t need = (nbatch + nwg - 1) / nwg;
+    const int64_t need = (nbatch + nw - 1) / nw;
     if (grid > need) grid = need;
-    decode_kernel<false><<<static_cast<int>(grid), nwg * 32, smem, st>>>(
+    decode_kernel<false><<<static_cast<int>(grid), nw * 32, smem, st>>>(
         D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
   }
   count_launches(1);

@@ -180,7 +180,10 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmAr
     ph[st] ^= 1u;
   }
   tc_fence_after();
-  const int row = m0 + warp * 32 + lane;
+  // Epilogue: each warp moves its 32 rows x 32 columns from TMEM through a
+  // padded shared-memory tile, so every global store writes 32 consecutive
+  // columns of one row (the operand stages are free once the MMAs are done).
+  float* stg = reinterpret_cast<float*>(smem) + warp * 32 * 33;
   if (ok) {
     for (int cb = 0; cb < GN; cb += 32) {
       float v[32];
@@ -191,17 +194,19 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmAr
 #pragma unroll
         for (int k = 0; k < 32; ++k) v[k] = 0.f;
       }
-      if (row < g.M) {
 #pragma unroll
-        for (int k = 0; k < 32; ++k) {
-          const int col = n0 + cb + k;
-          if (col < g.N) {
-            float z = v[k];
-            if (g.epi != EPI_STORE) z += g.bias[col];
+      for (int k = 0; k < 32; ++k) stg[lane * 33 + k] = v[k];
+      __syncwarp();
+      const int col = n0 + cb + lane;
+      const float bcol = (g.epi != EPI_STORE && col < g.N) ? g.bias[col] : 0.f;
+      for (int r = 0; r < 32; ++r) {
+        const int row = m0 + warp * 32 + r;
+        if (row < g.M && col < g.N) {
+          const float z = stg[r * 33 + lane] + bcol;
+          if (g.C)
             g.C[static_cast<long long>(blockIdx.z) * g.zstride + static_cast<long long>(row) * g.ldc + col] = z;
-            if (g.epi == EPI_BIAS_GELU)
-              g.H[static_cast<long long>(row) * g.ldh + col] = __float2bfloat16(gelu_f(z));
-          }
+          if (g.epi == EPI_BIAS_GELU)
+            g.H[static_cast<long long>(row) * g.ldh + col] = __float2bfloat16(gelu_f(z));
         }
       }
     }
@@ -532,15 +537,18 @@ static inline Mat rowmajor(const __nv_bfloat16* p, long long ld) { return Mat{p,
 static inline Mat transposed(const __nv_bfloat16* p, long long ld) { return Mat{p, 1, ld}; }
 
 // forward through the three layers: logits in w.Z3 (B x K)
-static int forward(const Blob& b, int K, const float* X, long long B, const TWs& w, cudaStream_t st) {
+// keep_pre: also store the hidden pre-activations (needed by backward only).
+static int forward(const Blob& b, int K, const float* X, long long B, const TWs& w, cudaStream_t st,
+                   bool keep_pre = true) {
   const Layout L = layout(K);
   normalize_kernel<<<static_cast<int>((B + 7) / 8), 256, 0, st>>>(X, B, w.Xn);
   count_launches(1);
-  int rc = gemm(rowmajor(w.Xn, XIN), rowmajor(b.Pb + L.W1, XIN), B, HID, XIN, w.Z1, HID,
-                EPI_BIAS_GELU, b.P + L.b1, w.H1, HID, 1, 0, w.status, st);
+  int rc = gemm(rowmajor(w.Xn, XIN), rowmajor(b.Pb + L.W1, XIN), B, HID, XIN,
+                keep_pre ? w.Z1 : nullptr, HID, EPI_BIAS_GELU, b.P + L.b1, w.H1, HID, 1, 0,
+                w.status, st);
   if (rc) return rc;
-  rc = gemm(rowmajor(w.H1, HID), rowmajor(b.Pb + L.W2, HID), B, HID, HID, w.Z2, HID, EPI_BIAS_GELU,
-            b.P + L.b2, w.H2, HID, 1, 0, w.status, st);
+  rc = gemm(rowmajor(w.H1, HID), rowmajor(b.Pb + L.W2, HID), B, HID, HID, keep_pre ? w.Z2 : nullptr,
+            HID, EPI_BIAS_GELU, b.P + L.b2, w.H2, HID, 1, 0, w.status, st);
   if (rc) return rc;
   return gemm(rowmajor(w.H2, HID), rowmajor(b.Pb + L.W3, HID), B, K, HID, w.Z3, K, EPI_BIAS,
               b.P + L.b3, nullptr, 0, 1, 0, w.status, st);
@@ -634,7 +642,7 @@ int mlp_forward_enqueue(const void* blob, int K, const float* X, long long B, vo
   mlp::TWs w;
   mlp::carve_t(ws, K, B, w);
   *logits = w.Z3;
-  return mlp::forward(b, K, X, B, w, st);
+  return mlp::forward(b, K, X, B, w, st, /*keep_pre=*/false);
 }
 
 int mlp_topk_enqueue(const float* logits, long long rows, int K, int m, uint16_t* cand,
