@@ -52,7 +52,7 @@ def parse():
                          "size, K and s encoded by one graph-captured multi-scene call")
     ap.add_argument("--multi-scale", type=float, default=1.0,
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
-    ap.add_argument("--leg", default="step", choices=["step", "encode", "decode"],
+    ap.add_argument("--leg", default="step", choices=["step", "encode", "mod", "decode"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -329,6 +329,9 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     if a.leg == "decode":
         api.encode(D, X, s, precision=a.precision, out=out, sync=True)
         fn = lambda: api.decode(D, idx, coef, nnz, means=MU, cam=cam, out=rgb)
+    elif a.leg == "mod":
+        api.encode(D, X, s, precision=a.precision, out=out, sync=True)
+        fn = lambda: api.mod_update(X, D, idx, coef, nnz, resid)
     else:
         fn = lambda: api.encode(D, X, s, precision=a.precision, out=out)
     for _ in range(a.warmup):

@@ -161,13 +161,16 @@ int dlsh_decode(const float* D, int K, int d, const uint16_t* idx,
  * Dictionary update with the codes fixed (the second half of the alternating
  * minimisation of Eq. 1), read as MOD:
  *   G = A A^T, B = X A^T, lambda = 1e-6 trace(G)/K (1e-6 if trace is 0),
- *   D~ = (B + lambda D_old)(G + lambda I)^-1  (FP64 Cholesky on the device),
+ *   D~ = (B + lambda D_old)(G + lambda I)^-1, solved on the device with an FP32
+ *   Cholesky factor of the Jacobi-scaled matrix and FP64 iterative refinement
+ *   (G and B accumulated in float-float: about FP64 accuracy),
  *   d_j = d~_j / ||d~_j||; atoms with no nonzero in A (or d~_j = 0) are
  *   refilled in increasing j with the normalised signals of largest resid_sq
  *   (decreasing order, ties to the smallest index, zero signals skipped).
  * D_old, D_new [K*d]; resid_sq [N] (needed only when an atom is unused; may be
  * NULL, then unused atoms keep D_old).  Accumulation order is fixed: results
- * are bitwise reproducible.  Workspace: dlsh_mod_workspace_size(K, d, s, N).
+ * are bitwise reproducible.  Limits: K <= 4096, N < 2^26, N*s < 2^31
+ * (DLSH_ERR_UNSUPPORTED otherwise).  Workspace: dlsh_mod_workspace_size(K, d, s, N).
  */
 size_t dlsh_mod_workspace_size(int K, int d, int s, int64_t N);
 int dlsh_mod_update(const float* X, int64_t N, int d, int K,

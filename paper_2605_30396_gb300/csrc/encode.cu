@@ -733,9 +733,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
           cj[R1 * 4 + q1] = bestc * BN + q1 * QC + 31 - static_cast<int>(best & 31u);
         } else {
-          const int t1 = rowt[R1];
-          // Only strictly positive |c| are candidates: atoms already in the
-          // support and padding atoms are zeroed first, so they never qualify.
+          // Top 4 of |c| per thread: keys as in the FP32 path (|c| with its low
+          // 5 mantissa bits replaced by 31 - k), a chunk's largest key gates a
+          // branchless min/max network.  Support atoms are not masked: the
+          // residual is orthogonal to them, the FP32 re-score puts them near
+          // zero, and a row whose re-scored winner is a support atom stops.
+          // Padding atoms (j >= K) have zero rows, so their keys carry value 0
+          // and never enter the list.
           float tv[4] = {0.f, 0.f, 0.f, 0.f};
           int tj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
           for (int c = 0; c < nchunks; ++c, ++cc) {
@@ -749,33 +753,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             tmem_ld_wait<QC>(rr);
             release(cc);
             const int j0 = c * BN + q1 * QC;
-            // exclusion mask of this chunk quarter: selected atoms and j >= K
-            uint32_t em = (K - j0 < QC) ? ~((K - j0 <= 0) ? 0u : ((1u << (K - j0)) - 1u)) : 0u;
-            for (int mm = 0; mm < t1; ++mm) {
-              const unsigned d = static_cast<unsigned>(sel[mm * TILE_M + R1] - j0);
-              if (d < static_cast<unsigned>(QC)) em |= 1u << d;
-            }
             if constexpr (PREC == 2) {
 #pragma unroll
               for (int k = 0; k < QC; ++k) rr[k] = __float_as_uint(__uint_as_float(rr[k]) * sig[j0 + k]);
             }
-#pragma unroll
-            for (int k = 0; k < QC; ++k) rr[k] = ((em >> k) & 1u) ? 0u : (rr[k] & 0x7fffffffu);
-            float m0 = 0.f, m1 = 0.f;
+            uint32_t m0 = 0, m1 = 0;
 #pragma unroll
             for (int k = 0; k < QC; k += 2) {
-              m0 = fmaxf(m0, __uint_as_float(rr[k]));
-              m1 = fmaxf(m1, __uint_as_float(rr[k + 1]));
+              m0 = max(m0, rr[k] & 0x7fffffe0u);
+              m1 = max(m1, rr[k + 1] & 0x7fffffe0u);
             }
-            if (fmaxf(m0, m1) > tv[3]) {
-              // top 4 of this chunk quarter with a branchless min/max network on
-              // keys (|c| with its low 5 mantissa bits replaced by 31 - k, so
-              // larger keys mean larger values and, on ties, smaller indices),
-              // then merged into the running top 4
+            if (__uint_as_float(max(m0, m1)) > tv[3]) {
               uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
 #pragma unroll
               for (int k = 0; k < QC; ++k) {
-                uint32_t xk = (rr[k] & ~31u) | static_cast<uint32_t>(31 - k);
+                uint32_t xk = (rr[k] & 0x7fffffe0u) | static_cast<uint32_t>(31 - k);
                 uint32_t hi = max(k0, xk);
                 xk = min(k0, xk);
                 k0 = hi;
@@ -876,6 +868,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 js = mj[k];
               }
             }
+          }
+          if constexpr (PREC != 0) {
+            bool dup = false;
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) dup |= (m < t && sl[m] == js);
+            if (dup) js = -1;  // only support atoms were left: every |c| at rounding level
           }
           if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
             active = false;

@@ -33,7 +33,7 @@
 namespace dlsh {
 namespace mod {
 
-constexpr int TS = 2048;       // signals per counting-sort tile
+constexpr int TS = 512;        // signals per counting-sort tile (one scatter warp each)
 constexpr int NB = 32;         // Cholesky block
 constexpr int RW = 48;         // padded RHS width (45 used)
 constexpr int MAX_K = 4096;    // shared-memory G-row partials limit
@@ -47,9 +47,7 @@ struct Ws {
   int* off;        // K x T offsets
   int* atom_total; // K
   int* atom_start; // K + 1
-  int* list_sig;   // N*s
-  float* list_coef;
-  uint8_t* list_nnz;
+  uint2* list;     // N*s atom-major records: (signal | nnz << 26, coefficient bits)
   double* M;       // K x K: G + lambda I (FP64, kept for the refinement residuals)
   double* Z;       // K x RW right-hand sides (B^T + lambda D_old)
   double* lam;     // [0] lambda
@@ -61,14 +59,26 @@ struct Ws {
   float* R32;      // K x RW: current residual of the scaled system
   double* Xb;      // K x RW: D~^T = S Xs
   int* dead;       // K
-  int* seg_start;  // K + 1: first accumulation segment of each atom
+  int* seg_start;  // P*K + 1: first accumulation segment of each (block p, atom j), p-major
   double* Gp;      // max_segs x K partial G rows
   double* Bp;      // max_segs x RW partial B columns
 };
 
 constexpr int SEG = 4096;  // list entries per accumulation segment
+// Signals per accumulation block: segments never cross a block, and the grid
+// walks the blocks in order.  Blocks of 262,144 signals (47 MB of rows, held
+// in L2 while gathered) measured slower on GB300 than whole-list segments:
+// the gathers are not the binding limit, the per-segment work is.  The value
+// here puts every atom's list in one block.
+constexpr int64_t BLK = int64_t(1) << 40;
+static_assert(BLK % TS == 0, "blocks are whole counting-sort tiles");
 
-inline int64_t max_segments(int K, int s, int64_t N) { return (N * s + SEG - 1) / SEG + K; }
+inline int64_t n_blocks(int64_t N) { return N > 0 ? (N + BLK - 1) / BLK : 1; }
+// counting-sort tiles per block, capped at the tile count (fits an int)
+inline int tiles_per_block(int64_t T) { return static_cast<int>(BLK / TS < T ? BLK / TS : T); }
+inline int64_t max_segments(int K, int s, int64_t N) {
+  return (N * s + SEG - 1) / SEG + n_blocks(N) * K;
+}
 
 static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   Carver c(base);
@@ -79,9 +89,7 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.off = c.take<int>(static_cast<size_t>(K) * T);
   w.atom_total = c.take<int>(K);
   w.atom_start = c.take<int>(K + 1);
-  w.list_sig = c.take<int>(static_cast<size_t>(N) * s + 1);
-  w.list_coef = c.take<float>(static_cast<size_t>(N) * s + 1);
-  w.list_nnz = c.take<uint8_t>(static_cast<size_t>(N) * s + 1);
+  w.list = c.take<uint2>(static_cast<size_t>(N) * s + 1);
   w.M = c.take<double>(static_cast<size_t>(K) * K);
   w.Z = c.take<double>(static_cast<size_t>(K) * RW);
   w.lam = c.take<double>(4);
@@ -93,7 +101,7 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.R32 = c.take<float>(static_cast<size_t>(K) * RW);
   w.Xb = c.take<double>(static_cast<size_t>(K) * RW);
   w.dead = c.take<int>(K);
-  w.seg_start = c.take<int>(K + 1);
+  w.seg_start = c.take<int>(static_cast<size_t>(n_blocks(N)) * K + 1);
   w.Gp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * K);
   w.Bp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * RW);
   return c.size();
@@ -225,8 +233,7 @@ __global__ void tile_offsets_kernel(const int* __restrict__ cnt, int T,
 // list order is the signal order.
 __global__ void scatter_kernel(const uint16_t* __restrict__ idx, const float* __restrict__ coef,
                                const uint8_t* __restrict__ nnz, int s, int64_t N, int K, int T,
-                               const int* __restrict__ off, int* __restrict__ list_sig,
-                               float* __restrict__ list_coef, uint8_t* __restrict__ list_nnz) {
+                               const int* __restrict__ off, uint2* __restrict__ list) {
   extern __shared__ int cursor[];
   const int lane = threadIdx.x;
   const int b = blockIdx.x;
@@ -261,9 +268,8 @@ __global__ void scatter_kernel(const uint16_t* __restrict__ idx, const float* __
     for (int qq = 0; qq < P; ++qq) {
       if (q == qq && slot && jc >= 0 && jc < K) {
         const int pos = atomicAdd(&cursor[jc], 1);
-        list_sig[pos] = static_cast<int>(base + q);
-        list_coef[pos] = cc;
-        list_nnz[pos] = static_cast<uint8_t>(nzc);
+        list[pos] = make_uint2(static_cast<uint32_t>(base + q) | (static_cast<uint32_t>(nzc) << 26),
+                               __float_as_uint(cc));
       }
       __syncwarp();
     }
@@ -271,6 +277,16 @@ __global__ void scatter_kernel(const uint16_t* __restrict__ idx, const float* __
 }
 
 // ---- 4. G row j and B column j ---------------------------------------------------
+// Entry range [lo, hi) of atom j's list that lies in signal block p (tpb
+// counting-sort tiles per block).
+__device__ __forceinline__ void block_range(const int* __restrict__ off,
+                                            const int* __restrict__ atom_start, int T, int tpb,
+                                            int j, int p, int& lo, int& hi) {
+  const int t0 = p * tpb, t1 = t0 + tpb;
+  lo = t0 < T ? off[static_cast<size_t>(j) * T + t0] : atom_start[j + 1];
+  hi = t1 < T ? off[static_cast<size_t>(j) * T + t1] : atom_start[j + 1];
+}
+
 constexpr int AB = 32;  // list entries per batch
 __host__ __device__ constexpr int acc_buf_words(int s) {
   return 3 * AB + AB * DLSH_D + AB * s + AB * (s / 2 + 1);
@@ -279,36 +295,47 @@ __host__ __device__ constexpr int acc_buf_words(int s) {
 __global__ void __launch_bounds__(128)
     accum_kernel(const float* __restrict__ X, const uint32_t* __restrict__ idxw,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
-                 const int* __restrict__ seg_start, const int* __restrict__ list_sig,
-                 const float* __restrict__ list_coef, const uint8_t* __restrict__ list_nnz,
+                 const int* __restrict__ off, int T, int tpb, int PK,
+                 const int* __restrict__ seg_start, const uint2* __restrict__ list,
                  double* __restrict__ Gp, double* __restrict__ Bp) {
   extern __shared__ __align__(16) float smf[];
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sw = s / 2 + 1;
   const int bw = acc_buf_words(s);
+  // code staging: groups of gw = max(s, sw) lanes; lane t_lane of a group
+  // copies coefficient slot t_lane (< s) and index word t_lane (< sw) of
+  // entries e_lane, e_lane + e_step, ...
+  const int gw = s > sw ? s : sw;
+  const int e_step = 32 / gw;
+  const int e_lane = lane / gw < e_step ? lane / gw : 32;
+  const int t_lane = lane - (lane / gw) * gw;
   float* ghi = smf + static_cast<size_t>(warp) * 2 * K;
   float* glo = ghi + K;
   float* wbuf = smf + static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(warp) * 2 * bw;
-  const int nseg = seg_start[K];
+  const int nseg = seg_start[PK];
   for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-  // the segment's atom: the largest j with seg_start[j] <= seg
-  int j = 0;
+  // the segment's (block, atom): the largest pj with seg_start[pj] <= seg
+  int pj = 0;
   {
-    int lo = 0, hi = K - 1;
+    int lo = 0, hi = PK - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (seg_start[mid] <= seg) lo = mid; else hi = mid - 1;
     }
-    j = lo;
+    pj = lo;
   }
+  const int pb = pj / K, j = pj - pb * K;
   for (int k = lane; k < K; k += 32) {
     ghi[k] = 0.f;
     glo[k] = 0.f;
   }
-  float b0h = 0.f, b0l = 0.f, b1h = 0.f, b1l = 0.f;
-  const int e0 = atom_start[j] + (seg - seg_start[j]) * SEG;
-  const int e1 = e0 + SEG < atom_start[j + 1] ? e0 + SEG : atom_start[j + 1];
+  float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
+  float th[2] = {0.f, 0.f}, tl[2] = {0.f, 0.f};
+  int rlo, rhi;
+  block_range(off, atom_start, T, tpb, j, pb, rlo, rhi);
+  const int e0 = rlo + (seg - seg_start[pj]) * SEG;
+  const int e1 = e0 + SEG < rhi ? e0 + SEG : rhi;
   const int len = e1 - e0;
   const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
   const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
@@ -320,9 +347,10 @@ __global__ void __launch_bounds__(128)
     la = 0.f;
     ln = 0;
     if (e < q1) {
-      li = list_sig[e];
-      la = list_coef[e];
-      ln = list_nnz[e];
+      const uint2 rec = list[e];
+      li = static_cast<int>(rec.x & 0x3FFFFFFu);
+      la = __uint_as_float(rec.y);
+      ln = static_cast<int>(rec.x >> 26);
     }
   };
   auto stage = [&](int buf, int cnt, int li, float la, int ln) {
@@ -336,19 +364,18 @@ __global__ void __launch_bounds__(128)
     float* xb = B + 3 * AB;
     float* cf = xb + AB * DLSH_D;
     uint32_t* cw = reinterpret_cast<uint32_t*>(cf + AB * s);
-    for (int f = lane; f < cnt * DLSH_D; f += 32) {
-      const int e = f / DLSH_D, d = f - e * DLSH_D;
-      cp_async4(xb + f, X + static_cast<int64_t>(ei[e]) * DLSH_D + d);
+    // signal rows: two copy instructions per entry (45 = 32 + 13 words)
+    for (int e = 0; e < cnt; ++e) {
+      const float* src = X + static_cast<int64_t>(ei[e]) * DLSH_D;
+      cp_async4(xb + e * DLSH_D + lane, src + lane);
+      if (lane < DLSH_D - 32) cp_async4(xb + e * DLSH_D + 32 + lane, src + 32 + lane);
     }
-    for (int f = lane; f < cnt * s; f += 32) {
-      const int e = f / s, t = f - e * s;
-      cp_async4(cf + f, coef + static_cast<int64_t>(ei[e]) * s + t);
-    }
-    for (int f = lane; f < cnt * sw; f += 32) {
-      const int e = f / sw, w = f - e * sw;
+    // codes: lane (q, t) copies slot t of entry e0 + q, 32 / s entries per step
+    for (int e = e_lane; e < cnt; e += e_step) {
       const int64_t base = static_cast<int64_t>(ei[e]) * s;
+      if (t_lane < s) cp_async4(cf + e * s + t_lane, coef + base + t_lane);
       const int64_t w0 = base >> 1, wl = (base + s - 1) >> 1;
-      if (w0 + w <= wl) cp_async4(cw + f, idxw + w0 + w);
+      if (t_lane < sw && w0 + t_lane <= wl) cp_async4(cw + e * sw + t_lane, idxw + w0 + t_lane);
     }
     cp_async_commit();
   };
@@ -377,16 +404,32 @@ __global__ void __launch_bounds__(128)
     const float* xb = B + 3 * AB;
     const float* cf = xb + AB * DLSH_D;
     const uint32_t* cw = reinterpret_cast<const uint32_t*>(cf + AB * s);
-    for (int e = 0; e < cnt; ++e) {
-      const float a = ea[e];
-      ff_fma(b0h, b0l, a, xb[e * DLSH_D + lane]);
-      if (lane < DLSH_D - 32) ff_fma(b1h, b1l, a, xb[e * DLSH_D + 32 + lane]);
-      const int nz = en[e];
-      if (lane < nz) {
-        const int o = ((ei[e] * s) & 1) + lane;
-        const uint32_t wv = cw[e * sw + (o >> 1)];
-        const int k = (o & 1) ? static_cast<int>(wv >> 16) : static_cast<int>(wv & 0xFFFFu);
-        if (k < K) ff_fma(ghi[k], glo[k], a, cf[e * s + lane]);
+    // Four entries per step: B sums of entry e go to accumulator e mod 4 (and
+    // the 13-dim tails of each pair to accumulator (e mod 4) / 2), so the
+    // float-float chains are independent; the G updates stay in entry order.
+    for (int e = 0; e < cnt; e += 4) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (e + u < cnt) ff_fma(bh[u], bl[u], ea[e + u], xb[(e + u) * DLSH_D + lane]);
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        // dims 32..44: lanes 0..12 take the even entry of the pair, lanes 16..28 the odd one
+        const int et = e + 2 * pr + (lane >> 4);
+        if ((lane & 15) < DLSH_D - 32 && et < cnt)
+          ff_fma(th[pr], tl[pr], ea[et], xb[et * DLSH_D + 32 + (lane & 15)]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int eu = e + u;
+        if (eu < cnt) {
+          const int nz = en[eu];
+          if (lane < nz) {
+            const int o = ((ei[eu] * s) & 1) + lane;
+            const uint32_t wv = cw[eu * sw + (o >> 1)];
+            const int k = (o & 1) ? static_cast<int>(wv >> 16) : static_cast<int>(wv & 0xFFFFu);
+            if (k < K) ff_fma(ghi[k], glo[k], ea[eu], cf[eu * s + lane]);
+          }
+        }
       }
     }
     __syncwarp();
@@ -394,9 +437,18 @@ __global__ void __launch_bounds__(128)
   // publish this warp's B partial next to its G partial, then sum the warps in order
   __syncthreads();
   double* bpart = reinterpret_cast<double*>(wbuf);  // the warp's staging area is free now
-  bpart[lane] = static_cast<double>(b0h) + static_cast<double>(b0l);
-  if (lane < RW - 32)
-    bpart[32 + lane] = lane < DLSH_D - 32 ? static_cast<double>(b1h) + static_cast<double>(b1l) : 0.0;
+  {
+    double b = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) b += static_cast<double>(bh[u]) + static_cast<double>(bl[u]);
+    bpart[lane] = b;
+  }
+  {
+    const double tail = static_cast<double>(th[0]) + static_cast<double>(tl[0]) +
+                        static_cast<double>(th[1]) + static_cast<double>(tl[1]);
+    const double odd = __shfl_down_sync(0xffffffffu, tail, 16);
+    if (lane < RW - 32) bpart[32 + lane] = lane < DLSH_D - 32 ? tail + odd : 0.0;
+  }
   __syncthreads();
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
@@ -419,40 +471,50 @@ __global__ void __launch_bounds__(128)
   }
 }
 
-// Segment counts per atom (ceil(n_j / SEG)) and their exclusive scan.
-__global__ void seg_scan_kernel(const int* __restrict__ atom_total, int K,
-                                int* __restrict__ seg_start) {
+// Segment counts per (block p, atom j) (ceil(n_pj / SEG)) and their exclusive
+// scan, p-major.
+__global__ void seg_scan_kernel(const int* __restrict__ off, const int* __restrict__ atom_start,
+                                int T, int tpb, int K, int PK, int* __restrict__ seg_start) {
   __shared__ int sm[1024];
   __shared__ int carry_s;
   int carry = 0;
-  for (int base = 0; base < K; base += 1024) {
-    const int j = base + threadIdx.x;
-    const int v = j < K ? (atom_total[j] + SEG - 1) / SEG : 0;
+  for (int base = 0; base < PK; base += 1024) {
+    const int pj = base + threadIdx.x;
+    int v = 0;
+    if (pj < PK) {
+      const int p = pj / K, j = pj - p * K;
+      int lo, hi;
+      block_range(off, atom_start, T, tpb, j, p, lo, hi);
+      v = (hi - lo + SEG - 1) / SEG;
+    }
     int tot = 0;
     const int ex = block_exclusive_scan(v, sm, &tot);
-    if (j < K) seg_start[j] = carry + ex;
+    if (pj < PK) seg_start[pj] = carry + ex;
     if (threadIdx.x == 0) carry_s = carry + tot;
     __syncthreads();
     carry = carry_s;
     __syncthreads();
   }
-  if (threadIdx.x == 0) seg_start[K] = carry;
+  if (threadIdx.x == 0) seg_start[PK] = carry;
 }
 
 // Row j of G and column j of B: the atom's segment partials summed in order.
 __global__ void seg_reduce_kernel(const int* __restrict__ seg_start, const double* __restrict__ Gp,
-                                  const double* __restrict__ Bp, int K, double* __restrict__ M,
-                                  double* __restrict__ Z) {
+                                  const double* __restrict__ Bp, int K, int P,
+                                  double* __restrict__ M, double* __restrict__ Z) {
   const int j = blockIdx.x;
-  const int s0 = seg_start[j], s1 = seg_start[j + 1];
   for (int k = threadIdx.x; k < K; k += blockDim.x) {
     double acc = 0.0;
-    for (int sg = s0; sg < s1; ++sg) acc += Gp[static_cast<size_t>(sg) * K + k];
+    for (int p = 0; p < P; ++p)
+      for (int sg = seg_start[p * K + j]; sg < seg_start[p * K + j + 1]; ++sg)
+        acc += Gp[static_cast<size_t>(sg) * K + k];
     M[static_cast<size_t>(j) * K + k] = acc;
   }
   for (int q = threadIdx.x; q < RW; q += blockDim.x) {
     double acc = 0.0;
-    for (int sg = s0; sg < s1; ++sg) acc += Bp[static_cast<size_t>(sg) * RW + q];
+    for (int p = 0; p < P; ++p)
+      for (int sg = seg_start[p * K + j]; sg < seg_start[p * K + j + 1]; ++sg)
+        acc += Bp[static_cast<size_t>(sg) * RW + q];
     Z[static_cast<size_t>(j) * RW + q] = acc;
   }
 }
@@ -632,50 +694,114 @@ __global__ void __launch_bounds__(256) syrk_kernel(float* __restrict__ M, int K,
 }
 
 // ---- 5d. FP32 solve (L L^T) c = r for one right-hand side per CTA, then
-// X += c in FP64.  Forward: per 32-row block B, u = r_B - L[B][<B] y, y_B =
-// Linv_B u; backward: v = y_B - L[>B][B]^T x, x_B = Linv_B^T v.  256 threads.
+// X += c in FP64.  Forward, per 32-row block B: the panel L[B][0, k0) is
+// staged in shared memory with cp.async, u = r_B - L[B][<B] y, y_B = Linv_B u.
+// Backward, last block first: the panel L[>B][B] (32 columns of every later
+// row) is staged, v = y_B - L[>B][B]^T x, x_B = Linv_B^T v.  256 threads.
 constexpr int SV_T = 256;
+
+// Copies n floats from global to shared memory (16-byte pieces when both
+// ends allow it), cooperatively over the CTA.
+__device__ __forceinline__ void stage_row(float* dst, const float* src, int n, int tid, int nthreads) {
+  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 &&
+      (n & 3) == 0) {
+    for (int q = tid; q < n / 4; q += nthreads)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 4 * q)),
+                   "l"(src + 4 * q)
+                   : "memory");
+  } else {
+    for (int q = tid; q < n; q += nthreads) cp_async4(dst + q, src + q);
+  }
+}
+
+constexpr int PW = 1024;  // panel chunk: columns (forward) or rows (backward)
+
 __global__ void __launch_bounds__(SV_T) solve32_kernel(const float* __restrict__ L,
                                                        const float* __restrict__ Linv, int K,
                                                        const float* __restrict__ R32,
                                                        double* __restrict__ Xs) {
-  extern __shared__ float sv[];
-  float* y = sv;             // K: forward result, then the solution
-  float* part = sv + K;      // 8 x 32 partial sums
-  float* u = part + 8 * 32;  // 32
+  extern __shared__ __align__(16) float sv[];
+  float* pan = sv;                      // 32 x PW (forward) / PW x 32 (backward)
+  float* y = pan + NB * PW;             // K: forward result, then the solution
+  float* part = y + ((K + 3) & ~3);     // 8 x 32 partial sums
+  float* u = part + 8 * 32;             // 32
   const int col = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nblk = (K + NB - 1) / NB;
   // forward
   for (int b = 0; b < nblk; ++b) {
     const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
-    // rows k0 + (4 per warp), columns [0, k0) split over lanes
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};  // rows warp * 4 + rr
+    for (int c0 = 0; c0 < k0; c0 += PW) {
+      const int cw = k0 - c0 < PW ? k0 - c0 : PW;
+      __syncthreads();  // the previous chunk has been consumed
+      for (int r = 0; r < nb; ++r)
+        stage_row(pan + static_cast<size_t>(r) * cw, L + static_cast<size_t>(k0 + r) * K + c0, cw, tid, SV_T);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int r = warp * 4 + rr;
+        if (r < nb) {
+          const float* pr = pan + static_cast<size_t>(r) * cw;
+          float a0 = 0.f, a1 = 0.f;
+          int k = lane;
+          for (; k + 32 < cw; k += 64) {
+            a0 = fmaf(pr[k], y[c0 + k], a0);
+            a1 = fmaf(pr[k + 32], y[c0 + k + 32], a1);
+          }
+          if (k < cw) a0 = fmaf(pr[k], y[c0 + k], a0);
+          acc[rr] += a0 + a1;
+        }
+      }
+    }
+#pragma unroll
     for (int rr = 0; rr < 4; ++rr) {
       const int r = warp * 4 + rr;
-      float acc = 0.f;
-      if (r < nb) {
-        const float* lr = L + static_cast<size_t>(k0 + r) * K;
-        for (int k = lane; k < k0; k += 32) acc = fmaf(lr[k], y[k], acc);
-      }
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0 && r < NB) u[r] = r < nb ? R32[static_cast<size_t>(k0 + r) * RW + col] - acc : 0.f;
+      float v = acc[rr];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) u[r] = r < nb ? R32[static_cast<size_t>(k0 + r) * RW + col] - v : 0.f;
     }
     __syncthreads();
     if (warp == 0) {
       const float* inv = Linv + static_cast<size_t>(b) * NB * NB;
-      float acc = 0.f;
+      float a = 0.f;
 #pragma unroll 8
-      for (int k = 0; k < NB; ++k) acc = fmaf(inv[lane * NB + k], u[k], acc);
-      if (lane < nb) y[k0 + lane] = acc;
+      for (int k = 0; k < NB; ++k) a = fmaf(inv[lane * NB + k], u[k], a);
+      if (lane < nb) y[k0 + lane] = a;
     }
     __syncthreads();
   }
   // backward (y is overwritten by x block by block, last block first)
   for (int b = nblk - 1; b >= 0; --b) {
     const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
+    const int k1 = k0 + NB, rest = K > k1 ? K - k1 : 0;
     float acc = 0.f;
-    for (int k = k0 + NB + warp; k < K; k += 8)
-      if (lane < nb) acc = fmaf(L[static_cast<size_t>(k) * K + k0 + lane], y[k], acc);
+    for (int q0 = 0; q0 < rest; q0 += PW) {
+      const int qw = rest - q0 < PW ? rest - q0 : PW;
+      __syncthreads();
+      // 32 columns of qw rows: 16-byte pieces when the rows allow it (K % 4 == 0)
+      const float* src0 = L + static_cast<size_t>(k1 + q0) * K + k0;
+      if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(src0) & 15u) == 0) {
+        for (int f = tid; f < qw * (NB / 4); f += SV_T) {
+          const int k = f >> 3, q = f & 7;
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(pan + k * NB + 4 * q)),
+                       "l"(src0 + static_cast<size_t>(k) * K + 4 * q)
+                       : "memory");
+        }
+      } else {
+        for (int f = tid; f < qw * NB; f += SV_T) {
+          const int k = f >> 5, q = f & 31;
+          cp_async4(pan + k * NB + q, src0 + static_cast<size_t>(k) * K + q);
+        }
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+      for (int k = warp; k < qw; k += 8)
+        acc = fmaf(pan[static_cast<size_t>(k) * NB + lane], y[k1 + q0 + k], acc);
+    }
     part[warp * 32 + lane] = acc;
     __syncthreads();
     if (warp == 0) {
@@ -696,44 +822,43 @@ __global__ void __launch_bounds__(SV_T) solve32_kernel(const float* __restrict__
 }
 
 // ---- 5e. FP64 residual of the scaled system: R = Zs - (S M S) X, as FP32 -----
-// 32 x 48 output tiles (one row per warp lane group), k in chunks of 32.
-__global__ void __launch_bounds__(256) residual_kernel(const double* __restrict__ M,
+// 8 x 48 output tiles (K/8 CTAs, so the FP64 pipes of every SM take part);
+// thread (row tid / 24, columns tid % 24 and tid % 24 + 24); k in chunks of 32.
+constexpr int RS_ROWS = 8;
+__global__ void __launch_bounds__(192) residual_kernel(const double* __restrict__ M,
                                                        const double* __restrict__ dsc, int K,
                                                        const double* __restrict__ Zs,
                                                        const double* __restrict__ Xs,
                                                        float* __restrict__ R32) {
-  __shared__ double Ms[32][33];
+  __shared__ double Ms[RS_ROWS][33];
   __shared__ double Xt[32][RW];
-  const int j0 = blockIdx.x * 32;
-  const int tr = threadIdx.x / 8, tc = threadIdx.x % 8;  // row tr, columns tc + 8q (q < 6)
-  double acc[6] = {};
+  const int j0 = blockIdx.x * RS_ROWS;
+  const int tr = threadIdx.x / 24, tc = threadIdx.x % 24;
+  double acc0 = 0.0, acc1 = 0.0;
   for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int f = threadIdx.x; f < 32 * 32; f += 256) {
+    for (int f = threadIdx.x; f < RS_ROWS * 32; f += 192) {
       const int r = f / 32, c = f % 32;
       Ms[r][c] = (j0 + r < K && k0 + c < K) ? M[static_cast<size_t>(j0 + r) * K + k0 + c] : 0.0;
     }
-    for (int f = threadIdx.x; f < 32 * RW; f += 256) {
+    for (int f = threadIdx.x; f < 32 * RW; f += 192) {
       const int r = f / RW, c = f % RW;
       Xt[r][c] = k0 + r < K ? dsc[k0 + r] * Xs[static_cast<size_t>(k0 + r) * RW + c] : 0.0;
     }
     __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
     for (int k = 0; k < 32; ++k) {
       const double m = Ms[tr][k];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) acc[q] = fma(m, Xt[k][tc + 8 * q], acc[q]);
+      acc0 = fma(m, Xt[k][tc], acc0);
+      acc1 = fma(m, Xt[k][tc + 24], acc1);
     }
     __syncthreads();
   }
   const int j = j0 + tr;
   if (j < K) {
     const double dj = dsc[j];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int c = tc + 8 * q;
-      R32[static_cast<size_t>(j) * RW + c] =
-          static_cast<float>(Zs[static_cast<size_t>(j) * RW + c] - dj * acc[q]);
-    }
+    R32[static_cast<size_t>(j) * RW + tc] = static_cast<float>(Zs[static_cast<size_t>(j) * RW + tc] - dj * acc0);
+    R32[static_cast<size_t>(j) * RW + tc + 24] =
+        static_cast<float>(Zs[static_cast<size_t>(j) * RW + tc + 24] - dj * acc1);
   }
 }
 
@@ -854,6 +979,9 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
                 const uint8_t* nnz, int s, const float* D_old, const float* resid,
                 float* D_new, void* ws, cudaStream_t st, uint32_t** status_out) {
   using namespace mod;
+  if (N >= (int64_t(1) << 26))
+    return set_error(DLSH_ERR_UNSUPPORTED,
+                     "dlsh_mod_update: N must be < 2^26 (the atom lists pack signal and nnz in 32 bits)");
   Ws w;
   carve(ws, K, s, N, w);
   if (status_out) *status_out = w.status;
@@ -874,14 +1002,15 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
-    scatter_kernel<<<T, 32, K * sizeof(int), st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list_sig,
-                                                  w.list_coef, w.list_nnz);
+    scatter_kernel<<<T, 32, K * sizeof(int), st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
     ++launches;
   }
   DLSH_CUDA_TRY(cudaFuncSetAttribute(accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(acc_smem)),
                 "dlsh_mod_update: attribute");
-  seg_scan_kernel<<<1, 1024, 0, st>>>(w.atom_total, K, w.seg_start);
+  const int P = static_cast<int>(n_blocks(N));
+  const int tpb = tiles_per_block(T);
+  seg_scan_kernel<<<1, 1024, 0, st>>>(w.off, w.atom_start, T, tpb, K, P * K, w.seg_start);
   {
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
@@ -892,10 +1021,11 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
     const int64_t ms = max_segments(K, s, N);
     if (grid > ms) grid = ms;
     accum_kernel<<<static_cast<int>(grid), acc_nw * 32, acc_smem, st>>>(
-        X, reinterpret_cast<const uint32_t*>(idx), coef, s, K, w.atom_start, w.seg_start,
-        w.list_sig, w.list_coef, w.list_nnz, w.Gp, w.Bp);
+        X, reinterpret_cast<const uint32_t*>(idx), coef, s, K, w.atom_start, w.off, T, tpb, P * K,
+        w.seg_start,
+        w.list, w.Gp, w.Bp);
   }
-  seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, w.M, w.Z);
+  seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, P, w.M, w.Z);
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
   launches += 4;
   // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
@@ -915,10 +1045,16 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
       launches += 2;
     }
   }
-  const size_t sv_smem = static_cast<size_t>(K + 8 * 32 + 32) * sizeof(float);
+  const size_t sv_smem =
+      (static_cast<size_t>(NB) * PW + ((K + 3) & ~3) + 8 * 32 + 32) * sizeof(float);
+  if (sv_smem > static_cast<size_t>(SMEM_LIMIT))
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mod_update: K=%d too large for the solve", K);
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(solve32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(sv_smem)),
+                "dlsh_mod_update: attribute");
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
-      residual_kernel<<<(K + 31) / 32, 256, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
+      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, 192, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
       ++launches;
     }
     solve32_kernel<<<DLSH_D, SV_T, sv_smem, st>>>(w.A32, w.Linv32, K, w.R32, w.Xs);
