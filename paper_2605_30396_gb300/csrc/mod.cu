@@ -287,7 +287,7 @@ __device__ __forceinline__ void block_range(const int* __restrict__ off,
   hi = t1 < T ? off[static_cast<size_t>(j) * T + t1] : atom_start[j + 1];
 }
 
-constexpr int AB = 32;  // list entries per batch
+constexpr int AB = 16;  // list entries per batch (<= 32: one lane per entry when staging)
 __host__ __device__ constexpr int acc_buf_words(int s) {
   return 3 * AB + AB * DLSH_D + AB * s + AB * (s / 2 + 1);
 }
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128)
     li = 0;
     la = 0.f;
     ln = 0;
-    if (e < q1) {
+    if (lane < AB && e < q1) {
       const uint2 rec = list[e];
       li = static_cast<int>(rec.x & 0x3FFFFFFu);
       la = __uint_as_float(rec.y);
@@ -357,9 +357,11 @@ __global__ void __launch_bounds__(128)
     float* B = bptr(buf);
     int* ei = reinterpret_cast<int*>(B);
     int* en = ei + 2 * AB;
-    B[AB + lane] = la;
-    ei[lane] = li;
-    en[lane] = ln;
+    if (lane < AB) {
+      B[AB + lane] = la;
+      ei[lane] = li;
+      en[lane] = ln;
+    }
     __syncwarp();
     float* xb = B + 3 * AB;
     float* cf = xb + AB * DLSH_D;
