@@ -287,7 +287,7 @@ __device__ __forceinline__ void block_range(const int* __restrict__ off,
   hi = t1 < T ? off[static_cast<size_t>(j) * T + t1] : atom_start[j + 1];
 }
 
-constexpr int AB = 16;  // list entries per batch (<= 32: one lane per entry when staging)
+constexpr int AB = 8;   // list entries per batch (<= 32: one lane per entry when staging)
 __host__ __device__ constexpr int acc_buf_words(int s) {
   return 3 * AB + AB * DLSH_D + AB * s + AB * (s / 2 + 1);
 }
@@ -1018,7 +1018,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
     if (sms <= 0) sms = 1;
     int per_sm = static_cast<int>(SMEM_LIMIT / (acc_smem > 0 ? acc_smem : 1));
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 4) per_sm = 4;
+    if (per_sm > 8) per_sm = 8;
     int64_t grid = static_cast<int64_t>(sms) * per_sm;
     const int64_t ms = max_segments(K, s, N);
     if (grid > ms) grid = ms;
