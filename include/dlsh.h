@@ -51,8 +51,10 @@ extern "C" {
 
 /* ---- correlation precision of the OMP atom selection (D^T r) --------- */
 #define DLSH_PREC_FP32 0 /* "plain FP32": 3xTF32 split on tcgen05, FP32 accumulate */
-#define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate, top-4 FP32 re-score    */
-#define DLSH_PREC_FP8  2 /* E4M3, per-atom and per-row scales, top-4 FP32 re-score */
+#define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; the best atom of each
+                            column quarter (j mod 128 in [32q, 32q+32)) is
+                            re-scored in FP32 before the commit                  */
+#define DLSH_PREC_FP8  2 /* E4M3 with per-atom and per-row scales; re-score as BF16 */
 
 /* ---- flags ------------------------------------------------------------ */
 #define DLSH_FLAG_SYNC 1 /* synchronise the stream and report device status */

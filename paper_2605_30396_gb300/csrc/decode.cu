@@ -5,7 +5,7 @@
 //
 // Memory-bound design: the FP32 dictionary is staged once per CTA in shared
 // memory and every nonzero costs three 16-lane reads of one dictionary row.  A
-// warp works on batches of 32 Gaussians: first all of the batch's codes are
+// warp works on batches of 16 Gaussians: first all of the batch's codes are
 // loaded (coalesced) into shared memory while one lane per Gaussian computes its
 // direction and 15 basis values; then each half-warp takes one Gaussian, lane b
 // owning basis b of all three channels, accumulates sum_t coef * D[j_t, c*15+b],
@@ -24,7 +24,8 @@ constexpr int YS = 17;          // basis values per Gaussian slot (15 used, slot
 constexpr int SMEM_LIMIT = 232448;
 
 // Per-warp shared memory: basis slots, staged rgb, and the batch's codes.
-__host__ __device__ constexpr int warp_floats(int s) { return 32 * YS + 96 + 32 * s * 2; }
+constexpr int GB = 16;          // Gaussians per warp batch (small batches: more warps fit per SM)
+__host__ __device__ constexpr int warp_floats(int s) { return GB * YS + GB * 3 + GB * s * 2; }
 
 // Real-SH constants of the Cartesian forms below, computed on the host from
 // N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) and the associated Legendre
@@ -57,7 +58,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[1
 }
 
 template <bool SMEM_D>
-__global__ void __launch_bounds__(512) decode_kernel(
+__global__ void __launch_bounds__(1024) decode_kernel(
     const float* __restrict__ D, int K, const uint16_t* __restrict__ idx,
     const float* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int64_t N,
     const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
@@ -69,21 +70,21 @@ __global__ void __launch_bounds__(512) decode_kernel(
   const int dwords = SMEM_D ? K * ROW + 16 : 0;
   float* wsm = sm + dwords + warp * warp_floats(s);
   float* Ys = wsm;
-  float* outs = wsm + 32 * YS;
-  float* ccoef = outs + 96;
-  uint32_t* cidx = reinterpret_cast<uint32_t*>(ccoef + 32 * s);
+  float* outs = wsm + GB * YS;
+  float* ccoef = outs + GB * 3;
+  uint32_t* cidx = reinterpret_cast<uint32_t*>(ccoef + GB * s);
   if (SMEM_D) {
     for (int f = threadIdx.x; f < dwords; f += blockDim.x) Ds[f] = f < K * ROW ? D[f] : 0.f;
     __syncthreads();
   }
   const int hl = lane & 15, h = lane >> 4;
   const unsigned FULL = 0xffffffffu;
-  const int64_t nbatch = (N + 31) / 32;
+  const int64_t nbatch = (N + GB - 1) / GB;
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
   bool bad = false;
   for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
-    const int64_t base = bt * 32;
-    const int nb = N - base < 32 ? static_cast<int>(N - base) : 32;
+    const int64_t base = bt * GB;
+    const int nb = N - base < GB ? static_cast<int>(N - base) : GB;
     // ---- phase A: every load of the batch is issued here, then one lane per
     // Gaussian computes its direction and 15 basis values
     for (int f = lane; f < nb * s; f += 32) {
@@ -111,13 +112,15 @@ __global__ void __launch_bounds__(512) decode_kernel(
       }
       float Y[15];
       sh_basis(vx, vy, vz, Y);
+      if (lane < GB) {
 #pragma unroll
-      for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
-      Ys[lane * YS + 15] = __int_as_float(nz);
+        for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
+        Ys[lane * YS + 15] = __int_as_float(nz);
+      }
     }
     __syncwarp();
     // ---- phase B: a half-warp per Gaussian, lane hl owns basis hl of R, G, B
-    for (int pp = 0; pp < 16; ++pp) {
+    for (int pp = 0; pp < GB / 2; ++pp) {
       const int gl = 2 * pp + h;
       int nz = gl < nb ? __float_as_int(Ys[gl * YS + 15]) : 0;
       if (nz > s) {
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(512) decode_kernel(
     __syncwarp();
     // ---- coalesced store of the batch's outputs
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
+    for (int q = 0; q < (GB * 3 + 31) / 32; ++q) {
       const int e = lane + 32 * q;
       if (e < nb * 3) rgb[base * 3 + e] = outs[e];
     }
@@ -238,11 +241,11 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
   int sms = device_sm_count();
   if (sms <= 0) sms = 1;
   const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
-  const int64_t nbatch = (N + 31) / 32;
+  const int64_t nbatch = (N + GB - 1) / GB;
   const size_t dbytes = (static_cast<size_t>(K) * ROW + 16) * 4;
   const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
   int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
-  if (nwarps > 16) nwarps = 16;
+  if (nwarps > 32) nwarps = 32;
   if (nwarps >= 6) {
     const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
     DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<true>,

@@ -13,9 +13,10 @@
 //   warps 0-15  selection + solver, in two phases per iteration:
 //            selection: four threads per TMEM lane (one per column quarter)
 //            read the row's correlations with tcgen05.ld and keep the running
-//            argmax (exact for FP32; top 4 for BF16/FP8);
+//            argmax on 32-bit keys (|c| and the column index);
 //            solver: four sub-lanes per signal, each owning 12 of the 48 dims,
-//            merge the quarters (FP32 re-score of the top 4 for BF16/FP8),
+//            merge the quarters (for BF16/FP8 the four quarter winners are
+//            re-scored in FP32),
 //            extend the Cholesky factor of the support's Gram matrix, solve
 //            the least-squares system, recompute r = x - D_I gamma in FP32 and
 //            write r back as the next A operand.
@@ -86,7 +87,7 @@ int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM
   p.off_g = take(s * TILE_M * 4);
   p.off_idg = take(s * TILE_M * 4);
   p.off_rowt = take(TILE_M * 4);
-  p.off_cand = take(TILE_M * 4 * (prec == 0 ? 1 : 4) * 8);
+  p.off_cand = take(TILE_M * 4 * 8);
   p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
   p.off_sig = take(prec == 2 ? p.Kp * 4 : 0);
   p.off_bar = take(1024);
@@ -402,24 +403,6 @@ __device__ __forceinline__ float quad_max(float v) {
   return v;
 }
 
-// Inserts (v, j) into a list sorted by (value desc, index asc) of length 4.
-__device__ __forceinline__ void top4_insert(float (&tv)[4], int (&tj)[4], float v, int j) {
-  auto before = [](float a, int ja, float b, int jb) { return a > b || (a == b && ja < jb); };
-  if (!before(v, j, tv[3], tj[3])) return;
-  if (before(v, j, tv[0], tj[0])) {
-    tv[3] = tv[2]; tj[3] = tj[2]; tv[2] = tv[1]; tj[2] = tj[1]; tv[1] = tv[0]; tj[1] = tj[0];
-    tv[0] = v; tj[0] = j;
-  } else if (before(v, j, tv[1], tj[1])) {
-    tv[3] = tv[2]; tj[3] = tj[2]; tv[2] = tv[1]; tj[2] = tj[1];
-    tv[1] = v; tj[1] = j;
-  } else if (before(v, j, tv[2], tj[2])) {
-    tv[3] = tv[2]; tj[3] = tj[2];
-    tv[2] = v; tj[2] = j;
-  } else {
-    tv[3] = v; tj[3] = j;
-  }
-}
-
 template <int NC>
 __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[NC]);
 template <>
@@ -458,8 +441,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NBUF = 512 / BN;
   constexpr int QC = BN / 4;  // columns of one chunk read by one phase-1 thread
-  constexpr int NCAND = PREC == 0 ? 1 : 4;
-  static_assert(PREC == 0 || QC == 32, "the top-4 key network packs a 5-bit column index");
+  constexpr int NCAND = 1;  // one candidate per thread (column quarter) and row
+  static_assert(QC <= 32, "selection keys pack a 5-bit column index");
   const Plan& p = a.p;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long NS = a.n_dev ? *a.n_dev : a.N;
@@ -698,14 +681,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           __syncwarp();
           if (lane == 0) mbar_arrive(&bar_empty[static_cast<int>(ccq % NBUF)]);
         };
-        if constexpr (PREC == 0) {
+        {
           // Argmax of |c| on 32-bit keys: |c| with its low 5 mantissa bits
           // replaced by 31 - k (k = column within the quarter), so one integer
           // max per element yields the largest value and, among values equal
           // to 2^-18 relative, the smallest column.  Chunks are compared on
           // the value bits only (strictly greater wins), so ties go to the
-          // smallest atom index overall.  Atoms already in the support are not
-          // masked here (see the solver's stop rule).
+          // smallest atom index overall.  FP32: this is the selection.  BF16 and
+          // FP8: each thread's winner (one per column quarter) is a candidate
+          // that the solver re-scores in FP32.  Atoms already in the support
+          // are not masked here (see the solver's stop rule).
           uint32_t best = 0;
           int bestc = 0;
           for (int c = 0; c < nchunks; ++c, ++cc) {
@@ -718,6 +703,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
             tmem_ld_wait<QC>(rr);
             release(cc);
+            if constexpr (PREC == 2) {
+              const int j0 = c * BN + q1 * QC;
+#pragma unroll
+              for (int k = 0; k < QC; ++k) rr[k] = __float_as_uint(__uint_as_float(rr[k]) * sig[j0 + k]);
+            }
             uint32_t m0 = 0, m1 = 0;
 #pragma unroll
             for (int k = 0; k < QC; k += 2) {
@@ -732,66 +722,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           }
           cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
           cj[R1 * 4 + q1] = bestc * BN + q1 * QC + 31 - static_cast<int>(best & 31u);
-        } else {
-          // Top 4 of |c| per thread: keys as in the FP32 path (|c| with its low
-          // 5 mantissa bits replaced by 31 - k), a chunk's largest key gates a
-          // branchless min/max network.  Support atoms are not masked: the
-          // residual is orthogonal to them, the FP32 re-score puts them near
-          // zero, and a row whose re-scored winner is a support atom stops.
-          // Padding atoms (j >= K) have zero rows, so their keys carry value 0
-          // and never enter the list.
-          float tv[4] = {0.f, 0.f, 0.f, 0.f};
-          int tj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-          for (int c = 0; c < nchunks; ++c, ++cc) {
-            if (!acquire(cc)) {
-              ok = false;
-              break;
-            }
-            __syncwarp();
-            uint32_t rr[QC];
-            tmem_ld_issue<QC>(trow + static_cast<uint32_t>((cc % NBUF) * BN), rr);
-            tmem_ld_wait<QC>(rr);
-            release(cc);
-            const int j0 = c * BN + q1 * QC;
-            if constexpr (PREC == 2) {
-#pragma unroll
-              for (int k = 0; k < QC; ++k) rr[k] = __float_as_uint(__uint_as_float(rr[k]) * sig[j0 + k]);
-            }
-            uint32_t m0 = 0, m1 = 0;
-#pragma unroll
-            for (int k = 0; k < QC; k += 2) {
-              m0 = max(m0, rr[k] & 0x7fffffe0u);
-              m1 = max(m1, rr[k + 1] & 0x7fffffe0u);
-            }
-            if (__uint_as_float(max(m0, m1)) > tv[3]) {
-              uint32_t k0 = 0, k1 = 0, k2 = 0, k3 = 0;
-#pragma unroll
-              for (int k = 0; k < QC; ++k) {
-                uint32_t xk = (rr[k] & 0x7fffffe0u) | static_cast<uint32_t>(31 - k);
-                uint32_t hi = max(k0, xk);
-                xk = min(k0, xk);
-                k0 = hi;
-                hi = max(k1, xk);
-                xk = min(k1, xk);
-                k1 = hi;
-                hi = max(k2, xk);
-                xk = min(k2, xk);
-                k2 = hi;
-                k3 = max(k3, xk);
-              }
-              const uint32_t kk[4] = {k0, k1, k2, k3};
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float val = __uint_as_float(kk[e] & ~31u);
-                if (val > tv[3]) top4_insert(tv, tj, val, j0 + 31 - static_cast<int>(kk[e] & 31u));
-              }
-            }
-          }
-#pragma unroll
-          for (int k = 0; k < NCAND; ++k) {
-            cv[(R1 * 4 + q1) * NCAND + k] = tv[k];
-            cj[(R1 * 4 + q1) * NCAND + k] = tj[k];
-          }
         }
         const long long T1 = prof_on ? clock64() : 0;
         // barrier + vote: every selection thread leaves together if any wait ran out
@@ -839,20 +769,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             for (int m = 0; m < SMAX; ++m) dup |= (m < t && sl[m] == js);
             if (dup) js = -1;
           } else {
-            // entries with j >= K are empty slots (value 0, index INT_MAX)
-            float mv[4] = {-1.f, -1.f, -1.f, -1.f};
-            int mj[4] = {0x7fffffff, 0x7fffffff, 0x7fffffff, 0x7fffffff};
-#pragma unroll 1
-            for (int e = 0; e < 16; ++e) {
-              const int j = cj[R2 * 16 + e];
-              if (j < K) top4_insert(mv, mj, cv[R2 * 16 + e], j);
-            }
-            // FP32 re-score of the four candidates: c = r . d_j
+            // the four column-quarter winners re-scored in FP32: c = r . d_j
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int qq = 0; qq < 4; ++qq) {
+              const int j = cj[R2 * 4 + qq];
               float c0 = 0.f;
-              if (mv[k] >= 0.f) {
-                const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(mj[k]) * DPAD + 12 * u);
+              if (j < K) {
+                const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(j) * DPAD + 12 * u);
 #pragma unroll
                 for (int w4 = 0; w4 < 3; ++w4) {
                   const float4 dv = __ldg(dr + w4);
@@ -863,9 +786,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 }
               }
               c0 = fabsf(quad_sum(c0));
-              if (mv[k] >= 0.f && (c0 > best || (c0 == best && mj[k] < js))) {
+              if (j < K && (c0 > best || (c0 == best && j < js))) {
                 best = c0;
-                js = mj[k];
+                js = j;
               }
             }
           }

@@ -29,11 +29,3 @@ def well_separated(topc, nnz, margin):
     steps = np.arange(s)[None, :] < np.asarray(nnz)[:, None]
     ok = np.where(steps, gaps > margin, True)
     return ok.all(axis=1)
-
-
-def in_top4(topc, nnz, rel_gap):
-    """Signals whose true winner clears the 5th-best by rel_gap at every step."""
-    gaps = topc[:, :, 0] - topc[:, :, 4]
-    s = topc.shape[1]
-    steps = np.arange(s)[None, :] < np.asarray(nnz)[:, None]
-    return np.where(steps, gaps > rel_gap, True).all(axis=1)

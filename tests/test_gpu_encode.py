@@ -3,7 +3,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import embed45, in_top4, well_separated
+from gpu_common import embed45, well_separated
 from oracle import omp as oomp
 from paper_2605_30396_gb300 import synth
 
@@ -74,17 +74,18 @@ def test_plain_fp32_matches_oracle(lib, N, K, s):
 
 @pytest.mark.parametrize("prec,delta", [("bf16", 6e-3), ("fp8", 6e-2)])
 def test_low_precision_with_rescore(lib, prec, delta):
-    """BF16 / FP8 correlation + FP32 re-score of the top 4.  delta bounds the
-    low-precision correlation error relative to ||r|| (the a1 tests measure it);
-    wherever the oracle's winner clears its 5th-best by more than 2 delta at every
-    step, the winner is inside the top 4 and the re-score must pick it exactly."""
+    """BF16 / FP8 correlation; each column quarter's low-precision winner is
+    re-scored in FP32.  delta bounds the low-precision correlation error relative
+    to ||r|| (the a1 tests measure it); wherever the oracle's winner clears the
+    runner-up by more than 2 delta at every step, it wins its quarter in low
+    precision and the re-score must pick it exactly."""
     N, K, s = 3000, 256, 4
     D = synth.hidden_dictionary(K, 7)
     X = synth.signals(N, D, s, 1).astype(np.float64)  # codes over D itself: large margins
     ref = oomp.omp(D.astype(np.float32).astype(np.float64), X, s)
     idx, cf, nnz, resid = run(lib, D, X, s, prec)
-    ok = in_top4(ref["topc"], ref["nnz"], 2 * delta) & well_separated(ref["topc"], ref["nnz"], 1e-4)
-    assert ok.mean() > 0.2, ok.mean()
+    ok = well_separated(ref["topc"], ref["nnz"], 2 * delta)
+    assert ok.sum() >= 100, ok.sum()
     np.testing.assert_array_equal(idx[ok], ref["idx"][ok])
     r_got = np.sqrt(resid.sum() / (N * 45))
     r_ref = np.sqrt(ref["resid_sq"].sum() / (N * 45))
