@@ -406,10 +406,18 @@ __global__ void topk_kernel(const float* __restrict__ Z, long long rows, int K,
     tj[q] = 0x7fffffff;
   }
   const float* zr = Z + r * K;
+  // Pre-filter: tau0 = the smallest of the lanes' maxima.  At least 32 >= M
+  // values reach tau0 (one per lane), so every value of the top M does too;
+  // only values >= tau0 enter the lists (usually one to three per lane).
+  float lmax = -INFINITY;
+  for (int k = lane; k < K; k += 32) lmax = fmaxf(lmax, zr[k]);
+  float tau0 = lmax;
+  for (int o = 16; o > 0; o >>= 1) tau0 = fminf(tau0, __shfl_xor_sync(0xffffffffu, tau0, o));
+  if (K < 32) tau0 = -INFINITY;  // some lane holds no value: keep all
   for (int k = lane; k < K; k += 32) {
     float cv = zr[k];
     int cj = k;
-    if (ranks_before(cv, cj, tv[M - 1], tj[M - 1])) {
+    if (cv >= tau0 && ranks_before(cv, cj, tv[M - 1], tj[M - 1])) {
 #pragma unroll
       for (int q = 0; q < M; ++q) {
         if (ranks_before(cv, cj, tv[q], tj[q])) {

@@ -1,0 +1,89 @@
+"""The scene workload at full size (N = 3,000,000, K = 1024, s = 8: the step
+bench.py times, through the same calls): encode and decode checked against the
+oracle on sampled signals, the properties that hold at any size checked on all
+of them, and the MOD update (which depends on every signal) against the
+oracle's full update from the same codes."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import close_rel, well_separated
+from oracle import mod as omod
+from oracle import omp as oomp
+from oracle import sh as osh
+from paper_2605_30396_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+N, K, S = 3_000_000, 1024, 8
+
+
+@pytest.fixture(scope="module")
+def scene(lib):
+    Dh = synth.hidden_dictionary(K, 0, rho=0.6)
+    X = synth.signals(N, Dh, S, 1)
+    init = synth.init_atom_indices(N, K, 0)
+    cam, mu = synth.camera_and_means(N, 2, 3)
+    Xt = torch.from_numpy(X).cuda()
+    D = lib.init_dictionary(Xt, init, sync=True)
+    idx, coef, nnz, resid = lib.encode(D, Xt, S, sync=True)
+    return {"X": X, "Xt": Xt, "D": D, "cam": cam, "mu": mu,
+            "idx": idx, "coef": coef, "nnz": nnz, "resid": resid}
+
+
+def test_encode_sampled_and_everywhere(lib, scene):
+    D = scene["D"].cpu().numpy().astype(np.float64)
+    idx = lib.idx_as_long(scene["idx"]).cpu().numpy()
+    coef = scene["coef"].cpu().numpy().astype(np.float64)
+    nnz = scene["nnz"].cpu().numpy()
+    resid = scene["resid"].cpu().numpy().astype(np.float64)
+    X = scene["X"]
+    # everywhere: support sizes, index range, no repeated atom, residual >= 0
+    assert nnz.max() <= S and idx.max() < K and (resid >= 0).all()
+    take = np.arange(S)[None, :] < nnz[:, None]
+    srt = np.sort(np.where(take, idx, -1 - np.arange(S)[None, :]), axis=1)
+    assert (np.diff(srt, axis=1) != 0).all()
+    # sampled: the oracle's OMP on the same dictionary
+    samp = np.random.default_rng(5).choice(N, 3000, replace=False)
+    ref = oomp.omp(D, X[samp].astype(np.float64), S)
+    sep = well_separated(ref["topc"], ref["nnz"], 1e-4)
+    assert sep.sum() > 1000, sep.sum()
+    np.testing.assert_array_equal(idx[samp][sep], ref["idx"][sep])
+    # reported residual = ||x - D_I gamma||^2 recomputed in FP64, and r is
+    # orthogonal to the selected atoms (least squares), on the sample
+    Xs = X[samp].astype(np.float64)
+    rec = osh.reconstruct(D, idx[samp], coef[samp], nnz[samp])
+    r = Xs - rec
+    assert (np.abs(resid[samp] - np.sum(r * r, axis=1)) <= 1e-4 * np.sum(Xs * Xs, axis=1)).all()
+    for i in range(200):
+        sel = idx[samp[i], :nnz[samp[i]]]
+        assert np.abs(D[sel] @ r[i]).max() <= 1e-5 * np.linalg.norm(Xs[i])
+    r_got = np.sqrt(resid[samp].sum() / (len(samp) * 45))
+    r_ref = np.sqrt(ref["resid_sq"].sum() / (len(samp) * 45))
+    assert abs(r_got - r_ref) <= 1e-4 * r_ref, (r_got, r_ref)
+
+
+def test_decode_sampled(lib, scene):
+    MU = torch.from_numpy(scene["mu"]).cuda()
+    rgb = lib.decode(scene["D"], scene["idx"], scene["coef"], scene["nnz"], means=MU,
+                     cam=scene["cam"], sync=True).cpu().numpy()
+    assert np.isfinite(rgb).all()
+    samp = np.random.default_rng(6).choice(N, 3000, replace=False)
+    D = scene["D"].cpu().numpy().astype(np.float64)
+    idx = lib.idx_as_long(scene["idx"]).cpu().numpy()[samp]
+    coef = scene["coef"].cpu().numpy().astype(np.float64)[samp]
+    nnz = scene["nnz"].cpu().numpy()[samp]
+    dirs = osh.view_directions(scene["mu"][samp].astype(np.float64), np.asarray(scene["cam"], dtype=np.float64))
+    ref = osh.decode(D, idx, coef, nnz, dirs)
+    ok, worst = close_rel(rgb[samp], ref)
+    assert ok, worst
+
+
+def test_mod_full_update(lib, scene):
+    Dn = lib.mod_update(scene["Xt"], scene["D"], scene["idx"], scene["coef"], scene["nnz"],
+                        scene["resid"], sync=True).cpu().numpy()
+    idx = lib.idx_as_long(scene["idx"]).cpu().numpy()
+    ref, _ = omod.mod_update(scene["X"].astype(np.float64), scene["D"].cpu().numpy().astype(np.float64),
+                             idx, scene["coef"].cpu().numpy().astype(np.float64),
+                             scene["nnz"].cpu().numpy(), scene["resid"].cpu().numpy().astype(np.float64))
+    np.testing.assert_allclose(Dn, ref, atol=3e-6, rtol=0)

@@ -27,7 +27,8 @@ def _gpu(lib, X, D0, idx, coef, nnz, resid):
                           c(resid) if resid is not None else None, sync=True).cpu().numpy()
 
 
-@pytest.mark.parametrize("N,K,s", [(5000, 128, 6), (3000, 256, 8), (20000, 1024, 8), (700, 64, 16)])
+@pytest.mark.parametrize("N,K,s", [(5000, 128, 6), (3000, 256, 8), (20000, 1024, 8), (700, 64, 16),
+                                   (4000, 300, 4), (30000, 2048, 8)])
 def test_mod_matches_oracle(lib, N, K, s):
     X, D0, idx, coef, nnz, resid = _inputs(N, K, s)
     got = _gpu(lib, X, D0, idx, coef, nnz, resid)
