@@ -471,24 +471,34 @@ def main():
     dec_bytes = N * (12 + 6 * s + 1 + 12)  # means, idx+coef, nnz, rgb
     dec_gbs = dec_bytes / (dec_ms * 1e-3) / 1e9
 
-    # end to end through the public API with host buffers (one step)
+    # End to end through the public API, one step per repetition: the step's
+    # inputs (signals, means, dictionary) go host -> device from pinned
+    # memory, the step runs on the device, and its results (codes, residuals,
+    # the new dictionary, the decoded colours) come back to pinned host memory.
     e2e = None
     if not a.no_e2e:
         Xh = torch.from_numpy(X_np).pin_memory()
         MUh = MU.cpu().pin_memory()
         Dh = Dcur.cpu().pin_memory()
+        oh = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (idx, coef, nnz, resid, rgb)]
+        Dnh = torch.empty(Dh.shape, dtype=Dh.dtype).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         reps = max(1, min(3, a.steps))
         for _ in range(reps):
-            hi, hc, hn, hr = api.encode(Dh, Xh, s, precision=a.precision)
-            Dn = api.mod_update(Xh.cuda(non_blocking=True), Dh.cuda(non_blocking=True),
-                                hi.cuda(), hc.cuda(), hn.cuda(), hr.cuda()).cpu()
-            api.decode(Dn, hi, hc, hn, means=MUh, cam=cam)
-        torch.cuda.synchronize()
+            Xd = Xh.to("cuda", non_blocking=True)
+            MUd = MUh.to("cuda", non_blocking=True)
+            Dd = Dh.to("cuda", non_blocking=True)
+            api.encode(Dd, Xd, s, precision=a.precision, out=out)
+            Dn = api.mod_update(Xd, Dd, idx, coef, nnz, resid)
+            api.decode(Dn, idx, coef, nnz, means=MUd, cam=cam, out=rgb)
+            for h, d in zip(oh, (idx, coef, nnz, resid, rgb)):
+                h.copy_(d, non_blocking=True)
+            Dnh.copy_(Dn, non_blocking=True)
+            torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
-        h2d = X_np.nbytes * 2 + mu.nbytes + Dh.numel() * 4 * 2 + N * s * 6 * 2 + N * 5 * 2
-        d2h = N * s * 6 + N * 5 + K * 45 * 4 + N * 12
+        h2d = X_np.nbytes + mu.nbytes + Dh.numel() * 4
+        d2h = sum(t.numel() * t.element_size() for t in (idx, coef, nnz, resid, rgb)) + Dh.numel() * 4
         e2e = {"value": N / dt, "unit": "Gaussians/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 

@@ -105,22 +105,6 @@ int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM
   return DLSH_OK;
 }
 
-// The arrays and sizes one tile is encoded with.
-struct SceneDev {
-  const float* X;
-  long long N;
-  const uint8_t* img;
-  const float* D32p;
-  const float* G;
-  const float* sigma;
-  uint16_t* idx;
-  float* coef;
-  uint8_t* nnz;
-  float* resid;
-  int K, s, nchunks;
-  float eps;
-};
-
 struct Args {
   const float* X;
   int64_t N;
@@ -139,26 +123,6 @@ struct Args {
   const long long* n_dev;    // optional: signal count read on the device (overrides N)
   Plan p;
 };
-
-// The arrays and sizes of tile `tile`.
-__device__ __forceinline__ void tile_scene(const Args& a, long long NS, int tile, SceneDev& sd,
-                                           int& lt) {
-  sd.X = a.X;
-  sd.N = NS;
-  sd.img = a.img;
-  sd.D32p = a.D32p;
-  sd.G = a.G;
-  sd.sigma = a.sigma;
-  sd.idx = a.idx;
-  sd.coef = a.coef;
-  sd.nnz = a.nnz;
-  sd.resid = a.resid_sq;
-  sd.K = a.p.K;
-  sd.s = a.p.s;
-  sd.nchunks = a.p.nchunks;
-  sd.eps = a.eps;
-  lt = tile;
-}
 
 // ---------------------------------------------------------------------------
 // Operand packing.  A row (signal i) occupies 16 bytes per K-block at
@@ -498,11 +462,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         long long ring = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-          SceneDev sd;
-          int lt;
-          tile_scene(a, NS, tile, sd, lt);
-          for (int it = 0; it < sd.s && ok; ++it) {
-            for (int c = 0; c < sd.nchunks; ++c, ++ring) {
+          for (int it = 0; it < p.s && ok; ++it) {
+            for (int c = 0; c < p.nchunks; ++c, ++ring) {
               const int st = static_cast<int>(ring % p.stages);
               const uint32_t par = static_cast<uint32_t>((ring / p.stages) & 1) ^ 1u;
               const long long Wp = prof_any ? clock64() : 0;
@@ -514,7 +475,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               if (prof_any) pcs[9] += clock64() - Wp;
               mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
               bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
-                       sd.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes,
+                       a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes,
                        &bar_dfull[st]);
             }
           }
@@ -535,11 +496,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       long long cc = 0, ring = 0;
       bool ok = true;
       for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        SceneDev sd;
-        int lt;
-        tile_scene(a, NS, tile, sd, lt);
-        const int nchunks = sd.nchunks;
-        for (int it = 0; it < sd.s && ok; ++it) {
+        const int nchunks = p.nchunks;
+        for (int it = 0; it < p.s && ok; ++it) {
           const long long Wa = prof_any ? clock64() : 0;
           if (!mbar_wait(bar_a, a_phase, a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
@@ -615,18 +573,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     bool ok = true;
     const bool prof_on = prof_any && tid == 0;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      SceneDev sd;
-      int lt;
-      tile_scene(a, NS, tile, sd, lt);
-      const int s = sd.s, K = sd.K, nchunks = sd.nchunks;
-      const float eps2 = sd.eps * sd.eps;
-      const int64_t g0 = static_cast<int64_t>(lt) * TILE_M;
-      const int rows = static_cast<int>(sd.N - g0 < TILE_M ? sd.N - g0 : TILE_M);
+      const int s = p.s, K = p.K, nchunks = p.nchunks;
+      const float eps2 = a.eps * a.eps;
+      const int64_t g0 = static_cast<int64_t>(tile) * TILE_M;
+      const int rows = static_cast<int>(NS - g0 < TILE_M ? NS - g0 : TILE_M);
       // -------- each sub-lane loads its 12 dims of the signal (a warp reads 8
       // consecutive rows: one contiguous 1440-byte span)
       // x and r live in registers only during the solver phase (the selection
       // phase needs the registers); x is re-read from L1/L2, r kept in smem.
-      const float* xr = sd.X + (g0 + R2) * DLSH_D + 12 * u;
+      const float* xr = a.X + (g0 + R2) * DLSH_D + 12 * u;
       const bool in_tile = R2 < rows;
       auto load_x = [&](float (&x)[12]) {
 #pragma unroll
@@ -775,7 +730,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               const int j = cj[R2 * 4 + qq];
               float c0 = 0.f;
               if (j < K) {
-                const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(j) * DPAD + 12 * u);
+                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(j) * DPAD + 12 * u);
 #pragma unroll
                 for (int w4 = 0; w4 < 3; ++w4) {
                   const float4 dv = __ldg(dr + w4);
@@ -803,14 +758,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           } else {
             // -------- prefetch: Gram row entries of the support and the new
             // atom's dictionary row
-            const float* Grow = sd.G + static_cast<size_t>(js) * K;
+            const float* Grow = a.G + static_cast<size_t>(js) * K;
             float gv[SMAX];
 #pragma unroll
             for (int m = 0; m < SMAX; ++m) gv[m] = m < t ? __ldg(Grow + sl[m]) : 0.f;
             const float gjj = __ldg(Grow + js);
             float4 dj[3];
             {
-              const float4* dr = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+              const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
 #pragma unroll
               for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
             }
@@ -882,7 +837,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 #pragma unroll
               for (int m = 0; m < SMAX; ++m) {
                 if (m < t) {
-                  const float4* da = reinterpret_cast<const float4*>(sd.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
+                  const float4* da = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
 #pragma unroll
                   for (int w4 = 0; w4 < 3; ++w4) {
                     const float4 dv = __ldg(da + w4);
@@ -941,12 +896,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       if (R2 < rows) {
         const int64_t g = g0 + R2;
         for (int mm = u; mm < s; mm += 4) {
-          sd.idx[g * s + mm] = mm < t ? static_cast<uint16_t>(sel[mm * TILE_M + R2]) : static_cast<uint16_t>(0);
-          sd.coef[g * s + mm] = mm < t ? gs[mm * TILE_M + R2] : 0.f;
+          a.idx[g * s + mm] = mm < t ? static_cast<uint16_t>(sel[mm * TILE_M + R2]) : static_cast<uint16_t>(0);
+          a.coef[g * s + mm] = mm < t ? gs[mm * TILE_M + R2] : 0.f;
         }
         if (u == 0) {
-          sd.nnz[g] = static_cast<uint8_t>(t);
-          if (sd.resid) sd.resid[g] = rn2;
+          a.nnz[g] = static_cast<uint8_t>(t);
+          if (a.resid_sq) a.resid_sq[g] = rn2;
         }
       }
     }
