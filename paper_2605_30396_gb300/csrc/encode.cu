@@ -52,7 +52,7 @@ __host__ __device__ constexpr int op_parts(int prec) { return prec == 0 ? 2 : 1;
 struct Plan {
   int prec, BN, K, Kp, nchunks, stages, resident, s;
   uint32_t a_bytes, chunk_bytes;
-  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_idg, off_rowt, off_cand, off_r,
+  uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_idg, off_cand, off_r,
       off_sig, off_bar, smem;
 };
 
@@ -86,7 +86,6 @@ int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM
   p.off_y = take(s * TILE_M * 4);
   p.off_g = take(s * TILE_M * 4);
   p.off_idg = take(s * TILE_M * 4);
-  p.off_rowt = take(TILE_M * 4);
   p.off_cand = take(TILE_M * 4 * 8);
   p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
   p.off_sig = take(prec == 2 ? p.Kp * 4 : 0);
@@ -552,7 +551,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     float* ys = reinterpret_cast<float*>(smem + p.off_y);       // [m][128]
     float* gs = reinterpret_cast<float*>(smem + p.off_g);       // [m][128]
     float* idg = reinterpret_cast<float*>(smem + p.off_idg);   // [m][128] 1 / L(m, m)
-    int* rowt = reinterpret_cast<int*>(smem + p.off_rowt);      // [128] support size
     float* cv = reinterpret_cast<float*>(smem + p.off_cand);    // [128][4][NCAND]
     int* cj = reinterpret_cast<int*>(smem + p.off_cand + TILE_M * 4 * NCAND * 4);
     float* sig = reinterpret_cast<float*>(smem + p.off_sig);
@@ -572,6 +570,40 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     long long cc = 0;
     bool ok = true;
     const bool prof_on = prof_any && tid == 0;
+    // pre: this tile's signals were written into the A operand (and the MMA
+    // warp released) during the previous tile's last iteration; pre_rn2 is
+    // the thread's row's ||x||^2 from then
+    bool pre = false;
+    float pre_rn2 = 0.f;
+    // Writes the sub-lane's 12 dims of row R2 of tile `tl` into A (FP8 scaled
+    // by the row's max) and returns the row's ||x||^2.
+    auto stage_x = [&](int tl, bool to_rsm) -> float {
+      const int64_t tg0 = static_cast<int64_t>(tl) * TILE_M;
+      const bool tin = R2 < (NS - tg0 < TILE_M ? NS - tg0 : TILE_M);
+      const float* txr = a.X + (tg0 + R2) * DLSH_D + 12 * u;
+      float x[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) x[k] = (tin && 12 * u + k < DLSH_D) ? __ldg(txr + k) : 0.f;
+      float part = 0.f;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) part = fmaf(x[k], x[k], part);
+      float inv = 1.f;
+      if constexpr (PREC == 2) {
+        float mx = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fabsf(x[k]));
+        mx = quad_max(mx);
+        inv = mx > 0.f ? FP8_MAX / mx : 1.f;
+      }
+      write_a_part<PREC>(A, R2, u, x, inv);
+      if constexpr (PREC != 0) {
+        if (to_rsm) {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = x[k];
+        }
+      }
+      return quad_sum(part);
+    };
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int s = p.s, K = p.K, nchunks = p.nchunks;
       const float eps2 = a.eps * a.eps;
@@ -590,32 +622,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       float xnorm, rn2;
       bool active = in_tile;
       int t = 0;
-      if (u == 0) rowt[R2] = 0;
-      {
-        float x[12];
-        load_x(x);
-        float part = 0.f;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) part = fmaf(x[k], x[k], part);
-        rn2 = quad_sum(part);
-        xnorm = sqrtf(rn2);
-        float inv = 1.f;
-        if constexpr (PREC == 2) {
-          float mx = 0.f;
-#pragma unroll
-          for (int k = 0; k < 12; ++k) mx = fmaxf(mx, fabsf(x[k]));
-          mx = quad_max(mx);
-          inv = mx > 0.f ? FP8_MAX / mx : 1.f;
-        }
-        write_a_part<PREC>(A, R2, u, x, inv);
+      if (!pre) {
+        rn2 = stage_x(tile, true);
+        fence_proxy_async_smem();
+        named_bar_sync(1, NEPI);
+        if (tid == 0) mbar_arrive(bar_a);
+      } else {
+        rn2 = pre_rn2;
         if constexpr (PREC != 0) {
+          // the residual copy starts as x (rsm was in use until the last barrier)
+          float x[12];
+          load_x(x);
 #pragma unroll
           for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = x[k];
         }
       }
-      fence_proxy_async_smem();
-      named_bar_sync(1, NEPI);
-      if (tid == 0) mbar_arrive(bar_a);
+      xnorm = sqrtf(rn2);
+      pre = false;
 
       for (int it = 0; it < s; ++it) {
         const long long T0 = prof_on ? clock64() : 0;
@@ -683,6 +706,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         if (named_bar_or(1, NEPI, !ok)) {
           ok = false;
           break;
+        }
+        // Last iteration: every chunk has been read, so the A operand is free.
+        // Stage the next tile's signals now and release the MMA warp, so the
+        // next tile's first correlations run during this solver phase.
+        if (it + 1 == s && tile + static_cast<int>(gridDim.x) < ntiles) {
+          pre_rn2 = stage_x(tile + static_cast<int>(gridDim.x), false);
+          fence_proxy_async_smem();
+          named_bar_sync(1, NEPI);
+          if (tid == 0) mbar_arrive(bar_a);
+          pre = true;
         }
         const long long T2 = prof_on ? clock64() : 0;
 
@@ -860,7 +893,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 #pragma unroll
               for (int k = 0; k < 12; ++k) pr = fmaf(r[k], r[k], pr);
               rn2 = quad_sum(pr);
-              if (u == 0) rowt[R2] = t;
               if (it + 1 < s) {
                 float inv = 1.f;
                 if constexpr (PREC == 2) {
