@@ -29,9 +29,9 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
 # DRAM bytes (read + write) per signal of the encoder, from one ncu capture of
 # encode_kernel at N = 1,000,000, K = 1024, s = 8, FP32 (profiles/
-# encode_kernel_fp32_N1M_K1024_s8.md: 185.07 MB + 37.91 MB); the traffic
+# encode_kernel_fp32_N1M_K1024_s8.md: 184.92 MB + 37.26 MB); the traffic
 # grows with the number of signals, so a launch over N signals moves N times it.
-ENCODE_TRAFFIC = {(1024, 8, "fp32"): (185.071104e6 + 37.910016e6) / 1_000_000}
+ENCODE_TRAFFIC = {(1024, 8, "fp32"): (184.9216e6 + 37.260032e6) / 1_000_000}
 
 
 def parse():
