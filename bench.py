@@ -52,7 +52,7 @@ def parse():
                          "size, K and s encoded by one graph-captured multi-scene call")
     ap.add_argument("--multi-scale", type=float, default=1.0,
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
-    ap.add_argument("--leg", default="step", choices=["step", "encode", "mod", "decode"],
+    ap.add_argument("--leg", default="step", choices=["step", "encode", "mod", "decode", "propose", "train"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -332,6 +332,18 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     elif a.leg == "mod":
         api.encode(D, X, s, precision=a.precision, out=out, sync=True)
         fn = lambda: api.mod_update(X, D, idx, coef, nnz, resid)
+    elif a.leg in ("propose", "train"):
+        # the proposal network at the learned encoder's sizes (2s candidates,
+        # batches of 8192 training pairs), random-init weights
+        from paper_2605_30396_gb300 import synth
+        net = api.MLP(K, synth.mlp_params(K, 7))
+        if a.leg == "propose":
+            fn = lambda: net.propose(X, 2 * s)
+        else:
+            B = 8192
+            ib, _, nb, _ = api.encode(D, X[:B], s, sync=True)
+            fn = lambda: net.train_step(X[:B], ib, nb, lr=1e-3)
+            N = B
     else:
         fn = lambda: api.encode(D, X, s, precision=a.precision, out=out)
     for _ in range(a.warmup):

@@ -264,7 +264,8 @@ size_t dlsh_mlp_workspace_size(int K, int64_t B);
 int dlsh_mlp_init(void* mlp, int K, const float* params, void* stream, int flags);
 /* Copies the FP32 parameter vector out (device). */
 int dlsh_mlp_params(const void* mlp, int K, float* params, void* stream, int flags);
-/* Logits [B x K] of the signals X [B x 45]. */
+/* Logits [B x K] of the signals X [B x 45], by the fused inference kernel of
+ * dlsh_mlp_propose (the layer-by-layer training forward gives the same bits). */
 int dlsh_mlp_forward(const void* mlp, int K, const float* X, int64_t B, float* logits,
                      void* ws, size_t ws_bytes, void* stream, int flags);
 /* Gradients of the mean BCE loss (layout of the parameter vector) for the
@@ -282,8 +283,13 @@ int dlsh_mlp_train_step(void* mlp, int K, const float* X, int64_t B, const uint1
 int dlsh_mlp_train(void* mlp, int K, const float* X, int64_t N, const uint16_t* idx,
                    const uint8_t* nnz, int s, int epochs, int64_t batch, float lr,
                    float* loss_per_step, void* ws, size_t ws_bytes, void* stream, int flags);
-/* The m (2, 4, 8, 16 or 32) largest logits of every signal, largest first:
- * cand [N x m] uint16 atom indices. */
+/* The m (2, 4, 8, 16 or 32) largest logits of every signal, largest first,
+ * equal logits by smaller atom index: cand [N x m] uint16 atom indices (0xFFFF
+ * where K < m leaves a slot empty).  One fused kernel computes the three layers
+ * and the selection on chip, with the arithmetic of dlsh_mlp_forward, so cand
+ * is exactly the top m of that call's logits.  cand must be aligned to
+ * min(16, 2m) bytes and ws to 256 bytes (else DLSH_ERR_INVALID_ARG); the
+ * workspace size depends on K only. */
 size_t dlsh_mlp_propose_workspace_size(int K, int64_t N);
 int dlsh_mlp_propose(const void* mlp, int K, const float* X, int64_t N, int m,
                      uint16_t* cand, void* ws, size_t ws_bytes, void* stream, int flags);

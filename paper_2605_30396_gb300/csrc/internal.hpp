@@ -30,9 +30,14 @@ size_t mod_ws_bytes(int K, int s, int64_t N);
 
 // Support-proposal MLP (mlp.cu).
 size_t mlp_train_ws_bytes(int K, long long B);
-int mlp_forward_enqueue(const void* blob, int K, const float* X, long long B, void* ws,
-                        float** logits, cudaStream_t st);
-int mlp_topk_enqueue(const float* logits, long long rows, int K, int m, uint16_t* cand,
-                     cudaStream_t st);
+
+// Fused inference (propose.cu): the m highest-logit atoms of every signal, or
+// (infer_logits_enqueue) the logits themselves, N x K.  The workspace
+// (propose_ws_bytes, 256-byte aligned) holds the packed weights.
+size_t propose_ws_bytes(int K);
+int propose_enqueue(const void* mlp_blob, int K, const float* X, long long N, int m, uint16_t* cand,
+                    void* ws, uint32_t* status, cudaStream_t st);
+int infer_logits_enqueue(const void* mlp_blob, int K, const float* X, long long N, float* logits,
+                         void* ws, uint32_t* status, cudaStream_t st);
 
 }  // namespace dlsh

@@ -293,12 +293,10 @@ static int restricted_launch(const float* X, long long N, const float* D32p, con
 }
 
 namespace lrn {
-constexpr long long CHUNK = 65536;  // rows per MLP inference chunk
-
 struct Ws {
   uint32_t* status;
   void* enc;          // encoder workspace (prepared dictionary, Gram)
-  void* mlpws;        // MLP forward workspace for CHUNK rows
+  void* mlpws;        // proposal workspace (packed weights)
   uint16_t* cand;     // N x m
   uint16_t* iP;       // N x s   plain / fallback codes
   float* cP;
@@ -312,11 +310,10 @@ struct Ws {
 };
 inline size_t carve(void* base, int K, int s, long long N, Ws& w) {
   const long long m = 2 * s;
-  const long long rows = N < CHUNK ? (N > 0 ? N : 1) : CHUNK;
   Carver c(base);
   w.status = c.take<uint32_t>(64);
   w.enc = c.take<uint8_t>(encode_ws_bytes(K, s, 0));
-  w.mlpws = c.take<uint8_t>(mlp_train_ws_bytes(K, rows));
+  w.mlpws = c.take<uint8_t>(propose_ws_bytes(K));
   w.cand = c.take<uint16_t>(N * m + 1);
   w.iP = c.take<uint16_t>(N * s + 1);
   w.cP = c.take<float>(N * s + 1);
@@ -331,26 +328,13 @@ inline size_t carve(void* base, int K, int s, long long N, Ws& w) {
 }
 }  // namespace lrn
 
-int propose_enqueue(const void* mlp, int K, const float* X, long long N, int m, uint16_t* cand,
-                    void* mlpws, cudaStream_t st) {
-  for (long long r0 = 0; r0 < N; r0 += lrn::CHUNK) {
-    const long long rows = N - r0 < lrn::CHUNK ? N - r0 : lrn::CHUNK;
-    float* logits = nullptr;
-    int rc = mlp_forward_enqueue(mlp, K, X + r0 * DLSH_D, rows, mlpws, &logits, st);
-    if (rc) return rc;
-    rc = mlp_topk_enqueue(logits, rows, K, m, cand + r0 * m, st);
-    if (rc) return rc;
-  }
-  return DLSH_OK;
-}
-
 }  // namespace dlsh
 
 extern "C" {
 
 size_t dlsh_mlp_propose_workspace_size(int K, int64_t N) {
   if (K < 1 || K > DLSH_MAX_K || N < 0) return 0;
-  return dlsh::mlp_train_ws_bytes(K, N < dlsh::lrn::CHUNK ? (N > 0 ? N : 1) : dlsh::lrn::CHUNK);
+  return dlsh::propose_ws_bytes(K);
 }
 
 int dlsh_mlp_propose(const void* mlp, int K, const float* X, int64_t N, int m, uint16_t* cand,
@@ -364,9 +348,11 @@ int dlsh_mlp_propose(const void* mlp, int K, const float* X, int64_t N, int m, u
   int rc = check_workspace(ws, ws_bytes, dlsh_mlp_propose_workspace_size(K, N), "dlsh_mlp_propose");
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = propose_enqueue(mlp, K, X, N, m, cand, ws, st);
+  uint32_t* status = static_cast<uint32_t*>(ws);  // the workspace opens with its status word
+  DLSH_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st), "dlsh_mlp_propose: reset");
+  rc = propose_enqueue(mlp, K, X, N, m, cand, ws, status, st);
   if (rc) return rc;
-  return finish(st, nullptr, flags, "dlsh_mlp_propose");
+  return finish(st, status, flags, "dlsh_mlp_propose");
 }
 
 int dlsh_encode_restricted(const float* D, int K, int d, const float* X, int64_t N,
@@ -432,7 +418,7 @@ int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N,
   uint32_t* status = nullptr;
   rc = encode_prepare_only(D, K, s, 0, w.enc, st, &D32p, &G, &status);
   if (rc) return rc;
-  rc = propose_enqueue(mlp, K, X, N, m, w.cand, w.mlpws, st);
+  rc = propose_enqueue(mlp, K, X, N, m, w.cand, w.mlpws, status, st);
   if (rc) return rc;
   rc = restricted_launch(X, N, D32p, G, K, w.cand, m, s, eps, idx, coef, nnz, resid_sq, status, st);
   if (rc) return rc;

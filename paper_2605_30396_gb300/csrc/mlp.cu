@@ -13,7 +13,8 @@
 //                   +bias with GELU (stores the pre-activation for backward).
 //   small kernels   input normalisation, BCE-with-logits gradient and loss,
 //                   GELU backward, bias gradients, split-K reduction, Adam.
-//   topk_kernel     the m largest logits per signal (warp per signal).
+// Inference (the logits, or the m best atoms per signal) is one fused kernel
+// (propose.cu); the layer-by-layer forward here serves training.
 #include <cuda_bf16.h>
 #include <math.h>
 
@@ -22,6 +23,7 @@
 #include "common.cuh"
 #include "host.hpp"
 #include "internal.hpp"
+#include "mlp.cuh"
 
 namespace dlsh {
 namespace mlp {
@@ -54,12 +56,6 @@ struct GemmArgs {
   uint32_t* status;
   long long budget;
 };
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.f + erff(z * 0.70710678118654752f)) +
-         z * 0.39894228040143268f * expf(-0.5f * z * z);
-}
 
 // Stages rows [r0, r0+rows_tile) x k-range [k0, k0+GK) of X into the canonical
 // layout at `dst` (16-byte K-blocks: byte (kk/8) * rows_tile*16 + r*16 + (kk%8)*2).
@@ -202,7 +198,7 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmAr
       for (int r = 0; r < 32; ++r) {
         const int row = m0 + warp * 32 + r;
         if (row < g.M && col < g.N) {
-          const float z = stg[r * 33 + lane] + bcol;
+          const float z = add_bias(stg[r * 33 + lane], bcol);
           if (g.C)
             g.C[static_cast<long long>(blockIdx.z) * g.zstride + static_cast<long long>(row) * g.ldc + col] = z;
           if (g.epi == EPI_BIAS_GELU)
@@ -225,44 +221,6 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmAr
 namespace dlsh {
 namespace mlp {
 
-constexpr int HID = 256;    // hidden width
-constexpr int XIN = 64;     // input width (45 padded to a whole k-tile)
-
-// Parameter vector layout (FP32 masters; a BF16 mirror has the same offsets).
-struct Layout {
-  long long W1, b1, W2, b2, W3, b3, n;
-};
-__host__ __device__ inline Layout layout(int K) {
-  Layout L;
-  L.W1 = 0;
-  L.b1 = L.W1 + static_cast<long long>(HID) * XIN;
-  L.W2 = L.b1 + HID;
-  L.b2 = L.W2 + static_cast<long long>(HID) * HID;
-  L.W3 = L.b2 + HID;
-  L.b3 = L.W3 + static_cast<long long>(K) * HID;
-  L.n = L.b3 + K;
-  return L;
-}
-
-// Blob: P (FP32) | M1 (FP32) | M2 (FP32) | Pb (BF16) | step counter.
-struct Blob {
-  float* P;
-  float* m1;
-  float* m2;
-  __nv_bfloat16* Pb;
-  long long* step;
-};
-inline size_t carve_blob(void* base, int K, Blob& b) {
-  const Layout L = layout(K);
-  Carver c(base);
-  b.P = c.take<float>(L.n);
-  b.m1 = c.take<float>(L.n);
-  b.m2 = c.take<float>(L.n);
-  b.Pb = c.take<__nv_bfloat16>(L.n);
-  b.step = c.take<long long>(2);
-  return c.size();
-}
-
 // ---- input: xn = x / ||x|| (0 if x = 0), padded to 64 columns, BF16 ---------
 __global__ void normalize_kernel(const float* __restrict__ X, long long n, __nv_bfloat16* __restrict__ Xn) {
   const long long i = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -270,11 +228,10 @@ __global__ void normalize_kernel(const float* __restrict__ X, long long n, __nv_
   if (i >= n) return;
   const float x0 = X[i * DLSH_D + lane];
   const float x1 = lane < DLSH_D - 32 ? X[i * DLSH_D + 32 + lane] : 0.f;
-  float n2 = x0 * x0 + x1 * x1;
-  for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-  const float inv = n2 > 0.f ? rsqrtf(n2) : 0.f;
-  Xn[i * XIN + lane] = __float2bfloat16(x0 * inv);
-  Xn[i * XIN + 32 + lane] = __float2bfloat16(x1 * inv);
+  __nv_bfloat16 y0, y1;
+  normalise_pair(x0, x1, y0, y1);
+  Xn[i * XIN + lane] = y0;
+  Xn[i * XIN + 32 + lane] = y1;
 }
 
 // ---- BCE-with-logits gradient (mean over B*K) and per-row loss ----------------
@@ -386,75 +343,6 @@ __global__ void mirror_kernel(const float* __restrict__ P, __nv_bfloat16* __rest
   if (i < n) Pb[i] = __float2bfloat16(P[i]);
 }
 
-// ---- top-m logits per row (warp per row): each lane keeps its own top m of
-// the columns lane, lane+32, ...; m rounds of a warp arg-max merge them.  Order:
-// larger logit first, on ties the smaller atom index.
-__device__ __forceinline__ bool ranks_before(float a, int ja, float b, int jb) {
-  return a > b || (a == b && ja < jb);
-}
-template <int M>
-__global__ void topk_kernel(const float* __restrict__ Z, long long rows, int K,
-                            uint16_t* __restrict__ cand) {
-  const long long r = static_cast<long long>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (r >= rows) return;
-  float tv[M];
-  int tj[M];
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    tv[q] = -INFINITY;
-    tj[q] = 0x7fffffff;
-  }
-  const float* zr = Z + r * K;
-  // Pre-filter: tau0 = the smallest of the lanes' maxima.  At least 32 >= M
-  // values reach tau0 (one per lane), so every value of the top M does too;
-  // only values >= tau0 enter the lists (usually one to three per lane).
-  float lmax = -INFINITY;
-  for (int k = lane; k < K; k += 32) lmax = fmaxf(lmax, zr[k]);
-  float tau0 = lmax;
-  for (int o = 16; o > 0; o >>= 1) tau0 = fminf(tau0, __shfl_xor_sync(0xffffffffu, tau0, o));
-  if (K < 32) tau0 = -INFINITY;  // some lane holds no value: keep all
-  for (int k = lane; k < K; k += 32) {
-    float cv = zr[k];
-    int cj = k;
-    if (cv >= tau0 && ranks_before(cv, cj, tv[M - 1], tj[M - 1])) {
-#pragma unroll
-      for (int q = 0; q < M; ++q) {
-        if (ranks_before(cv, cj, tv[q], tj[q])) {
-          const float t1 = tv[q];
-          const int t2 = tj[q];
-          tv[q] = cv;
-          tj[q] = cj;
-          cv = t1;
-          cj = t2;
-        }
-      }
-    }
-  }
-  for (int q = 0; q < M; ++q) {
-    float bv = tv[0];
-    int bj = tj[0];
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-      if (ranks_before(ov, oj, bv, bj)) {
-        bv = ov;
-        bj = oj;
-      }
-    }
-    if (lane == 0) cand[r * M + q] = static_cast<uint16_t>(bj);
-    if (tj[0] == bj) {  // the owner pops its head
-#pragma unroll
-      for (int p = 0; p < M - 1; ++p) {
-        tv[p] = tv[p + 1];
-        tj[p] = tj[p + 1];
-      }
-      tv[M - 1] = -INFINITY;
-      tj[M - 1] = 0x7fffffff;
-    }
-  }
-}
-
 }  // namespace mlp
 }  // namespace dlsh
 
@@ -544,18 +432,17 @@ static size_t carve_t(void* base, int K, long long B, TWs& w) {
 static inline Mat rowmajor(const __nv_bfloat16* p, long long ld) { return Mat{p, ld, 1}; }
 static inline Mat transposed(const __nv_bfloat16* p, long long ld) { return Mat{p, 1, ld}; }
 
-// forward through the three layers: logits in w.Z3 (B x K)
-// keep_pre: also store the hidden pre-activations (needed by backward only).
-static int forward(const Blob& b, int K, const float* X, long long B, const TWs& w, cudaStream_t st,
-                   bool keep_pre = true) {
+// Training forward through the three layers: logits in w.Z3 (B x K), hidden
+// pre-activations in w.Z1 / w.Z2 for the backward pass.
+static int forward(const Blob& b, int K, const float* X, long long B, const TWs& w, cudaStream_t st) {
   const Layout L = layout(K);
   normalize_kernel<<<static_cast<int>((B + 7) / 8), 256, 0, st>>>(X, B, w.Xn);
   count_launches(1);
   int rc = gemm(rowmajor(w.Xn, XIN), rowmajor(b.Pb + L.W1, XIN), B, HID, XIN,
-                keep_pre ? w.Z1 : nullptr, HID, EPI_BIAS_GELU, b.P + L.b1, w.H1, HID, 1, 0,
+                w.Z1, HID, EPI_BIAS_GELU, b.P + L.b1, w.H1, HID, 1, 0,
                 w.status, st);
   if (rc) return rc;
-  rc = gemm(rowmajor(w.H1, HID), rowmajor(b.Pb + L.W2, HID), B, HID, HID, keep_pre ? w.Z2 : nullptr,
+  rc = gemm(rowmajor(w.H1, HID), rowmajor(b.Pb + L.W2, HID), B, HID, HID, w.Z2,
             HID, EPI_BIAS_GELU, b.P + L.b2, w.H2, HID, 1, 0, w.status, st);
   if (rc) return rc;
   return gemm(rowmajor(w.H2, HID), rowmajor(b.Pb + L.W3, HID), B, K, HID, w.Z3, K, EPI_BIAS,
@@ -641,33 +528,6 @@ size_t mlp_train_ws_bytes(int K, long long B) {
   return mlp::carve_t(nullptr, K, B, w);
 }
 
-// Used by the learned encoder: logits of B rows into `logits` (B x K) with a
-// training workspace sized for B.
-int mlp_forward_enqueue(const void* blob, int K, const float* X, long long B, void* ws,
-                        float** logits, cudaStream_t st) {
-  mlp::Blob b;
-  mlp::carve_blob(const_cast<void*>(blob), K, b);
-  mlp::TWs w;
-  mlp::carve_t(ws, K, B, w);
-  *logits = w.Z3;
-  return mlp::forward(b, K, X, B, w, st, /*keep_pre=*/false);
-}
-
-int mlp_topk_enqueue(const float* logits, long long rows, int K, int m, uint16_t* cand,
-                     cudaStream_t st) {
-  const int blocks = static_cast<int>((rows + 7) / 8);
-  switch (m) {
-    case 2: mlp::topk_kernel<2><<<blocks, 256, 0, st>>>(logits, rows, K, cand); break;
-    case 4: mlp::topk_kernel<4><<<blocks, 256, 0, st>>>(logits, rows, K, cand); break;
-    case 8: mlp::topk_kernel<8><<<blocks, 256, 0, st>>>(logits, rows, K, cand); break;
-    case 16: mlp::topk_kernel<16><<<blocks, 256, 0, st>>>(logits, rows, K, cand); break;
-    case 32: mlp::topk_kernel<32><<<blocks, 256, 0, st>>>(logits, rows, K, cand); break;
-    default: return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mlp_propose: m must be 2, 4, 8, 16 or 32");
-  }
-  count_launches(1);
-  return check_launch("dlsh_mlp: topk");
-}
-
 }  // namespace dlsh
 
 extern "C" {
@@ -682,7 +542,7 @@ size_t dlsh_mlp_size(int K) {
 
 size_t dlsh_mlp_workspace_size(int K, int64_t B) {
   if (K < 1 || K > DLSH_MAX_K || B < 1) return 0;
-  return dlsh::mlp_train_ws_bytes(K, B);
+  return std::max(dlsh::mlp_train_ws_bytes(K, B), dlsh::propose_ws_bytes(K));
 }
 
 int dlsh_mlp_init(void* mlp, int K, const float* params, void* stream, int flags) {
@@ -724,7 +584,7 @@ static int mlp_common_checks(const char* call, const void* mlp, int K, const flo
   using namespace dlsh;
   if (!mlp || K < 1 || K > DLSH_MAX_K) return set_error(DLSH_ERR_INVALID_ARG, "%s: bad blob or K", call);
   if (B < 1 || !X) return set_error(DLSH_ERR_INVALID_ARG, "%s: bad batch", call);
-  return check_workspace(ws, ws_bytes, mlp_train_ws_bytes(K, B), call);
+  return check_workspace(ws, ws_bytes, dlsh_mlp_workspace_size(K, B), call);
 }
 
 int dlsh_mlp_forward(const void* mlp, int K, const float* X, int64_t B, float* logits, void* ws,
@@ -735,15 +595,11 @@ int dlsh_mlp_forward(const void* mlp, int K, const float* X, int64_t B, float* l
   if (rc) return rc;
   if (!logits) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_mlp_forward: NULL logits");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  mlp::TWs w;
-  mlp::carve_t(ws, K, B, w);
-  DLSH_CUDA_TRY(cudaMemsetAsync(w.status, 0, 4, st), "dlsh_mlp_forward: reset");
-  float* z = nullptr;
-  rc = mlp_forward_enqueue(mlp, K, X, B, ws, &z, st);
+  uint32_t* status = static_cast<uint32_t*>(ws);  // both workspace layouts open with it
+  DLSH_CUDA_TRY(cudaMemsetAsync(status, 0, 4, st), "dlsh_mlp_forward: reset");
+  rc = infer_logits_enqueue(mlp, K, X, B, logits, ws, status, st);
   if (rc) return rc;
-  DLSH_CUDA_TRY(cudaMemcpyAsync(logits, z, sizeof(float) * B * K, cudaMemcpyDeviceToDevice, st),
-                "dlsh_mlp_forward: copy");
-  return finish(st, w.status, flags, "dlsh_mlp_forward");
+  return finish(st, status, flags, "dlsh_mlp_forward");
 }
 
 int dlsh_mlp_gradients(const void* mlp, int K, const float* X, int64_t B, const uint16_t* idx,

@@ -102,6 +102,41 @@ def test_propose_is_top_2s_of_the_logits(lib):
         np.testing.assert_array_equal(cand, P.top_candidates(z, m))
 
 
+@pytest.mark.parametrize("K,N,m", [(300, 1000, 2), (1000, 777, 4), (256, 129, 16), (64, 1, 32),
+                                   (8, 300, 16), (4096, 500, 16)])
+def test_fused_propose_ragged_shapes(lib, K, N, m):
+    """Blocks of 256 atoms with a ragged last block, tiles of 128 signals with a
+    ragged last tile, every m; K < m leaves the trailing slots empty (0xFFFF)."""
+    net = lib.MLP(K, _params(K, 40 + K))
+    X = torch.from_numpy(synth.signals(N, synth.hidden_dictionary(max(K, 16), 41), 4, 42))
+    z = net.forward(X).cpu().numpy()
+    cand = net.propose(X, m).cpu().numpy().view(np.uint16).astype(np.int64)
+    ref = P.top_candidates(z, min(m, K))
+    np.testing.assert_array_equal(cand[:, :min(m, K)], ref)
+    if K < m:
+        assert (cand[:, K:] == 0xFFFF).all()
+
+
+def test_fused_propose_ties_and_many_tiles(lib):
+    """Exactly tied logits (duplicated W3 rows and biases, in both halves of a
+    block and across blocks) go to the smaller index; 60,000 signals give every
+    CTA several tiles."""
+    K, N, m = 640, 60_000, 16
+    p = _params(K, 50)
+    for a, b in ((5, 300), (130, 2), (257, 600), (129, 128), (511, 7)):
+        p["W3"][b] = p["W3"][a]
+        p["b3"][b] = p["b3"][a]
+    net = lib.MLP(K, p)
+    X = torch.from_numpy(synth.signals(N, synth.hidden_dictionary(K, 51), 4, 52)).cuda()
+    z = net.forward(X).cpu().numpy()
+    cand = net.propose(X, m).cpu().numpy().view(np.uint16).astype(np.int64)
+    ref = P.top_candidates(z, m)
+    np.testing.assert_array_equal(cand, ref)
+    # the duplicated pairs really tie and really reach the top m somewhere
+    both = np.isin(ref, [5, 300]).sum(axis=1) == 2
+    assert both.any()
+
+
 @pytest.mark.parametrize("m,s,K", [(16, 8, 256), (8, 4, 1024), (32, 16, 512), (32, 8, 32)])
 def test_restricted_omp_matches_oracle(lib, m, s, K):
     N = 2000
