@@ -18,11 +18,13 @@
 //                       since GB300's FP64 units are slow); slices are added
 //                       in a fixed order in FP64
 //   5. mixed-precision solve of (G + lambda I) D~^T = (B + lambda D_old)^T:
-//      Jacobi scaling S = diag^-1/2 (unit diagonal), FP32 blocked Cholesky of
-//      S (G + lambda I) S (diagonal factor with its inverse, panel, trailing
-//      update), FP32 triangular solves, and iterative refinement with the
-//      residual of the scaled system computed in FP64 (GB300's FP64 rate is
-//      a small fraction of its FP32 rate, so FP64 is spent only there)
+//      Jacobi scaling S = diag^-1/2 (unit diagonal); one cooperative kernel
+//      factors S (G + lambda I) S = L L^T in FP32 and inverts L on the way
+//      (right-looking steps over [A | I], a grid barrier between phases);
+//      each FP32 solve is then two triangular products with W = L^-1, and
+//      iterative refinement uses the residual of the scaled system computed
+//      in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate, so
+//      FP64 is spent only there)
 //   6. normalise, then refill unused atoms (argmax passes over resid_sq)
 #include <math.h>
 
@@ -53,7 +55,9 @@ struct Ws {
   double* lam;     // [0] lambda
   double* dsc;     // K: Jacobi scale 1 / sqrt(M_jj)
   float* A32;      // K x K: S M S, then its FP32 Cholesky factor (lower)
-  float* Linv32;   // nblk x 32 x 32 inverses of the factor's diagonal blocks
+  float* W32;      // K x K: L^-1 (lower)
+  float* Y32;      // K x RW: W r, between the two triangular products
+  unsigned* gbar;  // grid barrier of the factorisation: arrivals, generation
   double* Zs;      // K x RW: S Z
   double* Xs;      // K x RW: solution of the scaled system (FP64 accumulation)
   float* R32;      // K x RW: current residual of the scaled system
@@ -83,7 +87,6 @@ inline int64_t max_segments(int K, int s, int64_t N) {
 static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   Carver c(base);
   const int64_t T = (N + TS - 1) / TS > 0 ? (N + TS - 1) / TS : 1;
-  const int nblk = (K + NB - 1) / NB;
   w.status = c.take<uint32_t>(64);
   w.cnt = c.take<int>(static_cast<size_t>(K) * T);
   w.off = c.take<int>(static_cast<size_t>(K) * T);
@@ -95,7 +98,9 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.lam = c.take<double>(4);
   w.dsc = c.take<double>(K);
   w.A32 = c.take<float>(static_cast<size_t>(K) * K);
-  w.Linv32 = c.take<float>(static_cast<size_t>(nblk) * NB * NB);
+  w.W32 = c.take<float>(static_cast<size_t>(K) * K);
+  w.Y32 = c.take<float>(static_cast<size_t>(K) * RW);
+  w.gbar = c.take<unsigned>(64);
   w.Zs = c.take<double>(static_cast<size_t>(K) * RW);
   w.Xs = c.take<double>(static_cast<size_t>(K) * RW);
   w.R32 = c.take<float>(static_cast<size_t>(K) * RW);
@@ -578,22 +583,72 @@ __global__ void scale_kernel(const double* __restrict__ M, const double* __restr
   }
 }
 
-// ---- 5c. FP32 blocked Cholesky of A (lower, in place, row-major A[r*K + c]) ----
-// Factor and invert one 32 x 32 diagonal block in one warp: lane r holds row
-// r of the block in registers; pivots and L entries move by shuffles.  Rows
-// past the matrix end are padded with the identity and not written back.
-__global__ void __launch_bounds__(32) potrf_diag_kernel(float* __restrict__ M, int K, int k0,
-                                                        float* __restrict__ Linv,
-                                                        uint32_t* status) {
+// ---- 5c. FP32 Cholesky of A and the inverse of its factor, W = L^-1 ----------
+// One cooperative launch (every CTA resident) walks the 32-column steps of a
+// right-looking factorisation of the augmented matrix [A | I]:
+//   phase 1  each CTA factors the diagonal block in one warp (L_kk and its
+//            inverse); the grid computes the panel L_ik = A_ik L_kk^-T (i > k)
+//            and the rows W_k = L_kk^-1 R_k of the inverse
+//   phase 2  CTA 0 stores L_kk; trailing update A_ij -= L_ik L_jk^T (j <= i)
+//            and right-hand sides R_i -= L_ik W_k (i > k), on 64 x 64 tiles
+//            spread over the CTAs
+// with a grid barrier after each phase.  After the last step A holds L and W
+// holds L^-1 (lower; its upper triangle stays exactly zero), so every later
+// solve is two triangular products, parallel over the whole matrix.
+constexpr int CH_T = 256;   // threads per CTA
+constexpr int CH_TILE = 64;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
+// the generation.  The wait is bounded: on timeout it records ST_TIMEOUT and
+// returns false, and the caller leaves the kernel.
+__device__ bool grid_barrier(unsigned* bar, long long budget, uint32_t* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(bar + 1) == g) {
+        if (clock64() - t0 > budget) {
+          flag_status(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+// One warp factors the nb x nb diagonal block at k0 (rows past K padded with
+// the identity): L into Ls, L^-1 into Li (both lower, [32][33]).  Lane r holds
+// row r in registers; pivots and entries move by shuffles.
+__device__ void factor_diag(const float* __restrict__ A, int K, int k0, int nb, float (*Ls)[NB + 1],
+                            float (*Li)[NB + 1], bool& bad) {
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x;
-  const int nb = K - k0 < NB ? K - k0 : NB;
+  const int lane = threadIdx.x & 31;
   float a[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k)
-    a[k] = (lane < nb && k < nb) ? (k <= lane ? M[static_cast<size_t>(k0 + lane) * K + k0 + k] : 0.f)
+    a[k] = (lane < nb && k < nb) ? (k <= lane ? A[static_cast<size_t>(k0 + lane) * K + k0 + k] : 0.f)
                                  : (k == lane ? 1.f : 0.f);
-  bool bad = false;
+  bad = false;
 #pragma unroll
   for (int c = 0; c < NB; ++c) {
     float d = __shfl_sync(FULL, a[c], c);
@@ -611,12 +666,8 @@ __global__ void __launch_bounds__(32) potrf_diag_kernel(float* __restrict__ M, i
       if (lane >= k) a[k] = fmaf(-a[c], lkc, a[k]);
     }
   }
-  if (bad && lane == 0) flag_status(status, ST_BAD_INPUT);
-  if (lane < nb) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k)
-      if (k < nb) M[static_cast<size_t>(k0 + lane) * K + k0 + k] = k <= lane ? a[k] : 0.f;
-  }
+  for (int k = 0; k < NB; ++k) Ls[lane][k] = k <= lane ? a[k] : 0.f;
   // X = L^-1, one column per lane: X[r][c] = (delta_rc - sum_{k<r} L[r][k] X[k][c]) / L[r][r]
   float x[NB];
 #pragma unroll
@@ -627,200 +678,193 @@ __global__ void __launch_bounds__(32) potrf_diag_kernel(float* __restrict__ M, i
     for (int k = 0; k < r; ++k) acc = fmaf(-__shfl_sync(FULL, a[k], r), x[k], acc);
     x[r] = r >= lane ? acc * irr : 0.f;
   }
-  float* out = Linv + static_cast<size_t>(k0 / NB) * NB * NB;
 #pragma unroll
-  for (int r = 0; r < NB; ++r) out[r * NB + lane] = (r < nb && lane < nb) ? x[r] : 0.f;
+  for (int r = 0; r < NB; ++r) Li[r][lane] = x[r];
 }
 
-// Rows below the diagonal block: L21 = A21 L11^-T = A21 (L11^-1)^T with the
-// block inverse from potrf_diag_kernel, one thread per row.
-__global__ void trsm_panel_kernel(float* __restrict__ M, int K, int k0,
-                                  const float* __restrict__ Linv) {
-  __shared__ float Li[NB][NB + 1];
-  const float* inv = Linv + static_cast<size_t>(k0 / NB) * NB * NB;
-  for (int f = threadIdx.x; f < NB * NB; f += blockDim.x) Li[f / NB][f % NB] = inv[f];
-  __syncthreads();
-  const int nb = K - k0 < NB ? K - k0 : NB;
-  const int row = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= K) return;
-  float* mr = M + static_cast<size_t>(row) * K + k0;
-  float v[NB];
-#pragma unroll
-  for (int c = 0; c < NB; ++c) v[c] = c < nb ? mr[c] : 0.f;
-#pragma unroll
-  for (int c = 0; c < NB; ++c) {
-    if (c < nb) {
-      float acc = 0.f;
-#pragma unroll
-      for (int q = 0; q <= c; ++q) acc = fmaf(v[q], Li[c][q], acc);
-      mr[c] = acc;
-    }
-  }
-}
-
-// Trailing update A22 -= L21 L21^T on lower 64 x 64 tiles (4 x 4 per thread).
-__global__ void __launch_bounds__(256) syrk_kernel(float* __restrict__ M, int K, int k0) {
-  const int k1 = k0 + NB;
-  const int bi = blockIdx.y, bj = blockIdx.x;
-  if (bj > bi) return;
-  __shared__ float Li[NB][64 + 1];
-  __shared__ float Lj[NB][64 + 1];
-  const int r0 = k1 + bi * 64, c0 = k1 + bj * 64;
-  for (int f = threadIdx.x; f < 64 * NB; f += 256) {
+// C[64 x 64 tile] -= P Q^T over 32 k: P rows from pload(r, q), Q rows from
+// qload(c, q), both staged transposed; 4 x 4 outputs per thread, applied by
+// cupd(r, c, value).
+template <class PF, class QF, class CF>
+__device__ __forceinline__ void tile_update(float (*Ps)[CH_TILE + 1], float (*Qs)[CH_TILE + 1], PF pload,
+                                            QF qload, CF cupd) {
+  for (int f = threadIdx.x; f < CH_TILE * NB; f += CH_T) {
     const int r = f / NB, q = f % NB;
-    Li[q][r] = (r0 + r < K) ? M[static_cast<size_t>(r0 + r) * K + k0 + q] : 0.f;
-    Lj[q][r] = (c0 + r < K) ? M[static_cast<size_t>(c0 + r) * K + k0 + q] : 0.f;
+    Ps[q][r] = pload(r, q);
+    Qs[q][r] = qload(r, q);
   }
   __syncthreads();
   const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // rows tr + 16i, cols tc + 16j
   float acc[4][4] = {};
 #pragma unroll 8
   for (int q = 0; q < NB; ++q) {
-    float li[4], lj[4];
+    float pi[4], qj[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) li[i] = Li[q][tr + 16 * i];
+    for (int i = 0; i < 4; ++i) pi[i] = Ps[q][tr + 16 * i];
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) lj[jj] = Lj[q][tc + 16 * jj];
+    for (int j = 0; j < 4; ++j) qj[j] = Qs[q][tc + 16 * j];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fmaf(li[i], lj[jj], acc[i][jj]);
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(pi[i], qj[j], acc[i][j]);
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int gr = r0 + tr + 16 * i, gc = c0 + tc + 16 * jj;
-      if (gr < K && gc < K && gc <= gr) M[static_cast<size_t>(gr) * K + gc] -= acc[i][jj];
-    }
+    for (int j = 0; j < 4; ++j) cupd(tr + 16 * i, tc + 16 * j, acc[i][j]);
+  __syncthreads();  // the staging tiles are reused by the next tile
 }
 
-// ---- 5d. FP32 solve (L L^T) c = r for one right-hand side per CTA, then
-// X += c in FP64.  Forward, per 32-row block B: the panel L[B][0, k0) is
-// staged in shared memory with cp.async, u = r_B - L[B][<B] y, y_B = Linv_B u.
-// Backward, last block first: the panel L[>B][B] (32 columns of every later
-// row) is staged, v = y_B - L[>B][B]^T x, x_B = Linv_B^T v.  256 threads.
-constexpr int SV_T = 256;
-
-// Copies n floats from global to shared memory (16-byte pieces when both
-// ends allow it), cooperatively over the CTA.
-__device__ __forceinline__ void stage_row(float* dst, const float* src, int n, int tid, int nthreads) {
-  if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 &&
-      (n & 3) == 0) {
-    for (int q = tid; q < n / 4; q += nthreads)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst + 4 * q)),
-                   "l"(src + 4 * q)
-                   : "memory");
-  } else {
-    for (int q = tid; q < n; q += nthreads) cp_async4(dst + q, src + q);
-  }
-}
-
-constexpr int PW = 1024;  // panel chunk: columns (forward) or rows (backward)
-
-__global__ void __launch_bounds__(SV_T) solve32_kernel(const float* __restrict__ L,
-                                                       const float* __restrict__ Linv, int K,
-                                                       const float* __restrict__ R32,
-                                                       double* __restrict__ Xs) {
-  extern __shared__ __align__(16) float sv[];
-  float* pan = sv;                      // 32 x PW (forward) / PW x 32 (backward)
-  float* y = pan + NB * PW;             // K: forward result, then the solution
-  float* part = y + ((K + 3) & ~3);     // 8 x 32 partial sums
-  float* u = part + 8 * 32;             // 32
-  const int col = blockIdx.x;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+__global__ void __launch_bounds__(CH_T) chol_inv_kernel(float* __restrict__ A, float* __restrict__ W, int K,
+                                                        unsigned* __restrict__ bar,
+                                                        uint32_t* __restrict__ status, long long budget) {
+  __shared__ float Ls[NB][NB + 1];
+  __shared__ float Li[NB][NB + 1];
+  __shared__ float Ps[NB][CH_TILE + 1];
+  __shared__ float Qs[NB][CH_TILE + 1];
+  const int tid = threadIdx.x;
+  const long long gt = static_cast<long long>(blockIdx.x) * CH_T + tid;
+  const long long gstride = static_cast<long long>(gridDim.x) * CH_T;
+  // W = I (the augmented right-hand sides)
+  for (long long e = gt; e < static_cast<long long>(K) * K; e += gstride)
+    W[e] = (e / K == e % K) ? 1.f : 0.f;
+  if (!grid_barrier(bar, budget, status)) return;
   const int nblk = (K + NB - 1) / NB;
-  // forward
-  for (int b = 0; b < nblk; ++b) {
-    const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};  // rows warp * 4 + rr
-    for (int c0 = 0; c0 < k0; c0 += PW) {
-      const int cw = k0 - c0 < PW ? k0 - c0 : PW;
-      __syncthreads();  // the previous chunk has been consumed
-      for (int r = 0; r < nb; ++r)
-        stage_row(pan + static_cast<size_t>(r) * cw, L + static_cast<size_t>(k0 + r) * K + c0, cw, tid, SV_T);
-      cp_async_commit();
-      cp_async_wait<0>();
-      __syncthreads();
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int k0 = kb * NB, nb = K - k0 < NB ? K - k0 : NB, k1 = k0 + nb;
+    // ---- phase 1 (the diagonal block is read by every CTA: nobody writes it here)
+    if (tid < 32) {
+      bool bad = false;
+      factor_diag(A, K, k0, nb, Ls, Li, bad);
+      if (bad && tid == 0 && blockIdx.x == 0) flag_status(status, ST_BAD_INPUT);
+    }
+    __syncthreads();
+    // panel rows: L_ik = A_ik L_kk^-T
+    for (long long i = k1 + gt; i < K; i += gstride) {
+      float* ar = A + static_cast<size_t>(i) * K + k0;
+      float v[NB];
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        const int r = warp * 4 + rr;
-        if (r < nb) {
-          const float* pr = pan + static_cast<size_t>(r) * cw;
-          float a0 = 0.f, a1 = 0.f;
-          int k = lane;
-          for (; k + 32 < cw; k += 64) {
-            a0 = fmaf(pr[k], y[c0 + k], a0);
-            a1 = fmaf(pr[k + 32], y[c0 + k + 32], a1);
-          }
-          if (k < cw) a0 = fmaf(pr[k], y[c0 + k], a0);
-          acc[rr] += a0 + a1;
+      for (int q = 0; q < NB; ++q) v[q] = q < nb ? ar[q] : 0.f;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nb) {
+          float acc = 0.f;
+#pragma unroll
+          for (int q = 0; q <= c; ++q) acc = fmaf(v[q], Li[c][q], acc);
+          ar[c] = acc;
         }
       }
     }
+    // rows k0..k1 of W: W_k = L_kk^-1 R_k, one column per thread (columns < k1)
+    for (long long c = gt; c < k1; c += gstride) {
+      float r[NB];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr) {
-      const int r = warp * 4 + rr;
-      float v = acc[rr];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) u[r] = r < nb ? R32[static_cast<size_t>(k0 + r) * RW + col] - v : 0.f;
+      for (int p = 0; p < NB; ++p) r[p] = p < nb ? W[static_cast<size_t>(k0 + p) * K + c] : 0.f;
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nb) {
+          float acc = 0.f;
+#pragma unroll
+          for (int p = 0; p <= q; ++p) acc = fmaf(Li[q][p], r[p], acc);
+          W[static_cast<size_t>(k0 + q) * K + c] = acc;
+        }
+      }
     }
-    __syncthreads();
-    if (warp == 0) {
-      const float* inv = Linv + static_cast<size_t>(b) * NB * NB;
-      float a = 0.f;
-#pragma unroll 8
-      for (int k = 0; k < NB; ++k) a = fmaf(inv[lane * NB + k], u[k], a);
-      if (lane < nb) y[k0 + lane] = a;
+    if (!grid_barrier(bar, budget, status)) return;
+    // ---- phase 2: the factored diagonal block, the trailing update of A
+    // (lower tiles) and of the right-hand sides
+    if (blockIdx.x == 0 && tid < nb)
+      for (int k = 0; k < nb; ++k) A[static_cast<size_t>(k0 + tid) * K + k0 + k] = Ls[tid][k];
+    const int rest = K - k1;  // > 0 only when nb = NB (a partial block is the last)
+    if (rest > 0) {
+      const int T1 = (rest + CH_TILE - 1) / CH_TILE;
+      const int T2 = (k1 + CH_TILE - 1) / CH_TILE;
+      const int nsyrk = T1 * (T1 + 1) / 2;
+      const int total = nsyrk + T1 * T2;
+      for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        if (t < nsyrk) {
+          int bi = static_cast<int>((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+          while (bi * (bi + 1) / 2 > t) --bi;
+          while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+          const int bj = t - bi * (bi + 1) / 2;
+          const int r0 = k1 + bi * CH_TILE, c0 = k1 + bj * CH_TILE;
+          tile_update(
+              Ps, Qs,
+              [&](int r, int q) { return r0 + r < K ? A[static_cast<size_t>(r0 + r) * K + k0 + q] : 0.f; },
+              [&](int r, int q) { return c0 + r < K ? A[static_cast<size_t>(c0 + r) * K + k0 + q] : 0.f; },
+              [&](int r, int c, float v) {
+                const int gr = r0 + r, gc = c0 + c;
+                if (gr < K && gc <= gr) A[static_cast<size_t>(gr) * K + gc] -= v;
+              });
+        } else {
+          const int u = t - nsyrk;
+          const int bi = u / T2, bc = u % T2;
+          const int r0 = k1 + bi * CH_TILE, c0 = bc * CH_TILE;
+          tile_update(
+              Ps, Qs,
+              [&](int r, int q) { return r0 + r < K ? A[static_cast<size_t>(r0 + r) * K + k0 + q] : 0.f; },
+              [&](int c, int q) {
+                return (c0 + c < k1 && q < nb) ? W[static_cast<size_t>(k0 + q) * K + c0 + c] : 0.f;
+              },
+              [&](int r, int c, float v) {
+                const int gr = r0 + r, gc = c0 + c;
+                if (gr < K && gc < k1) W[static_cast<size_t>(gr) * K + gc] -= v;
+              });
+        }
+      }
     }
-    __syncthreads();
+    if (!grid_barrier(bar, budget, status)) return;
   }
-  // backward (y is overwritten by x block by block, last block first)
-  for (int b = nblk - 1; b >= 0; --b) {
-    const int k0 = b * NB, nb = K - k0 < NB ? K - k0 : NB;
-    const int k1 = k0 + NB, rest = K > k1 ? K - k1 : 0;
-    float acc = 0.f;
-    for (int q0 = 0; q0 < rest; q0 += PW) {
-      const int qw = rest - q0 < PW ? rest - q0 : PW;
-      __syncthreads();
-      // 32 columns of qw rows: 16-byte pieces when the rows allow it (K % 4 == 0)
-      const float* src0 = L + static_cast<size_t>(k1 + q0) * K + k0;
-      if ((K & 3) == 0 && (reinterpret_cast<uintptr_t>(src0) & 15u) == 0) {
-        for (int f = tid; f < qw * (NB / 4); f += SV_T) {
-          const int k = f >> 3, q = f & 7;
-          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(pan + k * NB + 4 * q)),
-                       "l"(src0 + static_cast<size_t>(k) * K + 4 * q)
-                       : "memory");
-        }
-      } else {
-        for (int f = tid; f < qw * NB; f += SV_T) {
-          const int k = f >> 5, q = f & 31;
-          cp_async4(pan + k * NB + q, src0 + static_cast<size_t>(k) * K + q);
-        }
-      }
-      cp_async_commit();
-      cp_async_wait<0>();
-      __syncthreads();
-      for (int k = warp; k < qw; k += 8)
-        acc = fmaf(pan[static_cast<size_t>(k) * NB + lane], y[k1 + q0 + k], acc);
-    }
-    part[warp * 32 + lane] = acc;
-    __syncthreads();
-    if (warp == 0) {
+}
+
+// ---- 5d. FP32 solve of (L L^T) c = r with W = L^-1: y = W r, then c = W^T y,
+// and X += c in FP64.  16 output rows x 48 columns per CTA; k in chunks of 32.
+constexpr int TR_ROWS = 16;
+template <bool TRANS>
+__global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, int K,
+                                                   const float* __restrict__ in, float* __restrict__ out,
+                                                   double* __restrict__ Xs) {
+  __shared__ float Wt[32][TR_ROWS + 1];
+  __shared__ float In[32][RW];
+  const int i0 = blockIdx.x * TR_ROWS;
+  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // row tr, columns tc + 16 {0, 1, 2}
+  float acc[3] = {0.f, 0.f, 0.f};
+  // W lower: y_i uses j <= i (j < i0 + 16); W^T: c_j uses i >= j (i >= i0)
+  const int kb = TRANS ? i0 : 0;
+  const int ke = TRANS ? K : (i0 + TR_ROWS < K ? i0 + TR_ROWS : K);
+  for (int k0 = kb; k0 < ke; k0 += 32) {
+    for (int f = threadIdx.x; f < 32 * TR_ROWS; f += 256) {
+      const int q = f / TR_ROWS, r = f % TR_ROWS;
       float v = 0.f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) v += part[q * 32 + lane];
-      u[lane] = lane < nb ? y[k0 + lane] - v : 0.f;
-      __syncwarp();
-      const float* inv = Linv + static_cast<size_t>(b) * NB * NB;
-      float xr = 0.f;
+      if (k0 + q < K && i0 + r < K)
+        v = TRANS ? W[static_cast<size_t>(k0 + q) * K + i0 + r] : W[static_cast<size_t>(i0 + r) * K + k0 + q];
+      Wt[q][r] = v;
+    }
+    for (int f = threadIdx.x; f < 32 * RW; f += 256) {
+      const int q = f / RW, c = f % RW;
+      In[q][c] = k0 + q < K ? in[static_cast<size_t>(k0 + q) * RW + c] : 0.f;
+    }
+    __syncthreads();
 #pragma unroll 8
-      for (int k = 0; k < NB; ++k) xr = fmaf(inv[k * NB + lane], u[k], xr);
-      if (lane < nb) y[k0 + lane] = xr;
+    for (int q = 0; q < 32; ++q) {
+      const float w = Wt[q][tr];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) acc[u] = fmaf(w, In[q][tc + 16 * u], acc[u]);
     }
     __syncthreads();
   }
-  for (int j = tid; j < K; j += SV_T) Xs[static_cast<size_t>(j) * RW + col] += static_cast<double>(y[j]);
+  const int i = i0 + tr;
+  if (i < K) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int c = tc + 16 * u;
+      if (TRANS) {
+        if (c < DLSH_D) Xs[static_cast<size_t>(i) * RW + c] += static_cast<double>(acc[u]);
+      } else {
+        out[static_cast<size_t>(i) * RW + c] = acc[u];
+      }
+    }
+  }
 }
 
 // ---- 5e. FP64 residual of the scaled system: R = Zs - (S M S) X, as FP32 -----
@@ -1032,35 +1076,41 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   launches += 4;
   // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
   // kRefine FP32 solves with FP64 residuals in between
-  const int nblk = (K + NB - 1) / NB;
   scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
   ++launches;
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int k0 = kb * NB;
-    potrf_diag_kernel<<<1, 32, 0, st>>>(w.A32, K, k0, w.Linv32, w.status);
-    ++launches;
-    const int rest = K - k0 - NB;
-    if (rest > 0) {
-      trsm_panel_kernel<<<(rest + 127) / 128, 128, 0, st>>>(w.A32, K, k0, w.Linv32);
-      const int tiles = (rest + 63) / 64;
-      syrk_kernel<<<dim3(tiles, tiles), 256, 0, st>>>(w.A32, K, k0);
-      launches += 2;
+  {
+    static int coop_grid = 0;
+    if (coop_grid == 0) {
+      int per_sm = 0;
+      DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_kernel, CH_T, 0),
+                    "dlsh_mod_update: occupancy");
+      int sms = device_sm_count();
+      if (sms <= 0) sms = 1;
+      if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_mod_update: factorisation kernel does not fit");
+      coop_grid = sms * (per_sm < 2 ? per_sm : 2);
     }
+    DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_mod_update: barrier");
+    float* A32 = w.A32;
+    float* W32 = w.W32;
+    int Kk = K;
+    unsigned* gb = w.gbar;
+    uint32_t* stw = w.status;
+    long long budget = kWaitBudget;
+    void* args[] = {&A32, &W32, &Kk, &gb, &stw, &budget};
+    DLSH_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(chol_inv_kernel), dim3(coop_grid),
+                                              dim3(CH_T), args, 0, st),
+                  "dlsh_mod_update: factorisation");
+    ++launches;
   }
-  const size_t sv_smem =
-      (static_cast<size_t>(NB) * PW + ((K + 3) & ~3) + 8 * 32 + 32) * sizeof(float);
-  if (sv_smem > static_cast<size_t>(SMEM_LIMIT))
-    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_mod_update: K=%d too large for the solve", K);
-  DLSH_CUDA_TRY(cudaFuncSetAttribute(solve32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     static_cast<int>(sv_smem)),
-                "dlsh_mod_update: attribute");
+  const int tr_grid = (K + TR_ROWS - 1) / TR_ROWS;
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
       residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, 192, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
       ++launches;
     }
-    solve32_kernel<<<DLSH_D, SV_T, sv_smem, st>>>(w.A32, w.Linv32, K, w.R32, w.Xs);
-    ++launches;
+    trmm_kernel<false><<<tr_grid, 256, 0, st>>>(w.W32, K, w.R32, w.Y32, nullptr);
+    trmm_kernel<true><<<tr_grid, 256, 0, st>>>(w.W32, K, w.Y32, nullptr, w.Xs);
+    launches += 2;
   }
   unscale_kernel<<<static_cast<int>((static_cast<int64_t>(K) * RW + 255) / 256), 256, 0, st>>>(
       w.dsc, w.Xs, K, w.Xb);
