@@ -638,12 +638,15 @@ __device__ bool grid_barrier(unsigned* bar, long long budget, uint32_t* status) 
 
 // One warp factors the nb x nb diagonal block at k0 (rows past K padded with
 // the identity): L into Ls, L^-1 into Li (both lower, [32][33]).  Lane r holds
-// row r in registers; pivots and entries move by shuffles.
+// row r in registers; pivots and entries move by shuffles.  Every loop is
+// unrolled over the full block so that the rows stay in registers, and the
+// pivots use the hardware reciprocal square root: the FP64 refinement of the
+// solve absorbs its last-bit error.
 __device__ void factor_diag(const float* __restrict__ A, int K, int k0, int nb, float (*Ls)[NB + 1],
                             float (*Li)[NB + 1], bool& bad) {
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  float a[NB];
+  float a[NB], il[NB];
 #pragma unroll
   for (int k = 0; k < NB; ++k)
     a[k] = (lane < nb && k < nb) ? (k <= lane ? A[static_cast<size_t>(k0 + lane) * K + k0 + k] : 0.f)
@@ -656,14 +659,15 @@ __device__ void factor_diag(const float* __restrict__ A, int K, int k0, int nb, 
       bad = true;
       d = 1e-30f;
     }
-    const float l = sqrtf(d);
-    const float il = 1.f / l;
-    if (lane == c) a[c] = l;
-    else if (lane > c) a[c] *= il;  // L[lane][c]
+    const float r = rsqrtf(d);
+    il[c] = r;  // 1 / L[c][c]
+    a[c] = lane == c ? d * r : (lane > c ? a[c] * r : a[c]);  // L[lane][c]
 #pragma unroll
-    for (int k = c + 1; k < NB; ++k) {
-      const float lkc = __shfl_sync(FULL, a[c], k);  // L[k][c]
-      if (lane >= k) a[k] = fmaf(-a[c], lkc, a[k]);
+    for (int k = 0; k < NB; ++k) {
+      if (k > c) {
+        const float lkc = __shfl_sync(FULL, a[c], k);  // L[k][c]
+        a[k] = lane >= k ? fmaf(-a[c], lkc, a[k]) : a[k];
+      }
     }
   }
 #pragma unroll
@@ -672,11 +676,11 @@ __device__ void factor_diag(const float* __restrict__ A, int K, int k0, int nb, 
   float x[NB];
 #pragma unroll
   for (int r = 0; r < NB; ++r) {
-    const float irr = 1.f / __shfl_sync(FULL, a[r], r);
     float acc = r == lane ? 1.f : 0.f;
 #pragma unroll
-    for (int k = 0; k < r; ++k) acc = fmaf(-__shfl_sync(FULL, a[k], r), x[k], acc);
-    x[r] = r >= lane ? acc * irr : 0.f;
+    for (int k = 0; k < NB; ++k)
+      if (k < r) acc = fmaf(-__shfl_sync(FULL, a[k], r), x[k], acc);
+    x[r] = r >= lane ? acc * il[r] : 0.f;
   }
 #pragma unroll
   for (int r = 0; r < NB; ++r) Li[r][lane] = x[r];
@@ -818,52 +822,50 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(float* __restrict__ A, f
 }
 
 // ---- 5d. FP32 solve of (L L^T) c = r with W = L^-1: y = W r, then c = W^T y,
-// and X += c in FP64.  16 output rows x 48 columns per CTA; k in chunks of 32.
-constexpr int TR_ROWS = 16;
+// and X += c in FP64.  One warp per output row: the lanes split the inner index,
+// each keeps the row's 48 partial sums, and a butterfly adds them up.  No
+// shared memory and no block barriers: every row proceeds independently.
 template <bool TRANS>
 __global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, int K,
                                                    const float* __restrict__ in, float* __restrict__ out,
                                                    double* __restrict__ Xs) {
-  __shared__ float Wt[32][TR_ROWS + 1];
-  __shared__ float In[32][RW];
-  const int i0 = blockIdx.x * TR_ROWS;
-  const int tr = threadIdx.x / 16, tc = threadIdx.x % 16;  // row tr, columns tc + 16 {0, 1, 2}
-  float acc[3] = {0.f, 0.f, 0.f};
-  // W lower: y_i uses j <= i (j < i0 + 16); W^T: c_j uses i >= j (i >= i0)
-  const int kb = TRANS ? i0 : 0;
-  const int ke = TRANS ? K : (i0 + TR_ROWS < K ? i0 + TR_ROWS : K);
-  for (int k0 = kb; k0 < ke; k0 += 32) {
-    for (int f = threadIdx.x; f < 32 * TR_ROWS; f += 256) {
-      const int q = f / TR_ROWS, r = f % TR_ROWS;
-      float v = 0.f;
-      if (k0 + q < K && i0 + r < K)
-        v = TRANS ? W[static_cast<size_t>(k0 + q) * K + i0 + r] : W[static_cast<size_t>(i0 + r) * K + k0 + q];
-      Wt[q][r] = v;
-    }
-    for (int f = threadIdx.x; f < 32 * RW; f += 256) {
-      const int q = f / RW, c = f % RW;
-      In[q][c] = k0 + q < K ? in[static_cast<size_t>(k0 + q) * RW + c] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int q = 0; q < 32; ++q) {
-      const float w = Wt[q][tr];
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= K) return;
+  float acc[RW];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) acc[u] = fmaf(w, In[q][tc + 16 * u], acc[u]);
+  for (int c = 0; c < RW; ++c) acc[c] = 0.f;
+  // W lower: y_i = sum_{j <= i} W_ij r_j;  W^T: c_j = sum_{i >= j} W_ij y_i
+  const int k_begin = TRANS ? row : 0;
+  const int k_end = TRANS ? K : row + 1;
+  for (int k = k_begin + lane; k < k_end; k += 32) {
+    const float w = TRANS ? W[static_cast<size_t>(k) * K + row] : W[static_cast<size_t>(row) * K + k];
+    const float4* v = reinterpret_cast<const float4*>(in + static_cast<size_t>(k) * RW);
+#pragma unroll
+    for (int q = 0; q < RW / 4; ++q) {
+      const float4 x = v[q];
+      acc[4 * q] = fmaf(w, x.x, acc[4 * q]);
+      acc[4 * q + 1] = fmaf(w, x.y, acc[4 * q + 1]);
+      acc[4 * q + 2] = fmaf(w, x.z, acc[4 * q + 2]);
+      acc[4 * q + 3] = fmaf(w, x.w, acc[4 * q + 3]);
     }
-    __syncthreads();
   }
-  const int i = i0 + tr;
-  if (i < K) {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      const int c = tc + 16 * u;
-      if (TRANS) {
-        if (c < DLSH_D) Xs[static_cast<size_t>(i) * RW + c] += static_cast<double>(acc[u]);
-      } else {
-        out[static_cast<size_t>(i) * RW + c] = acc[u];
-      }
-    }
+  for (int c = 0; c < RW; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
+  // every lane holds every sum; lane l stores columns l and 32 + l
+  float v0 = 0.f, v1 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) v0 = lane == c ? acc[c] : v0;
+#pragma unroll
+  for (int c = 32; c < RW; ++c) v1 = lane == c - 32 ? acc[c] : v1;
+  if (TRANS) {
+    Xs[static_cast<size_t>(row) * RW + lane] += static_cast<double>(v0);
+    if (lane < DLSH_D - 32) Xs[static_cast<size_t>(row) * RW + 32 + lane] += static_cast<double>(v1);
+  } else {
+    out[static_cast<size_t>(row) * RW + lane] = v0;
+    if (lane < RW - 32) out[static_cast<size_t>(row) * RW + 32 + lane] = v1;
   }
 }
 
@@ -1102,7 +1104,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
                   "dlsh_mod_update: factorisation");
     ++launches;
   }
-  const int tr_grid = (K + TR_ROWS - 1) / TR_ROWS;
+  const int tr_grid = (K + 7) / 8;
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
       residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, 192, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
