@@ -546,9 +546,12 @@ __global__ void ridge_kernel(double* __restrict__ M, double* __restrict__ Z,
   for (int j = threadIdx.x; j < K; j += blockDim.x) acc += M[static_cast<size_t>(j) * K + j];
   part[threadIdx.x] = acc;
   __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {  // fixed-order tree (blockDim.x = 1024)
+    if (static_cast<int>(threadIdx.x) < w) part[threadIdx.x] += part[threadIdx.x + w];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int q = 0; q < static_cast<int>(blockDim.x); ++q) tr += part[q];
+    const double tr = part[0];
     lam_s = tr > 0.0 ? RIDGE_REL * tr / K : RIDGE_REL;
     *lam_out = lam_s;
   }
@@ -946,17 +949,34 @@ __global__ void __launch_bounds__(1024)
                   const int* __restrict__ dead, float* __restrict__ D_new) {
   __shared__ float bv[1024];
   __shared__ long long bi[1024];
+  __shared__ int dl[MAX_K];   // the dead atoms, increasing
+  __shared__ int wcount[32];
   __shared__ float prev_v;
   __shared__ long long prev_i;
-  __shared__ int found;
-  const int tid = threadIdx.x;
+  __shared__ int found, ndead;
+  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   if (tid == 0) {
     prev_v = INFINITY;
     prev_i = -1;
+    ndead = 0;
   }
   __syncthreads();
-  for (int j = 0; j < K; ++j) {
-    if (!dead[j]) continue;  // uniform across the block
+  // ordered compaction of the dead flags (one pass of ballots per 1024 atoms)
+  for (int base = 0; base < K; base += 1024) {
+    const bool d = base + tid < K && dead[base + tid] != 0;
+    const unsigned m = __ballot_sync(0xffffffffu, d);
+    if (lane == 0) wcount[wp] = __popc(m);
+    __syncthreads();
+    int before = ndead;
+    for (int q = 0; q < wp; ++q) before += wcount[q];
+    if (d) dl[before + __popc(m & ((1u << lane) - 1u))] = base + tid;
+    __syncthreads();
+    if (tid == 0)
+      for (int q = 0; q < 32; ++q) ndead += wcount[q];
+    __syncthreads();
+  }
+  for (int t = 0; t < ndead; ++t) {
+    const int j = dl[t];
     while (true) {
       const float pv = prev_v;
       const long long pi = prev_i;
