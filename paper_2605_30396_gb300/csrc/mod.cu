@@ -10,13 +10,12 @@
 //   2. scan kernels     per-atom totals, atom offsets, per-(atom, tile) offsets
 //   3. scatter_kernel   one warp per signal tile writes (signal, coef, nnz) into
 //                       the atom-major list in signal order (a counting sort)
-//   4. accum_kernel     one CTA per atom: row j of G and column j of B.  Each
-//                       warp owns a fixed slice of the atom's list; batches are
-//                       staged with cp.async (double-buffered) and summed in
-//                       float-float arithmetic (exact FMA products, two-sum
-//                       accumulation: about FP64 accuracy on the FP32 pipe,
-//                       since GB300's FP64 units are slow); slices are added
-//                       in a fixed order in FP64
+//   4. accum_kernel     one CTA per segment of an atom's list: row j of G and
+//                       column j of B.  Each warp owns a fixed slice, one list
+//                       entry per lane; sums are float-float (exact FMA
+//                       products, two-sum accumulation: about FP64 accuracy
+//                       on the FP32 pipe, since GB300's FP64 units are slow),
+//                       lanes and warps are added in a fixed order
 //   5. mixed-precision solve of (G + lambda I) D~^T = (B + lambda D_old)^T:
 //      Jacobi scaling S = diag^-1/2 (unit diagonal); one cooperative kernel
 //      factors S (G + lambda I) S = L L^T in FP32 and inverts L on the way
@@ -110,16 +109,6 @@ static size_t carve(void* base, int K, int s, int64_t N, Ws& w) {
   w.Gp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * K);
   w.Bp = c.take<double>(static_cast<size_t>(max_segments(K, s, N)) * RW);
   return c.size();
-}
-
-// ---- cp.async (4-byte global -> shared copies, no registers) -----------------
-__device__ __forceinline__ void cp_async4(void* smem, const void* g) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem)), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ---- float-float accumulation: (hi, lo) += a * b, product exact via FMA ------
@@ -292,13 +281,28 @@ __device__ __forceinline__ void block_range(const int* __restrict__ off,
   hi = t1 < T ? off[static_cast<size_t>(j) * T + t1] : atom_start[j + 1];
 }
 
-constexpr int AB = 8;   // list entries per batch (<= 32: one lane per entry when staging)
-__host__ __device__ constexpr int acc_buf_words(int s) {
-  return 3 * AB + AB * DLSH_D + AB * s + AB * (s / 2 + 1);
+// One CTA per accumulation segment (a slice of atom j's list inside one signal
+// block); the warps split the segment, one list entry per lane and 32 entries
+// per step:
+//   B   each lane keeps the 45 float-float sums of its entries' a_ij x_i in
+//       registers (the signal row is read straight from global memory); a
+//       butterfly of two-sums adds the lanes up at the end
+//   G   for each support slot t, the lanes add a_ij a_ik into the warp's row
+//       partial in shared memory; lanes that hit the same atom k are grouped
+//       (match) and their products summed in lane order by the group's first
+//       lane before its single update; the diagonal k = j stays in registers
+// Every sum runs in a fixed order, so the result does not depend on timing.
+__device__ __forceinline__ void ff_add(float& h, float& l, float p, float pl) {
+  const float s = __fadd_rn(h, p);
+  const float v = __fadd_rn(s, -h);
+  const float e = __fadd_rn(__fadd_rn(h, -__fadd_rn(s, -v)), __fadd_rn(p, -v));
+  const float t = __fadd_rn(e, __fadd_rn(l, pl));
+  h = __fadd_rn(s, t);
+  l = __fadd_rn(t, -__fadd_rn(h, -s));
 }
 
 __global__ void __launch_bounds__(128)
-    accum_kernel(const float* __restrict__ X, const uint32_t* __restrict__ idxw,
+    accum_kernel(const float* __restrict__ X, const uint16_t* __restrict__ idx,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
                  const int* __restrict__ off, int T, int tpb, int PK,
                  const int* __restrict__ seg_start, const uint2* __restrict__ list,
@@ -306,175 +310,150 @@ __global__ void __launch_bounds__(128)
   extern __shared__ __align__(16) float smf[];
   const int nw = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int sw = s / 2 + 1;
-  const int bw = acc_buf_words(s);
-  // code staging: groups of gw = max(s, sw) lanes; lane t_lane of a group
-  // copies coefficient slot t_lane (< s) and index word t_lane (< sw) of
-  // entries e_lane, e_lane + e_step, ...
-  const int gw = s > sw ? s : sw;
-  const int e_step = 32 / gw;
-  const int e_lane = lane / gw < e_step ? lane / gw : 32;
-  const int t_lane = lane - (lane / gw) * gw;
+  const unsigned FULL = 0xffffffffu;
   float* ghi = smf + static_cast<size_t>(warp) * 2 * K;
   float* glo = ghi + K;
-  float* wbuf = smf + static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(warp) * 2 * bw;
+  double* bpart = reinterpret_cast<double*>(smf + static_cast<size_t>(nw) * 2 * K) + warp * RW;
   const int nseg = seg_start[PK];
   for (int seg = blockIdx.x; seg < nseg; seg += gridDim.x) {
-  // the segment's (block, atom): the largest pj with seg_start[pj] <= seg
-  int pj = 0;
-  {
-    int lo = 0, hi = PK - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (seg_start[mid] <= seg) lo = mid; else hi = mid - 1;
-    }
-    pj = lo;
-  }
-  const int pb = pj / K, j = pj - pb * K;
-  for (int k = lane; k < K; k += 32) {
-    ghi[k] = 0.f;
-    glo[k] = 0.f;
-  }
-  float bh[4] = {0.f, 0.f, 0.f, 0.f}, bl[4] = {0.f, 0.f, 0.f, 0.f};
-  float th[2] = {0.f, 0.f}, tl[2] = {0.f, 0.f};
-  int rlo, rhi;
-  block_range(off, atom_start, T, tpb, j, pb, rlo, rhi);
-  const int e0 = rlo + (seg - seg_start[pj]) * SEG;
-  const int e1 = e0 + SEG < rhi ? e0 + SEG : rhi;
-  const int len = e1 - e0;
-  const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
-  const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
-  const int nbt = (q1 - q0 + AB - 1) / AB;
-  auto bptr = [&](int buf) { return wbuf + buf * bw; };
-  auto load_list = [&](int bt, int& li, float& la, int& ln) {
-    const int e = q0 + bt * AB + lane;
-    li = 0;
-    la = 0.f;
-    ln = 0;
-    if (lane < AB && e < q1) {
-      const uint2 rec = list[e];
-      li = static_cast<int>(rec.x & 0x3FFFFFFu);
-      la = __uint_as_float(rec.y);
-      ln = static_cast<int>(rec.x >> 26);
-    }
-  };
-  auto stage = [&](int buf, int cnt, int li, float la, int ln) {
-    float* B = bptr(buf);
-    int* ei = reinterpret_cast<int*>(B);
-    int* en = ei + 2 * AB;
-    if (lane < AB) {
-      B[AB + lane] = la;
-      ei[lane] = li;
-      en[lane] = ln;
-    }
-    __syncwarp();
-    float* xb = B + 3 * AB;
-    float* cf = xb + AB * DLSH_D;
-    uint32_t* cw = reinterpret_cast<uint32_t*>(cf + AB * s);
-    // signal rows: two copy instructions per entry (45 = 32 + 13 words)
-    for (int e = 0; e < cnt; ++e) {
-      const float* src = X + static_cast<int64_t>(ei[e]) * DLSH_D;
-      cp_async4(xb + e * DLSH_D + lane, src + lane);
-      if (lane < DLSH_D - 32) cp_async4(xb + e * DLSH_D + 32 + lane, src + 32 + lane);
-    }
-    // codes: lane (q, t) copies slot t of entry e0 + q, 32 / s entries per step
-    for (int e = e_lane; e < cnt; e += e_step) {
-      const int64_t base = static_cast<int64_t>(ei[e]) * s;
-      if (t_lane < s) cp_async4(cf + e * s + t_lane, coef + base + t_lane);
-      const int64_t w0 = base >> 1, wl = (base + s - 1) >> 1;
-      if (t_lane < sw && w0 + t_lane <= wl) cp_async4(cw + e * sw + t_lane, idxw + w0 + t_lane);
-    }
-    cp_async_commit();
-  };
-  int li = 0, ln = 0;
-  float la = 0.f;
-  if (nbt > 0) {
-    load_list(0, li, la, ln);
-    stage(0, q1 - q0 < AB ? q1 - q0 : AB, li, la, ln);
-  }
-  if (nbt > 1) load_list(1, li, la, ln);
-  for (int bt = 0; bt < nbt; ++bt) {
-    const int cnt = q1 - q0 - bt * AB < AB ? q1 - q0 - bt * AB : AB;
-    if (bt + 1 < nbt) {
-      const int cn = q1 - q0 - (bt + 1) * AB < AB ? q1 - q0 - (bt + 1) * AB : AB;
-      stage((bt + 1) & 1, cn, li, la, ln);
-      if (bt + 2 < nbt) load_list(bt + 2, li, la, ln);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncwarp();
-    const float* B = bptr(bt & 1);
-    const int* ei = reinterpret_cast<const int*>(B);
-    const float* ea = B + AB;
-    const int* en = ei + 2 * AB;
-    const float* xb = B + 3 * AB;
-    const float* cf = xb + AB * DLSH_D;
-    const uint32_t* cw = reinterpret_cast<const uint32_t*>(cf + AB * s);
-    // Four entries per step: B sums of entry e go to accumulator e mod 4 (and
-    // the 13-dim tails of each pair to accumulator (e mod 4) / 2), so the
-    // float-float chains are independent; the G updates stay in entry order.
-    for (int e = 0; e < cnt; e += 4) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (e + u < cnt) ff_fma(bh[u], bl[u], ea[e + u], xb[(e + u) * DLSH_D + lane]);
-#pragma unroll
-      for (int pr = 0; pr < 2; ++pr) {
-        // dims 32..44: lanes 0..12 take the even entry of the pair, lanes 16..28 the odd one
-        const int et = e + 2 * pr + (lane >> 4);
-        if ((lane & 15) < DLSH_D - 32 && et < cnt)
-          ff_fma(th[pr], tl[pr], ea[et], xb[et * DLSH_D + 32 + (lane & 15)]);
+    // the segment's (block, atom): the largest pj with seg_start[pj] <= seg
+    int pj = 0;
+    {
+      int lo = 0, hi = PK - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (seg_start[mid] <= seg) lo = mid; else hi = mid - 1;
       }
+      pj = lo;
+    }
+    const int pb = pj / K, j = pj - pb * K;
+    for (int k = lane; k < K; k += 32) {
+      ghi[k] = 0.f;
+      glo[k] = 0.f;
+    }
+    __syncwarp();
+    int rlo, rhi;
+    block_range(off, atom_start, T, tpb, j, pb, rlo, rhi);
+    const int e0 = rlo + (seg - seg_start[pj]) * SEG;
+    const int e1 = e0 + SEG < rhi ? e0 + SEG : rhi;
+    const int len = e1 - e0;
+    const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
+    const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
+    float bh[DLSH_D], bl[DLSH_D];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int eu = e + u;
-        if (eu < cnt) {
-          const int nz = en[eu];
-          if (lane < nz) {
-            const int o = ((ei[eu] * s) & 1) + lane;
-            const uint32_t wv = cw[eu * sw + (o >> 1)];
-            const int k = (o & 1) ? static_cast<int>(wv >> 16) : static_cast<int>(wv & 0xFFFFu);
-            if (k < K) ff_fma(ghi[k], glo[k], ea[eu], cf[eu * s + lane]);
+    for (int d = 0; d < DLSH_D; ++d) {
+      bh[d] = 0.f;
+      bl[d] = 0.f;
+    }
+    float dh = 0.f, dl = 0.f;  // G[j][j]
+    for (int eb = q0; eb < q1; eb += 32) {
+      const int e = eb + lane;
+      const bool act = e < q1;
+      long long sig = 0;
+      int nz = 0;
+      float a = 0.f;
+      if (act) {
+        const uint2 rec = list[e];
+        sig = static_cast<long long>(rec.x & 0x3FFFFFFu);
+        nz = static_cast<int>(rec.x >> 26);
+        a = __uint_as_float(rec.y);
+      }
+      if (act) {
+        const float* xr = X + sig * DLSH_D;
+        float xv[DLSH_D];
+#pragma unroll
+        for (int d = 0; d < DLSH_D; ++d) xv[d] = __ldg(xr + d);
+#pragma unroll
+        for (int d = 0; d < DLSH_D; ++d) ff_fma(bh[d], bl[d], a, xv[d]);
+      }
+      const int mx = __reduce_max_sync(FULL, act ? nz : 0);
+      const uint16_t* ir = idx + sig * s;
+      const float* cr = coef + sig * s;
+      for (int t = 0; t < mx; ++t) {
+        const bool on = act && t < nz;
+        const int k = on ? static_cast<int>(ir[t]) : -1;
+        const float c = on ? cr[t] : 0.f;
+        if (on && k == j) ff_fma(dh, dl, a, c);
+        const bool upd = on && k != j && k < K;
+        const unsigned m = __ballot_sync(FULL, upd);
+        if (upd) {
+          const unsigned grp = __match_any_sync(m, k);
+          float ph = __fmul_rn(a, c);
+          float pl = __fmaf_rn(a, c, -ph);
+          const int first = __ffs(grp) - 1;
+          if (grp != (1u << lane)) {
+            // the group's products, summed in lane order on its first lane
+            unsigned rest = grp & ~(1u << first);
+            float sh = ph, sl = pl;
+            while (rest) {
+              const int src = __ffs(rest) - 1;
+              const float h2 = __shfl_sync(grp, ph, src);
+              const float l2 = __shfl_sync(grp, pl, src);
+              ff_add(sh, sl, h2, l2);
+              rest &= rest - 1;
+            }
+            ph = sh;
+            pl = sl;
+          }
+          if (lane == first) {
+            float h = ghi[k], l = glo[k];
+            ff_add(h, l, ph, pl);
+            ghi[k] = h;
+            glo[k] = l;
           }
         }
+        __syncwarp();
       }
     }
-    __syncwarp();
-  }
-  // publish this warp's B partial next to its G partial, then sum the warps in order
-  __syncthreads();
-  double* bpart = reinterpret_cast<double*>(wbuf);  // the warp's staging area is free now
-  {
-    double b = 0.0;
+    // the lanes' sums: butterfly of two-sums (every lane ends with the totals)
 #pragma unroll
-    for (int u = 0; u < 4; ++u) b += static_cast<double>(bh[u]) + static_cast<double>(bl[u]);
-    bpart[lane] = b;
-  }
-  {
-    const double tail = static_cast<double>(th[0]) + static_cast<double>(tl[0]) +
-                        static_cast<double>(th[1]) + static_cast<double>(tl[1]);
-    const double odd = __shfl_down_sync(0xffffffffu, tail, 16);
-    if (lane < RW - 32) bpart[32 + lane] = lane < DLSH_D - 32 ? tail + odd : 0.0;
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < K; k += blockDim.x) {
-    double acc = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      const float* gh = smf + static_cast<size_t>(w) * 2 * K;
-      acc += static_cast<double>(gh[k]) + static_cast<double>(gh[K + k]);
+    for (int d = 0; d < DLSH_D; ++d)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(FULL, bh[d], o);
+        const float l2 = __shfl_xor_sync(FULL, bl[d], o);
+        ff_add(bh[d], bl[d], h2, l2);
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(FULL, dh, o);
+      const float l2 = __shfl_xor_sync(FULL, dl, o);
+      ff_add(dh, dl, h2, l2);
     }
-    Gp[static_cast<size_t>(seg) * K + k] = acc;
-  }
-  for (int q = threadIdx.x; q < RW; q += blockDim.x) {
-    double acc = 0.0;
-    for (int w = 0; w < nw; ++w) {
-      const double* bp = reinterpret_cast<const double*>(smf + static_cast<size_t>(nw) * 2 * K +
-                                                         static_cast<size_t>(w) * 2 * bw);
-      acc += bp[q];
+    if (lane == 0) {
+      float h = ghi[j], l = glo[j];
+      ff_add(h, l, dh, dl);
+      ghi[j] = h;
+      glo[j] = l;
     }
-    Bp[static_cast<size_t>(seg) * RW + q] = acc;
-  }
-  __syncthreads();  // shared partials are reused by the next segment
+    {
+      double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 32; ++d)
+        if (lane == d) b0 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
+#pragma unroll
+      for (int d = 32; d < DLSH_D; ++d)
+        if (lane == d - 32) b1 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
+      bpart[lane] = b0;
+      if (lane < RW - 32) bpart[32 + lane] = b1;  // zero past the 45 dimensions
+    }
+    // sum the warps' partials in order
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      double acc = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        const float* gh = smf + static_cast<size_t>(w) * 2 * K;
+        acc += static_cast<double>(gh[k]) + static_cast<double>(gh[K + k]);
+      }
+      Gp[static_cast<size_t>(seg) * K + k] = acc;
+    }
+    for (int q = threadIdx.x; q < RW; q += blockDim.x) {
+      double acc = 0.0;
+      for (int w = 0; w < nw; ++w)
+        acc += reinterpret_cast<const double*>(smf + static_cast<size_t>(nw) * 2 * K)[w * RW + q];
+      Bp[static_cast<size_t>(seg) * RW + q] = acc;
+    }
+    __syncthreads();  // shared partials are reused by the next segment
   }
 }
 
@@ -527,8 +506,9 @@ __global__ void seg_reduce_kernel(const int* __restrict__ seg_start, const doubl
 }
 
 static int accum_warps(int K, int s, size_t* smem) {
+  (void)s;
   for (int nw = 4; nw >= 1; --nw) {
-    const size_t b = (static_cast<size_t>(nw) * 2 * K + static_cast<size_t>(nw) * 2 * acc_buf_words(s)) * 4;
+    const size_t b = static_cast<size_t>(nw) * 2 * K * 4 + static_cast<size_t>(nw) * RW * 8;
     if (b <= static_cast<size_t>(SMEM_LIMIT)) {
       *smem = b;
       return nw;
@@ -1082,14 +1062,16 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   {
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
-    int per_sm = static_cast<int>(SMEM_LIMIT / (acc_smem > 0 ? acc_smem : 1));
+    int per_sm = 0;
+    DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accum_kernel, acc_nw * 32,
+                                                                acc_smem),
+                  "dlsh_mod_update: occupancy");
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
     int64_t grid = static_cast<int64_t>(sms) * per_sm;
     const int64_t ms = max_segments(K, s, N);
     if (grid > ms) grid = ms;
     accum_kernel<<<static_cast<int>(grid), acc_nw * 32, acc_smem, st>>>(
-        X, reinterpret_cast<const uint32_t*>(idx), coef, s, K, w.atom_start, w.off, T, tpb, P * K,
+        X, idx, coef, s, K, w.atom_start, w.off, T, tpb, P * K,
         w.seg_start,
         w.list, w.Gp, w.Bp);
   }
