@@ -301,7 +301,11 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float p, float pl) {
   l = __fadd_rn(t, -__fadd_rn(h, -s));
 }
 
-__global__ void __launch_bounds__(128)
+// SMAX >= s: the support slots of a lane's entry are loaded into registers at
+// the start of each step, next to its signal row, so no load waits inside the
+// slot loop.
+template <int SMAX>
+__global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
     accum_kernel(const float* __restrict__ X, const uint16_t* __restrict__ idx,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
                  const int* __restrict__ off, int T, int tpb, int PK,
@@ -358,6 +362,18 @@ __global__ void __launch_bounds__(128)
         nz = static_cast<int>(rec.x >> 26);
         a = __uint_as_float(rec.y);
       }
+      int kk[SMAX];
+      float cc[SMAX];
+      {
+        const uint16_t* ir = idx + sig * s;
+        const float* cr = coef + sig * s;
+#pragma unroll
+        for (int t = 0; t < SMAX; ++t) {
+          const bool on = act && t < nz;
+          kk[t] = on ? static_cast<int>(__ldg(ir + t)) : -1;
+          cc[t] = on ? __ldg(cr + t) : 0.f;
+        }
+      }
       if (act) {
         const float* xr = X + sig * DLSH_D;
         float xv[DLSH_D];
@@ -367,12 +383,12 @@ __global__ void __launch_bounds__(128)
         for (int d = 0; d < DLSH_D; ++d) ff_fma(bh[d], bl[d], a, xv[d]);
       }
       const int mx = __reduce_max_sync(FULL, act ? nz : 0);
-      const uint16_t* ir = idx + sig * s;
-      const float* cr = coef + sig * s;
-      for (int t = 0; t < mx; ++t) {
-        const bool on = act && t < nz;
-        const int k = on ? static_cast<int>(ir[t]) : -1;
-        const float c = on ? cr[t] : 0.f;
+#pragma unroll
+      for (int t = 0; t < SMAX; ++t) {
+        if (t >= mx) break;  // uniform over the warp
+        const bool on = kk[t] >= 0;
+        const int k = kk[t];
+        const float c = cc[t];
         if (on && k == j) ff_fma(dh, dl, a, c);
         const bool upd = on && k != j && k < K;
         const unsigned m = __ballot_sync(FULL, upd);
@@ -1053,7 +1069,10 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
     scatter_kernel<<<T, 32, K * sizeof(int), st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
     ++launches;
   }
-  DLSH_CUDA_TRY(cudaFuncSetAttribute(accum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  void (*accum)(const float*, const uint16_t*, const float*, int, int, const int*, const int*, int, int, int,
+                const int*, const uint2*, double*, double*) =
+      s <= 8 ? accum_kernel<8> : (s <= 16 ? accum_kernel<16> : accum_kernel<32>);
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(accum, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      static_cast<int>(acc_smem)),
                 "dlsh_mod_update: attribute");
   const int P = static_cast<int>(n_blocks(N));
@@ -1063,17 +1082,14 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
     int per_sm = 0;
-    DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accum_kernel, acc_nw * 32,
-                                                                acc_smem),
+    DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accum, acc_nw * 32, acc_smem),
                   "dlsh_mod_update: occupancy");
     if (per_sm < 1) per_sm = 1;
     int64_t grid = static_cast<int64_t>(sms) * per_sm;
     const int64_t ms = max_segments(K, s, N);
     if (grid > ms) grid = ms;
-    accum_kernel<<<static_cast<int>(grid), acc_nw * 32, acc_smem, st>>>(
-        X, idx, coef, s, K, w.atom_start, w.off, T, tpb, P * K,
-        w.seg_start,
-        w.list, w.Gp, w.Bp);
+    accum<<<static_cast<int>(grid), acc_nw * 32, acc_smem, st>>>(X, idx, coef, s, K, w.atom_start, w.off, T, tpb,
+                                                                 P * K, w.seg_start, w.list, w.Gp, w.Bp);
   }
   seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, P, w.M, w.Z);
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
