@@ -282,11 +282,11 @@ __device__ __forceinline__ void block_range(const int* __restrict__ off,
 }
 
 // One CTA per accumulation segment (a slice of atom j's list inside one signal
-// block); the warps split the segment, one list entry per lane and 32 entries
-// per step:
-//   B   each lane keeps the 45 float-float sums of its entries' a_ij x_i in
-//       registers (the signal row is read straight from global memory); a
-//       butterfly of two-sums adds the lanes up at the end
+// block); the warps split the segment, one list entry per lane pair and 16
+// entries per step:
+//   B   each lane keeps float-float sums of its entries' a_ij x_i over half of
+//       the 45 dimensions in registers (the signal row is read straight from
+//       global memory); a butterfly of two-sums adds the lanes up at the end
 //   G   for each support slot t, the lanes add a_ij a_ik into the warp's row
 //       partial in shared memory; lanes that hit the same atom k are grouped
 //       (match) and their products summed in lane order by the group's first
@@ -303,9 +303,11 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float p, float pl) {
 
 // SMAX >= s: the support slots of a lane's entry are loaded into registers at
 // the start of each step, next to its signal row, so no load waits inside the
-// slot loop.
+// slot loop.  Two lanes share an entry (half of its dimensions and slots each),
+// which halves the registers and doubles the warps an SM can hold.
+constexpr int DH = (DLSH_D + 1) / 2;  // dimensions per lane of a pair (23)
 template <int SMAX>
-__global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
+__global__ void __launch_bounds__(128, SMAX <= 16 ? 4 : 3)
     accum_kernel(const float* __restrict__ X, const uint16_t* __restrict__ idx,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
                  const int* __restrict__ off, int T, int tpb, int PK,
@@ -343,15 +345,20 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
     const int len = e1 - e0;
     const int q0 = e0 + static_cast<int>(static_cast<long long>(len) * warp / nw);
     const int q1 = e0 + static_cast<int>(static_cast<long long>(len) * (warp + 1) / nw);
-    float bh[DLSH_D], bl[DLSH_D];
+    // lane pair (2p, 2p + 1) takes entry p of each step of 16: the even lane
+    // dimensions 0..22 and slots 0..SMAX/2-1, the odd lane the rest
+    const int sub = lane & 1, pe = lane >> 1;
+    const int d0 = sub * DH;
+    float bh[DH], bl[DH];
 #pragma unroll
-    for (int d = 0; d < DLSH_D; ++d) {
+    for (int d = 0; d < DH; ++d) {
       bh[d] = 0.f;
       bl[d] = 0.f;
     }
     float dh = 0.f, dl = 0.f;  // G[j][j]
-    for (int eb = q0; eb < q1; eb += 32) {
-      const int e = eb + lane;
+    constexpr int SH = SMAX / 2;
+    for (int eb = q0; eb < q1; eb += 16) {
+      const int e = eb + pe;
       const bool act = e < q1;
       long long sig = 0;
       int nz = 0;
@@ -362,33 +369,35 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
         nz = static_cast<int>(rec.x >> 26);
         a = __uint_as_float(rec.y);
       }
-      int kk[SMAX];
-      float cc[SMAX];
+      int kk[SH];
+      float cc[SH];
       {
         const uint16_t* ir = idx + sig * s;
         const float* cr = coef + sig * s;
 #pragma unroll
-        for (int t = 0; t < SMAX; ++t) {
+        for (int u = 0; u < SH; ++u) {
+          const int t = sub * SH + u;
           const bool on = act && t < nz;
-          kk[t] = on ? static_cast<int>(__ldg(ir + t)) : -1;
-          cc[t] = on ? __ldg(cr + t) : 0.f;
+          kk[u] = on ? static_cast<int>(__ldg(ir + t)) : -1;
+          cc[u] = on ? __ldg(cr + t) : 0.f;
         }
       }
       if (act) {
-        const float* xr = X + sig * DLSH_D;
-        float xv[DLSH_D];
+        const float* xr = X + sig * DLSH_D + d0;
+        float xv[DH];
 #pragma unroll
-        for (int d = 0; d < DLSH_D; ++d) xv[d] = __ldg(xr + d);
+        for (int d = 0; d < DH; ++d) xv[d] = (d0 + d < DLSH_D) ? __ldg(xr + d) : 0.f;
 #pragma unroll
-        for (int d = 0; d < DLSH_D; ++d) ff_fma(bh[d], bl[d], a, xv[d]);
+        for (int d = 0; d < DH; ++d) ff_fma(bh[d], bl[d], a, xv[d]);
       }
-      const int mx = __reduce_max_sync(FULL, act ? nz : 0);
+      const int mine = act ? (nz - sub * SH < 0 ? 0 : (nz - sub * SH > SH ? SH : nz - sub * SH)) : 0;
+      const int mx = __reduce_max_sync(FULL, mine);
 #pragma unroll
-      for (int t = 0; t < SMAX; ++t) {
-        if (t >= mx) break;  // uniform over the warp
-        const bool on = kk[t] >= 0;
-        const int k = kk[t];
-        const float c = cc[t];
+      for (int u = 0; u < SH; ++u) {
+        if (u >= mx) break;  // uniform over the warp
+        const bool on = kk[u] >= 0;
+        const int k = kk[u];
+        const float c = cc[u];
         if (on && k == j) ff_fma(dh, dl, a, c);
         const bool upd = on && k != j && k < K;
         const unsigned m = __ballot_sync(FULL, upd);
@@ -421,11 +430,12 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
         __syncwarp();
       }
     }
-    // the lanes' sums: butterfly of two-sums (every lane ends with the totals)
+    // the lanes' sums: butterflies of two-sums, B over the lanes of equal
+    // parity (their dimensions agree), the diagonal over all lanes
 #pragma unroll
-    for (int d = 0; d < DLSH_D; ++d)
+    for (int d = 0; d < DH; ++d)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = 16; o > 1; o >>= 1) {
         const float h2 = __shfl_xor_sync(FULL, bh[d], o);
         const float l2 = __shfl_xor_sync(FULL, bl[d], o);
         ff_add(bh[d], bl[d], h2, l2);
@@ -443,15 +453,16 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 3 : 2)
       glo[j] = l;
     }
     {
+      // lane (pe, sub) stores dimensions d0 + pe and d0 + pe + 16 of its half
       double b0 = 0.0, b1 = 0.0;
 #pragma unroll
-      for (int d = 0; d < 32; ++d)
-        if (lane == d) b0 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
-#pragma unroll
-      for (int d = 32; d < DLSH_D; ++d)
-        if (lane == d - 32) b1 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
-      bpart[lane] = b0;
-      if (lane < RW - 32) bpart[32 + lane] = b1;  // zero past the 45 dimensions
+      for (int d = 0; d < DH; ++d) {
+        if (pe == d) b0 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
+        if (pe + 16 == d) b1 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
+      }
+      if (d0 + pe < DLSH_D) bpart[d0 + pe] = b0;
+      if (pe + 16 < DH && d0 + pe + 16 < DLSH_D) bpart[d0 + pe + 16] = b1;
+      if (lane < RW - DLSH_D) bpart[DLSH_D + lane] = 0.0;
     }
     // sum the warps' partials in order
     __syncthreads();
