@@ -28,7 +28,7 @@ def _gpu(lib, X, D0, idx, coef, nnz, resid):
 
 
 @pytest.mark.parametrize("N,K,s", [(5000, 128, 6), (3000, 256, 8), (20000, 1024, 8), (700, 64, 16),
-                                   (4000, 300, 4), (30000, 2048, 8)])
+                                   (4000, 300, 4), (30000, 2048, 8), (1000, 20, 4), (12000, 4096, 8)])
 def test_mod_matches_oracle(lib, N, K, s):
     X, D0, idx, coef, nnz, resid = _inputs(N, K, s)
     got = _gpu(lib, X, D0, idx, coef, nnz, resid)
