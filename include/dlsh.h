@@ -330,6 +330,20 @@ int dlsh_csc_from_ell(const uint16_t* idx, const float* coef,
                       uint16_t* row_idx, float* val, void* ws, size_t ws_bytes,
                       void* stream, int flags);
 
+/* ---- self-test of the bounded device waits --------------------------------
+ * Not part of the method (the paper has no counterpart): every pipelined kernel
+ * here waits on mbarriers or a grid barrier with a cycle budget, so that a lost
+ * arrival ends in DLSH_ERR_TIMEOUT instead of a hung GPU.  This call makes such
+ * a wait run out on purpose, with nothing else in flight: kind 0 waits on an
+ * mbarrier nobody arrives on; kind 1 is a cooperative launch in which one CTA
+ * skips the grid barrier.  budget_cycles (1 .. 4e9 SM cycles) bounds the wait.
+ * Returns DLSH_ERR_TIMEOUT when the wait gave up as designed; the CUDA context
+ * stays usable.  ws: dlsh_selftest_workspace_size() bytes of device memory,
+ * 256-byte aligned.  Synchronises the stream. */
+size_t dlsh_selftest_workspace_size(void);
+int dlsh_selftest_bounded_wait(int kind, int64_t budget_cycles, void* ws, size_t ws_bytes,
+                               void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,45 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return true;
 }
 
+// ---- grid barrier (cooperative launches only) --------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
+// the generation.  The wait is bounded: on timeout it records ST_TIMEOUT and
+// returns false, and the caller leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, long long budget, uint32_t* status) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = ld_acquire_u32(bar + 1);
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(bar + 1) == g) {
+        if (clock64() - t0 > budget) {
+          flag_status(status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
 // ---- proxy fences --------------------------------------------------------
 // Make generic-proxy shared-memory writes visible to the async proxy (TMA and
 // the tensor cores read shared memory through it).

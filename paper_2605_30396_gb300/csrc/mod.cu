@@ -608,44 +608,6 @@ __global__ void scale_kernel(const double* __restrict__ M, const double* __restr
 constexpr int CH_T = 256;   // threads per CTA
 constexpr int CH_TILE = 64;
 
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier of a cooperative launch: bar[0] counts arrivals, bar[1] is
-// the generation.  The wait is bounded: on timeout it records ST_TIMEOUT and
-// returns false, and the caller leaves the kernel.
-__device__ bool grid_barrier(unsigned* bar, long long budget, uint32_t* status) {
-  __shared__ int ok_s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned g = ld_acquire_u32(bar + 1);
-    __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (ld_acquire_u32(bar + 1) == g) {
-        if (clock64() - t0 > budget) {
-          flag_status(status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    ok_s = ok;
-  }
-  __syncthreads();
-  return ok_s != 0;
-}
-
 // One warp factors the nb x nb diagonal block at k0 (rows past K padded with
 // the identity): L into Ls, L^-1 into Li (both lower, [32][33]).  Lane r holds
 // row r in registers; pivots and entries move by shuffles.  Every loop is
