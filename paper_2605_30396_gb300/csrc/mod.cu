@@ -715,34 +715,44 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(float* __restrict__ A, f
       if (bad && tid == 0 && blockIdx.x == 0) flag_status(status, ST_BAD_INPUT);
     }
     __syncthreads();
-    // panel rows: L_ik = A_ik L_kk^-T
-    for (long long i = k1 + gt; i < K; i += gstride) {
-      float* ar = A + static_cast<size_t>(i) * K + k0;
-      float v[NB];
+    // Warp tasks over the whole grid: the panel rows (lane c, holding row c of
+    // L_kk^-1 in registers: L_ic = sum_q A_iq Li[c][q]) and 32-column tiles of
+    // the rows of W (one column per lane: W_qc = sum_p Li[q][p] R_pc).
+    {
+      const int lane = tid & 31;
+      float lr[NB];
 #pragma unroll
-      for (int q = 0; q < NB; ++q) v[q] = q < nb ? ar[q] : 0.f;
-#pragma unroll
-      for (int c = 0; c < NB; ++c) {
-        if (c < nb) {
+      for (int q = 0; q < NB; ++q) lr[q] = Li[lane][q];
+      const int gw = blockIdx.x * (CH_T / 32) + (tid >> 5);
+      const int nwarps = gridDim.x * (CH_T / 32);
+      const int npanel = K - k1;
+      const int ntiles = (k1 + 31) / 32;
+      for (int task = gw; task < npanel + ntiles; task += nwarps) {
+        if (task < npanel) {
+          const int i = k1 + task;
+          float* ar = A + static_cast<size_t>(i) * K + k0;
+          const float v = lane < nb ? ar[lane] : 0.f;
           float acc = 0.f;
 #pragma unroll
-          for (int q = 0; q <= c; ++q) acc = fmaf(v[q], Li[c][q], acc);
-          ar[c] = acc;
-        }
-      }
-    }
-    // rows k0..k1 of W: W_k = L_kk^-1 R_k, one column per thread (columns < k1)
-    for (long long c = gt; c < k1; c += gstride) {
-      float r[NB];
+          for (int q = 0; q < NB; ++q) acc = fmaf(__shfl_sync(0xffffffffu, v, q), lr[q], acc);
+          if (lane < nb) ar[lane] = acc;
+        } else {
+          // lane c: column c0 + c of R_k, y_q = sum_{p <= q} Li[q][p] R_pc
+          const int c = (task - npanel) * 32 + lane;
+          if (c < k1) {
+            float r[NB];
 #pragma unroll
-      for (int p = 0; p < NB; ++p) r[p] = p < nb ? W[static_cast<size_t>(k0 + p) * K + c] : 0.f;
+            for (int p = 0; p < NB; ++p) r[p] = p < nb ? W[static_cast<size_t>(k0 + p) * K + c] : 0.f;
 #pragma unroll
-      for (int q = 0; q < NB; ++q) {
-        if (q < nb) {
-          float acc = 0.f;
+            for (int q = 0; q < NB; ++q) {
+              if (q < nb) {
+                float acc = 0.f;
 #pragma unroll
-          for (int p = 0; p <= q; ++p) acc = fmaf(Li[q][p], r[p], acc);
-          W[static_cast<size_t>(k0 + q) * K + c] = acc;
+                for (int p = 0; p <= q; ++p) acc = fmaf(Li[q][p], r[p], acc);
+                W[static_cast<size_t>(k0 + q) * K + c] = acc;
+              }
+            }
+          }
         }
       }
     }
@@ -1080,7 +1090,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
       int sms = device_sm_count();
       if (sms <= 0) sms = 1;
       if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_mod_update: factorisation kernel does not fit");
-      coop_grid = sms * (per_sm < 2 ? per_sm : 2);
+      coop_grid = sms;  // one CTA per SM: fewer arrivals at each grid barrier
     }
     DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_mod_update: barrier");
     float* A32 = w.A32;
