@@ -34,7 +34,7 @@
 namespace dlsh {
 namespace mod {
 
-constexpr int TS = 512;        // signals per counting-sort tile (one scatter warp each)
+constexpr int TS = 512;        // signals per counting-sort tile (one scatter CTA each)
 constexpr int NB = 32;         // Cholesky block
 constexpr int RW = 48;         // padded RHS width (45 used)
 constexpr int MAX_K = 4096;    // shared-memory G-row partials limit
@@ -220,53 +220,93 @@ __global__ void tile_offsets_kernel(const int* __restrict__ cnt, int T,
   }
 }
 
-// ---- 3. counting-sort scatter, one warp per tile, signal order ---------------
-// The warp loads 32/s signals per step (one lane per code slot) one step ahead,
-// then commits them to the atom-major list one signal at a time; a signal's
-// atoms are distinct, so the shared-memory cursors see no contention and the
-// list order is the signal order.
-__global__ void scatter_kernel(const uint16_t* __restrict__ idx, const float* __restrict__ coef,
-                               const uint8_t* __restrict__ nnz, int s, int64_t N, int K, int T,
-                               const int* __restrict__ off, uint2* __restrict__ list) {
-  extern __shared__ int cursor[];
-  const int lane = threadIdx.x;
+// ---- 3. counting-sort scatter, one CTA of 8 warps per tile, signal order ------
+// Warp w owns signals [64 w, 64 w + 64) of the tile and walks their code slots
+// in order, 32 at a time.  Pass 1 counts each atom per warp (lanes with the same
+// atom found by match-any); the counts become per-warp bases; pass 2 gives each
+// entry its rank among the earlier entries of its atom (warps in order, then
+// lanes in order) and writes it to the atom-major list.  A signal's atoms are
+// distinct, so within an atom the entries stay in signal order.
+constexpr int SC_T = 256;
+__global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restrict__ idx,
+                                                      const float* __restrict__ coef,
+                                                      const uint8_t* __restrict__ nnz, int s, int64_t N,
+                                                      int K, int T, const int* __restrict__ off,
+                                                      uint2* __restrict__ list) {
+  extern __shared__ int scs[];
+  int* wc = scs;                                   // [8][K] per-warp counts, then bases
+  int* toff = scs + static_cast<size_t>(SC_T / 32) * K;  // [K] this tile's list offsets
   const int b = blockIdx.x;
-  for (int j = lane; j < K; j += 32) cursor[j] = off[static_cast<size_t>(j) * T + b];
-  __syncwarp();
-  const int P = 32 / s;  // signals per step
-  const int q = lane / s, t = lane - q * s;
-  const bool slot = lane < P * s;
-  const int64_t i0 = static_cast<int64_t>(b) * TS;
-  const int64_t i1 = i0 + TS < N ? i0 + TS : N;
-  auto load = [&](int64_t base, int& j, float& c, int& nz) {
-    const int64_t i = base + q;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int j = tid; j < K; j += SC_T) {
+    toff[j] = off[static_cast<size_t>(j) * T + b];
+#pragma unroll
+    for (int w = 0; w < SC_T / 32; ++w) wc[w * K + j] = 0;
+  }
+  __syncthreads();
+  constexpr int SPW = TS / (SC_T / 32);  // signals per warp (64)
+  const int64_t i0 = static_cast<int64_t>(b) * TS + static_cast<int64_t>(warp) * SPW;
+  const int64_t i1w = i0 + SPW;
+  const int64_t iend = i1w < N ? i1w : N;
+  const int e_end = static_cast<int>(iend > i0 ? iend - i0 : 0) * s;  // <= 64 * 32
+  int* mine = wc + static_cast<size_t>(warp) * K;
+  const unsigned lt = (1u << lane) - 1u;
+  auto entry = [&](int e, int& j, float& c, int& nz, int64_t& sig) {
     j = -1;
     c = 0.f;
     nz = 0;
-    if (slot && i < i1) {
-      nz = nnz[i];
+    sig = 0;
+    if (e < e_end) {
+      const int q = e / s;
+      sig = i0 + q;
+      const int t = e - q * s;
+      nz = nnz[sig];
       nz = nz > s ? s : nz;
       if (t < nz) {
-        j = idx[i * s + t];
-        c = coef[i * s + t];
+        const int jj = idx[sig * s + t];
+        if (jj < K) {
+          j = jj;
+          c = coef[sig * s + t];
+        }
       }
     }
   };
-  int jn, nzn;
-  float cn;
-  load(i0, jn, cn, nzn);
-  for (int64_t base = i0; base < i1; base += P) {
-    const int jc = jn, nzc = nzn;
-    const float cc = cn;
-    if (base + P < i1) load(base + P, jn, cn, nzn);
-    for (int qq = 0; qq < P; ++qq) {
-      if (q == qq && slot && jc >= 0 && jc < K) {
-        const int pos = atomicAdd(&cursor[jc], 1);
-        list[pos] = make_uint2(static_cast<uint32_t>(base + q) | (static_cast<uint32_t>(nzc) << 26),
-                               __float_as_uint(cc));
-      }
-      __syncwarp();
+  // pass 1: counts
+  for (int e0 = 0; e0 < e_end; e0 += 32) {
+    int j, nz;
+    float c;
+    int64_t sig;
+    entry(e0 + lane, j, c, nz, sig);
+    const unsigned m = __match_any_sync(0xffffffffu, j);
+    if (j >= 0 && (m & lt) == 0) mine[j] += __popc(m);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per-warp bases: warps in order
+  for (int j = tid; j < K; j += SC_T) {
+    int run = toff[j];
+#pragma unroll
+    for (int w = 0; w < SC_T / 32; ++w) {
+      const int cw = wc[w * K + j];
+      wc[w * K + j] = run;
+      run += cw;
     }
+  }
+  __syncthreads();
+  // pass 2: ranks and writes
+  for (int e0 = 0; e0 < e_end; e0 += 32) {
+    int j, nz;
+    float c;
+    int64_t sig;
+    entry(e0 + lane, j, c, nz, sig);
+    const unsigned m = __match_any_sync(0xffffffffu, j);
+    if (j >= 0) {
+      const int pos = mine[j] + __popc(m & lt);
+      list[pos] = make_uint2(static_cast<uint32_t>(sig) | (static_cast<uint32_t>(nz) << 26), __float_as_uint(c));
+    }
+    __syncwarp();
+    if (j >= 0 && (m & lt) == 0) mine[j] += __popc(m);
+    __syncwarp();
   }
 }
 
@@ -1049,7 +1089,11 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
-    scatter_kernel<<<T, 32, K * sizeof(int), st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
+    const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sc_smem)),
+                  "dlsh_mod_update: attribute");
+    scatter_kernel<<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
     ++launches;
   }
   void (*accum)(const float*, const uint16_t*, const float*, int, int, const int*, const int*, int, int, int,
