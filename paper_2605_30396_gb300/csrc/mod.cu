@@ -397,14 +397,31 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 4 : 3)
     }
     float dh = 0.f, dl = 0.f;  // G[j][j]
     constexpr int SH = SMAX / 2;
+    // the next step's list record is loaded one step ahead, and its signal row
+    // and code slots are prefetched into L2 while this step computes
+    uint2 rec_next = make_uint2(0u, 0u);
+    if (q0 + pe < q1) rec_next = list[q0 + pe];
     for (int eb = q0; eb < q1; eb += 16) {
       const int e = eb + pe;
       const bool act = e < q1;
+      const uint2 rec = rec_next;
+      if (eb + 16 + pe < q1) {
+        rec_next = list[eb + 16 + pe];
+        const long long sn = static_cast<long long>(rec_next.x & 0x3FFFFFFu);
+        const char* xr = reinterpret_cast<const char*>(X + sn * DLSH_D);
+        if (sub == 0) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(xr));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + 92));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(xr + 176));
+        } else {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(idx + sn * s));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(coef + sn * s));
+        }
+      }
       long long sig = 0;
       int nz = 0;
       float a = 0.f;
       if (act) {
-        const uint2 rec = list[e];
         sig = static_cast<long long>(rec.x & 0x3FFFFFFu);
         nz = static_cast<int>(rec.x >> 26);
         a = __uint_as_float(rec.y);
