@@ -500,8 +500,16 @@ def main():
         MUd = torch.empty_like(MU)
         Dd = torch.empty_like(Dcur)
         copy = torch.cuda.Stream()
-        nch = 4 if N >= 400_000 else 1
-        bnd = [N * c // nch for c in range(nch + 1)]
+        # chunk edges on whole waves of the encoder (one 128-signal tile per
+        # SM), the first chunk small so that the encode starts early
+        wave = 128 * torch.cuda.get_device_properties(0).multi_processor_count
+        if N >= 40 * wave:
+            first = 8 * wave
+            rest = (N - first) // (3 * wave) * wave
+            bnd = [0, first, first + rest, first + 2 * rest, N]
+        else:
+            bnd = [0, N]
+        nch = len(bnd) - 1
         reps = max(1, min(3, a.steps))
         for rep in range(reps + 1):  # the first repetition is an untimed warm-up
             if rep == 1:
