@@ -912,40 +912,56 @@ __global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, 
 // 8 x 48 output tiles (K/8 CTAs, so the FP64 pipes of every SM take part);
 // thread (row tid / 24, columns tid % 24 and tid % 24 + 24); k in chunks of 32.
 constexpr int RS_ROWS = 8;
-__global__ void __launch_bounds__(192) residual_kernel(const double* __restrict__ M,
-                                                       const double* __restrict__ dsc, int K,
-                                                       const double* __restrict__ Zs,
-                                                       const double* __restrict__ Xs,
-                                                       float* __restrict__ R32) {
+constexpr int RS_T = 256;   // four groups of 64 threads split each k chunk
+__global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict__ M,
+                                                        const double* __restrict__ dsc, int K,
+                                                        const double* __restrict__ Zs,
+                                                        const double* __restrict__ Xs,
+                                                        float* __restrict__ R32) {
   __shared__ double Ms[RS_ROWS][33];
-  __shared__ double Xt[32][RW];
+  __shared__ double Xt[32][RW + 1];
+  __shared__ double red[4][RS_ROWS][RW];
   const int j0 = blockIdx.x * RS_ROWS;
-  const int tr = threadIdx.x / 24, tc = threadIdx.x % 24;
-  double acc0 = 0.0, acc1 = 0.0;
+  const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
+  const int r0 = (t >> 4) * 2, c0 = (t & 15) * 3;  // 2 rows x 3 columns per thread
+  double acc[2][3] = {};
   for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int f = threadIdx.x; f < RS_ROWS * 32; f += 192) {
-      const int r = f / 32, c = f % 32;
+    {
+      const int r = threadIdx.x / 32, c = threadIdx.x % 32;
       Ms[r][c] = (j0 + r < K && k0 + c < K) ? M[static_cast<size_t>(j0 + r) * K + k0 + c] : 0.0;
     }
-    for (int f = threadIdx.x; f < 32 * RW; f += 192) {
+    for (int f = threadIdx.x; f < 32 * RW; f += RS_T) {
       const int r = f / RW, c = f % RW;
       Xt[r][c] = k0 + r < K ? dsc[k0 + r] * Xs[static_cast<size_t>(k0 + r) * RW + c] : 0.0;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < 32; ++k) {
-      const double m = Ms[tr][k];
-      acc0 = fma(m, Xt[k][tc], acc0);
-      acc1 = fma(m, Xt[k][tc + 24], acc1);
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      const int k = kk * 4 + g;
+      const double m0 = Ms[r0][k], m1 = Ms[r0 + 1][k];
+      const double x0 = Xt[k][c0], x1 = Xt[k][c0 + 1], x2 = Xt[k][c0 + 2];
+      acc[0][0] = fma(m0, x0, acc[0][0]);
+      acc[0][1] = fma(m0, x1, acc[0][1]);
+      acc[0][2] = fma(m0, x2, acc[0][2]);
+      acc[1][0] = fma(m1, x0, acc[1][0]);
+      acc[1][1] = fma(m1, x1, acc[1][1]);
+      acc[1][2] = fma(m1, x2, acc[1][2]);
     }
     __syncthreads();
   }
-  const int j = j0 + tr;
-  if (j < K) {
-    const double dj = dsc[j];
-    R32[static_cast<size_t>(j) * RW + tc] = static_cast<float>(Zs[static_cast<size_t>(j) * RW + tc] - dj * acc0);
-    R32[static_cast<size_t>(j) * RW + tc + 24] =
-        static_cast<float>(Zs[static_cast<size_t>(j) * RW + tc + 24] - dj * acc1);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) red[g][r0 + i][c0 + jj] = acc[i][jj];
+  __syncthreads();
+  // the four k groups in a fixed order
+  for (int f = threadIdx.x; f < RS_ROWS * RW; f += RS_T) {
+    const int r = f / RW, c = f % RW;
+    const int j = j0 + r;
+    if (j < K) {
+      const double sum = ((red[0][r][c] + red[1][r][c]) + red[2][r][c]) + red[3][r][c];
+      R32[static_cast<size_t>(j) * RW + c] = static_cast<float>(Zs[static_cast<size_t>(j) * RW + c] - dsc[j] * sum);
+    }
   }
 }
 
@@ -1169,7 +1185,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   const int tr_grid = (K + 7) / 8;
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
-      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, 192, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
+      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, RS_T, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
       ++launches;
     }
     trmm_kernel<false><<<tr_grid, 256, 0, st>>>(w.W32, K, w.R32, w.Y32, nullptr);
