@@ -50,7 +50,7 @@ struct Ws {
   int* atom_start; // K + 1
   uint2* list;     // N*s atom-major records: (signal | nnz << 26, coefficient bits)
   double* M;       // K x K: G + lambda I (FP64, kept for the refinement residuals)
-  double* Z;       // K x RW right-hand sides (B^T + lambda D_old)
+  double* Z;       // K x RW: B^T (lambda D_old is added where Z is read)
   double* lam;     // [0] lambda
   double* dsc;     // K: Jacobi scale 1 / sqrt(M_jj)
   float* A32;      // K x K: S M S, then its FP32 Cholesky factor (lower)
@@ -601,11 +601,9 @@ static int accum_warps(int K, int s, size_t* smem) {
   return 0;
 }
 
-// ---- 5a. lambda = 1e-6 trace(G)/K; M += lambda I; Z += lambda D_old -----------
-__global__ void ridge_kernel(double* __restrict__ M, double* __restrict__ Z,
-                             const float* __restrict__ D_old, int K, double* lam_out) {
+// ---- 5a. lambda = 1e-6 trace(G)/K (applied where M and Z are read) ----------
+__global__ void ridge_kernel(const double* __restrict__ M, int K, double* lam_out) {
   __shared__ double part[1024];
-  __shared__ double lam_s;
   double acc = 0.0;
   for (int j = threadIdx.x; j < K; j += blockDim.x) acc += M[static_cast<size_t>(j) * K + j];
   part[threadIdx.x] = acc;
@@ -616,34 +614,33 @@ __global__ void ridge_kernel(double* __restrict__ M, double* __restrict__ Z,
   }
   if (threadIdx.x == 0) {
     const double tr = part[0];
-    lam_s = tr > 0.0 ? RIDGE_REL * tr / K : RIDGE_REL;
-    *lam_out = lam_s;
-  }
-  __syncthreads();
-  const double lam = lam_s;
-  for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    M[static_cast<size_t>(j) * K + j] += lam;
-    for (int q = 0; q < DLSH_D; ++q)
-      Z[static_cast<size_t>(j) * RW + q] += lam * static_cast<double>(D_old[static_cast<size_t>(j) * DLSH_D + q]);
+    *lam_out = tr > 0.0 ? RIDGE_REL * tr / K : RIDGE_REL;
   }
 }
 
 // ---- 5b. Jacobi scaling: S = diag(M)^-1/2, A = S M S (FP32, lower), Zs = S Z --
 // One CTA per row j.  A has a unit diagonal, which keeps the FP32 factorisation
 // well scaled; the refinement below works on the same scaled system in FP64.
-__global__ void scale_kernel(const double* __restrict__ M, const double* __restrict__ Z, int K,
+// M and Z stay as accumulated; lambda enters here and in the residuals:
+// (M + lambda I) and (Z + lambda D_old).
+__global__ void scale_kernel(const double* __restrict__ M, const double* __restrict__ Z,
+                             const float* __restrict__ D_old, const double* __restrict__ lamp, int K,
                              double* __restrict__ dsc, float* __restrict__ A,
                              double* __restrict__ Zs, float* __restrict__ R32,
                              double* __restrict__ Xs) {
   const int j = blockIdx.x;
-  const double dj = 1.0 / sqrt(M[static_cast<size_t>(j) * K + j]);
+  const double lam = *lamp;
+  const double dj = 1.0 / sqrt(M[static_cast<size_t>(j) * K + j] + lam);
   if (threadIdx.x == 0) dsc[j] = dj;
   for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-    const double dk = 1.0 / sqrt(M[static_cast<size_t>(k) * K + k]);
-    A[static_cast<size_t>(j) * K + k] = static_cast<float>(dj * M[static_cast<size_t>(j) * K + k] * dk);
+    const double dk = 1.0 / sqrt(M[static_cast<size_t>(k) * K + k] + lam);
+    const double m = M[static_cast<size_t>(j) * K + k] + (k == j ? lam : 0.0);
+    A[static_cast<size_t>(j) * K + k] = static_cast<float>(dj * m * dk);
   }
   for (int c = threadIdx.x; c < RW; c += blockDim.x) {
-    const double z = c < DLSH_D ? dj * Z[static_cast<size_t>(j) * RW + c] : 0.0;
+    const double z = c < DLSH_D ? dj * (Z[static_cast<size_t>(j) * RW + c] +
+                                        lam * static_cast<double>(D_old[static_cast<size_t>(j) * DLSH_D + c]))
+                                : 0.0;
     Zs[static_cast<size_t>(j) * RW + c] = z;
     R32[static_cast<size_t>(j) * RW + c] = static_cast<float>(z);
     Xs[static_cast<size_t>(j) * RW + c] = 0.0;
@@ -914,6 +911,7 @@ __global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, 
 constexpr int RS_ROWS = 8;
 constexpr int RS_T = 256;   // four groups of 64 threads split each k chunk
 __global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict__ M,
+                                                        const double* __restrict__ lamp,
                                                         const double* __restrict__ dsc, int K,
                                                         const double* __restrict__ Zs,
                                                         const double* __restrict__ Xs,
@@ -922,13 +920,16 @@ __global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict
   __shared__ double Xt[32][RW + 1];
   __shared__ double red[4][RS_ROWS][RW];
   const int j0 = blockIdx.x * RS_ROWS;
+  const double lam = *lamp;
   const int g = threadIdx.x >> 6, t = threadIdx.x & 63;
   const int r0 = (t >> 4) * 2, c0 = (t & 15) * 3;  // 2 rows x 3 columns per thread
   double acc[2][3] = {};
   for (int k0 = 0; k0 < K; k0 += 32) {
     {
       const int r = threadIdx.x / 32, c = threadIdx.x % 32;
-      Ms[r][c] = (j0 + r < K && k0 + c < K) ? M[static_cast<size_t>(j0 + r) * K + k0 + c] : 0.0;
+      Ms[r][c] = (j0 + r < K && k0 + c < K)
+                     ? M[static_cast<size_t>(j0 + r) * K + k0 + c] + (j0 + r == k0 + c ? lam : 0.0)
+                     : 0.0;
     }
     for (int f = threadIdx.x; f < 32 * RW; f += RS_T) {
       const int r = f / RW, c = f % RW;
@@ -1152,11 +1153,11 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
                                                                  P * K, w.seg_start, w.list, w.Gp, w.Bp);
   }
   seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, P, w.M, w.Z);
-  ridge_kernel<<<1, 1024, 0, st>>>(w.M, w.Z, D_old, K, w.lam);
+  ridge_kernel<<<1, 1024, 0, st>>>(w.M, K, w.lam);
   launches += 4;
   // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
   // kRefine FP32 solves with FP64 residuals in between
-  scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
+  scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, D_old, w.lam, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
   ++launches;
   {
     static int coop_grid = 0;
@@ -1185,7 +1186,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   const int tr_grid = (K + 7) / 8;
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
-      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, RS_T, 0, st>>>(w.M, w.dsc, K, w.Zs, w.Xs, w.R32);
+      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, RS_T, 0, st>>>(w.M, w.lam, w.dsc, K, w.Zs, w.Xs, w.R32);
       ++launches;
     }
     trmm_kernel<false><<<tr_grid, 256, 0, st>>>(w.W32, K, w.R32, w.Y32, nullptr);
