@@ -6,10 +6,11 @@
 // GPU design:
 //   gemm_kernel     tcgen05 BF16 GEMM, C = A B^T with FP32 accumulation in TMEM.
 //                   Operands are read with arbitrary row/column strides (so
-//                   transposed activations need no copies) and staged by the
-//                   threads into the canonical no-swizzle K-major layout; two
-//                   shared-memory stages overlap the next k-tile's loads with
-//                   the current MMAs.  Epilogues: store (split-K partials), +bias,
+//                   transposed activations need no copies) and staged into the
+//                   canonical no-swizzle K-major layout (cp.async 16-byte copies
+//                   where a row's 8 k values are contiguous, else by the
+//                   threads); three shared-memory stages keep the loads two
+//                   k-tiles ahead of the MMAs.  Epilogues: store (split-K partials), +bias,
 //                   +bias with GELU (stores the pre-activation for backward).
 //   small kernels   input normalisation, BCE-with-logits gradient and loss,
 //                   GELU backward, bias gradients, split-K reduction, Adam.
@@ -32,6 +33,7 @@ constexpr int GM = 128;  // tile rows = MMA M
 constexpr int GN = 128;  // tile cols = MMA N
 constexpr int GK = 64;   // k-tile: four MMAs of K = 16
 constexpr int GT = 128;  // threads per GEMM CTA
+constexpr int NS = 3;    // operand stages (loads run NS - 1 k-tiles ahead)
 constexpr uint32_t A_STAGE = GM * GK * 2;  // 16 KB
 constexpr uint32_t B_STAGE = GN * GK * 2;  // 16 KB
 
@@ -70,18 +72,22 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const Mat& X, int r0, i
     for (int c = t; c < ROWS * (GK / 8); c += GT) {
       const int kb = c / ROWS, r = c - kb * ROWS;
       const int row = r0 + r, k = k0 + kb * 8;
-      uint4 v = make_uint4(0, 0, 0, 0);
-      if (row < nrows) {
-        const __nv_bfloat16* src = X.p + static_cast<long long>(row) * X.srow + k;
-        if (k + 8 <= kend) {
-          v = *reinterpret_cast<const uint4*>(src);
-        } else {
+      uint8_t* d = dst + kb * (ROWS * 16) + r * 16;
+      if (row < nrows && k + 8 <= kend) {
+        // asynchronous 16-byte copy, completed by the caller's cp.async wait
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(d)),
+                     "l"(X.p + static_cast<long long>(row) * X.srow + k)
+                     : "memory");
+      } else {
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (row < nrows && k < kend) {
+          const __nv_bfloat16* src = X.p + static_cast<long long>(row) * X.srow + k;
           __nv_bfloat16 tmp[8];
           for (int e = 0; e < 8; ++e) tmp[e] = (k + e < kend) ? src[e] : __float2bfloat16(0.f);
           v = *reinterpret_cast<uint4*>(tmp);
         }
+        *reinterpret_cast<uint4*>(d) = v;
       }
-      *reinterpret_cast<uint4*>(dst + kb * (ROWS * 16) + r * 16) = v;
     }
   } else if (rvec) {
     // chunk = 8 consecutive rows at one k; scattered into 8 core-matrix rows
@@ -115,17 +121,17 @@ __device__ __forceinline__ void stage_tile(uint8_t* dst, const Mat& X, int r0, i
 
 __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmArgs g) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* As = smem;                       // 2 stages
-  uint8_t* Bs = smem + 2 * A_STAGE;         // 2 stages
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * A_STAGE + 2 * B_STAGE);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint8_t* As = smem;                        // NS stages
+  uint8_t* Bs = smem + NS * A_STAGE;         // NS stages
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NS * (A_STAGE + B_STAGE));
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + NS);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.y * GM, n0 = blockIdx.x * GN;
   const int kbeg = blockIdx.z * g.klen;
   const int kend = kbeg + g.klen < g.Kd ? kbeg + g.klen : g.Kd;
+  const int nkt = kend > kbeg ? (kend - kbeg + GK - 1) / GK : 0;
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int q = 0; q < NS; ++q) mbar_init(&bar[q], 1);
     fence_mbar_init();
   }
   if (warp == 0) {
@@ -137,44 +143,57 @@ __global__ void __launch_bounds__(GT) gemm_kernel(const __grid_constant__ GemmAr
   tc_fence_after();
   const uint32_t tmem = *tslot;
   constexpr uint32_t idesc = umma_idesc(1, 1, GM, GN);
-  uint32_t ph[2] = {0, 0};
+  auto stage = [&](int t) {
+    const int sl = t % NS, k0 = kbeg + t * GK;
+    stage_tile<GM>(As + sl * A_STAGE, g.A, m0, g.M, k0, kend);
+    stage_tile<GN>(Bs + sl * B_STAGE, g.B, n0, g.N, k0, kend);
+  };
+  // k-tile t lands in slot t % NS; its MMAs' completion is phase t / NS of that
+  // slot's barrier.  Loads run NS - 1 tiles ahead of the MMAs.
+  for (int t = 0; t < NS - 1; ++t) {
+    if (t < nkt) stage(t);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   bool ok = true;
-  int nk = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += GK, ++nk) {
-    const int st = nk & 1;
-    if (nk >= 2) {  // the MMAs that read this stage two k-tiles ago are done
-      if (!mbar_wait(&bar[st], ph[st], g.budget)) {
+  for (int nk = 0; nk < nkt; ++nk) {
+    const int nx = nk + NS - 1;
+    if (nx < nkt && nk >= 1) {  // the slot's previous tile (nk - 1) must be consumed
+      const int tp = nk - 1;
+      if (!mbar_wait(&bar[tp % NS], static_cast<uint32_t>((tp / NS) & 1), g.budget)) {
         flag_status(g.status, ST_TIMEOUT);
         ok = false;
       }
-      ph[st] ^= 1u;
     }
     if (__syncthreads_or(!ok)) break;
-    stage_tile<GM>(As + st * A_STAGE, g.A, m0, g.M, k0, kend);
-    stage_tile<GN>(Bs + st * B_STAGE, g.B, n0, g.N, k0, kend);
+    if (nx < nkt) stage(nx);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");  // tile nk has landed
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
-      const uint32_t a = smem_u32(As + st * A_STAGE), b = smem_u32(Bs + st * B_STAGE);
+      const int sl = nk % NS;
+      const uint32_t a = smem_u32(As + sl * A_STAGE), b = smem_u32(Bs + sl * B_STAGE);
 #pragma unroll
       for (int ks = 0; ks < GK / 16; ++ks) {
         const uint64_t ad = umma_smem_desc(a + ks * 2 * (GM * 16), GM * 16, 128);
         const uint64_t bd = umma_smem_desc(b + ks * 2 * (GN * 16), GN * 16, 128);
         umma_bf16(tmem, ad, bd, idesc, (nk > 0 || ks > 0) ? 1u : 0u);
       }
-      tc_commit(&bar[st]);
+      tc_commit(&bar[sl]);
     }
   }
-  // drain: wait for the last commit of each stage still outstanding
-  for (int q = nk >= 2 ? nk - 2 : 0; ok && q < nk; ++q) {
-    const int st = q & 1;
-    if (!mbar_wait(&bar[st], ph[st], g.budget)) {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // drain: the last tile's commit completes after every earlier MMA
+  if (ok && nkt > 0) {
+    const int tl = nkt - 1;
+    if (!mbar_wait(&bar[tl % NS], static_cast<uint32_t>((tl / NS) & 1), g.budget)) {
       flag_status(g.status, ST_TIMEOUT);
       ok = false;
     }
-    ph[st] ^= 1u;
   }
+  const int nk = nkt;
+  __syncthreads();
   tc_fence_after();
   // Epilogue: each warp moves its 32 rows x 32 columns from TMEM through a
   // padded shared-memory tile, so every global store writes 32 consecutive
@@ -360,7 +379,7 @@ static int gemm(const Mat& A, const Mat& B, int M, int N, int Kd, float* C, long
   static bool attr_set = false;
   if (!attr_set) {
     DLSH_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       2 * (A_STAGE + B_STAGE) + 64),
+                                       NS * (A_STAGE + B_STAGE) + 64),
                   "dlsh_mlp: attribute");
     attr_set = true;
   }
@@ -383,7 +402,7 @@ static int gemm(const Mat& A, const Mat& B, int M, int N, int Kd, float* C, long
   g.status = status;
   g.budget = kWaitBudget;
   dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM, splits);
-  gemm_kernel<<<grid, GT, 2 * (A_STAGE + B_STAGE) + 64, st>>>(g);
+  gemm_kernel<<<grid, GT, NS * (A_STAGE + B_STAGE) + 64, st>>>(g);
   count_launches(1);
   return check_launch("dlsh_mlp: gemm");
 }
