@@ -8,11 +8,11 @@
 // GPU design (deterministic, no floating-point atomics):
 //   1. count_kernel     per-tile atom histograms (integer counts)
 //   2. scan kernels     per-atom totals, atom offsets, per-(atom, tile) offsets
-//   3. scatter_kernel   one warp per signal tile writes (signal, coef, nnz) into
+//   3. scatter_kernel   one CTA per signal tile writes (signal, coef, nnz) into
 //                       the atom-major list in signal order (a counting sort)
 //   4. accum_kernel     one CTA per segment of an atom's list: row j of G and
 //                       column j of B.  Each warp owns a fixed slice, one list
-//                       entry per lane; sums are float-float (exact FMA
+//                       entry per lane pair; sums are float-float (exact FMA
 //                       products, two-sum accumulation: about FP64 accuracy
 //                       on the FP32 pipe, since GB300's FP64 units are slow),
 //                       lanes and warps are added in a fixed order
