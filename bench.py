@@ -53,7 +53,8 @@ def parse():
     ap.add_argument("--multi-scale", type=float, default=1.0,
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step",
-                    choices=["step", "encode", "mod", "decode", "propose", "train", "tolerance"],
+                    choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
+                             "tolerance"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -330,6 +331,11 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     if a.leg == "decode":
         api.encode(D, X, s, precision=a.precision, out=out, sync=True)
         fn = lambda: api.decode(D, idx, coef, nnz, means=MU, cam=cam, out=rgb)
+    elif a.leg == "decode_compact":
+        api.encode(D, X, s, precision=a.precision, out=out, sync=True)
+        idx_c, coef_c = api.compact_codes(idx, coef, K, sync=True)
+        ref = api.decode(D, idx, coef, nnz, means=MU, cam=cam, sync=True).clone()
+        fn = lambda: api.decode_compact(D, idx_c, coef_c, nnz, means=MU, cam=cam, out=rgb)
     elif a.leg == "mod":
         api.encode(D, X, s, precision=a.precision, out=out, sync=True)
         fn = lambda: api.mod_update(X, D, idx, coef, nnz, resid)
@@ -362,6 +368,13 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
             "gaussians_per_s": N / (ms * 1e-3)}
     if a.leg == "decode":
         line["GBps"] = N * (12 + 6 * s + 1 + 12) / (ms * 1e-3) / 1e9
+    if a.leg == "decode_compact":
+        ib = 1 if K <= 256 else 2
+        line["GBps"] = N * (12 + (ib + 2) * s + 1 + 12) / (ms * 1e-3) / 1e9
+        line["code_bytes_per_gaussian"] = {"fp32_ell": 6 * s + 1, "compact": (ib + 2) * s + 1}
+        diff = (rgb - ref).double()
+        line["rgb_rms_vs_fp32_decode"] = float(torch.sqrt((diff * diff).mean()).item())
+        line["rgb_rms"] = float(torch.sqrt((ref.double() ** 2).mean()).item())
     print(json.dumps(line))
 
 

@@ -319,6 +319,29 @@ int dlsh_calibrate_fallback(const float* resid_learned, const float* resid_plain
                             float max_ratio, float* tau, void* stream);
 
 /*
+ * Compact code storage (the paper stores each Gaussian's nonzeros and their
+ * indices, Sec. 2.2; here at reduced width): FP16 coefficients and 8-bit atom
+ * indices when K <= 256 (else 16-bit), nnz unchanged.
+ * dlsh_compact_codes converts ELL codes (idx [N x s] uint16, coef [N x s] FP32)
+ * to that form: idx_out [N x s] of idx_bytes (1 or 2) each, coef_out [N x s]
+ * IEEE FP16 bits (round to nearest).  DLSH_ERR_UNSUPPORTED when idx_bytes = 1
+ * and K > 256.
+ * dlsh_decode_compact is dlsh_decode on compact codes: the FP32 dictionary D
+ * is rounded to FP16 as it is staged in shared memory (128 bytes per atom, the
+ * three channels of a basis in one 8-byte word); sums are FP32.  K must not
+ * exceed dlsh_decode_compact_max_k(s) (the shared-memory dictionary, about
+ * 1600 atoms), else DLSH_ERR_UNSUPPORTED.  The result differs from dlsh_decode
+ * by the FP16 rounding of D and of the coefficients only.
+ */
+size_t dlsh_decode_compact_max_k(int s);
+int dlsh_compact_codes(const uint16_t* idx, const float* coef, int64_t N, int s, int K,
+                       void* idx_out, int idx_bytes, uint16_t* coef_out, void* stream, int flags);
+int dlsh_decode_compact(const float* D, int K, int d, const void* idx, int idx_bytes,
+                        const uint16_t* coef_f16, const uint8_t* nnz, int s, int64_t N,
+                        const float* dirs_or_means, const float* cam_pos, float* rgb,
+                        void* stream, int flags);
+
+/*
  * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in
  * Compressed Sparse Column form, one column per Gaussian.  col_ptr [N+1]
  * (int64), row_idx and val have room for N*s entries; col_ptr[N] = total nnz.

@@ -70,6 +70,10 @@ SIGNATURES = {
                                      c_size_t, P, P]),
     "dlsh_csc_workspace_size": (c_size_t, [c_int64]),
     "dlsh_csc_from_ell": (c_int, [P, P, P, c_int64, c_int, P, P, P, P, c_size_t, P, c_int]),
+    "dlsh_decode_compact_max_k": (c_size_t, [c_int]),
+    "dlsh_compact_codes": (c_int, [P, P, c_int64, c_int, c_int, P, c_int, P, P, c_int]),
+    "dlsh_decode_compact": (c_int, [P, c_int, c_int, P, c_int, P, P, c_int, c_int64, P, P, P, P,
+                                    c_int]),
     "dlsh_selftest_workspace_size": (c_size_t, []),
     "dlsh_selftest_bounded_wait": (c_int, [c_int, c_int64, P, c_size_t, P]),
 }

@@ -169,6 +169,38 @@ def decode(D, idx, coef, nnz, dirs=None, means=None, cam=None, sync: bool = Fals
     return rgb.cpu() if host else rgb
 
 
+def compact_codes(idx, coef, K: int, sync: bool = False):
+    """ELL codes -> compact codes: (uint8 indices if K <= 256 else int16, FP16 coefficients)."""
+    N, s = coef.shape
+    ib = 1 if K <= 256 else 2
+    idx_c = torch.empty((N, s), dtype=torch.uint8 if ib == 1 else torch.int16, device=coef.device)
+    coef_c = torch.empty((N, s), dtype=torch.float16, device=coef.device)
+    rc = _lib.lib().dlsh_compact_codes(_p(idx.contiguous()), _p(coef.contiguous()), N, s, K, _p(idx_c), ib,
+                                       _p(coef_c), _stream(), FLAG_SYNC if sync else 0)
+    _check(rc, "dlsh_compact_codes")
+    return idx_c, coef_c
+
+
+def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync: bool = False, out=None):
+    """decode() on compact codes (FP16 coefficients, 8/16-bit indices, FP16 dictionary in shared memory)."""
+    D = _dev_f32(D)
+    N, s = coef_c.shape
+    ib = 1 if idx_c.dtype == torch.uint8 else 2
+    if dirs is not None:
+        dm = _dev_f32(dirs)
+        cam_arr = None
+    else:
+        dm = _dev_f32(means)
+        c = [float(v) for v in (cam.tolist() if hasattr(cam, "tolist") else cam)]
+        cam_arr = (ctypes.c_float * 3)(*c)
+    rgb = out if out is not None else torch.empty((N, 3), dtype=torch.float32, device=coef_c.device)
+    rc = _lib.lib().dlsh_decode_compact(_p(D), D.shape[0], D.shape[1], _p(idx_c.contiguous()), ib,
+                                        _p(coef_c.contiguous()), _p(nnz.contiguous()), s, N, _p(dm), cam_arr,
+                                        _p(rgb), _stream(), FLAG_SYNC if sync else 0)
+    _check(rc, "dlsh_decode_compact")
+    return rgb
+
+
 def mod_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     """One MOD dictionary update; returns D_new (K, 45)."""
     X = _dev_f32(X)

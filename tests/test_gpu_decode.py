@@ -69,3 +69,49 @@ def test_decode_one_sparse_is_scaled_atom(lib):
     ref = coef * osh.sh_eval(D[idx[:, 0]], dirs)
     ok, worst = close_rel(rgb, ref)
     assert ok, worst
+
+
+def _half(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+@pytest.mark.parametrize("N,K,s", [(1, 16, 1), (1000, 256, 8), (4099, 1024, 16), (333, 1100, 4), (700, 200, 32)])
+def test_compact_decode_matches_oracle_on_rounded_inputs(lib, N, K, s):
+    """Compact storage: 8-bit indices for K <= 256 (else 16-bit) and FP16
+    coefficients; the dictionary is rounded to FP16 in shared memory.  The
+    result equals the oracle's decode of the FP16-rounded dictionary and
+    coefficients (FP32 sums), and stays close to the FP32 decode."""
+    rng = np.random.default_rng(N + 3 * K)
+    D = synth.hidden_dictionary(K, 5).astype(np.float32)
+    idx, coef, nnz = _codes(rng, N, K, s)
+    dirs = synth.unit_directions(N, 6)
+    Dt = torch.from_numpy(D).cuda()
+    it = torch.from_numpy(idx.astype(np.int16)).cuda()
+    ct = torch.from_numpy(coef).cuda()
+    nt = torch.from_numpy(nnz).cuda()
+    dt = torch.from_numpy(dirs).cuda()
+    idx_c, coef_c = lib.compact_codes(it, ct, K, sync=True)
+    assert idx_c.dtype == (torch.uint8 if K <= 256 else torch.int16)
+    got_idx = idx_c.cpu().numpy().astype(np.int64) if K <= 256 else lib.idx_as_long(idx_c).cpu().numpy()
+    np.testing.assert_array_equal(got_idx, idx.astype(np.int64))
+    np.testing.assert_array_equal(coef_c.cpu().numpy(), coef.astype(np.float16))
+    rgb = lib.decode_compact(Dt, idx_c, coef_c, nt, dirs=dt, sync=True).cpu().numpy()
+    ref = osh.decode(_half(D), idx, _half(coef), nnz, dirs=dirs)
+    ok, worst = close_rel(rgb, ref)
+    assert ok, worst
+    full = osh.decode(D, idx, coef, nnz, dirs=dirs)
+    scale = np.abs(full).max() + 1e-6
+    assert np.abs(rgb - full).max() <= 5e-3 * scale, np.abs(rgb - full).max() / scale
+
+
+def test_compact_decode_rejects_bad_sizes(lib):
+    from paper_2605_30396_gb300 import _lib as L
+    kmax = L.lib().dlsh_decode_compact_max_k(8)
+    assert 1200 < kmax < 2000
+    t = torch.zeros(8, dtype=torch.float32, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    # 8-bit indices with K > 256, and a dictionary beyond shared memory
+    assert L.lib().dlsh_compact_codes(t.data_ptr(), t.data_ptr(), 1, 8, 300, t.data_ptr(), 1, t.data_ptr(),
+                                      st, 0) != 0
+    assert L.lib().dlsh_decode_compact(t.data_ptr(), kmax + 1, 45, t.data_ptr(), 2, t.data_ptr(), t.data_ptr(),
+                                       8, 1, t.data_ptr(), None, t.data_ptr(), st, 0) != 0
