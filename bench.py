@@ -54,7 +54,7 @@ def parse():
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step",
                     choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
-                             "tolerance"],
+                             "tolerance", "splat"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -427,6 +427,77 @@ def tolerance_leg(a, api, X):
                       "rows": rows}))
 
 
+def splat_leg(a):
+    """Splatting preprocess (project, cull, colour) of N synthetic Gaussians,
+    with the colour read from 45 dense FP32 SH coefficients (the baseline
+    renderer) or from sparse codes and the shared dictionary (Sec. 2.2), for two
+    views: outside the cloud (nearly all Gaussians visible) and inside it (most
+    culled).  Dictionaries: the scene's K = 1024 at s = 8, and the paper's
+    rendering size K = 90 with 12 nonzeros (its mean k is 11.7).  Inputs
+    (>= 300 MB) exceed L2.  Algorithmic HBM bytes per Gaussian: 52 in (mean,
+    scale, rotation, DC) + 40 out (xy, depth, conic, radius, rgb), plus 180 B of
+    SH per visible Gaussian, or the codes of every Gaussian."""
+    import numpy as np
+    import torch
+    from paper_2605_30396_gb300 import api, synth
+    torch.cuda.set_device(0)
+    N = a.N
+    g = [torch.from_numpy(x).cuda() for x in synth.splat_gaussians(N, 11)]
+    sh = (0.2 * torch.randn((N, 45), generator=torch.Generator().manual_seed(12))).cuda()
+    views = {"outside": ((0.4, -3.2, 1.1), (0.0, 0.0, 0.0)), "inside": ((0.15, -0.1, 0.05), (1.0, 0.4, -0.3))}
+    W, H, F = 1920, 1080, 1100.0
+    codes = {}
+    for K, s in ((1024, 8), (90, 12)):
+        D = torch.from_numpy(synth.hidden_dictionary(K, 13).astype(np.float32)).cuda()
+        idx, coef, nnz = synth.random_codes(N, K, s, 14, nnz_min=s)
+        idx_t = torch.from_numpy(idx.astype(np.int16)).cuda()
+        coef_t = torch.from_numpy(coef).cuda()
+        nnz_t = torch.from_numpy(nnz).cuda()
+        idx_c, coef_c = api.compact_codes(idx_t, coef_t, K, sync=True)
+        codes[(K, s)] = (D, idx_t, coef_t, nnz_t, idx_c, coef_c)
+    out = None
+    st = torch.cuda.current_stream()
+    rows = []
+    for view, (eye, target) in views.items():
+        R, t = synth.look_at(eye, target)
+        cam = api.camera(R, t, F, F, W, H, 0.2)
+        cases = [("sh", None, {"sh": sh})]
+        for (K, s), (D, idx_t, coef_t, nnz_t, idx_c, coef_c) in codes.items():
+            cases.append(("codes_fp32", (K, s), {"D": D, "idx": idx_t, "coef": coef_t, "nnz": nnz_t}))
+            cases.append(("codes_compact", (K, s), {"D": D, "idx": idx_c, "coef": coef_c, "nnz": nnz_t}))
+        vis = None
+        for name, ks, kw in cases:
+            fn = lambda: api.preprocess(cam, *g, out=out, **kw)
+            out = fn()
+            torch.cuda.synchronize()
+            if vis is None:
+                vis = float((out["radius"] > 0).double().mean().item())
+            for _ in range(a.warmup):
+                fn()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(a.steps):
+                fn()
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / max(a.steps, 1)
+            if name == "sh":
+                colour_bytes = 180.0 * vis
+            else:
+                K, s = ks
+                colour_bytes = (6 * s + 1) if name == "codes_fp32" else ((1 if K <= 256 else 2) + 2) * s + 1
+            bpg = 92.0 + colour_bytes
+            rows.append({"view": view, "colour": name, "K": ks[0] if ks else None, "s": ks[1] if ks else None,
+                         "visible": vis, "ms": ms, "gaussians_per_s": N / (ms * 1e-3),
+                         "bytes_per_gaussian": bpg, "GBps": N * bpg / (ms * 1e-3) / 1e9})
+        base = next(r["ms"] for r in rows if r["view"] == view and r["colour"] == "sh")
+        for r in rows:
+            if r["view"] == view:
+                r["speedup_vs_sh"] = base / r["ms"]
+    print(json.dumps({"leg": "splat", "N": N, "image": [W, H], "focal": F, "rows": rows}))
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -451,6 +522,8 @@ def main():
         return run_reference(a)
     if a.workload == "multi":
         return run_multi(a)
+    if a.leg == "splat":
+        return splat_leg(a)
     import numpy as np
     import torch
 

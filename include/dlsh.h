@@ -353,6 +353,69 @@ int dlsh_csc_from_ell(const uint16_t* idx, const float* coef,
                       uint16_t* row_idx, float* val, void* ws, size_t ws_bytes,
                       void* stream, int flags);
 
+/* ---- splatting preprocess: project, cull, colour ----------------------------
+ * The per-Gaussian preprocess of a Gaussian-splatting renderer, with the
+ * colour step read either from dense SH (the baseline renderer) or from the
+ * shared dictionary and each Gaussian's nonzeros (the paper's renderer,
+ * Sec. 2.2).  With p_c = R mu + t (camera space, z forward):
+ *   Sigma   = R(q) diag(scale)^2 R(q)^T, q = (w, x, y, z), normalised here;
+ *   J       = [[fx/z, 0, -fx x'/z], [0, fy/z, -fy y'/z]], x' = clamp(x/z, +-1.3 W/(2 fx)),
+ *             y' likewise with H and fy;
+ *   S2      = (J R) Sigma (J R)^T + 0.3 I = [[a, b], [b, c]];
+ *   xy      = (fx x/z + W/2, fy y/z + H/2), depth = z, conic = S2^-1 as (a', b', c');
+ *   radius  = ceil(3 sqrt(mid + sqrt(max(0.1, mid^2 - det)))), mid = (a + c)/2;
+ *   visible = z > z_near, det > 0, and the square of that radius meets the image;
+ *   rgb     = max(0, Y00 dc + sum_b Y_b(v) y[c*15+b] + 0.5), Y00 = 1/(2 sqrt(pi)),
+ *             v = (mu - C)/|mu - C|, C = -R^T t the camera centre,
+ *             y the Gaussian's 45 SH coefficients or D^T alpha from its codes.
+ * A culled Gaussian gets radius 0 and zeros in every other output; its colour
+ * coefficients are not read.  All arrays are device memory, caller-owned;
+ * cam, g and out are HOST pointers to the structs.  quats must be 16-byte and
+ * xy 8-byte aligned.  Code entries with t >= nnz, or an index >= K, count as
+ * zero (as in dlsh_decode).  No workspace.  Results are FP32. */
+typedef struct dlsh_camera {
+  float R[9];         /* world -> camera rotation, row-major */
+  float t[3];         /* world -> camera translation */
+  float fx, fy;       /* focal lengths in pixels (> 0) */
+  int width, height;  /* image size in pixels; the principal point is its centre */
+  float z_near;       /* near plane */
+} dlsh_camera;
+
+typedef struct dlsh_gaussians {
+  const float* means;   /* [N*3] world positions */
+  const float* scales;  /* [N*3] standard deviations along the local axes */
+  const float* quats;   /* [N*4] rotations (w, x, y, z), nonzero */
+  const float* dc;      /* [N*3] DC SH coefficient of each channel */
+  int64_t N;
+} dlsh_gaussians;
+
+typedef struct dlsh_splat_out {
+  float* xy;       /* [N*2] pixel centre */
+  float* depth;    /* [N] camera-space z */
+  float* conic;    /* [N*3] inverse screen covariance (a', b', c') */
+  int32_t* radius; /* [N] pixels; 0 = culled */
+  float* rgb;      /* [N*3] colour */
+} dlsh_splat_out;
+
+/* Colour from dense SH: sh [N*45], channel-major (c*15 + b). */
+int dlsh_preprocess_sh(const dlsh_camera* cam, const dlsh_gaussians* g, const float* sh,
+                       const dlsh_splat_out* out, void* stream, int flags);
+/* Colour from ELL codes (idx [N*s] u16, coef [N*s] FP32, nnz [N]) and the FP32
+ * dictionary D [K*45], held in shared memory: K <= dlsh_preprocess_max_k(s, 0),
+ * else DLSH_ERR_UNSUPPORTED. */
+int dlsh_preprocess_codes(const dlsh_camera* cam, const dlsh_gaussians* g, const float* D, int K,
+                          const uint16_t* idx, const float* coef, const uint8_t* nnz, int s,
+                          const dlsh_splat_out* out, void* stream, int flags);
+/* Colour from compact codes (the dlsh_compact_codes format); D is rounded to
+ * FP16 in shared memory as in dlsh_decode_compact; K <= dlsh_preprocess_max_k(s, 1). */
+int dlsh_preprocess_compact(const dlsh_camera* cam, const dlsh_gaussians* g, const float* D, int K,
+                            const void* idx, int idx_bytes, const uint16_t* coef_f16,
+                            const uint8_t* nnz, int s, const dlsh_splat_out* out, void* stream,
+                            int flags);
+/* Largest K the shared-memory dictionary of the codes (compact = 0) or compact
+ * (compact = 1) preprocess holds at sparsity s; 0 for an invalid s. */
+size_t dlsh_preprocess_max_k(int s, int compact);
+
 /* ---- self-test of the bounded device waits --------------------------------
  * Not part of the method (the paper has no counterpart): every pipelined kernel
  * here waits on mbarriers or a grid barrier with a cycle budget, so that a lost

@@ -90,7 +90,8 @@ def preprocess(means, scales, quats, Rv, tv, fx, fy, W, H, z_near, dc, y=None, D
                coef=None, nnz=None):
     """Per-Gaussian preprocess.  Colour from dense SH y (N, 45) or from codes
     (D, idx, coef, nnz).  Returns dict of xy (N, 2), depth (N,), conic (N, 3),
-    radius (N,) int, rgb (N, 3)."""
+    radius (N,) int, rgb (N, 3), and under "raw" the unmasked z, pixel centre,
+    det and 3 sqrt(lambda_max) from which visibility and the radius were decided."""
     mu = np.asarray(means, dtype=np.float64)
     N = mu.shape[0]
     Rv = np.asarray(Rv, dtype=np.float64)
@@ -122,6 +123,8 @@ def preprocess(means, scales, quats, Rv, tv, fx, fy, W, H, z_near, dc, y=None, D
         "depth": np.where(vis, z, 0.0),
         "conic": np.where(vis[:, None], np.stack([c / dets, -b / dets, a / dets], axis=1), 0.0),
         "radius": np.where(vis, radius, 0).astype(np.int64),
+        "raw": {"z": z, "px": px, "py": py, "det": det, "extent": 3.0 * np.sqrt(np.maximum(lam, 0.0)),
+                "front": front},
     }
     cam = -Rv.T @ tv
     dirs = sh.view_directions(mu, cam)

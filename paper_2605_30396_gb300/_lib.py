@@ -23,6 +23,25 @@ class Scene(ctypes.Structure):
                 ("resid_sq", ctypes.c_void_p)]
 
 
+class Camera(ctypes.Structure):
+    """Mirror of dlsh_camera."""
+    _fields_ = [("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("z_near", ctypes.c_float)]
+
+
+class Gaussians(ctypes.Structure):
+    """Mirror of dlsh_gaussians."""
+    _fields_ = [("means", ctypes.c_void_p), ("scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("dc", ctypes.c_void_p), ("N", ctypes.c_int64)]
+
+
+class SplatOut(ctypes.Structure):
+    """Mirror of dlsh_splat_out."""
+    _fields_ = [("xy", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("conic", ctypes.c_void_p),
+                ("radius", ctypes.c_void_p), ("rgb", ctypes.c_void_p)]
+
+
 SIGNATURES = {
     "dlsh_last_error": (ctypes.c_char_p, []),
     "dlsh_version": (c_int, []),
@@ -74,6 +93,10 @@ SIGNATURES = {
     "dlsh_compact_codes": (c_int, [P, P, c_int64, c_int, c_int, P, c_int, P, P, c_int]),
     "dlsh_decode_compact": (c_int, [P, c_int, c_int, P, c_int, P, P, c_int, c_int64, P, P, P, P,
                                     c_int]),
+    "dlsh_preprocess_sh": (c_int, [P, P, P, P, P, c_int]),
+    "dlsh_preprocess_codes": (c_int, [P, P, P, c_int, P, P, P, c_int, P, P, c_int]),
+    "dlsh_preprocess_compact": (c_int, [P, P, P, c_int, P, c_int, P, P, c_int, P, P, c_int]),
+    "dlsh_preprocess_max_k": (c_size_t, [c_int, c_int]),
     "dlsh_selftest_workspace_size": (c_size_t, []),
     "dlsh_selftest_bounded_wait": (c_int, [c_int, c_int64, P, c_size_t, P]),
 }

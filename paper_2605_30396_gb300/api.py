@@ -201,6 +201,55 @@ def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync:
     return rgb
 
 
+def camera(R, t, fx: float, fy: float, width: int, height: int, z_near: float = 0.2) -> "_lib.Camera":
+    """A dlsh_camera: world -> camera rotation R (3x3, row-major) and translation t."""
+    Rf = [float(v) for v in torch.as_tensor(R, dtype=torch.float64).reshape(9).tolist()]
+    tf = [float(v) for v in torch.as_tensor(t, dtype=torch.float64).reshape(3).tolist()]
+    return _lib.Camera((ctypes.c_float * 9)(*Rf), (ctypes.c_float * 3)(*tf), fx, fy, int(width), int(height),
+                       z_near)
+
+
+def preprocess(cam, means, scales, quats, dc, sh=None, D=None, idx=None, coef=None, nnz=None,
+               sync: bool = False, out=None):
+    """Splatting preprocess (project, cull, colour) of N Gaussians on the device.
+
+    Colour from dense SH `sh` (N, 45), or from codes (D, idx, coef, nnz): FP32
+    `coef` selects the ELL path, FP16 `coef` the compact path (uint8 or int16
+    `idx`).  Returns a dict of xy (N, 2), depth (N,), conic (N, 3), radius (N,)
+    int32 and rgb (N, 3); `out` may supply that dict preallocated."""
+    N = means.shape[0]
+    dev = means.device
+    if out is None:
+        out = {"xy": torch.empty((N, 2), dtype=torch.float32, device=dev),
+               "depth": torch.empty((N,), dtype=torch.float32, device=dev),
+               "conic": torch.empty((N, 3), dtype=torch.float32, device=dev),
+               "radius": torch.empty((N,), dtype=torch.int32, device=dev),
+               "rgb": torch.empty((N, 3), dtype=torch.float32, device=dev)}
+    keep = [t.contiguous() for t in (means, scales, quats, dc)]
+    g = _lib.Gaussians(*(t.data_ptr() for t in keep), N)
+    o = _lib.SplatOut(*(out[k].data_ptr() for k in ("xy", "depth", "conic", "radius", "rgb")))
+    flags = FLAG_SYNC if sync else 0
+    L = _lib.lib()
+    if sh is not None:
+        sh = sh.contiguous()
+        rc = L.dlsh_preprocess_sh(ctypes.byref(cam), ctypes.byref(g), _p(sh), ctypes.byref(o), _stream(), flags)
+        _check(rc, "dlsh_preprocess_sh")
+        return out
+    D = _dev_f32(D)
+    s = coef.shape[1]
+    idx, coef, nnz = idx.contiguous(), coef.contiguous(), nnz.contiguous()
+    if coef.dtype == torch.float16:
+        ib = 1 if idx.dtype == torch.uint8 else 2
+        rc = L.dlsh_preprocess_compact(ctypes.byref(cam), ctypes.byref(g), _p(D), D.shape[0], _p(idx), ib, _p(coef),
+                                       _p(nnz), s, ctypes.byref(o), _stream(), flags)
+        _check(rc, "dlsh_preprocess_compact")
+    else:
+        rc = L.dlsh_preprocess_codes(ctypes.byref(cam), ctypes.byref(g), _p(D), D.shape[0], _p(idx), _p(coef),
+                                     _p(nnz), s, ctypes.byref(o), _stream(), flags)
+        _check(rc, "dlsh_preprocess_codes")
+    return out
+
+
 def mod_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     """One MOD dictionary update; returns D_new (K, 45)."""
     X = _dev_f32(X)

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "host.hpp"
+#include "sh.cuh"
 
 namespace dlsh {
 namespace dec {
@@ -28,35 +29,7 @@ constexpr int SMEM_LIMIT = 232448;
 constexpr int GB = 16;          // Gaussians per warp batch (small batches: more warps fit per SM)
 __host__ __device__ constexpr int warp_floats(int s) { return GB * YS + GB * 3 + GB * s * 2; }
 
-// Real-SH constants of the Cartesian forms below, computed on the host from
-// N_lm = sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) and the associated Legendre
-// polynomials' leading factors.
-struct ShConst {
-  float c[15];
-};
 __constant__ ShConst g_sh;
-
-// Y_b(v) for unit v, basis order b = l*l + l + m - 1 (l = 1..3, m = -l..l),
-// Condon-Shortley phase included in the constants' signs.
-__device__ __forceinline__ void sh_basis(float x, float y, float z, float (&Y)[15]) {
-  const float* c = g_sh.c;
-  const float xx = x * x, yy = y * y, zz = z * z;
-  Y[0] = c[0] * y;
-  Y[1] = c[1] * z;
-  Y[2] = c[2] * x;
-  Y[3] = c[3] * x * y;
-  Y[4] = c[4] * y * z;
-  Y[5] = c[5] * (3.f * zz - 1.f);
-  Y[6] = c[6] * x * z;
-  Y[7] = c[7] * (xx - yy);
-  Y[8] = c[8] * y * (3.f * xx - yy);
-  Y[9] = c[9] * x * y * z;
-  Y[10] = c[10] * y * (5.f * zz - 1.f);
-  Y[11] = c[11] * z * (5.f * zz - 3.f);
-  Y[12] = c[12] * x * (5.f * zz - 1.f);
-  Y[13] = c[13] * z * (xx - yy);
-  Y[14] = c[14] * x * (xx - 3.f * yy);
-}
 
 template <bool SMEM_D>
 __global__ void __launch_bounds__(1024) decode_kernel(
@@ -112,7 +85,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
         }
       }
       float Y[15];
-      sh_basis(vx, vy, vz, Y);
+      sh_basis(g_sh.c, vx, vy, vz, Y);
       if (lane < GB) {
 #pragma unroll
         for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
@@ -247,7 +220,7 @@ __global__ void __launch_bounds__(1024) decode_compact_kernel(
         }
       }
       float Y[15];
-      sh_basis(vx, vy, vz, Y);
+      sh_basis(g_sh.c, vx, vy, vz, Y);
       if (lane < GB) {
 #pragma unroll
         for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
@@ -319,48 +292,12 @@ __global__ void compact_codes_kernel(const uint16_t* __restrict__ idx, const flo
   coef_out[e] = __float2half_rn(coef[e]);
 }
 
-static double factorial(int n) {
-  double f = 1.0;
-  for (int k = 2; k <= n; ++k) f *= k;
-  return f;
-}
-
-static double nlm(int l, int m) {
-  const int am = m < 0 ? -m : m;
-  return sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * factorial(l - am) / factorial(l + am));
-}
-
-// Constants of the Cartesian forms used by sh_basis.  With P_l^m carrying the
-// Condon-Shortley phase: P_1^1 = -sin, P_2^1 = -3z sin, P_2^2 = 3 sin^2,
-// P_3^1 = -1.5 (5z^2-1) sin, P_3^2 = 15 z sin^2, P_3^3 = -15 sin^3, and
-// sin^m(theta) {cos,sin}(m phi) expands to the x/y polynomials of sh_basis.
-static ShConst make_constants() {
-  const double r2 = sqrt(2.0);
-  ShConst k;
-  k.c[0] = static_cast<float>(-r2 * nlm(1, -1));          // y
-  k.c[1] = static_cast<float>(nlm(1, 0));                 // z
-  k.c[2] = static_cast<float>(-r2 * nlm(1, 1));           // x
-  k.c[3] = static_cast<float>(r2 * nlm(2, -2) * 3.0 * 2.0);  // xy   (sin^2 sin 2phi = 2xy)
-  k.c[4] = static_cast<float>(-r2 * nlm(2, -1) * 3.0);    // yz
-  k.c[5] = static_cast<float>(nlm(2, 0) * 0.5);           // 3z^2 - 1
-  k.c[6] = static_cast<float>(-r2 * nlm(2, 1) * 3.0);     // xz
-  k.c[7] = static_cast<float>(r2 * nlm(2, 2) * 3.0);      // x^2 - y^2
-  k.c[8] = static_cast<float>(-r2 * nlm(3, -3) * 15.0);   // y(3x^2 - y^2)
-  k.c[9] = static_cast<float>(r2 * nlm(3, -2) * 15.0 * 2.0);  // xyz
-  k.c[10] = static_cast<float>(-r2 * nlm(3, -1) * 1.5);   // y(5z^2 - 1)
-  k.c[11] = static_cast<float>(nlm(3, 0) * 0.5);          // z(5z^2 - 3)
-  k.c[12] = static_cast<float>(-r2 * nlm(3, 1) * 1.5);    // x(5z^2 - 1)
-  k.c[13] = static_cast<float>(r2 * nlm(3, 2) * 15.0);    // z(x^2 - y^2)
-  k.c[14] = static_cast<float>(-r2 * nlm(3, 3) * 15.0);   // x(x^2 - 3y^2)
-  return k;
-}
-
 static int upload_constants(cudaStream_t st) {
   static thread_local int uploaded_dev = -1;
   int dev = 0;
   DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_decode: cudaGetDevice");
   if (uploaded_dev == dev) return DLSH_OK;
-  const ShConst k = make_constants();
+  const ShConst k = make_sh_constants();
   DLSH_CUDA_TRY(cudaMemcpyToSymbolAsync(g_sh, &k, sizeof(k), 0, cudaMemcpyHostToDevice, st),
                 "dlsh_decode: constants");
   DLSH_CUDA_TRY(cudaStreamSynchronize(st), "dlsh_decode: constants");

@@ -120,3 +120,45 @@ def mlp_params(K: int, seed: int, d_in: int = D_SH, hidden: int = 256):
     b2 = np.zeros(hidden)
     b3 = np.full(K, -np.log(K / 16.0))
     return {"W1": W1, "b1": b1, "W2": W2, "b2": b2, "W3": W3, "b3": b3}
+
+
+def splat_gaussians(N: int, seed: int, log_scale_mean: float = float(np.log(0.01)),
+                    log_scale_std: float = 0.5, dtype=np.float32):
+    """Gaussians of a splatting scene: means ~ U[-1,1]^3, per-axis scales
+    exp(N(log_scale_mean, log_scale_std^2)), unnormalised rotations q ~ N(0, I4)
+    as (w, x, y, z), and DC colours ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    means = rng.uniform(-1.0, 1.0, size=(N, 3))
+    scales = np.exp(rng.normal(log_scale_mean, log_scale_std, size=(N, 3)))
+    quats = rng.standard_normal((N, 4))
+    dc = rng.standard_normal((N, 3))
+    return tuple(a.astype(dtype) for a in (means, scales, quats, dc))
+
+
+def look_at(eye, target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0)):
+    """World -> camera pose (R, t) of a camera at `eye` looking at `target`,
+    camera axes x right, y down, z forward: p_c = R p + t."""
+    eye = np.asarray(eye, dtype=np.float64)
+    f = np.asarray(target, dtype=np.float64) - eye
+    f /= np.linalg.norm(f)
+    up = np.asarray(up, dtype=np.float64)
+    if abs(float(f @ up)) > 0.99 * np.linalg.norm(up):
+        up = np.array([0.0, 1.0, 0.0]) if abs(f[1]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    r = np.cross(f, up)
+    r /= np.linalg.norm(r)
+    d = np.cross(f, r)
+    R = np.stack([r, d, f])
+    return R, -R @ eye
+
+
+def random_codes(N: int, K: int, s: int, seed: int, nnz_min: int = 0):
+    """Random ELL codes: uniform indices (repeats allowed), N(0,1) coefficients,
+    nnz uniform in [nnz_min, s]; slots t >= nnz hold index 0 and coefficient 0."""
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, K, size=(N, s))
+    coef = rng.standard_normal((N, s))
+    nnz = rng.integers(nnz_min, s + 1, size=N)
+    pad = np.arange(s)[None, :] >= nnz[:, None]
+    idx[pad] = 0
+    coef[pad] = 0.0
+    return idx.astype(np.uint16), coef.astype(np.float32), nnz.astype(np.uint8)
