@@ -85,6 +85,11 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
+// a0 b0 + a1 b1 + a2 b2, rounded in a fixed order
+__device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  return fmaf(a0, b0, fmaf(a1, b1, __fmul_rn(a2, b2)));
+}
+
 template <int CM>
 __global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(16) float sm[];
@@ -179,58 +184,66 @@ __global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__
     const bool front = valid && z > p.z_near;
     const float zs = front ? z : 1.f;
     const float xs = front ? x : 0.f, ys = front ? y : 0.f;
-    const float iz = 1.f / zs;
+    // Every product and sum below is rounded explicitly (no contraction left to
+    // the compiler), so the geometry is bit-identical whichever colour source
+    // the kernel is instantiated for.
+    const float iz = __frcp_rn(zs);
     // rotation of the normalised quaternion
-    const float qn = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    const float qw = q.x * qn, qx = q.y * qn, qy = q.z * qn, qz = q.w * qn;
-    const float r00 = 1.f - 2.f * (qy * qy + qz * qz), r01 = 2.f * (qx * qy - qw * qz),
-                r02 = 2.f * (qx * qz + qw * qy);
-    const float r10 = 2.f * (qx * qy + qw * qz), r11 = 1.f - 2.f * (qx * qx + qz * qz),
-                r12 = 2.f * (qy * qz - qw * qx);
-    const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx),
-                r22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float qn = rsqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, fmaf(q.z, q.z, __fmul_rn(q.w, q.w)))));
+    const float qw = __fmul_rn(q.x, qn), qx = __fmul_rn(q.y, qn), qy = __fmul_rn(q.z, qn), qz = __fmul_rn(q.w, qn);
+    const float r00 = __fsub_rn(1.f, __fmul_rn(2.f, fmaf(qy, qy, __fmul_rn(qz, qz))));
+    const float r11 = __fsub_rn(1.f, __fmul_rn(2.f, fmaf(qx, qx, __fmul_rn(qz, qz))));
+    const float r22 = __fsub_rn(1.f, __fmul_rn(2.f, fmaf(qx, qx, __fmul_rn(qy, qy))));
+    const float r01 = __fmul_rn(2.f, fmaf(qx, qy, -__fmul_rn(qw, qz)));
+    const float r02 = __fmul_rn(2.f, fmaf(qx, qz, __fmul_rn(qw, qy)));
+    const float r10 = __fmul_rn(2.f, fmaf(qx, qy, __fmul_rn(qw, qz)));
+    const float r12 = __fmul_rn(2.f, fmaf(qy, qz, -__fmul_rn(qw, qx)));
+    const float r20 = __fmul_rn(2.f, fmaf(qx, qz, -__fmul_rn(qw, qy)));
+    const float r21 = __fmul_rn(2.f, fmaf(qy, qz, __fmul_rn(qw, qx)));
     // M = R(q) diag(s); Sigma = M M^T
-    const float m00 = r00 * sx, m01 = r01 * sy, m02 = r02 * sz;
-    const float m10 = r10 * sx, m11 = r11 * sy, m12 = r12 * sz;
-    const float m20 = r20 * sx, m21 = r21 * sy, m22 = r22 * sz;
-    const float S00 = m00 * m00 + m01 * m01 + m02 * m02;
-    const float S01 = m00 * m10 + m01 * m11 + m02 * m12;
-    const float S02 = m00 * m20 + m01 * m21 + m02 * m22;
-    const float S11 = m10 * m10 + m11 * m11 + m12 * m12;
-    const float S12 = m10 * m20 + m11 * m21 + m12 * m22;
-    const float S22 = m20 * m20 + m21 * m21 + m22 * m22;
+    const float m00 = __fmul_rn(r00, sx), m01 = __fmul_rn(r01, sy), m02 = __fmul_rn(r02, sz);
+    const float m10 = __fmul_rn(r10, sx), m11 = __fmul_rn(r11, sy), m12 = __fmul_rn(r12, sz);
+    const float m20 = __fmul_rn(r20, sx), m21 = __fmul_rn(r21, sy), m22 = __fmul_rn(r22, sz);
+    const float S00 = dot3(m00, m01, m02, m00, m01, m02);
+    const float S01 = dot3(m00, m01, m02, m10, m11, m12);
+    const float S02 = dot3(m00, m01, m02, m20, m21, m22);
+    const float S11 = dot3(m10, m11, m12, m10, m11, m12);
+    const float S12 = dot3(m10, m11, m12, m20, m21, m22);
+    const float S22 = dot3(m20, m21, m22, m20, m21, m22);
     // T = J R (2 x 3)
-    const float cx = fminf(fmaxf(xs * iz, -p.limx), p.limx);
-    const float cy = fminf(fmaxf(ys * iz, -p.limy), p.limy);
-    const float j00 = p.fx * iz, j02 = -p.fx * cx * iz;
-    const float j11 = p.fy * iz, j12 = -p.fy * cy * iz;
-    const float t00 = j00 * R[0] + j02 * R[6], t01 = j00 * R[1] + j02 * R[7], t02 = j00 * R[2] + j02 * R[8];
-    const float t10 = j11 * R[3] + j12 * R[6], t11 = j11 * R[4] + j12 * R[7], t12 = j11 * R[5] + j12 * R[8];
+    const float cx = fminf(fmaxf(__fmul_rn(xs, iz), -p.limx), p.limx);
+    const float cy = fminf(fmaxf(__fmul_rn(ys, iz), -p.limy), p.limy);
+    const float j00 = __fmul_rn(p.fx, iz), j02 = -__fmul_rn(__fmul_rn(p.fx, cx), iz);
+    const float j11 = __fmul_rn(p.fy, iz), j12 = -__fmul_rn(__fmul_rn(p.fy, cy), iz);
+    const float t00 = fmaf(j00, R[0], __fmul_rn(j02, R[6])), t01 = fmaf(j00, R[1], __fmul_rn(j02, R[7])),
+                t02 = fmaf(j00, R[2], __fmul_rn(j02, R[8]));
+    const float t10 = fmaf(j11, R[3], __fmul_rn(j12, R[6])), t11 = fmaf(j11, R[4], __fmul_rn(j12, R[7])),
+                t12 = fmaf(j11, R[5], __fmul_rn(j12, R[8]));
     // U = T Sigma; Sigma2D = U T^T
-    const float u00 = t00 * S00 + t01 * S01 + t02 * S02;
-    const float u01 = t00 * S01 + t01 * S11 + t02 * S12;
-    const float u02 = t00 * S02 + t01 * S12 + t02 * S22;
-    const float u10 = t10 * S00 + t11 * S01 + t12 * S02;
-    const float u11 = t10 * S01 + t11 * S11 + t12 * S12;
-    const float u12 = t10 * S02 + t11 * S12 + t12 * S22;
-    const float ca = u00 * t00 + u01 * t01 + u02 * t02 + kLowpass;
-    const float cb = u00 * t10 + u01 * t11 + u02 * t12;
-    const float cc = u10 * t10 + u11 * t11 + u12 * t12 + kLowpass;
-    const float det = ca * cc - cb * cb;
+    const float u00 = dot3(t00, t01, t02, S00, S01, S02);
+    const float u01 = dot3(t00, t01, t02, S01, S11, S12);
+    const float u02 = dot3(t00, t01, t02, S02, S12, S22);
+    const float u10 = dot3(t10, t11, t12, S00, S01, S02);
+    const float u11 = dot3(t10, t11, t12, S01, S11, S12);
+    const float u12 = dot3(t10, t11, t12, S02, S12, S22);
+    const float ca = __fadd_rn(dot3(u00, u01, u02, t00, t01, t02), kLowpass);
+    const float cb = dot3(u00, u01, u02, t10, t11, t12);
+    const float cc = __fadd_rn(dot3(u10, u11, u12, t10, t11, t12), kLowpass);
+    const float det = fmaf(ca, cc, -__fmul_rn(cb, cb));
     const bool ok = front && det > 0.f;
-    const float mid = 0.5f * (ca + cc);
-    const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
-    const float rad = ceilf(3.f * sqrtf(fmaxf(lam, 0.f)));
-    const float px = p.fx * xs * iz + p.hw;
-    const float py = p.fy * ys * iz + p.hh;
+    const float mid = __fmul_rn(0.5f, __fadd_rn(ca, cc));
+    const float lam = __fadd_rn(mid, __fsqrt_rn(fmaxf(0.1f, fmaf(mid, mid, -det))));
+    const float rad = ceilf(__fmul_rn(3.f, __fsqrt_rn(fmaxf(lam, 0.f))));
+    const float px = fmaf(__fmul_rn(p.fx, xs), iz, p.hw);
+    const float py = fmaf(__fmul_rn(p.fy, ys), iz, p.hh);
     const bool vis = ok && px + rad > 0.f && px - rad < p.W && py + rad > 0.f && py - rad < p.H;
     if (valid) {
-      const float idet = vis ? 1.f / det : 0.f;
+      const float idet = vis ? __frcp_rn(det) : 0.f;
       p.xy[g] = vis ? make_float2(px, py) : make_float2(0.f, 0.f);
       p.depth[g] = vis ? z : 0.f;
-      p.conic[g * 3 + 0] = vis ? cc * idet : 0.f;
-      p.conic[g * 3 + 1] = vis ? -cb * idet : 0.f;
-      p.conic[g * 3 + 2] = vis ? ca * idet : 0.f;
+      p.conic[g * 3 + 0] = vis ? __fmul_rn(cc, idet) : 0.f;
+      p.conic[g * 3 + 1] = vis ? -__fmul_rn(cb, idet) : 0.f;
+      p.conic[g * 3 + 2] = vis ? __fmul_rn(ca, idet) : 0.f;
       p.radius[g] = vis ? static_cast<int>(rad) : 0;
     }
     // view direction and basis values
