@@ -439,7 +439,7 @@ def splat_leg(a):
     SH per visible Gaussian, or the codes of every Gaussian."""
     import numpy as np
     import torch
-    from paper_2605_30396_gb300 import api, synth
+    from paper_2605_30396_gb300 import _lib, api, synth
     torch.cuda.set_device(0)
     N = a.N
     g = [torch.from_numpy(x).cuda() for x in synth.splat_gaussians(N, 11)]
@@ -463,7 +463,8 @@ def splat_leg(a):
         cam = api.camera(R, t, F, F, W, H, 0.2)
         cases = [("sh", None, {"sh": sh})]
         for (K, s), (D, idx_t, coef_t, nnz_t, idx_c, coef_c) in codes.items():
-            cases.append(("codes_fp32", (K, s), {"D": D, "idx": idx_t, "coef": coef_t, "nnz": nnz_t}))
+            if K <= _lib.lib().dlsh_preprocess_max_k(s, 0):  # FP32 table in shared memory
+                cases.append(("codes_fp32", (K, s), {"D": D, "idx": idx_t, "coef": coef_t, "nnz": nnz_t}))
             cases.append(("codes_compact", (K, s), {"D": D, "idx": idx_c, "coef": coef_c, "nnz": nnz_t}))
         vis = None
         for name, ks, kw in cases:

@@ -41,8 +41,8 @@ namespace spl {
 enum : int { CM_SH = 0, CM_F32 = 1, CM_C8 = 2, CM_C16 = 3 };
 
 constexpr int GB = 32;         // Gaussians per warp batch
-constexpr int ROW = 45;        // FP32 dictionary row (plus 16 zero words after the last)
-constexpr int YS = 17;         // basis slot per Gaussian (15 values, nnz in word 15)
+constexpr int ROW = 45;        // dense SH row
+constexpr int YS = 16;         // basis slot per Gaussian (15 values and a zero)
 constexpr int SMEM_LIMIT = 232448;
 constexpr float kLowpass = 0.3f;
 constexpr float kClamp = 1.3f;
@@ -73,7 +73,10 @@ struct Params {
 };
 
 __host__ __device__ constexpr int dense_warp_floats() { return GB * ROW + GB; }
-__host__ __device__ constexpr int codes_warp_floats(int sp) { return GB * YS + GB * 3 + GB * sp * 2 + GB; }
+__host__ __device__ constexpr int codes_warp_floats(int sp) { return GB * YS + GB * 3 + GB * sp * 2 + 2 * GB; }
+// shared-memory dictionary: 16 slots per atom (basis b < 15, then zeros) of
+// (R, G, B, 0) as FP32 (256 bytes) or FP16 (128 bytes)
+__host__ __device__ constexpr int dict_floats(int cm, int K) { return cm == 1 ? K * 64 : cm >= 2 ? K * 32 : 0; }
 
 inline int staged_slots(int s) {
   int sp = (s + 1) & ~1;
@@ -91,45 +94,57 @@ __device__ __forceinline__ float dot3(float a0, float a1, float a2, float b0, fl
 }
 
 template <int CM>
-__global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__ Params p) {
+__global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant__ Params p) {
   extern __shared__ __align__(16) float sm[];
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const int K = p.K, s = p.s, sp = p.sp;
 
-  // ---- dictionary in shared memory (codes variants)
-  int dwords = 0;
-  if (CM == CM_F32) {
-    dwords = (K * ROW + 16 + 3) & ~3;
-    for (int f = threadIdx.x; f < dwords; f += blockDim.x) sm[f] = f < K * ROW ? p.D[f] : 0.f;
-  } else if (CM == CM_C8 || CM == CM_C16) {
-    dwords = K * 32;
-    uint2* Ds = reinterpret_cast<uint2*>(sm);
-    for (int f = threadIdx.x; f < K * 16; f += blockDim.x) {
-      const int j = f >> 4, b = f & 15;
-      uint2 v = make_uint2(0u, 0u);
-      if (b < 15) {
-        const float* dr = p.D + static_cast<size_t>(j) * DLSH_D + b;
-        const __half2 rg = __floats2half2_rn(dr[0], dr[15]);
-        const __half2 bz = __floats2half2_rn(dr[30], 0.f);
-        v.x = *reinterpret_cast<const uint32_t*>(&rg);
-        v.y = *reinterpret_cast<const uint32_t*>(&bz);
+  // ---- dictionary in shared memory (codes variants); four slots per thread
+  // per round, their loads issued before any is converted
+  const int dwords = dict_floats(CM, K);
+  if (CM != CM_SH) {
+    for (int f0 = threadIdx.x; f0 < K * 16; f0 += 4 * blockDim.x) {
+      float v[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * blockDim.x, j = f >> 4, b = f & 15;
+        const bool live = f < K * 16 && b < 15;
+        const float* dr = p.D + static_cast<size_t>(live ? j : 0) * DLSH_D + (live ? b : 0);
+        v[u][0] = live ? dr[0] : 0.f;
+        v[u][1] = live ? dr[15] : 0.f;
+        v[u][2] = live ? dr[30] : 0.f;
       }
-      Ds[f] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * blockDim.x;
+        if (f >= K * 16) break;
+        if (CM == CM_F32) {
+          reinterpret_cast<float4*>(sm)[f] = make_float4(v[u][0], v[u][1], v[u][2], 0.f);
+        } else {
+          const __half2 rg = __floats2half2_rn(v[u][0], v[u][1]);
+          const __half2 bz = __floats2half2_rn(v[u][2], 0.f);
+          reinterpret_cast<uint2*>(sm)[f] =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&rg), *reinterpret_cast<const uint32_t*>(&bz));
+        }
+      }
     }
+    __syncthreads();
   }
-  if (CM != CM_SH) __syncthreads();
 
   float* wsm = sm + dwords + warp * (CM == CM_SH ? dense_warp_floats() : codes_warp_floats(sp));
-  // dense: stage [32 x 45] + vlist[32];  codes: Ys [32 x 17], outs [32 x 3], codes [32 x sp] uint2, vlist[32]
+  // dense: stage [32 x 45], vlist[32]
+  // codes: Ys [32 x 16], outs [32 x 3], codes [32 x sp] uint2, vlist[32], nzs[32]
   float* stage = wsm;
   float* Ys = wsm;
   float* outs = wsm + GB * YS;
   uint2* cpk = reinterpret_cast<uint2*>(wsm + GB * YS + GB * 3);
   int* vlist = reinterpret_cast<int*>(CM == CM_SH ? wsm + GB * ROW : wsm + GB * YS + GB * 3 + GB * sp * 2);
+  int* nzs = vlist + GB;
 
-  const int hl = lane & 15, h = lane >> 4;
+  // phase B of the codes variants: a quarter-warp (8 lanes) per Gaussian
+  const int ql = lane & 7, grp = lane >> 3;
   const int64_t N = p.N;
   const int64_t nbatch = (N + GB - 1) / GB;
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
@@ -141,21 +156,35 @@ __global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__
 
     // codes of the whole batch, staged as (index, coefficient bits) pairs
     if (CM != CM_SH) {
-      for (int f = lane; f < nb * s; f += 32) {
-        const int gl = s == 1 ? f : static_cast<int>(__umulhi(static_cast<uint32_t>(f), p.sdiv));
-        const int t = f - gl * s;
-        const int64_t e = base * s + f;
-        uint32_t j;
-        float a;
-        if (CM == CM_F32) {
-          j = static_cast<const uint16_t*>(p.idx)[e];
-          a = static_cast<const float*>(p.coef)[e];
-        } else {
-          j = CM == CM_C8 ? static_cast<uint32_t>(static_cast<const uint8_t*>(p.idx)[e])
-                          : static_cast<uint32_t>(static_cast<const uint16_t*>(p.idx)[e]);
-          a = __half2float(static_cast<const __half*>(p.coef)[e]);
+      // element f = lane + 32 k of the batch (k < s); four loads in flight per lane
+      for (int k0 = 0; k0 < s; k0 += 4) {
+        uint32_t jj[4];
+        float aa[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int f = lane + 32 * (k0 + u);
+          jj[u] = 0;
+          aa[u] = 0.f;
+          if (k0 + u < s && f < nb * s) {
+            const int64_t e = base * s + f;
+            if (CM == CM_F32) {
+              jj[u] = static_cast<const uint16_t*>(p.idx)[e];
+              aa[u] = static_cast<const float*>(p.coef)[e];
+            } else {
+              jj[u] = CM == CM_C8 ? static_cast<uint32_t>(static_cast<const uint8_t*>(p.idx)[e])
+                                  : static_cast<uint32_t>(static_cast<const uint16_t*>(p.idx)[e]);
+              aa[u] = __half2float(static_cast<const __half*>(p.coef)[e]);
+            }
+          }
         }
-        cpk[gl * sp + t] = make_uint2(j, __float_as_uint(a));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int f = lane + 32 * (k0 + u);
+          if (k0 + u < s && f < nb * s) {
+            const int gl = s == 1 ? f : static_cast<int>(__umulhi(static_cast<uint32_t>(f), p.sdiv));
+            cpk[gl * sp + (f - gl * s)] = make_uint2(jj[u], __float_as_uint(aa[u]));
+          }
+        }
       }
       for (int t = s; t < sp; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
     }
@@ -291,18 +320,25 @@ __global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__
     } else {
 #pragma unroll
       for (int b = 0; b < 15; ++b) Ys[lane * YS + b] = Y[b];
-      Ys[lane * YS + 15] = __int_as_float(nz);
+      Ys[lane * YS + 15] = 0.f;
+      nzs[lane] = nz;
       __syncwarp();
-      // ---- phase B: a half-warp per visible Gaussian
-      const uint2* Ds2 = reinterpret_cast<const uint2*>(sm);
-      for (int v0 = 0; v0 < nvis; v0 += 2) {
-        const int v = v0 + h;
+      // ---- phase B: 8 lanes per visible Gaussian.  Lane ql owns two bases:
+      // FP16 dictionary: 2ql and 2ql+1 (one 16-byte read per nonzero);
+      // FP32 dictionary: ql and ql+8 (two 16-byte reads).  In both cases the
+      // 8 lanes of a Gaussian read one contiguous 128-byte span per
+      // instruction: no bank conflicts.  Basis 15 is the zero slot.
+      const int bA = CM == CM_F32 ? ql : 2 * ql, bB = CM == CM_F32 ? ql + 8 : 2 * ql + 1;
+      for (int v0 = 0; v0 < nvis; v0 += 4) {
+        const int v = v0 + grp;
         const bool act = v < nvis;
         const int gl = act ? vlist[v] : 0;
-        int nzl = act ? __float_as_int(Ys[gl * YS + 15]) : 0;
+        int nzl = act ? nzs[gl] : 0;
         nzl = nzl > s ? s : nzl;
-        const int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 16));
-        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+        int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
+        nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
+        float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
+#pragma unroll 2
         for (int t = 0; t < nzp; t += 2) {
           const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gl * sp + t);
           uint32_t j0 = c2.x, j1 = c2.z;
@@ -316,43 +352,59 @@ __global__ void __launch_bounds__(512) preprocess_kernel(const __grid_constant__
             a1 = 0.f;
           }
           if (CM == CM_F32) {
-            const float* w0 = sm + j0 * ROW + hl;
-            const float* w1 = sm + j1 * ROW + hl;
-            acc0 = fmaf(a0, w0[0], acc0);
-            acc1 = fmaf(a0, w0[15], acc1);
-            acc2 = fmaf(a0, w0[30], acc2);
-            acc0 = fmaf(a1, w1[0], acc0);
-            acc1 = fmaf(a1, w1[15], acc1);
-            acc2 = fmaf(a1, w1[30], acc2);
+            const float4* D4 = reinterpret_cast<const float4*>(sm);
+            const float4 x0 = D4[j0 * 16 + bA], y0 = D4[j0 * 16 + bB];
+            const float4 x1 = D4[j1 * 16 + bA], y1 = D4[j1 * 16 + bB];
+            aR = fmaf(a0, x0.x, aR);
+            aG = fmaf(a0, x0.y, aG);
+            aB = fmaf(a0, x0.z, aB);
+            bR = fmaf(a0, y0.x, bR);
+            bG = fmaf(a0, y0.y, bG);
+            bBl = fmaf(a0, y0.z, bBl);
+            aR = fmaf(a1, x1.x, aR);
+            aG = fmaf(a1, x1.y, aG);
+            aB = fmaf(a1, x1.z, aB);
+            bR = fmaf(a1, y1.x, bR);
+            bG = fmaf(a1, y1.y, bG);
+            bBl = fmaf(a1, y1.z, bBl);
           } else {
-            const uint2 d0 = Ds2[j0 * 16 + hl];
-            const uint2 d1 = Ds2[j1 * 16 + hl];
-            const float2 rg0 = __half22float2(*reinterpret_cast<const __half2*>(&d0.x));
-            const float2 bz0 = __half22float2(*reinterpret_cast<const __half2*>(&d0.y));
-            const float2 rg1 = __half22float2(*reinterpret_cast<const __half2*>(&d1.x));
-            const float2 bz1 = __half22float2(*reinterpret_cast<const __half2*>(&d1.y));
-            acc0 = fmaf(a0, rg0.x, acc0);
-            acc1 = fmaf(a0, rg0.y, acc1);
-            acc2 = fmaf(a0, bz0.x, acc2);
-            acc0 = fmaf(a1, rg1.x, acc0);
-            acc1 = fmaf(a1, rg1.y, acc1);
-            acc2 = fmaf(a1, bz1.x, acc2);
+            // (R, G) and (B, 0) of basis 2ql, then of basis 2ql + 1
+            const uint4* D4 = reinterpret_cast<const uint4*>(sm);
+            const uint4 w0 = D4[j0 * 8 + ql], w1 = D4[j1 * 8 + ql];
+            const float2 rg0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.x));
+            const float2 bz0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.y));
+            const float2 rh0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.z));
+            const float2 bh0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.w));
+            const float2 rg1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.x));
+            const float2 bz1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.y));
+            const float2 rh1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.z));
+            const float2 bh1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.w));
+            aR = fmaf(a0, rg0.x, aR);
+            aG = fmaf(a0, rg0.y, aG);
+            aB = fmaf(a0, bz0.x, aB);
+            bR = fmaf(a0, rh0.x, bR);
+            bG = fmaf(a0, rh0.y, bG);
+            bBl = fmaf(a0, bh0.x, bBl);
+            aR = fmaf(a1, rg1.x, aR);
+            aG = fmaf(a1, rg1.y, aG);
+            aB = fmaf(a1, bz1.x, aB);
+            bR = fmaf(a1, rh1.x, bR);
+            bG = fmaf(a1, rh1.y, bG);
+            bBl = fmaf(a1, bh1.x, bBl);
           }
         }
-        // lane 15's words belong to no basis (a neighbouring row's word, or the
-        // zero slot); its basis value is 0
-        const float yb = hl < 15 ? Ys[gl * YS + hl] : 0.f;
-        const float p0 = acc0 * yb, p1 = acc1 * yb, p2 = acc2 * yb;
-        // transposing butterfly: after it lane hl holds channel hl >> 2 (hl = 0, 4, 8)
-        const bool b3 = (hl & 8) != 0, b2 = (hl & 4) != 0;
-        const float r0 = __shfl_xor_sync(FULL, b3 ? p0 : p2, 8);
-        const float r1 = __shfl_xor_sync(FULL, b3 ? p1 : 0.f, 8);
-        const float k0 = (b3 ? p2 : p0) + r0;
-        const float k1 = (b3 ? 0.f : p1) + r1;
-        float m = (b2 ? k1 : k0) + __shfl_xor_sync(FULL, b2 ? k0 : k1, 4);
-        m += __shfl_xor_sync(FULL, m, 2);
+        const float yA = Ys[gl * YS + bA], yB = Ys[gl * YS + bB];
+        const float p0 = fmaf(yA, aR, yB * bR), p1 = fmaf(yA, aG, yB * bG), p2 = fmaf(yA, aB, yB * bBl);
+        // transposing butterfly over the 8 lanes: afterwards lane ql holds
+        // channel ql >> 1 (ql = 0, 2, 4)
+        const bool b2 = (ql & 4) != 0, b1 = (ql & 2) != 0;
+        const float r0 = __shfl_xor_sync(FULL, b2 ? p0 : p2, 4);
+        const float r1 = __shfl_xor_sync(FULL, b2 ? p1 : 0.f, 4);
+        const float k0 = (b2 ? p2 : p0) + r0;
+        const float k1 = (b2 ? 0.f : p1) + r1;
+        float m = (b1 ? k1 : k0) + __shfl_xor_sync(FULL, b1 ? k0 : k1, 2);
         m += __shfl_xor_sync(FULL, m, 1);
-        if (act && (hl & 3) == 0 && hl < 12) outs[gl * 3 + (hl >> 2)] = m;
+        if (act && (ql & 1) == 0 && ql < 6) outs[gl * 3 + (ql >> 1)] = m;
       }
       __syncwarp();
       if (vis) {
@@ -427,11 +479,11 @@ static int launch(const Params& p, cudaStream_t st, const char* call) {
   if (CM == CM_SH) {
     wbytes = static_cast<size_t>(dense_warp_floats()) * 4;
   } else {
-    dbytes = CM == CM_F32 ? static_cast<size_t>((p.K * ROW + 16 + 3) & ~3) * 4 : static_cast<size_t>(p.K) * 128;
+    dbytes = static_cast<size_t>(dict_floats(CM, p.K)) * 4;
     wbytes = static_cast<size_t>(codes_warp_floats(p.sp)) * 4;
   }
   int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
-  if (nwarps > 16) nwarps = 16;
+  if (nwarps > 32) nwarps = 32;
   if (nwarps < 1)
     return set_error(DLSH_ERR_UNSUPPORTED, "%s: K=%d leaves no shared memory for a warp", call, p.K);
   const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
@@ -479,7 +531,7 @@ size_t preprocess_max_k(int s, int compact) {
   if (s < 1 || s > DLSH_MAX_S) return 0;
   const size_t wb = static_cast<size_t>(codes_warp_floats(staged_slots(s))) * 4;
   const size_t room = static_cast<size_t>(SMEM_LIMIT) - 4 * wb;
-  return compact ? room / 128 : (room / 4 - 19) / ROW;
+  return room / (compact ? 128 : 256);
 }
 
 }  // namespace dlsh

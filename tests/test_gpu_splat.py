@@ -103,8 +103,8 @@ def test_views_cover_culling(lib):
 
 
 @pytest.mark.parametrize("view", sorted(VIEWS))
-@pytest.mark.parametrize("N,K,s", [(5003, 300, 8), (2100, 90, 12), (1000, 1024, 5), (257, 16, 1),
-                                   (300, 64, 32)])
+@pytest.mark.parametrize("N,K,s", [(5003, 300, 8), (2100, 90, 12), (1000, 800, 5), (257, 16, 1),
+                                   (300, 64, 32), (700, 33, 3)])
 def test_preprocess_codes(lib, view, N, K, s):
     cam, R, t = _camera(lib, view)
     g = _gauss(N, 20 + N)
