@@ -3,14 +3,22 @@
 // coefficients.  For Gaussian i and unit view direction v_i,
 //   rgb_c = sum_b Y_b(v_i) * sum_{t < nnz_i} coef[i,t] * D[idx[i,t], c*15 + b].
 //
-// Memory-bound design: the FP32 dictionary is staged once per CTA in shared
-// memory and every nonzero costs three 16-lane reads of one dictionary row.  A
-// warp works on batches of 16 Gaussians: first all of the batch's codes are
-// loaded (coalesced) into shared memory while one lane per Gaussian computes its
-// direction and 15 basis values; then each half-warp takes one Gaussian, lane b
-// owning basis b of all three channels, accumulates sum_t coef * D[j_t, c*15+b],
-// multiplies by Y_b and reduces across the half with shuffles.  Results are
-// staged and written back coalesced.
+// Bound by shared-memory wavefronts, not HBM: the dictionary is staged once
+// per CTA in shared memory and every nonzero reads a whole atom (45 values).
+// A warp takes batches of 16 Gaussians: the batch's codes are loaded
+// (coalesced) into shared memory as (index, coefficient) pairs while one lane
+// per Gaussian computes its direction and 15 basis values; then eight lanes take
+// one Gaussian (four Gaussians per warp step), lane q owning bases 2q and 2q+1
+// of all three channels, so that the eight lanes read one contiguous span of the
+// atom per instruction:
+//  - FP32 table: three channel planes of 16 floats per atom (192 bytes), read
+//    as three 8-byte words per lane;
+//  - FP16 table (compact storage): 16 slots of (R, G, B, 0) halves per atom
+//    (128 bytes), read as one 16-byte word per lane.
+// The lane's three channel sums are multiplied by Y_b and reduced over the
+// eight lanes in four shuffles (a transposing butterfly); results are staged
+// and written back coalesced.  For dictionaries too large for shared memory
+// the FP32 rows are read through the read-only cache instead.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -21,50 +29,114 @@
 namespace dlsh {
 namespace dec {
 
-constexpr int ROW = 45;         // dictionary row in shared memory (plus 16 zero words at the end)
-constexpr int YS = 17;          // basis values per Gaussian slot (15 used, slot 15 holds nnz)
-constexpr int SMEM_LIMIT = 232448;
+enum : int { FM_F32 = 0, FM_GLOBAL = 1, FM_C8 = 2, FM_C16 = 3 };
 
-// Per-warp shared memory: basis slots, staged rgb, and the batch's codes.
+constexpr int YS = 16;          // basis values per Gaussian slot (15 and a zero)
+constexpr int SMEM_LIMIT = 232448;
 constexpr int GB = 16;          // Gaussians per warp batch (small batches: more warps fit per SM)
-__host__ __device__ constexpr int warp_floats(int s) { return GB * YS + GB * 3 + GB * s * 2; }
+
+// Code slots staged per Gaussian: even (16-byte pair reads), and not a multiple
+// of four, so that the four Gaussians of a step read different bank groups.
+inline int staged_slots(int s) {
+  int sp = (s + 1) & ~1;
+  if (sp % 4 == 0) sp += 2;
+  return sp;
+}
+// Per-warp shared memory: basis slots, staged rgb, codes, nnz.
+__host__ __device__ constexpr int warp_floats(int sp) { return GB * YS + GB * 3 + GB * sp * 2 + GB; }
+__host__ __device__ constexpr int dict_floats(int fm, int K) { return fm == FM_F32 ? K * 48 : fm >= FM_C8 ? K * 32 : 0; }
 
 __constant__ ShConst g_sh;
 
-template <bool SMEM_D>
+template <int FM>
 __global__ void __launch_bounds__(1024) decode_kernel(
-    const float* __restrict__ D, int K, const uint16_t* __restrict__ idx,
-    const float* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int64_t N,
+    const float* __restrict__ D, int K, const void* __restrict__ idxv, const void* __restrict__ coefv,
+    const uint8_t* __restrict__ nnz, int s, int sp, uint32_t sdiv, int64_t N,
     const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
     float* __restrict__ rgb, uint32_t* status) {
   extern __shared__ __align__(16) float sm[];
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* Ds = sm;
-  const int dwords = SMEM_D ? K * ROW + 16 : 0;
-  float* wsm = sm + dwords + warp * warp_floats(s);
-  float* Ys = wsm;
-  float* outs = wsm + GB * YS;
-  float* ccoef = outs + GB * 3;
-  uint32_t* cidx = reinterpret_cast<uint32_t*>(ccoef + GB * s);
-  if (SMEM_D) {
-    for (int f = threadIdx.x; f < dwords; f += blockDim.x) Ds[f] = f < K * ROW ? D[f] : 0.f;
+  const unsigned FULL = 0xffffffffu;
+  // ---- dictionary in shared memory; four slots per thread per round, their
+  // loads issued before any is stored
+  const int dwords = dict_floats(FM, K);
+  if (FM != FM_GLOBAL) {
+    for (int f0 = threadIdx.x; f0 < K * 16; f0 += 4 * blockDim.x) {
+      float v[4][3];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * blockDim.x, j = f >> 4, b = f & 15;
+        const bool live = f < K * 16 && b < 15;
+        const float* dr = D + static_cast<size_t>(live ? j : 0) * DLSH_D + (live ? b : 0);
+        v[u][0] = live ? dr[0] : 0.f;
+        v[u][1] = live ? dr[15] : 0.f;
+        v[u][2] = live ? dr[30] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = f0 + u * blockDim.x;
+        if (f >= K * 16) break;
+        if (FM == FM_F32) {
+          const int j = f >> 4, b = f & 15;
+          sm[j * 48 + b] = v[u][0];
+          sm[j * 48 + 16 + b] = v[u][1];
+          sm[j * 48 + 32 + b] = v[u][2];
+        } else {
+          const __half2 rg = __floats2half2_rn(v[u][0], v[u][1]);
+          const __half2 bz = __floats2half2_rn(v[u][2], 0.f);
+          reinterpret_cast<uint2*>(sm)[f] =
+              make_uint2(*reinterpret_cast<const uint32_t*>(&rg), *reinterpret_cast<const uint32_t*>(&bz));
+        }
+      }
+    }
     __syncthreads();
   }
-  const int hl = lane & 15, h = lane >> 4;
-  const unsigned FULL = 0xffffffffu;
+  float* wsm = sm + dwords + warp * warp_floats(sp);
+  float* Ys = wsm;
+  float* outs = wsm + GB * YS;
+  uint2* cpk = reinterpret_cast<uint2*>(wsm + GB * YS + GB * 3);
+  int* nzs = reinterpret_cast<int*>(wsm + GB * YS + GB * 3 + GB * sp * 2);
+  const int ql = lane & 7, grp = lane >> 3;
   const int64_t nbatch = (N + GB - 1) / GB;
   const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
   bool bad = false;
   for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
     const int64_t base = bt * GB;
     const int nb = N - base < GB ? static_cast<int>(N - base) : GB;
-    // ---- phase A: every load of the batch is issued here, then one lane per
-    // Gaussian computes its direction and 15 basis values
-    for (int f = lane; f < nb * s; f += 32) {
-      cidx[f] = idx[base * s + f];
-      ccoef[f] = coef[base * s + f];
+    // ---- phase A: the batch's codes as (index, coefficient) pairs, element
+    // f = lane + 32 k (k < s/2 rounded up), four loads in flight per lane
+    for (int k0 = 0; 32 * k0 < GB * s; k0 += 4) {
+      uint32_t jj[4];
+      float aa[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = lane + 32 * (k0 + u);
+        jj[u] = 0;
+        aa[u] = 0.f;
+        if (f < nb * s) {
+          const int64_t e = base * s + f;
+          if (FM == FM_F32 || FM == FM_GLOBAL) {
+            jj[u] = static_cast<const uint16_t*>(idxv)[e];
+            aa[u] = static_cast<const float*>(coefv)[e];
+          } else {
+            jj[u] = FM == FM_C8 ? static_cast<uint32_t>(static_cast<const uint8_t*>(idxv)[e])
+                                : static_cast<uint32_t>(static_cast<const uint16_t*>(idxv)[e]);
+            aa[u] = __half2float(static_cast<const __half*>(coefv)[e]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int f = lane + 32 * (k0 + u);
+        if (f < nb * s) {
+          const int gl = s == 1 ? f : static_cast<int>(__umulhi(static_cast<uint32_t>(f), sdiv));
+          cpk[gl * sp + (f - gl * s)] = make_uint2(jj[u], __float_as_uint(aa[u]));
+        }
+      }
     }
+    if (lane < GB)
+      for (int t = s; t < sp; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
     {
       const int64_t g = base + lane;
       float vx = 0.f, vy = 0.f, vz = 1.f;
@@ -89,187 +161,96 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       if (lane < GB) {
 #pragma unroll
         for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
-        Ys[lane * YS + 15] = __int_as_float(nz);
+        Ys[lane * YS + 15] = 0.f;
+        nzs[lane] = nz;
       }
     }
     __syncwarp();
-    // ---- phase B: a half-warp per Gaussian, lane hl owns basis hl of R, G, B
-    for (int pp = 0; pp < GB / 2; ++pp) {
-      const int gl = 2 * pp + h;
-      int nz = gl < nb ? __float_as_int(Ys[gl * YS + 15]) : 0;
-      if (nz > s) {
+    // ---- phase B: eight lanes per Gaussian, four Gaussians per step
+    for (int g0 = 0; g0 < nb; g0 += 4) {
+      const int gl = g0 + grp;
+      const bool act = gl < nb;
+      const int gs = act ? gl : 0;
+      int nzl = act ? nzs[gs] : 0;
+      if (nzl > s) {
         bad = true;
-        nz = s;
+        nzl = s;
       }
-      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-      for (int t = 0; t < s; ++t) {
-        uint32_t j = 0;
-        float a = 0.f;
-        if (t < nz) {
-          j = cidx[gl * s + t];
-          a = ccoef[gl * s + t];
-        }
-        if (j >= static_cast<uint32_t>(K)) {
-          bad = true;
-          j = 0;
-          a = 0.f;
-        }
-        if (SMEM_D) {
-          const float* row = Ds + j * ROW + hl;
-          acc0 = fmaf(a, row[0], acc0);
-          acc1 = fmaf(a, row[15], acc1);
-          acc2 = fmaf(a, row[30], acc2);
-        } else if (hl < 15) {
-          const float* row = D + static_cast<size_t>(j) * DLSH_D + hl;
-          acc0 = fmaf(a, __ldg(row), acc0);
-          acc1 = fmaf(a, __ldg(row + 15), acc1);
-          acc2 = fmaf(a, __ldg(row + 30), acc2);
-        }
-      }
-      // lane 15 read a neighbouring word (finite) times Y = 0
-      const float yb = hl < 15 ? Ys[gl * YS + hl] : 0.f;
-      float p0 = acc0 * yb, p1 = acc1 * yb, p2 = acc2 * yb;
+      int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
+      nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
+      float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
+#pragma unroll 2
+      for (int t = 0; t < nzp; t += 2) {
+        const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gs * sp + t);
+        uint32_t jt[2] = {c2.x, c2.z};
+        float at[2] = {__uint_as_float(c2.y), __uint_as_float(c2.w)};
 #pragma unroll
-      for (int off = 8; off > 0; off >>= 1) {
-        p0 += __shfl_xor_sync(FULL, p0, off);
-        p1 += __shfl_xor_sync(FULL, p1, off);
-        p2 += __shfl_xor_sync(FULL, p2, off);
+        for (int u = 0; u < 2; ++u) {
+          if (t + u >= nzl) {
+            jt[u] = 0;
+            at[u] = 0.f;
+          } else if (jt[u] >= static_cast<uint32_t>(K)) {
+            bad = true;
+            jt[u] = 0;
+            at[u] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float a = at[u];
+          if (FM == FM_F32) {
+            const float* row = sm + jt[u] * 48 + 2 * ql;
+            const float2 r = *reinterpret_cast<const float2*>(row);
+            const float2 gg = *reinterpret_cast<const float2*>(row + 16);
+            const float2 bb = *reinterpret_cast<const float2*>(row + 32);
+            aR = fmaf(a, r.x, aR);
+            bR = fmaf(a, r.y, bR);
+            aG = fmaf(a, gg.x, aG);
+            bG = fmaf(a, gg.y, bG);
+            aB = fmaf(a, bb.x, aB);
+            bBl = fmaf(a, bb.y, bBl);
+          } else if (FM == FM_GLOBAL) {
+            // bases 2ql and 2ql + 1 of the atom's row (basis 15 does not exist)
+            const float* row = D + static_cast<size_t>(jt[u]) * DLSH_D + 2 * ql;
+            aR = fmaf(a, __ldg(row), aR);
+            aG = fmaf(a, __ldg(row + 15), aG);
+            aB = fmaf(a, __ldg(row + 30), aB);
+            if (ql < 7) {
+              bR = fmaf(a, __ldg(row + 1), bR);
+              bG = fmaf(a, __ldg(row + 16), bG);
+              bBl = fmaf(a, __ldg(row + 31), bBl);
+            }
+          } else {
+            const uint4 w = reinterpret_cast<const uint4*>(sm)[jt[u] * 8 + ql];
+            const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+            const float2 bz = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
+            const float2 rh = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
+            const float2 bh = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
+            aR = fmaf(a, rg.x, aR);
+            aG = fmaf(a, rg.y, aG);
+            aB = fmaf(a, bz.x, aB);
+            bR = fmaf(a, rh.x, bR);
+            bG = fmaf(a, rh.y, bG);
+            bBl = fmaf(a, bh.x, bBl);
+          }
+        }
       }
-      if (hl == 0) {
-        outs[gl * 3 + 0] = p0;
-        outs[gl * 3 + 1] = p1;
-        outs[gl * 3 + 2] = p2;
-      }
+      const float2 yy = *reinterpret_cast<const float2*>(Ys + gs * YS + 2 * ql);
+      const float p0 = fmaf(yy.x, aR, yy.y * bR), p1 = fmaf(yy.x, aG, yy.y * bG),
+                  p2 = fmaf(yy.x, aB, yy.y * bBl);
+      // transposing butterfly over the 8 lanes: afterwards lane ql holds
+      // channel ql >> 1 (ql = 0, 2, 4)
+      const bool b2 = (ql & 4) != 0, b1 = (ql & 2) != 0;
+      const float r0 = __shfl_xor_sync(FULL, b2 ? p0 : p2, 4);
+      const float r1 = __shfl_xor_sync(FULL, b2 ? p1 : 0.f, 4);
+      const float k0 = (b2 ? p2 : p0) + r0;
+      const float k1 = (b2 ? 0.f : p1) + r1;
+      float m = (b1 ? k1 : k0) + __shfl_xor_sync(FULL, b1 ? k0 : k1, 2);
+      m += __shfl_xor_sync(FULL, m, 1);
+      if (act && (ql & 1) == 0 && ql < 6) outs[gl * 3 + (ql >> 1)] = m;
     }
     __syncwarp();
     // ---- coalesced store of the batch's outputs
-#pragma unroll
-    for (int q = 0; q < (GB * 3 + 31) / 32; ++q) {
-      const int e = lane + 32 * q;
-      if (e < nb * 3) rgb[base * 3 + e] = outs[e];
-    }
-    __syncwarp();
-  }
-  if (bad) flag_status(status, ST_BAD_INPUT);
-}
-
-// ---- compact storage: FP16 coefficients, 8- or 16-bit atom indices ----------
-// The dictionary is staged in shared memory as FP16, 16 slots of four halves
-// per atom (slot b < 15: the R, G, B coefficients of basis b, then a zero):
-// 128 bytes per atom, so a half-warp reads one atom's row for all three
-// channels in a single 8-byte load per lane (one wavefront), where the FP32
-// kernel needs three.  Sums stay FP32.
-template <int IDXB>
-__global__ void __launch_bounds__(1024) decode_compact_kernel(
-    const float* __restrict__ D, int K, const void* __restrict__ idxv,
-    const __half* __restrict__ coef, const uint8_t* __restrict__ nnz, int s, int64_t N,
-    const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
-    float* __restrict__ rgb, uint32_t* status) {
-  extern __shared__ __align__(16) float sm[];
-  const int nwarps = blockDim.x >> 5;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint2* Ds = reinterpret_cast<uint2*>(sm);  // [K][16]
-  float* wsm = sm + static_cast<size_t>(K) * 32 + warp * warp_floats(s);
-  float* Ys = wsm;
-  float* outs = wsm + GB * YS;
-  float* ccoef = outs + GB * 3;
-  uint32_t* cidx = reinterpret_cast<uint32_t*>(ccoef + GB * s);
-  for (int f = threadIdx.x; f < K * 16; f += blockDim.x) {
-    const int j = f >> 4, b = f & 15;
-    uint2 v = make_uint2(0u, 0u);
-    if (b < 15) {
-      const float* dr = D + static_cast<size_t>(j) * DLSH_D + b;
-      const __half2 rg = __floats2half2_rn(dr[0], dr[15]);
-      const __half2 bz = __floats2half2_rn(dr[30], 0.f);
-      v.x = *reinterpret_cast<const uint32_t*>(&rg);
-      v.y = *reinterpret_cast<const uint32_t*>(&bz);
-    }
-    Ds[f] = v;
-  }
-  __syncthreads();
-  const int hl = lane & 15, h = lane >> 4;
-  const unsigned FULL = 0xffffffffu;
-  const int64_t nbatch = (N + GB - 1) / GB;
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * nwarps;
-  bool bad = false;
-  for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
-    const int64_t base = bt * GB;
-    const int nb = N - base < GB ? static_cast<int>(N - base) : GB;
-    for (int f = lane; f < nb * s; f += 32) {
-      cidx[f] = IDXB == 1 ? static_cast<uint32_t>(static_cast<const uint8_t*>(idxv)[base * s + f])
-                          : static_cast<uint32_t>(static_cast<const uint16_t*>(idxv)[base * s + f]);
-      ccoef[f] = __half2float(coef[base * s + f]);
-    }
-    {
-      const int64_t g = base + lane;
-      float vx = 0.f, vy = 0.f, vz = 1.f;
-      int nz = 0;
-      if (lane < nb) {
-        vx = dm[g * 3 + 0];
-        vy = dm[g * 3 + 1];
-        vz = dm[g * 3 + 2];
-        nz = nnz[g];
-        if (use_cam) {
-          vx -= cx;
-          vy -= cy;
-          vz -= cz;
-          const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-          vx *= inv;
-          vy *= inv;
-          vz *= inv;
-        }
-      }
-      float Y[15];
-      sh_basis(g_sh.c, vx, vy, vz, Y);
-      if (lane < GB) {
-#pragma unroll
-        for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
-        Ys[lane * YS + 15] = __int_as_float(nz);
-      }
-    }
-    __syncwarp();
-    for (int pp = 0; pp < GB / 2; ++pp) {
-      const int gl = 2 * pp + h;
-      int nz = gl < nb ? __float_as_int(Ys[gl * YS + 15]) : 0;
-      if (nz > s) {
-        bad = true;
-        nz = s;
-      }
-      float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-      for (int t = 0; t < s; ++t) {
-        uint32_t j = 0;
-        float a = 0.f;
-        if (t < nz) {
-          j = cidx[gl * s + t];
-          a = ccoef[gl * s + t];
-        }
-        if (j >= static_cast<uint32_t>(K)) {
-          bad = true;
-          j = 0;
-          a = 0.f;
-        }
-        const uint2 v = Ds[j * 16 + hl];
-        const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
-        const float2 bz = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
-        acc0 = fmaf(a, rg.x, acc0);
-        acc1 = fmaf(a, rg.y, acc1);
-        acc2 = fmaf(a, bz.x, acc2);
-      }
-      const float yb = hl < 15 ? Ys[gl * YS + hl] : 0.f;
-      float p0 = acc0 * yb, p1 = acc1 * yb, p2 = acc2 * yb;
-#pragma unroll
-      for (int off = 8; off > 0; off >>= 1) {
-        p0 += __shfl_xor_sync(FULL, p0, off);
-        p1 += __shfl_xor_sync(FULL, p1, off);
-        p2 += __shfl_xor_sync(FULL, p2, off);
-      }
-      if (hl == 0) {
-        outs[gl * 3 + 0] = p0;
-        outs[gl * 3 + 1] = p1;
-        outs[gl * 3 + 2] = p2;
-      }
-    }
-    __syncwarp();
 #pragma unroll
     for (int q = 0; q < (GB * 3 + 31) / 32; ++q) {
       const int e = lane + 32 * q;
@@ -305,9 +286,47 @@ static int upload_constants(cudaStream_t st) {
   return DLSH_OK;
 }
 
+// One decode launch with the dictionary format FM: shared-memory sizes from
+// the format, as many warps per CTA as shared memory allows (at most 32), and
+// a grid of (CTAs resident per SM) x SMs, capped by the work.
+template <int FM>
+static int launch_decode(const float* D, int K, const void* idx, const void* coef, const uint8_t* nnz,
+                         int s, int64_t N, const float* dm, const float* cam, float* rgb,
+                         uint32_t* status, int nwarps, cudaStream_t st, const char* call) {
+  int sms = device_sm_count();
+  if (sms <= 0) sms = 1;
+  const int sp = staged_slots(s);
+  const uint32_t sdiv = s >= 2 ? static_cast<uint32_t>((uint64_t(1) << 32) / static_cast<uint64_t>(s) + 1) : 0u;
+  const size_t smem = static_cast<size_t>(dict_floats(FM, K) + nwarps * warp_floats(sp)) * 4;
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
+                call);
+  int per_sm = 0;
+  DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<FM>, nwarps * 32, smem), call);
+  if (per_sm < 1) per_sm = 1;
+  const int64_t nbatch = (N + GB - 1) / GB;
+  int64_t grid = static_cast<int64_t>(sms) * per_sm;
+  const int64_t need = (nbatch + nwarps - 1) / nwarps;
+  if (grid > need) grid = need;
+  const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
+  decode_kernel<FM><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(D, K, idx, coef, nnz, s, sp, sdiv, N, dm,
+                                                                       cam != nullptr, cx, cy, cz, rgb, status);
+  count_launches(1);
+  return check_launch(call);
+}
+
+// Warps per CTA that fit beside the dictionary of format fm (0 if none do).
+static int fit_warps(int fm, int K, int s) {
+  const long long room = SMEM_LIMIT - 4LL * dict_floats(fm, K);
+  const long long wb = 4LL * warp_floats(staged_slots(s));
+  long long n = room > 0 ? room / wb : 0;
+  return static_cast<int>(n > 32 ? 32 : n);
+}
+
 }  // namespace dec
 
-// Shared with the bench / learn paths: enqueue one decode.
+// Shared with the bench / learn paths: enqueue one decode.  The FP32 table
+// stays in shared memory while at least six warps fit beside it; beyond that
+// (about 1150 atoms) the rows are read through the read-only cache.
 int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef,
                    const uint8_t* nnz, int s, int64_t N, const float* dm, const float* cam,
                    float* rgb, uint32_t* status, cudaStream_t st) {
@@ -315,40 +334,9 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
   int rc = upload_constants(st);
   if (rc) return rc;
   if (N == 0) return DLSH_OK;
-  int sms = device_sm_count();
-  if (sms <= 0) sms = 1;
-  const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
-  const int64_t nbatch = (N + GB - 1) / GB;
-  const size_t dbytes = (static_cast<size_t>(K) * ROW + 16) * 4;
-  const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
-  int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
-  if (nwarps > 32) nwarps = 32;
-  if (nwarps >= 6) {
-    const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
-                  "dlsh_decode: attribute");
-    int per_sm = static_cast<int>(SMEM_LIMIT / smem);
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = static_cast<int64_t>(sms) * per_sm;
-    const int64_t need = (nbatch + nwarps - 1) / nwarps;
-    if (grid > need) grid = need;
-    decode_kernel<true><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
-        D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
-  } else {
-    const int nw = 8;
-    const size_t smem = static_cast<size_t>(nw) * wbytes;
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
-                  "dlsh_decode: attribute");
-    int64_t grid = static_cast<int64_t>(sms) * 4;
-    const int64_t need = (nbatch + nw - 1) / nw;
-    if (grid > need) grid = need;
-    decode_kernel<false><<<static_cast<int>(grid), nw * 32, smem, st>>>(
-        D, K, idx, coef, nnz, s, N, dm, cam != nullptr, cx, cy, cz, rgb, status);
-  }
-  count_launches(1);
-  return check_launch("dlsh_decode: launch");
+  const int nw = fit_warps(FM_F32, K, s);
+  if (nw >= 6) return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dm, cam, rgb, status, nw, st, "dlsh_decode");
+  return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dm, cam, rgb, status, 16, st, "dlsh_decode");
 }
 
 }  // namespace dlsh
@@ -373,16 +361,10 @@ extern "C" int dlsh_decode(const float* D, int K, int d, const uint16_t* idx, co
   return finish(st, nullptr, flags, "dlsh_decode");
 }
 
-namespace dlsh {
-namespace dec {
-inline size_t compact_dict_bytes(int K) { return static_cast<size_t>(K) * 128; }
-}  // namespace dec
-}  // namespace dlsh
-
 extern "C" size_t dlsh_decode_compact_max_k(int s) {
   using namespace dlsh::dec;
   if (s < 1 || s > DLSH_MAX_S) return 0;
-  const size_t wb = static_cast<size_t>(warp_floats(s)) * 4;
+  const size_t wb = static_cast<size_t>(warp_floats(staged_slots(s))) * 4;
   return (static_cast<size_t>(SMEM_LIMIT) - 6 * wb) / 128;
 }
 
@@ -434,37 +416,11 @@ extern "C" int dlsh_decode_compact(const float* D, int K, int d, const void* idx
   int rc = upload_constants(st);
   if (rc) return rc;
   if (N > 0) {
-    int sms = device_sm_count();
-    if (sms <= 0) sms = 1;
-    const float cx = cam_pos ? cam_pos[0] : 0.f, cy = cam_pos ? cam_pos[1] : 0.f,
-                cz = cam_pos ? cam_pos[2] : 0.f;
-    const int64_t nbatch = (N + GB - 1) / GB;
-    const size_t dbytes = compact_dict_bytes(K);
-    const size_t wbytes = static_cast<size_t>(warp_floats(s)) * 4;
-    int nwarps = static_cast<int>((SMEM_LIMIT - static_cast<long long>(dbytes)) / static_cast<long long>(wbytes));
-    if (nwarps > 32) nwarps = 32;
-    const size_t smem = dbytes + static_cast<size_t>(nwarps) * wbytes;
-    int per_sm = static_cast<int>(SMEM_LIMIT / smem);
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = static_cast<int64_t>(sms) * per_sm;
-    const int64_t need = (nbatch + nwarps - 1) / nwarps;
-    if (grid > need) grid = need;
-    const __half* cf = reinterpret_cast<const __half*>(coef_f16);
-    if (idx_bytes == 1) {
-      DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_compact_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_LIMIT),
-                    "dlsh_decode_compact: attribute");
-      decode_compact_kernel<1><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
-          D, K, idx, cf, nnz, s, N, dirs_or_means, cam_pos != nullptr, cx, cy, cz, rgb, nullptr);
-    } else {
-      DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_compact_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_LIMIT),
-                    "dlsh_decode_compact: attribute");
-      decode_compact_kernel<2><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
-          D, K, idx, cf, nnz, s, N, dirs_or_means, cam_pos != nullptr, cx, cy, cz, rgb, nullptr);
-    }
-    count_launches(1);
-    rc = check_launch("dlsh_decode_compact: launch");
+    const int nw = fit_warps(FM_C8, K, s);
+    rc = idx_bytes == 1 ? launch_decode<FM_C8>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, rgb,
+                                               nullptr, nw, st, "dlsh_decode_compact")
+                        : launch_decode<FM_C16>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, rgb,
+                                                nullptr, nw, st, "dlsh_decode_compact");
     if (rc) return rc;
   }
   return finish(st, nullptr, flags, "dlsh_decode_compact");
