@@ -104,6 +104,16 @@ __global__ void __launch_bounds__(1024) decode_kernel(
   for (int64_t bt = static_cast<int64_t>(blockIdx.x) * nwarps + warp; bt < nbatch; bt += wstride) {
     const int64_t base = bt * GB;
     const int nb = N - base < GB ? static_cast<int>(N - base) : GB;
+    // direction inputs first: their loads are in flight while the codes are staged
+    const int64_t g = base + lane;
+    float vx = 0.f, vy = 0.f, vz = 1.f;
+    int nz = 0;
+    if (lane < nb) {
+      vx = dm[g * 3 + 0];
+      vy = dm[g * 3 + 1];
+      vz = dm[g * 3 + 2];
+      nz = nnz[g];
+    }
     // ---- phase A: the batch's codes as (index, coefficient) pairs, element
     // f = lane + 32 k (k < s/2 rounded up), four loads in flight per lane
     for (int k0 = 0; 32 * k0 < GB * s; k0 += 4) {
@@ -131,30 +141,24 @@ __global__ void __launch_bounds__(1024) decode_kernel(
         const int f = lane + 32 * (k0 + u);
         if (f < nb * s) {
           const int gl = s == 1 ? f : static_cast<int>(__umulhi(static_cast<uint32_t>(f), sdiv));
-          cpk[gl * sp + (f - gl * s)] = make_uint2(jj[u], __float_as_uint(aa[u]));
+          // an index beyond the dictionary is reported and counts as zero
+          const bool ok = jj[u] < static_cast<uint32_t>(K);
+          bad |= !ok;
+          cpk[gl * sp + (f - gl * s)] = make_uint2(ok ? jj[u] : 0u, ok ? __float_as_uint(aa[u]) : 0u);
         }
       }
     }
     if (lane < GB)
       for (int t = s; t < sp; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
     {
-      const int64_t g = base + lane;
-      float vx = 0.f, vy = 0.f, vz = 1.f;
-      int nz = 0;
-      if (lane < nb) {
-        vx = dm[g * 3 + 0];
-        vy = dm[g * 3 + 1];
-        vz = dm[g * 3 + 2];
-        nz = nnz[g];
-        if (use_cam) {
-          vx -= cx;
-          vy -= cy;
-          vz -= cz;
-          const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
-          vx *= inv;
-          vy *= inv;
-          vz *= inv;
-        }
+      if (use_cam && lane < nb) {
+        vx -= cx;
+        vy -= cy;
+        vz -= cz;
+        const float inv = rsqrtf(vx * vx + vy * vy + vz * vz);
+        vx *= inv;
+        vy *= inv;
+        vz *= inv;
       }
       float Y[15];
       sh_basis(g_sh.c, vx, vy, vz, Y);
@@ -162,8 +166,17 @@ __global__ void __launch_bounds__(1024) decode_kernel(
 #pragma unroll
         for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
         Ys[lane * YS + 15] = 0.f;
+        if (nz > s) {
+          bad = true;
+          nz = s;
+        }
         nzs[lane] = nz;
       }
+      __syncwarp();  // the batch's codes are staged
+      // entries t >= nnz count as zero: clear them, so that the loop below
+      // needs no per-entry test
+      if (lane < GB)
+        for (int t = nz; t < s; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
     }
     __syncwarp();
     // ---- phase B: eight lanes per Gaussian, four Gaussians per step
@@ -171,30 +184,15 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       const int gl = g0 + grp;
       const bool act = gl < nb;
       const int gs = act ? gl : 0;
-      int nzl = act ? nzs[gs] : 0;
-      if (nzl > s) {
-        bad = true;
-        nzl = s;
-      }
+      const int nzl = act ? nzs[gs] : 0;
       int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
       nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
       float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
 #pragma unroll 2
       for (int t = 0; t < nzp; t += 2) {
         const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gs * sp + t);
-        uint32_t jt[2] = {c2.x, c2.z};
-        float at[2] = {__uint_as_float(c2.y), __uint_as_float(c2.w)};
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (t + u >= nzl) {
-            jt[u] = 0;
-            at[u] = 0.f;
-          } else if (jt[u] >= static_cast<uint32_t>(K)) {
-            bad = true;
-            jt[u] = 0;
-            at[u] = 0.f;
-          }
-        }
+        const uint32_t jt[2] = {c2.x, c2.z};
+        const float at[2] = {__uint_as_float(c2.y), __uint_as_float(c2.w)};
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const float a = at[u];

@@ -154,6 +154,24 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
     const int64_t g = base + lane;
     const bool valid = lane < nb;
 
+    // ---- phase A: geometry, one lane per Gaussian.  Its loads are issued
+    // first, so that they are in flight while the codes are staged.
+    float mx = 0.f, my = 0.f, mz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
+    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
+    int nz = 0;
+    if (valid) {
+      mx = p.means[g * 3 + 0];
+      my = p.means[g * 3 + 1];
+      mz = p.means[g * 3 + 2];
+      sx = p.scales[g * 3 + 0];
+      sy = p.scales[g * 3 + 1];
+      sz = p.scales[g * 3 + 2];
+      q = p.quats[g];
+      dr = p.dc[g * 3 + 0];
+      dg = p.dc[g * 3 + 1];
+      db = p.dc[g * 3 + 2];
+      if (CM != CM_SH) nz = p.nnz[g];
+    }
     // codes of the whole batch, staged as (index, coefficient bits) pairs
     if (CM != CM_SH) {
       // element f = lane + 32 k of the batch (k < s); four loads in flight per lane
@@ -182,30 +200,15 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
           const int f = lane + 32 * (k0 + u);
           if (k0 + u < s && f < nb * s) {
             const int gl = s == 1 ? f : static_cast<int>(__umulhi(static_cast<uint32_t>(f), p.sdiv));
-            cpk[gl * sp + (f - gl * s)] = make_uint2(jj[u], __float_as_uint(aa[u]));
+            // an index beyond the dictionary counts as a zero entry
+            const bool ok = jj[u] < static_cast<uint32_t>(K);
+            cpk[gl * sp + (f - gl * s)] = make_uint2(ok ? jj[u] : 0u, ok ? __float_as_uint(aa[u]) : 0u);
           }
         }
       }
       for (int t = s; t < sp; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
     }
 
-    // ---- phase A: geometry, one lane per Gaussian
-    float mx = 0.f, my = 0.f, mz = 0.f, sx = 0.f, sy = 0.f, sz = 0.f, dr = 0.f, dg = 0.f, db = 0.f;
-    float4 q = make_float4(1.f, 0.f, 0.f, 0.f);
-    int nz = 0;
-    if (valid) {
-      mx = p.means[g * 3 + 0];
-      my = p.means[g * 3 + 1];
-      mz = p.means[g * 3 + 2];
-      sx = p.scales[g * 3 + 0];
-      sy = p.scales[g * 3 + 1];
-      sz = p.scales[g * 3 + 2];
-      q = p.quats[g];
-      dr = p.dc[g * 3 + 0];
-      dg = p.dc[g * 3 + 1];
-      db = p.dc[g * 3 + 2];
-      if (CM != CM_SH) nz = p.nnz[g];
-    }
     const float* R = p.R;
     const float x = fmaf(R[0], mx, fmaf(R[1], my, fmaf(R[2], mz, p.t[0])));
     const float y = fmaf(R[3], mx, fmaf(R[4], my, fmaf(R[5], mz, p.t[1])));
@@ -321,7 +324,12 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
 #pragma unroll
       for (int b = 0; b < 15; ++b) Ys[lane * YS + b] = Y[b];
       Ys[lane * YS + 15] = 0.f;
+      nz = nz > s ? s : nz;
       nzs[lane] = nz;
+      __syncwarp();  // the batch's codes are staged
+      // entries t >= nnz count as zero: clear them, so that the loop below
+      // needs no per-entry test
+      for (int t = nz; t < s; ++t) cpk[lane * sp + t] = make_uint2(0u, 0u);
       __syncwarp();
       // ---- phase B: 8 lanes per visible Gaussian.  Lane ql owns two bases:
       // FP16 dictionary: 2ql and 2ql+1 (one 16-byte read per nonzero);
@@ -333,24 +341,15 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
         const int v = v0 + grp;
         const bool act = v < nvis;
         const int gl = act ? vlist[v] : 0;
-        int nzl = act ? nzs[gl] : 0;
-        nzl = nzl > s ? s : nzl;
+        const int nzl = act ? nzs[gl] : 0;
         int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
         nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
         float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
 #pragma unroll 2
         for (int t = 0; t < nzp; t += 2) {
           const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gl * sp + t);
-          uint32_t j0 = c2.x, j1 = c2.z;
-          float a0 = __uint_as_float(c2.y), a1 = __uint_as_float(c2.w);
-          if (t >= nzl || j0 >= static_cast<uint32_t>(K)) {
-            j0 = 0;
-            a0 = 0.f;
-          }
-          if (t + 1 >= nzl || j1 >= static_cast<uint32_t>(K)) {
-            j1 = 0;
-            a1 = 0.f;
-          }
+          const uint32_t j0 = c2.x, j1 = c2.z;
+          const float a0 = __uint_as_float(c2.y), a1 = __uint_as_float(c2.w);
           if (CM == CM_F32) {
             const float4* D4 = reinterpret_cast<const float4*>(sm);
             const float4 x0 = D4[j0 * 16 + bA], y0 = D4[j0 * 16 + bB];
