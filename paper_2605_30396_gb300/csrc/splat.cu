@@ -64,6 +64,7 @@ struct Params {
   float* rgb;
   int64_t N;
   int K, s, sp;          // sp: staged code slots per Gaussian (even)
+  int sh_aligned;        // dense SH rows start on a 16-byte boundary
   uint32_t sdiv;         // floor(2^32 / s) + 1 (s >= 2): f / s = umulhi(f, sdiv) for f < 2^16
   float R[9], t[3];
   float fx, fy, W, H, hw, hh, limx, limy, z_near;
@@ -86,6 +87,9 @@ inline int staged_slots(int s) {
 
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 
 // a0 b0 + a1 b1 + a2 b2, rounded in a fixed order
@@ -298,14 +302,21 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
     float o0 = 0.f, o1 = 0.f, o2 = 0.f;
     if (CM == CM_SH) {
       __syncwarp();
-      // copy the visible rows; word f of the stage is word col of row `row`
-      int row = 0, col = lane;
-      for (int f = lane; f < nvis * ROW; f += 32) {
-        cp_async4(stage + f, p.sh + (base + vlist[row]) * ROW + col);
-        col += 32;
-        if (col >= ROW) {
-          col -= ROW;
-          ++row;
+      if (nvis == GB && p.sh_aligned) {
+        // all 32 visible: the batch's rows are one contiguous, 16-byte aligned
+        // block of 5760 bytes
+        const float4* src = reinterpret_cast<const float4*>(p.sh + base * ROW);
+        for (int f = lane; f < GB * ROW / 4; f += 32) cp_async16(stage + 4 * f, src + f);
+      } else {
+        // copy the visible rows; word f of the stage is word col of row `row`
+        int row = 0, col = lane;
+        for (int f = lane; f < nvis * ROW; f += 32) {
+          cp_async4(stage + f, p.sh + (base + vlist[row]) * ROW + col);
+          col += 32;
+          if (col >= ROW) {
+            col -= ROW;
+            ++row;
+          }
         }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -546,6 +557,7 @@ extern "C" int dlsh_preprocess_sh(const dlsh_camera* cam, const dlsh_gaussians* 
   if (rc) return rc;
   if (gs->N > 0 && !sh) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_preprocess_sh: sh is NULL");
   p.sh = sh;
+  p.sh_aligned = (reinterpret_cast<uintptr_t>(sh) % 16) == 0;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = spl::launch<spl::CM_SH>(p, st, "dlsh_preprocess_sh");
   if (rc) return rc;

@@ -78,12 +78,17 @@ def _compare(out, ref, colour_rel=1e-4):
 
 
 @pytest.mark.parametrize("view", sorted(VIEWS))
-@pytest.mark.parametrize("N", [1, 33, 5003])
-def test_preprocess_sh(lib, view, N):
+@pytest.mark.parametrize("N,offset", [(1, 0), (33, 0), (5003, 0), (5003, 1)])
+def test_preprocess_sh(lib, view, N, offset):
+    # offset 1 starts the SH rows 4 bytes past a 16-byte boundary (the copy
+    # then takes 4-byte granules even for fully visible batches)
     cam, R, t = _camera(lib, view)
     g = _gauss(N, 10 + N)
     y = (0.2 * np.random.default_rng(N).standard_normal((N, 45))).astype(np.float32)
-    out = _run(lib, cam, g, sh=torch.from_numpy(y).cuda())
+    buf = torch.zeros(N * 45 + offset, device="cuda")
+    sh = buf[offset:].view(N, 45)
+    sh.copy_(torch.from_numpy(y))
+    out = _run(lib, cam, g, sh=sh)
     ref = _oracle(g, R, t, y=y.astype(np.float64))
     _compare(out, ref)
 
