@@ -54,7 +54,7 @@ def parse():
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step",
                     choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
-                             "tolerance", "splat"],
+                             "tolerance", "splat", "ksvd"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -427,6 +427,59 @@ def tolerance_leg(a, api, X):
                       "rows": rows}))
 
 
+def ksvd_leg(a, api, X, init):
+    """Objective against time for the two readings of the D-step: the learning
+    loop {encode (FP32); D-update} from the same initial dictionary, with MOD or
+    with the approximate K-SVD sweep.  Per iteration: the RMSE of the encoder's
+    codes, the RMSE right after the update (K-SVD refits the coefficients; MOD
+    keeps them), and the device times of both steps."""
+    import numpy as np
+    import torch
+    N, K, s = X.shape[0], a.K, a.s
+    st = torch.cuda.current_stream()
+    iters = max(2, min(a.steps, 8))
+
+    def rmse_of(D, idx, coef, nnz):
+        il = idx.to(torch.int64) & 0xFFFF
+        live = torch.arange(s, device="cuda")[None, :] < nnz[:, None].to(torch.int64)
+        c = torch.where(live, coef, torch.zeros_like(coef)).double()
+        rec = torch.zeros((N, 45), dtype=torch.float64, device="cuda")
+        for t in range(s):
+            rec += c[:, t, None] * D.double()[il[:, t]]
+        r = X.double() - rec
+        return float(torch.sqrt((r * r).sum() / (N * 45)).item())
+
+    out = {}
+    for method in ("mod", "ksvd"):
+        D = api.init_dictionary(X, init)
+        idx = torch.empty((N, s), dtype=torch.int16, device="cuda")
+        coef = torch.empty((N, s), dtype=torch.float32, device="cuda")
+        nnz = torch.empty((N,), dtype=torch.uint8, device="cuda")
+        resid = torch.empty((N,), dtype=torch.float32, device="cuda")
+        rows, cum = [], 0.0
+        for it in range(iters):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(st)
+            api.encode(D, X, s, precision="fp32", out=(idx, coef, nnz, resid))
+            e[1].record(st)
+            if method == "mod":
+                Dn = api.mod_update(X, D, idx, coef, nnz, resid)
+            else:
+                Dn = api.ksvd_update(X, D, idx, coef, nnz, resid)
+            e[2].record(st)
+            torch.cuda.synchronize()
+            enc_ms, upd_ms = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+            cum += enc_ms + upd_ms
+            rows.append({"iter": it, "rmse_codes": float(torch.sqrt(resid.double().sum() / (N * 45)).item()),
+                         "rmse_after_update": rmse_of(Dn, idx, coef, nnz), "encode_ms": enc_ms,
+                         "update_ms": upd_ms, "cumulative_ms": cum})
+            D = Dn
+        api.encode(D, X, s, precision="fp32", out=(idx, coef, nnz, resid))
+        torch.cuda.synchronize()
+        out[method] = {"iters": rows, "final_rmse": float(torch.sqrt(resid.double().sum() / (N * 45)).item())}
+    print(json.dumps({"leg": "ksvd", "N": N, "K": K, "s": s, "precision": "fp32", **out}))
+
+
 def splat_leg(a):
     """Splatting preprocess (project, cull, colour) of N synthetic Gaussians,
     with the colour read from 45 dense FP32 SH coefficients (the baseline
@@ -566,6 +619,8 @@ def main():
 
     if a.leg == "tolerance":
         return tolerance_leg(a, api, X)
+    if a.leg == "ksvd":
+        return ksvd_leg(a, api, X, init)
     if a.leg != "step":
         return run_leg(a, api, L, X, MU, cam, D, out, rgb, stream)
 

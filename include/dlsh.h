@@ -353,6 +353,29 @@ int dlsh_csc_from_ell(const uint16_t* idx, const float* coef,
                       uint16_t* row_idx, float* val, void* ws, size_t ws_bytes,
                       void* stream, int flags);
 
+/*
+ * Dictionary update read as approximate K-SVD (an alternative to MOD under the
+ * same alternating minimisation of Eq. 1, Sec. 2.1; one power step per atom as
+ * in Rubinstein, Zibulevsky and Elad, 2008).  A sweep over j = 0..K-1 in order:
+ * with w the Gaussians whose first nnz code slots hold atom j, g their current
+ * coefficients of atom j, and R = X - D A the current residual,
+ *   E = R_w + g d_j^T,  d = E^T g / ||E^T g||,  g' = E d,
+ *   d_j <- d,  A[j, w] <- g',  R_w <- E - g' d^T.
+ * An atom whose d is zero is left as it was; atoms no code uses are refilled,
+ * in increasing j, with the normalised signals of largest resid_sq (as in
+ * dlsh_mod_update; with resid_sq NULL they keep D_old).  The supports (idx,
+ * nnz) are unchanged; coef [N*s] is updated IN PLACE.  Atom indices within a
+ * code must be distinct (as the encoder writes them).  D_new [K*d] must not
+ * alias D_old.  Every sum runs in a fixed order: results are bitwise
+ * reproducible.  Limits: K <= 4096, N < 2^26, N*s < 2^31.  The sweep is one
+ * cooperative launch with two bounded grid barriers per used atom.
+ * Workspace: dlsh_ksvd_workspace_size(K, d, s, N) (it holds R: N*45 floats).
+ */
+size_t dlsh_ksvd_workspace_size(int K, int d, int s, int64_t N);
+int dlsh_ksvd_update(const float* X, int64_t N, int d, int K, const uint16_t* idx, float* coef,
+                     const uint8_t* nnz, int s, const float* D_old, const float* resid_sq,
+                     float* D_new, void* ws, size_t ws_bytes, void* stream, int flags);
+
 /* ---- splatting preprocess: project, cull, colour ----------------------------
  * The per-Gaussian preprocess of a Gaussian-splatting renderer, with the
  * colour step read either from dense SH (the baseline renderer) or from the

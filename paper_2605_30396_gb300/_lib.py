@@ -93,6 +93,8 @@ SIGNATURES = {
     "dlsh_compact_codes": (c_int, [P, P, c_int64, c_int, c_int, P, c_int, P, P, c_int]),
     "dlsh_decode_compact": (c_int, [P, c_int, c_int, P, c_int, P, P, c_int, c_int64, P, P, P, P,
                                     c_int]),
+    "dlsh_ksvd_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
+    "dlsh_ksvd_update": (c_int, [P, c_int64, c_int, c_int, P, P, P, c_int, P, P, P, P, c_size_t, P, c_int]),
     "dlsh_preprocess_sh": (c_int, [P, P, P, P, P, c_int]),
     "dlsh_preprocess_codes": (c_int, [P, P, P, c_int, P, P, P, c_int, P, P, c_int]),
     "dlsh_preprocess_compact": (c_int, [P, P, P, c_int, P, c_int, P, P, c_int, P, P, c_int]),

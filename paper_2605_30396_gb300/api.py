@@ -270,6 +270,28 @@ def mod_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     return D_new
 
 
+def ksvd_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
+    """One approximate K-SVD sweep; returns D_new (K, 45).  `coef` (a contiguous
+    FP32 device tensor) is updated in place with the refitted coefficients."""
+    X = _dev_f32(X)
+    D_old = _dev_f32(D_old)
+    N, s = coef.shape
+    K = D_old.shape[0]
+    if not (coef.is_cuda and coef.dtype == torch.float32 and coef.is_contiguous()):
+        raise ValueError("ksvd_update: coef must be a contiguous FP32 CUDA tensor (it is updated in place)")
+    D_new = torch.empty_like(D_old)
+    L = _lib.lib()
+    need = L.dlsh_ksvd_workspace_size(K, D_SH, s, N)
+    if need == 0:
+        raise DlshError(-2, "dlsh_ksvd_workspace_size")
+    ws = workspace(need, key="ksvd")
+    rc = L.dlsh_ksvd_update(_p(X), N, D_SH, K, _p(idx.contiguous()), _p(coef), _p(nnz.contiguous()), s,
+                            _p(D_old), _p(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
+                            _p(ws), ws.numel(), _stream(), FLAG_SYNC if sync else 0)
+    _check(rc, "dlsh_ksvd_update")
+    return D_new
+
+
 def init_dictionary(X, init_idx, sync: bool = False):
     """D_0 = normalised rows of X at init_idx (the learning loop's first step)."""
     X = _dev_f32(X)

@@ -1088,6 +1088,188 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
+// ---- approximate K-SVD (the alternative D-update) ------------------------------
+// A sweep over the atoms in order; atom j and the coefficients that use it are
+// refitted with one power step from the current coefficients g (Rubinstein,
+// Zibulevsky and Elad, 2008):
+//   E = R_w + g d_j^T (R = X - D A, kept current),  d = E^T g / ||E^T g||,
+//   g' = E d,  R_w <- E - g' d^T,  d_j <- d,  A[j, w] <- g'.
+// R lives in the workspace.  One cooperative kernel runs the sweep: per atom,
+// every thread takes list entries lo + tid, lo + tid + (grid threads), ...;
+// phase 1 sums g R_i and g^2 (per-thread, then per CTA in thread order, then
+// over CTAs in CTA order: the result does not depend on timing); a grid
+// barrier; phase 2 forms d in every CTA and updates R, the coefficients and
+// the atom; a second grid barrier before the next atom reads R.
+constexpr int KS_T = 256;          // threads per sweep CTA
+constexpr int KS_RS = KS_T + 1;    // reduction row stride (conflict-free)
+
+struct KsWs {
+  uint32_t* status;
+  int* cnt;
+  int* off;
+  int* atom_total;
+  int* atom_start;
+  uint2* list;
+  float* R;        // N x 45 residual
+  float* part;     // grid x 48 per-CTA partial sums (45 of g R_i, then g^2)
+  int* dead;
+  unsigned* gbar;
+};
+
+constexpr int KS_MAX_GRID = 1024;
+
+static size_t carve_ksvd(void* base, int K, int s, int64_t N, KsWs& w) {
+  Carver c(base);
+  const int64_t T = (N + TS - 1) / TS > 0 ? (N + TS - 1) / TS : 1;
+  w.status = c.take<uint32_t>(64);
+  w.cnt = c.take<int>(static_cast<size_t>(K) * T);
+  w.off = c.take<int>(static_cast<size_t>(K) * T);
+  w.atom_total = c.take<int>(K);
+  w.atom_start = c.take<int>(K + 1);
+  w.list = c.take<uint2>(static_cast<size_t>(N) * s + 1);
+  w.R = c.take<float>(static_cast<size_t>(N) * DLSH_D);
+  w.part = c.take<float>(static_cast<size_t>(KS_MAX_GRID) * 48);
+  w.dead = c.take<int>(K);
+  w.gbar = c.take<unsigned>(64);
+  return c.size();
+}
+
+// R = X - D A with the input codes; one warp per signal, lane d owning
+// dimensions d and d + 32.
+__global__ void __launch_bounds__(256) ksvd_resid_kernel(const float* __restrict__ X, const float* __restrict__ D,
+                                                         int K, const uint16_t* __restrict__ idx,
+                                                         const float* __restrict__ coef,
+                                                         const uint8_t* __restrict__ nnz, int s, int64_t N,
+                                                         float* __restrict__ R) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= N) return;
+  const bool hi = lane < DLSH_D - 32;
+  float r0 = X[i * DLSH_D + lane];
+  float r1 = hi ? X[i * DLSH_D + 32 + lane] : 0.f;
+  int nz = nnz[i];
+  nz = nz > s ? s : nz;
+  const int jl = lane < nz ? idx[i * s + lane] : 0;
+  const float al = lane < nz ? coef[i * s + lane] : 0.f;
+  for (int t = 0; t < nz; ++t) {
+    const int j = __shfl_sync(0xffffffffu, jl, t);
+    const float a = __shfl_sync(0xffffffffu, al, t);
+    if (j >= K) continue;
+    const float* dr = D + static_cast<size_t>(j) * DLSH_D;
+    r0 = fmaf(-a, dr[lane], r0);
+    if (hi) r1 = fmaf(-a, dr[32 + lane], r1);
+  }
+  R[i * DLSH_D + lane] = r0;
+  if (hi) R[i * DLSH_D + 32 + lane] = r1;
+}
+
+__global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict__ atom_start,
+                                                          const uint2* __restrict__ list, int K,
+                                                          const uint16_t* __restrict__ idx, int s,
+                                                          float* __restrict__ coef, const float* __restrict__ D_old,
+                                                          float* __restrict__ D_new, float* __restrict__ R,
+                                                          float* __restrict__ part, int* __restrict__ dead,
+                                                          unsigned* gbar, uint32_t* status, long long budget) {
+  extern __shared__ float red[];  // [46][KS_RS] per-thread sums, transposed
+  __shared__ float dj[48], dn[48], tot[48];
+  __shared__ float dd_s;
+  __shared__ int skip_s;
+  const int tid = threadIdx.x;
+  const int64_t gthreads = static_cast<int64_t>(gridDim.x) * KS_T;
+  const int64_t gtid = static_cast<int64_t>(blockIdx.x) * KS_T + tid;
+  for (int j = 0; j < K; ++j) {
+    const int lo = atom_start[j], hi = atom_start[j + 1];
+    if (blockIdx.x == 0 && tid == 0) dead[j] = hi == lo ? 1 : 0;
+    if (hi == lo) {
+      if (blockIdx.x == 0 && tid < DLSH_D) D_new[static_cast<size_t>(j) * DLSH_D + tid] = D_old[static_cast<size_t>(j) * DLSH_D + tid];
+      continue;  // the same decision in every CTA
+    }
+    if (tid < 48) dj[tid] = tid < DLSH_D ? D_old[static_cast<size_t>(j) * DLSH_D + tid] : 0.f;
+    // ---- phase 1: sum g R_i and g^2 over this thread's entries
+    float acc[DLSH_D];
+#pragma unroll
+    for (int d = 0; d < DLSH_D; ++d) acc[d] = 0.f;
+    float gg = 0.f;
+    for (int64_t e = lo + gtid; e < hi; e += gthreads) {
+      const uint2 rec = list[e];
+      const int64_t i = rec.x & 0x3FFFFFFu;
+      const float g = __uint_as_float(rec.y);
+      gg = fmaf(g, g, gg);
+      const float* ri = R + i * DLSH_D;
+#pragma unroll
+      for (int d = 0; d < DLSH_D; ++d) acc[d] = fmaf(g, __ldcg(ri + d), acc[d]);
+    }
+#pragma unroll
+    for (int d = 0; d < DLSH_D; ++d) red[d * KS_RS + tid] = acc[d];
+    red[DLSH_D * KS_RS + tid] = gg;
+    __syncthreads();
+    if (tid < DLSH_D + 1) {
+      float sum = 0.f;
+      for (int k = 0; k < KS_T; ++k) sum += red[tid * KS_RS + k];
+      __stcg(part + static_cast<size_t>(blockIdx.x) * 48 + tid, sum);
+    }
+    if (!grid_barrier(gbar, budget, status)) return;
+    // ---- phase 2: d = E^T g = sum g R_i + d_j sum g^2, in every CTA
+    if (tid < DLSH_D + 1) {
+      float sum = 0.f;
+      for (int c = 0; c < static_cast<int>(gridDim.x); ++c) sum += __ldcg(part + static_cast<size_t>(c) * 48 + tid);
+      tot[tid] = sum;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const float v0 = fmaf(dj[tid], tot[DLSH_D], tot[tid]);
+      const float v1 = tid < DLSH_D - 32 ? fmaf(dj[32 + tid], tot[DLSH_D], tot[32 + tid]) : 0.f;
+      float n2 = fmaf(v0, v0, v1 * v1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+      const bool zero = !(n2 > 0.f);
+      const float inv = zero ? 0.f : rsqrtf(n2);
+      const float u0 = v0 * inv, u1 = v1 * inv;
+      dn[tid] = u0;
+      if (tid < DLSH_D - 32) dn[32 + tid] = u1;
+      float dd = fmaf(dj[tid], u0, tid < DLSH_D - 32 ? dj[32 + tid] * u1 : 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      if (tid == 0) {
+        dd_s = dd;
+        skip_s = zero ? 1 : 0;
+      }
+      if (blockIdx.x == 0) {
+        float* out = D_new + static_cast<size_t>(j) * DLSH_D;
+        out[tid] = zero ? dj[tid] : u0;
+        if (tid < DLSH_D - 32) out[32 + tid] = zero ? dj[32 + tid] : u1;
+      }
+    }
+    __syncthreads();
+    if (!skip_s) {
+      const float dd = dd_s;
+      for (int64_t e = lo + gtid; e < hi; e += gthreads) {
+        const uint2 rec = list[e];
+        const int64_t i = rec.x & 0x3FFFFFFu;
+        const int nz = static_cast<int>(rec.x >> 26);
+        const float g = __uint_as_float(rec.y);
+        float* ri = R + i * DLSH_D;
+        float r[DLSH_D];
+        float e_dot = 0.f;
+#pragma unroll
+        for (int d = 0; d < DLSH_D; ++d) {
+          r[d] = __ldcg(ri + d);
+          e_dot = fmaf(r[d], dn[d], e_dot);
+        }
+        const float gn = fmaf(g, dd, e_dot);  // E_i . d = R_i . d + g (d_j . d)
+#pragma unroll
+        for (int d = 0; d < DLSH_D; ++d) __stcg(ri + d, fmaf(-gn, dn[d], fmaf(g, dj[d], r[d])));
+        for (int t = 0; t < nz; ++t)
+          if (idx[i * s + t] == j) {
+            coef[i * s + t] = gn;
+            break;
+          }
+      }
+    }
+    if (!grid_barrier(gbar, budget, status)) return;
+  }
+}
+
 }  // namespace mod
 
 size_t mod_ws_bytes(int K, int s, int64_t N) {
@@ -1206,6 +1388,82 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   return check_launch("dlsh_mod_update: launch");
 }
 
+size_t ksvd_ws_bytes(int K, int s, int64_t N) {
+  mod::KsWs w;
+  return mod::carve_ksvd(nullptr, K, s, N, w);
+}
+
+// Enqueues one approximate K-SVD sweep (no host synchronisation).
+int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* coef, const uint8_t* nnz, int s,
+                 const float* D_old, const float* resid, float* D_new, void* ws, cudaStream_t st,
+                 uint32_t** status_out) {
+  using namespace mod;
+  if (N >= (int64_t(1) << 26))
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_ksvd_update: N must be < 2^26");
+  KsWs w;
+  carve_ksvd(ws, K, s, N, w);
+  if (status_out) *status_out = w.status;
+  DLSH_CUDA_TRY(cudaMemsetAsync(w.status, 0, sizeof(uint32_t), st), "dlsh_ksvd_update: reset");
+  const int T = static_cast<int>((N + TS - 1) / TS > 0 ? (N + TS - 1) / TS : 1);
+  int launches = 0;
+  if (N > 0) {
+    count_kernel<<<T, 256, K * sizeof(int), st>>>(idx, nnz, s, N, K, T, w.cnt, w.status);
+  } else {
+    DLSH_CUDA_TRY(cudaMemsetAsync(w.cnt, 0, sizeof(int) * K * T, st), "dlsh_ksvd_update: cnt");
+  }
+  atom_total_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_total);
+  atom_scan_kernel<<<1, 1024, 0, st>>>(w.atom_total, K, w.atom_start);
+  tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
+  launches += (N > 0 ? 1 : 0) + 3;
+  if (N > 0) {
+    const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sc_smem)),
+                  "dlsh_ksvd_update: attribute");
+    scatter_kernel<<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
+    ksvd_resid_kernel<<<static_cast<int>((N + 7) / 8), 256, 0, st>>>(X, D_old, K, idx, coef, nnz, s, N, w.R);
+    launches += 2;
+  }
+  {
+    const size_t smem = static_cast<size_t>(DLSH_D + 1) * KS_RS * sizeof(float);
+    static int coop_grid = 0;
+    if (coop_grid == 0) {
+      int per_sm = 0;
+      DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksvd_sweep_kernel, KS_T, smem),
+                    "dlsh_ksvd_update: occupancy");
+      if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: sweep kernel does not fit");
+      int sms = device_sm_count();
+      if (sms <= 0) sms = 1;
+      coop_grid = sms < KS_MAX_GRID ? sms : KS_MAX_GRID;  // one CTA per SM
+    }
+    DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_ksvd_update: barrier");
+    const int* as = w.atom_start;
+    const uint2* li = w.list;
+    int Kk = K, ss = s;
+    const uint16_t* ix = idx;
+    float* cf = coef;
+    const float* Do = D_old;
+    float* Dn = D_new;
+    float* Rr = w.R;
+    float* pt = w.part;
+    int* dd = w.dead;
+    unsigned* gb = w.gbar;
+    uint32_t* stw = w.status;
+    long long budget = kWaitBudget;
+    void* args[] = {&as, &li, &Kk, &ix, &ss, &cf, &Do, &Dn, &Rr, &pt, &dd, &gb, &stw, &budget};
+    DLSH_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ksvd_sweep_kernel), dim3(coop_grid),
+                                              dim3(KS_T), args, smem, st),
+                  "dlsh_ksvd_update: sweep");
+    ++launches;
+  }
+  if (resid && N > 0) {
+    refill_kernel<<<1, 1024, 0, st>>>(X, resid, N, K, w.dead, D_new);
+    ++launches;
+  }
+  count_launches(launches);
+  return check_launch("dlsh_ksvd_update: launch");
+}
+
 }  // namespace dlsh
 
 extern "C" {
@@ -1240,6 +1498,37 @@ int dlsh_mod_update(const float* X, int64_t N, int d, int K, const uint16_t* idx
   rc = mod_enqueue(X, N, K, idx, coef, nnz, s, D_old, resid_sq, D_new, ws, st, &status);
   if (rc) return rc;
   return finish(st, status, flags, "dlsh_mod_update");
+}
+
+size_t dlsh_ksvd_workspace_size(int K, int d, int s, int64_t N) {
+  if (d != DLSH_D || K < 1 || K > dlsh::mod::MAX_K || s < 1 || s > DLSH_MAX_S || N < 0) return 0;
+  return dlsh::ksvd_ws_bytes(K, s, N);
+}
+
+int dlsh_ksvd_update(const float* X, int64_t N, int d, int K, const uint16_t* idx, float* coef,
+                     const uint8_t* nnz, int s, const float* D_old, const float* resid_sq, float* D_new,
+                     void* ws, size_t ws_bytes, void* stream, int flags) {
+  using namespace dlsh;
+  clear_error();
+  if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_ksvd_update: d must be 45");
+  if (K < 1 || K > mod::MAX_K)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_ksvd_update: K must be in [1, 4096], got %d", K);
+  if (s < 1 || s > DLSH_MAX_S) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_ksvd_update: s must be in [1, 32]");
+  if (N < 0 || N * s >= (1LL << 31))
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_ksvd_update: N*s must be < 2^31");
+  if (!D_old || !D_new) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_ksvd_update: NULL D");
+  if (D_old == D_new) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_ksvd_update: D_new must not alias D_old");
+  if (reinterpret_cast<uintptr_t>(idx) % 4 != 0)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_ksvd_update: idx must be 4-byte aligned");
+  if (N > 0 && (!X || !idx || !coef || !nnz))
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_ksvd_update: NULL array");
+  int rc = check_workspace(ws, ws_bytes, ksvd_ws_bytes(K, s, N), "dlsh_ksvd_update");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint32_t* status = nullptr;
+  rc = ksvd_enqueue(X, N, K, idx, coef, nnz, s, D_old, resid_sq, D_new, ws, st, &status);
+  if (rc) return rc;
+  return finish(st, status, flags, "dlsh_ksvd_update");
 }
 
 }  // extern "C"
