@@ -88,8 +88,9 @@ def test_rank_one_recovery_and_reproducibility(lib):
     for j in range(K):
         w = assign == j
         sign = np.sign(np.dot(c[w], g0[w]))
-        np.testing.assert_allclose(Dg[j], sign * U[j], atol=2e-6)
-        np.testing.assert_allclose(cg[w, 0], sign * c[w], rtol=1e-5, atol=1e-6)
+        # FP32 sums over 500 entries (and X rounded to FP32): a few ulps of drift
+        np.testing.assert_allclose(Dg[j], sign * U[j], atol=1e-5)
+        np.testing.assert_allclose(cg[w, 0], sign * c[w], rtol=3e-5, atol=1e-5)
     Dg2, cg2 = _gpu(lib, X, D0, idx, g0[:, None], nnz, None)
     np.testing.assert_array_equal(Dg, Dg2)
     np.testing.assert_array_equal(cg, cg2)
