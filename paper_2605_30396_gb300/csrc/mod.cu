@@ -227,7 +227,9 @@ __global__ void tile_offsets_kernel(const int* __restrict__ cnt, int T,
 // entry its rank among the earlier entries of its atom (warps in order, then
 // lanes in order) and writes it to the atom-major list.  A signal's atoms are
 // distinct, so within an atom the entries stay in signal order.
+// SLOT: the record's upper 6 bits hold the entry's code slot t instead of nnz.
 constexpr int SC_T = 256;
+template <bool SLOT>
 __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restrict__ idx,
                                                       const float* __restrict__ coef,
                                                       const uint8_t* __restrict__ nnz, int s, int64_t N,
@@ -262,7 +264,9 @@ __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restric
       const int t = e - q * s;
       nz = nnz[sig];
       nz = nz > s ? s : nz;
-      if (t < nz) {
+      const bool live = t < nz;
+      if (SLOT) nz = t;
+      if (live) {
         const int jj = idx[sig * s + t];
         if (jj < K) {
           j = jj;
@@ -1094,14 +1098,18 @@ __global__ void __launch_bounds__(1024)
 // Zibulevsky and Elad, 2008):
 //   E = R_w + g d_j^T (R = X - D A, kept current),  d = E^T g / ||E^T g||,
 //   g' = E d,  R_w <- E - g' d^T,  d_j <- d,  A[j, w] <- g'.
-// R lives in the workspace.  One cooperative kernel runs the sweep: per atom,
-// every thread takes list entries lo + tid, lo + tid + (grid threads), ...;
-// phase 1 sums g R_i and g^2 (per-thread, then per CTA in thread order, then
-// over CTAs in CTA order: the result does not depend on timing); a grid
-// barrier; phase 2 forms d in every CTA and updates R, the coefficients and
-// the atom; a second grid barrier before the next atom reads R.
+// R lives in the workspace, rows padded to 48 floats (16-byte loads).  One
+// cooperative kernel runs the sweep: per atom, every thread takes list entries
+// lo + tid, lo + tid + (grid threads), ...; phase 1 sums g R_i and g^2 (per
+// thread, then a transposing butterfly per warp, then the warps and the CTAs
+// in a fixed order: the result does not depend on timing); a grid barrier;
+// phase 2 forms d in every CTA and updates R, the coefficients and the atom; a
+// second grid barrier before the next atom reads R.  The atom-major list
+// records each entry's code slot, so the coefficient is written directly.
 constexpr int KS_T = 256;          // threads per sweep CTA
-constexpr int KS_RS = KS_T + 1;    // reduction row stride (conflict-free)
+constexpr int KS_W = KS_T / 32;
+constexpr int RROW = 48;           // residual row stride in floats
+constexpr int KS_V = DLSH_D + 1;   // reduced values: 45 of g R_i, then g^2
 
 struct KsWs {
   uint32_t* status;
@@ -1110,8 +1118,8 @@ struct KsWs {
   int* atom_total;
   int* atom_start;
   uint2* list;
-  float* R;        // N x 45 residual
-  float* part;     // grid x 48 per-CTA partial sums (45 of g R_i, then g^2)
+  float* R;        // N x 48 residual (45 used)
+  float* part;     // grid x 48 per-CTA partial sums
   int* dead;
   unsigned* gbar;
 };
@@ -1127,7 +1135,7 @@ static size_t carve_ksvd(void* base, int K, int s, int64_t N, KsWs& w) {
   w.atom_total = c.take<int>(K);
   w.atom_start = c.take<int>(K + 1);
   w.list = c.take<uint2>(static_cast<size_t>(N) * s + 1);
-  w.R = c.take<float>(static_cast<size_t>(N) * DLSH_D);
+  w.R = c.take<float>(static_cast<size_t>(N) * RROW);
   w.part = c.take<float>(static_cast<size_t>(KS_MAX_GRID) * 48);
   w.dead = c.take<int>(K);
   w.gbar = c.take<unsigned>(64);
@@ -1135,7 +1143,7 @@ static size_t carve_ksvd(void* base, int K, int s, int64_t N, KsWs& w) {
 }
 
 // R = X - D A with the input codes; one warp per signal, lane d owning
-// dimensions d and d + 32.
+// dimensions d and d + 32 (and the zero padding 45..47).
 __global__ void __launch_bounds__(256) ksvd_resid_kernel(const float* __restrict__ X, const float* __restrict__ D,
                                                          int K, const uint16_t* __restrict__ idx,
                                                          const float* __restrict__ coef,
@@ -1159,60 +1167,83 @@ __global__ void __launch_bounds__(256) ksvd_resid_kernel(const float* __restrict
     r0 = fmaf(-a, dr[lane], r0);
     if (hi) r1 = fmaf(-a, dr[32 + lane], r1);
   }
-  R[i * DLSH_D + lane] = r0;
-  if (hi) R[i * DLSH_D + 32 + lane] = r1;
+  R[i * RROW + lane] = r0;
+  if (lane < RROW - 32) R[i * RROW + 32 + lane] = r1;
 }
 
 __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict__ atom_start,
-                                                          const uint2* __restrict__ list, int K,
-                                                          const uint16_t* __restrict__ idx, int s,
+                                                          const uint2* __restrict__ list, int K, int s,
                                                           float* __restrict__ coef, const float* __restrict__ D_old,
                                                           float* __restrict__ D_new, float* __restrict__ R,
                                                           float* __restrict__ part, int* __restrict__ dead,
                                                           unsigned* gbar, uint32_t* status, long long budget) {
-  extern __shared__ float red[];  // [46][KS_RS] per-thread sums, transposed
-  __shared__ float dj[48], dn[48], tot[48];
+  extern __shared__ float pall[];  // [gridDim.x][48] the CTAs' partial sums, phase 2
+  __shared__ float wsum[KS_W][64];
+  __shared__ __align__(16) float dj[RROW], dn[RROW];
+  __shared__ float tot[48];
   __shared__ float dd_s;
   __shared__ int skip_s;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t gthreads = static_cast<int64_t>(gridDim.x) * KS_T;
   const int64_t gtid = static_cast<int64_t>(blockIdx.x) * KS_T + tid;
+  const int G = gridDim.x;
   for (int j = 0; j < K; ++j) {
     const int lo = atom_start[j], hi = atom_start[j + 1];
     if (blockIdx.x == 0 && tid == 0) dead[j] = hi == lo ? 1 : 0;
     if (hi == lo) {
-      if (blockIdx.x == 0 && tid < DLSH_D) D_new[static_cast<size_t>(j) * DLSH_D + tid] = D_old[static_cast<size_t>(j) * DLSH_D + tid];
+      if (blockIdx.x == 0 && tid < DLSH_D)
+        D_new[static_cast<size_t>(j) * DLSH_D + tid] = D_old[static_cast<size_t>(j) * DLSH_D + tid];
       continue;  // the same decision in every CTA
     }
-    if (tid < 48) dj[tid] = tid < DLSH_D ? D_old[static_cast<size_t>(j) * DLSH_D + tid] : 0.f;
+    if (tid < RROW) dj[tid] = tid < DLSH_D ? D_old[static_cast<size_t>(j) * DLSH_D + tid] : 0.f;
     // ---- phase 1: sum g R_i and g^2 over this thread's entries
-    float acc[DLSH_D];
+    float v[64];
 #pragma unroll
-    for (int d = 0; d < DLSH_D; ++d) acc[d] = 0.f;
-    float gg = 0.f;
+    for (int d = 0; d < 64; ++d) v[d] = 0.f;
     for (int64_t e = lo + gtid; e < hi; e += gthreads) {
       const uint2 rec = list[e];
       const int64_t i = rec.x & 0x3FFFFFFu;
       const float g = __uint_as_float(rec.y);
-      gg = fmaf(g, g, gg);
-      const float* ri = R + i * DLSH_D;
+      v[DLSH_D] = fmaf(g, g, v[DLSH_D]);
+      const float4* r4 = reinterpret_cast<const float4*>(R + i * RROW);
 #pragma unroll
-      for (int d = 0; d < DLSH_D; ++d) acc[d] = fmaf(g, __ldcg(ri + d), acc[d]);
+      for (int q = 0; q < RROW / 4; ++q) {
+        const float4 x = __ldcg(r4 + q);
+        v[4 * q + 0] = fmaf(g, x.x, v[4 * q + 0]);
+        v[4 * q + 1] = fmaf(g, x.y, v[4 * q + 1]);
+        v[4 * q + 2] = fmaf(g, x.z, v[4 * q + 2]);
+        if (4 * q + 3 < DLSH_D) v[4 * q + 3] = fmaf(g, x.w, v[4 * q + 3]);
+      }
     }
+    // transposing butterfly: after it, lane l holds the warp's sums of values
+    // 2l and 2l + 1 in v[0], v[1]
 #pragma unroll
-    for (int d = 0; d < DLSH_D; ++d) red[d * KS_RS + tid] = acc[d];
-    red[DLSH_D * KS_RS + tid] = gg;
+    for (int m = 64, o = 16; o > 0; m >>= 1, o >>= 1) {
+      const bool up = (lane & o) != 0;
+#pragma unroll
+      for (int k = 0; k < m / 2; ++k) {
+        const float send = up ? v[k] : v[k + m / 2];
+        const float keep = up ? v[k + m / 2] : v[k];
+        v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+      }
+    }
+    wsum[warp][2 * lane] = v[0];
+    wsum[warp][2 * lane + 1] = v[1];
     __syncthreads();
-    if (tid < DLSH_D + 1) {
+    if (tid < KS_V) {
       float sum = 0.f;
-      for (int k = 0; k < KS_T; ++k) sum += red[tid * KS_RS + k];
+#pragma unroll
+      for (int w = 0; w < KS_W; ++w) sum += wsum[w][tid];
       __stcg(part + static_cast<size_t>(blockIdx.x) * 48 + tid, sum);
     }
     if (!grid_barrier(gbar, budget, status)) return;
     // ---- phase 2: d = E^T g = sum g R_i + d_j sum g^2, in every CTA
-    if (tid < DLSH_D + 1) {
+    for (int f = tid; f < G * 48; f += KS_T) pall[f] = __ldcg(part + f);
+    __syncthreads();
+    if (tid < KS_V) {
       float sum = 0.f;
-      for (int c = 0; c < static_cast<int>(gridDim.x); ++c) sum += __ldcg(part + static_cast<size_t>(c) * 48 + tid);
+#pragma unroll 8
+      for (int c = 0; c < G; ++c) sum += pall[c * 48 + tid];
       tot[tid] = sum;
     }
     __syncthreads();
@@ -1226,7 +1257,7 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
       const float inv = zero ? 0.f : rsqrtf(n2);
       const float u0 = v0 * inv, u1 = v1 * inv;
       dn[tid] = u0;
-      if (tid < DLSH_D - 32) dn[32 + tid] = u1;
+      if (tid < RROW - 32) dn[32 + tid] = u1;
       float dd = fmaf(dj[tid], u0, tid < DLSH_D - 32 ? dj[32 + tid] * u1 : 0.f);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
@@ -1243,27 +1274,37 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
     __syncthreads();
     if (!skip_s) {
       const float dd = dd_s;
+      const float4* dn4 = reinterpret_cast<const float4*>(dn);
+      const float4* dj4 = reinterpret_cast<const float4*>(dj);
       for (int64_t e = lo + gtid; e < hi; e += gthreads) {
         const uint2 rec = list[e];
         const int64_t i = rec.x & 0x3FFFFFFu;
-        const int nz = static_cast<int>(rec.x >> 26);
+        const int slot = static_cast<int>(rec.x >> 26);
         const float g = __uint_as_float(rec.y);
-        float* ri = R + i * DLSH_D;
-        float r[DLSH_D];
+        float4* r4 = reinterpret_cast<float4*>(R + i * RROW);
+        float4 r[RROW / 4];
         float e_dot = 0.f;
 #pragma unroll
-        for (int d = 0; d < DLSH_D; ++d) {
-          r[d] = __ldcg(ri + d);
-          e_dot = fmaf(r[d], dn[d], e_dot);
+        for (int q = 0; q < RROW / 4; ++q) {
+          r[q] = __ldcg(r4 + q);
+          const float4 u = dn4[q];
+          e_dot = fmaf(r[q].x, u.x, e_dot);
+          e_dot = fmaf(r[q].y, u.y, e_dot);
+          e_dot = fmaf(r[q].z, u.z, e_dot);
+          e_dot = fmaf(r[q].w, u.w, e_dot);  // padding: r = 0, u = 0
         }
         const float gn = fmaf(g, dd, e_dot);  // E_i . d = R_i . d + g (d_j . d)
 #pragma unroll
-        for (int d = 0; d < DLSH_D; ++d) __stcg(ri + d, fmaf(-gn, dn[d], fmaf(g, dj[d], r[d])));
-        for (int t = 0; t < nz; ++t)
-          if (idx[i * s + t] == j) {
-            coef[i * s + t] = gn;
-            break;
-          }
+        for (int q = 0; q < RROW / 4; ++q) {
+          const float4 u = dn4[q], o = dj4[q];
+          float4 y;
+          y.x = fmaf(-gn, u.x, fmaf(g, o.x, r[q].x));
+          y.y = fmaf(-gn, u.y, fmaf(g, o.y, r[q].y));
+          y.z = fmaf(-gn, u.z, fmaf(g, o.z, r[q].z));
+          y.w = fmaf(-gn, u.w, fmaf(g, o.w, r[q].w));
+          __stcg(r4 + q, y);
+        }
+        coef[i * s + slot] = gn;
       }
     }
     if (!grid_barrier(gbar, budget, status)) return;
@@ -1306,10 +1347,10 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
     const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sc_smem)),
                   "dlsh_mod_update: attribute");
-    scatter_kernel<<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
+    scatter_kernel<false><<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
     ++launches;
   }
   void (*accum)(const float*, const uint16_t*, const float*, int, int, const int*, const int*, int, int, int,
@@ -1417,30 +1458,34 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
     const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sc_smem)),
                   "dlsh_ksvd_update: attribute");
-    scatter_kernel<<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
+    scatter_kernel<true><<<T, SC_T, sc_smem, st>>>(idx, coef, nnz, s, N, K, T, w.off, w.list);
     ksvd_resid_kernel<<<static_cast<int>((N + 7) / 8), 256, 0, st>>>(X, D_old, K, idx, coef, nnz, s, N, w.R);
     launches += 2;
   }
   {
-    const size_t smem = static_cast<size_t>(DLSH_D + 1) * KS_RS * sizeof(float);
     static int coop_grid = 0;
     if (coop_grid == 0) {
       int per_sm = 0;
-      DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksvd_sweep_kernel, KS_T, smem),
-                    "dlsh_ksvd_update: occupancy");
-      if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: sweep kernel does not fit");
       int sms = device_sm_count();
       if (sms <= 0) sms = 1;
-      coop_grid = sms < KS_MAX_GRID ? sms : KS_MAX_GRID;  // one CTA per SM
+      const int g = sms < KS_MAX_GRID ? sms : KS_MAX_GRID;  // one CTA per SM
+      const size_t sm_need = static_cast<size_t>(g) * 48 * sizeof(float);
+      DLSH_CUDA_TRY(cudaFuncSetAttribute(ksvd_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm_need)),
+                    "dlsh_ksvd_update: attribute");
+      DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksvd_sweep_kernel, KS_T, sm_need),
+                    "dlsh_ksvd_update: occupancy");
+      if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: sweep kernel does not fit");
+      coop_grid = g;
     }
+    const size_t smem = static_cast<size_t>(coop_grid) * 48 * sizeof(float);
     DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_ksvd_update: barrier");
     const int* as = w.atom_start;
     const uint2* li = w.list;
     int Kk = K, ss = s;
-    const uint16_t* ix = idx;
     float* cf = coef;
     const float* Do = D_old;
     float* Dn = D_new;
@@ -1450,7 +1495,7 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
     unsigned* gb = w.gbar;
     uint32_t* stw = w.status;
     long long budget = kWaitBudget;
-    void* args[] = {&as, &li, &Kk, &ix, &ss, &cf, &Do, &Dn, &Rr, &pt, &dd, &gb, &stw, &budget};
+    void* args[] = {&as, &li, &Kk, &ss, &cf, &Do, &Dn, &Rr, &pt, &dd, &gb, &stw, &budget};
     DLSH_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ksvd_sweep_kernel), dim3(coop_grid),
                                               dim3(KS_T), args, smem, st),
                   "dlsh_ksvd_update: sweep");
