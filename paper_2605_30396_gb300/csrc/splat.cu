@@ -23,11 +23,12 @@
 //    4-byte granules, coalesced along each row) into a per-warp stage, and each
 //    lane then dots its own row (stride 45 words: no bank conflicts) with its
 //    basis values;
-//  - codes: the dictionary sits in shared memory (FP32 rows of 45, or FP16
-//    (R, G, B, 0) words, 128 bytes per atom), the batch's codes are staged as
-//    (index, coefficient) pairs, and each half-warp takes one visible Gaussian,
-//    lane b owning basis b of the three channels; the three channel sums are
-//    reduced across the half in five shuffles (a transposing butterfly).
+//  - codes: the dictionary sits in shared memory as 16 slots of (R, G, B, 0)
+//    per atom, FP32 (256 bytes) or FP16 (128 bytes); the batch's codes are
+//    staged as (index, coefficient) pairs, and eight lanes take one visible
+//    Gaussian, each lane owning two bases of the three channels; the channel
+//    sums are reduced over the eight lanes in four shuffles (a transposing
+//    butterfly).
 #include <cuda_fp16.h>
 #include <math.h>
 
