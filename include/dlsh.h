@@ -367,9 +367,8 @@ int dlsh_csc_from_ell(const uint16_t* idx, const float* coef,
  * nnz) are unchanged; coef [N*s] is updated IN PLACE.  Atom indices within a
  * code must be distinct (as the encoder writes them).  D_new [K*d] must not
  * alias D_old.  Every sum runs in a fixed order: results are bitwise
- * reproducible.  Limits: K <= 4096, N < 2^26, N*s < 2^31.  The sweep runs on
- * one thread-block cluster (16 CTAs, or 8) with two cluster barriers per used
- * atom.
+ * reproducible.  Limits: K <= 4096, N < 2^26, N*s < 2^31.  The sweep is one
+ * cooperative launch with two bounded grid barriers per used atom.
  * Workspace: dlsh_ksvd_workspace_size(K, d, s, N) (it holds R: N*45 floats).
  */
 size_t dlsh_ksvd_workspace_size(int K, int d, int s, int64_t N);

@@ -1099,14 +1099,14 @@ __global__ void __launch_bounds__(1024)
 //   E = R_w + g d_j^T (R = X - D A, kept current),  d = E^T g / ||E^T g||,
 //   g' = E d,  R_w <- E - g' d^T,  d_j <- d,  A[j, w] <- g'.
 // R lives in the workspace, rows padded to 48 floats (16-byte loads).  One
-// thread-block cluster runs the sweep: per atom, every thread takes list
-// entries lo + tid, lo + tid + (cluster threads), ...; phase 1 sums g R_i and
-// g^2 (per thread, then a transposing butterfly per warp, then the warps and
-// the CTAs in a fixed order: the result does not depend on timing); a cluster
-// barrier; phase 2 forms d in every CTA and updates R, the coefficients and
-// the atom; a second cluster barrier before the next atom reads R.  The atom-major list
+// cooperative kernel runs the sweep: per atom, every thread takes list entries
+// lo + tid, lo + tid + (grid threads), ...; phase 1 sums g R_i and g^2 (per
+// thread, then a transposing butterfly per warp, then the warps and the CTAs
+// in a fixed order: the result does not depend on timing); a grid barrier;
+// phase 2 forms d in every CTA and updates R, the coefficients and the atom; a
+// second grid barrier before the next atom reads R.  The atom-major list
 // records each entry's code slot, so the coefficient is written directly.
-constexpr int KS_T = 512;          // threads per sweep CTA
+constexpr int KS_T = 256;          // threads per sweep CTA
 constexpr int KS_W = KS_T / 32;
 constexpr int RROW = 48;           // residual row stride in floats
 constexpr int KS_V = DLSH_D + 1;   // reduced values: 45 of g R_i, then g^2
@@ -1119,8 +1119,12 @@ struct KsWs {
   int* atom_start;
   uint2* list;
   float* R;        // N x 48 residual (45 used)
+  float* part;     // grid x 48 per-CTA partial sums
   int* dead;
+  unsigned* gbar;
 };
+
+constexpr int KS_MAX_GRID = 1024;
 
 static size_t carve_ksvd(void* base, int K, int s, int64_t N, KsWs& w) {
   Carver c(base);
@@ -1132,7 +1136,9 @@ static size_t carve_ksvd(void* base, int K, int s, int64_t N, KsWs& w) {
   w.atom_start = c.take<int>(K + 1);
   w.list = c.take<uint2>(static_cast<size_t>(N) * s + 1);
   w.R = c.take<float>(static_cast<size_t>(N) * RROW);
+  w.part = c.take<float>(static_cast<size_t>(KS_MAX_GRID) * 48);
   w.dead = c.take<int>(K);
+  w.gbar = c.take<unsigned>(64);
   return c.size();
 }
 
@@ -1165,50 +1171,27 @@ __global__ void __launch_bounds__(256) ksvd_resid_kernel(const float* __restrict
   if (lane < RROW - 32) R[i * RROW + 32 + lane] = r1;
 }
 
-// ---- thread-block cluster helpers (the sweep runs as one cluster) ----------------
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-// Reads the float at the same shared-memory offset in CTA `rank` of the cluster.
-__device__ __forceinline__ float ld_cluster_f32(const float* local, uint32_t rank) {
-  uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
-  return v;
-}
-
-// One thread-block cluster runs the whole sweep: the atoms are sequential, and
-// the cluster's hardware barrier (two per used atom) costs far less than a
-// grid-wide one.  The CTAs' partial sums are read over distributed shared
-// memory.  Every CTA takes the same branches (all decisions come from data
-// every CTA reads identically), so every barrier is reached by all.
 __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict__ atom_start,
                                                           const uint2* __restrict__ list, int K, int s,
                                                           float* __restrict__ coef, const float* __restrict__ D_old,
                                                           float* __restrict__ D_new, float* __restrict__ R,
-                                                          int* __restrict__ dead) {
+                                                          float* __restrict__ part, int* __restrict__ dead,
+                                                          unsigned* gbar, uint32_t* status, long long budget) {
+  extern __shared__ float pall[];  // [gridDim.x][48] the CTAs' partial sums, phase 2
   __shared__ float wsum[KS_W][64];
-  __shared__ float mypart[48];
   __shared__ __align__(16) float dj[RROW], dn[RROW];
   __shared__ float tot[48];
   __shared__ float dd_s;
   __shared__ int skip_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t crank = cluster_rank();
-  const int C = gridDim.x;  // the grid is one cluster
-  const int64_t gthreads = static_cast<int64_t>(C) * KS_T;
-  const int64_t gtid = static_cast<int64_t>(crank) * KS_T + tid;
+  const int64_t gthreads = static_cast<int64_t>(gridDim.x) * KS_T;
+  const int64_t gtid = static_cast<int64_t>(blockIdx.x) * KS_T + tid;
+  const int G = gridDim.x;
   for (int j = 0; j < K; ++j) {
     const int lo = atom_start[j], hi = atom_start[j + 1];
-    if (crank == 0 && tid == 0) dead[j] = hi == lo ? 1 : 0;
+    if (blockIdx.x == 0 && tid == 0) dead[j] = hi == lo ? 1 : 0;
     if (hi == lo) {
-      if (crank == 0 && tid < DLSH_D)
+      if (blockIdx.x == 0 && tid < DLSH_D)
         D_new[static_cast<size_t>(j) * DLSH_D + tid] = D_old[static_cast<size_t>(j) * DLSH_D + tid];
       continue;  // the same decision in every CTA
     }
@@ -1251,13 +1234,16 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
       float sum = 0.f;
 #pragma unroll
       for (int w = 0; w < KS_W; ++w) sum += wsum[w][tid];
-      mypart[tid] = sum;
+      __stcg(part + static_cast<size_t>(blockIdx.x) * 48 + tid, sum);
     }
-    cluster_sync_all();  // every CTA's partial sums are in place
+    if (!grid_barrier(gbar, budget, status)) return;
     // ---- phase 2: d = E^T g = sum g R_i + d_j sum g^2, in every CTA
+    for (int f = tid; f < G * 48; f += KS_T) pall[f] = __ldcg(part + f);
+    __syncthreads();
     if (tid < KS_V) {
       float sum = 0.f;
-      for (int c = 0; c < C; ++c) sum += ld_cluster_f32(mypart + tid, static_cast<uint32_t>(c));
+#pragma unroll 8
+      for (int c = 0; c < G; ++c) sum += pall[c * 48 + tid];
       tot[tid] = sum;
     }
     __syncthreads();
@@ -1279,7 +1265,7 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
         dd_s = dd;
         skip_s = zero ? 1 : 0;
       }
-      if (crank == 0) {
+      if (blockIdx.x == 0) {
         float* out = D_new + static_cast<size_t>(j) * DLSH_D;
         out[tid] = zero ? dj[tid] : u0;
         if (tid < DLSH_D - 32) out[32 + tid] = zero ? dj[32 + tid] : u1;
@@ -1321,9 +1307,7 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
         coef[i * s + slot] = gn;
       }
     }
-    // the residual updates are visible to the whole cluster before the next
-    // atom reads them, and no CTA rewrites its partials while another reads
-    cluster_sync_all();
+    if (!grid_barrier(gbar, budget, status)) return;
   }
 }
 
@@ -1482,45 +1466,38 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
     launches += 2;
   }
   {
-    // one cluster of 16 CTAs (8 where 16 cannot be scheduled)
-    static int csize = 0;
-    if (csize == 0) {
-      DLSH_CUDA_TRY(cudaFuncSetAttribute(ksvd_sweep_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+    static int coop_grid = 0;
+    if (coop_grid == 0) {
+      int per_sm = 0;
+      int sms = device_sm_count();
+      if (sms <= 0) sms = 1;
+      const int g = sms < KS_MAX_GRID ? sms : KS_MAX_GRID;  // one CTA per SM
+      const size_t sm_need = static_cast<size_t>(g) * 48 * sizeof(float);
+      DLSH_CUDA_TRY(cudaFuncSetAttribute(ksvd_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(sm_need)),
                     "dlsh_ksvd_update: attribute");
-      for (int c : {16, 8}) {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(c);
-        cfg.blockDim = dim3(KS_T);
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = c;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, ksvd_sweep_kernel, &cfg) == cudaSuccess && n >= 1) {
-          csize = c;
-          break;
-        }
-        cudaGetLastError();
-      }
-      if (csize == 0) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: no cluster of 8 CTAs fits");
+      DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksvd_sweep_kernel, KS_T, sm_need),
+                    "dlsh_ksvd_update: occupancy");
+      if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: sweep kernel does not fit");
+      coop_grid = g;
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(csize);
-    cfg.blockDim = dim3(KS_T);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = csize;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    DLSH_CUDA_TRY(cudaLaunchKernelEx(&cfg, ksvd_sweep_kernel, static_cast<const int*>(w.atom_start),
-                                     static_cast<const uint2*>(w.list), K, s, coef, D_old, D_new, w.R, w.dead),
+    const size_t smem = static_cast<size_t>(coop_grid) * 48 * sizeof(float);
+    DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_ksvd_update: barrier");
+    const int* as = w.atom_start;
+    const uint2* li = w.list;
+    int Kk = K, ss = s;
+    float* cf = coef;
+    const float* Do = D_old;
+    float* Dn = D_new;
+    float* Rr = w.R;
+    float* pt = w.part;
+    int* dd = w.dead;
+    unsigned* gb = w.gbar;
+    uint32_t* stw = w.status;
+    long long budget = kWaitBudget;
+    void* args[] = {&as, &li, &Kk, &ss, &cf, &Do, &Dn, &Rr, &pt, &dd, &gb, &stw, &budget};
+    DLSH_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ksvd_sweep_kernel), dim3(coop_grid),
+                                              dim3(KS_T), args, smem, st),
                   "dlsh_ksvd_update: sweep");
     ++launches;
   }
