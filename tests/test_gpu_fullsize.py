@@ -87,3 +87,53 @@ def test_mod_full_update(lib, scene):
                              idx, scene["coef"].cpu().numpy().astype(np.float64),
                              scene["nnz"].cpu().numpy(), scene["resid"].cpu().numpy().astype(np.float64))
     np.testing.assert_allclose(Dn, ref, atol=3e-6, rtol=0)
+
+
+def test_splat_preprocess_full_size_sampled(lib):
+    """The splatting preprocess at the bench leg's size (3M Gaussians, image
+    1920 x 1080, focal 1100, the view outside the cloud), dense SH and compact
+    codes (K = 1024, s = 8): 2,000 sampled Gaussians against the oracle (the
+    preprocess is independent per Gaussian)."""
+    from oracle import splat as osp
+    n = 3_000_000
+    W_, H_, F = 1920, 1080, 1100.0
+    g = synth.splat_gaussians(n, 11)
+    R, t = synth.look_at((0.4, -3.2, 1.1), (0.0, 0.0, 0.0))
+    R32, t32 = R.astype(np.float32), t.astype(np.float32)
+    cam = lib.camera(R32, t32, F, F, W_, H_, 0.2)
+    gd = [torch.from_numpy(a).cuda() for a in g]
+    y = (0.2 * np.random.default_rng(12).standard_normal((n, 45))).astype(np.float32)
+    D = synth.hidden_dictionary(K, 13).astype(np.float32)
+    idx, coef, nnz = synth.random_codes(n, K, S, 14, nnz_min=1)
+    samp = np.random.default_rng(15).choice(n, 2000, replace=False)
+    gs = [a[samp].astype(np.float64) for a in g]
+    for colour in ("sh", "compact"):
+        if colour == "sh":
+            out = lib.preprocess(cam, *gd, sh=torch.from_numpy(y).cuda(), sync=True)
+            ref = osp.preprocess(gs[0], gs[1], gs[2], R32.astype(np.float64), t32.astype(np.float64), F, F, W_, H_,
+                                 0.2, gs[3], y=y[samp].astype(np.float64))
+        else:
+            idx_c, coef_c = lib.compact_codes(torch.from_numpy(idx.view(np.int16)).cuda(),
+                                              torch.from_numpy(coef).cuda(), K, sync=True)
+            out = lib.preprocess(cam, *gd, D=torch.from_numpy(D), idx=idx_c, coef=coef_c,
+                                 nnz=torch.from_numpy(nnz).cuda(), sync=True)
+            ref = osp.preprocess(gs[0], gs[1], gs[2], R32.astype(np.float64), t32.astype(np.float64), F, F, W_, H_,
+                                 0.2, gs[3], D=D.astype(np.float16).astype(np.float64),
+                                 idx=idx[samp].astype(np.int64),
+                                 coef=coef[samp].astype(np.float16).astype(np.float64), nnz=nnz[samp])
+        got = {k: v.cpu().numpy()[samp] for k, v in out.items()}
+        raw = ref["raw"]
+        ext = raw["extent"]
+        rc = np.ceil(ext)
+        # a deciding quantity within rounding of its threshold may go either way
+        amb = np.abs(ext - np.round(ext)) < 1e-4 * (1 + ext)
+        for edge in (raw["px"] + rc, W_ - (raw["px"] - rc), raw["py"] + rc, H_ - (raw["py"] - rc)):
+            amb |= np.abs(edge) < 2e-2
+        vo, vg = ref["radius"] > 0, got["radius"] > 0
+        assert vo.mean() > 0.99
+        assert (vo == vg)[~amb].all()
+        sel = vo & vg & ~amb
+        assert (got["radius"][sel] == ref["radius"][sel]).all()
+        for k in ("xy", "depth", "conic", "rgb"):
+            ok, worst = close_rel(got[k][sel], ref[k][sel])
+            assert ok, (colour, k, worst)

@@ -112,3 +112,21 @@ def test_ksvd_rejects_aliasing_and_bad_sizes(lib):
     rc = L.dlsh_ksvd_update(p(X), 10, 45, 8, p(idx), p(coef), p(nnz), 4, p(D), None, p(D), p(ws), ws.numel(),
                             None, 1)
     assert rc != 0
+
+
+def test_ksvd_k1024_random_codes(lib):
+    """K = 1024, s = 8 (the scene's dictionary size) on 200,000 signals with
+    random distinct supports: every atom's entries spread over many CTAs."""
+    N, K, s = 200_000, 1024, 8
+    rng = np.random.default_rng(31)
+    X = synth.signals(N, synth.hidden_dictionary(K, 32), s, 33)
+    D0 = synth.hidden_dictionary(K, 34).astype(np.float32)
+    idx = synth.distinct_supports(rng, N, K, s).astype(np.uint16)
+    coef = rng.laplace(0, 1, (N, s)).astype(np.float32)
+    nnz = np.full(N, s, dtype=np.uint8)
+    Dg, cg = _gpu(lib, X, D0, idx, coef, nnz, None)
+    Do, co, info = _oracle(X, D0, idx, coef, nnz, None)
+    ok, worst = close_rel(Dg, Do)
+    assert ok, ("D", worst)
+    ok, worst = close_rel(cg, co)
+    assert ok, ("coef", worst)
