@@ -5,7 +5,7 @@
 //
 // Bound by shared-memory wavefronts, not HBM: the dictionary is staged once
 // per CTA in shared memory and every nonzero reads a whole atom (45 values).
-// A warp takes batches of 16 Gaussians: the batch's codes are loaded
+// A warp takes batches of 8 (FP32 table) or 16 Gaussians: the batch's codes are loaded
 // (coalesced) into shared memory as (index, coefficient) pairs while one lane
 // per Gaussian computes its direction and 15 basis values; then eight lanes take
 // one Gaussian (four Gaussians per warp step), lane q owning bases 2q and 2q+1
@@ -33,7 +33,11 @@ enum : int { FM_F32 = 0, FM_GLOBAL = 1, FM_C8 = 2, FM_C16 = 3 };
 
 constexpr int YS = 16;          // basis values per Gaussian slot (15 and a zero)
 constexpr int SMEM_LIMIT = 232448;
-constexpr int GB = 16;          // Gaussians per warp batch (small batches: more warps fit per SM)
+// Gaussians per warp batch: 8 beside the 192 KB FP32 table (small batches let
+// more warps fit in the shared memory left), 16 with the FP16 table (whose
+// warps already reach 32 per CTA, where the larger batch costs less per
+// Gaussian).
+__host__ __device__ constexpr int batch_of(int fm) { return fm == 0 ? 8 : 16; }
 
 // Code slots staged per Gaussian: even (16-byte pair reads), and not a multiple
 // of four, so that the four Gaussians of a step read different bank groups.
@@ -43,7 +47,7 @@ inline int staged_slots(int s) {
   return sp;
 }
 // Per-warp shared memory: basis slots, staged rgb, codes, nnz.
-__host__ __device__ constexpr int warp_floats(int sp) { return GB * YS + GB * 3 + GB * sp * 2 + GB; }
+__host__ __device__ constexpr int warp_floats(int sp, int gb) { return gb * YS + gb * 3 + gb * sp * 2 + gb; }
 __host__ __device__ constexpr int dict_floats(int fm, int K) { return fm == FM_F32 ? K * 48 : fm >= FM_C8 ? K * 32 : 0; }
 
 __constant__ ShConst g_sh;
@@ -55,6 +59,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
     const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
     float* __restrict__ rgb, uint32_t* status) {
   extern __shared__ __align__(16) float sm[];
+  constexpr int GB = batch_of(FM);
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
     }
     __syncthreads();
   }
-  float* wsm = sm + dwords + warp * warp_floats(sp);
+  float* wsm = sm + dwords + warp * warp_floats(sp, GB);
   float* Ys = wsm;
   float* outs = wsm + GB * YS;
   uint2* cpk = reinterpret_cast<uint2*>(wsm + GB * YS + GB * 3);
@@ -295,13 +300,14 @@ static int launch_decode(const float* D, int K, const void* idx, const void* coe
   if (sms <= 0) sms = 1;
   const int sp = staged_slots(s);
   const uint32_t sdiv = s >= 2 ? static_cast<uint32_t>((uint64_t(1) << 32) / static_cast<uint64_t>(s) + 1) : 0u;
-  const size_t smem = static_cast<size_t>(dict_floats(FM, K) + nwarps * warp_floats(sp)) * 4;
+  constexpr int gb = batch_of(FM);
+  const size_t smem = static_cast<size_t>(dict_floats(FM, K) + nwarps * warp_floats(sp, gb)) * 4;
   DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                 call);
   int per_sm = 0;
   DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<FM>, nwarps * 32, smem), call);
   if (per_sm < 1) per_sm = 1;
-  const int64_t nbatch = (N + GB - 1) / GB;
+  const int64_t nbatch = (N + gb - 1) / gb;
   int64_t grid = static_cast<int64_t>(sms) * per_sm;
   const int64_t need = (nbatch + nwarps - 1) / nwarps;
   if (grid > need) grid = need;
@@ -315,7 +321,7 @@ static int launch_decode(const float* D, int K, const void* idx, const void* coe
 // Warps per CTA that fit beside the dictionary of format fm (0 if none do).
 static int fit_warps(int fm, int K, int s) {
   const long long room = SMEM_LIMIT - 4LL * dict_floats(fm, K);
-  const long long wb = 4LL * warp_floats(staged_slots(s));
+  const long long wb = 4LL * warp_floats(staged_slots(s), batch_of(fm));
   long long n = room > 0 ? room / wb : 0;
   return static_cast<int>(n > 32 ? 32 : n);
 }
@@ -362,7 +368,7 @@ extern "C" int dlsh_decode(const float* D, int K, int d, const uint16_t* idx, co
 extern "C" size_t dlsh_decode_compact_max_k(int s) {
   using namespace dlsh::dec;
   if (s < 1 || s > DLSH_MAX_S) return 0;
-  const size_t wb = static_cast<size_t>(warp_floats(staged_slots(s))) * 4;
+  const size_t wb = static_cast<size_t>(warp_floats(staged_slots(s), batch_of(FM_C8))) * 4;
   return (static_cast<size_t>(SMEM_LIMIT) - 6 * wb) / 128;
 }
 
