@@ -1187,12 +1187,23 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
   const int64_t gthreads = static_cast<int64_t>(gridDim.x) * KS_T;
   const int64_t gtid = static_cast<int64_t>(blockIdx.x) * KS_T + tid;
   const int G = gridDim.x;
+  // The list is read-only during the sweep: the next atom's bounds and this
+  // thread's first record of it are loaded ahead, while the current atom is
+  // being processed.  A thread's first entry of the current atom (record and
+  // residual row) stays in registers from phase 1 to phase 2.
+  int lo = atom_start[0], hi = K > 0 ? atom_start[1] : 0;
+  uint2 rec_next = lo + gtid < hi ? list[lo + gtid] : make_uint2(0u, 0u);
   for (int j = 0; j < K; ++j) {
-    const int lo = atom_start[j], hi = atom_start[j + 1];
+    const uint2 rec0 = rec_next;
+    const int nlo = hi;
+    const int nhi = j + 2 <= K ? atom_start[j + 2] : hi;
     if (blockIdx.x == 0 && tid == 0) dead[j] = hi == lo ? 1 : 0;
     if (hi == lo) {
       if (blockIdx.x == 0 && tid < DLSH_D)
         D_new[static_cast<size_t>(j) * DLSH_D + tid] = D_old[static_cast<size_t>(j) * DLSH_D + tid];
+      rec_next = nlo + gtid < nhi ? list[nlo + gtid] : make_uint2(0u, 0u);
+      lo = nlo;
+      hi = nhi;
       continue;  // the same decision in every CTA
     }
     if (tid < RROW) dj[tid] = tid < DLSH_D ? D_old[static_cast<size_t>(j) * DLSH_D + tid] : 0.f;
@@ -1200,7 +1211,27 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
     float v[64];
 #pragma unroll
     for (int d = 0; d < 64; ++d) v[d] = 0.f;
-    for (int64_t e = lo + gtid; e < hi; e += gthreads) {
+    const bool has0 = lo + gtid < hi;
+    const int64_t i0 = rec0.x & 0x3FFFFFFu;
+    const float g0 = __uint_as_float(rec0.y);
+    float4 r0[RROW / 4];
+    if (has0) {
+      const float4* r4 = reinterpret_cast<const float4*>(R + i0 * RROW);
+#pragma unroll
+      for (int q = 0; q < RROW / 4; ++q) r0[q] = __ldcg(r4 + q);
+#pragma unroll
+      for (int q = 0; q < RROW / 4; ++q) {
+        if (4 * q + 0 < DLSH_D) v[4 * q + 0] = g0 * r0[q].x;
+        if (4 * q + 1 < DLSH_D) v[4 * q + 1] = g0 * r0[q].y;
+        if (4 * q + 2 < DLSH_D) v[4 * q + 2] = g0 * r0[q].z;
+        if (4 * q + 3 < DLSH_D) v[4 * q + 3] = g0 * r0[q].w;
+      }
+      v[DLSH_D] = g0 * g0;  // after the row: slot 45 of the row is padding
+    } else {
+#pragma unroll
+      for (int q = 0; q < RROW / 4; ++q) r0[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int64_t e = lo + gtid + gthreads; e < hi; e += gthreads) {
       const uint2 rec = list[e];
       const int64_t i = rec.x & 0x3FFFFFFu;
       const float g = __uint_as_float(rec.y);
@@ -1237,6 +1268,7 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
       __stcg(part + static_cast<size_t>(blockIdx.x) * 48 + tid, sum);
     }
     if (!grid_barrier(gbar, budget, status)) return;
+    rec_next = nlo + gtid < nhi ? list[nlo + gtid] : make_uint2(0u, 0u);
     // ---- phase 2: d = E^T g = sum g R_i + d_j sum g^2, in every CTA
     for (int f = tid; f < G * 48; f += KS_T) pall[f] = __ldcg(part + f);
     __syncthreads();
@@ -1276,7 +1308,32 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
       const float dd = dd_s;
       const float4* dn4 = reinterpret_cast<const float4*>(dn);
       const float4* dj4 = reinterpret_cast<const float4*>(dj);
-      for (int64_t e = lo + gtid; e < hi; e += gthreads) {
+      if (has0) {
+        // the first entry: record and row still in registers
+        float e_dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < RROW / 4; ++q) {
+          const float4 u = dn4[q];
+          e_dot = fmaf(r0[q].x, u.x, e_dot);
+          e_dot = fmaf(r0[q].y, u.y, e_dot);
+          e_dot = fmaf(r0[q].z, u.z, e_dot);
+          e_dot = fmaf(r0[q].w, u.w, e_dot);
+        }
+        const float gn = fmaf(g0, dd, e_dot);
+        float4* r4 = reinterpret_cast<float4*>(R + i0 * RROW);
+#pragma unroll
+        for (int q = 0; q < RROW / 4; ++q) {
+          const float4 u = dn4[q], o = dj4[q];
+          float4 y;
+          y.x = fmaf(-gn, u.x, fmaf(g0, o.x, r0[q].x));
+          y.y = fmaf(-gn, u.y, fmaf(g0, o.y, r0[q].y));
+          y.z = fmaf(-gn, u.z, fmaf(g0, o.z, r0[q].z));
+          y.w = fmaf(-gn, u.w, fmaf(g0, o.w, r0[q].w));
+          __stcg(r4 + q, y);
+        }
+        coef[i0 * s + static_cast<int>(rec0.x >> 26)] = gn;
+      }
+      for (int64_t e = lo + gtid + gthreads; e < hi; e += gthreads) {
         const uint2 rec = list[e];
         const int64_t i = rec.x & 0x3FFFFFFu;
         const int slot = static_cast<int>(rec.x >> 26);
@@ -1308,6 +1365,8 @@ __global__ void __launch_bounds__(KS_T) ksvd_sweep_kernel(const int* __restrict_
       }
     }
     if (!grid_barrier(gbar, budget, status)) return;
+    lo = nlo;
+    hi = nhi;
   }
 }
 

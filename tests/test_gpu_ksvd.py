@@ -130,3 +130,12 @@ def test_ksvd_k1024_random_codes(lib):
     assert ok, ("D", worst)
     ok, worst = close_rel(cg, co)
     assert ok, ("coef", worst)
+
+
+def test_ksvd_empty(lib):
+    D0 = synth.hidden_dictionary(12, 2).astype(np.float32)
+    X = np.zeros((0, 45), dtype=np.float32)
+    Dg, cg = _gpu(lib, X, D0, np.zeros((0, 4), dtype=np.uint16), np.zeros((0, 4), dtype=np.float32),
+                  np.zeros(0, dtype=np.uint8), np.zeros(0, dtype=np.float32))
+    np.testing.assert_array_equal(Dg, D0)  # every atom unused, nothing to refill from
+    assert cg.shape == (0, 4)
