@@ -115,18 +115,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, long long budget, ui
   return ok_s != 0;
 }
 
-// ---- packed FP32 FMA (two lanes of fma.rn per instruction) ------------------
-// d = a * b + c per component, each rounded once as fmaf does.
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-  float2 d;
-  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
-      "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
-      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-      : "=f"(d.x), "=f"(d.y)
-      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-  return d;
-}
-
 // ---- proxy fences --------------------------------------------------------
 // Make generic-proxy shared-memory writes visible to the async proxy (TMA and
 // the tensor cores read shared memory through it).

@@ -192,9 +192,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       const int nzl = act ? nzs[gs] : 0;
       int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
       nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
-      // accumulators in pairs for the packed FMA: (R, G) of basis 2ql, (R, G)
-      // of basis 2ql + 1, and (B of 2ql, B of 2ql + 1)
-      float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f), accC = make_float2(0.f, 0.f);
+      float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
 #pragma unroll 2
       for (int t = 0; t < nzp; t += 2) {
         const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gs * sp + t);
@@ -203,37 +201,43 @@ __global__ void __launch_bounds__(1024) decode_kernel(
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const float a = at[u];
-          const float2 aa = make_float2(a, a);
           if (FM == FM_F32) {
-            // planes: R of bases 2ql, 2ql + 1; then G; then B
             const float* row = sm + jt[u] * 48 + 2 * ql;
             const float2 r = *reinterpret_cast<const float2*>(row);
             const float2 gg = *reinterpret_cast<const float2*>(row + 16);
             const float2 bb = *reinterpret_cast<const float2*>(row + 32);
-            accA = ffma2(aa, make_float2(r.x, gg.x), accA);
-            accB = ffma2(aa, make_float2(r.y, gg.y), accB);
-            accC = ffma2(aa, bb, accC);
+            aR = fmaf(a, r.x, aR);
+            bR = fmaf(a, r.y, bR);
+            aG = fmaf(a, gg.x, aG);
+            bG = fmaf(a, gg.y, bG);
+            aB = fmaf(a, bb.x, aB);
+            bBl = fmaf(a, bb.y, bBl);
           } else if (FM == FM_GLOBAL) {
             // bases 2ql and 2ql + 1 of the atom's row (basis 15 does not exist)
             const float* row = D + static_cast<size_t>(jt[u]) * DLSH_D + 2 * ql;
-            accA = ffma2(aa, make_float2(__ldg(row), __ldg(row + 15)), accA);
-            const float b1 = ql < 7 ? __ldg(row + 31) : 0.f;
-            accC = ffma2(aa, make_float2(__ldg(row + 30), b1), accC);
-            if (ql < 7) accB = ffma2(aa, make_float2(__ldg(row + 1), __ldg(row + 16)), accB);
+            aR = fmaf(a, __ldg(row), aR);
+            aG = fmaf(a, __ldg(row + 15), aG);
+            aB = fmaf(a, __ldg(row + 30), aB);
+            if (ql < 7) {
+              bR = fmaf(a, __ldg(row + 1), bR);
+              bG = fmaf(a, __ldg(row + 16), bG);
+              bBl = fmaf(a, __ldg(row + 31), bBl);
+            }
           } else {
-            // (R, G) and (B, 0) of basis 2ql, then of basis 2ql + 1
             const uint4 w = reinterpret_cast<const uint4*>(sm)[jt[u] * 8 + ql];
             const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
+            const float2 bz = __half22float2(*reinterpret_cast<const __half2*>(&w.y));
             const float2 rh = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
-            const float b0 = __low2float(*reinterpret_cast<const __half2*>(&w.y));
-            const float b1 = __low2float(*reinterpret_cast<const __half2*>(&w.w));
-            accA = ffma2(aa, rg, accA);
-            accB = ffma2(aa, rh, accB);
-            accC = ffma2(aa, make_float2(b0, b1), accC);
+            const float2 bh = __half22float2(*reinterpret_cast<const __half2*>(&w.w));
+            aR = fmaf(a, rg.x, aR);
+            aG = fmaf(a, rg.y, aG);
+            aB = fmaf(a, bz.x, aB);
+            bR = fmaf(a, rh.x, bR);
+            bG = fmaf(a, rh.y, bG);
+            bBl = fmaf(a, bh.x, bBl);
           }
         }
       }
-      const float aR = accA.x, aG = accA.y, aB = accC.x, bR = accB.x, bG = accB.y, bBl = accC.y;
       const float2 yy = *reinterpret_cast<const float2*>(Ys + gs * YS + 2 * ql);
       const float p0 = fmaf(yy.x, aR, yy.y * bR), p1 = fmaf(yy.x, aG, yy.y * bG),
                   p2 = fmaf(yy.x, aB, yy.y * bBl);

@@ -356,37 +356,54 @@ __global__ void __launch_bounds__(1024) preprocess_kernel(const __grid_constant_
         const int nzl = act ? nzs[gl] : 0;
         int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
         nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
-        // accumulators in pairs for the packed FMA: (R, G) of basis A, (R, G)
-        // of basis B, and (B of A, B of B)
-        float2 accA = make_float2(0.f, 0.f), accB = make_float2(0.f, 0.f), accC = make_float2(0.f, 0.f);
+        float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
 #pragma unroll 2
         for (int t = 0; t < nzp; t += 2) {
           const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gl * sp + t);
-          const uint32_t jt[2] = {c2.x, c2.z};
-          const float at[2] = {__uint_as_float(c2.y), __uint_as_float(c2.w)};
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const float2 aa = make_float2(at[u], at[u]);
-            if (CM == CM_F32) {
-              const float4* D4 = reinterpret_cast<const float4*>(sm);
-              const float4 x = D4[jt[u] * 16 + bA], y = D4[jt[u] * 16 + bB];
-              accA = ffma2(aa, make_float2(x.x, x.y), accA);
-              accB = ffma2(aa, make_float2(y.x, y.y), accB);
-              accC = ffma2(aa, make_float2(x.z, y.z), accC);
-            } else {
-              // (R, G) and (B, 0) of basis 2ql, then of basis 2ql + 1
-              const uint4 w = reinterpret_cast<const uint4*>(sm)[jt[u] * 8 + ql];
-              const float2 rg = __half22float2(*reinterpret_cast<const __half2*>(&w.x));
-              const float2 rh = __half22float2(*reinterpret_cast<const __half2*>(&w.z));
-              const float b0 = __low2float(*reinterpret_cast<const __half2*>(&w.y));
-              const float b1 = __low2float(*reinterpret_cast<const __half2*>(&w.w));
-              accA = ffma2(aa, rg, accA);
-              accB = ffma2(aa, rh, accB);
-              accC = ffma2(aa, make_float2(b0, b1), accC);
-            }
+          const uint32_t j0 = c2.x, j1 = c2.z;
+          const float a0 = __uint_as_float(c2.y), a1 = __uint_as_float(c2.w);
+          if (CM == CM_F32) {
+            const float4* D4 = reinterpret_cast<const float4*>(sm);
+            const float4 x0 = D4[j0 * 16 + bA], y0 = D4[j0 * 16 + bB];
+            const float4 x1 = D4[j1 * 16 + bA], y1 = D4[j1 * 16 + bB];
+            aR = fmaf(a0, x0.x, aR);
+            aG = fmaf(a0, x0.y, aG);
+            aB = fmaf(a0, x0.z, aB);
+            bR = fmaf(a0, y0.x, bR);
+            bG = fmaf(a0, y0.y, bG);
+            bBl = fmaf(a0, y0.z, bBl);
+            aR = fmaf(a1, x1.x, aR);
+            aG = fmaf(a1, x1.y, aG);
+            aB = fmaf(a1, x1.z, aB);
+            bR = fmaf(a1, y1.x, bR);
+            bG = fmaf(a1, y1.y, bG);
+            bBl = fmaf(a1, y1.z, bBl);
+          } else {
+            // (R, G) and (B, 0) of basis 2ql, then of basis 2ql + 1
+            const uint4* D4 = reinterpret_cast<const uint4*>(sm);
+            const uint4 w0 = D4[j0 * 8 + ql], w1 = D4[j1 * 8 + ql];
+            const float2 rg0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.x));
+            const float2 bz0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.y));
+            const float2 rh0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.z));
+            const float2 bh0 = __half22float2(*reinterpret_cast<const __half2*>(&w0.w));
+            const float2 rg1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.x));
+            const float2 bz1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.y));
+            const float2 rh1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.z));
+            const float2 bh1 = __half22float2(*reinterpret_cast<const __half2*>(&w1.w));
+            aR = fmaf(a0, rg0.x, aR);
+            aG = fmaf(a0, rg0.y, aG);
+            aB = fmaf(a0, bz0.x, aB);
+            bR = fmaf(a0, rh0.x, bR);
+            bG = fmaf(a0, rh0.y, bG);
+            bBl = fmaf(a0, bh0.x, bBl);
+            aR = fmaf(a1, rg1.x, aR);
+            aG = fmaf(a1, rg1.y, aG);
+            aB = fmaf(a1, bz1.x, aB);
+            bR = fmaf(a1, rh1.x, bR);
+            bG = fmaf(a1, rh1.y, bG);
+            bBl = fmaf(a1, bh1.x, bBl);
           }
         }
-        const float aR = accA.x, aG = accA.y, aB = accC.x, bR = accB.x, bG = accB.y, bBl = accC.y;
         const float yA = Ys[gl * YS + bA], yB = Ys[gl * YS + bB];
         const float p0 = fmaf(yA, aR, yB * bR), p1 = fmaf(yA, aG, yB * bG), p2 = fmaf(yA, aB, yB * bBl);
         // transposing butterfly over the 8 lanes: afterwards lane ql holds
