@@ -59,6 +59,24 @@ def parse():
     return ap.parse_args()
 
 
+def aggregate_ranks(ms_local: float, n_local: int, world: int, device=None):
+    """Whole-job timing over replicas: the step time is the slowest rank's
+    (max over ranks) and the value counts every rank's Gaussians.  Returns
+    (ms, Gaussians/s).  With world > 1 the process group must be initialised."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local, float(n_local)], dtype=torch.float64, device=device)
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms, n = float(mx.item()), float(tot.item())
+    else:
+        ms, n = ms_local, float(n_local)
+    return ms, n / (ms * 1e-3)
+
+
 def workload(N, K, s, seed_offset=0):
     """Scene-scale inputs: hidden K-atom dictionary (rho = 0.6), s-sparse signals,
     initial dictionary from K signals, camera on a radius-4 sphere, means in [-1,1]^3."""
@@ -661,11 +679,7 @@ def main():
     torch.cuda.synchronize()
     launches = (L.dlsh_kernel_launches() - launches0) if launches0 is not None else None
     cl = clocks.stop()
-    ms = t_start.elapsed_time(t_end) / a.steps
-    if world > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, value = aggregate_ranks(t_start.elapsed_time(t_end) / a.steps, N, world, device="cuda")
     enc_ms = statistics.mean(x.elapsed_time(y) for x, y in ev["enc"])
     mod_ms = statistics.mean(x.elapsed_time(y) for x, y in ev["mod"])
     dec_ms = statistics.mean(x.elapsed_time(y) for x, y in ev["dec"])
@@ -758,7 +772,6 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = cpu_oracle_rate(X_np, init, K, s)
-    value = N * world / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "Gaussians/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
