@@ -37,7 +37,7 @@ ENCODE_TRAFFIC = {(1024, 8, "fp32"): (184.9216e6 + 37.260032e6) / 1_000_000}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=3_000_000)
@@ -117,6 +117,12 @@ class Clocks:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # let the sampler reach its steady 100 ms cadence before the timed
+            # region starts, then keep only the samples taken inside it
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.rows = []
         except OSError:
             self.proc = None
 
