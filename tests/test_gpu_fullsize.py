@@ -2,7 +2,9 @@
 bench.py times, through the same calls): encode and decode checked against the
 oracle on sampled signals, the properties that hold at any size checked on all
 of them, and the MOD update (which depends on every signal) against the
-oracle's full update from the same codes."""
+oracle's full update.  Every oracle input comes from the seeded generators or
+the oracle itself (the initial dictionary is the oracle's; the codes for decode
+and MOD are seeded random codes of the same shape), never from the GPU."""
 import numpy as np
 import pytest
 import torch
@@ -25,14 +27,15 @@ def scene(lib):
     init = synth.init_atom_indices(N, K, 0)
     cam, mu = synth.camera_and_means(N, 2, 3)
     Xt = torch.from_numpy(X).cuda()
-    D = lib.init_dictionary(Xt, init, sync=True)
+    D_np = omod.init_dictionary(X, init).astype(np.float32)
+    D = torch.from_numpy(D_np).cuda()
     idx, coef, nnz, resid = lib.encode(D, Xt, S, sync=True)
-    return {"X": X, "Xt": Xt, "D": D, "cam": cam, "mu": mu,
+    return {"X": X, "Xt": Xt, "D": D, "D_np": D_np, "cam": cam, "mu": mu,
             "idx": idx, "coef": coef, "nnz": nnz, "resid": resid}
 
 
 def test_encode_sampled_and_everywhere(lib, scene):
-    D = scene["D"].cpu().numpy().astype(np.float64)
+    D = scene["D_np"].astype(np.float64)
     idx = lib.idx_as_long(scene["idx"]).cpu().numpy()
     coef = scene["coef"].cpu().numpy().astype(np.float64)
     nnz = scene["nnz"].cpu().numpy()
@@ -52,7 +55,10 @@ def test_encode_sampled_and_everywhere(lib, scene):
     # reported residual = ||x - D_I gamma||^2 recomputed in FP64, and r is
     # orthogonal to the selected atoms (least squares), on the sample
     Xs = X[samp].astype(np.float64)
-    rec = osh.reconstruct(D, idx[samp], coef[samp], nnz[samp])
+    rec = np.zeros_like(Xs)  # D_I gamma from the kernel's own codes (a property check)
+    for t in range(S):
+        m = t < nnz[samp]
+        rec[m] += coef[samp][m, t, None] * D[idx[samp][m, t]]
     r = Xs - rec
     assert (np.abs(resid[samp] - np.sum(r * r, axis=1)) <= 1e-4 * np.sum(Xs * Xs, axis=1)).all()
     for i in range(200):
@@ -63,29 +69,44 @@ def test_encode_sampled_and_everywhere(lib, scene):
     assert abs(r_got - r_ref) <= 1e-4 * r_ref, (r_got, r_ref)
 
 
-def test_decode_sampled(lib, scene):
+@pytest.fixture(scope="module")
+def random_codes():
+    """Seeded codes of the scene's shape: distinct atoms, Laplace coefficients,
+    nnz from 1 to s (inputs of the decode and MOD checks)."""
+    rng = np.random.default_rng(21)
+    idx = synth.distinct_supports(rng, N, K, S).astype(np.uint16)
+    coef = rng.laplace(0, 1, (N, S)).astype(np.float32)
+    nnz = rng.integers(1, S + 1, N).astype(np.uint8)
+    coef[np.arange(S)[None, :] >= nnz[:, None]] = 0.0
+    idx[np.arange(S)[None, :] >= nnz[:, None]] = 0
+    return idx, coef, nnz
+
+
+def test_decode_sampled(lib, scene, random_codes):
+    idx, coef, nnz = random_codes
     MU = torch.from_numpy(scene["mu"]).cuda()
-    rgb = lib.decode(scene["D"], scene["idx"], scene["coef"], scene["nnz"], means=MU,
-                     cam=scene["cam"], sync=True).cpu().numpy()
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    rgb = lib.decode(scene["D"], c(idx.view(np.int16)), c(coef), c(nnz), means=MU, cam=scene["cam"],
+                     sync=True).cpu().numpy()
     assert np.isfinite(rgb).all()
     samp = np.random.default_rng(6).choice(N, 3000, replace=False)
-    D = scene["D"].cpu().numpy().astype(np.float64)
-    idx = lib.idx_as_long(scene["idx"]).cpu().numpy()[samp]
-    coef = scene["coef"].cpu().numpy().astype(np.float64)[samp]
-    nnz = scene["nnz"].cpu().numpy()[samp]
+    D = scene["D_np"].astype(np.float64)  # the oracle's initial dictionary, in FP32
     dirs = osh.view_directions(scene["mu"][samp].astype(np.float64), np.asarray(scene["cam"], dtype=np.float64))
-    ref = osh.decode(D, idx, coef, nnz, dirs)
+    ref = osh.decode(D, idx[samp].astype(np.int64), coef[samp].astype(np.float64), nnz[samp], dirs)
     ok, worst = close_rel(rgb[samp], ref)
     assert ok, worst
 
 
-def test_mod_full_update(lib, scene):
-    Dn = lib.mod_update(scene["Xt"], scene["D"], scene["idx"], scene["coef"], scene["nnz"],
-                        scene["resid"], sync=True).cpu().numpy()
-    idx = lib.idx_as_long(scene["idx"]).cpu().numpy()
-    ref, _ = omod.mod_update(scene["X"].astype(np.float64), scene["D"].cpu().numpy().astype(np.float64),
-                             idx, scene["coef"].cpu().numpy().astype(np.float64),
-                             scene["nnz"].cpu().numpy(), scene["resid"].cpu().numpy().astype(np.float64))
+def test_mod_full_update(lib, scene, random_codes):
+    idx, coef, nnz = random_codes
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    # every atom is used by about 13,000 signals: no atom is refilled, so no
+    # residuals are needed
+    Dn = lib.mod_update(scene["Xt"], scene["D"], c(idx.view(np.int16)), c(coef), c(nnz), None,
+                        sync=True).cpu().numpy()
+    ref, info = omod.mod_update(scene["X"].astype(np.float64), scene["D_np"].astype(np.float64),
+                                idx.astype(np.int64), coef.astype(np.float64), nnz, None)
+    assert info["dead"].size == 0
     np.testing.assert_allclose(Dn, ref, atol=3e-6, rtol=0)
 
 
