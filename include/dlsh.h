@@ -151,13 +151,16 @@ int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M,
  * direction v_i,  rgb_c = sum_{b} Y_b(v_i) * sum_{t < nnz_i} coef[i,t] * D[idx[i,t], c*15+b].
  * If cam_pos (HOST pointer to 3 floats) is NULL, dirs_or_means [N*3] holds unit
  * view directions; otherwise it holds Gaussian means mu_i and
- * v_i = (mu_i - cam) / ||mu_i - cam||.  Output rgb [N*3] FP32 (view-dependent
- * part only; the DC term is not part of the dictionary).  No workspace.
+ * v_i = (mu_i - cam) / ||mu_i - cam||.  Output rgb [N*3] FP32.  With dc NULL
+ * the output is the view-dependent part only (the DC term is not part of the
+ * dictionary); with dc [N*3] (device, the DC SH coefficient of each channel)
+ * it is the full colour max(0, Y00 dc + view-dependent part + 0.5),
+ * Y00 = 1/(2 sqrt(pi)).  No workspace.
  */
 int dlsh_decode(const float* D, int K, int d, const uint16_t* idx,
                 const float* coef, const uint8_t* nnz, int s, int64_t N,
-                const float* dirs_or_means, const float* cam_pos, float* rgb,
-                void* stream, int flags);
+                const float* dirs_or_means, const float* cam_pos, const float* dc,
+                float* rgb, void* stream, int flags);
 
 /*
  * Dictionary update with the codes fixed (the second half of the alternating
@@ -338,8 +341,8 @@ int dlsh_compact_codes(const uint16_t* idx, const float* coef, int64_t N, int s,
                        void* idx_out, int idx_bytes, uint16_t* coef_out, void* stream, int flags);
 int dlsh_decode_compact(const float* D, int K, int d, const void* idx, int idx_bytes,
                         const uint16_t* coef_f16, const uint8_t* nnz, int s, int64_t N,
-                        const float* dirs_or_means, const float* cam_pos, float* rgb,
-                        void* stream, int flags);
+                        const float* dirs_or_means, const float* cam_pos, const float* dc,
+                        float* rgb, void* stream, int flags);
 
 /*
  * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in

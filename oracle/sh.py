@@ -116,3 +116,11 @@ def decode(D, idx, coef, nnz, dirs=None, means=None, cam=None) -> np.ndarray:
     if dirs is None:
         dirs = view_directions(means, cam)
     return sh_eval(reconstruct(D, idx, coef, nnz), dirs)
+
+
+def full_colour(view, dc):
+    """A Gaussian's colour with its DC term, in the usual 3DGS convention (the
+    paper leaves the DC coefficient outside the dictionary, Sec. 2.2):
+    max(0, Y00 dc + view-dependent part + 0.5), Y00 = N_00 = 1/(2 sqrt(pi))."""
+    return np.maximum(0.0, norm_lm(0, 0) * np.asarray(dc, dtype=np.float64) + np.asarray(view, dtype=np.float64)
+                      + 0.5)

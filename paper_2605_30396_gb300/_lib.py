@@ -56,7 +56,7 @@ SIGNATURES = {
     "dlsh_encode_noalloc": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P,
                                     P, P, c_int]),
     "dlsh_correlate": (c_int, [P, c_int, c_int, P, c_int64, c_int, P, P, c_size_t, P, c_int]),
-    "dlsh_decode": (c_int, [P, c_int, c_int, P, P, P, c_int, c_int64, P, P, P, P, c_int]),
+    "dlsh_decode": (c_int, [P, c_int, c_int, P, P, P, c_int, c_int64, P, P, P, P, P, c_int]),
     "dlsh_mod_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
     "dlsh_mod_update": (c_int, [P, c_int64, c_int, c_int, P, P, P, c_int, P, P, P, P, c_size_t,
                                 P, c_int]),
@@ -91,7 +91,7 @@ SIGNATURES = {
     "dlsh_csc_from_ell": (c_int, [P, P, P, c_int64, c_int, P, P, P, P, c_size_t, P, c_int]),
     "dlsh_decode_compact_max_k": (c_size_t, [c_int]),
     "dlsh_compact_codes": (c_int, [P, P, c_int64, c_int, c_int, P, c_int, P, P, c_int]),
-    "dlsh_decode_compact": (c_int, [P, c_int, c_int, P, c_int, P, P, c_int, c_int64, P, P, P, P,
+    "dlsh_decode_compact": (c_int, [P, c_int, c_int, P, c_int, P, P, c_int, c_int64, P, P, P, P, P,
                                     c_int]),
     "dlsh_ksvd_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
     "dlsh_ksvd_update": (c_int, [P, c_int64, c_int, c_int, P, P, P, c_int, P, P, P, P, c_size_t, P, c_int]),

@@ -146,8 +146,9 @@ def correlate(D, R, precision="fp32", sync: bool = True):
     return C
 
 
-def decode(D, idx, coef, nnz, dirs=None, means=None, cam=None, sync: bool = False, out=None):
-    """View-dependent RGB (N, 3) from sparse codes; either dirs, or means + cam."""
+def decode(D, idx, coef, nnz, dirs=None, means=None, cam=None, sync: bool = False, out=None, dc=None):
+    """RGB (N, 3) from sparse codes; either dirs, or means + cam.  View-dependent
+    part only, or with dc (N, 3) the full colour max(0, Y00 dc + view + 0.5)."""
     host = not coef.is_cuda
     D = _to_device(D, torch.float32)
     idx = _to_device(idx)
@@ -161,10 +162,11 @@ def decode(D, idx, coef, nnz, dirs=None, means=None, cam=None, sync: bool = Fals
         dm = _to_device(means, torch.float32)
         c = [float(v) for v in (cam.tolist() if hasattr(cam, "tolist") else cam)]
         cam_arr = (ctypes.c_float * 3)(*c)
+    dcd = _to_device(dc, torch.float32) if dc is not None else None
     rgb = out if out is not None else torch.empty((N, 3), dtype=torch.float32, device=coef.device)
     L = _lib.lib()
     rc = L.dlsh_decode(_p(D), D.shape[0], D.shape[1], _p(idx), _p(coef), _p(nnz), s, N, _p(dm),
-                       cam_arr, _p(rgb), _stream(), FLAG_SYNC if sync else 0)
+                       cam_arr, _p(dcd), _p(rgb), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_decode")
     return rgb.cpu() if host else rgb
 
@@ -181,7 +183,8 @@ def compact_codes(idx, coef, K: int, sync: bool = False):
     return idx_c, coef_c
 
 
-def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync: bool = False, out=None):
+def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync: bool = False, out=None,
+                   dc=None):
     """decode() on compact codes (FP16 coefficients, 8/16-bit indices, FP16 dictionary in shared memory)."""
     D = _dev_f32(D)
     N, s = coef_c.shape
@@ -194,9 +197,10 @@ def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync:
         c = [float(v) for v in (cam.tolist() if hasattr(cam, "tolist") else cam)]
         cam_arr = (ctypes.c_float * 3)(*c)
     rgb = out if out is not None else torch.empty((N, 3), dtype=torch.float32, device=coef_c.device)
+    dcd = _dev_f32(dc) if dc is not None else None
     rc = _lib.lib().dlsh_decode_compact(_p(D), D.shape[0], D.shape[1], _p(idx_c.contiguous()), ib,
                                         _p(coef_c.contiguous()), _p(nnz.contiguous()), s, N, _p(dm), cam_arr,
-                                        _p(rgb), _stream(), FLAG_SYNC if sync else 0)
+                                        _p(dcd), _p(rgb), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_decode_compact")
     return rgb
 

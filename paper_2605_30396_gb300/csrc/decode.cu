@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
     const float* __restrict__ D, int K, const void* __restrict__ idxv, const void* __restrict__ coefv,
     const uint8_t* __restrict__ nnz, int s, int sp, uint32_t sdiv, int64_t N,
     const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
-    float* __restrict__ rgb, uint32_t* status) {
+    const float* __restrict__ dc, float y00, float* __restrict__ rgb, uint32_t* status) {
   extern __shared__ __align__(16) float sm[];
   constexpr int GB = batch_of(FM);
   const int nwarps = blockDim.x >> 5;
@@ -257,7 +257,12 @@ __global__ void __launch_bounds__(1024) decode_kernel(
 #pragma unroll
     for (int q = 0; q < (GB * 3 + 31) / 32; ++q) {
       const int e = lane + 32 * q;
-      if (e < nb * 3) rgb[base * 3 + e] = outs[e];
+      if (e < nb * 3) {
+        float v = outs[e];
+        // full colour: the DC term and the usual +0.5 offset, clamped at zero
+        if (dc) v = fmaxf(0.f, fmaf(y00, dc[base * 3 + e], v) + 0.5f);
+        rgb[base * 3 + e] = v;
+      }
     }
     __syncwarp();
   }
@@ -294,7 +299,7 @@ static int upload_constants(cudaStream_t st) {
 // a grid of (CTAs resident per SM) x SMs, capped by the work.
 template <int FM>
 static int launch_decode(const float* D, int K, const void* idx, const void* coef, const uint8_t* nnz,
-                         int s, int64_t N, const float* dm, const float* cam, float* rgb,
+                         int s, int64_t N, const float* dm, const float* cam, const float* dc, float* rgb,
                          uint32_t* status, int nwarps, cudaStream_t st, const char* call) {
   int sms = device_sm_count();
   if (sms <= 0) sms = 1;
@@ -312,8 +317,10 @@ static int launch_decode(const float* D, int K, const void* idx, const void* coe
   const int64_t need = (nbatch + nwarps - 1) / nwarps;
   if (grid > need) grid = need;
   const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
+  const float y00 = static_cast<float>(0.5 / sqrt(M_PI));
   decode_kernel<FM><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(D, K, idx, coef, nnz, s, sp, sdiv, N, dm,
-                                                                       cam != nullptr, cx, cy, cz, rgb, status);
+                                                                       cam != nullptr, cx, cy, cz, dc, y00, rgb,
+                                                                       status);
   count_launches(1);
   return check_launch(call);
 }
@@ -333,21 +340,22 @@ static int fit_warps(int fm, int K, int s) {
 // (about 1150 atoms) the rows are read through the read-only cache.
 int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef,
                    const uint8_t* nnz, int s, int64_t N, const float* dm, const float* cam,
-                   float* rgb, uint32_t* status, cudaStream_t st) {
+                   const float* dc, float* rgb, uint32_t* status, cudaStream_t st) {
   using namespace dec;
   int rc = upload_constants(st);
   if (rc) return rc;
   if (N == 0) return DLSH_OK;
   const int nw = fit_warps(FM_F32, K, s);
-  if (nw >= 6) return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dm, cam, rgb, status, nw, st, "dlsh_decode");
-  return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dm, cam, rgb, status, 16, st, "dlsh_decode");
+  if (nw >= 6)
+    return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, nw, st, "dlsh_decode");
+  return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, 16, st, "dlsh_decode");
 }
 
 }  // namespace dlsh
 
 extern "C" int dlsh_decode(const float* D, int K, int d, const uint16_t* idx, const float* coef,
                            const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
-                           const float* cam_pos, float* rgb, void* stream, int flags) {
+                           const float* cam_pos, const float* dc, float* rgb, void* stream, int flags) {
   using namespace dlsh;
   clear_error();
   if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_decode: d must be 45, got %d", d);
@@ -360,7 +368,7 @@ extern "C" int dlsh_decode(const float* D, int K, int d, const uint16_t* idx, co
   if (N > 0 && (!idx || !coef || !nnz || !dirs_or_means || !rgb))
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_decode: NULL array");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = decode_enqueue(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, rgb, nullptr, st);
+  int rc = decode_enqueue(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, dc, rgb, nullptr, st);
   if (rc) return rc;
   return finish(st, nullptr, flags, "dlsh_decode");
 }
@@ -397,8 +405,8 @@ extern "C" int dlsh_compact_codes(const uint16_t* idx, const float* coef, int64_
 
 extern "C" int dlsh_decode_compact(const float* D, int K, int d, const void* idx, int idx_bytes,
                                    const uint16_t* coef_f16, const uint8_t* nnz, int s, int64_t N,
-                                   const float* dirs_or_means, const float* cam_pos, float* rgb,
-                                   void* stream, int flags) {
+                                   const float* dirs_or_means, const float* cam_pos, const float* dc,
+                                   float* rgb, void* stream, int flags) {
   using namespace dlsh;
   using namespace dlsh::dec;
   clear_error();
@@ -421,9 +429,9 @@ extern "C" int dlsh_decode_compact(const float* D, int K, int d, const void* idx
   if (rc) return rc;
   if (N > 0) {
     const int nw = fit_warps(FM_C8, K, s);
-    rc = idx_bytes == 1 ? launch_decode<FM_C8>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, rgb,
+    rc = idx_bytes == 1 ? launch_decode<FM_C8>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
                                                nullptr, nw, st, "dlsh_decode_compact")
-                        : launch_decode<FM_C16>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, rgb,
+                        : launch_decode<FM_C16>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
                                                 nullptr, nw, st, "dlsh_decode_compact");
     if (rc) return rc;
   }

@@ -114,4 +114,28 @@ def test_compact_decode_rejects_bad_sizes(lib):
     assert L.lib().dlsh_compact_codes(t.data_ptr(), t.data_ptr(), 1, 8, 300, t.data_ptr(), 1, t.data_ptr(),
                                       st, 0) != 0
     assert L.lib().dlsh_decode_compact(t.data_ptr(), kmax + 1, 45, t.data_ptr(), 2, t.data_ptr(), t.data_ptr(),
-                                       8, 1, t.data_ptr(), None, t.data_ptr(), st, 0) != 0
+                                       8, 1, t.data_ptr(), None, None, t.data_ptr(), st, 0) != 0
+
+
+@pytest.mark.parametrize("compact", [False, True])
+def test_decode_full_colour_with_dc(lib, compact):
+    """With the DC coefficients the decode returns max(0, Y00 dc + view + 0.5)."""
+    N, K, s = 3001, 200, 6
+    rng = np.random.default_rng(71)
+    D = synth.hidden_dictionary(K, 72).astype(np.float32)
+    idx, coef, nnz = _codes(rng, N, K, s)
+    dirs = synth.unit_directions(N, 73)
+    dc = (2.0 * rng.standard_normal((N, 3))).astype(np.float32)  # some colours clamp at 0
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    if compact:
+        idx_c, coef_c = lib.compact_codes(c(idx.astype(np.int16)), c(coef), K, sync=True)
+        rgb = lib.decode_compact(c(D), idx_c, coef_c, c(nnz), dirs=c(dirs), dc=c(dc), sync=True).cpu().numpy()
+        view = osh.decode(_half(D), idx, _half(coef), nnz, dirs=dirs)
+    else:
+        rgb = lib.decode(c(D), c(idx.astype(np.int16)), c(coef), c(nnz), dirs=c(dirs), dc=c(dc),
+                         sync=True).cpu().numpy()
+        view = osh.decode(D, idx, coef, nnz, dirs=dirs)
+    ref = osh.full_colour(view, dc.astype(np.float64))
+    assert (ref == 0).any() and (ref > 0).any()
+    ok, worst = close_rel(rgb, ref)
+    assert ok, worst

@@ -70,9 +70,9 @@ def test_host_side_argument_errors(L):
     rc = L.dlsh_encode(fake, 16, 45, fake, 10, 4, 0.0, 7, fake, fake, fake, None, fake, 1 << 20, None, 0)
     assert rc == -1
     # decode
-    rc = L.dlsh_decode(fake, 16, 45, fake, fake, fake, 33, 10, fake, None, fake, None, 0)
+    rc = L.dlsh_decode(fake, 16, 45, fake, fake, fake, 33, 10, fake, None, None, fake, None, 0)
     assert rc == -2
-    rc = L.dlsh_decode(fake, 16, 45, None, fake, fake, 4, 10, fake, None, fake, None, 0)
+    rc = L.dlsh_decode(fake, 16, 45, None, fake, fake, 4, 10, fake, None, None, fake, None, 0)
     assert rc == -1
     # mod
     rc = L.dlsh_mod_update(fake, 10, 45, 5000, fake, fake, fake, 4, fake, None, fake, fake, 1 << 30, None, 0)

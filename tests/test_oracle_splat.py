@@ -96,3 +96,7 @@ def test_colour_of_zero_sh_and_codes_path():
                          FX, FY, W, H, NEAR, dc, y=sh.reconstruct(D, idx, coef, nnz))
     np.testing.assert_allclose(a["rgb"], b["rgb"], rtol=1e-12)
     assert splat.Y00 == sh.norm_lm(0, 0)
+    # the decode's full colour: Y00 = 1 / (2 sqrt(pi)) = 0.28209479177..., the
+    # +0.5 offset and the clamp at zero
+    np.testing.assert_allclose(sh.full_colour(np.zeros(3), [1.0, -3.0, 0.0]), [0.78209479177387814, 0.0, 0.5],
+                               rtol=1e-15)
