@@ -83,3 +83,46 @@ def test_host_side_argument_errors(L):
     # csc
     rc = L.dlsh_csc_from_ell(fake, fake, fake, 10, 0, fake, fake, fake, fake, 1 << 20, None, 0)
     assert rc == -1
+
+
+def test_host_side_errors_of_the_later_entries(L):
+    """K-SVD, the splatting preprocess and compact decode reject bad arguments on
+    the host, before any launch."""
+    from paper_2605_30396_gb300 import _lib
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    # K-SVD: d, K, aliasing D_new with D_old, misaligned indices, small workspace
+    assert L.dlsh_ksvd_workspace_size(64, 45, 4, 1000) > 0
+    assert L.dlsh_ksvd_workspace_size(64, 45, 33, 1000) == 0
+    rc = L.dlsh_ksvd_update(fake, 10, 44, 8, fake, fake, fake, 4, fake, None, P(0x2000), fake, 1 << 30, None, 0)
+    assert rc == -2
+    rc = L.dlsh_ksvd_update(fake, 10, 45, 5000, fake, fake, fake, 4, fake, None, P(0x2000), fake, 1 << 30, None, 0)
+    assert rc == -2
+    rc = L.dlsh_ksvd_update(fake, 10, 45, 8, fake, fake, fake, 4, fake, None, fake, fake, 1 << 30, None, 0)
+    assert rc == -1 and b"alias" in L.dlsh_last_error()
+    rc = L.dlsh_ksvd_update(fake, 10, 45, 8, P(0x1002), fake, fake, 4, fake, None, P(0x2000), fake, 1 << 30,
+                            None, 0)
+    assert rc == -1
+    rc = L.dlsh_ksvd_update(fake, 10, 45, 8, fake, fake, fake, 4, fake, None, P(0x2000), fake, 16, None, 0)
+    assert rc == -5
+    # preprocess: missing structs, bad camera, misaligned rotations, dictionary too large
+    assert L.dlsh_preprocess_max_k(0, 0) == 0 and L.dlsh_preprocess_max_k(33, 1) == 0
+    assert 600 < L.dlsh_preprocess_max_k(8, 0) < L.dlsh_preprocess_max_k(8, 1) < 2000
+    cam = _lib.Camera((ctypes.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1), (ctypes.c_float * 3)(0, 0, 0),
+                      100.0, 100.0, 64, 48, 0.1)
+    g = _lib.Gaussians(0x1000, 0x1000, 0x1000, 0x1000, 10)
+    o = _lib.SplatOut(0x1000, 0x1000, 0x1000, 0x1000, 0x1000)
+    br = ctypes.byref
+    assert L.dlsh_preprocess_sh(None, br(g), fake, br(o), None, 0) == -1
+    assert L.dlsh_preprocess_sh(br(cam), br(g), None, br(o), None, 0) == -1
+    bad_cam = _lib.Camera(cam.R, cam.t, 0.0, 100.0, 64, 48, 0.1)
+    assert L.dlsh_preprocess_sh(br(bad_cam), br(g), fake, br(o), None, 0) == -1
+    g_mis = _lib.Gaussians(0x1000, 0x1000, 0x1004, 0x1000, 10)
+    assert L.dlsh_preprocess_sh(br(cam), br(g_mis), fake, br(o), None, 0) == -1
+    big = int(L.dlsh_preprocess_max_k(8, 1)) + 1
+    assert L.dlsh_preprocess_compact(br(cam), br(g), fake, big, fake, 2, fake, fake, 8, br(o), None, 0) == -2
+    assert L.dlsh_preprocess_compact(br(cam), br(g), fake, 300, fake, 1, fake, fake, 8, br(o), None, 0) == -2
+    assert L.dlsh_preprocess_codes(br(cam), br(g), fake, 16, fake, fake, fake, 40, br(o), None, 0) == -2
+    # compact decode: 8-bit indices need K <= 256
+    rc = L.dlsh_decode_compact(fake, 300, 45, fake, 1, fake, fake, 8, 10, fake, None, None, fake, None, 0)
+    assert rc == -2
