@@ -25,6 +25,11 @@
 //      in FP64 (GB300's FP64 rate is a small fraction of its FP32 rate, so
 //      FP64 is spent only there)
 //   6. normalise, then refill unused atoms (argmax passes over resid_sq)
+//
+// The same file holds the other reading of the D-step, the approximate K-SVD
+// sweep (dlsh_ksvd_update): it reuses the counting sort (1-3, with each
+// record's code slot), then runs the atoms in order on one cooperative kernel,
+// and refills unused atoms as in 6.
 #include <math.h>
 
 #include "common.cuh"
