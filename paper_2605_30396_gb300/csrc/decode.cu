@@ -8,17 +8,19 @@
 // A warp takes batches of 8 (FP32 table) or 16 Gaussians: the batch's codes are loaded
 // (coalesced) into shared memory as (index, coefficient) pairs while one lane
 // per Gaussian computes its direction and 15 basis values; then eight lanes take
-// one Gaussian (four Gaussians per warp step), lane q owning bases 2q and 2q+1
-// of all three channels, so that the eight lanes read one contiguous span of the
-// atom per instruction:
-//  - FP32 table: three channel planes of 16 floats per atom (192 bytes), read
-//    as three 8-byte words per lane;
+// one Gaussian (four Gaussians per warp step) and read contiguous spans of the
+// atom:
+//  - FP32 table: three channel planes of 16 floats per atom (192 bytes); lane
+//    q reads 16 bytes of the R and G planes (lanes 0-3: R of bases 4q..4q+3,
+//    lanes 4-7: G), one 128-byte span per Gaussian, and 8 bytes of the B plane
+//    (bases 2q, 2q+1); the channel sums are reduced in five shuffles;
 //  - FP16 table (compact storage): 16 slots of (R, G, B, 0) halves per atom
-//    (128 bytes), read as one 16-byte word per lane.
-// The lane's three channel sums are multiplied by Y_b and reduced over the
-// eight lanes in four shuffles (a transposing butterfly); results are staged
-// and written back coalesced.  For dictionaries too large for shared memory
-// the FP32 rows are read through the read-only cache instead.
+//    (128 bytes), lane q reading bases 2q and 2q+1 of all three channels in
+//    one 16-byte word; its three channel sums are reduced over the eight lanes
+//    in four shuffles (a transposing butterfly).
+// Results are staged and written back coalesced.  For dictionaries too large
+// for shared memory the FP32 rows are read through the read-only cache, with
+// the FP16 path's lane mapping.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -192,6 +194,49 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       const int nzl = act ? nzs[gs] : 0;
       int nzp = max(nzl, __shfl_xor_sync(FULL, nzl, 8));
       nzp = max(nzp, __shfl_xor_sync(FULL, nzp, 16));
+      if (FM == FM_F32) {
+        // FP32 planes: lane ql reads 16 bytes of the R and G planes (lanes
+        // 0-3: R of bases 4ql..4ql+3; lanes 4-7: G of bases 4(ql-4)..), so the
+        // eight lanes of a Gaussian read one contiguous 128-byte span, and
+        // 8 bytes of the B plane (bases 2ql, 2ql+1)
+        float4 acc4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 accb = make_float2(0.f, 0.f);
+#pragma unroll 2
+        for (int t = 0; t < nzp; t += 2) {
+          const uint4 c2 = *reinterpret_cast<const uint4*>(cpk + gs * sp + t);
+          const uint32_t jt[2] = {c2.x, c2.z};
+          const float at[2] = {__uint_as_float(c2.y), __uint_as_float(c2.w)};
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const float a = at[u];
+            const float* row = sm + jt[u] * 48;
+            const float4 w = *reinterpret_cast<const float4*>(row + 4 * ql);
+            const float2 bb = *reinterpret_cast<const float2*>(row + 32 + 2 * ql);
+            acc4.x = fmaf(a, w.x, acc4.x);
+            acc4.y = fmaf(a, w.y, acc4.y);
+            acc4.z = fmaf(a, w.z, acc4.z);
+            acc4.w = fmaf(a, w.w, acc4.w);
+            accb.x = fmaf(a, bb.x, accb.x);
+            accb.y = fmaf(a, bb.y, accb.y);
+          }
+        }
+        const float4 y4 = *reinterpret_cast<const float4*>(Ys + gs * YS + 4 * (ql & 3));
+        const float2 yb = *reinterpret_cast<const float2*>(Ys + gs * YS + 2 * ql);
+        float prg = fmaf(y4.x, acc4.x, fmaf(y4.y, acc4.y, fmaf(y4.z, acc4.z, y4.w * acc4.w)));
+        float pb = fmaf(yb.x, accb.x, yb.y * accb.y);
+        // R over lanes 0-3, G over lanes 4-7, B over all eight
+        prg += __shfl_xor_sync(FULL, prg, 1);
+        prg += __shfl_xor_sync(FULL, prg, 2);
+        pb += __shfl_xor_sync(FULL, pb, 1);
+        pb += __shfl_xor_sync(FULL, pb, 2);
+        pb += __shfl_xor_sync(FULL, pb, 4);
+        if (act && ql == 0) {
+          outs[gl * 3 + 0] = prg;
+          outs[gl * 3 + 2] = pb;
+        }
+        if (act && ql == 4) outs[gl * 3 + 1] = prg;
+        continue;
+      }
       float aR = 0.f, aG = 0.f, aB = 0.f, bR = 0.f, bG = 0.f, bBl = 0.f;
 #pragma unroll 2
       for (int t = 0; t < nzp; t += 2) {
@@ -201,18 +246,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const float a = at[u];
-          if (FM == FM_F32) {
-            const float* row = sm + jt[u] * 48 + 2 * ql;
-            const float2 r = *reinterpret_cast<const float2*>(row);
-            const float2 gg = *reinterpret_cast<const float2*>(row + 16);
-            const float2 bb = *reinterpret_cast<const float2*>(row + 32);
-            aR = fmaf(a, r.x, aR);
-            bR = fmaf(a, r.y, bR);
-            aG = fmaf(a, gg.x, aG);
-            bG = fmaf(a, gg.y, bG);
-            aB = fmaf(a, bb.x, aB);
-            bBl = fmaf(a, bb.y, bBl);
-          } else if (FM == FM_GLOBAL) {
+          if (FM == FM_GLOBAL) {
             // bases 2ql and 2ql + 1 of the atom's row (basis 15 does not exist)
             const float* row = D + static_cast<size_t>(jt[u]) * DLSH_D + 2 * ql;
             aR = fmaf(a, __ldg(row), aR);
