@@ -221,27 +221,32 @@ def preprocess(cam, means, scales, quats, dc, sh=None, D=None, idx=None, coef=No
     `coef` selects the ELL path, FP16 `coef` the compact path (uint8 or int16
     `idx`).  Returns a dict of xy (N, 2), depth (N,), conic (N, 3), radius (N,)
     int32 and rgb (N, 3); `out` may supply that dict preallocated."""
-    N = means.shape[0]
-    dev = means.device
+    # the kernels read and write device memory only: host inputs are copied over
+    keep = [_to_device(t, torch.float32) for t in (means, scales, quats, dc)]
+    N = keep[0].shape[0]
+    dev = keep[0].device
     if out is None:
         out = {"xy": torch.empty((N, 2), dtype=torch.float32, device=dev),
                "depth": torch.empty((N,), dtype=torch.float32, device=dev),
                "conic": torch.empty((N, 3), dtype=torch.float32, device=dev),
                "radius": torch.empty((N,), dtype=torch.int32, device=dev),
                "rgb": torch.empty((N, 3), dtype=torch.float32, device=dev)}
-    keep = [t.contiguous() for t in (means, scales, quats, dc)]
+    for k in ("xy", "depth", "conic", "radius", "rgb"):
+        if not (out[k].is_cuda and out[k].is_contiguous()):
+            raise ValueError(f"preprocess: out[{k!r}] must be a contiguous CUDA tensor")
     g = _lib.Gaussians(*(t.data_ptr() for t in keep), N)
     o = _lib.SplatOut(*(out[k].data_ptr() for k in ("xy", "depth", "conic", "radius", "rgb")))
     flags = FLAG_SYNC if sync else 0
     L = _lib.lib()
     if sh is not None:
-        sh = sh.contiguous()
+        sh = _to_device(sh, torch.float32)
         rc = L.dlsh_preprocess_sh(ctypes.byref(cam), ctypes.byref(g), _p(sh), ctypes.byref(o), _stream(), flags)
         _check(rc, "dlsh_preprocess_sh")
         return out
     D = _dev_f32(D)
     s = coef.shape[1]
-    idx, coef, nnz = idx.contiguous(), coef.contiguous(), nnz.contiguous()
+    idx, nnz = _to_device(idx), _to_device(nnz)
+    coef = _to_device(coef, None if coef.dtype == torch.float16 else torch.float32)
     if coef.dtype == torch.float16:
         ib = 1 if idx.dtype == torch.uint8 else 2
         rc = L.dlsh_preprocess_compact(ctypes.byref(cam), ctypes.byref(g), _p(D), D.shape[0], _p(idx), ib, _p(coef),
@@ -289,7 +294,8 @@ def ksvd_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     if need == 0:
         raise DlshError(-2, "dlsh_ksvd_workspace_size")
     ws = workspace(need, key="ksvd")
-    rc = L.dlsh_ksvd_update(_p(X), N, D_SH, K, _p(idx.contiguous()), _p(coef), _p(nnz.contiguous()), s,
+    idx, nnz = _to_device(idx), _to_device(nnz)
+    rc = L.dlsh_ksvd_update(_p(X), N, D_SH, K, _p(idx), _p(coef), _p(nnz), s,
                             _p(D_old), _p(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
                             _p(ws), ws.numel(), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_ksvd_update")
