@@ -38,6 +38,16 @@ def _p(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+def _pd(t):
+    """Pointer of a tensor the kernels read or write: it must live on the GPU
+    (a host pointer reaching a kernel would fault it)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"expected a CUDA tensor, got one on {t.device}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -177,7 +187,7 @@ def compact_codes(idx, coef, K: int, sync: bool = False):
     ib = 1 if K <= 256 else 2
     idx_c = torch.empty((N, s), dtype=torch.uint8 if ib == 1 else torch.int16, device=coef.device)
     coef_c = torch.empty((N, s), dtype=torch.float16, device=coef.device)
-    rc = _lib.lib().dlsh_compact_codes(_p(idx.contiguous()), _p(coef.contiguous()), N, s, K, _p(idx_c), ib,
+    rc = _lib.lib().dlsh_compact_codes(_pd(idx.contiguous()), _pd(coef.contiguous()), N, s, K, _p(idx_c), ib,
                                        _p(coef_c), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_compact_codes")
     return idx_c, coef_c
@@ -198,8 +208,8 @@ def decode_compact(D, idx_c, coef_c, nnz, dirs=None, means=None, cam=None, sync:
         cam_arr = (ctypes.c_float * 3)(*c)
     rgb = out if out is not None else torch.empty((N, 3), dtype=torch.float32, device=coef_c.device)
     dcd = _dev_f32(dc) if dc is not None else None
-    rc = _lib.lib().dlsh_decode_compact(_p(D), D.shape[0], D.shape[1], _p(idx_c.contiguous()), ib,
-                                        _p(coef_c.contiguous()), _p(nnz.contiguous()), s, N, _p(dm), cam_arr,
+    rc = _lib.lib().dlsh_decode_compact(_p(D), D.shape[0], D.shape[1], _pd(idx_c.contiguous()), ib,
+                                        _pd(coef_c.contiguous()), _pd(nnz.contiguous()), s, N, _p(dm), cam_arr,
                                         _p(dcd), _p(rgb), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_decode_compact")
     return rgb
@@ -271,9 +281,9 @@ def mod_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     if need == 0:
         raise DlshError(-2, "dlsh_mod_workspace_size")
     ws = workspace(need, key="mod")
-    rc = L.dlsh_mod_update(_p(X), N, D_SH, K, _p(idx.contiguous()), _p(coef.contiguous()),
-                           _p(nnz.contiguous()), s, _p(D_old),
-                           _p(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
+    rc = L.dlsh_mod_update(_p(X), N, D_SH, K, _pd(idx.contiguous()), _pd(coef.contiguous()),
+                           _pd(nnz.contiguous()), s, _p(D_old),
+                           _pd(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
                            _p(ws), ws.numel(), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_mod_update")
     return D_new
@@ -296,7 +306,7 @@ def ksvd_update(X, D_old, idx, coef, nnz, resid_sq=None, sync: bool = False):
     ws = workspace(need, key="ksvd")
     idx, nnz = _to_device(idx), _to_device(nnz)
     rc = L.dlsh_ksvd_update(_p(X), N, D_SH, K, _p(idx), _p(coef), _p(nnz), s,
-                            _p(D_old), _p(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
+                            _p(D_old), _pd(resid_sq.contiguous()) if resid_sq is not None else None, _p(D_new),
                             _p(ws), ws.numel(), _stream(), FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_ksvd_update")
     return D_new
@@ -347,7 +357,7 @@ def csc_from_ell(idx, coef, nnz, sync: bool = False):
     L = _lib.lib()
     need = L.dlsh_csc_workspace_size(N)
     ws = workspace(need, key="csc")
-    rc = L.dlsh_csc_from_ell(_p(idx.contiguous()), _p(coef.contiguous()), _p(nnz.contiguous()), N,
+    rc = L.dlsh_csc_from_ell(_pd(idx.contiguous()), _pd(coef.contiguous()), _pd(nnz.contiguous()), N,
                              s, _p(col_ptr), _p(row_idx), _p(val), _p(ws), ws.numel(), _stream(),
                              FLAG_SYNC if sync else 0)
     _check(rc, "dlsh_csc_from_ell")
@@ -425,8 +435,8 @@ class MLP:
         g = torch.empty(mlp_num_params(self.K), dtype=torch.float32, device="cuda")
         loss = torch.empty((1,), dtype=torch.float32, device="cuda")
         ws = self._ws(B)
-        _check(_lib.lib().dlsh_mlp_gradients(_p(self.blob), self.K, _p(X), B, _p(idx.contiguous()),
-                                             _p(nnz.contiguous()), s, _p(g), _p(loss), _p(ws),
+        _check(_lib.lib().dlsh_mlp_gradients(_p(self.blob), self.K, _p(X), B, _pd(idx.contiguous()),
+                                             _pd(nnz.contiguous()), s, _p(g), _p(loss), _p(ws),
                                              ws.numel(), _stream(), FLAG_SYNC), "dlsh_mlp_gradients")
         return g, float(loss.item())
 
@@ -436,8 +446,8 @@ class MLP:
         self.step += 1
         loss = torch.empty((1,), dtype=torch.float32, device="cuda")
         ws = self._ws(B)
-        _check(_lib.lib().dlsh_mlp_train_step(_p(self.blob), self.K, _p(X), B, _p(idx.contiguous()),
-                                              _p(nnz.contiguous()), s, float(lr), self.step,
+        _check(_lib.lib().dlsh_mlp_train_step(_p(self.blob), self.K, _p(X), B, _pd(idx.contiguous()),
+                                              _pd(nnz.contiguous()), s, float(lr), self.step,
                                               _p(loss), _p(ws), ws.numel(), _stream(), FLAG_SYNC),
                "dlsh_mlp_train_step")
         return float(loss.item())
@@ -448,8 +458,8 @@ class MLP:
         steps = (N // batch) * epochs
         losses = torch.empty((max(steps, 1),), dtype=torch.float32, device="cuda")
         ws = self._ws(batch)
-        _check(_lib.lib().dlsh_mlp_train(_p(self.blob), self.K, _p(X), N, _p(idx.contiguous()),
-                                         _p(nnz.contiguous()), s, epochs, batch, float(lr),
+        _check(_lib.lib().dlsh_mlp_train(_p(self.blob), self.K, _p(X), N, _pd(idx.contiguous()),
+                                         _pd(nnz.contiguous()), s, epochs, batch, float(lr),
                                          _p(losses), _p(ws), ws.numel(), _stream(),
                                          FLAG_SYNC if sync else 0), "dlsh_mlp_train")
         self.step += steps
@@ -476,7 +486,7 @@ def encode_restricted(D, X, cand, s: int, eps: float = 0.0, sync: bool = True):
     resid = torch.empty((N,), dtype=torch.float32, device="cuda")
     L = _lib.lib()
     ws = workspace(L.dlsh_encode_workspace_size(K, D_SH, s, 0), key="encode")
-    _check(L.dlsh_encode_restricted(_p(D), K, D_SH, _p(X), N, _p(cand.contiguous()), m, s,
+    _check(L.dlsh_encode_restricted(_p(D), K, D_SH, _p(X), N, _pd(cand.contiguous()), m, s,
                                     float(eps), _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws),
                                     ws.numel(), _stream(), FLAG_SYNC if sync else 0),
            "dlsh_encode_restricted")
@@ -515,8 +525,8 @@ def encode_learned(D, X, s: int, mlp: "MLP", mode: str = "deploy", tau: float = 
 
 def calibrate_fallback(resid_learned, resid_plain, max_ratio: float = 1.01) -> float:
     tau = ctypes.c_float(0.0)
-    _check(_lib.lib().dlsh_calibrate_fallback(_p(resid_learned.contiguous()),
-                                              _p(resid_plain.contiguous()), resid_learned.numel(),
+    _check(_lib.lib().dlsh_calibrate_fallback(_pd(resid_learned.contiguous()),
+                                              _pd(resid_plain.contiguous()), resid_learned.numel(),
                                               float(max_ratio), ctypes.byref(tau), _stream()),
            "dlsh_calibrate_fallback")
     return float(tau.value)
