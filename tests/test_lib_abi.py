@@ -126,3 +126,13 @@ def test_host_side_errors_of_the_later_entries(L):
     # compact decode: 8-bit indices need K <= 256
     rc = L.dlsh_decode_compact(fake, 300, 45, fake, 1, fake, fake, 8, 10, fake, None, None, fake, None, 0)
     assert rc == -2
+
+
+def test_binding_refuses_host_tensors_for_device_arguments():
+    import torch
+
+    from paper_2605_30396_gb300 import api
+    import pytest
+    with pytest.raises(ValueError):
+        api._pd(torch.zeros(4))
+    assert api._pd(None) is None
