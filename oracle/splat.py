@@ -30,8 +30,11 @@ Invisible Gaussians get radius 0 and zeros elsewhere.
 Pins (tests/test_oracle_splat.py): the Jacobian against central differences of
 the projection, an isotropic Gaussian on the optical axis in closed form,
 rotation invariance of isotropic Gaussians, a 90-degree quaternion that swaps
-two axes, the clamp far off-axis, culling behind the camera and off-screen, and
-the colour of zero SH.
+two axes, the quaternion rotation against scipy's, invariance of the geometry
+under a joint rotation of scene and camera, the conic as the inverse of the
+screen covariance, the clamp far off-axis in x and y, culling behind the
+camera and off-screen, the colour of zero SH, and the colour along the
+direction from a camera built at a known position.
 """
 from __future__ import annotations
 
