@@ -109,3 +109,17 @@ def test_legendre_recurrence_closed_form(l):
     }
     for m in range(l + 1):
         np.testing.assert_allclose(sh.assoc_legendre(l, m, z), table[(l, m)], atol=1e-13)
+
+
+def test_channel_major_layout():
+    """Coefficient c*15 + b belongs to channel c and basis b: a single unit
+    coefficient at (c, b = 1, the l = 1, m = 0 basis sqrt(3/(4 pi)) z) lights
+    channel c only."""
+    v = np.array([[0.36, -0.48, 0.8]])
+    for c in range(3):
+        y = np.zeros((1, 45))
+        y[0, c * 15 + 1] = 1.0
+        rgb = sh.sh_eval(y, v)[0]
+        want = np.zeros(3)
+        want[c] = math.sqrt(3.0 / (4.0 * math.pi)) * 0.8
+        np.testing.assert_allclose(rgb, want, atol=1e-15)
