@@ -136,3 +136,12 @@ def test_restricted_equals_plain_when_candidates_are_all_atoms():
     b = O.omp_restricted(D, X, cand, 5)
     np.testing.assert_array_equal(a["idx"], b["idx"])
     np.testing.assert_allclose(a["coef"], b["coef"], atol=1e-12)
+
+
+def test_tolerance_boundary_is_inclusive():
+    """The stop test is ||r||_2 <= eps: a residual exactly at eps stops."""
+    D = np.eye(4)
+    X = np.array([[3.0, 4.0, 0.0, 0.0]])  # ||x|| = 5 exactly
+    assert O.omp(D, X, 2, eps=5.0)["nnz"][0] == 0
+    out = O.omp(D, X, 2, eps=4.0)  # after atom 1 (coefficient 4), ||r|| = 3 <= 4
+    assert out["nnz"][0] == 1 and out["idx"][0, 0] == 1
