@@ -102,3 +102,9 @@ def test_learn_loop_reduces_rmse_and_recovers_atoms():
     assert len(hist) == 9
     cos = np.abs(D @ Dh.T).max(axis=1)
     assert np.mean(cos > 0.99) > 0.5
+
+
+def test_ridge_lambda_reading():
+    """lambda = 1e-6 trace(G) / K (the mean diagonal), 1e-6 when G is zero."""
+    assert M.ridge_lambda(2.0 * np.eye(7)) == 2e-6
+    assert M.ridge_lambda(np.zeros((5, 5))) == 1e-6
