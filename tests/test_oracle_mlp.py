@@ -75,3 +75,32 @@ def test_encode_learned_never_worse_than_plain():
     from oracle.omp import omp
     pl = omp(D, X, 3)
     assert (np.sqrt(out["resid_sq"]) <= np.sqrt(pl["resid_sq"]) * (1 + 1e-6) + 1e-15).all()
+
+
+def test_input_is_normalised():
+    """The network sees x / ||x||: scaling a signal leaves the logits unchanged,
+    and a zero signal gives the biases' forward pass."""
+    K = 32
+    p = synth.mlp_params(K, 3)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((5, 45))
+    np.testing.assert_allclose(P.forward(p, 3.7 * X)["z3"], P.forward(p, X)["z3"], rtol=1e-12)
+    z0 = P.forward(p, np.zeros((1, 45)))
+    np.testing.assert_allclose(z0["z1"], p["b1"][None, :], atol=0)
+
+
+def test_adam_epsilon_outside_the_root():
+    """eps is added to sqrt(v_hat): with g = 1e-9 the first step is
+    lr * 1e-9 / (1e-9 + 1e-8) = lr / 11."""
+    p = {"w": np.zeros(1)}
+    g = {"w": np.array([1e-9])}
+    z = {"w": np.zeros(1)}
+    p2, _, _ = P.adam_step(p, g, z, z, 1, lr=1.0)
+    np.testing.assert_allclose(p2["w"], [-1.0 / 11.0], rtol=1e-12)
+
+
+def test_support_targets_ignore_padding_slots():
+    Y = P.support_targets(np.array([[3, 5], [1, 2]]), np.array([1, 0]), 8)
+    want = np.zeros((2, 8))
+    want[0, 3] = 1.0
+    np.testing.assert_array_equal(Y, want)
