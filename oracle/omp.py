@@ -32,7 +32,11 @@ Pins (tests/test_oracle_omp.py): exact support recovery under Tropp's exact
 recovery condition; orthonormal D gives hard thresholding; s = 1 is the best
 1-subset; for d <= 8 the OMP residual never beats brute force; residual
 orthogonality to the selected atoms; gamma equals numpy.linalg.lstsq on D_I;
-the residual norm never increases.
+the residual norm never increases.  omp_restricted: over a shuffled strict
+candidate subset it equals omp on the sub-dictionary with positions mapped back
+to atom ids; it recovers planted atom ids under the exact recovery condition;
+equal correlations go to the smallest atom id wherever it sits in the candidate
+list; it never beats the best s-subset of the candidates (d <= 8).
 """
 from __future__ import annotations
 

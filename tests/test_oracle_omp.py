@@ -145,3 +145,82 @@ def test_tolerance_boundary_is_inclusive():
     assert O.omp(D, X, 2, eps=5.0)["nnz"][0] == 0
     out = O.omp(D, X, 2, eps=4.0)  # after atom 1 (coefficient 4), ||r|| = 3 <= 4
     assert out["nnz"][0] == 1 and out["idx"][0, 0] == 1
+
+
+def _shuffled_subsets(rng, K, m, must):
+    """Per row: m distinct atoms in random order, containing the atoms of must[i]."""
+    out = np.empty((len(must), m), dtype=np.int64)
+    for i, sup in enumerate(must):
+        rest = np.setdiff1d(np.arange(K), sup)
+        extra = rng.choice(rest, m - len(sup), replace=False)
+        out[i] = rng.permutation(np.concatenate([sup, extra]))
+    return out
+
+
+def test_restricted_equals_plain_omp_on_the_candidate_subdictionary():
+    """Restricted OMP over a shuffled strict subset is plain OMP on the
+    sub-dictionary D[cand_i], its positions mapped back to atom ids through
+    cand_i (generic real-valued atoms, so no ties arise)."""
+    rng = np.random.default_rng(31)
+    K, m, s = 40, 12, 5
+    D = synth.hidden_dictionary(K, 9)
+    X = synth.signals(60, D, 4, 10, dtype=np.float64)
+    cand = np.stack([rng.choice(K, m, replace=False) for _ in range(60)])
+    got = O.omp_restricted(D, X, cand, s)
+    for i in range(60):
+        ref = O.omp(D[cand[i]], X[i:i + 1], s)
+        n = int(ref["nnz"][0])
+        assert got["nnz"][i] == n
+        np.testing.assert_array_equal(got["idx"][i, :n], cand[i][ref["idx"][0, :n]])
+        np.testing.assert_allclose(got["coef"][i, :n], ref["coef"][0, :n], atol=1e-12)
+        np.testing.assert_allclose(got["resid_sq"][i], ref["resid_sq"][0], rtol=1e-10, atol=1e-14)
+
+
+def test_restricted_recovers_planted_atom_ids_from_shuffled_candidates():
+    """Under the exact recovery condition, OMP over any candidate set that holds
+    the planted support returns the planted atom ids (not candidate positions)."""
+    D = synth.erc_dictionary(64)  # 128 atoms, mu = 1/8
+    rng = np.random.default_rng(12)
+    x, sup, coef = synth.planted_sparse(rng, D, 200, 4)
+    cand = _shuffled_subsets(rng, D.shape[0], 16, sup)
+    out = O.omp_restricted(D, x, cand, 4)
+    assert (out["nnz"] == 4).all()
+    np.testing.assert_array_equal(np.sort(out["idx"], 1), np.sort(sup, 1))
+    assert out["resid_sq"].max() < 1e-24
+    for i in range(200):
+        got = dict(zip(out["idx"][i], out["coef"][i]))
+        for j, c in zip(sup[i], coef[i]):
+            assert abs(got[j] - c) < 1e-12
+
+
+def test_restricted_tie_goes_to_smallest_atom_id_not_first_position():
+    """Candidates listed in decreasing atom order: equal correlations must pick
+    the smallest atom id, which sits at the largest candidate position."""
+    D = np.eye(6)
+    X = np.array([[0.0, 1.0, 0.0, 1.0, 0.0, 1.0]])  # atoms 1, 3, 5 tie
+    cand = np.array([[5, 4, 3, 2, 1, 0]])
+    out = O.omp_restricted(D, X, cand, 3)
+    np.testing.assert_array_equal(out["idx"][0], [1, 3, 5])
+    # the same tie over a candidate list in a shuffled order
+    out = O.omp_restricted(D, X, np.array([[3, 0, 5, 2, 1, 4]]), 2)
+    np.testing.assert_array_equal(out["idx"][0], [1, 3])
+
+
+@pytest.mark.parametrize("d,K,m,s", [(6, 10, 6, 2), (8, 12, 7, 3)])
+def test_restricted_never_beats_brute_force_over_the_candidates(d, K, m, s):
+    """Greedy over the candidates never beats the best s-subset of the
+    candidates; for s = 1 both are the single best candidate atom."""
+    rng = np.random.default_rng(40 + d)
+    D = rng.standard_normal((K, d))
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    X = rng.standard_normal((25, d))
+    cand = np.stack([rng.choice(K, m, replace=False) for _ in range(25)])
+    out = O.omp_restricted(D, X, cand, s)
+    one = O.omp_restricted(D, X, cand, 1)
+    for i in range(25):
+        sub = D[cand[i]]
+        sup, _, rbest = brute.best_subset(sub, X[i], s)
+        assert np.sqrt(out["resid_sq"][i]) >= rbest - 1e-12
+        sup1, _, r1 = brute.best_subset(sub, X[i], 1)
+        assert one["idx"][i, 0] == cand[i][sup1[0]]
+        assert abs(np.sqrt(one["resid_sq"][i]) - r1) < 1e-12
