@@ -315,17 +315,19 @@ __global__ void compact_codes_kernel(const uint16_t* __restrict__ idx, const flo
   coef_out[e] = __float2half_rn(coef[e]);
 }
 
+// The SH constants go to each device once (the first decode on a device should
+// therefore not be inside a stream capture).
 static int upload_constants(cudaStream_t st) {
-  static thread_local int uploaded_dev = -1;
-  int dev = 0;
-  DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_decode: cudaGetDevice");
-  if (uploaded_dev == dev) return DLSH_OK;
-  const ShConst k = make_sh_constants();
-  DLSH_CUDA_TRY(cudaMemcpyToSymbolAsync(g_sh, &k, sizeof(k), 0, cudaMemcpyHostToDevice, st),
-                "dlsh_decode: constants");
-  DLSH_CUDA_TRY(cudaStreamSynchronize(st), "dlsh_decode: constants");
-  uploaded_dev = dev;
-  return DLSH_OK;
+  static PerDevice<int> uploaded;
+  int ok = 0;
+  return uploaded.get(&ok, [&](int& v) {
+    const ShConst k = make_sh_constants();
+    DLSH_CUDA_TRY(cudaMemcpyToSymbolAsync(g_sh, &k, sizeof(k), 0, cudaMemcpyHostToDevice, st),
+                  "dlsh_decode: constants");
+    DLSH_CUDA_TRY(cudaStreamSynchronize(st), "dlsh_decode: constants");
+    v = 1;
+    return DLSH_OK;
+  });
 }
 
 // One decode launch with the dictionary format FM: shared-memory sizes from

@@ -7,6 +7,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/dlsh.h"
 
 namespace dlsh {
@@ -57,6 +59,37 @@ int finish(cudaStream_t st, const uint32_t* status_dev, int flags, const char* c
 constexpr long long kWaitBudget = 4000000000LL;
 
 int device_sm_count();
+
+// A value set up once per device, with that device current, and cached for the
+// life of the process (function attributes, cooperative grid sizes).  Safe to
+// call from several host threads; a failed set-up caches nothing.
+template <class T>
+class PerDevice {
+ public:
+  template <class F>
+  int get(T* out, F&& init) {
+    int dev = 0;
+    DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh: cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDev)
+      return set_error(DLSH_ERR_UNSUPPORTED, "dlsh: device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(mu_);
+    if (!done_[dev]) {
+      T v{};
+      const int rc = init(v);
+      if (rc) return rc;
+      val_[dev] = v;
+      done_[dev] = true;
+    }
+    *out = val_[dev];
+    return DLSH_OK;
+  }
+
+ private:
+  static constexpr int kMaxDev = 64;
+  std::mutex mu_;
+  bool done_[kMaxDev] = {};
+  T val_[kMaxDev] = {};
+};
 
 // Adds n to the process-wide count of kernels this library has enqueued.
 void count_launches(int n);

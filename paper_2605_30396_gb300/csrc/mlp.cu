@@ -376,13 +376,16 @@ constexpr int SPLIT_K = 1024;  // batch rows per split of the weight-gradient GE
 static int gemm(const Mat& A, const Mat& B, int M, int N, int Kd, float* C, long long ldc, int epi,
                 const float* bias, __nv_bfloat16* H, long long ldh, int splits, long long zstride,
                 uint32_t* status, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
+  static PerDevice<int> attr;
+  int attr_ok = 0;
+  const int arc = attr.get(&attr_ok, [](int& v) {
     DLSH_CUDA_TRY(cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        NS * (A_STAGE + B_STAGE) + 64),
                   "dlsh_mlp: attribute");
-    attr_set = true;
-  }
+    v = 1;
+    return DLSH_OK;
+  });
+  if (arc) return arc;
   GemmArgs g;
   g.A = A;
   g.B = B;

@@ -1447,16 +1447,19 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, D_old, w.lam, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
   ++launches;
   {
-    static int coop_grid = 0;
-    if (coop_grid == 0) {
+    static PerDevice<int> coop;
+    int coop_grid = 0;
+    const int crc = coop.get(&coop_grid, [](int& g) {
       int per_sm = 0;
       DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_inv_kernel, CH_T, 0),
                     "dlsh_mod_update: occupancy");
       int sms = device_sm_count();
       if (sms <= 0) sms = 1;
       if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_mod_update: factorisation kernel does not fit");
-      coop_grid = sms;  // one CTA per SM: fewer arrivals at each grid barrier
-    }
+      g = sms;  // one CTA per SM: fewer arrivals at each grid barrier
+      return DLSH_OK;
+    });
+    if (crc) return crc;
     DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_mod_update: barrier");
     float* A32 = w.A32;
     float* W32 = w.W32;
@@ -1530,8 +1533,9 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
     launches += 2;
   }
   {
-    static int coop_grid = 0;
-    if (coop_grid == 0) {
+    static PerDevice<int> coop;
+    int coop_grid = 0;
+    const int crc = coop.get(&coop_grid, [](int& grid) {
       int per_sm = 0;
       int sms = device_sm_count();
       if (sms <= 0) sms = 1;
@@ -1543,8 +1547,10 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
       DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksvd_sweep_kernel, KS_T, sm_need),
                     "dlsh_ksvd_update: occupancy");
       if (per_sm < 1) return set_error(DLSH_ERR_CUDA, "dlsh_ksvd_update: sweep kernel does not fit");
-      coop_grid = g;
-    }
+      grid = g;
+      return DLSH_OK;
+    });
+    if (crc) return crc;
     const size_t smem = static_cast<size_t>(coop_grid) * 48 * sizeof(float);
     DLSH_CUDA_TRY(cudaMemsetAsync(w.gbar, 0, 2 * sizeof(unsigned), st), "dlsh_ksvd_update: barrier");
     const int* as = w.atom_start;

@@ -606,13 +606,16 @@ static int fused_enqueue(const void* mlp_blob, int K, const float* X, long long 
   const int grid = static_cast<int>(ntiles < device_sm_count() ? ntiles : device_sm_count());
 #define LAUNCH(MM, LG)                                                                             \
   do {                                                                                             \
-    static bool attr = false;                                                                      \
-    if (!attr) {                                                                                   \
+    static PerDevice<int> attr;                                                                    \
+    int attr_ok = 0;                                                                               \
+    const int arc = attr.get(&attr_ok, [&](int& v) {                                               \
       DLSH_CUDA_TRY(cudaFuncSetAttribute(propose_kernel<MM, LG>,                                   \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES), \
                     call);                                                                         \
-      attr = true;                                                                                 \
-    }                                                                                              \
+      v = 1;                                                                                       \
+      return DLSH_OK;                                                                              \
+    });                                                                                            \
+    if (arc) return arc;                                                                           \
     propose_kernel<MM, LG><<<grid, NTHREADS, SMEM_BYTES, st>>>(a);                                 \
   } while (0)
   switch (m) {
