@@ -25,19 +25,28 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static std::mutex g_mu;
 static void* g_addr[kMaxDevices] = {};
 
-// Looks up (once per device, with that device current) the device address of
-// g_scratch.
-static int scratch_address(void** out) {
+// The device address of g_scratch on the current device.  Outside a stream
+// capture it is looked up with cudaGetSymbolAddress on every call (so a context
+// rebuilt after cudaDeviceReset is seen) and remembered per device; inside a
+// capture the remembered address is used, so the first call on a device must
+// come before any capture.
+static int scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_encode_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: device %d out of range", dev);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DLSH_CUDA_TRY(cudaStreamIsCapturing(st, &cs), "dlsh_encode_noalloc: cudaStreamIsCapturing");
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
+  if (cs == cudaStreamCaptureStatusNone) {
     void* p = nullptr;
     DLSH_CUDA_TRY(cudaGetSymbolAddress(&p, g_scratch), "dlsh_encode_noalloc: cudaGetSymbolAddress");
     if (!p) return set_error(DLSH_ERR_CUDA, "dlsh_encode_noalloc: null scratch address");
     g_addr[dev] = p;
+  } else if (!g_addr[dev]) {
+    return set_error(DLSH_ERR_INVALID_ARG,
+                     "dlsh_encode_noalloc: the first call on device %d must come before any stream "
+                     "capture", dev);
   }
   *out = g_addr[dev];
   return DLSH_OK;
@@ -73,10 +82,10 @@ extern "C" int dlsh_encode_noalloc(const float* D, int K, int d, const float* X,
                      "dlsh_encode_noalloc: K=%d s=%d precision=%d needs %zu bytes of scratch, "
                      "more than the fixed %zu (use dlsh_encode with a workspace)",
                      K, s, precision, need, noalloc::kScratchBytes);
-  void* ws = nullptr;
-  int rc = noalloc::scratch_address(&ws);
-  if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* ws = nullptr;
+  int rc = noalloc::scratch_address(st, &ws);
+  if (rc) return rc;
   uint32_t* status = nullptr;
   rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status);
   if (rc) return rc;

@@ -79,3 +79,37 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
     rc = L.dlsh_encode_noalloc(fake, 2048, 45, fake, 10, 8, 0.0, 0, fake, fake, fake, None, None, 0)
     assert rc == -2
     assert b"scratch" in L.dlsh_last_error()
+
+
+def _largest_fitting_k(L, s, prec):
+    """Largest K whose encoder scratch fits the fixed array (host-side sizes only)."""
+    cap = L.dlsh_encode_noalloc_max_bytes()
+    K = 1024
+    while L.dlsh_encode_workspace_size(K + 1, 45, s, prec) <= cap:
+        K += 1
+    return K
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_noalloc_at_the_edges_of_its_scratch(lib, prec):
+    """K = 1024 with s = 16, and the largest K whose scratch fits, both against
+    the workspace encoder; one atom more must be refused before any launch."""
+    L = _lib.lib()
+    D = torch.from_numpy(synth.hidden_dictionary(1024, 31 + prec).astype(np.float32)).cuda()
+    X = torch.from_numpy(synth.signals(3000, synth.hidden_dictionary(1024, 32), 12, 33)).cuda()
+    _compare(_noalloc(L, D, X, 16, prec), _with_workspace(L, D, X, 16, prec))
+    Kmax = _largest_fitting_k(L, 8, prec)
+    assert Kmax >= 1024
+    Dm = torch.from_numpy(synth.hidden_dictionary(Kmax, 41 + prec).astype(np.float32)).cuda()
+    Xm = torch.from_numpy(synth.signals(1500, synth.hidden_dictionary(Kmax, 42), 8, 43)).cuda()
+    _compare(_noalloc(L, Dm, Xm, 8, prec), _with_workspace(L, Dm, Xm, 8, prec))
+    Dn = torch.from_numpy(synth.hidden_dictionary(Kmax + 1, 44).astype(np.float32)).cuda()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    n = Xm.shape[0]
+    out = (torch.empty((n, 8), dtype=torch.int16, device="cuda"),
+           torch.empty((n, 8), dtype=torch.float32, device="cuda"),
+           torch.empty((n,), dtype=torch.uint8, device="cuda"),
+           torch.empty((n,), dtype=torch.float32, device="cuda"))
+    rc = L.dlsh_encode_noalloc(_ptr(Dn), Kmax + 1, 45, _ptr(Xm), n, 8, 0.0, prec,
+                               *[_ptr(t) for t in out], stream, 1)
+    assert rc == -2 and b"scratch" in L.dlsh_last_error()
