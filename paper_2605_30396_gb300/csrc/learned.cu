@@ -1,12 +1,13 @@
 // Learned support proposal, second half: OMP restricted to the MLP's 2s
 // candidate atoms, then plain OMP (Sec. 2.1) as the fallback.
 //
-// restricted_omp_kernel  one thread per signal.  The candidates' correlations
-//                        with x (alpha0 = D_C^T x) and their Gram block G_CC are
-//                        gathered once; the s greedy steps then run on these
-//                        small arrays alone (c = alpha0 - G_CI gamma), with the
-//                        same incremental Cholesky least squares as the full
-//                        encoder.  The final residual is recomputed explicitly.
+// restricted_omp_kernel  one lane per candidate (a signal's m candidates on m
+//                        lanes of a warp).  alpha = D_C^T x once; then per step
+//                        the correlations with the least-squares residual come
+//                        from the lanes' projected Gram columns and y = L^-1
+//                        D_I^T x, the argmax is a shuffle reduction, and adding
+//                        an atom costs one Gram entry per lane.  The final
+//                        residual is recomputed explicitly.
 // fallback               "exact": plain OMP on every signal, keep whichever code
 //                        has the smaller residual (ties keep the learned one);
 //                        "deploy": plain OMP only for signals whose learned
@@ -23,156 +24,199 @@ namespace dlsh {
 
 namespace lrn {
 
-constexpr int RT = 64;  // threads per block of the restricted OMP
+constexpr int RW = 8;  // warps per block of the restricted OMP
 constexpr float CORR_STOP_REL = 1e-7f;
 constexpr float PIVOT_MIN = 1e-6f;
 constexpr int DPAD = 48;
 
 __host__ __device__ constexpr int tri(int n) { return n * (n + 1) / 2; }
-__host__ __device__ constexpr int rest_words(int m, int s) { return tri(m) + m + tri(s) + 3 * s; }
 
-// Shared arrays are [entry][RT] so consecutive threads hit consecutive banks.
-template <int M>
-__global__ void __launch_bounds__(RT)
+// One lane per candidate: M lanes serve one signal, 32 / M signals per warp.
+// Lane q owns candidate q (atom j_q) and keeps, for the current support I,
+//   v_q = L^-1 G_{I,q}   (L L^T = G_II, the Cholesky factor of the support's Gram)
+// while every lane of the signal keeps y = L^-1 D_I^T x.  The correlation with
+// the least-squares residual is then c_q = alpha_q - v_q . y (alpha = D_C^T x),
+// the new atom p's factor row is w = v_p (taken from lane p with shuffles), and
+// adding p appends (G_qp - w . v_q) / ell to v_q and (alpha_p - w . y) / ell to
+// y, ell = sqrt(G_pp - w . w).  Each step is O(t) per lane; gamma comes from
+// one back substitution L^T gamma = y at the end, and the reported residual is
+// recomputed explicitly as x - D_I gamma.
+template <int M, int SMAX>
+__global__ void __launch_bounds__(RW * 32)
     restricted_omp_kernel(const float* __restrict__ X, long long N, const float* __restrict__ D32p,
                           const float* __restrict__ G, int K, const uint16_t* __restrict__ cand,
                           int s, float eps, uint16_t* __restrict__ idx, float* __restrict__ coef,
                           uint8_t* __restrict__ nnz, float* __restrict__ resid,
                           uint32_t* status) {
-  extern __shared__ float rs[];
-  const int tid = threadIdx.x;
-  const long long n = static_cast<long long>(blockIdx.x) * RT + tid;
-  float* Gc = rs;                          // tri(M)
-  float* a0 = Gc + tri(M) * RT;            // M
-  float* Ls = a0 + M * RT;                 // tri(s)
-  float* ys = Ls + tri(s) * RT;            // s
-  float* gs = ys + s * RT;                 // s
-  int* si = reinterpret_cast<int*>(gs + s * RT);  // s: positions (0..M-1) in selection order
-#define GC(q, p) Gc[((q) >= (p) ? tri(q) + (p) : tri(p) + (q)) * RT + tid]
-#define LS(r, c) Ls[(tri(r) + (c)) * RT + tid]
-  if (n >= N) return;
-  int cj[M];
+  constexpr int SPW = 32 / M;
+  __shared__ float Lsh[RW][SPW][tri(SMAX)];  // the factor's rows, for the final solve
+  __shared__ float Ish[RW][SPW][SMAX];       // 1 / L(m, m)
+  __shared__ int Jsh[RW][SPW][SMAX];         // selected atoms in order
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q = lane % M, g = lane / M;
+  const long long n = (static_cast<long long>(blockIdx.x) * RW + warp) * SPW + g;
+  const bool live = n < N;
+  float* Lg = Lsh[warp][g];
+  float* Ig = Ish[warp][g];
+  int* Jg = Jsh[warp][g];
+  int j = 0;
   bool bad = false;
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    int j = cand[n * M + q];
+  if (live) {
+    j = cand[n * M + q];
     if (j >= K) {
       bad = true;
       j = 0;
     }
-    cj[q] = j;
   }
-  float x[48];
-  float xn2 = 0.f;
-#pragma unroll
-  for (int k = 0; k < 48; ++k) {
-    x[k] = k < DLSH_D ? X[n * DLSH_D + k] : 0.f;
-    xn2 = fmaf(x[k], x[k], xn2);
-  }
-  // alpha0 = D_C^T x and the Gram block of the candidates
-#pragma unroll
-  for (int q = 0; q < M; ++q) {
-    const float4* dr = reinterpret_cast<const float4*>(D32p + static_cast<size_t>(cj[q]) * DPAD);
-    float acc = 0.f;
+  // alpha_q = d_q . x and ||x||^2 (every lane of a signal reads the same x)
+  float alpha = 0.f, xn2 = 0.f;
+  if (live) {
+    const float4* dr = reinterpret_cast<const float4*>(D32p + static_cast<size_t>(j) * DPAD);
+    const float* xr = X + n * DLSH_D;
 #pragma unroll
     for (int u = 0; u < 12; ++u) {
       const float4 dv = __ldg(dr + u);
-      acc = fmaf(dv.x, x[4 * u + 0], acc);
-      acc = fmaf(dv.y, x[4 * u + 1], acc);
-      acc = fmaf(dv.z, x[4 * u + 2], acc);
-      acc = fmaf(dv.w, x[4 * u + 3], acc);
+      // the row holds 45 values: dims 45..47 are the dictionary's zero padding
+      const float x0 = __ldg(xr + 4 * u);
+      const float x1 = 4 * u + 1 < DLSH_D ? __ldg(xr + 4 * u + 1) : 0.f;
+      const float x2 = 4 * u + 2 < DLSH_D ? __ldg(xr + 4 * u + 2) : 0.f;
+      const float x3 = 4 * u + 3 < DLSH_D ? __ldg(xr + 4 * u + 3) : 0.f;
+      alpha = fmaf(dv.x, x0, alpha);
+      alpha = fmaf(dv.y, x1, alpha);
+      alpha = fmaf(dv.z, x2, alpha);
+      alpha = fmaf(dv.w, x3, alpha);
+      xn2 = fmaf(x0, x0, xn2);
+      xn2 = fmaf(x1, x1, xn2);
+      xn2 = fmaf(x2, x2, xn2);
+      xn2 = fmaf(x3, x3, xn2);
     }
-    a0[q * RT + tid] = acc;
   }
-#pragma unroll
-  for (int q = 0; q < M; ++q)
-#pragma unroll
-    for (int p = 0; p <= q; ++p) GC(q, p) = __ldg(G + static_cast<size_t>(cj[q]) * K + cj[p]);
+  const float gself = live ? __ldg(G + static_cast<size_t>(j) * K + j) : 0.f;
   const float xnorm = sqrtf(xn2);
-  uint32_t taken = 0;
+  float v[SMAX], y[SMAX];
+#pragma unroll
+  for (int m = 0; m < SMAX; ++m) v[m] = y[m] = 0.f;
+  bool act = live, chosen = false;
   int t = 0;
   for (int it = 0; it < s; ++it) {
-    if (eps > 0.f) {
-      // ||r||^2 = ||x||^2 - y.y for the current least-squares fit
+    if (act && eps > 0.f) {
+      // ||r||^2 = ||x||^2 - y . y for the current least-squares fit
       float yy = 0.f;
-      for (int k = 0; k < t; ++k) yy = fmaf(ys[k * RT + tid], ys[k * RT + tid], yy);
-      if (xn2 - yy <= eps * eps) break;
-    }
-    // c = alpha0 - G_{C,I} gamma over the candidates not yet selected
-    float best = 0.f;
-    int bq = -1, bj = 0x7fffffff;
 #pragma unroll
-    for (int q = 0; q < M; ++q) {
-      float c = a0[q * RT + tid];
-      for (int k = 0; k < t; ++k) c = fmaf(-GC(q, si[k * RT + tid]), gs[k * RT + tid], c);
-      const float ac = fabsf(c);
-      if (!((taken >> q) & 1u) && (ac > best || (ac == best && cj[q] < bj))) {
-        best = ac;
-        bq = q;
-        bj = cj[q];
+      for (int m = 0; m < SMAX; ++m)
+        if (m < t) yy = fmaf(y[m], y[m], yy);
+      if (xn2 - yy <= eps * eps) act = false;
+    }
+    float c = alpha;
+#pragma unroll
+    for (int m = 0; m < SMAX; ++m)
+      if (m < t) c = fmaf(-v[m], y[m], c);
+    // key: |c| (a non-negative float orders as its bits), then the smaller
+    // atom id, then the lane (unique); 0 = no candidate
+    const float ac = fabsf(c);
+    unsigned long long key = 0ull;
+    if (act && !chosen && ac >= 0.f)
+      key = (static_cast<unsigned long long>(__float_as_uint(ac)) << 32) |
+            (static_cast<unsigned long long>(0xFFFFu - static_cast<unsigned>(j)) << 5) |
+            static_cast<unsigned long long>(31 - q);
+#pragma unroll
+    for (int o = 1; o < M; o <<= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, key, o);
+      key = other > key ? other : key;
+    }
+    const float best = __uint_as_float(static_cast<uint32_t>(key >> 32));
+    const int jp = 0xFFFF - static_cast<int>((key >> 5) & 0xFFFFu);
+    const int src = g * M + 31 - static_cast<int>(key & 31u);
+    if (key == 0ull || !(best > CORR_STOP_REL * xnorm)) act = false;
+    // the new atom's factor row w = v_p, its Gram diagonal and alpha_p
+    float w[SMAX];
+#pragma unroll
+    for (int m = 0; m < SMAX; ++m) w[m] = __shfl_sync(0xffffffffu, v[m], src & 31);
+    const float gpp = __shfl_sync(0xffffffffu, gself, src & 31);
+    const float ap = __shfl_sync(0xffffffffu, alpha, src & 31);
+    if (act) {
+      const float gqp = __ldg(G + static_cast<size_t>(j) * K + jp);
+      float wn2 = 0.f;
+#pragma unroll
+      for (int m = 0; m < SMAX; ++m)
+        if (m < t) wn2 = fmaf(w[m], w[m], wn2);
+      const float ell2 = gpp - wn2;
+      if (!(ell2 > PIVOT_MIN * gpp)) {
+        act = false;
+      } else {
+        const float ell = sqrtf(ell2);
+        const float iell = 1.f / ell;
+        float vt = gqp, yt = ap;
+#pragma unroll
+        for (int m = 0; m < SMAX; ++m) {
+          if (m < t) {
+            vt = fmaf(-w[m], v[m], vt);
+            yt = fmaf(-w[m], y[m], yt);
+          }
+        }
+        vt *= iell;
+        yt *= iell;
+#pragma unroll
+        for (int m = 0; m < SMAX; ++m) {
+          if (m == t) {
+            v[m] = vt;
+            y[m] = yt;
+          }
+        }
+        if (q == 0) {
+#pragma unroll
+          for (int m = 0; m < SMAX; ++m)
+            if (m < t) Lg[tri(t) + m] = w[m];
+          Lg[tri(t) + t] = ell;
+          Ig[t] = iell;
+          Jg[t] = jp;
+        }
+        chosen |= (lane == src);
+        ++t;
       }
     }
-    if (bq < 0 || !(best > CORR_STOP_REL * xnorm)) break;
-    // Cholesky update with g_k = G[j*][I_k]
-    float wn2 = 0.f;
-    for (int m = 0; m < t; ++m) {
-      float acc = GC(bq, si[m * RT + tid]);
-      for (int qq = 0; qq < m; ++qq) acc = fmaf(-LS(m, qq), LS(t, qq), acc);
-      const float w = acc / LS(m, m);
-      LS(t, m) = w;
-      wn2 = fmaf(w, w, wn2);
-    }
-    const float gjj = GC(bq, bq);
-    const float ell2 = gjj - wn2;
-    if (!(ell2 > PIVOT_MIN * gjj)) break;
-    const float ell = sqrtf(ell2);
-    LS(t, t) = ell;
-    float yt = a0[bq * RT + tid];
-    for (int m = 0; m < t; ++m) yt = fmaf(-LS(t, m), ys[m * RT + tid], yt);
-    ys[t * RT + tid] = yt / ell;
-    si[t * RT + tid] = bq;
-    taken |= 1u << bq;
-    ++t;
-    for (int m = t - 1; m >= 0; --m) {
-      float acc = ys[m * RT + tid];
-      for (int qq = m + 1; qq < t; ++qq) acc = fmaf(-LS(qq, m), gs[qq * RT + tid], acc);
-      gs[m * RT + tid] = acc / LS(m, m);
+  }
+  __syncwarp();
+  // gamma from L^T gamma = y (every lane of the signal, identical values)
+  float gam[SMAX];
+#pragma unroll
+  for (int m = SMAX - 1; m >= 0; --m) {
+    gam[m] = 0.f;
+    if (m < t) {
+      float acc = y[m];
+#pragma unroll
+      for (int r = m + 1; r < SMAX; ++r)
+        if (r < t) acc = fmaf(-Lg[tri(r) + m], gam[r], acc);
+      gam[m] = acc * Ig[m];
     }
   }
-  // explicit residual of the final code
-#pragma unroll
-  for (int k = 0; k < 48; ++k) x[k] = k < DLSH_D ? x[k] : 0.f;
-  for (int m = 0; m < t; ++m) {
-    const float gm = gs[m * RT + tid];
-    int qsel = si[m * RT + tid];
-    int j = 0;
-#pragma unroll
-    for (int q = 0; q < M; ++q)
-      if (q == qsel) j = cj[q];
-    const float4* dr = reinterpret_cast<const float4*>(D32p + static_cast<size_t>(j) * DPAD);
-#pragma unroll
-    for (int u = 0; u < 12; ++u) {
-      const float4 dv = __ldg(dr + u);
-      x[4 * u + 0] = fmaf(-gm, dv.x, x[4 * u + 0]);
-      x[4 * u + 1] = fmaf(-gm, dv.y, x[4 * u + 1]);
-      x[4 * u + 2] = fmaf(-gm, dv.z, x[4 * u + 2]);
-      x[4 * u + 3] = fmaf(-gm, dv.w, x[4 * u + 3]);
-    }
-    idx[n * s + m] = static_cast<uint16_t>(j);
-    coef[n * s + m] = gm;
-  }
-  for (int m = t; m < s; ++m) {
-    idx[n * s + m] = 0;
-    coef[n * s + m] = 0.f;
-  }
+  // explicit residual of the final code: lane q takes dimensions q, q + M, ...
   float r2 = 0.f;
+  if (live) {
+    for (int k = q; k < DLSH_D; k += M) {
+      float r = __ldg(X + n * DLSH_D + k);
 #pragma unroll
-  for (int k = 0; k < 48; ++k) r2 = fmaf(x[k], x[k], r2);
-  nnz[n] = static_cast<uint8_t>(t);
-  resid[n] = r2;
+      for (int m = 0; m < SMAX; ++m)
+        if (m < t) r = fmaf(-gam[m], __ldg(D32p + static_cast<size_t>(Jg[m]) * DPAD + k), r);
+      r2 = fmaf(r, r, r2);
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < M; o <<= 1) r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < SMAX; ++m) {
+      if (m < s && m % M == q) {
+        idx[n * s + m] = m < t ? static_cast<uint16_t>(Jg[m]) : static_cast<uint16_t>(0);
+        coef[n * s + m] = m < t ? gam[m] : 0.f;
+      }
+    }
+    if (q == 0) {
+      nnz[n] = static_cast<uint8_t>(t);
+      resid[n] = r2;
+    }
+  }
   if (bad) flag_status(status, ST_BAD_INPUT);
-#undef GC
-#undef LS
 }
 
 // exact mode: keep the plain code where its residual is smaller (1e-6 relative)
@@ -268,23 +312,17 @@ static int restricted_launch(const float* X, long long N, const float* D32p, con
                              cudaStream_t st) {
   using namespace lrn;
   if (N == 0) return DLSH_OK;
-  const size_t smem = static_cast<size_t>(rest_words(m, s)) * RT * 4;
-  const int grid = static_cast<int>((N + RT - 1) / RT);
-#define LAUNCH(MM)                                                                              \
-  do {                                                                                          \
-    DLSH_CUDA_TRY(cudaFuncSetAttribute(restricted_omp_kernel<MM>,                               \
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize,             \
-                                       static_cast<int>(smem)),                                 \
-                  "dlsh_encode_restricted: attribute");                                         \
-    restricted_omp_kernel<MM><<<grid, RT, smem, st>>>(X, N, D32p, G, K, cand, s, eps, idx, coef, \
-                                                      nnz, resid, status);                      \
-  } while (0)
+  const long long per_block = static_cast<long long>(RW) * (32 / m);
+  const int grid = static_cast<int>((N + per_block - 1) / per_block);
+#define LAUNCH(MM, SM)                                                                     \
+  restricted_omp_kernel<MM, SM><<<grid, RW * 32, 0, st>>>(X, N, D32p, G, K, cand, s, eps, idx, \
+                                                          coef, nnz, resid, status)
   switch (m) {
-    case 2: LAUNCH(2); break;
-    case 4: LAUNCH(4); break;
-    case 8: LAUNCH(8); break;
-    case 16: LAUNCH(16); break;
-    case 32: LAUNCH(32); break;
+    case 2: LAUNCH(2, 8); break;
+    case 4: LAUNCH(4, 8); break;
+    case 8: LAUNCH(8, 8); break;
+    case 16: if (s <= 8) LAUNCH(16, 8); else LAUNCH(16, 16); break;
+    case 32: if (s <= 8) LAUNCH(32, 8); else LAUNCH(32, 16); break;
     default: return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_restricted: m must be 2, 4, 8, 16 or 32");
   }
 #undef LAUNCH
