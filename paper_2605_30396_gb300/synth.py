@@ -162,3 +162,36 @@ def random_codes(N: int, K: int, s: int, seed: int, nnz_min: int = 0):
     idx[pad] = 0
     coef[pad] = 0.0
     return idx.astype(np.uint16), coef.astype(np.float32), nnz.astype(np.uint8)
+
+
+def signals_device(N: int, atoms, s: int, seed: int, noise_std: float = 1e-3,
+                   device="cuda", chunk: int = 1 << 20):
+    """`signals` drawn on the GPU with torch's seeded generator: the same recipe
+    (s distinct uniform atoms per signal, Laplace(b=1) coefficients, N(0,
+    noise_std^2) noise), another random stream.  For bench-scale inputs, where
+    drawing tens of millions of signals on the host would dominate the run.
+    Returns an (N, 45) float32 CUDA tensor."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    A = torch.as_tensor(np.asarray(atoms), dtype=torch.float32, device=device)
+    K = A.shape[0]
+    out = torch.empty((N, D_SH), dtype=torch.float32, device=device)
+    for lo in range(0, N, chunk):
+        n = min(chunk, N - lo)
+        # s distinct atoms: draw, then redraw every row that holds a repeat
+        sup = torch.randint(0, K, (n, s), generator=g, device=device)
+        while True:
+            srt, _ = torch.sort(sup, dim=1)
+            bad = (srt[:, 1:] == srt[:, :-1]).any(dim=1).nonzero().flatten()
+            if bad.numel() == 0:
+                break
+            sup[bad] = torch.randint(0, K, (bad.numel(), s), generator=g, device=device)
+        # Laplace(0, 1) by inversion of a uniform on (-1/2, 1/2)
+        u = torch.rand((n, s), generator=g, device=device, dtype=torch.float64) - 0.5
+        u = u.clamp(-0.5 + 1e-12, 0.5 - 1e-12)
+        coef = (-torch.sign(u) * torch.log1p(-2.0 * u.abs())).to(torch.float32)
+        x = torch.einsum("ns,nsd->nd", coef, A[sup])
+        x += noise_std * torch.randn((n, D_SH), generator=g, device=device)
+        out[lo:lo + n] = x
+    return out
