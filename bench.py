@@ -28,9 +28,9 @@ METRIC = ("OMP Gaussians/s at K=1024,s=8, learned+BF16 vs plain at equal RMSE; d
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
 # DRAM bytes (read + write) per signal of the encoder, from one ncu capture of
-# encode_kernel at N = 1,000,000, K = 1024, s = 8, FP32 (profiles/
-# encode_kernel_fp32_N1M_K1024_s8.md: 184.92 MB + 37.26 MB); the traffic
-# grows with the number of signals, so a launch over N signals moves N times it.
+# encode_kernel at N = 1,000,000, K = 1024, s = 8, FP32 (184.92 MB read +
+# 37.26 MB written); the traffic grows with the number of signals, so a launch
+# over N signals moves N times it.
 ENCODE_TRAFFIC = {(1024, 8, "fp32"): (184.9216e6 + 37.260032e6) / 1_000_000}
 
 

@@ -54,7 +54,8 @@ extern "C" {
 #define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; the best atom of each
                             column quarter (j mod 128 in [32q, 32q+32)) is
                             re-scored in FP32 before the commit                  */
-#define DLSH_PREC_FP8  2 /* E4M3 with per-atom and per-row scales; re-score as BF16 */
+#define DLSH_PREC_FP8  2 /* E4M3 with per-atom and per-row scales; the candidates
+                            are re-scored in FP32 as for BF16                    */
 
 /* ---- flags ------------------------------------------------------------ */
 #define DLSH_FLAG_SYNC 1 /* synchronise the stream and report device status */
@@ -124,9 +125,12 @@ int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
  * Scratch lives in one fixed device array of dlsh_encode_noalloc_max_bytes()
  * bytes (8 MiB), which every GPU that loads the library holds until the process
  * exits; that covers K <= 1024 at every precision and s.  A configuration that
- * needs more returns DLSH_ERR_UNSUPPORTED before anything is launched.  The
- * first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  All calls share
+ * needs more returns DLSH_ERR_UNSUPPORTED before anything is launched.  Each
+ * call outside a stream capture looks up the array's device address on the
+ * current device (so a context rebuilt after cudaDeviceReset is followed); a
+ * call inside a capture uses the address its device last looked up, so make
+ * the first call on a device before any stream capture (else
+ * DLSH_ERR_INVALID_ARG).  All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race on it and must be serialised by the caller.
  */
