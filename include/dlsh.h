@@ -51,11 +51,16 @@ extern "C" {
 
 /* ---- correlation precision of the OMP atom selection (D^T r) --------- */
 #define DLSH_PREC_FP32 0 /* "plain FP32": 3xTF32 split on tcgen05, FP32 accumulate */
-#define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; the best atom of each
-                            column quarter (j mod 128 in [32q, 32q+32)) is
-                            re-scored in FP32 before the commit                  */
-#define DLSH_PREC_FP8  2 /* E4M3 with per-atom and per-row scales; the candidates
-                            are re-scored in FP32 as for BF16                    */
+#define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; each row's exact
+                            low-precision top 4 (|c| truncated below the bits
+                            that carry the column, then the smaller atom index)
+                            is re-scored in FP32 before the commit              */
+#define DLSH_PREC_FP8  2 /* E4M3 with per-atom and per-row scales; top 4
+                            re-scored in FP32 as for BF16                        */
+#define DLSH_PREC_BF16_QW 3 /* BF16 with a cheaper candidate set: the best atom of
+                            each column quarter (j mod 128 in [32q, 32q+32)),
+                            re-scored in FP32                                    */
+#define DLSH_PREC_FP8_QW  4 /* FP8 with the column-quarter winners               */
 
 /* ---- flags ------------------------------------------------------------ */
 #define DLSH_FLAG_SYNC 1 /* synchronise the stream and report device status */
@@ -308,14 +313,15 @@ int dlsh_encode_restricted(const float* D, int K, int d, const float* X, int64_t
                            const uint16_t* cand, int m, int s, float eps, uint16_t* idx,
                            float* coef, uint8_t* nnz, float* resid_sq, void* ws,
                            size_t ws_bytes, void* stream, int flags);
-/* Learned encoder: MLP proposal of 2s candidates, restricted OMP, and plain OMP
- * (at fallback_precision) as the fallback.  mode 0 ("exact"): plain OMP runs on
+/* Learned encoder: MLP proposal of m candidates (m = 0: 2s; otherwise one of
+ * 2, 4, 8, 16, 32 with s <= m), restricted OMP, and plain OMP (at
+ * fallback_precision, any DLSH_PREC_*) as the fallback.  mode 0 ("exact"): plain OMP runs on
  * every signal and replaces the learned code when ||r_learned|| > ||r_plain|| *
  * (1 + 1e-6).  mode 1 ("deploy"): plain OMP runs only on the signals with
  * ||r_learned|| > tau.  n_fallback (device, uint64) receives the count. */
-size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N);
+size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N, int m);
 int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N, int s,
-                        float eps, const void* mlp, int mode, float tau,
+                        float eps, const void* mlp, int m, int mode, float tau,
                         int fallback_precision, uint16_t* idx, float* coef, uint8_t* nnz,
                         float* resid_sq, unsigned long long* n_fallback, void* ws,
                         size_t ws_bytes, void* stream, int flags);

@@ -18,7 +18,7 @@ import torch
 
 from . import _lib
 
-PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2}
+PRECISION = {"fp32": 0, "bf16": 1, "fp8": 2, "bf16_qw": 3, "fp8_qw": 4}
 FLAG_SYNC = 1
 D_SH = 45
 
@@ -494,9 +494,10 @@ def encode_restricted(D, X, cand, s: int, eps: float = 0.0, sync: bool = True):
 
 
 def encode_learned(D, X, s: int, mlp: "MLP", mode: str = "deploy", tau: float = 0.0,
-                   eps: float = 0.0, fallback_precision="fp32", sync: bool = False, out=None):
-    """Learned proposal + restricted OMP + plain-OMP fallback.  Returns
-    (idx, coef, nnz, resid_sq, n_fallback_tensor)."""
+                   eps: float = 0.0, fallback_precision="fp32", sync: bool = False, out=None,
+                   m: int = 0):
+    """Learned proposal (m candidates, 0 = 2s) + restricted OMP + plain-OMP
+    fallback.  Returns (idx, coef, nnz, resid_sq, n_fallback_tensor)."""
     host = not X.is_cuda
     D = _to_device(D, torch.float32)
     X = _to_device(X, torch.float32)
@@ -510,11 +511,11 @@ def encode_learned(D, X, s: int, mlp: "MLP", mode: str = "deploy", tau: float = 
         idx, coef, nnz, resid = out
     nfb = torch.zeros((1,), dtype=torch.int64, device="cuda")
     L = _lib.lib()
-    need = L.dlsh_encode_learned_workspace_size(K, D_SH, s, N)
+    need = L.dlsh_encode_learned_workspace_size(K, D_SH, s, N, int(m))
     if need == 0:
         raise DlshError(-2, "dlsh_encode_learned_workspace_size")
     ws = workspace(need, key="learned")
-    _check(L.dlsh_encode_learned(_p(D), K, D_SH, _p(X), N, s, float(eps), _p(mlp.blob),
+    _check(L.dlsh_encode_learned(_p(D), K, D_SH, _p(X), N, s, float(eps), _p(mlp.blob), int(m),
                                  0 if mode == "exact" else 1, float(tau), _prec(fallback_precision),
                                  _p(idx), _p(coef), _p(nnz), _p(resid), _p(nfb), _p(ws), ws.numel(),
                                  _stream(), FLAG_SYNC if sync else 0), "dlsh_encode_learned")

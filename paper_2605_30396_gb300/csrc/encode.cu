@@ -50,7 +50,7 @@ __host__ __device__ constexpr int op_kb(int prec) { return prec == 0 ? 12 : (pre
 __host__ __device__ constexpr int op_parts(int prec) { return prec == 0 ? 2 : 1; }
 
 struct Plan {
-  int prec, BN, K, Kp, nchunks, stages, resident, s;
+  int prec, top4, ib, BN, K, Kp, nchunks, stages, resident, s;
   uint32_t a_bytes, chunk_bytes;
   uint32_t off_a, off_ring, off_x, off_L, off_sel, off_y, off_g, off_idg, off_cand, off_r,
       off_sig, off_bar, smem;
@@ -58,19 +58,33 @@ struct Plan {
 
 inline int choose_bn(int prec, int s) { return (prec == 0 && s > 8) ? 64 : 128; }
 
+// Precision codes of the C ABI: 0 FP32 (3xTF32), 1 BF16 and 2 FP8 with the
+// exact low-precision top 4 re-scored in FP32, 3 BF16 and 4 FP8 with the four
+// column-quarter winners re-scored in FP32.  Returns the operand precision
+// (0 FP32, 1 BF16, 2 FP8) and whether the top-4 candidates are used.
+inline int operand_precision(int code, int* top4) {
+  if (top4) *top4 = (code == 1 || code == 2) ? 1 : 0;
+  return code == 0 ? 0 : ((code == 1 || code == 3) ? 1 : 2);
+}
+
 // Atom-chunk widths picked by dlsh_autotune_encode, keyed by (K, s, precision).
 int tuned_bn(int K, int s, int prec);
 
 // bn = 0: the tuned width if one was recorded, else the default.  BF16 and FP8
 // use 128 (the selection's key network packs 32 columns per thread).
-int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM_LIMIT) {
+int make_plan(int K, int s, int code, Plan& p, int bn = 0, int smem_limit = SMEM_LIMIT) {
+  const int prec = operand_precision(code, &p.top4);
   p.prec = prec;
   p.K = K;
   p.s = s;
-  if (bn == 0) bn = tuned_bn(K, s, prec);
+  if (bn == 0) bn = tuned_bn(K, s, code);
   p.BN = prec != 0 ? 128 : (bn == 64 || bn == 128 ? bn : choose_bn(prec, s));
   p.nchunks = (K + p.BN - 1) / p.BN;
   p.Kp = p.nchunks * p.BN;
+  // top-4 keys carry the column within the thread's quarter (chunk, then
+  // column in the chunk) in their low ib bits
+  p.ib = 5;
+  while ((1 << (p.ib - 5)) < p.nchunks) ++p.ib;
   p.a_bytes = TILE_M * op_kb(prec) * 16 * op_parts(prec);
   p.chunk_bytes = p.BN * op_kb(prec) * 16 * op_parts(prec);
   uint32_t off = 0;
@@ -86,7 +100,7 @@ int make_plan(int K, int s, int prec, Plan& p, int bn = 0, int smem_limit = SMEM
   p.off_y = take(s * TILE_M * 4);
   p.off_g = take(s * TILE_M * 4);
   p.off_idg = take(s * TILE_M * 4);
-  p.off_cand = take(TILE_M * 4 * 8);
+  p.off_cand = take(p.top4 ? TILE_M * 4 * 4 * 4 : TILE_M * 4 * 8);
   p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
   p.off_sig = take(prec == 2 ? p.Kp * 4 : 0);
   p.off_bar = take(1024);
@@ -398,8 +412,62 @@ __device__ __forceinline__ void tmem_ld_wait<16>(uint32_t (&r)[16]) {
   tmem_ld16_wait(r);
 }
 
+// ---------------------------------------------------------------------------
+// Exact top 4 on 32-bit keys with min/max only (no branches): lists are kept
+// sorted in decreasing order, a[0] >= a[1] >= a[2] >= a[3].
+// ---------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ void cex(T& hi, T& lo) {
+  const T h = hi > lo ? hi : lo;
+  const T l = hi > lo ? lo : hi;
+  hi = h;
+  lo = l;
+}
+// a := the sorted top 4 of a and b (both sorted).  The pairwise maxima of a
+// and b reversed hold the top 4 as a bitonic sequence, which two
+// compare-exchange stages sort.
+template <class T>
+__device__ __forceinline__ void merge_top4(T (&a)[4], const T (&b)[4]) {
+  T m0 = a[0] > b[3] ? a[0] : b[3];
+  T m1 = a[1] > b[2] ? a[1] : b[2];
+  T m2 = a[2] > b[1] ? a[2] : b[1];
+  T m3 = a[3] > b[0] ? a[3] : b[0];
+  cex(m0, m2);
+  cex(m1, m3);
+  cex(m0, m1);
+  cex(m2, m3);
+  a[0] = m0;
+  a[1] = m1;
+  a[2] = m2;
+  a[3] = m3;
+}
+// o := the sorted top 4 of k[0..7]: sorted pairs, merged into two sorted
+// quads, then the top 4 of the two quads.
+__device__ __forceinline__ void top4_of8(const uint32_t* k, uint32_t (&o)[4]) {
+  uint32_t p[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) p[i] = k[i];
+#pragma unroll
+  for (int i = 0; i < 8; i += 2) cex(p[i], p[i + 1]);
+  uint32_t q[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t a0 = p[4 * h], a1 = p[4 * h + 1], b0 = p[4 * h + 2], b1 = p[4 * h + 3];
+    const uint32_t x = min(a0, b0), y = max(a1, b1);
+    q[h][0] = max(a0, b0);
+    q[h][1] = max(x, y);
+    q[h][2] = min(x, y);
+    q[h][3] = min(a1, b1);
+  }
+  merge_top4(q[0], q[1]);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) o[i] = q[0][i];
+}
+
 // SMAX: compile-time bound on s (8 or 16) for the solver's register arrays.
-template <int PREC, int BN, int SMAX>
+// T4: BF16/FP8 candidates are each row's exact low-precision top 4 (else the
+// four column-quarter winners).
+template <int PREC, int BN, int SMAX, bool T4>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_constant__ Args a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NBUF = 512 / BN;
@@ -671,6 +739,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           // are not masked here (see the solver's stop rule).
           uint32_t best = 0;
           int bestc = 0;
+          // top-4 keys: |c| truncated to its bits above ib, then the column
+          // within the quarter (chunk * 32 + k) as (2^ib - 1) - column, so
+          // larger keys are larger values and, among equal truncated values,
+          // smaller columns
+          const uint32_t vmask = 0x7fffffffu & ~((1u << p.ib) - 1u);
+          uint32_t run[4] = {0u, 0u, 0u, 0u};
           for (int c = 0; c < nchunks; ++c, ++cc) {
             if (!acquire(cc)) {
               ok = false;
@@ -686,20 +760,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 #pragma unroll
               for (int k = 0; k < QC; ++k) rr[k] = __float_as_uint(__uint_as_float(rr[k]) * sig[j0 + k]);
             }
-            uint32_t m0 = 0, m1 = 0;
+            if constexpr (T4) {
+              static_assert(QC == 32, "top-4 keys pack a 5-bit column in the chunk");
 #pragma unroll
-            for (int k = 0; k < QC; k += 2) {
-              m0 = max(m0, (rr[k] & 0x7fffffe0u) | static_cast<uint32_t>(31 - k));
-              m1 = max(m1, (rr[k + 1] & 0x7fffffe0u) | static_cast<uint32_t>(30 - k));
-            }
-            const uint32_t m = max(m0, m1);
-            if ((m & ~31u) > (best & ~31u)) {
-              best = m;
-              bestc = c;
+              for (int k = 0; k < QC; ++k) rr[k] = (rr[k] & vmask) | static_cast<uint32_t>(31 - k);
+              uint32_t ct[4];
+              top4_of8(rr, ct);
+#pragma unroll
+              for (int o = 8; o < QC; o += 8) {
+                uint32_t t8[4];
+                top4_of8(rr + o, t8);
+                merge_top4(ct, t8);
+              }
+              const uint32_t cf = ((1u << p.ib) - 32u) - static_cast<uint32_t>(c) * 32u;
+#pragma unroll
+              for (int i = 0; i < 4; ++i) ct[i] |= cf;
+              merge_top4(run, ct);
+            } else {
+              uint32_t m0 = 0, m1 = 0;
+#pragma unroll
+              for (int k = 0; k < QC; k += 2) {
+                m0 = max(m0, (rr[k] & 0x7fffffe0u) | static_cast<uint32_t>(31 - k));
+                m1 = max(m1, (rr[k + 1] & 0x7fffffe0u) | static_cast<uint32_t>(30 - k));
+              }
+              const uint32_t m = max(m0, m1);
+              if ((m & ~31u) > (best & ~31u)) {
+                best = m;
+                bestc = c;
+              }
             }
           }
-          cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
-          cj[R1 * 4 + q1] = bestc * BN + q1 * QC + 31 - static_cast<int>(best & 31u);
+          if constexpr (T4) {
+            uint32_t* ck = reinterpret_cast<uint32_t*>(smem + p.off_cand) + (R1 * 4 + q1) * 4;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ck[i] = run[i];
+          } else {
+            cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
+            cj[R1 * 4 + q1] = bestc * BN + q1 * QC + 31 - static_cast<int>(best & 31u);
+          }
         }
         const long long T1 = prof_on ? clock64() : 0;
         // barrier + vote: every selection thread leaves together if any wait ran out
@@ -757,10 +855,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
             for (int m = 0; m < SMAX; ++m) dup |= (m < t && sl[m] == js);
             if (dup) js = -1;
           } else {
-            // the four column-quarter winners re-scored in FP32: c = r . d_j
+            // the candidates re-scored in FP32: c = r . d_j.  T4: the row's
+            // exact low-precision top 4, merged from the four quarters' top-4
+            // lists (sub-lane u reads quarter u, two butterfly rounds) on
+            // 64-bit keys (truncated |c|, then the smaller atom index);
+            // otherwise the four column-quarter winners.
+            int cjr[4];
+            if constexpr (T4) {
+              const uint32_t* ck = reinterpret_cast<const uint32_t*>(smem + p.off_cand) + (R2 * 4 + u) * 4;
+              const uint32_t imask = (1u << p.ib) - 1u;
+              const uint32_t vmask = 0x7fffffffu & ~imask;
+              unsigned long long lst[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const uint32_t key = ck[i];
+                const uint32_t col = imask - (key & imask);
+                const uint32_t j = (col >> 5) * BN + static_cast<uint32_t>(u * QC) + (col & 31u);
+                lst[i] = key == 0u ? 0ull
+                                   : (static_cast<unsigned long long>(key & vmask) << 32) |
+                                         static_cast<unsigned long long>(0xFFFFFFFFu - j);
+              }
+#pragma unroll
+              for (int o = 1; o <= 2; o <<= 1) {
+                unsigned long long oth[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) oth[i] = __shfl_xor_sync(quad_mask(), lst[i], o);
+                merge_top4(lst, oth);
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+                cjr[i] = lst[i] == 0ull ? 0x7fffffff
+                                        : static_cast<int>(0xFFFFFFFFu - static_cast<uint32_t>(lst[i]));
+            } else {
+#pragma unroll
+              for (int qq = 0; qq < 4; ++qq) cjr[qq] = cj[R2 * 4 + qq];
+            }
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
-              const int j = cj[R2 * 4 + qq];
+              const int j = cjr[qq];
               float c0 = 0.f;
               if (j < K) {
                 const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(j) * DPAD + 12 * u);
@@ -1069,15 +1201,15 @@ static int validate(const char* call, const float* D, int K, int d, int s, int p
     return set_error(DLSH_ERR_UNSUPPORTED, "%s: K must be in [1, 65535], got %d", call, K);
   if (s < 1 || s > 16)
     return set_error(DLSH_ERR_UNSUPPORTED, "%s: s must be in [1, 16], got %d", call, s);
-  if (prec < 0 || prec > 2)
+  if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "%s: unknown precision %d", call, prec);
   if (!D) return set_error(DLSH_ERR_INVALID_ARG, "%s: D is NULL", call);
   return DLSH_OK;
 }
 
-template <int PREC, int BN>
+template <int PREC, int BN, bool T4 = false>
 static int launch_encode(const Args& a, int grid, cudaStream_t st) {
-  auto fn = a.p.s <= 8 ? encode_kernel<PREC, BN, 8> : encode_kernel<PREC, BN, 16>;
+  auto fn = a.p.s <= 8 ? encode_kernel<PREC, BN, 8, T4> : encode_kernel<PREC, BN, 16, T4>;
   DLSH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
                 "dlsh_encode: cudaFuncSetAttribute");
   fn<<<grid, NTHREADS, a.p.smem, st>>>(a);
@@ -1157,9 +1289,10 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   if (sms <= 0) sms = 1;
   const int grid = (n_dev || ntiles > sms) ? sms : (ntiles > 0 ? ntiles : 1);
   if (p.BN == 128) {
-    if (prec == 0) return launch_encode<0, 128>(a, grid, st);
-    if (prec == 1) return launch_encode<1, 128>(a, grid, st);
-    return launch_encode<2, 128>(a, grid, st);
+    if (p.prec == 0) return launch_encode<0, 128>(a, grid, st);
+    if (p.prec == 1)
+      return p.top4 ? launch_encode<1, 128, true>(a, grid, st) : launch_encode<1, 128>(a, grid, st);
+    return p.top4 ? launch_encode<2, 128, true>(a, grid, st) : launch_encode<2, 128>(a, grid, st);
   }
   return launch_encode<0, 64>(a, grid, st);
 }
@@ -1198,7 +1331,7 @@ size_t encode_ws_bytes(int K, int s, int prec) {
 extern "C" {
 
 size_t dlsh_encode_workspace_size(int K, int d, int s, int precision) {
-  if (d != DLSH_D || K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || precision < 0 || precision > 2)
+  if (d != DLSH_D || K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || precision < 0 || precision > 4)
     return 0;
   return dlsh::encode_ws_bytes(K, s, precision);
 }
@@ -1275,8 +1408,8 @@ int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M, int 
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
     const int grid = ntiles < sms ? ntiles : sms;
-    if (precision == 0) rc = launch_correlate<0, 128>(R, M, p, w, C, grid, st);
-    else if (precision == 1) rc = launch_correlate<1, 128>(R, M, p, w, C, grid, st);
+    if (p.prec == 0) rc = launch_correlate<0, 128>(R, M, p, w, C, grid, st);
+    else if (p.prec == 1) rc = launch_correlate<1, 128>(R, M, p, w, C, grid, st);
     else rc = launch_correlate<2, 128>(R, M, p, w, C, grid, st);
     if (rc) return rc;
   }
@@ -1445,7 +1578,7 @@ static size_t multi_carve(void* base, const dlsh_scene* sc, int n, int prec, uin
 static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
   if (!sc || n < 1 || n > MAX_SCENES)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
-  if (prec < 0 || prec > 2)
+  if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
   if (bn != 0 && bn != 64 && bn != 128)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 64 or 128");

@@ -194,7 +194,7 @@ extern "C" {
 
 size_t dlsh_learn_workspace_size(int K, int d, int s, int64_t N, int precision) {
   if (d != DLSH_D || K < 1 || K > 4096 || s < 1 || s > 16 || N < 0 || precision < 0 ||
-      precision > 2)
+      precision > 4)
     return 0;
   if (dlsh::encode_ws_bytes(K, s, precision) == 0) return 0;
   return dlsh::learn_ws_bytes(K, s, N, precision);
@@ -211,7 +211,7 @@ int dlsh_learn_dictionary(const float* X, int64_t N, int d, int K, int s, float 
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_learn_dictionary: K must be in [1, 4096]");
   if (s < 1 || s > 16)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_learn_dictionary: s must be in [1, 16]");
-  if (precision < 0 || precision > 2)
+  if (precision < 0 || precision > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_learn_dictionary: unknown precision");
   if (iters < 0) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_learn_dictionary: iters < 0");
   if (N < K)

@@ -67,7 +67,7 @@ extern "C" int dlsh_encode_noalloc(const float* D, int K, int d, const float* X,
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: K must be in [1, 65535]");
   if (s < 1 || s > 16)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_noalloc: s must be in [1, 16]");
-  if (precision < 0 || precision > 2)
+  if (precision < 0 || precision > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: unknown precision %d", precision);
   if (!D) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: D is NULL");
   if (N < 0) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_noalloc: N < 0");
