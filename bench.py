@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the s-sweep, precision and multi-scene legs of the default run")
     ap.add_argument("--workload", default="scene", choices=["scene", "multi"],
                     help="scene: the single-scene step (default); multi: 13 scenes of uneven "
                          "size, K and s encoded by one graph-captured multi-scene call")
@@ -54,7 +56,7 @@ def parse():
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step",
                     choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
-                             "tolerance", "splat", "ksvd"],
+                             "tolerance", "splat", "ksvd", "precision"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -77,12 +79,14 @@ def aggregate_ranks(ms_local: float, n_local: int, world: int, device=None):
     return ms, n / (ms * 1e-3)
 
 
-def workload(N, K, s, seed_offset=0):
-    """Scene-scale inputs: hidden K-atom dictionary (rho = 0.6), s-sparse signals,
-    initial dictionary from K signals, camera on a radius-4 sphere, means in [-1,1]^3."""
+def workload(N, K, s, seed_offset=0, device="cuda"):
+    """Scene-scale inputs of one replica: s-sparse signals of the hidden K-atom
+    dictionary (rho = 0.6) drawn on `device`, the initial dictionary's signal
+    indices, a camera on a radius-4 sphere and means in [-1, 1]^3.  Replicas
+    draw with seeds offset by 100 per rank."""
     from paper_2605_30396_gb300 import synth
     Dh = synth.hidden_dictionary(K, 0 + seed_offset, rho=0.6)
-    X = synth.signals(N, Dh, s, 1 + seed_offset)
+    X = synth.signals_device(N, Dh, s, 1 + seed_offset, device=device)
     init = synth.init_atom_indices(N, K, 0 + seed_offset)
     cam, mu = synth.camera_and_means(N, 2 + seed_offset, 3 + seed_offset)
     return X, init, cam, mu
@@ -154,27 +158,33 @@ class Clocks:
 def _oracle_worker(args):
     D, X, s = args
     from oracle import omp as oomp
-    return oomp.omp(D, X, s)["resid_sq"]
+    out = oomp.omp(D, X, s)
+    return out["idx"], out["coef"], out["nnz"], out["resid_sq"]
 
 
-def cpu_oracle_rate(X, init, K, s, budget_s=15.0):
-    """The FP64 oracle OMP timed on this host's cores over a bounded sample of the
-    workload (processes started with spawn, one BLAS thread each)."""
+def cpu_oracle_step(X, init_rows, mu, cam, K, s, budget_s=15.0):
+    """The FP64 oracle timed on this host's cores over a bounded sample of the
+    workload, doing what one GPU step does: OMP codes of the sample against the
+    initial dictionary (spawned processes, one BLAS thread each), the MOD update
+    from those codes, and the decode of one colour per Gaussian.  Returns the
+    rate (sample Gaussians per second of the three) and the oracle's codes.
+
+    X: (n_max, 45) host sample; init_rows: K rows of X that seed the dictionary."""
     import multiprocessing as mp
 
     import numpy as np
     from oracle import mod as omod
-    cores = os.cpu_count() or 1
-    D0 = omod.init_dictionary(X, init)
-    X = X[:400_000]
-    # probe: size the sample for ~budget_s of work
     from oracle import omp as oomp
+    from oracle import sh as osh
+    cores = os.cpu_count() or 1
+    D0 = omod.init_dictionary(X, init_rows)
+    # probe: size the sample for about budget_s of OMP work over all cores
     n_probe = 2000
     t0 = time.perf_counter()
     oomp.omp(D0, X[:n_probe].astype(np.float64), s)
     per = (time.perf_counter() - t0) / n_probe
     n = int(min(len(X), max(cores * 200, budget_s * cores / max(per, 1e-9))))
-    n = min(n, 400_000)
+    Xs = X[:n].astype(np.float64)
     chunks = np.array_split(np.arange(n), cores * 2)
     env_old = os.environ.get("OMP_NUM_THREADS")
     os.environ["OMP_NUM_THREADS"] = "1"
@@ -183,35 +193,94 @@ def cpu_oracle_rate(X, init, K, s, budget_s=15.0):
         ctx = mp.get_context("spawn")
         with ctx.Pool(cores) as pool:
             t0 = time.perf_counter()
-            pool.map(_oracle_worker, [(D0, X[c].astype(np.float64), s) for c in chunks])
-            dt = time.perf_counter() - t0
+            parts = pool.map(_oracle_worker, [(D0, Xs[c], s) for c in chunks])
+            t_omp = time.perf_counter() - t0
     finally:
         if env_old is None:
             os.environ.pop("OMP_NUM_THREADS", None)
         else:
             os.environ["OMP_NUM_THREADS"] = env_old
-    return {"value": n / dt, "unit": "Gaussians/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 numpy OMP (K={K}, s={s}) on the first {n} of the {len(X)} signals "
-                      f"against the initial dictionary, {cores} spawn workers x 1 BLAS thread; "
-                      f"{dt:.1f} s",
-            "single_process": {"value": 1.0 / per, "unit": "Gaussians/s",
-                               "sample": f"the first {n_probe} signals in one process"}}
+    idx = np.concatenate([p[0] for p in parts])
+    coef = np.concatenate([p[1] for p in parts])
+    nnz = np.concatenate([p[2] for p in parts])
+    rsq = np.concatenate([p[3] for p in parts])
+    t0 = time.perf_counter()
+    D1, _ = omod.mod_update(Xs, D0, idx, coef, nnz, rsq)
+    t_mod = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    osh.decode(D1, idx, coef, nnz, means=mu[:n], cam=cam)
+    t_dec = time.perf_counter() - t0
+    dt = t_omp + t_mod + t_dec
+    return ({"value": n / dt, "unit": "Gaussians/s", "cores": cores, "kind": "oracle",
+             "sample": f"FP64 numpy oracle step on the first {n} signals of the workload (K={K}, "
+                       f"s={s}): OMP against the initial dictionary on {cores} spawn workers x 1 "
+                       f"BLAS thread ({t_omp:.1f} s), the MOD update ({t_mod:.1f} s) and the decode "
+                       f"({t_dec:.2f} s) in one process",
+             "omp_only": {"value": n / t_omp, "unit": "Gaussians/s"},
+             "single_process_omp": {"value": 1.0 / per, "unit": "Gaussians/s",
+                                    "sample": f"the first {n_probe} signals in one process"}},
+            {"n": n, "D0": D0, "idx": idx, "nnz": nnz, "resid_sq": rsq})
 
 
-def learned_leg(api, synth, D, X, s, K, cal_tau=1.01, n_train=2_000_000, n_cal=200_000,
-                epochs=10, batch=8192, lr=1e-2, seed=7):
+def oracle_agreement(api, X, oracle_codes, s):
+    """Codes of the GPU encoder at each precision on the oracle's sample, against
+    the oracle's FP64 codes (same initial dictionary): the fraction of signals
+    whose support sequence is identical, the fraction of selections that agree,
+    and the RMSE of the GPU codes (reconstructed in FP64) over the oracle's."""
+    import numpy as np
+    import torch
+    n = oracle_codes["n"]
+    D0 = torch.from_numpy(oracle_codes["D0"].astype(np.float32)).cuda()
+    Xs = X[:n]
+    oi = torch.from_numpy(oracle_codes["idx"]).cuda()
+    on = torch.from_numpy(oracle_codes["nnz"]).cuda()
+    o_rmse = float(np.sqrt(oracle_codes["resid_sq"].sum() / (n * 45)))
+    live = torch.arange(s, device="cuda")[None, :] < on[:, None]
+    out = {"n": n, "oracle_rmse": o_rmse}
+    for prec in ("fp32", "bf16", "fp8", "bf16_qw", "fp8_qw"):
+        idx, coef, nnz, _ = api.encode(D0, Xs, s, precision=prec, sync=True)
+        gi = api.idx_as_long(idx)
+        same = ((gi == oi) | ~live).all(dim=1) & (nnz.to(torch.int64) == on)
+        out[prec] = {"supports_identical": float(same.double().mean()),
+                     "selections_agree": float(((gi == oi) & live).sum() / live.sum()),
+                     "rmse_over_oracle": exact_rmse(D0, Xs, idx, coef, nnz) / o_rmse}
+    return out
+
+
+def exact_rmse(D, X, idx, coef, nnz):
+    """RMSE of codes, the reconstruction evaluated in FP64 (independent of the
+    kernel's own FP32 residual)."""
+    import torch
+    N, s = coef.shape
+    il = idx.to(torch.int64) & 0xFFFF
+    live = torch.arange(s, device=coef.device)[None, :] < nnz[:, None].to(torch.int64)
+    c = torch.where(live, coef, torch.zeros_like(coef)).double()
+    Dd = D.double()
+    tot = 0.0
+    for lo in range(0, N, 1 << 20):
+        hi = min(N, lo + (1 << 20))
+        rec = torch.einsum("ns,nsd->nd", c[lo:hi], Dd[il[lo:hi]])
+        r = X[lo:hi].double() - rec
+        tot += float((r * r).sum().item())
+    return (tot / (N * 45)) ** 0.5
+
+
+def learned_leg(api, synth, D, X, s, K, Dh, cal_tau=1.008, n_train=2_000_000, n_cal=200_000,
+                epochs=10, batch=8192, lr=1e-2, seed=7, m=None, fallback="bf16_qw"):
     """The learned encoder against plain FP32 OMP at (near) equal RMSE.
 
     The MLP is trained by the library's own kernels on (signal, OMP support)
     pairs the codec generates: n_train fresh signals from the same hidden
-    dictionary, encoded with the current dictionary D.  The fallback threshold
+    dictionary Dh, encoded with the current dictionary D.  The fallback threshold
     tau is calibrated on another fresh n_cal signals so that the deployed RMSE
-    stays within cal_tau of plain OMP's; then both encoders are timed on X (the
-    held-out scene, inputs resident)."""
+    stays within cal_tau of plain OMP's (a little under the 1.01 target, so the
+    held-out scene lands within it); then both encoders are timed on X (the
+    held-out scene, inputs resident).  m: candidates per signal (2s by default);
+    fallback: the plain-OMP precision used for the signals that fall back."""
     import numpy as np
     import torch
-    Dh = synth.hidden_dictionary(K, 0, rho=0.6)
-    Xtr = torch.from_numpy(synth.signals(n_train, Dh, s, seed)).cuda()
+    m = m or 2 * s
+    Xtr = synth.signals_device(n_train, Dh, s, seed)
     itr, _, ntr, _ = api.encode(D, Xtr, s, sync=True)
     net = api.MLP(K, synth.mlp_params(K, seed))
     torch.cuda.synchronize()
@@ -220,9 +289,9 @@ def learned_leg(api, synth, D, X, s, K, cal_tau=1.01, n_train=2_000_000, n_cal=2
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
     del Xtr, itr, ntr
-    Xc = torch.from_numpy(synth.signals(n_cal, Dh, s, seed + 1)).cuda()
+    Xc = synth.signals_device(n_cal, Dh, s, seed + 1)
     _, _, _, rp_c = api.encode(D, Xc, s, sync=True)
-    cand = net.propose(Xc, 2 * s)
+    cand = net.propose(Xc, m)
     _, _, _, rr_c = api.encode_restricted(D, Xc, cand, s)
     tau = api.calibrate_fallback(rr_c, rp_c, cal_tau)
     del Xc, cand
@@ -244,26 +313,36 @@ def learned_leg(api, synth, D, X, s, K, cal_tau=1.01, n_train=2_000_000, n_cal=2
 
     ms_plain, (_, _, _, rp) = timed(lambda: api.encode(D, X, s, precision="fp32"))
     ms_l, (_, _, _, rl, nfb) = timed(lambda: api.encode_learned(D, X, s, net, mode="deploy", tau=tau,
-                                                               fallback_precision="bf16"))
+                                                               fallback_precision=fallback, m=m))
     ms_b, (_, _, _, rb) = timed(lambda: api.encode(D, X, s, precision="bf16"))
+    ms_bq, (_, _, _, rbq) = timed(lambda: api.encode(D, X, s, precision="bf16_qw"))
+    # the learned path's parts, timed alone
+    ms_prop, cand = timed(lambda: net.propose(X, m))
+    ms_rest, _ = timed(lambda: api.encode_restricted(D, X, cand, s, sync=False))
     rm = lambda r: float(np.sqrt(r.double().sum().item() / (N * 45)))
     l = losses.float().cpu().numpy()
     return {
+        "candidates": m, "fallback_precision": fallback, "calibrated_rmse_ratio": cal_tau,
         "train_pairs": n_train, "train_epochs": epochs, "train_s": train_s,
         "train_loss_first_last": [float(l[:20].mean()), float(l[-20:].mean())],
         "tau": tau, "fallback_rate": int(nfb.item()) / N,
         "learned_bf16_gaussians_per_s": N / (ms_l * 1e-3),
         "plain_fp32_gaussians_per_s": N / (ms_plain * 1e-3),
-        "plain_bf16_gaussians_per_s": N / (ms_b * 1e-3),
-        "rmse_learned": rm(rl), "rmse_plain_fp32": rm(rp), "rmse_plain_bf16": rm(rb),
+        "plain_bf16_top4_gaussians_per_s": N / (ms_b * 1e-3),
+        "plain_bf16_qw_gaussians_per_s": N / (ms_bq * 1e-3),
+        "rmse_learned": rm(rl), "rmse_plain_fp32": rm(rp), "rmse_plain_bf16_top4": rm(rb),
+        "rmse_plain_bf16_qw": rm(rbq),
+        "rmse_ratio_learned_vs_plain_fp32": rm(rl) / rm(rp),
         "speedup_learned_vs_plain_fp32": ms_plain / ms_l,
+        "ms": {"plain_fp32": ms_plain, "learned": ms_l, "propose": ms_prop, "restricted": ms_rest},
     }
 
 
 def multi_scenes(scale=1.0, n_scenes=13):
     """Config-5 scenes: K = (512, 1024, 2048)[i % 3], s = (4, 8, 16)[(i // 3) % 3],
     hidden dictionary of K atoms with seed 1000 + i, N log-uniform in
-    [0.5M, 6M] (drawn with seed 0), times `scale`."""
+    [0.5M, 6M] (drawn with seed 0), times `scale`.  Signals are drawn on the
+    device (seed 2000 + i); means and cameras on the host."""
     import numpy as np
     from paper_2605_30396_gb300 import synth
     rng = np.random.default_rng(0)
@@ -274,32 +353,31 @@ def multi_scenes(scale=1.0, n_scenes=13):
         s = (4, 8, 16)[(i // 3) % 3]
         N = max(1, int(round(ns[i] * scale)))
         Dh = synth.hidden_dictionary(K, 1000 + i)
-        X = synth.signals(N, Dh, s, 2000 + i)
+        X = synth.signals_device(N, Dh, s, 2000 + i)
         init = synth.init_atom_indices(N, K, 3000 + i)
         cam, mu = synth.camera_and_means(N, 4000 + i, 5000 + i)
         out.append({"K": K, "s": s, "N": N, "X": X, "init": init, "cam": cam, "mu": mu})
     return out
 
 
-def run_multi(a):
+def multi_leg(scale=1.0, steps=5, warmup=3):
     """13 scenes encoded by one graph-captured dlsh_encode_multi call (each
     scene's (K, s) autotuned on a sample first), then decoded from one camera
-    per scene.  A step = the graph replay plus the decodes."""
+    per scene.  A step = the graph replay plus the decodes.  Returns the timing,
+    the per-scene RMSE and the launch count of one step."""
     import torch
 
     from paper_2605_30396_gb300 import _lib, api
-    torch.cuda.set_device(0)
     L = _lib.lib()
-    sc = multi_scenes(a.multi_scale)
+    sc = multi_scenes(scale)
     scenes, decs = [], []
     tuned = {}
     for x in sc:
-        X = torch.from_numpy(x["X"]).cuda()
-        D = api.init_dictionary(X, x["init"])
+        D = api.init_dictionary(x["X"], x["init"])
         key = (x["K"], x["s"])
         if key not in tuned:
-            tuned[key] = api.autotune_encode(D, X[:65536], x["s"])
-        scenes.append({"D": D, "X": X, "s": x["s"]})
+            tuned[key] = api.autotune_encode(D, x["X"][:65536], x["s"])
+        scenes.append({"D": D, "X": x["X"], "s": x["s"]})
         decs.append((torch.from_numpy(x["mu"]).cuda(), x["cam"]))
     total = sum(x["N"] for x in sc)
     st = torch.cuda.Stream()
@@ -316,37 +394,119 @@ def run_multi(a):
         for o, (mu, cam), sc_, rgb in zip(outs, decs, scenes, rgbs):
             api.decode(sc_["D"], o[0], o[1], o[2], means=mu, cam=cam, out=rgb)
 
-    for _ in range(a.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    clocks = Clocks(0)
-    clocks.start()
     launches0 = L.dlsh_kernel_launches()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(a.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rm = [float((o[3].double().sum() / (x["N"] * 45)).sqrt().item()) for o, x in zip(outs, sc)]
+    return {"total_N": total, "ms_per_step": ms, "gaussians_per_s": total / (ms * 1e-3),
+            "scenes": [[x["N"], x["K"], x["s"]] for x in sc], "rmse_per_scene": rm,
+            "tuned_bn": {f"{k[0]},{k[1]}": v for k, v in tuned.items()},
+            "decode_launches_per_step": (L.dlsh_kernel_launches() - launches0) // max(steps, 1)}
+
+
+def run_multi(a):
+    """`--workload multi`: the multi-scene step alone, as its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    clocks = Clocks(0)
+    clocks.start()
+    r = multi_leg(a.multi_scale, a.steps, a.warmup)
     cl = clocks.stop()
-    ms = e0.elapsed_time(e1) / a.steps
-    rm = []
-    for o, x in zip(outs, sc):
-        rm.append(float((o[3].double().sum() / (x["N"] * 45)).sqrt().item()))
     print(json.dumps({
-        "metric": METRIC, "value": total / (ms * 1e-3), "unit": "Gaussians/s", "n_gpus": 1,
-        "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "metric": METRIC, "value": r["gaussians_per_s"], "unit": "Gaussians/s", "n_gpus": 1,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "multi-scene: 13 scenes, N log-uniform in [0.5M, 6M] x %g, "
                                "K in {512,1024,2048}, s in {4,8,16}; step = one graph replay of "
                                "the multi-scene encode + a decode per scene" % a.multi_scale,
-                   "total_N": total, "scenes": [[x["N"], x["K"], x["s"]] for x in sc],
-                   "tuned_bn": {f"{k[0]},{k[1]}": v for k, v in tuned.items()}},
-        "gpu_launches_untimed_graph": L.dlsh_kernel_launches() - launches0,
-        "clocks": cl, "detail": {"rmse_per_scene": rm},
+                   "total_N": r["total_N"], "scenes": r["scenes"], "tuned_bn": r["tuned_bn"]},
+        "clocks": cl, "detail": {"rmse_per_scene": r["rmse_per_scene"]},
     }))
+
+
+def config2_leg(api, synth, N, K, Dh, init, seed=1):
+    """The scene workload at s = 4, 8, 16: the 15-iteration learning loop
+    (alternating OMP and MOD, graph-captured; Sec. 2.1, Eq. 1) timed once, then
+    one encode pass at FP32 and BF16 (top 4) with the learned dictionary."""
+    import torch
+    st = torch.cuda.current_stream()
+    out = {}
+    for s in (4, 8, 16):
+        X = synth.signals_device(N, Dh, s, seed)
+        api.learn_dictionary(X, K, s, 1, init, sync=True)  # workspace and graph warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        D, _, _, _, rmse = api.learn_dictionary(X, K, s, 15, init)
+        e1.record(st)
+        torch.cuda.synchronize()
+        row = {"learn_15_iters_ms": e0.elapsed_time(e1),
+               "rmse_first_last": [float(rmse[0]), float(rmse[-1])]}
+        for prec in ("fp32", "bf16"):
+            api.encode(D, X, s, precision=prec, sync=True)
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(st)
+            for _ in range(3):
+                api.encode(D, X, s, precision=prec)
+            f1.record(st)
+            torch.cuda.synchronize()
+            ms = f0.elapsed_time(f1) / 3
+            row[f"encode_{prec}_ms"] = ms
+            row[f"encode_{prec}_gaussians_per_s"] = N / (ms * 1e-3)
+        out[f"s{s}"] = row
+        del X
+    return out
+
+
+def precision_leg(api, synth, Dsc, Xsc, s):
+    """Config 3: the correlation precisions on config 1 (N = 10,000, d = 45,
+    hidden K = 256, s = 8, dictionary learned for 10 iterations) and on the
+    scene workload.  Per precision: Gaussians/s, the RMSE of its codes
+    (reconstructed in FP64), and the agreement of its supports with the
+    3xTF32 ("plain FP32") codes.  The comparison with the FP64 oracle is in the
+    cpu_baseline entry (same sample, same initial dictionary)."""
+    import numpy as np
+    import torch
+    st = torch.cuda.current_stream()
+    K1, s1, N1 = 256, 8, 10_000
+    Dh1 = synth.hidden_dictionary(K1, 0)
+    X1 = torch.from_numpy(synth.signals(N1, Dh1, s1, 0)).cuda()
+    init1 = synth.init_atom_indices(N1, K1, 0)
+    D1, _, _, _, _ = api.learn_dictionary(X1, K1, s1, 10, init1, sync=True)
+    out = {}
+    for name, D, X, ss, reps in (("config1_N10k_K256", D1, X1, s1, 20),
+                                 ("scene_N%d_K%d" % (Xsc.shape[0], Dsc.shape[0]), Dsc, Xsc, s, 3)):
+        N = X.shape[0]
+        ref = api.encode(D, X, ss, precision="fp32", sync=True)
+        ri = api.idx_as_long(ref[0])
+        rows = {}
+        for prec in ("fp32", "bf16", "fp8", "bf16_qw", "fp8_qw"):
+            codes = api.encode(D, X, ss, precision=prec, sync=True)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                api.encode(D, X, ss, precision=prec, out=codes)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            gi = api.idx_as_long(codes[0])
+            rows[prec] = {"ms": ms, "gaussians_per_s": N / (ms * 1e-3),
+                          "rmse_fp64": exact_rmse(D, X, *codes[:3]),
+                          "supports_identical_to_fp32": float((gi == ri).all(dim=1).double().mean())}
+        out[name] = rows
+    return out
 
 
 def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
@@ -589,21 +749,110 @@ def splat_leg(a):
 
 
 def run_reference(a):
+    """`--impl reference`: the FP64 oracle step (OMP + MOD update + decode) on a
+    bounded sample of the same workload, on this host's cores (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    X, init, cam, mu = workload(min(a.N, 400_000), a.K, a.s)
-    cb = cpu_oracle_rate(X, init, a.K, a.s, budget_s=max(5.0, 60.0 / max(1, a.steps + a.warmup)))
+    import numpy as np
+    from paper_2605_30396_gb300 import synth
+    n_max = min(a.N, 400_000)
+    Dh = synth.hidden_dictionary(a.K, 0, rho=0.6)
+    X = synth.signals(n_max, Dh, a.s, 1)
+    init = synth.init_atom_indices(n_max, a.K, 0)
+    cam, mu = synth.camera_and_means(n_max, 2, 3)
+    cb, _ = cpu_oracle_step(X, init, mu, cam, a.K, a.s,
+                            budget_s=max(5.0, 60.0 / max(1, a.steps + a.warmup)))
     v = cb["value"]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "Gaussians/s",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": a.N / v * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"scene N={a.N} d=45 K={a.K} s={a.s} (oracle on a sample)"},
+        "config": {"workload": f"scene N={a.N} d=45 K={a.K} s={a.s}; step = OMP encode + MOD "
+                               f"update + decode (the oracle on a sample, rate scaled to the step)"},
         "cpu_baseline": cb,
         "e2e": {"value": v, "unit": "Gaussians/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def e2e_leg(api, X, MU, Dcur, cam, s, out, rgb, precision, steps):
+    """The step end to end through the public API, one step per repetition: the
+    step's inputs (signals, means, dictionary) go host -> device from pinned
+    memory and its results (codes, residuals, the new dictionary, the decoded
+    colours) come back to pinned host memory.  The copies run on a second
+    stream: the signals go in chunks, each chunk encoded as soon as it has
+    landed, and the codes go back while the MOD update and the decode run.
+    Events on the copy stream give the achieved copy bandwidths."""
+    import torch
+    idx, coef, nnz, resid = out
+    N = X.shape[0]
+    stream = torch.cuda.current_stream()
+    Xh = X.cpu().pin_memory()
+    MUh = MU.cpu().pin_memory()
+    Dh = Dcur.cpu().pin_memory()
+    oh = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (idx, coef, nnz, resid, rgb)]
+    Dnh = torch.empty(Dh.shape, dtype=Dh.dtype).pin_memory()
+    Xd = torch.empty_like(X)
+    MUd = torch.empty_like(MU)
+    Dd = torch.empty_like(Dcur)
+    copy = torch.cuda.Stream()
+    # chunk edges on whole waves of the encoder (one 128-signal tile per SM),
+    # the first chunk small so that the encode starts early
+    wave = 128 * torch.cuda.get_device_properties(0).multi_processor_count
+    if N >= 40 * wave:
+        first = 8 * wave
+        rest = (N - first) // (3 * wave) * wave
+        bnd = [0, first, first + rest, first + 2 * rest, N]
+    else:
+        bnd = [0, N]
+    nch = len(bnd) - 1
+    reps = max(1, min(3, steps))
+    h2d_ms, d2h_ms = [], []
+    for rep in range(reps + 1):  # the first repetition is an untimed warm-up
+        if rep == 1:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        landed = []
+        with torch.cuda.stream(copy):
+            ev[0].record(copy)
+            Dd.copy_(Dh, non_blocking=True)
+            for c in range(nch):
+                Xd[bnd[c]:bnd[c + 1]].copy_(Xh[bnd[c]:bnd[c + 1]], non_blocking=True)
+                landed.append(copy.record_event())
+            MUd.copy_(MUh, non_blocking=True)
+            ev[1].record(copy)
+            mu_in = copy.record_event()
+        for c in range(nch):
+            stream.wait_event(landed[c])
+            sl = slice(bnd[c], bnd[c + 1])
+            api.encode(Dd, Xd[sl], s, precision=precision,
+                       out=(idx[sl], coef[sl], nnz[sl], resid[sl]))
+        coded = stream.record_event()
+        with torch.cuda.stream(copy):
+            copy.wait_event(coded)
+            ev[2].record(copy)
+            for h, d in zip(oh[:4], (idx, coef, nnz, resid)):
+                h.copy_(d, non_blocking=True)
+            ev[3].record(copy)
+        Dn = api.mod_update(Xd, Dd, idx, coef, nnz, resid)
+        stream.wait_event(mu_in)
+        api.decode(Dn, idx, coef, nnz, means=MUd, cam=cam, out=rgb)
+        oh[4].copy_(rgb, non_blocking=True)
+        Dnh.copy_(Dn, non_blocking=True)
+        torch.cuda.synchronize()
+        if rep >= 1:
+            h2d_ms.append(ev[0].elapsed_time(ev[1]))
+            d2h_ms.append(ev[2].elapsed_time(ev[3]))
+    dt = (time.perf_counter() - t0) / reps
+    h2d = Xh.numel() * 4 + MUh.numel() * 4 + Dh.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in (idx, coef, nnz, resid, rgb)) + Dh.numel() * 4
+    codes_b = sum(t.numel() * t.element_size() for t in (idx, coef, nnz, resid))
+    return {"value": N / dt, "unit": "Gaussians/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "signal_chunks": nch, "host_ms_per_step": dt * 1e3,
+            "h2d_GBps": (Xh.numel() + MUh.numel() + Dh.numel()) * 4 / (statistics.mean(h2d_ms) * 1e-3) / 1e9,
+            "d2h_codes_GBps": codes_b / (statistics.mean(d2h_ms) * 1e-3) / 1e9}
 
 
 def main():
@@ -630,8 +879,12 @@ def main():
         torch.cuda.set_device(0)
     L = _lib.lib()
     N, K, s = a.N, a.K, a.s
-    X_np, init, cam, mu = workload(N, K, s, seed_offset=100 * rank)
-    X = torch.from_numpy(X_np).cuda()
+    off = 100 * rank
+    # scene workload (config 2): hidden K-atom dictionary (rho = 0.6), s-sparse
+    # signals drawn on the device, initial dictionary from K signals, camera on
+    # a radius-4 sphere, means in [-1, 1]^3
+    Dh = synth.hidden_dictionary(K, 0 + off, rho=0.6)
+    X, init, cam, mu = workload(N, K, s, seed_offset=off)
     MU = torch.from_numpy(mu).cuda()
     D = api.init_dictionary(X, init)
     idx = torch.empty((N, s), dtype=torch.int16, device="cuda")
@@ -648,6 +901,9 @@ def main():
         return tolerance_leg(a, api, X)
     if a.leg == "ksvd":
         return ksvd_leg(a, api, X, init)
+    if a.leg == "precision":
+        print(json.dumps({"leg": "precision", **precision_leg(api, synth, D, X, s)}))
+        return
     if a.leg != "step":
         return run_leg(a, api, L, X, MU, cam, D, out, rgb, stream)
 
@@ -694,93 +950,57 @@ def main():
     dec_ms = statistics.mean(x.elapsed_time(y) for x, y in ev["dec"])
     rmse = float(np.sqrt(resid.double().sum().item() / (N * 45)))
 
-    # roofline of the dominant kernel (encode: correlation GEMM on the tensor pipe)
+    # roofline of the dominant kernel (encode: correlation GEMM on the tensor pipe);
+    # the kernel is timed per launch inside a 23 ms step, so the burst peak applies
     peaks, src = load_peaks()
-    bf16 = float(peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]))
+    bf16 = float(peaks["bf16_tflops"])
     if a.precision == "fp32":
         peak = bf16 * TF32_PER_BF16 / 3.0
-        peak_note = "TF32 dense (bf16 sustained x 1.1/2.25) / 3 for the 3xTF32 split"
-    elif a.precision == "bf16":
-        peak, peak_note = bf16, "bf16 dense sustained"
+        peak_note = "TF32 dense (bf16 burst x 1.1/2.25) / 3 for the 3xTF32 split"
+    elif a.precision in ("bf16", "bf16_qw"):
+        peak, peak_note = bf16, "bf16 dense burst"
     else:
-        peak, peak_note = bf16 * 2.0, "fp8 dense (bf16 sustained x 2)"
+        peak, peak_note = bf16 * 2.0, "fp8 dense (bf16 burst x 2)"
     flops = 2.0 * K * 45 * s * N  # algorithmic correlation FLOPs of one encode pass
     achieved = flops / (enc_ms * 1e-3) / 1e12
     dec_bytes = N * (12 + 6 * s + 1 + 12)  # means, idx+coef, nnz, rgb
     dec_gbs = dec_bytes / (dec_ms * 1e-3) / 1e9
+    # the decode's on-chip roof: each nonzero reads its atom from the FP32 table in
+    # shared memory, about 1.75 wavefronts of 128 B, one wavefront per SM clock
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    clk = (cl.get("sm_mhz") or 2070.0) * 1e6
+    dec_roof_ms = N * s * 1.75 / (sms * clk) * 1e3
 
-    # End to end through the public API, one step per repetition.  The step's
-    # inputs (signals, means, dictionary) go host -> device from pinned memory
-    # and its results (codes, residuals, the new dictionary, the decoded
-    # colours) come back to pinned host memory.  The copies run on a second
-    # stream: the signals go in chunks, each chunk encoded as soon as it has
-    # landed, and the codes go back while the MOD update and the decode run.
-    e2e = None
-    if not a.no_e2e:
-        Xh = torch.from_numpy(X_np).pin_memory()
-        MUh = MU.cpu().pin_memory()
-        Dh = Dcur.cpu().pin_memory()
-        oh = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in (idx, coef, nnz, resid, rgb)]
-        Dnh = torch.empty(Dh.shape, dtype=Dh.dtype).pin_memory()
-        Xd = torch.empty_like(X)
-        MUd = torch.empty_like(MU)
-        Dd = torch.empty_like(Dcur)
-        copy = torch.cuda.Stream()
-        # chunk edges on whole waves of the encoder (one 128-signal tile per
-        # SM), the first chunk small so that the encode starts early
-        wave = 128 * torch.cuda.get_device_properties(0).multi_processor_count
-        if N >= 40 * wave:
-            first = 8 * wave
-            rest = (N - first) // (3 * wave) * wave
-            bnd = [0, first, first + rest, first + 2 * rest, N]
-        else:
-            bnd = [0, N]
-        nch = len(bnd) - 1
-        reps = max(1, min(3, a.steps))
-        for rep in range(reps + 1):  # the first repetition is an untimed warm-up
-            if rep == 1:
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-            landed = []
-            with torch.cuda.stream(copy):
-                Dd.copy_(Dh, non_blocking=True)
-                for c in range(nch):
-                    Xd[bnd[c]:bnd[c + 1]].copy_(Xh[bnd[c]:bnd[c + 1]], non_blocking=True)
-                    landed.append(copy.record_event())
-                MUd.copy_(MUh, non_blocking=True)
-                mu_in = copy.record_event()
-            for c in range(nch):
-                stream.wait_event(landed[c])
-                sl = slice(bnd[c], bnd[c + 1])
-                api.encode(Dd, Xd[sl], s, precision=a.precision,
-                           out=(idx[sl], coef[sl], nnz[sl], resid[sl]))
-            coded = stream.record_event()
-            with torch.cuda.stream(copy):
-                copy.wait_event(coded)
-                for h, d in zip(oh[:4], (idx, coef, nnz, resid)):
-                    h.copy_(d, non_blocking=True)
-            Dn = api.mod_update(Xd, Dd, idx, coef, nnz, resid)
-            stream.wait_event(mu_in)
-            api.decode(Dn, idx, coef, nnz, means=MUd, cam=cam, out=rgb)
-            oh[4].copy_(rgb, non_blocking=True)
-            Dnh.copy_(Dn, non_blocking=True)
-            torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / reps
-        h2d = X_np.nbytes + mu.nbytes + Dh.numel() * 4
-        d2h = sum(t.numel() * t.element_size() for t in (idx, coef, nnz, resid, rgb)) + Dh.numel() * 4
-        e2e = {"value": N / dt, "unit": "Gaussians/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "signal_chunks": nch}
+    e2e = None if a.no_e2e else e2e_leg(api, X, MU, Dcur, cam, s, out, rgb, a.precision, a.steps)
 
     learned = None
     if not a.no_learned:
-        learned = learned_leg(api, synth, Dcur, X, s, K)
+        learned = learned_leg(api, synth, Dcur, X, s, K, Dh)
         learned["workload"] = ("MLP 45-256-256-%d trained on 2M fresh (signal, OMP support) pairs; "
-                               "learned proposal (2s candidates) + restricted OMP + BF16 plain-OMP "
-                               "fallback on the %d scene signals" % (K, N))
+                               "learned proposal (%d candidates) + restricted OMP + %s plain-OMP "
+                               "fallback on the %d scene signals" % (K, learned["candidates"],
+                                                                     learned["fallback_precision"], N))
+    extra = {}
+    if not a.no_extra:
+        extra["config2"] = config2_leg(api, synth, N, K, Dh, init)
+        extra["precision"] = precision_leg(api, synth, Dcur, X, s)
+        extra["multi"] = multi_leg(1.0, steps=3, warmup=2)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
-        cpu = cpu_oracle_rate(X_np, init, K, s)
+        n_max = min(N, 400_000)
+        Xs = X[:n_max].cpu().numpy()
+        init_s = synth.init_atom_indices(n_max, K, 0 + off)
+        cpu, ocodes = cpu_oracle_step(Xs, init_s, mu, cam, K, s)
+        cpu["precision_vs_oracle"] = oracle_agreement(api, X[:n_max], ocodes, s)
+    omp = None
+    if learned is not None:
+        omp = {"N": N, "K": K, "s": s, "unit": "Gaussians/s",
+               "plain_fp32": learned["plain_fp32_gaussians_per_s"],
+               "learned_bf16": learned["learned_bf16_gaussians_per_s"],
+               "learned_over_plain": learned["speedup_learned_vs_plain_fp32"],
+               "rmse_ratio_learned_over_plain": learned["rmse_ratio_learned_vs_plain_fp32"],
+               "equal_rmse_bound": 1.01, "fallback_rate": learned["fallback_rate"]}
     line = {
         "metric": METRIC, "value": value, "unit": "Gaussians/s", "n_gpus": world,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -789,19 +1009,24 @@ def main():
                                f"K={K} atoms, s={s}; step = OMP encode ({a.precision}) + MOD "
                                f"update + decode from a random camera",
                    "N": N, "K": K, "s": s, "precision": a.precision,
-                   "l2": "inputs larger than L2 (X = %.0f MB)" % (X_np.nbytes / 1e6),
+                   "l2": "inputs larger than L2 (X = %.0f MB)" % (N * 45 * 4 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "omp": omp,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": (ENCODE_TRAFFIC[(K, s, a.precision)] * N
                                  if (K, s, a.precision) in ENCODE_TRAFFIC else None),
                      "kernel": "encode_kernel (prep+gram included in the timing)",
                      "peak_source": f"{src}: {peak_note}"},
+        "decode_roofline": {"bound": "shared-memory wavefronts", "achieved": dec_gbs, "unit": "GB/s",
+                            "hbm_peak": float(peaks["hbm_gbs"]),
+                            "hbm_frac": dec_gbs / float(peaks["hbm_gbs"]), "ms": dec_ms,
+                            "onchip_roof_ms": dec_roof_ms, "onchip_frac": dec_roof_ms / dec_ms},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": cl,
         "detail": {"encode_ms": enc_ms, "encode_gaussians_per_s": N / (enc_ms * 1e-3),
                    "mod_ms": mod_ms, "decode_ms": dec_ms, "decode_GBps": dec_gbs,
                    "decode_hbm_frac": dec_gbs / float(peaks["hbm_gbs"]), "rmse": rmse,
-                   "learned": learned},
+                   "learned": learned, **extra},
     }
     if rank == 0:
         print(json.dumps(line))

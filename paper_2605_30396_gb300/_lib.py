@@ -79,8 +79,8 @@ SIGNATURES = {
     "dlsh_mlp_propose": (c_int, [P, c_int, P, c_int64, c_int, P, P, c_size_t, P, c_int]),
     "dlsh_encode_restricted": (c_int, [P, c_int, c_int, P, c_int64, P, c_int, c_int, c_float, P, P,
                                        P, P, P, c_size_t, P, c_int]),
-    "dlsh_encode_learned_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64]),
-    "dlsh_encode_learned": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, P, c_int, c_float,
+    "dlsh_encode_learned_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int64, c_int]),
+    "dlsh_encode_learned": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, P, c_int, c_int, c_float,
                                     c_int, P, P, P, P, P, P, c_size_t, P, c_int]),
     "dlsh_calibrate_fallback": (c_int, [P, P, c_int64, c_float, P, P]),
     "dlsh_encode_multi_workspace_size": (c_size_t, [P, c_int, c_int, c_int]),

@@ -346,8 +346,8 @@ struct Ws {
   long long* total;   // 1
   unsigned long long* nfb;
 };
-inline size_t carve(void* base, int K, int s, long long N, Ws& w) {
-  const long long m = 2 * s;
+inline size_t carve(void* base, int K, int s, long long N, int mc, Ws& w) {
+  const long long m = mc;
   Carver c(base);
   w.status = c.take<uint32_t>(64);
   w.enc = c.take<uint8_t>(encode_ws_bytes(K, s, 0));
@@ -419,26 +419,37 @@ int dlsh_encode_restricted(const float* D, int K, int d, const float* X, int64_t
   return finish(st, status, flags, "dlsh_encode_restricted");
 }
 
-size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N) {
+// The candidate count: m = 0 means 2s; otherwise 2, 4, 8, 16 or 32 with s <= m.
+static int learned_m(int s, int m) {
+  if (m == 0) m = 2 * s;
+  if (m < s || m > 32 || (m & (m - 1)) != 0 || m < 2) return 0;
+  return m;
+}
+
+size_t dlsh_encode_learned_workspace_size(int K, int d, int s, int64_t N, int m) {
   if (d != DLSH_D || K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || N < 0) return 0;
-  if (dlsh::encode_ws_bytes(K, s, 0) == 0) return 0;
+  if (dlsh::encode_ws_bytes(K, s, 0) == 0 || learned_m(s, m) == 0) return 0;
   dlsh::lrn::Ws w;
-  return dlsh::lrn::carve(nullptr, K, s, N, w);
+  return dlsh::lrn::carve(nullptr, K, s, N, learned_m(s, m), w);
 }
 
 int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N, int s, float eps,
-                        const void* mlp, int mode, float tau, int fallback_precision,
+                        const void* mlp, int m_req, int mode, float tau, int fallback_precision,
                         uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq,
                         unsigned long long* n_fallback, void* ws, size_t ws_bytes, void* stream,
                         int flags) {
   using namespace dlsh;
   using namespace dlsh::lrn;
   clear_error();
-  const size_t need = dlsh_encode_learned_workspace_size(K, d, s, N);
+  const int m = learned_m(s, m_req);
+  if (m == 0)
+    return set_error(DLSH_ERR_UNSUPPORTED,
+                     "dlsh_encode_learned: m = %d with s = %d (need 2s <= 32 for m = 0, else m in "
+                     "{2, 4, 8, 16, 32}, m >= s)", m_req, s);
+  const size_t need = dlsh_encode_learned_workspace_size(K, d, s, N, m);
   if (need == 0 || !mlp || !D) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: bad sizes");
-  if (2 * s > 32) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_learned: 2s must be <= 32");
   if (mode != 0 && mode != 1) return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: mode 0 or 1");
-  if (fallback_precision < 0 || fallback_precision > 2)
+  if (fallback_precision < 0 || fallback_precision > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: unknown fallback precision");
   if (N > 0 && (!X || !idx || !coef || !nnz || !resid_sq || !n_fallback))
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_learned: NULL array");
@@ -447,10 +458,9 @@ int dlsh_encode_learned(const float* D, int K, int d, const float* X, int64_t N,
   int rc = check_workspace(ws, ws_bytes, need, "dlsh_encode_learned");
   if (rc) return rc;
   Ws w;
-  carve(ws, K, s, N, w);
+  carve(ws, K, s, N, m, w);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   DLSH_CUDA_TRY(cudaMemsetAsync(w.nfb, 0, sizeof(unsigned long long), st), "dlsh_encode_learned: reset");
-  const int m = 2 * s;
   const float* D32p = nullptr;
   const float* G = nullptr;
   uint32_t* status = nullptr;

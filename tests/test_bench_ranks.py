@@ -20,7 +20,7 @@ def _rank(rank, world, port, out):
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
     ms, value = bench.aggregate_ranks(10.0 + 5.0 * rank, 1000 * (rank + 1), world, device="cpu")
-    X, _, _, _ = bench.workload(64, 16, 2, seed_offset=100 * rank)
+    X, _, _, _ = bench.workload(64, 16, 2, seed_offset=100 * rank, device="cpu")
     out[rank] = (ms, value, float(np.asarray(X)[0, 0]))
     dist.barrier()
     dist.destroy_process_group()
