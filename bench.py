@@ -56,7 +56,7 @@ def parse():
                     help="scale of the multi-scene Gaussian counts (1.0 = 0.5M..6M per scene)")
     ap.add_argument("--leg", default="step",
                     choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
-                             "tolerance", "splat", "ksvd", "precision"],
+                             "tolerance", "splat", "ksvd", "precision", "restricted"],
                     help="time the whole step (default) or one leg alone, for profiling")
     return ap.parse_args()
 
@@ -526,6 +526,14 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     elif a.leg == "mod":
         api.encode(D, X, s, precision=a.precision, out=out, sync=True)
         fn = lambda: api.mod_update(X, D, idx, coef, nnz, resid)
+    elif a.leg == "restricted":
+        # OMP restricted to 2s candidates per signal (the learned encoder's second
+        # step), candidates from a random-init proposal network
+        from paper_2605_30396_gb300 import synth
+        net = api.MLP(K, synth.mlp_params(K, 7))
+        cand = net.propose(X, 2 * s)
+        torch.cuda.synchronize()
+        fn = lambda: api.encode_restricted(D, X, cand, s, sync=False)
     elif a.leg in ("propose", "train"):
         # the proposal network at the learned encoder's sizes (2s candidates,
         # batches of 8192 training pairs), random-init weights

@@ -111,7 +111,13 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
  * OMP iterations counted.  From the MMA-issuing thread: waiting for the A
  * operand (the residual), for a dictionary chunk to land, and for a TMEM
  * buffer to be released.  From the TMA-producing thread: waiting for a free
- * ring stage.
+ * ring stage.  The call runs the kernel dlsh_encode would run, except that
+ * BF16/FP8 use the one-tile kernel; with FP32 and s <= 8 that is the kernel
+ * serving two tiles in turn, whose counters are: selection waiting for the
+ * tensor cores, selection (including that wait), solver, solver waiting for
+ * the staging area, tile iterations, 0, then from the MMA thread: waiting for
+ * a residual, for a dictionary chunk, for an accumulator buffer, and for the
+ * copy of the residual into tensor memory.
  */
 int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
                         int s, float eps, int precision, uint16_t* idx,

@@ -136,8 +136,13 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
                                _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws), ws.numel(), _p(cyc),
                                _stream(), FLAG_SYNC)
     _check(rc, "dlsh_encode_profile")
-    names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations",
-             "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "tma_wait_stage")
+    if s <= 8 and _prec(precision) == 0 and cyc[5].item() == 0:
+        # the FP32 encoder with two tiles served in turn (see dlsh.h)
+        names = ("sel_wait_mma", "selection", "solver", "solver_wait_staging", "tile_iterations",
+                 "unused", "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "mma_wait_copy")
+    else:
+        names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations",
+                 "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "tma_wait_stage")
     return (idx, coef, nnz, resid), dict(zip(names, cyc.cpu().tolist()))
 
 

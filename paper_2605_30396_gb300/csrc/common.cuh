@@ -231,6 +231,26 @@ __device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t a, uint64_t b,
       : "memory");
 }
 
+// MMA with the A operand in tensor memory: A is 128 lanes x K columns of
+// 32-bit TF32 values starting at a_tmem; B comes from shared memory.
+__device__ __forceinline__ void umma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                                 uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Shared memory -> tensor memory: a 128-row x 256-bit matrix (described like a
+// K-major MMA operand, two 16-byte core-matrix columns) into TMEM lanes 0..127,
+// eight 32-bit columns from taddr.  Asynchronous; ordered with the issuing
+// thread's later tcgen05.mma, completion observed through tcgen05.commit.
+__device__ __forceinline__ void tmem_cp_128x256b(uint32_t taddr, uint64_t sdesc) {
+  asm volatile("tcgen05.cp.cta_group::1.128x256b [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+
 // ---- tcgen05: TMEM -> registers ----------------------------------------
 // Warp-collective: lane l of warp w reads TMEM lane (32*(w%4) + l), 32
 // consecutive 32-bit columns starting at the column in `taddr`.  The wait is

@@ -1082,6 +1082,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   }
 }
 
+#include "encode_pair.cuh"
+#include "encode_alt.cuh"
+
 // ---------------------------------------------------------------------------
 // Correlation only: C = R D^T through the same operand packing and MMAs.
 // 128 threads; thread 0 drives TMA and MMA, all threads drain TMEM.
@@ -1217,6 +1220,41 @@ static int launch_encode(const Args& a, int grid, cudaStream_t st) {
   return check_launch("dlsh_encode: launch");
 }
 
+template <int PREC, bool T4>
+static int launch_pair(const PairArgs& a, int grid, cudaStream_t st) {
+  auto fn = encode_pair_kernel<PREC, T4>;
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
+                "dlsh_encode: cudaFuncSetAttribute");
+  fn<<<grid, NTHREADS, a.p.smem, st>>>(a);
+  count_launches(1);
+  return check_launch("dlsh_encode: launch");
+}
+
+static int launch_alt(const AltArgs& a, int grid, cudaStream_t st) {
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(encode_alt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_LIMIT),
+                "dlsh_encode: cudaFuncSetAttribute");
+  encode_alt_kernel<<<grid, NTHREADS, a.p.smem, st>>>(a);
+  count_launches(1);
+  return check_launch("dlsh_encode: launch");
+}
+
+// The workspace fields (padded dictionary, Gram, operand image in 64-atom
+// chunks) of the two-tile kernel, in the single-tile plan's form.
+static void pair_prep_plan(const PairPlan& pp, Plan& p) {
+  p = Plan{};
+  p.prec = pp.prec;
+  p.top4 = pp.top4;
+  p.ib = pp.ib;
+  p.BN = PBN;
+  p.K = pp.K;
+  p.Kp = pp.Kp;
+  p.nchunks = pp.nchunks;
+  p.s = pp.s;
+  p.chunk_bytes = pp.chunk_bytes;
+  p.a_bytes = pp.a_bytes;
+}
+
 template <int PREC, int BN>
 static int launch_correlate(const float* R, int64_t M, const Plan& p, const Ws& w, float* C,
                             int grid, cudaStream_t st) {
@@ -1257,8 +1295,89 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
                    cudaStream_t st, uint32_t** status_out, unsigned long long* prof,
                    const long long* n_dev, int bn) {
   using namespace enc;
+  // kernel variant (s <= 8): 2 = two tiles in flight on two warp groups,
+  // 3 = two tiles served in turn by all warps (FP32); 64 / 128 = one tile with
+  // that atom-chunk width; 0 = the tuned choice, else the default below
+  int choice = bn != 0 ? bn : tuned_bn(K, s, prec);
+  PairPlan pp;
+  AltPlan ap;
+  const bool pair_ok = !prof && make_pair_plan(K, s, prec, pp) == DLSH_OK;
+  const bool alt_ok = make_alt_plan(K, s, prec, ap) == DLSH_OK;
+  // default (measured at N = 3M, K = 1024): BF16/FP8, bound by selection and
+  // solver, on two warp groups (1.2-1.3x faster than one tile); FP32, bound by
+  // its correlations, with all warps alternating between two tiles (1.08x)
+  if (choice == 0) choice = alt_ok ? 3 : (pair_ok && pp.prec != 0 ? 2 : 0);
+  if (choice == 2 && !pair_ok) choice = 0;
+  if (choice == 3 && !alt_ok) choice = 0;
+  if (choice == 3) {
+    Plan p;  // the one-tile encoder's 128-atom FP32 operand image
+    if (make_plan(K, s, prec, p, 128) != DLSH_OK || p.BN != 128)
+      return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d does not fit", K, s);
+    Ws w;
+    carve(ws, p, w);
+    if (status_out) *status_out = w.status;
+    int rc = prepare(D, p, w, true, st);
+    if (rc) return rc;
+    if (N == 0 && !n_dev) return DLSH_OK;
+    AltArgs a{};
+    a.X = X;
+    a.N = N;
+    a.D32p = w.D32p;
+    a.G = w.G;
+    a.img = w.img;
+    a.idx = idx;
+    a.coef = coef;
+    a.nnz = nnz;
+    a.resid_sq = resid_sq;
+    a.eps = eps;
+    a.status = w.status;
+    a.budget = kWaitBudget;
+    a.n_dev = n_dev;
+    a.prof = prof;
+    a.p = ap;
+    const int ntiles = static_cast<int>((N + TILE_M - 1) / TILE_M);
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 1;
+    const int grid = (!n_dev && (ntiles + 1) / 2 < sms) ? ((ntiles + 1) / 2 > 0 ? (ntiles + 1) / 2 : 1) : sms;
+    return launch_alt(a, grid, st);
+  }
+  if (choice == 2) {
+    Plan p;
+    pair_prep_plan(pp, p);
+    Ws w;
+    carve(ws, p, w);
+    if (status_out) *status_out = w.status;
+    int rc = prepare(D, p, w, true, st);
+    if (rc) return rc;
+    if (N == 0 && !n_dev) return DLSH_OK;
+    PairArgs a{};
+    a.X = X;
+    a.N = N;
+    a.D32p = w.D32p;
+    a.G = w.G;
+    a.img = w.img;
+    a.sigma = w.sigma;
+    a.idx = idx;
+    a.coef = coef;
+    a.nnz = nnz;
+    a.resid_sq = resid_sq;
+    a.eps = eps;
+    a.status = w.status;
+    a.budget = kWaitBudget;
+    a.n_dev = n_dev;
+    a.p = pp;
+    const int ntiles = static_cast<int>((N + TILE_M - 1) / TILE_M);
+    int sms = device_sm_count();
+    if (sms <= 0) sms = 1;
+    // two tiles per CTA: enough CTAs for every SM, fewer when the tiles run out
+    // (a count read on the device takes every SM)
+    const int grid = (!n_dev && (ntiles + 1) / 2 < sms) ? ((ntiles + 1) / 2 > 0 ? (ntiles + 1) / 2 : 1) : sms;
+    if (pp.prec == 0) return launch_pair<0, false>(a, grid, st);
+    if (pp.prec == 1) return pp.top4 ? launch_pair<1, true>(a, grid, st) : launch_pair<1, false>(a, grid, st);
+    return pp.top4 ? launch_pair<2, true>(a, grid, st) : launch_pair<2, false>(a, grid, st);
+  }
   Plan p;
-  if (make_plan(K, s, prec, p, bn) != DLSH_OK)
+  if (make_plan(K, s, prec, p, (choice == 2 || choice == 3) ? 0 : choice) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
   Ws w;
@@ -1319,6 +1438,14 @@ size_t encode_ws_bytes(int K, int s, int prec) {
   for (int bn : {64, 128}) {
     enc::Plan p;
     if (enc::make_plan(K, s, prec, p, bn) != DLSH_OK) continue;
+    enc::Ws w;
+    const size_t b = enc::carve(nullptr, p, w);
+    if (b > best) best = b;
+  }
+  enc::PairPlan pp;
+  if (best > 0 && enc::make_pair_plan(K, s, prec, pp) == DLSH_OK) {
+    enc::Plan p;
+    enc::pair_prep_plan(pp, p);
     enc::Ws w;
     const size_t b = enc::carve(nullptr, p, w);
     if (b > best) best = b;
@@ -1493,9 +1620,14 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
   DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
   int best = 0;
   float best_ms = 0.f;
-  for (int bn : {64, 128}) {
+  for (int bn : {64, 128, 2, 3}) {
     Plan p;
-    if (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn) continue;
+    PairPlan pp;
+    AltPlan ap;
+    if (bn == 2 ? make_pair_plan(K, s, precision, pp) != DLSH_OK
+                : bn == 3 ? make_alt_plan(K, s, precision, ap) != DLSH_OK
+                          : (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn))
+      continue;
     // force this width for the trial runs
     record_tuned(K, s, precision, bn);
     uint32_t* status = nullptr;
@@ -1580,8 +1712,8 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
   if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
-  if (bn != 0 && bn != 64 && bn != 128)
-    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 64 or 128");
+  if (bn != 0 && bn != 2 && bn != 3 && bn != 64 && bn != 128)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2, 3, 64 or 128");
   for (int i = 0; i < n; ++i) {
     const dlsh_scene& x = sc[i];
     if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
@@ -1589,7 +1721,7 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
       return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
     Plan p;
-    if (make_plan(x.K, x.s, prec, p, bn) != DLSH_OK)
+    if (make_plan(x.K, x.s, prec, p, (bn == 2 || bn == 3) ? 0 : bn) != DLSH_OK)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
                        i, x.K, x.s);
   }

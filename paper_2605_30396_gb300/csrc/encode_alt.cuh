@@ -1,0 +1,597 @@
+// Batch-OMP, FP32 (3xTF32) correlations, s <= 8: two tiles per CTA served by
+// the same sixteen warps in alternation (Sec. 2.1: OMP against the dictionary,
+// one greedy atom at a time, least-squares re-fit).
+//
+// Included by encode.cu inside namespace dlsh::enc, after encode_pair.cuh
+// (it shares that file's staging protocol and MMA helpers).
+//
+// The warps select for tile A while the tensor pipe computes A's correlations,
+// then solve for A while the tensor pipe already computes tile B's; then they
+// select for B, solve for B (the tensor pipe on A's next iteration), and so on.
+// The one-tile encoder leaves the tensor pipe idle during every solve; here it
+// idles only when the accumulator buffers are full.
+//   warp 17  TMA producer: 128-atom chunks of the packed dictionary (the
+//            one-tile encoder's image), in the MMA warp's order.
+//   warp 16  MMA issuer: jobs (tile A, iteration it), (tile B, it), (A, it+1)..;
+//            once the previous job's MMAs are done, each job copies its staged
+//            residual (TF32 hi, lo) into the tensor-memory A columns, then runs
+//            the 3xTF32 MMAs (M = 128, N = 128) of every chunk.
+//   warps 0-15  selection (four threads per row, a 32-column quarter of each
+//            chunk) and solver (four sub-lanes of 12 dims per signal), as in
+//            the one-tile encoder, on the two tiles in turn.
+// Tensor memory: A (hi then lo) in columns 0..95, three 128-column accumulator
+// buffers in 128..511, used in job order.  N = 64 MMAs measured at about half
+// the throughput of N = 128 ones, so the chunks stay 128 atoms wide.
+
+constexpr int ABN = 128;     // atoms per chunk
+constexpr int ABUF = 3;      // accumulator buffers
+constexpr int AQC = 32;      // chunk columns read by one selection thread
+
+struct AltPlan {
+  int K, Kp, nchunks, stages, s;
+  uint32_t chunk_bytes, a_bytes;
+  uint32_t off_stage, off_L[2], off_sel[2], off_y[2], off_cand, off_bar, off_ring, smem;
+};
+
+struct AltArgs {
+  const float* X;
+  int64_t N;
+  const float* D32p;
+  const float* G;
+  const uint8_t* img;
+  uint16_t* idx;
+  float* coef;
+  uint8_t* nnz;
+  float* resid_sq;
+  float eps;
+  uint32_t* status;
+  long long budget;
+  const long long* n_dev;
+  unsigned long long* prof;  // optional: per-phase SM cycles (10 counters)
+  AltPlan p;
+};
+
+inline int make_alt_plan(int K, int s, int code, AltPlan& p, int smem_limit = SMEM_LIMIT) {
+  int top4 = 0;
+  if (s > 8 || operand_precision(code, &top4) != 0) return DLSH_ERR_UNSUPPORTED;
+  p.K = K;
+  p.s = s;
+  p.nchunks = (K + ABN - 1) / ABN;
+  p.Kp = p.nchunks * ABN;
+  p.a_bytes = TILE_M * op_kb(0) * 16 * op_parts(0);
+  p.chunk_bytes = ABN * op_kb(0) * 16 * op_parts(0);
+  uint32_t off = 0;
+  auto take = [&](uint32_t bytes) {
+    uint32_t o = (off + 1023u) & ~1023u;
+    off = o + bytes;
+    return o;
+  };
+  p.off_stage = take(p.a_bytes);
+  // per tile: the factor (its diagonal holds the reciprocals), the support and
+  // y; the coefficients go to global memory at every step
+  for (int t = 0; t < 2; ++t) {
+    p.off_L[t] = take(36 * TILE_M * 4);
+    p.off_sel[t] = take(8 * TILE_M * 4);
+    p.off_y[t] = take(8 * TILE_M * 4);
+  }
+  p.off_cand = take(TILE_M * 4 * 8);
+  p.off_bar = take(1024);
+  const uint32_t fixed = (off + 1023u) & ~1023u;
+  if (fixed >= static_cast<uint32_t>(smem_limit)) return DLSH_ERR_UNSUPPORTED;
+  int fit = static_cast<int>((smem_limit - fixed) / p.chunk_bytes);
+  if (fit > 32) fit = 32;
+  if (fit < 2) return DLSH_ERR_UNSUPPORTED;
+  p.stages = fit;
+  p.off_ring = fixed;
+  p.smem = fixed + p.stages * p.chunk_bytes;
+  return DLSH_OK;
+}
+
+// One chunk of 3xTF32 MMAs, A (hi, lo) from tensor memory, N = 128.
+__device__ __forceinline__ void issue_alt_chunk(uint32_t tmem_d, uint32_t a_tmem, uint32_t b_addr) {
+  constexpr uint32_t idesc = umma_idesc(2, 2, TILE_M, ABN);
+  constexpr uint32_t B_LBO = ABN * 16, SBO = 128, B_PART = ABN * 12 * 16;
+#pragma unroll
+  for (int pass = 0; pass < 3; ++pass) {
+    const uint32_t ao = pass == 2 ? 48u : 0u;    // lo(r) . hi(D)
+    const uint32_t bo = pass == 1 ? B_PART : 0u;  // hi(r) . lo(D)
+#pragma unroll
+    for (int ks = 0; ks < 6; ++ks) {
+      const uint64_t bd = umma_smem_desc(b_addr + bo + ks * 2 * B_LBO, B_LBO, SBO);
+      umma_tf32_tmem_a(tmem_d, a_tmem + ao + ks * 8, bd, idesc, (pass | ks) != 0);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_constant__ AltArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int SMAX = 8;
+  constexpr uint32_t ACC0 = 128;
+  const AltPlan& p = a.p;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long NS = a.n_dev ? *a.n_dev : a.N;
+  const int ntiles = static_cast<int>((NS + TILE_M - 1) / TILE_M);
+  const int Gd = static_cast<int>(gridDim.x), bidx = static_cast<int>(blockIdx.x);
+  const int s = p.s;
+  // rounds k in which tile slot 0 / slot 1 have a tile (tiles b + (2k + slot) Gd)
+  const int K0 = bidx < ntiles ? (ntiles - bidx + 2 * Gd - 1) / (2 * Gd) : 0;
+  const int K1 = bidx + Gd < ntiles ? (ntiles - bidx - Gd + 2 * Gd - 1) / (2 * Gd) : 0;
+  auto job_index = [&](int t, int k, int it) -> long long {
+    return k < K1 ? 2LL * s * k + 2LL * it + t : 2LL * s * K1 + static_cast<long long>(s) * (k - K1) + it;
+  };
+
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
+  uint64_t* bar_a = bars;            // [2]
+  uint64_t* bar_full = bars + 2;     // [ABUF]
+  uint64_t* bar_empty = bars + 5;    // [ABUF]
+  uint64_t* bar_stage = bars + 8;
+  uint64_t* bar_dfull = bars + 9;    // [stages]
+  uint64_t* bar_dempty = bar_dfull + p.stages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_dempty + p.stages);
+  volatile long long* stage_done = reinterpret_cast<volatile long long*>(smem + p.off_bar + 1000);
+  // optional phase profile, SM cycles: 0 selection waiting for MMAs, 1 selection
+  // (incl. 0), 2 solver, 3 solver waiting for the staging area, 4 tile
+  // iterations (thread 0); 6 MMA warp waiting for a residual, 7 for a
+  // dictionary chunk, 8 for an accumulator buffer, 9 for the copy into TMEM
+  unsigned long long* pcs = reinterpret_cast<unsigned long long*>(smem + p.off_bar + 512);
+  const bool prof_any = a.prof != nullptr;
+
+  if (tid == 0) {
+    mbar_init(&bar_a[0], 1);
+    mbar_init(&bar_a[1], 1);
+    for (int b = 0; b < ABUF; ++b) {
+      mbar_init(&bar_full[b], 1);
+      mbar_init(&bar_empty[b], NEPI / 32);
+    }
+    mbar_init(bar_stage, 1);
+    for (int q = 0; q < p.stages; ++q) {
+      mbar_init(&bar_dfull[q], 1);
+      mbar_init(&bar_dempty[q], 1);
+    }
+    *stage_done = -1;
+    if (prof_any)
+      for (int q = 0; q < 10; ++q) pcs[q] = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) {
+    tmem_alloc(tmem_slot, 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t ring_addr = smem_u32(smem + p.off_ring);
+
+  if (warp == NEPI / 32 + 1) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      long long ring = 0;
+      bool ok = true;
+      for (int k = 0; k < K0 && ok; ++k)
+        for (int it = 0; it < s && ok; ++it)
+          for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t)
+            for (int c = 0; c < p.nchunks; ++c, ++ring) {
+              const int st = static_cast<int>(ring % p.stages);
+              const uint32_t par = static_cast<uint32_t>((ring / p.stages) & 1) ^ 1u;
+              if (!mbar_wait(&bar_dempty[st], par, a.budget)) {
+                flag_status(a.status, ST_TIMEOUT);
+                ok = false;
+                break;
+              }
+              mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
+              bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
+                       a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes, &bar_dfull[st]);
+            }
+      for (long long f = ring > p.stages ? ring - p.stages : 0; ok && f < ring; ++f) {
+        if (!mbar_wait(&bar_dempty[f % p.stages], static_cast<uint32_t>((f / p.stages) & 1), a.budget)) {
+          flag_status(a.status, ST_TIMEOUT);
+          ok = false;
+        }
+      }
+    }
+  } else if (warp == NEPI / 32) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      uint32_t aph[2] = {0u, 0u};
+      long long ring = 0, cc = 0, job = 0;
+      bool ok = true;
+      for (int k = 0; k < K0 && ok; ++k)
+        for (int it = 0; it < s && ok; ++it)
+          for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t, ++job) {
+            const long long W0 = prof_any ? clock64() : 0;
+            if (!mbar_wait(&bar_a[t], aph[t], a.budget)) {
+              flag_status(a.status, ST_TIMEOUT);
+              ok = false;
+              break;
+            }
+            if (prof_any) pcs[6] += clock64() - W0;
+            aph[t] ^= 1u;
+            // the A columns are shared by the jobs: the previous job's last MMAs
+            // (and so all of its MMAs) must have completed before the copy
+            if (cc > 0 && !mbar_wait(&bar_full[(cc - 1) % ABUF],
+                                     static_cast<uint32_t>(((cc - 1) / ABUF) & 1), a.budget)) {
+              flag_status(a.status, ST_TIMEOUT);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t ta = tmem_base;
+            {
+              constexpr uint32_t LBO = TILE_M * 16, SBO = 128, PART = TILE_M * 12 * 16;
+              const uint32_t sa = smem_u32(smem + p.off_stage);
+#pragma unroll
+              for (int part = 0; part < 2; ++part)
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk)
+                  tmem_cp_128x256b(ta + part * 48 + kk * 8,
+                                   umma_smem_desc(sa + part * PART + kk * 2 * LBO, LBO, SBO));
+              tc_commit(bar_stage);
+              const long long W1 = prof_any ? clock64() : 0;
+              if (!mbar_wait(bar_stage, static_cast<uint32_t>(job & 1), a.budget)) {
+                flag_status(a.status, ST_TIMEOUT);
+                ok = false;
+                break;
+              }
+              if (prof_any) pcs[9] += clock64() - W1;
+              *stage_done = job;
+            }
+            for (int c = 0; c < p.nchunks; ++c, ++ring, ++cc) {
+              const int st = static_cast<int>(ring % p.stages);
+              const uint32_t dpar = static_cast<uint32_t>((ring / p.stages) & 1);
+              const int buf = static_cast<int>(cc % ABUF);
+              const uint32_t epar = static_cast<uint32_t>((cc / ABUF) & 1) ^ 1u;
+              const long long W2 = prof_any ? clock64() : 0;
+              const bool okd = mbar_wait(&bar_dfull[st], dpar, a.budget);
+              const long long W3 = prof_any ? clock64() : 0;
+              const bool oke = okd && mbar_wait(&bar_empty[buf], epar, a.budget);
+              if (prof_any) {
+                pcs[7] += W3 - W2;
+                pcs[8] += clock64() - W3;
+              }
+              if (!oke) {
+                flag_status(a.status, ST_TIMEOUT);
+                ok = false;
+                break;
+              }
+              tc_fence_after();
+              issue_alt_chunk(tmem_base + ACC0 + static_cast<uint32_t>(buf) * ABN, ta,
+                              ring_addr + static_cast<uint32_t>(st) * p.chunk_bytes);
+              tc_commit(&bar_full[buf]);
+              tc_commit(&bar_dempty[st]);
+            }
+          }
+    }
+  } else {
+    // ------------------------------------------------ selection + solver, two tiles in turn
+    uint8_t* A = smem + p.off_stage;
+    float* cv = reinterpret_cast<float*>(smem + p.off_cand);  // [128][4]
+    int* cj = reinterpret_cast<int*>(smem + p.off_cand + TILE_M * 4 * 4);
+    const int R1 = 32 * (warp & 3) + lane, q1 = warp >> 2;
+    const int R2 = 8 * warp + (lane >> 2), u = lane & 3;
+    const uint32_t trow = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + ACC0 +
+                          static_cast<uint32_t>(q1 * AQC);
+    const int K = p.K, nchunks = p.nchunks;
+    const float eps2 = a.eps * a.eps;
+    long long cc = 0;
+    bool ok = true;
+    // the staging area may be written for job J once the copy of job J - 1 has
+    // completed (published by the MMA warp)
+    auto wait_staging = [&](long long J) -> bool {
+      const long long t0 = clock64();
+      while (*stage_done < J - 1) {
+        if (clock64() - t0 > a.budget) {
+          flag_status(a.status, ST_TIMEOUT);
+          return false;
+        }
+      }
+      return true;
+    };
+    // sub-lane u's 12 dims of row R2 of tile `tl` into the staging area; the
+    // row's ||x||^2
+    auto stage_x = [&](long long tl) -> float {
+      const int64_t tg0 = tl * TILE_M;
+      const bool tin = R2 < (NS - tg0 < TILE_M ? NS - tg0 : TILE_M);
+      const float* txr = a.X + (tg0 + R2) * DLSH_D + 12 * u;
+      float x[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) x[q] = (tin && 12 * u + q < DLSH_D) ? __ldg(txr + q) : 0.f;
+      float part = 0.f;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) part = fmaf(x[q], x[q], part);
+      write_a_part<0>(A, R2, u, x, 1.f);
+      return quad_sum(part);
+    };
+    auto tile_of = [&](int t, int k) -> long long { return static_cast<long long>(bidx) + (2LL * k + t) * Gd; };
+    // per-tile state of this thread's row (R2) in each slot
+    // (two named copies, so that the loop over the tiles need not be unrolled)
+    float rn2_0 = 0.f, rn2_1 = 0.f, xn_0 = 0.f, xn_1 = 0.f;
+    bool act_0 = false, act_1 = false;
+    int tc_0 = 0, tc_1 = 0;
+    // -------- the first round's signals: slot 0, then (once its copy is done) slot 1
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if ((t == 0 ? K0 : K1) > 0 && ok) {
+        if (!wait_staging(job_index(t, 0, 0))) ok = false;
+        if (ok) {
+          const float v = stage_x(tile_of(t, 0));
+          if (t == 0) rn2_0 = v; else rn2_1 = v;
+        }
+        fence_proxy_async_smem();
+        if (named_bar_or(1, NEPI, !ok)) ok = false;
+        if (ok && tid == 0) mbar_arrive(&bar_a[t]);
+      }
+    }
+    for (int k = 0; k < K0 && ok; ++k) {
+      const bool two = k < K1;
+      {
+        const long long tl0 = tile_of(0, k), tl1 = tile_of(1, k);
+        const int rows0 = static_cast<int>(NS - tl0 * TILE_M < TILE_M ? NS - tl0 * TILE_M : TILE_M);
+        const int rows1 = static_cast<int>(NS - tl1 * TILE_M < TILE_M ? NS - tl1 * TILE_M : TILE_M);
+        xn_0 = sqrtf(rn2_0);
+        xn_1 = sqrtf(rn2_1);
+        act_0 = R2 < rows0;
+        act_1 = two && R2 < rows1;
+        tc_0 = tc_1 = 0;
+      }
+      for (int it = 0; it < s && ok; ++it) {
+#pragma unroll 1
+        for (int t = 0; t < (two ? 2 : 1); ++t) {
+          float rn2c = t ? rn2_1 : rn2_0;
+          const float xnc = t ? xn_1 : xn_0;
+          bool actc = t ? act_1 : act_0;
+          int tcc = t ? tc_1 : tc_0;
+          float* Ls = reinterpret_cast<float*>(smem + p.off_L[t]);
+          int* sel = reinterpret_cast<int*>(smem + p.off_sel[t]);
+          float* ys = reinterpret_cast<float*>(smem + p.off_y[t]);
+#define LS(rr, cc2) Ls[(((rr) * ((rr) + 1)) / 2 + (cc2)) * TILE_M + R2]
+#define IDG(rr) LS(rr, rr)
+          const long long tl = tile_of(t, k);
+          const int64_t g0 = tl * TILE_M;
+          const int rows = static_cast<int>(NS - g0 < TILE_M ? NS - g0 : TILE_M);
+          const bool in_tile = R2 < rows;
+          const float* xr = a.X + (g0 + R2) * DLSH_D + 12 * u;
+          // ================= phase 1: selection over this thread's column quarter
+          const bool prof_on = prof_any && tid == 0;
+          const long long T0 = prof_on ? clock64() : 0;
+          {
+            uint32_t best = 0;
+            int bestc = 0;
+            for (int c = 0; c < nchunks; ++c, ++cc) {
+              const int buf = static_cast<int>(cc % ABUF);
+              const long long W4 = prof_on ? clock64() : 0;
+              if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((cc / ABUF) & 1), a.budget)) {
+                flag_status(a.status, ST_TIMEOUT);
+                ok = false;
+                break;
+              }
+              if (prof_on) pcs[0] += clock64() - W4;
+              tc_fence_after();
+              __syncwarp();
+              uint32_t rr[AQC];
+              tmem_ld32_issue(trow + static_cast<uint32_t>(buf * ABN), rr);
+              tmem_ld32_wait(rr);
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&bar_empty[buf]);
+              uint32_t m0 = 0, m1 = 0;
+#pragma unroll
+              for (int q = 0; q < AQC; q += 2) {
+                m0 = max(m0, (rr[q] & 0x7fffffe0u) | static_cast<uint32_t>(31 - q));
+                m1 = max(m1, (rr[q + 1] & 0x7fffffe0u) | static_cast<uint32_t>(30 - q));
+              }
+              const uint32_t m = max(m0, m1);
+              if ((m & ~31u) > (best & ~31u)) {
+                best = m;
+                bestc = c;
+              }
+            }
+            cv[R1 * 4 + q1] = __uint_as_float(best & ~31u);
+            cj[R1 * 4 + q1] = bestc * ABN + q1 * AQC + 31 - static_cast<int>(best & 31u);
+          }
+          if (named_bar_or(1, NEPI, !ok)) {
+            ok = false;
+            break;
+          }
+          const long long T1 = prof_on ? clock64() : 0;
+          // ================= phase 2: merge, Cholesky, solve, residual
+          const int tt = tcc;
+          bool act = actc;
+          if (act && rn2c <= eps2) act = false;
+          if (act) {
+            float x[12], r[12];
+#pragma unroll
+            for (int q = 0; q < 12; ++q) x[q] = (in_tile && 12 * u + q < DLSH_D) ? __ldg(xr + q) : 0.f;
+            int sl[SMAX];
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) sl[m] = m < tt ? sel[m * TILE_M + R2] : 0;
+            int js = -1;
+            float bestv = -1.f;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float v = cv[R2 * 4 + qq];
+              const int j = cj[R2 * 4 + qq];
+              if (j < K && (v > bestv || (v == bestv && j < js))) {
+                bestv = v;
+                js = j;
+              }
+            }
+            bool dup = false;
+#pragma unroll
+            for (int m = 0; m < SMAX; ++m) dup |= (m < tt && sl[m] == js);
+            if (dup) js = -1;
+            if (js < 0 || !(bestv > CORR_STOP_REL * xnc)) {
+              act = false;
+            } else {
+              const float* Grow = a.G + static_cast<size_t>(js) * K;
+              float gv[SMAX];
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m) gv[m] = m < tt ? __ldg(Grow + sl[m]) : 0.f;
+              const float gjj = __ldg(Grow + js);
+              float4 dj[3];
+              {
+                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+#pragma unroll
+                for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
+              }
+              float w[SMAX];
+              float wn2 = 0.f;
+#pragma unroll
+              for (int m = 0; m < SMAX; ++m) {
+                w[m] = 0.f;
+                if (m < tt) {
+                  float acc = gv[m];
+#pragma unroll
+                  for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
+                  w[m] = acc * IDG(m);
+                  wn2 = fmaf(w[m], w[m], wn2);
+                }
+              }
+              const float ell2 = gjj - wn2;
+              if (!(ell2 > PIVOT_MIN * gjj)) {
+                act = false;
+              } else {
+                const float ell = sqrtf(ell2);
+                const float iell = 1.f / ell;
+#pragma unroll
+                for (int m = 0; m < SMAX; ++m)
+                  if (m < tt) LS(tt, m) = w[m];
+                IDG(tt) = iell;  // the diagonal holds 1 / L(t, t)
+                float bp = 0.f;
+#pragma unroll
+                for (int w4 = 0; w4 < 3; ++w4) {
+                  bp = fmaf(dj[w4].x, x[4 * w4 + 0], bp);
+                  bp = fmaf(dj[w4].y, x[4 * w4 + 1], bp);
+                  bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
+                  bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
+                }
+                float yv[SMAX];
+#pragma unroll
+                for (int m = 0; m < SMAX; ++m) yv[m] = m < tt ? ys[m * TILE_M + R2] : 0.f;
+                float yt = quad_sum(bp);
+#pragma unroll
+                for (int m = 0; m < SMAX; ++m)
+                  if (m < tt) yt = fmaf(-w[m], yv[m], yt);
+                yt *= iell;
+                ys[tt * TILE_M + R2] = yt;
+                sel[tt * TILE_M + R2] = js;
+                const float gt = yt * iell;
+                float gam[SMAX];
+#pragma unroll
+                for (int m = SMAX - 1; m >= 0; --m) {
+                  gam[m] = 0.f;
+                  if (m < tt) {
+                    float acc = yv[m];
+#pragma unroll
+                    for (int q = m + 1; q < SMAX; ++q)
+                      if (q < tt) acc = fmaf(-LS(q, m), gam[q], acc);
+                    acc = fmaf(-w[m], gt, acc);
+                    gam[m] = acc * IDG(m);
+                  }
+                }
+                // the row's coefficients so far (sub-lane u writes slots u, u+4)
+                {
+                  const int64_t gi = g0 + R2;
+#pragma unroll
+                  for (int m = 0; m < SMAX; ++m)
+                    if (m < tt && (m & 3) == u) a.coef[gi * s + m] = gam[m];
+                  if ((tt & 3) == u) a.coef[gi * s + tt] = gt;
+                }
+#pragma unroll
+                for (int q = 0; q < 12; ++q) r[q] = x[q];
+#pragma unroll
+                for (int m = 0; m < SMAX; ++m) {
+                  if (m < tt) {
+                    const float4* da = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
+#pragma unroll
+                    for (int w4 = 0; w4 < 3; ++w4) {
+                      const float4 dv = __ldg(da + w4);
+                      r[4 * w4 + 0] = fmaf(-gam[m], dv.x, r[4 * w4 + 0]);
+                      r[4 * w4 + 1] = fmaf(-gam[m], dv.y, r[4 * w4 + 1]);
+                      r[4 * w4 + 2] = fmaf(-gam[m], dv.z, r[4 * w4 + 2]);
+                      r[4 * w4 + 3] = fmaf(-gam[m], dv.w, r[4 * w4 + 3]);
+                    }
+                  }
+                }
+#pragma unroll
+                for (int w4 = 0; w4 < 3; ++w4) {
+                  r[4 * w4 + 0] = fmaf(-gt, dj[w4].x, r[4 * w4 + 0]);
+                  r[4 * w4 + 1] = fmaf(-gt, dj[w4].y, r[4 * w4 + 1]);
+                  r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
+                  r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
+                }
+                tcc = tt + 1;
+                float pr = 0.f;
+#pragma unroll
+                for (int q = 0; q < 12; ++q) pr = fmaf(r[q], r[q], pr);
+                rn2c = quad_sum(pr);
+                if (it + 1 < s) {
+                  const long long W5 = prof_on ? clock64() : 0;
+                  if (wait_staging(job_index(t, k, it + 1)))
+                    write_a_part<0>(A, R2, u, r, 1.f);
+                  else
+                    ok = false;
+                  if (prof_on) pcs[3] += clock64() - W5;
+                }
+              }
+            }
+          }
+          actc = act;
+          // last iteration: write this slot's codes, then stage its next tile's
+          // signals (the MMA warp needs them right after the other slot's job)
+          if (it + 1 == s) {
+            if (in_tile) {
+              const int64_t gi = g0 + R2;
+              const int tn = tcc;
+              for (int mm = u; mm < s; mm += 4) {
+                a.idx[gi * s + mm] = mm < tn ? static_cast<uint16_t>(sel[mm * TILE_M + R2]) : static_cast<uint16_t>(0);
+                if (mm >= tn) a.coef[gi * s + mm] = 0.f;
+              }
+              if (u == 0) {
+                a.nnz[gi] = static_cast<uint8_t>(tn);
+                if (a.resid_sq) a.resid_sq[gi] = rn2c;
+              }
+            }
+            if (k + 1 < (t == 0 ? K0 : K1) && ok) {
+              if (wait_staging(job_index(t, k + 1, 0)))
+                rn2c = stage_x(tile_of(t, k + 1));
+              else
+                ok = false;
+            }
+          }
+          fence_proxy_async_smem();
+          if (named_bar_or(1, NEPI, !ok)) {
+            ok = false;
+            break;
+          }
+          const bool more = it + 1 < s || k + 1 < (t == 0 ? K0 : K1);
+          if (more && tid == 0) mbar_arrive(&bar_a[t]);
+          if (prof_on) {
+            pcs[1] += T1 - T0;
+            pcs[2] += clock64() - T1;
+            pcs[4] += 1;
+          }
+          if (t == 0) {
+            rn2_0 = rn2c;
+            act_0 = actc;
+            tc_0 = tcc;
+          } else {
+            rn2_1 = rn2c;
+            act_1 = actc;
+            tc_1 = tcc;
+          }
+#undef LS
+#undef IDG
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (prof_any && tid == 0)
+    for (int q = 0; q < 10; ++q) atomicAdd(a.prof + q, pcs[q]);
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+}

@@ -249,3 +249,34 @@ def test_learned_encoder_exact_and_deploy(lib):
     tau2 = np.float32(tau) * np.float32(tau)  # FP32, as the kernel compares
     assert int(nfd.item()) == int((rr32 > tau2).sum())
     assert int(nfd.item()) < len(rr32)
+
+
+def test_trained_network_gains_over_untrained_at_k1024(lib):
+    """The learned proposal at the scene's dictionary size: after training on
+    (signal, OMP support) pairs, the 2s candidates hold far more of OMP's atoms
+    than an untrained network's, and restricted OMP over them comes much closer
+    to plain OMP's residual.  Measured at this size: recall about 0.27 against
+    0.016, residual RMSE about 1.45x plain OMP's against 2.8x."""
+    K, s = 1024, 8
+    D = synth.hidden_dictionary(K, 40, rho=0.6)
+    Dt = torch.from_numpy(D.astype(np.float32)).cuda()
+    Xtr = synth.signals_device(400_000, D, s, 41)
+    itr, _, ntr, _ = lib.encode(Dt, Xtr, s, sync=True)
+    net = lib.MLP(K, synth.mlp_params(K, 42))
+    net.train(Xtr, itr, ntr, epochs=10, batch=8192, lr=1e-2)
+    fresh = lib.MLP(K, synth.mlp_params(K, 43))
+    Xv = synth.signals_device(20_000, D, s, 44)
+    iv, _, nv, rp = lib.encode(Dt, Xv, s, sync=True)
+    sup = lib.idx_as_long(iv)
+    live = torch.arange(s, device="cuda")[None, :] < nv[:, None].to(torch.int64)
+
+    def scores(n):
+        cand = n.propose(Xv, 2 * s)
+        c = cand.to(torch.int64) & 0xFFFF
+        hit = (sup[:, :, None] == c[:, None, :]).any(dim=2) & live
+        _, _, _, rr = lib.encode_restricted(Dt, Xv, cand, s)
+        return float(hit.sum()) / float(live.sum()), float((rr.double().sum() / rp.double().sum()).sqrt())
+
+    (r_tr, q_tr), (r_0, q_0) = scores(net), scores(fresh)
+    assert r_tr > 0.18 and r_tr > r_0 + 0.15, (r_tr, r_0)
+    assert q_tr < 0.75 * q_0, (q_tr, q_0)
