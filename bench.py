@@ -27,11 +27,15 @@ sys.path.insert(0, ROOT)
 METRIC = ("OMP Gaussians/s at K=1024,s=8, learned+BF16 vs plain at equal RMSE; decode GB/s")
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
-# DRAM bytes (read + write) per signal of the encoder, from one ncu capture of
-# encode_kernel at N = 1,000,000, K = 1024, s = 8, FP32 (184.92 MB read +
-# 37.26 MB written); the traffic grows with the number of signals, so a launch
-# over N signals moves N times it.
-ENCODE_TRAFFIC = {(1024, 8, "fp32"): (184.9216e6 + 37.260032e6) / 1_000_000}
+# DRAM bytes (read + write) per signal of the FP32 encoder, from one ncu capture of
+# encode_alt_kernel at N = 1,000,000, K = 1024, s = 8 (185.25 MB read + 36.88 MB
+# written); the traffic grows with the number of signals, so a launch over N
+# signals moves N times it.
+ENCODE_TRAFFIC = {(1024, 8, "fp32"): (185.253376e6 + 36.877824e6) / 1_000_000}
+
+# the encoder variant the default launch picks at K = 1024, s = 8 per precision
+ENCODE_KERNEL = {"fp32": "encode_alt_kernel", "bf16": "encode_pair_kernel", "fp8": "encode_pair_kernel",
+                 "bf16_qw": "encode_pair_kernel", "fp8_qw": "encode_pair_kernel"}
 
 
 def parse():
@@ -1024,7 +1028,7 @@ def main():
                      "frac": achieved / peak,
                      "traffic": (ENCODE_TRAFFIC[(K, s, a.precision)] * N
                                  if (K, s, a.precision) in ENCODE_TRAFFIC else None),
-                     "kernel": "encode_kernel (prep+gram included in the timing)",
+                     "kernel": ENCODE_KERNEL.get(a.precision, "encode_kernel") + " (prep+gram included in the timing)",
                      "peak_source": f"{src}: {peak_note}"},
         "decode_roofline": {"bound": "shared-memory wavefronts", "achieved": dec_gbs, "unit": "GB/s",
                             "hbm_peak": float(peaks["hbm_gbs"]),
