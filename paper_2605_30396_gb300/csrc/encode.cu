@@ -43,6 +43,25 @@ constexpr int NTHREADS = 576;  // + MMA warp + TMA producer warp
 constexpr int SMEM_LIMIT = 232448;  // 227 KB opt-in dynamic shared memory per CTA
 constexpr float CORR_STOP_REL = 1e-7f;
 constexpr float PIVOT_MIN = 1e-6f;
+
+// The solvers run one OMP step for a row whose support holds t atoms.  Active
+// rows of a tile all hold t == it atoms, so a warp's active threads agree on t
+// and the step can be compiled once per t as straight-line code: with_t calls
+// f(IntC<t>{}) for 0 <= t < NT.
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+};
+template <int NT, class F>
+__device__ __forceinline__ void with_t(int t, F&& f) {
+  if constexpr (NT > 0) {
+    if (t == NT - 1) {
+      f(IntC<NT - 1>{});
+      return;
+    }
+    with_t<NT - 1>(t, f);
+  }
+}
 constexpr float FP8_MAX = 448.f;
 
 // 16-byte K-blocks per operand row and operand parts, per precision.
@@ -818,10 +837,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         const long long T2 = prof_on ? clock64() : 0;
 
         // ================= phase 2: merge, re-score, Cholesky, solve, residual
-        // Per-iteration quantities live in registers (arrays of SMAX entries,
-        // predicated on m < t); the factor L, y, gamma and the support stay in
-        // shared memory across iterations.  Every Gram entry and dictionary
-        // row the step needs is loaded as soon as the new atom is known.
+        // Per-iteration quantities live in registers (arrays of t entries, the
+        // step compiled once per t); the factor L, y, gamma and the support
+        // stay in shared memory across iterations.
         if (active && rn2 <= eps2) active = false;
         if (active) {
           float x[12], r[12];
@@ -921,44 +939,44 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
             active = false;
           } else {
-            // -------- prefetch: Gram row entries of the support and the new
-            // atom's dictionary row
-            const float* Grow = a.G + static_cast<size_t>(js) * K;
-            float gv[SMAX];
+            auto step = [&](auto tag) {
+              constexpr int T = decltype(tag)::value;
+              constexpr int TA = T > 0 ? T : 1;
+              // -------- Gram row entries of the support and the new atom's
+              // dictionary row
+              const float* Grow = a.G + static_cast<size_t>(js) * K;
+              float gv[TA];
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) gv[m] = m < t ? __ldg(Grow + sl[m]) : 0.f;
-            const float gjj = __ldg(Grow + js);
-            float4 dj[3];
-            {
-              const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+              for (int m = 0; m < T; ++m) gv[m] = __ldg(Grow + sl[m]);
+              const float gjj = __ldg(Grow + js);
+              float4 dj[3];
+              {
+                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
 #pragma unroll
-              for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
-            }
-            // -------- Cholesky update: w = L^-1 g, g_m = <d_js, d_sel[m]>
-            float w[SMAX];
-            float wn2 = 0.f;
+                for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
+              }
+              // -------- Cholesky update: w = L^-1 g, g_m = <d_js, d_sel[m]>
+              float w[TA];
+              float wn2 = 0.f;
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) {
-              w[m] = 0.f;
-              if (m < t) {
+              for (int m = 0; m < T; ++m) {
                 float acc = gv[m];
 #pragma unroll
                 for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
                 w[m] = acc * IDG(m);
                 wn2 = fmaf(w[m], w[m], wn2);
               }
-            }
-            const float ell2 = gjj - wn2;
-            if (!(ell2 > PIVOT_MIN * gjj)) {
-              active = false;
-            } else {
+              const float ell2 = gjj - wn2;
+              if (!(ell2 > PIVOT_MIN * gjj)) {
+                active = false;
+                return;
+              }
               const float ell = sqrtf(ell2);
               const float iell = 1.f / ell;
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) LS(t, m) = w[m];  // the four sub-lanes store identical values
-              LS(t, t) = ell;
-              IDG(t) = iell;
+              for (int m = 0; m < T; ++m) LS(T, m) = w[m];  // the four sub-lanes store identical values
+              LS(T, T) = ell;
+              IDG(T) = iell;
               float bp = 0.f;
 #pragma unroll
               for (int w4 = 0; w4 < 3; ++w4) {
@@ -967,51 +985,57 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
                 bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
               }
-              float yv[SMAX];
+              float yv[TA];
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) yv[m] = m < t ? ys[m * TILE_M + R2] : 0.f;
+              for (int m = 0; m < T; ++m) yv[m] = ys[m * TILE_M + R2];
               float yt = quad_sum(bp);
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) yt = fmaf(-w[m], yv[m], yt);
+              for (int m = 0; m < T; ++m) yt = fmaf(-w[m], yv[m], yt);
               yt *= iell;
-              ys[t * TILE_M + R2] = yt;
-              sel[t * TILE_M + R2] = js;
+              ys[T * TILE_M + R2] = yt;
+              sel[T * TILE_M + R2] = js;
               // back substitution L^T gamma = y (the new atom's entry first)
               const float gt = yt * iell;
-              float gam[SMAX];
+              float gam[TA];
 #pragma unroll
-              for (int m = SMAX - 1; m >= 0; --m) {
-                gam[m] = 0.f;
-                if (m < t) {
-                  float acc = yv[m];
+              for (int m = T - 1; m >= 0; --m) {
+                float acc = yv[m];
 #pragma unroll
-                  for (int q = m + 1; q < SMAX; ++q)
-                    if (q < t) acc = fmaf(-LS(q, m), gam[q], acc);
-                  acc = fmaf(-w[m], gt, acc);
-                  gam[m] = acc * IDG(m);
-                }
+                for (int q = m + 1; q < T; ++q) acc = fmaf(-LS(q, m), gam[q], acc);
+                acc = fmaf(-w[m], gt, acc);
+                gam[m] = acc * IDG(m);
               }
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) gs[m * TILE_M + R2] = gam[m];
-              gs[t * TILE_M + R2] = gt;
+              for (int m = 0; m < T; ++m) gs[m * TILE_M + R2] = gam[m];
+              gs[T * TILE_M + R2] = gt;
               // residual r = x - D_I gamma on this sub-lane's 12 dims
 #pragma unroll
               for (int k = 0; k < 12; ++k) r[k] = x[k];
+              // the support atoms' rows in groups of up to 4, all loads of a
+              // group issued before its FMAs (one L2 round trip per group)
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) {
-                if (m < t) {
-                  const float4* da = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
+              for (int m0 = 0; m0 < T; m0 += 4) {
+                float4 dv[4][3];
 #pragma unroll
-                  for (int w4 = 0; w4 < 3; ++w4) {
-                    const float4 dv = __ldg(da + w4);
-                    r[4 * w4 + 0] = fmaf(-gam[m], dv.x, r[4 * w4 + 0]);
-                    r[4 * w4 + 1] = fmaf(-gam[m], dv.y, r[4 * w4 + 1]);
-                    r[4 * w4 + 2] = fmaf(-gam[m], dv.z, r[4 * w4 + 2]);
-                    r[4 * w4 + 3] = fmaf(-gam[m], dv.w, r[4 * w4 + 3]);
+                for (int mm = 0; mm < 4; ++mm)
+                  if (m0 + mm < T) {
+                    const float4* da =
+                        reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m0 + mm]) * DPAD + 12 * u);
+#pragma unroll
+                    for (int w4 = 0; w4 < 3; ++w4) dv[mm][w4] = __ldg(da + w4);
                   }
-                }
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm)
+                  if (m0 + mm < T) {
+                    const float gm = gam[m0 + mm];
+#pragma unroll
+                    for (int w4 = 0; w4 < 3; ++w4) {
+                      r[4 * w4 + 0] = fmaf(-gm, dv[mm][w4].x, r[4 * w4 + 0]);
+                      r[4 * w4 + 1] = fmaf(-gm, dv[mm][w4].y, r[4 * w4 + 1]);
+                      r[4 * w4 + 2] = fmaf(-gm, dv[mm][w4].z, r[4 * w4 + 2]);
+                      r[4 * w4 + 3] = fmaf(-gm, dv[mm][w4].w, r[4 * w4 + 3]);
+                    }
+                  }
               }
 #pragma unroll
               for (int w4 = 0; w4 < 3; ++w4) {
@@ -1020,7 +1044,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
                 r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
               }
-              ++t;
+              t = T + 1;
               float pr = 0.f;
 #pragma unroll
               for (int k = 0; k < 12; ++k) pr = fmaf(r[k], r[k], pr);
@@ -1040,19 +1064,23 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 #pragma unroll
                 for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = r[k];
               }
-            }
+            };
+            if (t < SMAX)
+              with_t<SMAX>(t, step);
+            else
+              active = false;
           }
         }
         fence_proxy_async_smem();
         const long long T3 = prof_on ? clock64() : 0;
         named_bar_sync(1, NEPI);
         if (it + 1 < s && tid == 0) mbar_arrive(bar_a);
-        const long long T4 = prof_on ? clock64() : 0;
+        const long long Tend = prof_on ? clock64() : 0;
         if (prof_on) {
           pcs[1] += T1 - T0;
           pcs[2] += T2 - T1;
           pcs[3] += T3 - T2;
-          pcs[4] += T4 - T3;
+          pcs[4] += Tend - T3;
           pcs[5] += 1;
         }
       }

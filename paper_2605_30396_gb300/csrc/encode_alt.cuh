@@ -17,13 +17,14 @@
 //            residual (TF32 hi, lo) into the tensor-memory A columns, then runs
 //            the 3xTF32 MMAs (M = 128, N = 128) of every chunk.
 //   warps 0-15  selection (four threads per row, a 32-column quarter of each
-//            chunk) and solver (four sub-lanes of 12 dims per signal), as in
+//            chunk) and solver (four sub-lanes of 12 interleaved dims per signal), as in
 //            the one-tile encoder, on the two tiles in turn.
 // Tensor memory: A (hi then lo) in columns 0..95, three 128-column accumulator
 // buffers in 128..511, used in job order.  N = 64 MMAs measured at about half
 // the throughput of N = 128 ones, so the chunks stay 128 atoms wide.
 
 constexpr int ABN = 128;     // atoms per chunk
+
 constexpr int ABUF = 3;      // accumulator buffers
 constexpr int AQC = 32;      // chunk columns read by one selection thread
 
@@ -87,14 +88,43 @@ inline int make_alt_plan(int K, int s, int code, AltPlan& p, int smem_limit = SM
   return DLSH_OK;
 }
 
-// One chunk of 3xTF32 MMAs, A (hi, lo) from tensor memory, N = 128.
-__device__ __forceinline__ void issue_alt_chunk(uint32_t tmem_d, uint32_t a_tmem, uint32_t b_addr) {
+// Sub-lane u of a row owns the dimensions 16k + 4u .. 16k + 4u + 3 (k = 0, 1,
+// 2): the four sub-lanes of a row read 16 contiguous bytes of each group, so a
+// warp's load touches one cache line per row where the 12-contiguous split
+// touched two.
+__device__ __forceinline__ int alt_dim(int u, int q) { return 16 * (q >> 2) + 4 * u + (q & 3); }
+
+// Sub-lane u's 12 values (TF32 hi, lo) into the A operand: dims 16k + 4u .. are
+// K block 4k + u.
+__device__ __forceinline__ void write_a_alt(uint8_t* A, int row, int u, const float (&r)[12]) {
+  constexpr uint32_t LBO = TILE_M * 16, PART = TILE_M * 12 * 16;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int kb = 4 * k + u;
+    float4 hi, lo;
+    hi.x = to_tf32(r[4 * k + 0]);
+    hi.y = to_tf32(r[4 * k + 1]);
+    hi.z = to_tf32(r[4 * k + 2]);
+    hi.w = to_tf32(r[4 * k + 3]);
+    lo.x = to_tf32(r[4 * k + 0] - hi.x);
+    lo.y = to_tf32(r[4 * k + 1] - hi.y);
+    lo.z = to_tf32(r[4 * k + 2] - hi.z);
+    lo.w = to_tf32(r[4 * k + 3] - hi.w);
+    *reinterpret_cast<float4*>(A + kb * LBO + row * 16) = hi;
+    *reinterpret_cast<float4*>(A + PART + kb * LBO + row * 16) = lo;
+  }
+}
+
+// Passes P0..P1-1 of one chunk of 3xTF32 MMAs, A (hi, lo) from tensor memory,
+// N = 128: pass 0 hi(r).hi(D), pass 1 hi(r).lo(D), pass 2 lo(r).hi(D).
+template <int P0, int P1>
+__device__ __forceinline__ void issue_alt_passes(uint32_t tmem_d, uint32_t a_tmem, uint32_t b_addr) {
   constexpr uint32_t idesc = umma_idesc(2, 2, TILE_M, ABN);
   constexpr uint32_t B_LBO = ABN * 16, SBO = 128, B_PART = ABN * 12 * 16;
 #pragma unroll
-  for (int pass = 0; pass < 3; ++pass) {
-    const uint32_t ao = pass == 2 ? 48u : 0u;    // lo(r) . hi(D)
-    const uint32_t bo = pass == 1 ? B_PART : 0u;  // hi(r) . lo(D)
+  for (int pass = P0; pass < P1; ++pass) {
+    const uint32_t ao = pass == 2 ? 48u : 0u;
+    const uint32_t bo = pass == 1 ? B_PART : 0u;
 #pragma unroll
     for (int ks = 0; ks < 6; ++ks) {
       const uint64_t bd = umma_smem_desc(b_addr + bo + ks * 2 * B_LBO, B_LBO, SBO);
@@ -105,7 +135,6 @@ __device__ __forceinline__ void issue_alt_chunk(uint32_t tmem_d, uint32_t a_tmem
 
 __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_constant__ AltArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int SMAX = 8;
   constexpr uint32_t ACC0 = 128;
   const AltPlan& p = a.p;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -167,13 +196,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
       long long ring = 0;
+      int st = 0;
+      uint32_t par = 1u;  // bar_dempty parity to wait for at stage st
       bool ok = true;
       for (int k = 0; k < K0 && ok; ++k)
         for (int it = 0; it < s && ok; ++it)
           for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t)
             for (int c = 0; c < p.nchunks; ++c, ++ring) {
-              const int st = static_cast<int>(ring % p.stages);
-              const uint32_t par = static_cast<uint32_t>((ring / p.stages) & 1) ^ 1u;
               if (!mbar_wait(&bar_dempty[st], par, a.budget)) {
                 flag_status(a.status, ST_TIMEOUT);
                 ok = false;
@@ -182,7 +211,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
               mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
               bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
                        a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes, &bar_dfull[st]);
+              if (++st == p.stages) {
+                st = 0;
+                par ^= 1u;
+              }
             }
+      // drain: the last `stages` chunks' MMAs must complete before the CTA exits
       for (long long f = ring > p.stages ? ring - p.stages : 0; ok && f < ring; ++f) {
         if (!mbar_wait(&bar_dempty[f % p.stages], static_cast<uint32_t>((f / p.stages) & 1), a.budget)) {
           flag_status(a.status, ST_TIMEOUT);
@@ -194,8 +228,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
       uint32_t aph[2] = {0u, 0u};
-      long long ring = 0, cc = 0, job = 0;
+      long long job = 0;
+      // the next chunk's ring stage and accumulator buffer with the parities
+      // of their bar_dfull / bar_full phases; the previous chunk's buffer
+      int st = 0, buf = 0, lbuf = -1;
+      uint32_t dpar = 0u, fpar = 0u, lfpar = 0u;
       bool ok = true;
+      // waits until chunk resources (st, buf) are ready: its dictionary chunk
+      // has landed and its accumulator buffer has been read
+      auto wait_chunk = [&]() -> bool {
+        const long long W2 = prof_any ? clock64() : 0;
+        const bool okd = mbar_wait(&bar_dfull[st], dpar, a.budget);
+        const long long W3 = prof_any ? clock64() : 0;
+        const bool oke = okd && mbar_wait(&bar_empty[buf], fpar ^ 1u, a.budget);
+        if (prof_any) {
+          pcs[7] += W3 - W2;
+          pcs[8] += clock64() - W3;
+        }
+        if (!oke) flag_status(a.status, ST_TIMEOUT);
+        return oke;
+      };
       for (int k = 0; k < K0 && ok; ++k)
         for (int it = 0; it < s && ok; ++it)
           for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t, ++job) {
@@ -209,8 +261,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
             aph[t] ^= 1u;
             // the A columns are shared by the jobs: the previous job's last MMAs
             // (and so all of its MMAs) must have completed before the copy
-            if (cc > 0 && !mbar_wait(&bar_full[(cc - 1) % ABUF],
-                                     static_cast<uint32_t>(((cc - 1) / ABUF) & 1), a.budget)) {
+            if (lbuf >= 0 && !mbar_wait(&bar_full[lbuf], lfpar, a.budget)) {
               flag_status(a.status, ST_TIMEOUT);
               ok = false;
               break;
@@ -236,29 +287,36 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
               if (prof_any) pcs[9] += clock64() - W1;
               *stage_done = job;
             }
-            for (int c = 0; c < p.nchunks; ++c, ++ring, ++cc) {
-              const int st = static_cast<int>(ring % p.stages);
-              const uint32_t dpar = static_cast<uint32_t>((ring / p.stages) & 1);
-              const int buf = static_cast<int>(cc % ABUF);
-              const uint32_t epar = static_cast<uint32_t>((cc / ABUF) & 1) ^ 1u;
-              const long long W2 = prof_any ? clock64() : 0;
-              const bool okd = mbar_wait(&bar_dfull[st], dpar, a.budget);
-              const long long W3 = prof_any ? clock64() : 0;
-              const bool oke = okd && mbar_wait(&bar_empty[buf], epar, a.budget);
-              if (prof_any) {
-                pcs[7] += W3 - W2;
-                pcs[8] += clock64() - W3;
+            if (!wait_chunk()) {
+              ok = false;
+              break;
+            }
+            for (int c = 0; c < p.nchunks; ++c) {
+              tc_fence_after();
+              const uint32_t d = tmem_base + ACC0 + static_cast<uint32_t>(buf) * ABN;
+              const uint32_t b = ring_addr + static_cast<uint32_t>(st) * p.chunk_bytes;
+              issue_alt_passes<0, 2>(d, ta, b);
+              // the next chunk's resources are checked while the last pass of
+              // this one runs, so the checks do not leave the tensor pipe idle
+              const int cst = st, cbuf = buf;
+              lbuf = buf;
+              lfpar = fpar;
+              if (++st == p.stages) {
+                st = 0;
+                dpar ^= 1u;
               }
-              if (!oke) {
-                flag_status(a.status, ST_TIMEOUT);
+              if (++buf == ABUF) {
+                buf = 0;
+                fpar ^= 1u;
+              }
+              const bool nok = c + 1 < p.nchunks ? wait_chunk() : true;
+              issue_alt_passes<2, 3>(d, ta, b);
+              tc_commit(&bar_full[cbuf]);
+              tc_commit(&bar_dempty[cst]);
+              if (!nok) {
                 ok = false;
                 break;
               }
-              tc_fence_after();
-              issue_alt_chunk(tmem_base + ACC0 + static_cast<uint32_t>(buf) * ABN, ta,
-                              ring_addr + static_cast<uint32_t>(st) * p.chunk_bytes);
-              tc_commit(&bar_full[buf]);
-              tc_commit(&bar_dempty[st]);
             }
           }
     }
@@ -273,7 +331,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
                           static_cast<uint32_t>(q1 * AQC);
     const int K = p.K, nchunks = p.nchunks;
     const float eps2 = a.eps * a.eps;
-    long long cc = 0;
+    int sbuf = 0;       // accumulator buffer of the next chunk
+    uint32_t spar = 0u;  // and the parity of its bar_full phase
     bool ok = true;
     // the staging area may be written for job J once the copy of job J - 1 has
     // completed (published by the MMA warp)
@@ -292,14 +351,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
     auto stage_x = [&](long long tl) -> float {
       const int64_t tg0 = tl * TILE_M;
       const bool tin = R2 < (NS - tg0 < TILE_M ? NS - tg0 : TILE_M);
-      const float* txr = a.X + (tg0 + R2) * DLSH_D + 12 * u;
+      const float* txr = a.X + (tg0 + R2) * DLSH_D;
       float x[12];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) x[q] = (tin && 12 * u + q < DLSH_D) ? __ldg(txr + q) : 0.f;
+      for (int q = 0; q < 12; ++q) x[q] = (tin && alt_dim(u, q) < DLSH_D) ? __ldg(txr + alt_dim(u, q)) : 0.f;
       float part = 0.f;
 #pragma unroll
       for (int q = 0; q < 12; ++q) part = fmaf(x[q], x[q], part);
-      write_a_part<0>(A, R2, u, x, 1.f);
+      write_a_alt(A, R2, u, x);
       return quad_sum(part);
     };
     auto tile_of = [&](int t, int k) -> long long { return static_cast<long long>(bidx) + (2LL * k + t) * Gd; };
@@ -350,17 +409,22 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
           const int64_t g0 = tl * TILE_M;
           const int rows = static_cast<int>(NS - g0 < TILE_M ? NS - g0 : TILE_M);
           const bool in_tile = R2 < rows;
-          const float* xr = a.X + (g0 + R2) * DLSH_D + 12 * u;
+          const float* xr = a.X + (g0 + R2) * DLSH_D;
           // ================= phase 1: selection over this thread's column quarter
           const bool prof_on = prof_any && tid == 0;
           const long long T0 = prof_on ? clock64() : 0;
           {
             uint32_t best = 0;
             int bestc = 0;
-            for (int c = 0; c < nchunks; ++c, ++cc) {
-              const int buf = static_cast<int>(cc % ABUF);
+            for (int c = 0; c < nchunks; ++c) {
+              const int buf = sbuf;
+              const uint32_t spar0 = spar;
+              if (++sbuf == ABUF) {
+                sbuf = 0;
+                spar ^= 1u;
+              }
               const long long W4 = prof_on ? clock64() : 0;
-              if (!mbar_wait(&bar_full[buf], static_cast<uint32_t>((cc / ABUF) & 1), a.budget)) {
+              if (!mbar_wait(&bar_full[buf], spar0, a.budget)) {
                 flag_status(a.status, ST_TIMEOUT);
                 ok = false;
                 break;
@@ -399,142 +463,154 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
           bool act = actc;
           if (act && rn2c <= eps2) act = false;
           if (act) {
-            float x[12], r[12];
+            // the step for a support of tt atoms, compiled once per tt
+            auto step = [&](auto tag) {
+              constexpr int T = decltype(tag)::value;
+              constexpr int TA = T > 0 ? T : 1;
+              float x[12], r[12];
 #pragma unroll
-            for (int q = 0; q < 12; ++q) x[q] = (in_tile && 12 * u + q < DLSH_D) ? __ldg(xr + q) : 0.f;
-            int sl[SMAX];
+              for (int q = 0; q < 12; ++q) x[q] = (in_tile && alt_dim(u, q) < DLSH_D) ? __ldg(xr + alt_dim(u, q)) : 0.f;
+              int sl[TA];
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) sl[m] = m < tt ? sel[m * TILE_M + R2] : 0;
-            int js = -1;
-            float bestv = -1.f;
+              for (int m = 0; m < T; ++m) sl[m] = sel[m * TILE_M + R2];
+              int js = -1;
+              float bestv = -1.f;
 #pragma unroll
-            for (int qq = 0; qq < 4; ++qq) {
-              const float v = cv[R2 * 4 + qq];
-              const int j = cj[R2 * 4 + qq];
-              if (j < K && (v > bestv || (v == bestv && j < js))) {
-                bestv = v;
-                js = j;
+              for (int qq = 0; qq < 4; ++qq) {
+                const float v = cv[R2 * 4 + qq];
+                const int j = cj[R2 * 4 + qq];
+                if (j < K && (v > bestv || (v == bestv && j < js))) {
+                  bestv = v;
+                  js = j;
+                }
               }
-            }
-            bool dup = false;
+              bool dup = false;
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) dup |= (m < tt && sl[m] == js);
-            if (dup) js = -1;
-            if (js < 0 || !(bestv > CORR_STOP_REL * xnc)) {
-              act = false;
-            } else {
+              for (int m = 0; m < T; ++m) dup |= sl[m] == js;
+              if (dup) js = -1;
+              if (js < 0 || !(bestv > CORR_STOP_REL * xnc)) {
+                act = false;
+                return;
+              }
               const float* Grow = a.G + static_cast<size_t>(js) * K;
-              float gv[SMAX];
+              float gv[TA];
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) gv[m] = m < tt ? __ldg(Grow + sl[m]) : 0.f;
+              for (int m = 0; m < T; ++m) gv[m] = __ldg(Grow + sl[m]);
               const float gjj = __ldg(Grow + js);
               float4 dj[3];
               {
-                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 12 * u);
+                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 4 * u);
 #pragma unroll
-                for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + w4);
+                for (int w4 = 0; w4 < 3; ++w4) dj[w4] = __ldg(dr + 4 * w4);
               }
-              float w[SMAX];
+              float w[TA];
               float wn2 = 0.f;
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) {
-                w[m] = 0.f;
-                if (m < tt) {
-                  float acc = gv[m];
+              for (int m = 0; m < T; ++m) {
+                float acc = gv[m];
 #pragma unroll
-                  for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
-                  w[m] = acc * IDG(m);
-                  wn2 = fmaf(w[m], w[m], wn2);
-                }
+                for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
+                w[m] = acc * IDG(m);
+                wn2 = fmaf(w[m], w[m], wn2);
               }
               const float ell2 = gjj - wn2;
               if (!(ell2 > PIVOT_MIN * gjj)) {
                 act = false;
-              } else {
-                const float ell = sqrtf(ell2);
-                const float iell = 1.f / ell;
+                return;
+              }
+              const float ell = sqrtf(ell2);
+              const float iell = 1.f / ell;
 #pragma unroll
-                for (int m = 0; m < SMAX; ++m)
-                  if (m < tt) LS(tt, m) = w[m];
-                IDG(tt) = iell;  // the diagonal holds 1 / L(t, t)
-                float bp = 0.f;
+              for (int m = 0; m < T; ++m) LS(T, m) = w[m];
+              IDG(T) = iell;  // the diagonal holds 1 / L(t, t)
+              float bp = 0.f;
 #pragma unroll
-                for (int w4 = 0; w4 < 3; ++w4) {
-                  bp = fmaf(dj[w4].x, x[4 * w4 + 0], bp);
-                  bp = fmaf(dj[w4].y, x[4 * w4 + 1], bp);
-                  bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
-                  bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
-                }
-                float yv[SMAX];
+              for (int w4 = 0; w4 < 3; ++w4) {
+                bp = fmaf(dj[w4].x, x[4 * w4 + 0], bp);
+                bp = fmaf(dj[w4].y, x[4 * w4 + 1], bp);
+                bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
+                bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
+              }
+              float yv[TA];
 #pragma unroll
-                for (int m = 0; m < SMAX; ++m) yv[m] = m < tt ? ys[m * TILE_M + R2] : 0.f;
-                float yt = quad_sum(bp);
+              for (int m = 0; m < T; ++m) yv[m] = ys[m * TILE_M + R2];
+              float yt = quad_sum(bp);
 #pragma unroll
-                for (int m = 0; m < SMAX; ++m)
-                  if (m < tt) yt = fmaf(-w[m], yv[m], yt);
-                yt *= iell;
-                ys[tt * TILE_M + R2] = yt;
-                sel[tt * TILE_M + R2] = js;
-                const float gt = yt * iell;
-                float gam[SMAX];
+              for (int m = 0; m < T; ++m) yt = fmaf(-w[m], yv[m], yt);
+              yt *= iell;
+              ys[T * TILE_M + R2] = yt;
+              sel[T * TILE_M + R2] = js;
+              const float gt = yt * iell;
+              float gam[TA];
 #pragma unroll
-                for (int m = SMAX - 1; m >= 0; --m) {
-                  gam[m] = 0.f;
-                  if (m < tt) {
-                    float acc = yv[m];
+              for (int m = T - 1; m >= 0; --m) {
+                float acc = yv[m];
 #pragma unroll
-                    for (int q = m + 1; q < SMAX; ++q)
-                      if (q < tt) acc = fmaf(-LS(q, m), gam[q], acc);
-                    acc = fmaf(-w[m], gt, acc);
-                    gam[m] = acc * IDG(m);
+                for (int q = m + 1; q < T; ++q) acc = fmaf(-LS(q, m), gam[q], acc);
+                acc = fmaf(-w[m], gt, acc);
+                gam[m] = acc * IDG(m);
+              }
+              // the row's coefficients so far (sub-lane u writes slots u, u+4)
+              {
+                const int64_t gi = g0 + R2;
+#pragma unroll
+                for (int m = 0; m < T; ++m)
+                  if ((m & 3) == u) a.coef[gi * s + m] = gam[m];
+                if ((T & 3) == u) a.coef[gi * s + T] = gt;
+              }
+#pragma unroll
+              for (int q = 0; q < 12; ++q) r[q] = x[q];
+              // the support atoms' rows in groups of up to four, all loads of a
+              // group issued before its FMAs (one L2 round trip per group)
+#pragma unroll
+              for (int m0 = 0; m0 < T; m0 += 4) {
+                float4 dv[4][3];
+#pragma unroll
+                for (int mm = 0; mm < 4; ++mm)
+                  if (m0 + mm < T) {
+                    const float4* da =
+                        reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m0 + mm]) * DPAD + 4 * u);
+#pragma unroll
+                    for (int w4 = 0; w4 < 3; ++w4) dv[mm][w4] = __ldg(da + 4 * w4);
                   }
-                }
-                // the row's coefficients so far (sub-lane u writes slots u, u+4)
-                {
-                  const int64_t gi = g0 + R2;
 #pragma unroll
-                  for (int m = 0; m < SMAX; ++m)
-                    if (m < tt && (m & 3) == u) a.coef[gi * s + m] = gam[m];
-                  if ((tt & 3) == u) a.coef[gi * s + tt] = gt;
-                }
-#pragma unroll
-                for (int q = 0; q < 12; ++q) r[q] = x[q];
-#pragma unroll
-                for (int m = 0; m < SMAX; ++m) {
-                  if (m < tt) {
-                    const float4* da = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m]) * DPAD + 12 * u);
+                for (int mm = 0; mm < 4; ++mm)
+                  if (m0 + mm < T) {
+                    const float gm = gam[m0 + mm];
 #pragma unroll
                     for (int w4 = 0; w4 < 3; ++w4) {
-                      const float4 dv = __ldg(da + w4);
-                      r[4 * w4 + 0] = fmaf(-gam[m], dv.x, r[4 * w4 + 0]);
-                      r[4 * w4 + 1] = fmaf(-gam[m], dv.y, r[4 * w4 + 1]);
-                      r[4 * w4 + 2] = fmaf(-gam[m], dv.z, r[4 * w4 + 2]);
-                      r[4 * w4 + 3] = fmaf(-gam[m], dv.w, r[4 * w4 + 3]);
+                      r[4 * w4 + 0] = fmaf(-gm, dv[mm][w4].x, r[4 * w4 + 0]);
+                      r[4 * w4 + 1] = fmaf(-gm, dv[mm][w4].y, r[4 * w4 + 1]);
+                      r[4 * w4 + 2] = fmaf(-gm, dv[mm][w4].z, r[4 * w4 + 2]);
+                      r[4 * w4 + 3] = fmaf(-gm, dv[mm][w4].w, r[4 * w4 + 3]);
                     }
                   }
-                }
-#pragma unroll
-                for (int w4 = 0; w4 < 3; ++w4) {
-                  r[4 * w4 + 0] = fmaf(-gt, dj[w4].x, r[4 * w4 + 0]);
-                  r[4 * w4 + 1] = fmaf(-gt, dj[w4].y, r[4 * w4 + 1]);
-                  r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
-                  r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
-                }
-                tcc = tt + 1;
-                float pr = 0.f;
-#pragma unroll
-                for (int q = 0; q < 12; ++q) pr = fmaf(r[q], r[q], pr);
-                rn2c = quad_sum(pr);
-                if (it + 1 < s) {
-                  const long long W5 = prof_on ? clock64() : 0;
-                  if (wait_staging(job_index(t, k, it + 1)))
-                    write_a_part<0>(A, R2, u, r, 1.f);
-                  else
-                    ok = false;
-                  if (prof_on) pcs[3] += clock64() - W5;
-                }
               }
-            }
+#pragma unroll
+              for (int w4 = 0; w4 < 3; ++w4) {
+                r[4 * w4 + 0] = fmaf(-gt, dj[w4].x, r[4 * w4 + 0]);
+                r[4 * w4 + 1] = fmaf(-gt, dj[w4].y, r[4 * w4 + 1]);
+                r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
+                r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
+              }
+              tcc = T + 1;
+              float pr = 0.f;
+#pragma unroll
+              for (int q = 0; q < 12; ++q) pr = fmaf(r[q], r[q], pr);
+              rn2c = quad_sum(pr);
+              if (it + 1 < s) {
+                const long long W5 = prof_on ? clock64() : 0;
+                if (wait_staging(job_index(t, k, it + 1)))
+                  write_a_alt(A, R2, u, r);
+                else
+                  ok = false;
+                if (prof_on) pcs[3] += clock64() - W5;
+              }
+            };
+            if (tt < 8)
+              with_t<8>(tt, step);
+            else
+              act = false;
           }
           actc = act;
           // last iteration: write this slot's codes, then stage its next tile's

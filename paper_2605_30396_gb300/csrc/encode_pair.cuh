@@ -556,42 +556,43 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_pair_kernel(const __grid_c
           if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
             active = false;
           } else {
-            const float* Grow = a.G + static_cast<size_t>(js) * K;
-            float gv[SMAX];
+            // the step for a support of t atoms, compiled once per t
+            auto step = [&](auto tag) {
+              constexpr int T = decltype(tag)::value;
+              constexpr int TA = T > 0 ? T : 1;
+              const float* Grow = a.G + static_cast<size_t>(js) * K;
+              float gv[TA];
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) gv[m] = m < t ? __ldg(Grow + sl[m]) : 0.f;
-            const float gjj = __ldg(Grow + js);
-            float4 dj[6];
-            {
-              const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 24 * u);
+              for (int m = 0; m < T; ++m) gv[m] = __ldg(Grow + sl[m]);
+              const float gjj = __ldg(Grow + js);
+              float4 dj[6];
+              {
+                const float4* dr = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(js) * DPAD + 24 * u);
 #pragma unroll
-              for (int w4 = 0; w4 < 6; ++w4) dj[w4] = __ldg(dr + w4);
-            }
-            load_x(r);  // r holds x until the residual is formed
-            float w[SMAX];
-            float wn2 = 0.f;
+                for (int w4 = 0; w4 < 6; ++w4) dj[w4] = __ldg(dr + w4);
+              }
+              load_x(r);  // r holds x until the residual is formed
+              float w[TA];
+              float wn2 = 0.f;
 #pragma unroll
-            for (int m = 0; m < SMAX; ++m) {
-              w[m] = 0.f;
-              if (m < t) {
+              for (int m = 0; m < T; ++m) {
                 float acc = gv[m];
 #pragma unroll
                 for (int q = 0; q < m; ++q) acc = fmaf(-LS(m, q), w[q], acc);
                 w[m] = acc * IDG(m);
                 wn2 = fmaf(w[m], w[m], wn2);
               }
-            }
-            const float ell2 = gjj - wn2;
-            if (!(ell2 > PIVOT_MIN * gjj)) {
-              active = false;
-            } else {
+              const float ell2 = gjj - wn2;
+              if (!(ell2 > PIVOT_MIN * gjj)) {
+                active = false;
+                return;
+              }
               const float ell = sqrtf(ell2);
               const float iell = 1.f / ell;
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) LS(t, m) = w[m];  // both sub-lanes store identical values
-              LS(t, t) = ell;
-              IDG(t) = iell;
+              for (int m = 0; m < T; ++m) LS(T, m) = w[m];  // both sub-lanes store identical values
+              LS(T, T) = ell;
+              IDG(T) = iell;
               float bp = 0.f;
 #pragma unroll
               for (int w4 = 0; w4 < 6; ++w4) {
@@ -600,48 +601,54 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_pair_kernel(const __grid_c
                 bp = fmaf(dj[w4].z, r[4 * w4 + 2], bp);
                 bp = fmaf(dj[w4].w, r[4 * w4 + 3], bp);
               }
-              float yv[SMAX];
+              float yv[TA];
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) yv[m] = m < t ? ys[m * TILE_M + R2] : 0.f;
+              for (int m = 0; m < T; ++m) yv[m] = ys[m * TILE_M + R2];
               float yt = pair_sum(bp);
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) yt = fmaf(-w[m], yv[m], yt);
+              for (int m = 0; m < T; ++m) yt = fmaf(-w[m], yv[m], yt);
               yt *= iell;
-              ys[t * TILE_M + R2] = yt;
-              sel[t * TILE_M + R2] = js;
+              ys[T * TILE_M + R2] = yt;
+              sel[T * TILE_M + R2] = js;
               const float gt = yt * iell;
-              float gam[SMAX];
+              float gam[TA];
 #pragma unroll
-              for (int m = SMAX - 1; m >= 0; --m) {
-                gam[m] = 0.f;
-                if (m < t) {
-                  float acc = yv[m];
+              for (int m = T - 1; m >= 0; --m) {
+                float acc = yv[m];
 #pragma unroll
-                  for (int q = m + 1; q < SMAX; ++q)
-                    if (q < t) acc = fmaf(-LS(q, m), gam[q], acc);
-                  acc = fmaf(-w[m], gt, acc);
-                  gam[m] = acc * IDG(m);
-                }
+                for (int q = m + 1; q < T; ++q) acc = fmaf(-LS(q, m), gam[q], acc);
+                acc = fmaf(-w[m], gt, acc);
+                gam[m] = acc * IDG(m);
               }
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m)
-                if (m < t) gs[m * TILE_M + R2] = gam[m];
-              gs[t * TILE_M + R2] = gt;
+              for (int m = 0; m < T; ++m) gs[m * TILE_M + R2] = gam[m];
+              gs[T * TILE_M + R2] = gt;
               // residual r = x - D_I gamma on this sub-lane's 24 dims
+              // the support atoms' rows in groups of up to 2, all loads of a
+              // group issued before its FMAs (one L2 round trip per group)
 #pragma unroll
-              for (int m = 0; m < SMAX; ++m) {
-                if (m < t) {
-                  const float4* da = reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m]) * DPAD + 24 * u);
+              for (int m0 = 0; m0 < T; m0 += 2) {
+                float4 dv[2][6];
 #pragma unroll
-                  for (int w4 = 0; w4 < 6; ++w4) {
-                    const float4 dv = __ldg(da + w4);
-                    r[4 * w4 + 0] = fmaf(-gam[m], dv.x, r[4 * w4 + 0]);
-                    r[4 * w4 + 1] = fmaf(-gam[m], dv.y, r[4 * w4 + 1]);
-                    r[4 * w4 + 2] = fmaf(-gam[m], dv.z, r[4 * w4 + 2]);
-                    r[4 * w4 + 3] = fmaf(-gam[m], dv.w, r[4 * w4 + 3]);
+                for (int mm = 0; mm < 2; ++mm)
+                  if (m0 + mm < T) {
+                    const float4* da =
+                        reinterpret_cast<const float4*>(a.D32p + static_cast<size_t>(sl[m0 + mm]) * DPAD + 24 * u);
+#pragma unroll
+                    for (int w4 = 0; w4 < 6; ++w4) dv[mm][w4] = __ldg(da + w4);
                   }
-                }
+#pragma unroll
+                for (int mm = 0; mm < 2; ++mm)
+                  if (m0 + mm < T) {
+                    const float gm = gam[m0 + mm];
+#pragma unroll
+                    for (int w4 = 0; w4 < 6; ++w4) {
+                      r[4 * w4 + 0] = fmaf(-gm, dv[mm][w4].x, r[4 * w4 + 0]);
+                      r[4 * w4 + 1] = fmaf(-gm, dv[mm][w4].y, r[4 * w4 + 1]);
+                      r[4 * w4 + 2] = fmaf(-gm, dv[mm][w4].z, r[4 * w4 + 2]);
+                      r[4 * w4 + 3] = fmaf(-gm, dv[mm][w4].w, r[4 * w4 + 3]);
+                    }
+                  }
               }
 #pragma unroll
               for (int w4 = 0; w4 < 6; ++w4) {
@@ -650,7 +657,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_pair_kernel(const __grid_c
                 r[4 * w4 + 2] = fmaf(-gt, dj[w4].z, r[4 * w4 + 2]);
                 r[4 * w4 + 3] = fmaf(-gt, dj[w4].w, r[4 * w4 + 3]);
               }
-              ++t;
+              t = T + 1;
               float pr = 0.f;
 #pragma unroll
               for (int q = 0; q < 24; ++q) pr = fmaf(r[q], r[q], pr);
@@ -673,7 +680,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_pair_kernel(const __grid_c
 #pragma unroll
                 for (int q = 0; q < 24; ++q) rsm[q * PGT + gtid] = r[q];
               }
-            }
+            };
+            if (t < 8)
+              with_t<8>(t, step);
+            else
+              active = false;
           }
         }
         fence_proxy_async_smem();
