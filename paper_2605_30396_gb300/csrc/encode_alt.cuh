@@ -27,6 +27,11 @@ constexpr int ABN = 128;     // atoms per chunk
 
 constexpr int ABUF = 3;      // accumulator buffers
 constexpr int AQC = 32;      // chunk columns read by one selection thread
+// K-block stride of the staged A operand: 128 rows of 16 bytes plus 32 bytes of
+// skew, so that the 16-byte stores of a quarter-warp (two rows, four K blocks)
+// fall on eight different bank groups
+constexpr uint32_t ALBO = TILE_M * 16 + 32;
+constexpr uint32_t APART = 12 * ALBO;  // the TF32 hi part, then the lo part
 
 struct AltPlan {
   int K, Kp, nchunks, stages, s;
@@ -59,7 +64,7 @@ inline int make_alt_plan(int K, int s, int code, AltPlan& p, int smem_limit = SM
   p.s = s;
   p.nchunks = (K + ABN - 1) / ABN;
   p.Kp = p.nchunks * ABN;
-  p.a_bytes = TILE_M * op_kb(0) * 16 * op_parts(0);
+  p.a_bytes = 2 * APART;
   p.chunk_bytes = ABN * op_kb(0) * 16 * op_parts(0);
   uint32_t off = 0;
   auto take = [&](uint32_t bytes) {
@@ -97,7 +102,6 @@ __device__ __forceinline__ int alt_dim(int u, int q) { return 16 * (q >> 2) + 4 
 // Sub-lane u's 12 values (TF32 hi, lo) into the A operand: dims 16k + 4u .. are
 // K block 4k + u.
 __device__ __forceinline__ void write_a_alt(uint8_t* A, int row, int u, const float (&r)[12]) {
-  constexpr uint32_t LBO = TILE_M * 16, PART = TILE_M * 12 * 16;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int kb = 4 * k + u;
@@ -110,8 +114,8 @@ __device__ __forceinline__ void write_a_alt(uint8_t* A, int row, int u, const fl
     lo.y = to_tf32(r[4 * k + 1] - hi.y);
     lo.z = to_tf32(r[4 * k + 2] - hi.z);
     lo.w = to_tf32(r[4 * k + 3] - hi.w);
-    *reinterpret_cast<float4*>(A + kb * LBO + row * 16) = hi;
-    *reinterpret_cast<float4*>(A + PART + kb * LBO + row * 16) = lo;
+    *reinterpret_cast<float4*>(A + kb * ALBO + row * 16) = hi;
+    *reinterpret_cast<float4*>(A + APART + kb * ALBO + row * 16) = lo;
   }
 }
 
@@ -269,14 +273,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
             tc_fence_after();
             const uint32_t ta = tmem_base;
             {
-              constexpr uint32_t LBO = TILE_M * 16, SBO = 128, PART = TILE_M * 12 * 16;
+              constexpr uint32_t SBO = 128;
               const uint32_t sa = smem_u32(smem + p.off_stage);
 #pragma unroll
               for (int part = 0; part < 2; ++part)
 #pragma unroll
                 for (int kk = 0; kk < 6; ++kk)
                   tmem_cp_128x256b(ta + part * 48 + kk * 8,
-                                   umma_smem_desc(sa + part * PART + kk * 2 * LBO, LBO, SBO));
+                                   umma_smem_desc(sa + part * APART + kk * 2 * ALBO, ALBO, SBO));
               tc_commit(bar_stage);
               const long long W1 = prof_any ? clock64() : 0;
               if (!mbar_wait(bar_stage, static_cast<uint32_t>(job & 1), a.budget)) {
