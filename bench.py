@@ -27,16 +27,11 @@ sys.path.insert(0, ROOT)
 METRIC = ("OMP Gaussians/s at K=1024,s=8, learned+BF16 vs plain at equal RMSE; decode GB/s")
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
-# DRAM bytes (read + write) per signal of the FP32 encoder, from one ncu capture of
-# encode_alt_kernel at N = 1,000,000, K = 1024, s = 8 (185.25 MB read + 36.88 MB
-# written); the traffic grows with the number of signals, so a launch over N
-# signals moves N times it.
-ENCODE_TRAFFIC = {(1024, 8, "fp32"): (185.253376e6 + 36.877824e6) / 1_000_000}
-
-# the encoder variant the default launch picks at K = 1024, s = 8 per precision
-ENCODE_KERNEL = {"fp32": "encode_alt_kernel", "bf16": "encode_pair_kernel", "fp8": "encode_pair_kernel",
-                 "bf16_qw": "encode_pair_kernel", "fp8_qw": "encode_pair_kernel"}
-
+# DRAM bytes (read + write) per signal of the encoder, keyed by (K, s, kernel
+# variant), from one ncu capture at N = 1,000,000; the traffic grows with the
+# number of signals, so a launch over N signals moves N times it.  A kernel
+# without a capture of its current form reports null.
+ENCODE_TRAFFIC = {}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -966,7 +961,11 @@ def main():
     # the kernel is timed per launch inside a 23 ms step, so the burst peak applies
     peaks, src = load_peaks()
     bf16 = float(peaks["bf16_tflops"])
-    if a.precision == "fp32":
+    variant = api.encode_variant(K, s, a.precision)
+    if a.precision == "fp32" and variant == 5:
+        peak = bf16 / 3.0
+        peak_note = "FP16 dense (= bf16 burst) / 3 for the three-product FP16 split"
+    elif a.precision == "fp32":
         peak = bf16 * TF32_PER_BF16 / 3.0
         peak_note = "TF32 dense (bf16 burst x 1.1/2.25) / 3 for the 3xTF32 split"
     elif a.precision in ("bf16", "bf16_qw"):
@@ -1026,9 +1025,9 @@ def main():
         "omp": omp,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": (ENCODE_TRAFFIC[(K, s, a.precision)] * N
-                                 if (K, s, a.precision) in ENCODE_TRAFFIC else None),
-                     "kernel": ENCODE_KERNEL.get(a.precision, "encode_kernel") + " (prep+gram included in the timing)",
+                     "traffic": (ENCODE_TRAFFIC[(K, s, variant)] * N
+                                 if (K, s, variant) in ENCODE_TRAFFIC else None),
+                     "kernel": api.ENCODE_VARIANTS.get(variant, "encode_kernel") + " (prep+gram included in the timing)",
                      "peak_source": f"{src}: {peak_note}"},
         "decode_roofline": {"bound": "shared-memory wavefronts", "achieved": dec_gbs, "unit": "GB/s",
                             "hbm_peak": float(peaks["hbm_gbs"]),

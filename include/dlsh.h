@@ -50,7 +50,15 @@ extern "C" {
 #define DLSH_ERR_DEVICE      (-6) /* a kernel flagged invalid data            */
 
 /* ---- correlation precision of the OMP atom selection (D^T r) --------- */
-#define DLSH_PREC_FP32 0 /* "plain FP32": 3xTF32 split on tcgen05, FP32 accumulate */
+#define DLSH_PREC_FP32 0 /* "plain FP32": each operand split into a high and a
+                            low part of 11 significant bits and D^T r taken as
+                            hi.hi + hi.lo + lo.hi on tcgen05 with FP32
+                            accumulation (about 22 significant bits).  The
+                            encoder for s <= 8 splits into FP16 parts of a
+                            power-of-two scaled copy (the residual per row,
+                            D by 256) -- twice the tensor rate and half the
+                            operand bytes of TF32 parts; the other encoders
+                            and dlsh_correlate split into TF32 parts        */
 #define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; each row's exact
                             low-precision top 4 (|c| truncated below the bits
                             that carry the column, then the smaller atom index)
@@ -92,7 +100,7 @@ unsigned long long dlsh_kernel_launches(void);
  * numerically dependent on the selected ones (Cholesky pivot^2 <= 1e-6).
  *
  * D [K*d] FP32, X [N*d] FP32 (16-byte aligned), d must be 45, 1 <= K <= 65535,
- * 1 <= s <= 32 (s <= 16 for DLSH_PREC_FP32), N >= 0.
+ * 1 <= s <= 16, N >= 0.
  * Outputs: idx [N*s], coef [N*s], nnz [N], resid_sq [N] (||r||^2; may be NULL).
  * Workspace: dlsh_encode_workspace_size(K, d, s, precision) bytes.
  */
@@ -103,21 +111,35 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                 void* stream, int flags);
 
 /*
- * dlsh_encode with per-phase timing: identical results, plus ten counters in
- * `cycles` (device, uint64[10], zeroed by the call) summed over all CTAs, in SM
- * clock cycles.  From the first selection/solver thread: waiting for the
+ * The encoder kernel dlsh_encode runs for (K, s, precision) with the built-in
+ * choice (no tuning record): 1 one tile per CTA, 2 two tiles on two warp
+ * groups, 3 two tiles served in turn, 4 / 5 two tiles with selection and solver
+ * warps (TF32 / FP16 parts); 0 if the configuration is unsupported.  A record
+ * from dlsh_autotune_encode overrides this choice.
+ */
+int dlsh_encode_variant(int K, int s, int precision);
+
+/*
+ * dlsh_encode with per-phase timing: identical results, plus twelve counters in
+ * `cycles` (device, uint64[12], zeroed by the call) summed over all CTAs, in SM
+ * clock cycles; counter 11 names the kernel that ran (1 one tile per CTA, 3 two
+ * tiles served in turn, 4 / 5 two tiles with selection and solver warps).  The call
+ * runs the kernel dlsh_encode would run, except that BF16/FP8 use the one-tile
+ * kernel.  One tile (1): from the first selection/solver thread, waiting for the
  * tensor cores, the selection phase (including that wait), the barrier after
  * selection, the solver phase, the barrier after the solver, and the number of
- * OMP iterations counted.  From the MMA-issuing thread: waiting for the A
- * operand (the residual), for a dictionary chunk to land, and for a TMEM
- * buffer to be released.  From the TMA-producing thread: waiting for a free
- * ring stage.  The call runs the kernel dlsh_encode would run, except that
- * BF16/FP8 use the one-tile kernel; with FP32 and s <= 8 that is the kernel
- * serving two tiles in turn, whose counters are: selection waiting for the
- * tensor cores, selection (including that wait), solver, solver waiting for
- * the staging area, tile iterations, 0, then from the MMA thread: waiting for
- * a residual, for a dictionary chunk, for an accumulator buffer, and for the
- * copy of the residual into tensor memory.
+ * OMP iterations counted; from the MMA-issuing thread, waiting for the A
+ * operand (the residual), for a dictionary chunk to land, and for a TMEM buffer
+ * to be released; from the TMA-producing thread, waiting for a free ring stage.
+ * Two tiles in turn (3): selection waiting for the tensor cores, selection
+ * (including that wait), solver, solver waiting for the staging area, tile
+ * iterations, 0, then from the MMA thread: waiting for a residual, for a
+ * dictionary chunk, for an accumulator buffer, and for the copy of the residual
+ * into tensor memory.  Selection and solver warps (4): selection waiting for the
+ * tensor cores, selection per job (including its waits), solver per job
+ * (including its waits), solver waiting for the staging area, jobs, solver
+ * waiting for candidates, the four MMA-thread counters as for (3), and
+ * selection waiting for the solver to take its previous candidates (5 as 4).
  */
 int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
                         int s, float eps, int precision, uint16_t* idx,

@@ -48,6 +48,7 @@ SIGNATURES = {
     "dlsh_num_sms": (c_int, []),
     "dlsh_kernel_launches": (ctypes.c_ulonglong, []),
     "dlsh_encode_workspace_size": (c_size_t, [c_int, c_int, c_int, c_int]),
+    "dlsh_encode_variant": (c_int, [c_int, c_int, c_int]),
     "dlsh_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P, P,
                             c_size_t, P, c_int]),
     "dlsh_encode_profile": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_float, c_int, P, P, P, P,

@@ -119,6 +119,17 @@ def encode(D, X, s: int, eps: float = 0.0, precision="fp32", sync: bool = False,
     return idx, coef, nnz, resid
 
 
+ENCODE_VARIANTS = {1: "encode_kernel (one tile per CTA)", 2: "encode_pair_kernel",
+                   3: "encode_alt_kernel", 4: "encode_split_kernel (TF32 parts)",
+                   5: "encode_split_kernel (FP16 parts)"}
+
+
+def encode_variant(K: int, s: int, precision="fp32") -> int:
+    """The encoder kernel encode() runs for (K, s, precision) without a tuning
+    record (see dlsh_encode_variant); 0 if unsupported."""
+    return int(_lib.lib().dlsh_encode_variant(int(K), int(s), _prec(precision)))
+
+
 def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
     """encode() plus per-phase SM-cycle counters of the encoder (see dlsh.h)."""
     D = _to_device(D, torch.float32)
@@ -128,7 +139,7 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
     coef = torch.empty((N, s), dtype=torch.float32, device=X.device)
     nnz = torch.empty((N,), dtype=torch.uint8, device=X.device)
     resid = torch.empty((N,), dtype=torch.float32, device=X.device)
-    cyc = torch.zeros((10,), dtype=torch.int64, device=X.device)
+    cyc = torch.zeros((12,), dtype=torch.int64, device=X.device)
     L = _lib.lib()
     need = L.dlsh_encode_workspace_size(K, D.shape[1], s, _prec(precision))
     ws = workspace(need, key="encode")
@@ -136,14 +147,21 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
                                _p(idx), _p(coef), _p(nnz), _p(resid), _p(ws), ws.numel(), _p(cyc),
                                _stream(), FLAG_SYNC)
     _check(rc, "dlsh_encode_profile")
-    if s <= 8 and _prec(precision) == 0 and cyc[5].item() == 0:
-        # the FP32 encoder with two tiles served in turn (see dlsh.h)
+    c = cyc.cpu().tolist()
+    variant = c[11]
+    if variant == 3:  # two tiles served in turn by all warps (see dlsh.h)
         names = ("sel_wait_mma", "selection", "solver", "solver_wait_staging", "tile_iterations",
                  "unused", "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "mma_wait_copy")
+    elif variant in (4, 5):  # two tiles, selection and solver warps (TF32 / FP16 products)
+        names = ("sel_wait_mma", "selection", "solver", "solver_wait_staging", "jobs",
+                 "solver_wait_cand", "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "mma_wait_copy",
+                 "sel_wait_solver")
     else:
         names = ("wait_mma", "selection", "barrier1", "solver", "barrier2", "iterations",
                  "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "tma_wait_stage")
-    return (idx, coef, nnz, resid), dict(zip(names, cyc.cpu().tolist()))
+    out = dict(zip(names, c))
+    out["variant"] = variant
+    return (idx, coef, nnz, resid), out
 
 
 def correlate(D, R, precision="fp32", sync: bool = True):

@@ -243,6 +243,18 @@ __device__ __forceinline__ void umma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tme
       : "memory");
 }
 
+// The same with FP16 operands (kind::f16, A and B both F16): A is 128 lanes x
+// K/2 columns, each 32-bit column holding two consecutive K elements.
+__device__ __forceinline__ void umma_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Shared memory -> tensor memory: a 128-row x 256-bit matrix (described like a
 // K-major MMA operand, two 16-byte core-matrix columns) into TMEM lanes 0..127,
 // eight 32-bit columns from taddr.  Asynchronous; ordered with the issuing

@@ -23,6 +23,7 @@
 // Correlation precisions: FP32 (3xTF32 split hi*hi + hi*lo + lo*hi, FP32
 // accumulate), BF16, FP8 E4M3 with per-row and per-atom scales.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -63,6 +64,9 @@ __device__ __forceinline__ void with_t(int t, F&& f) {
   }
 }
 constexpr float FP8_MAX = 448.f;
+// Operand-image code of the FP16-split FP32 format (prep_kernel): hi and lo
+// FP16 parts of 256 * D, 6 K blocks of 8 elements each
+constexpr int OPF16X2 = 3;
 
 // 16-byte K-blocks per operand row and operand parts, per precision.
 __host__ __device__ constexpr int op_kb(int prec) { return prec == 0 ? 12 : (prec == 1 ? 6 : 4); }
@@ -302,6 +306,18 @@ __global__ void prep_kernel(const float* __restrict__ D, int K, int Kp, int BN, 
       const uint32_t o = kb * BN * 16 + n * 16 + (k % 4) * 4;
       *reinterpret_cast<float*>(base + o) = hi;
       *reinterpret_cast<float*>(base + BN * 12 * 16 + o) = lo;
+    }
+  } else if (prec == OPF16X2) {
+    // FP32 as two FP16 parts of 256 * v (the scale keeps the low part normal
+    // down to |v| of about 2^-11; unit-norm atoms stay far below FP16's range)
+    if (k < DPAD) {
+      const float sv = 256.f * v;
+      const __half hi = __float2half_rn(sv);
+      const __half lo = __float2half_rn(sv - __half2float(hi));
+      const int kb = k / 8;
+      const uint32_t o = kb * BN * 16 + n * 16 + (k % 8) * 2;
+      *reinterpret_cast<__half*>(base + o) = hi;
+      *reinterpret_cast<__half*>(base + BN * 6 * 16 + o) = lo;
     }
   } else {
     const int kb = k / 16;
@@ -1102,8 +1118,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
   }
   tc_fence_before();
   __syncthreads();
-  if (prof_any && tid == 0)
+  if (prof_any && tid == 0) {
     for (int k = 0; k < 10; ++k) atomicAdd(a.prof + k, pcs[k]);
+    if (blockIdx.x == 0) a.prof[11] = 1;  // the variant that ran: one tile per CTA
+  }
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem_base, 512);
@@ -1112,6 +1130,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
 
 #include "encode_pair.cuh"
 #include "encode_alt.cuh"
+#include "encode_split.cuh"
 
 // ---------------------------------------------------------------------------
 // Correlation only: C = R D^T through the same operand packing and MMAs.
@@ -1267,6 +1286,16 @@ static int launch_alt(const AltArgs& a, int grid, cudaStream_t st) {
   return check_launch("dlsh_encode: launch");
 }
 
+template <bool F16>
+static int launch_split(const SplitArgs& a, int grid, cudaStream_t st) {
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(encode_split_kernel<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     SMEM_LIMIT),
+                "dlsh_encode: cudaFuncSetAttribute");
+  encode_split_kernel<F16><<<grid, NTHREADS, a.p.smem, st>>>(a);
+  count_launches(1);
+  return check_launch("dlsh_encode: launch");
+}
+
 // The workspace fields (padded dictionary, Gram, operand image in 64-atom
 // chunks) of the two-tile kernel, in the single-tile plan's form.
 static void pair_prep_plan(const PairPlan& pp, Plan& p) {
@@ -1317,6 +1346,14 @@ static int prepare(const float* D, const Plan& p, const Ws& w, bool gram, cudaSt
 
 }  // namespace enc
 
+// The built-in encoder choice among the kernels whose plans fit: 5 (FP32 on
+// selection and solver warps, FP16 parts), else 3 (FP32, two tiles in turn),
+// else 2 (BF16/FP8 on two warp groups), else 0 (one tile; the chunk width
+// from choose_bn).
+static int default_variant(bool split16_ok, bool alt_ok, bool pair_lowp_ok) {
+  return split16_ok ? 5 : (alt_ok ? 3 : (pair_lowp_ok ? 2 : 0));
+}
+
 // Entry points shared with the learning loop (learn.cu).
 int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, float eps, int prec,
                    uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq, void* ws,
@@ -1324,49 +1361,71 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
                    const long long* n_dev, int bn) {
   using namespace enc;
   // kernel variant (s <= 8): 2 = two tiles in flight on two warp groups,
-  // 3 = two tiles served in turn by all warps (FP32); 64 / 128 = one tile with
-  // that atom-chunk width; 0 = the tuned choice, else the default below
+  // 3 = two tiles served in turn by all warps (FP32), 4 / 5 = two tiles with
+  // the warps split into selection and solver groups (FP32 as three TF32 / three
+  // FP16 products); 64 / 128 = one tile with that atom-chunk width; 0 = the
+  // tuned choice, else the default below
   int choice = bn != 0 ? bn : tuned_bn(K, s, prec);
   PairPlan pp;
   AltPlan ap;
+  SplitPlan sp, sp16;
   const bool pair_ok = !prof && make_pair_plan(K, s, prec, pp) == DLSH_OK;
   const bool alt_ok = make_alt_plan(K, s, prec, ap) == DLSH_OK;
+  const bool split_ok = make_split_plan(K, s, prec, sp, false) == DLSH_OK;
+  const bool split16_ok = make_split_plan(K, s, prec, sp16, true) == DLSH_OK;
   // default (measured at N = 3M, K = 1024): BF16/FP8, bound by selection and
-  // solver, on two warp groups (1.2-1.3x faster than one tile); FP32, bound by
-  // its correlations, with all warps alternating between two tiles (1.08x)
-  if (choice == 0) choice = alt_ok ? 3 : (pair_ok && pp.prec != 0 ? 2 : 0);
+  // solver, on two warp groups (1.2-1.3x faster than one tile); FP32 on
+  // selection and solver warps with three FP16 products (1.9x faster than one
+  // tile at s = 8)
+  if (choice == 0) choice = default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0);
   if (choice == 2 && !pair_ok) choice = 0;
   if (choice == 3 && !alt_ok) choice = 0;
-  if (choice == 3) {
+  if (choice == 4 && !split_ok) choice = 0;
+  if (choice == 5 && !split16_ok) choice = 0;
+  if (choice == 3 || choice == 4 || choice == 5) {
     Plan p;  // the one-tile encoder's 128-atom FP32 operand image
     if (make_plan(K, s, prec, p, 128) != DLSH_OK || p.BN != 128)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d does not fit", K, s);
     Ws w;
     carve(ws, p, w);
     if (status_out) *status_out = w.status;
-    int rc = prepare(D, p, w, true, st);
+    Plan pi = p;  // the operand image: TF32 hi / lo, or FP16 hi / lo (half the bytes)
+    if (choice == 5) {
+      pi.prec = OPF16X2;
+      pi.chunk_bytes = sp16.chunk_bytes;
+    }
+    int rc = prepare(D, pi, w, true, st);
     if (rc) return rc;
     if (N == 0 && !n_dev) return DLSH_OK;
-    AltArgs a{};
-    a.X = X;
-    a.N = N;
-    a.D32p = w.D32p;
-    a.G = w.G;
-    a.img = w.img;
-    a.idx = idx;
-    a.coef = coef;
-    a.nnz = nnz;
-    a.resid_sq = resid_sq;
-    a.eps = eps;
-    a.status = w.status;
-    a.budget = kWaitBudget;
-    a.n_dev = n_dev;
-    a.prof = prof;
-    a.p = ap;
+    auto fill = [&](auto& a) {
+      a.X = X;
+      a.N = N;
+      a.D32p = w.D32p;
+      a.G = w.G;
+      a.img = w.img;
+      a.idx = idx;
+      a.coef = coef;
+      a.nnz = nnz;
+      a.resid_sq = resid_sq;
+      a.eps = eps;
+      a.status = w.status;
+      a.budget = kWaitBudget;
+      a.n_dev = n_dev;
+      a.prof = prof;
+    };
     const int ntiles = static_cast<int>((N + TILE_M - 1) / TILE_M);
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
     const int grid = (!n_dev && (ntiles + 1) / 2 < sms) ? ((ntiles + 1) / 2 > 0 ? (ntiles + 1) / 2 : 1) : sms;
+    if (choice == 4 || choice == 5) {
+      SplitArgs a{};
+      fill(a);
+      a.p = choice == 5 ? sp16 : sp;
+      return choice == 5 ? launch_split<true>(a, grid, st) : launch_split<false>(a, grid, st);
+    }
+    AltArgs a{};
+    fill(a);
+    a.p = ap;
     return launch_alt(a, grid, st);
   }
   if (choice == 2) {
@@ -1405,7 +1464,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
     return pp.top4 ? launch_pair<2, true>(a, grid, st) : launch_pair<2, false>(a, grid, st);
   }
   Plan p;
-  if (make_plan(K, s, prec, p, (choice == 2 || choice == 3) ? 0 : choice) != DLSH_OK)
+  if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 5) ? 0 : choice) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
   Ws w;
@@ -1491,6 +1550,21 @@ size_t dlsh_encode_workspace_size(int K, int d, int s, int precision) {
   return dlsh::encode_ws_bytes(K, s, precision);
 }
 
+int dlsh_encode_variant(int K, int s, int precision) {
+  using namespace dlsh::enc;
+  if (K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || precision < 0 || precision > 4) return 0;
+  PairPlan pp;
+  AltPlan ap;
+  SplitPlan sp16;
+  Plan p;
+  const bool pair_ok = make_pair_plan(K, s, precision, pp) == DLSH_OK;
+  const bool alt_ok = make_alt_plan(K, s, precision, ap) == DLSH_OK;
+  const bool split16_ok = make_split_plan(K, s, precision, sp16, true) == DLSH_OK;
+  const int v = dlsh::default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0);
+  if (v != 0) return v;
+  return make_plan(K, s, precision, p, 0) == DLSH_OK ? 1 : 0;
+}
+
 int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s, float eps,
                 int precision, uint16_t* idx, float* coef, uint8_t* nnz, float* resid_sq,
                 void* ws, size_t ws_bytes, void* stream, int flags) {
@@ -1529,7 +1603,7 @@ int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
   rc = check_workspace(ws, ws_bytes, encode_ws_bytes(K, s, precision), "dlsh_encode_profile");
   if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  DLSH_CUDA_TRY(cudaMemsetAsync(cycles, 0, 10 * sizeof(unsigned long long), st),
+  DLSH_CUDA_TRY(cudaMemsetAsync(cycles, 0, 12 * sizeof(unsigned long long), st),
                 "dlsh_encode_profile: reset");
   uint32_t* status = nullptr;
   rc = encode_enqueue(D, K, X, N, s, eps, precision, idx, coef, nnz, resid_sq, ws, st, &status,
@@ -1648,12 +1722,14 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
   DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
   int best = 0;
   float best_ms = 0.f;
-  for (int bn : {64, 128, 2, 3}) {
+  for (int bn : {64, 128, 2, 3, 4, 5}) {
     Plan p;
     PairPlan pp;
     AltPlan ap;
+    SplitPlan sp;
     if (bn == 2 ? make_pair_plan(K, s, precision, pp) != DLSH_OK
                 : bn == 3 ? make_alt_plan(K, s, precision, ap) != DLSH_OK
+                : bn == 4 || bn == 5 ? make_split_plan(K, s, precision, sp, bn == 5) != DLSH_OK
                           : (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn))
       continue;
     // force this width for the trial runs
@@ -1740,8 +1816,8 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
   if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
-  if (bn != 0 && bn != 2 && bn != 3 && bn != 64 && bn != 128)
-    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2, 3, 64 or 128");
+  if (bn != 0 && (bn < 2 || bn > 5) && bn != 64 && bn != 128)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2, 3, 4, 5, 64 or 128");
   for (int i = 0; i < n; ++i) {
     const dlsh_scene& x = sc[i];
     if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
@@ -1749,7 +1825,7 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
       return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
     Plan p;
-    if (make_plan(x.K, x.s, prec, p, (bn == 2 || bn == 3) ? 0 : bn) != DLSH_OK)
+    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 5) ? 0 : bn) != DLSH_OK)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
                        i, x.K, x.s);
   }

@@ -119,6 +119,53 @@ __device__ __forceinline__ void write_a_alt(uint8_t* A, int row, int u, const fl
   }
 }
 
+// The FP16-split form of the same operand (the split encoder's F16 variant):
+// the residual of a row scaled by a power of two, as FP16 hi and lo parts in
+// K blocks of 8 elements.  Sub-lane u's dims 16k + 4u .. 16k + 4u + 3 are the
+// half (u & 1) of K block 2k + (u >> 1).  A K-block stride of 2048 + 64 bytes
+// puts the 8-byte stores of a half-warp (four rows, four sub-lanes) on sixteen
+// different bank pairs.
+constexpr uint32_t ALBO16 = TILE_M * 16 + 64;
+constexpr uint32_t APART16 = 6 * ALBO16;
+__device__ __forceinline__ void write_a_f16(uint8_t* A, int row, int u, const float (&r)[12], float scale) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint32_t off = static_cast<uint32_t>(2 * k + (u >> 1)) * ALBO16 + row * 16 + (u & 1) * 8;
+    __half h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float v = r[4 * k + j] * scale;
+      h[j] = __float2half_rn(v);
+      l[j] = __float2half_rn(v - __half2float(h[j]));
+    }
+    uint2 ph, pl;
+    ph.x = static_cast<uint32_t>(__half_as_ushort(h[0])) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
+    ph.y = static_cast<uint32_t>(__half_as_ushort(h[2])) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
+    pl.x = static_cast<uint32_t>(__half_as_ushort(l[0])) | (static_cast<uint32_t>(__half_as_ushort(l[1])) << 16);
+    pl.y = static_cast<uint32_t>(__half_as_ushort(l[2])) | (static_cast<uint32_t>(__half_as_ushort(l[3])) << 16);
+    *reinterpret_cast<uint2*>(A + off) = ph;
+    *reinterpret_cast<uint2*>(A + APART16 + off) = pl;
+  }
+}
+
+// Passes P0..P1-1 of one chunk of 3xFP16 MMAs (A hi, lo in tensor-memory
+// columns 0..23, 24..47; N = 128): pass 0 hi.hi, pass 1 hi.lo(D), pass 2 lo.hi.
+template <int P0, int P1>
+__device__ __forceinline__ void issue_f16_passes(uint32_t tmem_d, uint32_t a_tmem, uint32_t b_addr) {
+  constexpr uint32_t idesc = umma_idesc(0, 0, TILE_M, ABN);
+  constexpr uint32_t B_LBO = ABN * 16, SBO = 128, B_PART = ABN * 6 * 16;
+#pragma unroll
+  for (int pass = P0; pass < P1; ++pass) {
+    const uint32_t ao = pass == 2 ? 24u : 0u;
+    const uint32_t bo = pass == 1 ? B_PART : 0u;
+#pragma unroll
+    for (int ks = 0; ks < 3; ++ks) {
+      const uint64_t bd = umma_smem_desc(b_addr + bo + ks * 2 * B_LBO, B_LBO, SBO);
+      umma_f16_tmem_a(tmem_d, a_tmem + ao + ks * 8, bd, idesc, (pass | ks) != 0);
+    }
+  }
+}
+
 // Passes P0..P1-1 of one chunk of 3xTF32 MMAs, A (hi, lo) from tensor memory,
 // N = 128: pass 0 hi(r).hi(D), pass 1 hi(r).lo(D), pass 2 lo(r).hi(D).
 template <int P0, int P1>
@@ -135,6 +182,168 @@ __device__ __forceinline__ void issue_alt_passes(uint32_t tmem_d, uint32_t a_tme
       umma_tf32_tmem_a(tmem_d, a_tmem + ao + ks * 8, bd, idesc, (pass | ks) != 0);
     }
   }
+}
+
+// Barriers and shared state of the dictionary producer and the MMA issuer,
+// shared by the two-tile FP32 encoders.
+struct AltSync {
+  uint64_t* bar_a;       // [2] a tile slot's A operand is staged
+  uint64_t* bar_full;    // [ABUF] an accumulator buffer holds a chunk's correlations
+  uint64_t* bar_empty;   // [ABUF] an accumulator buffer has been read
+  uint64_t* bar_stage;   // the staged A operand has been copied into tensor memory
+  uint64_t* bar_dfull;   // [stages] a dictionary chunk has landed in the ring
+  uint64_t* bar_dempty;  // [stages] the MMAs have finished with a ring stage
+  volatile long long* stage_done;  // the last job whose A copy has completed
+  unsigned long long* pcs;         // optional phase counters (6..9 are written here), or null
+};
+
+// One elected thread: chunk c of the packed dictionary image for every job, in
+// job order, through the ring; then waits until the MMAs have released the
+// last stages, so that no copy is in flight when the CTA exits.
+__device__ __forceinline__ void alt_produce(const AltSync& y, const uint8_t* img, uint8_t* ring, int stages,
+                                            uint32_t chunk_bytes, int nchunks, long long njobs,
+                                            uint32_t* status, long long budget) {
+  long long n = 0;
+  int st = 0;
+  uint32_t par = 1u;  // bar_dempty parity to wait for at stage st
+  bool ok = true;
+  for (long long j = 0; j < njobs && ok; ++j)
+    for (int c = 0; c < nchunks; ++c, ++n) {
+      if (!mbar_wait(&y.bar_dempty[st], par, budget)) {
+        flag_status(status, ST_TIMEOUT);
+        ok = false;
+        break;
+      }
+      mbar_arrive_expect_tx(&y.bar_dfull[st], chunk_bytes);
+      bulk_g2s(ring + static_cast<size_t>(st) * chunk_bytes, img + static_cast<size_t>(c) * chunk_bytes,
+               chunk_bytes, &y.bar_dfull[st]);
+      if (++st == stages) {
+        st = 0;
+        par ^= 1u;
+      }
+    }
+  for (long long f = n > stages ? n - stages : 0; ok && f < n; ++f) {
+    if (!mbar_wait(&y.bar_dempty[f % stages], static_cast<uint32_t>((f / stages) & 1), budget)) {
+      flag_status(status, ST_TIMEOUT);
+      ok = false;
+    }
+  }
+}
+
+// One elected thread: the jobs (slot 0, it), (slot 1, it), (slot 0, it + 1) ..
+// of K0 / K1 rounds of s iterations.  Each job waits for its staged residual,
+// for the previous job's MMAs (the A columns in tensor memory are shared),
+// copies the hi / lo residual into tensor memory (TF32: columns 0..95; F16:
+// 0..47), then runs the three-product MMAs of every chunk into the
+// accumulator buffers in turn.
+template <bool F16>
+__device__ __forceinline__ void alt_issue(const AltSync& y, uint32_t tmem_base, uint32_t acc0, uint32_t stage_addr,
+                                          uint32_t ring_addr, int stages, uint32_t chunk_bytes, int nchunks,
+                                          int K0, int K1, int s, uint32_t* status, long long budget) {
+  unsigned long long* pcs = y.pcs;
+  uint32_t aph[2] = {0u, 0u};
+  long long job = 0;
+  // the next chunk's ring stage and accumulator buffer with the parities of
+  // their bar_dfull / bar_full phases; the previous chunk's buffer
+  int st = 0, buf = 0, lbuf = -1;
+  uint32_t dpar = 0u, fpar = 0u, lfpar = 0u;
+  bool ok = true;
+  auto fail = [&]() {
+    flag_status(status, ST_TIMEOUT);
+    ok = false;
+  };
+  // the next chunk's resources: its dictionary chunk has landed and its
+  // accumulator buffer has been read
+  auto wait_chunk = [&]() -> bool {
+    const long long W2 = pcs ? clock64() : 0;
+    const bool okd = mbar_wait(&y.bar_dfull[st], dpar, budget);
+    const long long W3 = pcs ? clock64() : 0;
+    const bool oke = okd && mbar_wait(&y.bar_empty[buf], fpar ^ 1u, budget);
+    if (pcs) {
+      pcs[7] += W3 - W2;
+      pcs[8] += clock64() - W3;
+    }
+    return oke;
+  };
+  for (int k = 0; k < K0 && ok; ++k)
+    for (int it = 0; it < s && ok; ++it)
+      for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t, ++job) {
+        const long long W0 = pcs ? clock64() : 0;
+        if (!mbar_wait(&y.bar_a[t], aph[t], budget)) {
+          fail();
+          break;
+        }
+        if (pcs) pcs[6] += clock64() - W0;
+        aph[t] ^= 1u;
+        if (lbuf >= 0 && !mbar_wait(&y.bar_full[lbuf], lfpar, budget)) {
+          fail();
+          break;
+        }
+        tc_fence_after();
+        {
+          constexpr uint32_t SBO = 128;
+          if constexpr (F16) {
+#pragma unroll
+            for (int part = 0; part < 2; ++part)
+#pragma unroll
+              for (int kk = 0; kk < 3; ++kk)
+                tmem_cp_128x256b(tmem_base + part * 24 + kk * 8,
+                                 umma_smem_desc(stage_addr + part * APART16 + kk * 2 * ALBO16, ALBO16, SBO));
+          } else {
+#pragma unroll
+            for (int part = 0; part < 2; ++part)
+#pragma unroll
+              for (int kk = 0; kk < 6; ++kk)
+                tmem_cp_128x256b(tmem_base + part * 48 + kk * 8,
+                                 umma_smem_desc(stage_addr + part * APART + kk * 2 * ALBO, ALBO, SBO));
+          }
+          tc_commit(y.bar_stage);
+          const long long W1 = pcs ? clock64() : 0;
+          if (!mbar_wait(y.bar_stage, static_cast<uint32_t>(job & 1), budget)) {
+            fail();
+            break;
+          }
+          if (pcs) pcs[9] += clock64() - W1;
+          *y.stage_done = job;
+        }
+        if (!wait_chunk()) {
+          fail();
+          break;
+        }
+        for (int c = 0; c < nchunks; ++c) {
+          tc_fence_after();
+          const uint32_t d = tmem_base + acc0 + static_cast<uint32_t>(buf) * ABN;
+          const uint32_t b = ring_addr + static_cast<uint32_t>(st) * chunk_bytes;
+          if constexpr (F16)
+            issue_f16_passes<0, 2>(d, tmem_base, b);
+          else
+            issue_alt_passes<0, 2>(d, tmem_base, b);
+          // the next chunk's resources are checked while the last pass of
+          // this one runs, so the checks do not leave the tensor pipe idle
+          const int cst = st, cbuf = buf;
+          lbuf = buf;
+          lfpar = fpar;
+          if (++st == stages) {
+            st = 0;
+            dpar ^= 1u;
+          }
+          if (++buf == ABUF) {
+            buf = 0;
+            fpar ^= 1u;
+          }
+          const bool nok = c + 1 < nchunks ? wait_chunk() : true;
+          if constexpr (F16)
+            issue_f16_passes<2, 3>(d, tmem_base, b);
+          else
+            issue_alt_passes<2, 3>(d, tmem_base, b);
+          tc_commit(&y.bar_full[cbuf]);
+          tc_commit(&y.bar_dempty[cst]);
+          if (!nok) {
+            fail();
+            break;
+          }
+        }
+      }
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_constant__ AltArgs a) {
@@ -196,134 +405,17 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
   const uint32_t tmem_base = *tmem_slot;
   const uint32_t ring_addr = smem_u32(smem + p.off_ring);
 
+  const AltSync sy{bar_a, bar_full, bar_empty, bar_stage, bar_dfull, bar_dempty, stage_done, prof_any ? pcs : nullptr};
   if (warp == NEPI / 32 + 1) {
     // ------------------------------------------------ TMA producer
-    if (lane == 0) {
-      long long ring = 0;
-      int st = 0;
-      uint32_t par = 1u;  // bar_dempty parity to wait for at stage st
-      bool ok = true;
-      for (int k = 0; k < K0 && ok; ++k)
-        for (int it = 0; it < s && ok; ++it)
-          for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t)
-            for (int c = 0; c < p.nchunks; ++c, ++ring) {
-              if (!mbar_wait(&bar_dempty[st], par, a.budget)) {
-                flag_status(a.status, ST_TIMEOUT);
-                ok = false;
-                break;
-              }
-              mbar_arrive_expect_tx(&bar_dfull[st], p.chunk_bytes);
-              bulk_g2s(smem + p.off_ring + static_cast<size_t>(st) * p.chunk_bytes,
-                       a.img + static_cast<size_t>(c) * p.chunk_bytes, p.chunk_bytes, &bar_dfull[st]);
-              if (++st == p.stages) {
-                st = 0;
-                par ^= 1u;
-              }
-            }
-      // drain: the last `stages` chunks' MMAs must complete before the CTA exits
-      for (long long f = ring > p.stages ? ring - p.stages : 0; ok && f < ring; ++f) {
-        if (!mbar_wait(&bar_dempty[f % p.stages], static_cast<uint32_t>((f / p.stages) & 1), a.budget)) {
-          flag_status(a.status, ST_TIMEOUT);
-          ok = false;
-        }
-      }
-    }
+    if (lane == 0)
+      alt_produce(sy, a.img, smem + p.off_ring, p.stages, p.chunk_bytes, p.nchunks,
+                  static_cast<long long>(s) * (K0 + K1), a.status, a.budget);
   } else if (warp == NEPI / 32) {
     // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      uint32_t aph[2] = {0u, 0u};
-      long long job = 0;
-      // the next chunk's ring stage and accumulator buffer with the parities
-      // of their bar_dfull / bar_full phases; the previous chunk's buffer
-      int st = 0, buf = 0, lbuf = -1;
-      uint32_t dpar = 0u, fpar = 0u, lfpar = 0u;
-      bool ok = true;
-      // waits until chunk resources (st, buf) are ready: its dictionary chunk
-      // has landed and its accumulator buffer has been read
-      auto wait_chunk = [&]() -> bool {
-        const long long W2 = prof_any ? clock64() : 0;
-        const bool okd = mbar_wait(&bar_dfull[st], dpar, a.budget);
-        const long long W3 = prof_any ? clock64() : 0;
-        const bool oke = okd && mbar_wait(&bar_empty[buf], fpar ^ 1u, a.budget);
-        if (prof_any) {
-          pcs[7] += W3 - W2;
-          pcs[8] += clock64() - W3;
-        }
-        if (!oke) flag_status(a.status, ST_TIMEOUT);
-        return oke;
-      };
-      for (int k = 0; k < K0 && ok; ++k)
-        for (int it = 0; it < s && ok; ++it)
-          for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t, ++job) {
-            const long long W0 = prof_any ? clock64() : 0;
-            if (!mbar_wait(&bar_a[t], aph[t], a.budget)) {
-              flag_status(a.status, ST_TIMEOUT);
-              ok = false;
-              break;
-            }
-            if (prof_any) pcs[6] += clock64() - W0;
-            aph[t] ^= 1u;
-            // the A columns are shared by the jobs: the previous job's last MMAs
-            // (and so all of its MMAs) must have completed before the copy
-            if (lbuf >= 0 && !mbar_wait(&bar_full[lbuf], lfpar, a.budget)) {
-              flag_status(a.status, ST_TIMEOUT);
-              ok = false;
-              break;
-            }
-            tc_fence_after();
-            const uint32_t ta = tmem_base;
-            {
-              constexpr uint32_t SBO = 128;
-              const uint32_t sa = smem_u32(smem + p.off_stage);
-#pragma unroll
-              for (int part = 0; part < 2; ++part)
-#pragma unroll
-                for (int kk = 0; kk < 6; ++kk)
-                  tmem_cp_128x256b(ta + part * 48 + kk * 8,
-                                   umma_smem_desc(sa + part * APART + kk * 2 * ALBO, ALBO, SBO));
-              tc_commit(bar_stage);
-              const long long W1 = prof_any ? clock64() : 0;
-              if (!mbar_wait(bar_stage, static_cast<uint32_t>(job & 1), a.budget)) {
-                flag_status(a.status, ST_TIMEOUT);
-                ok = false;
-                break;
-              }
-              if (prof_any) pcs[9] += clock64() - W1;
-              *stage_done = job;
-            }
-            if (!wait_chunk()) {
-              ok = false;
-              break;
-            }
-            for (int c = 0; c < p.nchunks; ++c) {
-              tc_fence_after();
-              const uint32_t d = tmem_base + ACC0 + static_cast<uint32_t>(buf) * ABN;
-              const uint32_t b = ring_addr + static_cast<uint32_t>(st) * p.chunk_bytes;
-              issue_alt_passes<0, 2>(d, ta, b);
-              // the next chunk's resources are checked while the last pass of
-              // this one runs, so the checks do not leave the tensor pipe idle
-              const int cst = st, cbuf = buf;
-              lbuf = buf;
-              lfpar = fpar;
-              if (++st == p.stages) {
-                st = 0;
-                dpar ^= 1u;
-              }
-              if (++buf == ABUF) {
-                buf = 0;
-                fpar ^= 1u;
-              }
-              const bool nok = c + 1 < p.nchunks ? wait_chunk() : true;
-              issue_alt_passes<2, 3>(d, ta, b);
-              tc_commit(&bar_full[cbuf]);
-              tc_commit(&bar_dempty[cst]);
-              if (!nok) {
-                ok = false;
-                break;
-              }
-            }
-          }
-    }
+    if (lane == 0)
+      alt_issue<false>(sy, tmem_base, ACC0, smem_u32(smem + p.off_stage), ring_addr, p.stages, p.chunk_bytes, p.nchunks,
+                K0, K1, s, a.status, a.budget);
   } else {
     // ------------------------------------------------ selection + solver, two tiles in turn
     uint8_t* A = smem + p.off_stage;
@@ -668,8 +760,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
   }
   tc_fence_before();
   __syncthreads();
-  if (prof_any && tid == 0)
+  if (prof_any && tid == 0) {
     for (int q = 0; q < 10; ++q) atomicAdd(a.prof + q, pcs[q]);
+    if (blockIdx.x == 0) a.prof[11] = 3;  // the variant that ran: two tiles served in turn
+  }
   if (warp == 0) {
     tc_fence_after();
     tmem_dealloc(tmem_base, 512);

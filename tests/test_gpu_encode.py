@@ -192,11 +192,12 @@ def test_deterministic(lib):
         np.testing.assert_array_equal(u, v)
 
 
-@pytest.mark.parametrize("variant", [2, 3, 64, 128])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 64, 128])
 @pytest.mark.parametrize("N,K,s", [(3000, 256, 8), (2000, 1024, 8), (1500, 300, 4), (777, 64, 1)])
 def test_fp32_kernel_variants_match_oracle(lib, variant, N, K, s):
     """Every FP32 encoder the autotuner can pick (two tiles on two warp groups,
-    two tiles served in turn, one tile with 64- or 128-atom chunks): supports
+    two tiles served in turn, two tiles with selection and solver warps as three
+    TF32 or three FP16 products, one tile with 64- or 128-atom chunks): supports
     identical to the oracle's wherever its every selection margin exceeds 1e-4,
     RMSE within 1e-4 relative."""
     Dh = synth.hidden_dictionary(K, 0)
@@ -215,3 +216,27 @@ def test_fp32_kernel_variants_match_oracle(lib, variant, N, K, s):
     r_got = np.sqrt(resid.cpu().numpy().astype(np.float64).sum() / (N * 45))
     r_ref = np.sqrt(ref["resid_sq"].sum() / (N * 45))
     assert abs(r_got - r_ref) <= 1e-4 * r_ref, (r_got, r_ref)
+
+
+@pytest.mark.parametrize("variant", [3, 4, 5])
+def test_two_tile_fp32_encoders_over_several_rounds(lib, variant):
+    """40,077 signals are 314 tiles: on 152 CTAs of two tile slots some CTAs
+    take a third tile in a round of their own (slot 0 only) and the last tile
+    is ragged.  Supports as the oracle's wherever every selection margin exceeds
+    1e-4, residuals within 1e-4 relative per signal."""
+    N, K, s = 40077, 256, 8
+    Dh = synth.hidden_dictionary(K, 0)
+    X = synth.signals(N, Dh, s, 3).astype(np.float64)
+    D = synth.hidden_dictionary(K, 7)
+    ref = oomp.omp(D.astype(np.float32).astype(np.float64), X, s)
+    sc = [{"D": torch.from_numpy(D.astype(np.float32)).cuda(),
+           "X": torch.from_numpy(X.astype(np.float32)).cuda(), "s": s}]
+    idx, cf, nnz, resid = lib.encode_multi(sc, precision="fp32", bn=variant, sync=True)[0]
+    idx = lib.idx_as_long(idx).cpu().numpy()
+    nnz = nnz.cpu().numpy().astype(int)
+    sep = well_separated(ref["topc"], ref["nnz"], 1e-4)
+    assert sep.mean() > 0.8
+    np.testing.assert_array_equal(idx[sep], ref["idx"][sep])
+    np.testing.assert_array_equal(nnz[sep], ref["nnz"][sep])
+    r = resid.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(r[sep], ref["resid_sq"][sep], rtol=2e-4, atol=1e-9)

@@ -47,10 +47,18 @@ def test_multi_under_graph_capture(lib):
 
 
 def test_autotune_keeps_results(lib):
+    """Tuning changes which encoder kernel runs, not what OMP computes: the
+    kernels differ only in rounding order, so the supports agree on all but
+    near-tied rows, and where they agree the coefficients and residuals agree
+    to FP32 rounding."""
     sc = _scene(9, 20000, 1024, 8)
-    before = lib.encode(sc["D"], sc["X"], 8, sync=True)
+    before = [t.cpu().numpy() for t in lib.encode(sc["D"], sc["X"], 8, sync=True)]
     bn = lib.autotune_encode(sc["D"], sc["X"][:8192], 8)
-    assert bn in (64, 128)
-    after = lib.encode(sc["D"], sc["X"], 8, sync=True)
-    for a, b in zip(before, after):
-        np.testing.assert_array_equal(a.cpu().numpy(), b.cpu().numpy())
+    assert bn in (2, 3, 4, 5, 64, 128)
+    after = [t.cpu().numpy() for t in lib.encode(sc["D"], sc["X"], 8, sync=True)]
+    (ia, ca, na, ra), (ib, cb, nb, rb) = before, after
+    same = (ia == ib).all(axis=1) & (na == nb)
+    assert same.mean() >= 0.999, same.mean()
+    scale = np.abs(ca[same]).max(axis=1, keepdims=True) + 1e-30
+    assert (np.abs(ca[same] - cb[same]) / scale).max() <= 1e-4
+    np.testing.assert_allclose(rb[same], ra[same], rtol=1e-3, atol=1e-7)

@@ -136,3 +136,19 @@ def test_binding_refuses_host_tensors_for_device_arguments():
     with pytest.raises(ValueError):
         api._pd(torch.zeros(4))
     assert api._pd(None) is None
+
+
+def test_encode_variant_choice(L):
+    """The built-in encoder choice (host logic only): FP32 with s <= 8 on the
+    selection/solver warps with FP16 parts, s > 8 on one tile per CTA,
+    BF16/FP8 on two warp groups; unsupported arguments give 0."""
+    assert L.dlsh_encode_variant(1024, 8, 0) == 5
+    assert L.dlsh_encode_variant(256, 1, 0) == 5
+    assert L.dlsh_encode_variant(1024, 16, 0) == 1
+    assert L.dlsh_encode_variant(1024, 8, 1) == 2
+    assert L.dlsh_encode_variant(1024, 8, 2) == 2
+    assert L.dlsh_encode_variant(1024, 16, 1) == 1
+    assert L.dlsh_encode_variant(1024, 17, 1) == 0
+    assert L.dlsh_encode_variant(0, 8, 0) == 0
+    assert L.dlsh_encode_variant(1024, 0, 0) == 0
+    assert L.dlsh_encode_variant(1024, 8, 5) == 0
