@@ -31,12 +31,12 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
 # variant), from one ncu capture at N = 1,000,000; the traffic grows with the
 # number of signals, so a launch over N signals moves N times it.  A kernel
 # without a capture of its current form reports null.
-ENCODE_TRAFFIC = {}
+ENCODE_TRAFFIC = {(1024, 8, 5): (184.713472e6 + 36.308224e6) / 1_000_000}
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=3_000_000)
@@ -116,11 +116,11 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
-            # let the sampler reach its steady 100 ms cadence before the timed
+            # let the sampler reach its steady 50 ms cadence before the timed
             # region starts, then keep only the samples taken inside it
             t0 = time.time()
             while not self.rows and time.time() - t0 < 3.0 and self.proc.poll() is None:

@@ -152,7 +152,7 @@ def encode_profile(D, X, s: int, eps: float = 0.0, precision="fp32"):
     if variant == 3:  # two tiles served in turn by all warps (see dlsh.h)
         names = ("sel_wait_mma", "selection", "solver", "solver_wait_staging", "tile_iterations",
                  "unused", "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "mma_wait_copy")
-    elif variant in (4, 5):  # two tiles, selection and solver warps (TF32 / FP16 products)
+    elif variant in (4, 5, 6):  # selection and solver warps (TF32 / FP16 products, 2 or 3 tiles)
         names = ("sel_wait_mma", "selection", "solver", "solver_wait_staging", "jobs",
                  "solver_wait_cand", "mma_wait_a", "mma_wait_chunk", "mma_wait_tmem", "mma_wait_copy",
                  "sel_wait_solver")

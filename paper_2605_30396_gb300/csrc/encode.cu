@@ -1286,12 +1286,12 @@ static int launch_alt(const AltArgs& a, int grid, cudaStream_t st) {
   return check_launch("dlsh_encode: launch");
 }
 
-template <bool F16>
+template <bool F16, int NS>
 static int launch_split(const SplitArgs& a, int grid, cudaStream_t st) {
-  DLSH_CUDA_TRY(cudaFuncSetAttribute(encode_split_kernel<F16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  DLSH_CUDA_TRY(cudaFuncSetAttribute(encode_split_kernel<F16, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      SMEM_LIMIT),
                 "dlsh_encode: cudaFuncSetAttribute");
-  encode_split_kernel<F16><<<grid, NTHREADS, a.p.smem, st>>>(a);
+  encode_split_kernel<F16, NS><<<grid, NTHREADS, a.p.smem, st>>>(a);
   count_launches(1);
   return check_launch("dlsh_encode: launch");
 }
@@ -1363,16 +1363,18 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   // kernel variant (s <= 8): 2 = two tiles in flight on two warp groups,
   // 3 = two tiles served in turn by all warps (FP32), 4 / 5 = two tiles with
   // the warps split into selection and solver groups (FP32 as three TF32 / three
-  // FP16 products); 64 / 128 = one tile with that atom-chunk width; 0 = the
-  // tuned choice, else the default below
+  // FP16 products), 6 = the same with three tiles and FP16 products; 64 / 128 =
+  // one tile with that atom-chunk width; 0 = the tuned choice, else the default
+  // below
   int choice = bn != 0 ? bn : tuned_bn(K, s, prec);
   PairPlan pp;
   AltPlan ap;
-  SplitPlan sp, sp16;
+  SplitPlan sp, sp16, sp16x3;
   const bool pair_ok = !prof && make_pair_plan(K, s, prec, pp) == DLSH_OK;
   const bool alt_ok = make_alt_plan(K, s, prec, ap) == DLSH_OK;
   const bool split_ok = make_split_plan(K, s, prec, sp, false) == DLSH_OK;
   const bool split16_ok = make_split_plan(K, s, prec, sp16, true) == DLSH_OK;
+  const bool split16x3_ok = make_split_plan(K, s, prec, sp16x3, true, 3) == DLSH_OK;
   // default (measured at N = 3M, K = 1024): BF16/FP8, bound by selection and
   // solver, on two warp groups (1.2-1.3x faster than one tile); FP32 on
   // selection and solver warps with three FP16 products (1.9x faster than one
@@ -1382,7 +1384,8 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   if (choice == 3 && !alt_ok) choice = 0;
   if (choice == 4 && !split_ok) choice = 0;
   if (choice == 5 && !split16_ok) choice = 0;
-  if (choice == 3 || choice == 4 || choice == 5) {
+  if (choice == 6 && !split16x3_ok) choice = 0;
+  if (choice >= 3 && choice <= 6) {
     Plan p;  // the one-tile encoder's 128-atom FP32 operand image
     if (make_plan(K, s, prec, p, 128) != DLSH_OK || p.BN != 128)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d does not fit", K, s);
@@ -1390,7 +1393,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
     carve(ws, p, w);
     if (status_out) *status_out = w.status;
     Plan pi = p;  // the operand image: TF32 hi / lo, or FP16 hi / lo (half the bytes)
-    if (choice == 5) {
+    if (choice == 5 || choice == 6) {
       pi.prec = OPF16X2;
       pi.chunk_bytes = sp16.chunk_bytes;
     }
@@ -1416,12 +1419,17 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
     const int ntiles = static_cast<int>((N + TILE_M - 1) / TILE_M);
     int sms = device_sm_count();
     if (sms <= 0) sms = 1;
-    const int grid = (!n_dev && (ntiles + 1) / 2 < sms) ? ((ntiles + 1) / 2 > 0 ? (ntiles + 1) / 2 : 1) : sms;
-    if (choice == 4 || choice == 5) {
+    // two (three) tiles per CTA: enough CTAs for every SM, fewer when the
+    // tiles run out (a count read on the device takes every SM)
+    const int per = choice == 6 ? 3 : 2;
+    const int want = (ntiles + per - 1) / per;
+    const int grid = (!n_dev && want < sms) ? (want > 0 ? want : 1) : sms;
+    if (choice >= 4) {
       SplitArgs a{};
       fill(a);
-      a.p = choice == 5 ? sp16 : sp;
-      return choice == 5 ? launch_split<true>(a, grid, st) : launch_split<false>(a, grid, st);
+      a.p = choice == 6 ? sp16x3 : (choice == 5 ? sp16 : sp);
+      if (choice == 6) return launch_split<true, 3>(a, grid, st);
+      return choice == 5 ? launch_split<true, 2>(a, grid, st) : launch_split<false, 2>(a, grid, st);
     }
     AltArgs a{};
     fill(a);
@@ -1464,7 +1472,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
     return pp.top4 ? launch_pair<2, true>(a, grid, st) : launch_pair<2, false>(a, grid, st);
   }
   Plan p;
-  if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 5) ? 0 : choice) != DLSH_OK)
+  if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 6) ? 0 : choice) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
   Ws w;
@@ -1722,14 +1730,14 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
   DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
   int best = 0;
   float best_ms = 0.f;
-  for (int bn : {64, 128, 2, 3, 4, 5}) {
+  for (int bn : {64, 128, 2, 3, 4, 5, 6}) {
     Plan p;
     PairPlan pp;
     AltPlan ap;
     SplitPlan sp;
     if (bn == 2 ? make_pair_plan(K, s, precision, pp) != DLSH_OK
                 : bn == 3 ? make_alt_plan(K, s, precision, ap) != DLSH_OK
-                : bn == 4 || bn == 5 ? make_split_plan(K, s, precision, sp, bn == 5) != DLSH_OK
+                : bn >= 4 && bn <= 6 ? make_split_plan(K, s, precision, sp, bn >= 5, bn == 6 ? 3 : 2) != DLSH_OK
                           : (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn))
       continue;
     // force this width for the trial runs
@@ -1816,8 +1824,8 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
   if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
-  if (bn != 0 && (bn < 2 || bn > 5) && bn != 64 && bn != 128)
-    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2, 3, 4, 5, 64 or 128");
+  if (bn != 0 && (bn < 2 || bn > 6) && bn != 64 && bn != 128)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2..6, 64 or 128");
   for (int i = 0; i < n; ++i) {
     const dlsh_scene& x = sc[i];
     if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
@@ -1825,7 +1833,7 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
       return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
     Plan p;
-    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 5) ? 0 : bn) != DLSH_OK)
+    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 6) ? 0 : bn) != DLSH_OK)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
                        i, x.K, x.s);
   }

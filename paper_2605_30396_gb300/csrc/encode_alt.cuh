@@ -187,7 +187,7 @@ __device__ __forceinline__ void issue_alt_passes(uint32_t tmem_d, uint32_t a_tme
 // Barriers and shared state of the dictionary producer and the MMA issuer,
 // shared by the two-tile FP32 encoders.
 struct AltSync {
-  uint64_t* bar_a;       // [2] a tile slot's A operand is staged
+  uint64_t* bar_a;       // [slots] a tile slot's A operand is staged
   uint64_t* bar_full;    // [ABUF] an accumulator buffer holds a chunk's correlations
   uint64_t* bar_empty;   // [ABUF] an accumulator buffer has been read
   uint64_t* bar_stage;   // the staged A operand has been copied into tensor memory
@@ -230,18 +230,21 @@ __device__ __forceinline__ void alt_produce(const AltSync& y, const uint8_t* img
   }
 }
 
-// One elected thread: the jobs (slot 0, it), (slot 1, it), (slot 0, it + 1) ..
-// of K0 / K1 rounds of s iterations.  Each job waits for its staged residual,
+// One elected thread: the jobs (slot 0, it), (slot 1, it), .., (slot 0, it + 1)
+// .. of the rounds k (slot t has a tile in rounds k < Kt[t], Kt non-increasing)
+// of s iterations.  Each job waits for its staged residual,
 // for the previous job's MMAs (the A columns in tensor memory are shared),
 // copies the hi / lo residual into tensor memory (TF32: columns 0..95; F16:
 // 0..47), then runs the three-product MMAs of every chunk into the
 // accumulator buffers in turn.
-template <bool F16>
+template <bool F16, int NS>
 __device__ __forceinline__ void alt_issue(const AltSync& y, uint32_t tmem_base, uint32_t acc0, uint32_t stage_addr,
                                           uint32_t ring_addr, int stages, uint32_t chunk_bytes, int nchunks,
-                                          int K0, int K1, int s, uint32_t* status, long long budget) {
+                                          const int (&Kt)[NS], int s, uint32_t* status, long long budget) {
   unsigned long long* pcs = y.pcs;
-  uint32_t aph[2] = {0u, 0u};
+  uint32_t aph[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) aph[t] = 0u;
   long long job = 0;
   // the next chunk's ring stage and accumulator buffer with the parities of
   // their bar_dfull / bar_full phases; the previous chunk's buffer
@@ -265,9 +268,12 @@ __device__ __forceinline__ void alt_issue(const AltSync& y, uint32_t tmem_base, 
     }
     return oke;
   };
-  for (int k = 0; k < K0 && ok; ++k)
+  for (int k = 0; k < Kt[0] && ok; ++k) {
+    int nk = 0;  // slots with a tile in round k
+#pragma unroll
+    for (int t = 0; t < NS; ++t) nk += k < Kt[t];
     for (int it = 0; it < s && ok; ++it)
-      for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t, ++job) {
+      for (int t = 0; t < nk && ok; ++t, ++job) {
         const long long W0 = pcs ? clock64() : 0;
         if (!mbar_wait(&y.bar_a[t], aph[t], budget)) {
           fail();
@@ -344,6 +350,7 @@ __device__ __forceinline__ void alt_issue(const AltSync& y, uint32_t tmem_base, 
           }
         }
       }
+  }
 }
 
 __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_constant__ AltArgs a) {
@@ -414,8 +421,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_co
   } else if (warp == NEPI / 32) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0)
-      alt_issue<false>(sy, tmem_base, ACC0, smem_u32(smem + p.off_stage), ring_addr, p.stages, p.chunk_bytes, p.nchunks,
-                K0, K1, s, a.status, a.budget);
+      alt_issue<false, 2>(sy, tmem_base, ACC0, smem_u32(smem + p.off_stage), ring_addr, p.stages, p.chunk_bytes,
+                          p.nchunks, {K0, K1}, s, a.status, a.budget);
   } else {
     // ------------------------------------------------ selection + solver, two tiles in turn
     uint8_t* A = smem + p.off_stage;

@@ -1,5 +1,5 @@
-// Batch-OMP, FP32 (3xTF32) correlations, s <= 8: two tiles per CTA with the
-// warps split by task (Sec. 2.1: OMP against the dictionary, one greedy atom at
+// Batch-OMP, FP32 correlations (three TF32 or three FP16 products), s <= 8:
+// two or three tiles per CTA with the warps split by task (Sec. 2.1: OMP against the dictionary, one greedy atom at
 // a time, least-squares re-fit).
 //
 // Included by encode.cu inside namespace dlsh::enc, after encode_alt.cuh (it
@@ -18,14 +18,18 @@
 //               residual, which they stage as the tile's next A operand;
 //   warp 16     issues the MMAs, warp 17 streams the dictionary (as in the
 //               alternating encoder).
-// The selection warps run one job ahead of the solver warps: while the solver
-// works on tile A's iteration it, the tensor pipe computes and the selection
-// warps reduce tile B's correlations for the same iteration.  Per job the
-// time is the largest of the MMAs, the selection and the solver instead of the
-// sum of selection and solver.
+// The selection warps run ahead of the solver warps: while the solver works on
+// tile A's iteration it, the tensor pipe computes and the selection warps
+// reduce tile B's correlations.  With two tiles a tile's solver, MMAs and
+// selection still form one chain per iteration, so each warp group waits for
+// the other part of the time; a third tile (which fits beside the FP16
+// operands) lets the solver run two jobs behind the selection.  Per job the
+// time is then the largest of the MMAs, the selection and the solver instead
+// of the sum of selection and solver.
 
 constexpr int SPW = 8;         // selection warps (0..7)
 constexpr int SVT = 256;       // solver threads (warps 8..15)
+constexpr int SMAXSLOT = 3;    // tile slots per CTA (2, or 3 with FP16 parts)
 
 struct SplitPlan {
   int K, Kp, nchunks, stages, s;
@@ -34,7 +38,9 @@ struct SplitPlan {
   // support, y, the row state (||r||^2, ||x||, atoms taken and a stop bit, the
   // inverse of the staged operand's scale) and the candidates of the selection
   // warps (two per row)
-  uint32_t off_stage, off_L[2], off_sel[2], off_y[2], off_row[2], off_cand[2], off_bar, off_ring, smem;
+  int nslots;
+  uint32_t off_stage, off_L[SMAXSLOT], off_sel[SMAXSLOT], off_y[SMAXSLOT], off_row[SMAXSLOT], off_cand[SMAXSLOT];
+  uint32_t off_bar, off_ring, smem;
 };
 
 struct SplitArgs {
@@ -56,12 +62,16 @@ struct SplitArgs {
 };
 
 // f16: the correlations as three FP16 products (the operand split into FP16 hi
-// and lo parts of a power-of-two scaled copy) instead of three TF32 products.
-inline int make_split_plan(int K, int s, int code, SplitPlan& p, bool f16, int smem_limit = SMEM_LIMIT) {
+// and lo parts of a power-of-two scaled copy) instead of three TF32 products;
+// nslots: tiles per CTA in flight (2 or 3).
+inline int make_split_plan(int K, int s, int code, SplitPlan& p, bool f16, int nslots = 2,
+                           int smem_limit = SMEM_LIMIT) {
   int top4 = 0;
-  if (s > 8 || operand_precision(code, &top4) != 0) return DLSH_ERR_UNSUPPORTED;
+  if (s > 8 || operand_precision(code, &top4) != 0 || nslots < 2 || nslots > SMAXSLOT)
+    return DLSH_ERR_UNSUPPORTED;
   p.K = K;
   p.s = s;
+  p.nslots = nslots;
   p.nchunks = (K + ABN - 1) / ABN;
   p.Kp = p.nchunks * ABN;
   p.a_bytes = f16 ? 2 * APART16 : 2 * APART;
@@ -73,7 +83,7 @@ inline int make_split_plan(int K, int s, int code, SplitPlan& p, bool f16, int s
     return o;
   };
   p.off_stage = take(p.a_bytes);
-  for (int t = 0; t < 2; ++t) {
+  for (int t = 0; t < nslots; ++t) {
     p.off_L[t] = take(36 * TILE_M * 4);
     p.off_sel[t] = take(8 * TILE_M * 4);
     p.off_y[t] = take(8 * TILE_M * 4);
@@ -92,7 +102,7 @@ inline int make_split_plan(int K, int s, int code, SplitPlan& p, bool f16, int s
   return DLSH_OK;
 }
 
-template <bool F16>
+template <bool F16, int NSL>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_constant__ SplitArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t ACC0 = 128;
@@ -102,26 +112,46 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
   const int ntiles = static_cast<int>((NS + TILE_M - 1) / TILE_M);
   const int Gd = static_cast<int>(gridDim.x), bidx = static_cast<int>(blockIdx.x);
   const int s = p.s;
-  // rounds k in which tile slot 0 / slot 1 have a tile (tiles b + (2k + slot) Gd)
-  const int K0 = bidx < ntiles ? (ntiles - bidx + 2 * Gd - 1) / (2 * Gd) : 0;
-  const int K1 = bidx + Gd < ntiles ? (ntiles - bidx - Gd + 2 * Gd - 1) / (2 * Gd) : 0;
-  auto job_index = [&](int t, int k, int it) -> long long {
-    return k < K1 ? 2LL * s * k + 2LL * it + t : 2LL * s * K1 + static_cast<long long>(s) * (k - K1) + it;
+  // rounds k in which tile slot t has a tile (tiles b + (NSL k + t) Gd); the
+  // counts do not increase with t
+  int Kt[NSL];
+#pragma unroll
+  for (int t = 0; t < NSL; ++t)
+    Kt[t] = bidx + t * Gd < ntiles ? (ntiles - bidx - t * Gd + NSL * Gd - 1) / (NSL * Gd) : 0;
+  auto slots_in = [&](int k) -> int {
+    int n = 0;
+#pragma unroll
+    for (int t = 0; t < NSL; ++t) n += k < Kt[t];
+    return n;
   };
-  auto tile_of = [&](int t, int k) -> long long { return static_cast<long long>(bidx) + (2LL * k + t) * Gd; };
+  // jobs run round by round, iteration by iteration, slot by slot
+  auto job_index = [&](int t, int k, int it) -> long long {
+    long long before = 0;
+#pragma unroll
+    for (int q = 0; q < NSL; ++q) before += k < Kt[q] ? k : Kt[q];
+    return before * s + static_cast<long long>(it) * slots_in(k) + t;
+  };
+  auto tile_of = [&](int t, int k) -> long long { return static_cast<long long>(bidx) + (static_cast<long long>(NSL) * k + t) * Gd; };
+  auto rounds_of = [&](int t) -> int {
+    int r = Kt[0];
+#pragma unroll
+    for (int q = 1; q < NSL; ++q)
+      if (q == t) r = Kt[q];
+    return r;
+  };
   auto rows_of = [&](long long tl) -> int {
     const long long g0 = tl * TILE_M;
     return static_cast<int>(NS - g0 < TILE_M ? NS - g0 : TILE_M);
   };
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + p.off_bar);
-  uint64_t* bar_a = bars;             // [2]
-  uint64_t* bar_full = bars + 2;      // [ABUF]
-  uint64_t* bar_empty = bars + 5;     // [ABUF]
-  uint64_t* bar_stage = bars + 8;
-  uint64_t* cand_full = bars + 9;     // [2] the selection warps' candidates of a slot are written
-  uint64_t* cand_empty = bars + 11;   // [2] the solver warps have read them
-  uint64_t* bar_dfull = bars + 13;    // [stages]
+  uint64_t* bar_a = bars;                  // [NSL]
+  uint64_t* bar_full = bars + NSL;          // [ABUF]
+  uint64_t* bar_empty = bar_full + ABUF;   // [ABUF]
+  uint64_t* bar_stage = bar_empty + ABUF;
+  uint64_t* cand_full = bar_stage + 1;     // [NSL] the selection warps' candidates of a slot are written
+  uint64_t* cand_empty = cand_full + NSL;   // [NSL] the solver warps have read them
+  uint64_t* bar_dfull = cand_empty + NSL;   // [stages]
   uint64_t* bar_dempty = bar_dfull + p.stages;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar_dempty + p.stages);
   volatile long long* stage_done = reinterpret_cast<volatile long long*>(smem + p.off_bar + 1000);
@@ -135,14 +165,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
   const bool prof_any = a.prof != nullptr;
 
   if (tid == 0) {
-    mbar_init(&bar_a[0], 1);
-    mbar_init(&bar_a[1], 1);
+    for (int t = 0; t < NSL; ++t) mbar_init(&bar_a[t], 1);
     for (int b = 0; b < ABUF; ++b) {
       mbar_init(&bar_full[b], 1);
       mbar_init(&bar_empty[b], SPW);
     }
     mbar_init(bar_stage, 1);
-    for (int t = 0; t < 2; ++t) {
+    for (int t = 0; t < NSL; ++t) {
       mbar_init(&cand_full[t], SPW);
       mbar_init(&cand_empty[t], SVT / 32);
     }
@@ -168,14 +197,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
 
   if (warp == NEPI / 32 + 1) {
     // ------------------------------------------------ TMA producer
-    if (lane == 0)
+    if (lane == 0) {
+      long long rounds = 0;
+#pragma unroll
+      for (int t = 0; t < NSL; ++t) rounds += Kt[t];
       alt_produce(sy, a.img, smem + p.off_ring, p.stages, p.chunk_bytes, p.nchunks,
-                  static_cast<long long>(s) * (K0 + K1), a.status, a.budget);
+                  static_cast<long long>(s) * rounds, a.status, a.budget);
+    }
   } else if (warp == NEPI / 32) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0)
-      alt_issue<F16>(sy, tmem_base, ACC0, smem_u32(smem + p.off_stage), ring_addr, p.stages, p.chunk_bytes, p.nchunks,
-                K0, K1, s, a.status, a.budget);
+      alt_issue<F16, NSL>(sy, tmem_base, ACC0, smem_u32(smem + p.off_stage), ring_addr, p.stages, p.chunk_bytes,
+                         p.nchunks, Kt, s, a.status, a.budget);
   } else if (warp < SPW) {
     // ------------------------------------------------ selection, one job ahead of the solver
     const int wq = warp & 3, h = warp >> 2;
@@ -184,11 +217,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
     const bool prof_on = prof_any && tid == 0;
     int sbuf = 0;         // accumulator buffer of the next chunk
     uint32_t spar = 0u;   // and the parity of its bar_full phase
-    uint32_t epar[2] = {1u, 1u};  // cand_empty parity to wait for (the first pass is free)
+    uint32_t epar = (1u << NSL) - 1u;  // bit t: cand_empty parity to wait for at slot t (the first pass is free)
     bool ok = true;
-    for (int k = 0; k < K0 && ok; ++k)
+    for (int k = 0; k < Kt[0] && ok; ++k)
       for (int it = 0; it < s && ok; ++it)
-        for (int t = 0; t < (k < K1 ? 2 : 1) && ok; ++t) {
+        for (int t = 0; t < slots_in(k) && ok; ++t) {
           const long long T0 = prof_on ? clock64() : 0;
           // the largest truncated |c| of each 32-column group with its column
           // in the low five bits (31 - column, so that ties keep the smaller
@@ -244,12 +277,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
           const int j1 = c1 * ABN + h * 64 + 32 + 31 - static_cast<int>(b1 & 31u);
           const bool second = v1 > v0 || (v1 == v0 && j1 < j0);
           const long long W1 = prof_on ? clock64() : 0;
-          if (!mbar_wait(&cand_empty[t], epar[t], a.budget)) {
+          if (!mbar_wait(&cand_empty[t], (epar >> t) & 1u, a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
             ok = false;
             break;
           }
-          epar[t] ^= 1u;
+          epar ^= 1u << t;
           if (prof_on) pcs[10] += clock64() - W1;
           float* cv = reinterpret_cast<float*>(smem + p.off_cand[t]);
           int* cj = reinterpret_cast<int*>(smem + p.off_cand[t] + TILE_M * 2 * 4);
@@ -267,7 +300,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
     uint8_t* A = smem + p.off_stage;
     const int K = p.K;
     const float eps2 = a.eps * a.eps;
-    uint32_t fpar[2] = {0u, 0u};  // cand_full parity per slot
+    uint32_t fpar = 0u;  // bit t: cand_full parity to wait for at slot t
     bool ok = true;
     auto row_of = [&](int ps) -> int { return 64 * ps + 8 * vw + (lane >> 2); };
     // the staging area may be written for job J once the copy of job J - 1 has
@@ -324,10 +357,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
       st_inv(t)[r] = stage_row(r, x);
       return quad_sum(part);
     };
-    // -------- the first round's signals: slot 0, then (once its copy is done) slot 1
+    // -------- the first round's signals: slot 0, then (once its copy is done) slot 1, ..
 #pragma unroll 1
-    for (int t = 0; t < 2; ++t) {
-      if ((t == 0 ? K0 : K1) > 0 && ok) {
+    for (int t = 0; t < NSL; ++t) {
+      if (rounds_of(t) > 0 && ok) {
         if (!wait_staging(job_index(t, 0, 0))) ok = false;
         if (ok)
           for (int ps = 0; ps < 2; ++ps) {
@@ -339,9 +372,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
         if (ok && vt == 0) mbar_arrive(&bar_a[t]);
       }
     }
-    for (int k = 0; k < K0 && ok; ++k) {
-      const bool two = k < K1;
-      for (int t = 0; t < (two ? 2 : 1); ++t) {
+    for (int k = 0; k < Kt[0] && ok; ++k) {
+      const int nk = slots_in(k);
+      for (int t = 0; t < nk; ++t) {
         const int rows = rows_of(tile_of(t, k));
         for (int ps = 0; ps < 2; ++ps) {
           const int r = row_of(ps);
@@ -351,14 +384,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
       }
       for (int it = 0; it < s && ok; ++it) {
 #pragma unroll 1
-        for (int t = 0; t < (two ? 2 : 1); ++t) {
+        for (int t = 0; t < nk; ++t) {
           const long long T0 = prof_on ? clock64() : 0;
-          if (!mbar_wait(&cand_full[t], fpar[t], a.budget)) {
+          if (!mbar_wait(&cand_full[t], (fpar >> t) & 1u, a.budget)) {
             flag_status(a.status, ST_TIMEOUT);
             ok = false;
             break;
           }
-          fpar[t] ^= 1u;
+          fpar ^= 1u << t;
           if (prof_on) pcs[5] += clock64() - T0;
           // both passes' candidates into registers, then release the area
           float cva[2][2];
@@ -563,7 +596,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
                   if (a.resid_sq) a.resid_sq[gi] = rn2c;
                 }
               }
-              if (k + 1 < (t == 0 ? K0 : K1) && ok) {
+              if (k + 1 < rounds_of(t) && ok) {
                 if (wait_staging(job_index(t, k + 1, 0)))
                   st_rn2(t)[R2] = stage_x(t, tile_of(t, k + 1), R2);
                 else
@@ -578,7 +611,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
             ok = false;
             break;
           }
-          const bool more = it + 1 < s || k + 1 < (t == 0 ? K0 : K1);
+          const bool more = it + 1 < s || k + 1 < rounds_of(t);
           if (more && vt == 0) mbar_arrive(&bar_a[t]);
           if (prof_on) {
             pcs[2] += clock64() - T0;
@@ -592,7 +625,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
   __syncthreads();
   if (prof_any && tid == 0) {
     for (int q = 0; q < 11; ++q) atomicAdd(a.prof + q, pcs[q]);
-    if (blockIdx.x == 0) a.prof[11] = F16 ? 5 : 4;  // the variant that ran: the split two-tile encoder
+    if (blockIdx.x == 0) a.prof[11] = F16 ? (NSL == 3 ? 6 : 5) : 4;  // the variant that ran
   }
   if (warp == 0) {
     tc_fence_after();

@@ -192,12 +192,13 @@ def test_deterministic(lib):
         np.testing.assert_array_equal(u, v)
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4, 5, 64, 128])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6, 64, 128])
 @pytest.mark.parametrize("N,K,s", [(3000, 256, 8), (2000, 1024, 8), (1500, 300, 4), (777, 64, 1)])
 def test_fp32_kernel_variants_match_oracle(lib, variant, N, K, s):
     """Every FP32 encoder the autotuner can pick (two tiles on two warp groups,
     two tiles served in turn, two tiles with selection and solver warps as three
-    TF32 or three FP16 products, one tile with 64- or 128-atom chunks): supports
+    TF32 or three FP16 products, three such tiles with FP16 products, one tile
+    with 64- or 128-atom chunks): supports
     identical to the oracle's wherever its every selection margin exceeds 1e-4,
     RMSE within 1e-4 relative."""
     Dh = synth.hidden_dictionary(K, 0)
@@ -218,13 +219,14 @@ def test_fp32_kernel_variants_match_oracle(lib, variant, N, K, s):
     assert abs(r_got - r_ref) <= 1e-4 * r_ref, (r_got, r_ref)
 
 
-@pytest.mark.parametrize("variant", [3, 4, 5])
-def test_two_tile_fp32_encoders_over_several_rounds(lib, variant):
-    """40,077 signals are 314 tiles: on 152 CTAs of two tile slots some CTAs
-    take a third tile in a round of their own (slot 0 only) and the last tile
-    is ragged.  Supports as the oracle's wherever every selection margin exceeds
-    1e-4, residuals within 1e-4 relative per signal."""
-    N, K, s = 40077, 256, 8
+@pytest.mark.parametrize("variant", [3, 4, 5, 6])
+def test_multi_tile_fp32_encoders_over_several_rounds(lib, variant):
+    """75,077 signals are 587 tiles: on 152 CTAs of two tile slots, CTAs 131
+    and up have a second round with slot 0 only; with three slots, CTAs below
+    131 have a second round with slot 0 only and the others one round of three
+    tiles; the last tile is ragged.  Supports as the oracle's wherever every
+    selection margin exceeds 1e-4, residuals within 2e-4 relative per signal."""
+    N, K, s = 75077, 256, 8
     Dh = synth.hidden_dictionary(K, 0)
     X = synth.signals(N, Dh, s, 3).astype(np.float64)
     D = synth.hidden_dictionary(K, 7)
