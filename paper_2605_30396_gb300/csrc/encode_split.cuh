@@ -40,6 +40,9 @@ struct SplitPlan {
   // warps (two per row)
   int nslots;
   uint32_t off_stage, off_L[SMAXSLOT], off_sel[SMAXSLOT], off_y[SMAXSLOT], off_row[SMAXSLOT], off_cand[SMAXSLOT];
+  // FP16 parts with two slots: each solver thread's 12 signal values of its
+  // rows, kept for the tile's iterations ([12][512] floats per slot)
+  uint32_t off_x[SMAXSLOT];
   uint32_t off_bar, off_ring, smem;
 };
 
@@ -89,6 +92,7 @@ inline int make_split_plan(int K, int s, int code, SplitPlan& p, bool f16, int n
     p.off_y[t] = take(8 * TILE_M * 4);
     p.off_row[t] = take(4 * TILE_M * 4);
     p.off_cand[t] = take(2 * TILE_M * 8);
+    p.off_x[t] = (f16 && nslots == 2) ? take(12 * 4 * TILE_M * 4) : 0u;
   }
   p.off_bar = take(1024);
   const uint32_t fixed = (off + 1023u) & ~1023u;
@@ -107,6 +111,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t ACC0 = 128;
   const SplitPlan& p = a.p;
+  // the signals stay in shared memory across a tile's iterations (only the
+  // two-slot FP16 layout has room for them)
+  constexpr bool XC = F16 && NSL == 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long NS = a.n_dev ? *a.n_dev : a.N;
   const int ntiles = static_cast<int>((NS + TILE_M - 1) / TILE_M);
@@ -354,6 +361,11 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
       float part = 0.f;
 #pragma unroll
       for (int q = 0; q < 12; ++q) part = fmaf(x[q], x[q], part);
+      if constexpr (XC) {
+        float* xs = reinterpret_cast<float*>(smem + p.off_x[t]);
+#pragma unroll
+        for (int q = 0; q < 12; ++q) xs[q * 4 * TILE_M + r * 4 + u] = x[q];
+      }
       st_inv(t)[r] = stage_row(r, x);
       return quad_sum(part);
     };
@@ -437,8 +449,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
                 constexpr int T = decltype(tag)::value;
                 constexpr int TA = T > 0 ? T : 1;
                 float x[12], r[12];
+                if constexpr (XC) {
+                  const float* xs = reinterpret_cast<const float*>(smem + p.off_x[t]);
 #pragma unroll
-                for (int q = 0; q < 12; ++q) x[q] = (in_tile && alt_dim(u, q) < DLSH_D) ? __ldg(xr + alt_dim(u, q)) : 0.f;
+                  for (int q = 0; q < 12; ++q) x[q] = xs[q * 4 * TILE_M + R2 * 4 + u];
+                } else {
+#pragma unroll
+                  for (int q = 0; q < 12; ++q)
+                    x[q] = (in_tile && alt_dim(u, q) < DLSH_D) ? __ldg(xr + alt_dim(u, q)) : 0.f;
+                }
                 int sl[TA];
 #pragma unroll
                 for (int m = 0; m < T; ++m) sl[m] = sel[m * TILE_M + R2];
