@@ -69,8 +69,12 @@ constexpr float FP8_MAX = 448.f;
 constexpr int OPF16X2 = 3;
 
 // 16-byte K-blocks per operand row and operand parts, per precision.
-__host__ __device__ constexpr int op_kb(int prec) { return prec == 0 ? 12 : (prec == 1 ? 6 : 4); }
-__host__ __device__ constexpr int op_parts(int prec) { return prec == 0 ? 2 : 1; }
+__host__ __device__ constexpr int op_kb(int prec) { return prec == 0 ? 12 : (prec == 1 || prec == 3 ? 6 : 4); }
+__host__ __device__ constexpr int op_parts(int prec) { return prec == 0 || prec == 3 ? 2 : 1; }
+// K-block stride of the one-tile kernel's A operand: FP16 parts get 64 bytes of
+// skew, so that a half-warp's 8-byte stores (four rows, four sub-lanes of 12
+// contiguous dims) fall on sixteen different bank pairs
+__host__ __device__ constexpr uint32_t a_lbo(int prec) { return prec == 3 ? TILE_M * 16 + 64 : TILE_M * 16; }
 
 struct Plan {
   int prec, top4, ib, BN, K, Kp, nchunks, stages, resident, s;
@@ -94,9 +98,15 @@ inline int operand_precision(int code, int* top4) {
 int tuned_bn(int K, int s, int prec);
 
 // bn = 0: the tuned width if one was recorded, else the default.  BF16 and FP8
-// use 128 (the selection's key network packs 32 columns per thread).
-int make_plan(int K, int s, int code, Plan& p, int bn = 0, int smem_limit = SMEM_LIMIT) {
-  const int prec = operand_precision(code, &p.top4);
+// use 128 (the selection's key network packs 32 columns per thread).  f16: FP32
+// as three FP16 products of power-of-two scaled hi / lo parts (operand format
+// OPF16X2, 128-atom chunks) instead of three TF32 products.
+int make_plan(int K, int s, int code, Plan& p, int bn = 0, int smem_limit = SMEM_LIMIT, bool f16 = false) {
+  int prec = operand_precision(code, &p.top4);
+  if (f16 && prec == 0) {
+    prec = OPF16X2;
+    bn = 128;
+  }
   p.prec = prec;
   p.K = K;
   p.s = s;
@@ -108,7 +118,7 @@ int make_plan(int K, int s, int code, Plan& p, int bn = 0, int smem_limit = SMEM
   // column in the chunk) in their low ib bits
   p.ib = 5;
   while ((1 << (p.ib - 5)) < p.nchunks) ++p.ib;
-  p.a_bytes = TILE_M * op_kb(prec) * 16 * op_parts(prec);
+  p.a_bytes = a_lbo(prec) * op_kb(prec) * op_parts(prec);
   p.chunk_bytes = p.BN * op_kb(prec) * 16 * op_parts(prec);
   uint32_t off = 0;
   auto take = [&](uint32_t bytes) {
@@ -124,7 +134,7 @@ int make_plan(int K, int s, int code, Plan& p, int bn = 0, int smem_limit = SMEM
   p.off_g = take(s * TILE_M * 4);
   p.off_idg = take(s * TILE_M * 4);
   p.off_cand = take(p.top4 ? TILE_M * 4 * 4 * 4 : TILE_M * 4 * 8);
-  p.off_r = take(prec == 0 ? 0 : NEPI * 12 * 4);
+  p.off_r = take(prec == 0 || prec == OPF16X2 ? 0 : NEPI * 12 * 4);
   p.off_sig = take(prec == 2 ? p.Kp * 4 : 0);
   p.off_bar = take(1024);
   const uint32_t fixed = (off + 1023u) & ~1023u;
@@ -256,6 +266,21 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem_d, uint32_t a_addr, ui
         umma_tf32(tmem_d, ad, bd, idesc, (pass | ks) != 0);
       }
     }
+  } else if constexpr (PREC == OPF16X2) {
+    // three FP16 products: hi.hi, hi.lo(D), lo(r).hi
+    constexpr uint32_t idesc = umma_idesc(0, 0, TILE_M, BN);
+    constexpr uint32_t AL = a_lbo(OPF16X2), A_PART = KB * AL, B_PART = BN * KB * 16;
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass) {
+      const uint32_t ao = pass == 2 ? A_PART : 0u;
+      const uint32_t bo = pass == 1 ? B_PART : 0u;
+#pragma unroll
+      for (int ks = 0; ks < NKS; ++ks) {
+        const uint64_t ad = umma_smem_desc(a_addr + ao + ks * 2 * AL, AL, SBO);
+        const uint64_t bd = umma_smem_desc(b_addr + bo + ks * 2 * B_LBO, B_LBO, SBO);
+        umma_bf16(tmem_d, ad, bd, idesc, (pass | ks) != 0);
+      }
+    }
   } else {
     constexpr uint32_t idesc = PREC == 1 ? umma_idesc(1, 1, TILE_M, BN) : umma_idesc(0, 0, TILE_M, BN);
 #pragma unroll
@@ -368,6 +393,29 @@ __device__ __forceinline__ void write_a_part(uint8_t* A, int row, int u, const f
       pk.x = pack_bf16x2(r[4 * k + 0], r[4 * k + 1]);
       pk.y = pack_bf16x2(r[4 * k + 2], r[4 * k + 3]);
       *reinterpret_cast<uint2*>(A + (e >> 3) * LBO + row * 16 + (e & 7) * 2) = pk;
+    }
+  } else if constexpr (PREC == OPF16X2) {
+    // dims 12u + 4k .. 12u + 4k + 3: half ((3u + k) & 1) of K block (12u + 4k) / 8,
+    // FP16 hi / lo of the scaled values (inv_rho holds the row's scale here)
+    constexpr uint32_t L = a_lbo(OPF16X2), PART = 6 * L;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = 12 * u + 4 * k;
+      const uint32_t off = static_cast<uint32_t>(e >> 3) * L + row * 16 + ((e >> 2) & 1) * 8;
+      __half h[4], l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float v = r[4 * k + j] * inv_rho;
+        h[j] = __float2half_rn(v);
+        l[j] = __float2half_rn(v - __half2float(h[j]));
+      }
+      uint2 ph, pl;
+      ph.x = static_cast<uint32_t>(__half_as_ushort(h[0])) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
+      ph.y = static_cast<uint32_t>(__half_as_ushort(h[2])) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
+      pl.x = static_cast<uint32_t>(__half_as_ushort(l[0])) | (static_cast<uint32_t>(__half_as_ushort(l[1])) << 16);
+      pl.y = static_cast<uint32_t>(__half_as_ushort(l[2])) | (static_cast<uint32_t>(__half_as_ushort(l[3])) << 16);
+      *reinterpret_cast<uint2*>(A + off) = ph;
+      *reinterpret_cast<uint2*>(A + PART + off) = pl;
     }
   } else if constexpr (PREC == 0) {
     constexpr uint32_t PART = TILE_M * 12 * 16;
@@ -502,8 +550,29 @@ __device__ __forceinline__ void top4_of8(const uint32_t* k, uint32_t (&o)[4]) {
 // SMAX: compile-time bound on s (8 or 16) for the solver's register arrays.
 // T4: BF16/FP8 candidates are each row's exact low-precision top 4 (else the
 // four column-quarter winners).
+// FP16 parts: the scale 2^e that puts the row's largest |value| (over the four
+// sub-lanes) in [2^14, 2^15), so the hi / lo parts keep FP32's 22 significant
+// bits; rinv receives 2^-(e + 8), the inverse of the correlations' scale (the
+// dictionary image holds 256 D).
+__device__ __forceinline__ float f16_scale(const float (&v)[12], float& rinv) {
+  float mx = 0.f;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) mx = fmaxf(mx, fabsf(v[q]));
+  mx = quad_max(mx);
+  int ex = 0;
+  if (mx > 0.f) frexpf(mx, &ex);
+  int e = 15 - ex;
+  e = e < -100 ? -100 : (e > 100 ? 100 : e);
+  rinv = ldexpf(1.f, -e - 8);
+  return ldexpf(1.f, e);
+}
+
 template <int PREC, int BN, int SMAX, bool T4>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_constant__ Args a) {
+  // FP32 (TF32 or FP16 parts): the argmax is the selection; BF16 / FP8: the
+  // candidates are re-scored in FP32 against a copy of the residual
+  constexpr bool EXACT = PREC == 0 || PREC == OPF16X2;
+  constexpr bool RESCORE = !EXACT;
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NBUF = 512 / BN;
   constexpr int QC = BN / 4;  // columns of one chunk read by one phase-1 thread
@@ -678,9 +747,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
     // the thread's row's ||x||^2 from then
     bool pre = false;
     float pre_rn2 = 0.f;
+    // FP16 parts: the inverse scale of the staged operand's correlations (the
+    // tile being encoded / the next tile, staged early)
+    float cur_rinv = 1.f, pre_rinv = 1.f;
     // Writes the sub-lane's 12 dims of row R2 of tile `tl` into A (FP8 scaled
-    // by the row's max) and returns the row's ||x||^2.
-    auto stage_x = [&](int tl, bool to_rsm) -> float {
+    // by the row's max; FP16 parts by a power of two) and returns the row's
+    // ||x||^2; rinv: the inverse of the correlations' scale (FP16 parts)
+    auto stage_x = [&](int tl, bool to_rsm, float& rinv) -> float {
       const int64_t tg0 = static_cast<int64_t>(tl) * TILE_M;
       const bool tin = R2 < (NS - tg0 < TILE_M ? NS - tg0 : TILE_M);
       const float* txr = a.X + (tg0 + R2) * DLSH_D + 12 * u;
@@ -698,8 +771,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         mx = quad_max(mx);
         inv = mx > 0.f ? FP8_MAX / mx : 1.f;
       }
+      if constexpr (PREC == OPF16X2) inv = f16_scale(x, rinv);
       write_a_part<PREC>(A, R2, u, x, inv);
-      if constexpr (PREC != 0) {
+      if constexpr (RESCORE) {
         if (to_rsm) {
 #pragma unroll
           for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = x[k];
@@ -726,13 +800,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
       bool active = in_tile;
       int t = 0;
       if (!pre) {
-        rn2 = stage_x(tile, true);
+        rn2 = stage_x(tile, true, cur_rinv);
         fence_proxy_async_smem();
         named_bar_sync(1, NEPI);
         if (tid == 0) mbar_arrive(bar_a);
       } else {
         rn2 = pre_rn2;
-        if constexpr (PREC != 0) {
+        cur_rinv = pre_rinv;
+        if constexpr (RESCORE) {
           // the residual copy starts as x (rsm was in use until the last barrier)
           float x[12];
           load_x(x);
@@ -844,7 +919,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         // Stage the next tile's signals now and release the MMA warp, so the
         // next tile's first correlations run during this solver phase.
         if (it + 1 == s && tile + static_cast<int>(gridDim.x) < ntiles) {
-          pre_rn2 = stage_x(tile + static_cast<int>(gridDim.x), false);
+          pre_rn2 = stage_x(tile + static_cast<int>(gridDim.x), false, pre_rinv);
           fence_proxy_async_smem();
           named_bar_sync(1, NEPI);
           if (tid == 0) mbar_arrive(bar_a);
@@ -860,7 +935,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
         if (active) {
           float x[12], r[12];
           load_x(x);
-          if constexpr (PREC != 0) {
+          if constexpr (RESCORE) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) r[k] = rsm[k * NEPI + tid];
           }
@@ -869,7 +944,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
           for (int m = 0; m < SMAX; ++m) sl[m] = m < t ? sel[m * TILE_M + R2] : 0;
           int js = -1;
           float best = -1.f;
-          if constexpr (PREC == 0) {
+          if constexpr (EXACT) {
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
               const float v = cv[R2 * 4 + qq];
@@ -946,13 +1021,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               }
             }
           }
-          if constexpr (PREC != 0) {
+          if constexpr (RESCORE) {
             bool dup = false;
 #pragma unroll
             for (int m = 0; m < SMAX; ++m) dup |= (m < t && sl[m] == js);
             if (dup) js = -1;  // only support atoms were left: every |c| at rounding level
           }
-          if (js < 0 || !(best > CORR_STOP_REL * xnorm)) {
+          if (js < 0 || !(best * cur_rinv > CORR_STOP_REL * xnorm)) {
             active = false;
           } else {
             auto step = [&](auto tag) {
@@ -1074,9 +1149,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                   mx = quad_max(mx);
                   inv = mx > 0.f ? FP8_MAX / mx : 1.f;
                 }
+                if constexpr (PREC == OPF16X2) inv = f16_scale(r, cur_rinv);
                 write_a_part<PREC>(A, R2, u, r, inv);
               }
-              if constexpr (PREC != 0) {
+              if constexpr (RESCORE) {
 #pragma unroll
                 for (int k = 0; k < 12; ++k) rsm[k * NEPI + tid] = r[k];
               }
@@ -1347,11 +1423,11 @@ static int prepare(const float* D, const Plan& p, const Ws& w, bool gram, cudaSt
 }  // namespace enc
 
 // The built-in encoder choice among the kernels whose plans fit: 5 (FP32 on
-// selection and solver warps, FP16 parts), else 3 (FP32, two tiles in turn),
-// else 2 (BF16/FP8 on two warp groups), else 0 (one tile; the chunk width
-// from choose_bn).
-static int default_variant(bool split16_ok, bool alt_ok, bool pair_lowp_ok) {
-  return split16_ok ? 5 : (alt_ok ? 3 : (pair_lowp_ok ? 2 : 0));
+// selection and solver warps, FP16 parts), else 7 (FP32, one tile, FP16
+// parts), else 3 (FP32, two tiles in turn), else 2 (BF16/FP8 on two warp
+// groups), else 0 (one tile; the chunk width from choose_bn).
+static int default_variant(bool split16_ok, bool alt_ok, bool pair_lowp_ok, bool one16_ok) {
+  return split16_ok ? 5 : (one16_ok ? 7 : (alt_ok ? 3 : (pair_lowp_ok ? 2 : 0)));
 }
 
 // Entry points shared with the learning loop (learn.cu).
@@ -1363,9 +1439,9 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   // kernel variant (s <= 8): 2 = two tiles in flight on two warp groups,
   // 3 = two tiles served in turn by all warps (FP32), 4 / 5 = two tiles with
   // the warps split into selection and solver groups (FP32 as three TF32 / three
-  // FP16 products), 6 = the same with three tiles and FP16 products; 64 / 128 =
-  // one tile with that atom-chunk width; 0 = the tuned choice, else the default
-  // below
+  // FP16 products), 6 = the same with three tiles and FP16 products, 7 = one
+  // tile with FP16 products (128-atom chunks); 64 / 128 = one tile with that
+  // atom-chunk width; 0 = the tuned choice, else the default below
   int choice = bn != 0 ? bn : tuned_bn(K, s, prec);
   PairPlan pp;
   AltPlan ap;
@@ -1375,16 +1451,19 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   const bool split_ok = make_split_plan(K, s, prec, sp, false) == DLSH_OK;
   const bool split16_ok = make_split_plan(K, s, prec, sp16, true) == DLSH_OK;
   const bool split16x3_ok = make_split_plan(K, s, prec, sp16x3, true, 3) == DLSH_OK;
+  Plan p16;
+  const bool one16_ok = prec == 0 && make_plan(K, s, prec, p16, 128, SMEM_LIMIT, true) == DLSH_OK;
   // default (measured at N = 3M, K = 1024): BF16/FP8, bound by selection and
   // solver, on two warp groups (1.2-1.3x faster than one tile); FP32 on
   // selection and solver warps with three FP16 products (1.9x faster than one
   // tile at s = 8)
-  if (choice == 0) choice = default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0);
+  if (choice == 0) choice = default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0, one16_ok);
   if (choice == 2 && !pair_ok) choice = 0;
   if (choice == 3 && !alt_ok) choice = 0;
   if (choice == 4 && !split_ok) choice = 0;
   if (choice == 5 && !split16_ok) choice = 0;
   if (choice == 6 && !split16x3_ok) choice = 0;
+  if (choice == 7 && !one16_ok) choice = 0;
   if (choice >= 3 && choice <= 6) {
     Plan p;  // the one-tile encoder's 128-atom FP32 operand image
     if (make_plan(K, s, prec, p, 128) != DLSH_OK || p.BN != 128)
@@ -1472,7 +1551,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
     return pp.top4 ? launch_pair<2, true>(a, grid, st) : launch_pair<2, false>(a, grid, st);
   }
   Plan p;
-  if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 6) ? 0 : choice) != DLSH_OK)
+  if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 7) ? 0 : choice, SMEM_LIMIT, choice == 7) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
   Ws w;
@@ -1504,6 +1583,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   const int grid = (n_dev || ntiles > sms) ? sms : (ntiles > 0 ? ntiles : 1);
   if (p.BN == 128) {
     if (p.prec == 0) return launch_encode<0, 128>(a, grid, st);
+    if (p.prec == OPF16X2) return launch_encode<OPF16X2, 128>(a, grid, st);
     if (p.prec == 1)
       return p.top4 ? launch_encode<1, 128, true>(a, grid, st) : launch_encode<1, 128>(a, grid, st);
     return p.top4 ? launch_encode<2, 128, true>(a, grid, st) : launch_encode<2, 128>(a, grid, st);
@@ -1530,9 +1610,9 @@ int encode_prepare_only(const float* D, int K, int s, int prec, void* ws, cudaSt
 // Largest workspace over the chunk widths the plan may pick.
 size_t encode_ws_bytes(int K, int s, int prec) {
   size_t best = 0;
-  for (int bn : {64, 128}) {
+  for (int bn : {64, 128, -128}) {  // -128: 128-atom chunks with FP16 parts
     enc::Plan p;
-    if (enc::make_plan(K, s, prec, p, bn) != DLSH_OK) continue;
+    if (enc::make_plan(K, s, prec, p, bn < 0 ? -bn : bn, enc::SMEM_LIMIT, bn < 0) != DLSH_OK) continue;
     enc::Ws w;
     const size_t b = enc::carve(nullptr, p, w);
     if (b > best) best = b;
@@ -1568,7 +1648,9 @@ int dlsh_encode_variant(int K, int s, int precision) {
   const bool pair_ok = make_pair_plan(K, s, precision, pp) == DLSH_OK;
   const bool alt_ok = make_alt_plan(K, s, precision, ap) == DLSH_OK;
   const bool split16_ok = make_split_plan(K, s, precision, sp16, true) == DLSH_OK;
-  const int v = dlsh::default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0);
+  Plan p16;
+  const bool one16_ok = precision == 0 && make_plan(K, s, precision, p16, 128, SMEM_LIMIT, true) == DLSH_OK;
+  const int v = dlsh::default_variant(split16_ok, alt_ok, pair_ok && pp.prec != 0, one16_ok);
   if (v != 0) return v;
   return make_plan(K, s, precision, p, 0) == DLSH_OK ? 1 : 0;
 }
@@ -1730,7 +1812,7 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
   DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
   int best = 0;
   float best_ms = 0.f;
-  for (int bn : {64, 128, 2, 3, 4, 5, 6}) {
+  for (int bn : {64, 128, 2, 3, 4, 5, 6, 7}) {
     Plan p;
     PairPlan pp;
     AltPlan ap;
@@ -1738,6 +1820,7 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
     if (bn == 2 ? make_pair_plan(K, s, precision, pp) != DLSH_OK
                 : bn == 3 ? make_alt_plan(K, s, precision, ap) != DLSH_OK
                 : bn >= 4 && bn <= 6 ? make_split_plan(K, s, precision, sp, bn >= 5, bn == 6 ? 3 : 2) != DLSH_OK
+                : bn == 7 ? (precision != 0 || make_plan(K, s, precision, p, 128, SMEM_LIMIT, true) != DLSH_OK)
                           : (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn))
       continue;
     // force this width for the trial runs
@@ -1824,8 +1907,8 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
   if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
-  if (bn != 0 && (bn < 2 || bn > 6) && bn != 64 && bn != 128)
-    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2..6, 64 or 128");
+  if (bn != 0 && (bn < 2 || bn > 7) && bn != 64 && bn != 128)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2..7, 64 or 128");
   for (int i = 0; i < n; ++i) {
     const dlsh_scene& x = sc[i];
     if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
@@ -1833,7 +1916,7 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
       return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
     Plan p;
-    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 6) ? 0 : bn) != DLSH_OK)
+    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 7) ? 0 : bn) != DLSH_OK)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
                        i, x.K, x.s);
   }

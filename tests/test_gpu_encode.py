@@ -192,13 +192,13 @@ def test_deterministic(lib):
         np.testing.assert_array_equal(u, v)
 
 
-@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6, 64, 128])
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6, 7, 64, 128])
 @pytest.mark.parametrize("N,K,s", [(3000, 256, 8), (2000, 1024, 8), (1500, 300, 4), (777, 64, 1)])
 def test_fp32_kernel_variants_match_oracle(lib, variant, N, K, s):
     """Every FP32 encoder the autotuner can pick (two tiles on two warp groups,
     two tiles served in turn, two tiles with selection and solver warps as three
     TF32 or three FP16 products, three such tiles with FP16 products, one tile
-    with 64- or 128-atom chunks): supports
+    with FP16 products or with 64- or 128-atom TF32 chunks): supports
     identical to the oracle's wherever its every selection margin exceeds 1e-4,
     RMSE within 1e-4 relative."""
     Dh = synth.hidden_dictionary(K, 0)
