@@ -962,7 +962,7 @@ def main():
     peaks, src = load_peaks()
     bf16 = float(peaks["bf16_tflops"])
     variant = api.encode_variant(K, s, a.precision)
-    if a.precision == "fp32" and variant == 5:
+    if a.precision == "fp32" and variant in (5, 6, 7):
         peak = bf16 / 3.0
         peak_note = "FP16 dense (= bf16 burst) / 3 for the three-product FP16 split"
     elif a.precision == "fp32":

@@ -57,8 +57,10 @@ extern "C" {
                             encoder for s <= 8 splits into FP16 parts of a
                             power-of-two scaled copy (the residual per row,
                             D by 256) -- twice the tensor rate and half the
-                            operand bytes of TF32 parts; the other encoders
-                            and dlsh_correlate split into TF32 parts        */
+                            operand bytes of TF32 parts; so does the one-tile
+                            encoder for s > 8.  dlsh_correlate and the kernels
+                            chosen by tuning records 3, 4, 64, 128 split into
+                            TF32 parts                                      */
 #define DLSH_PREC_BF16 1 /* BF16 operands, FP32 accumulate; each row's exact
                             low-precision top 4 (|c| truncated below the bits
                             that carry the column, then the smaller atom index)
@@ -114,7 +116,8 @@ int dlsh_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
  * The encoder kernel dlsh_encode runs for (K, s, precision) with the built-in
  * choice (no tuning record): 1 one tile per CTA, 2 two tiles on two warp
  * groups, 3 two tiles served in turn, 4 / 5 two tiles with selection and solver
- * warps (TF32 / FP16 parts); 0 if the configuration is unsupported.  A record
+ * warps (TF32 / FP16 parts), 6 three such tiles (FP16 parts), 7 one tile per
+ * CTA with FP16 parts; 0 if the configuration is unsupported.  A record
  * from dlsh_autotune_encode overrides this choice.
  */
 int dlsh_encode_variant(int K, int s, int precision);
@@ -123,7 +126,8 @@ int dlsh_encode_variant(int K, int s, int precision);
  * dlsh_encode with per-phase timing: identical results, plus twelve counters in
  * `cycles` (device, uint64[12], zeroed by the call) summed over all CTAs, in SM
  * clock cycles; counter 11 names the kernel that ran (1 one tile per CTA, 3 two
- * tiles served in turn, 4 / 5 two tiles with selection and solver warps).  The call
+ * tiles served in turn, 4 / 5 / 6 selection and solver warps; the one-tile
+ * kernel with FP16 parts reports 1).  The call
  * runs the kernel dlsh_encode would run, except that BF16/FP8 use the one-tile
  * kernel.  One tile (1): from the first selection/solver thread, waiting for the
  * tensor cores, the selection phase (including that wait), the barrier after

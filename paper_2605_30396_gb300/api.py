@@ -121,7 +121,8 @@ def encode(D, X, s: int, eps: float = 0.0, precision="fp32", sync: bool = False,
 
 ENCODE_VARIANTS = {1: "encode_kernel (one tile per CTA)", 2: "encode_pair_kernel",
                    3: "encode_alt_kernel", 4: "encode_split_kernel (TF32 parts)",
-                   5: "encode_split_kernel (FP16 parts)"}
+                   5: "encode_split_kernel (FP16 parts)", 6: "encode_split_kernel (FP16 parts, three tiles)",
+                   7: "encode_kernel (one tile per CTA, FP16 parts)"}
 
 
 def encode_variant(K: int, s: int, precision="fp32") -> int:

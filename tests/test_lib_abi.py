@@ -140,11 +140,12 @@ def test_binding_refuses_host_tensors_for_device_arguments():
 
 def test_encode_variant_choice(L):
     """The built-in encoder choice (host logic only): FP32 with s <= 8 on the
-    selection/solver warps with FP16 parts, s > 8 on one tile per CTA,
-    BF16/FP8 on two warp groups; unsupported arguments give 0."""
+    selection/solver warps with FP16 parts, s > 8 on one tile per CTA with FP16
+    parts, BF16/FP8 on two warp groups (one tile for s > 8); unsupported
+    arguments give 0."""
     assert L.dlsh_encode_variant(1024, 8, 0) == 5
     assert L.dlsh_encode_variant(256, 1, 0) == 5
-    assert L.dlsh_encode_variant(1024, 16, 0) == 1
+    assert L.dlsh_encode_variant(1024, 16, 0) == 7
     assert L.dlsh_encode_variant(1024, 8, 1) == 2
     assert L.dlsh_encode_variant(1024, 8, 2) == 2
     assert L.dlsh_encode_variant(1024, 16, 1) == 1
