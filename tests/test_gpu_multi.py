@@ -54,7 +54,7 @@ def test_autotune_keeps_results(lib):
     sc = _scene(9, 20000, 1024, 8)
     before = [t.cpu().numpy() for t in lib.encode(sc["D"], sc["X"], 8, sync=True)]
     bn = lib.autotune_encode(sc["D"], sc["X"][:8192], 8)
-    assert bn in (2, 3, 4, 5, 64, 128)
+    assert bn in (2, 3, 4, 5, 6, 7, 64, 128)
     after = [t.cpu().numpy() for t in lib.encode(sc["D"], sc["X"], 8, sync=True)]
     (ia, ca, na, ra), (ib, cb, nb, rb) = before, after
     same = (ia == ib).all(axis=1) & (na == nb)
