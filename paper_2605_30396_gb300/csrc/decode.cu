@@ -34,6 +34,10 @@ namespace dec {
 enum : int { FM_F32 = 0, FM_GLOBAL = 1, FM_C8 = 2, FM_C16 = 3 };
 
 constexpr int YS = 16;          // basis values per Gaussian slot (15 and a zero)
+// A slot is four 16-byte words; word k of slot g sits at word k ^ ((g >> 1) & 3),
+// so that the slot writes of a batch (one lane per Gaussian, 16-byte stores)
+// fall on different bank groups.  Returns the float offset of word k.
+__device__ __forceinline__ int ysw(int g, int k) { return (k ^ ((g >> 1) & 3)) * 4; }
 constexpr int SMEM_LIMIT = 232448;
 // Gaussians per warp batch: 8 beside the 192 KB FP32 table (small batches let
 // more warps fit in the shared memory left), 16 with the FP16 table (whose
@@ -171,8 +175,11 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       sh_basis(g_sh.c, vx, vy, vz, Y);
       if (lane < GB) {
 #pragma unroll
-        for (int q = 0; q < 15; ++q) Ys[lane * YS + q] = Y[q];
-        Ys[lane * YS + 15] = 0.f;
+        float* ys = Ys + lane * YS;
+        *reinterpret_cast<float4*>(ys + ysw(lane, 0)) = make_float4(Y[0], Y[1], Y[2], Y[3]);
+        *reinterpret_cast<float4*>(ys + ysw(lane, 1)) = make_float4(Y[4], Y[5], Y[6], Y[7]);
+        *reinterpret_cast<float4*>(ys + ysw(lane, 2)) = make_float4(Y[8], Y[9], Y[10], Y[11]);
+        *reinterpret_cast<float4*>(ys + ysw(lane, 3)) = make_float4(Y[12], Y[13], Y[14], 0.f);
         if (nz > s) {
           bad = true;
           nz = s;
@@ -220,8 +227,8 @@ __global__ void __launch_bounds__(1024) decode_kernel(
             accb.y = fmaf(a, bb.y, accb.y);
           }
         }
-        const float4 y4 = *reinterpret_cast<const float4*>(Ys + gs * YS + 4 * (ql & 3));
-        const float2 yb = *reinterpret_cast<const float2*>(Ys + gs * YS + 2 * ql);
+        const float4 y4 = *reinterpret_cast<const float4*>(Ys + gs * YS + ysw(gs, ql & 3));
+        const float2 yb = *reinterpret_cast<const float2*>(Ys + gs * YS + ysw(gs, ql >> 1) + ((2 * ql) & 3));
         float prg = fmaf(y4.x, acc4.x, fmaf(y4.y, acc4.y, fmaf(y4.z, acc4.z, y4.w * acc4.w)));
         float pb = fmaf(yb.x, accb.x, yb.y * accb.y);
         // R over lanes 0-3, G over lanes 4-7, B over all eight
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(1024) decode_kernel(
           }
         }
       }
-      const float2 yy = *reinterpret_cast<const float2*>(Ys + gs * YS + 2 * ql);
+      const float2 yy = *reinterpret_cast<const float2*>(Ys + gs * YS + ysw(gs, ql >> 1) + ((2 * ql) & 3));
       const float p0 = fmaf(yy.x, aR, yy.y * bR), p1 = fmaf(yy.x, aG, yy.y * bG),
                   p2 = fmaf(yy.x, aB, yy.y * bBl);
       // transposing butterfly over the 8 lanes: afterwards lane ql holds
