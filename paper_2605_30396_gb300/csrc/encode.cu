@@ -1076,12 +1076,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
                 bp = fmaf(dj[w4].z, x[4 * w4 + 2], bp);
                 bp = fmaf(dj[w4].w, x[4 * w4 + 3], bp);
               }
-              float yv[TA];
+              // the 16-atom instantiation reads y and the new factor row w back
+              // from shared memory where they are used, instead of holding
+              // them in registers across the back substitution (spills)
+              constexpr bool REG = SMAX <= 8;
+              float yv[REG ? TA : 1];
+              if constexpr (REG) {
 #pragma unroll
-              for (int m = 0; m < T; ++m) yv[m] = ys[m * TILE_M + R2];
+                for (int m = 0; m < T; ++m) yv[m] = ys[m * TILE_M + R2];
+              }
+              auto y_at = [&](int m) -> float {
+                if constexpr (REG) return yv[m];
+                else return ys[m * TILE_M + R2];
+              };
+              auto w_at = [&](int m) -> float {
+                if constexpr (REG) return w[m];
+                else return LS(T, m);
+              };
               float yt = quad_sum(bp);
 #pragma unroll
-              for (int m = 0; m < T; ++m) yt = fmaf(-w[m], yv[m], yt);
+              for (int m = 0; m < T; ++m) yt = fmaf(-w_at(m), y_at(m), yt);
               yt *= iell;
               ys[T * TILE_M + R2] = yt;
               sel[T * TILE_M + R2] = js;
@@ -1090,10 +1104,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_kernel(const __grid_consta
               float gam[TA];
 #pragma unroll
               for (int m = T - 1; m >= 0; --m) {
-                float acc = yv[m];
+                float acc = y_at(m);
 #pragma unroll
                 for (int q = m + 1; q < T; ++q) acc = fmaf(-LS(q, m), gam[q], acc);
-                acc = fmaf(-w[m], gt, acc);
+                acc = fmaf(-w_at(m), gt, acc);
                 gam[m] = acc * IDG(m);
               }
 #pragma unroll
