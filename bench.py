@@ -1025,6 +1025,9 @@ def main():
         "omp": omp,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
+                     # the same work against the 3xTF32 roof (TF32 dense / 3), for
+                     # comparison with the TF32-part encoders this kernel replaced
+                     "frac_of_3xtf32_roof": achieved / (bf16 * TF32_PER_BF16 / 3.0),
                      "traffic": (ENCODE_TRAFFIC[(K, s, variant)] * N
                                  if (K, s, variant) in ENCODE_TRAFFIC else None),
                      "kernel": api.ENCODE_VARIANTS.get(variant, "encode_kernel") + " (prep+gram included in the timing)",
