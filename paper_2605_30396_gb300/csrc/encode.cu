@@ -381,6 +381,29 @@ __global__ void gram_kernel(const float* __restrict__ D32p, int K, float* __rest
 //     of a row run the same scalar recurrences (bitwise identical values) and
 //     combine dot products with two butterfly shuffles.
 // ---------------------------------------------------------------------------
+// FP16 parts: the power of two 2^e that puts a row's largest |value| mx in
+// [2^14, 2^15) (e = 15 for mx = 0, clamped to [-100, 100]), read from mx's
+// exponent field; rinv receives 2^-(e + 8), the inverse of the correlations'
+// scale (the dictionary image holds 256 D).
+__device__ __forceinline__ float pow2_scale(float mx, float& rinv) {
+  const int E = static_cast<int>((__float_as_uint(mx) >> 23) & 0xffu);
+  int e = mx > 0.f ? 141 - E : 15;  // frexp exponent of mx is E - 126
+  e = e < -100 ? -100 : (e > 100 ? 100 : e);
+  rinv = __uint_as_float(static_cast<uint32_t>(119 - e) << 23);
+  return __uint_as_float(static_cast<uint32_t>(127 + e) << 23);
+}
+
+// FP16 hi and lo parts (round to nearest) of four scaled values, packed two per
+// word: hi = fp16(a), lo = fp16(a - hi)
+__device__ __forceinline__ void split_f16x4(float a0, float a1, float a2, float a3, uint2& ph, uint2& pl) {
+  const __half2 h01 = __floats2half2_rn(a0, a1), h23 = __floats2half2_rn(a2, a3);
+  const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+  const __half2 l01 = __floats2half2_rn(a0 - f01.x, a1 - f01.y);
+  const __half2 l23 = __floats2half2_rn(a2 - f23.x, a3 - f23.y);
+  ph = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+  pl = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+}
+
 template <int PREC>
 __device__ __forceinline__ void write_a_part(uint8_t* A, int row, int u, const float (&r)[12],
                                              float inv_rho) {
@@ -402,18 +425,9 @@ __device__ __forceinline__ void write_a_part(uint8_t* A, int row, int u, const f
     for (int k = 0; k < 3; ++k) {
       const int e = 12 * u + 4 * k;
       const uint32_t off = static_cast<uint32_t>(e >> 3) * L + row * 16 + ((e >> 2) & 1) * 8;
-      __half h[4], l[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float v = r[4 * k + j] * inv_rho;
-        h[j] = __float2half_rn(v);
-        l[j] = __float2half_rn(v - __half2float(h[j]));
-      }
       uint2 ph, pl;
-      ph.x = static_cast<uint32_t>(__half_as_ushort(h[0])) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
-      ph.y = static_cast<uint32_t>(__half_as_ushort(h[2])) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
-      pl.x = static_cast<uint32_t>(__half_as_ushort(l[0])) | (static_cast<uint32_t>(__half_as_ushort(l[1])) << 16);
-      pl.y = static_cast<uint32_t>(__half_as_ushort(l[2])) | (static_cast<uint32_t>(__half_as_ushort(l[3])) << 16);
+      split_f16x4(r[4 * k] * inv_rho, r[4 * k + 1] * inv_rho, r[4 * k + 2] * inv_rho, r[4 * k + 3] * inv_rho,
+                  ph, pl);
       *reinterpret_cast<uint2*>(A + off) = ph;
       *reinterpret_cast<uint2*>(A + PART + off) = pl;
     }
@@ -558,13 +572,7 @@ __device__ __forceinline__ float f16_scale(const float (&v)[12], float& rinv) {
   float mx = 0.f;
 #pragma unroll
   for (int q = 0; q < 12; ++q) mx = fmaxf(mx, fabsf(v[q]));
-  mx = quad_max(mx);
-  int ex = 0;
-  if (mx > 0.f) frexpf(mx, &ex);
-  int e = 15 - ex;
-  e = e < -100 ? -100 : (e > 100 ? 100 : e);
-  rinv = ldexpf(1.f, -e - 8);
-  return ldexpf(1.f, e);
+  return pow2_scale(quad_max(mx), rinv);
 }
 
 template <int PREC, int BN, int SMAX, bool T4>

@@ -131,18 +131,8 @@ __device__ __forceinline__ void write_a_f16(uint8_t* A, int row, int u, const fl
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const uint32_t off = static_cast<uint32_t>(2 * k + (u >> 1)) * ALBO16 + row * 16 + (u & 1) * 8;
-    __half h[4], l[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float v = r[4 * k + j] * scale;
-      h[j] = __float2half_rn(v);
-      l[j] = __float2half_rn(v - __half2float(h[j]));
-    }
     uint2 ph, pl;
-    ph.x = static_cast<uint32_t>(__half_as_ushort(h[0])) | (static_cast<uint32_t>(__half_as_ushort(h[1])) << 16);
-    ph.y = static_cast<uint32_t>(__half_as_ushort(h[2])) | (static_cast<uint32_t>(__half_as_ushort(h[3])) << 16);
-    pl.x = static_cast<uint32_t>(__half_as_ushort(l[0])) | (static_cast<uint32_t>(__half_as_ushort(l[1])) << 16);
-    pl.y = static_cast<uint32_t>(__half_as_ushort(l[2])) | (static_cast<uint32_t>(__half_as_ushort(l[3])) << 16);
+    split_f16x4(r[4 * k] * scale, r[4 * k + 1] * scale, r[4 * k + 2] * scale, r[4 * k + 3] * scale, ph, pl);
     *reinterpret_cast<uint2*>(A + off) = ph;
     *reinterpret_cast<uint2*>(A + APART16 + off) = pl;
   }

@@ -332,13 +332,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) encode_split_kernel(const __grid_
         float mx = 0.f;
 #pragma unroll
         for (int q = 0; q < 12; ++q) mx = fmaxf(mx, fabsf(v[q]));
-        mx = quad_max(mx);
-        int ex = 0;
-        if (mx > 0.f) frexpf(mx, &ex);
-        int e = 15 - ex;
-        e = e < -100 ? -100 : (e > 100 ? 100 : e);
-        write_a_f16(A, r, u, v, ldexpf(1.f, e));
-        return ldexpf(1.f, -e - 8);
+        float rinv;
+        const float sc = pow2_scale(quad_max(mx), rinv);
+        write_a_f16(A, r, u, v, sc);
+        return rinv;
       } else {
         write_a_alt(A, r, u, v);
         return 1.f;
