@@ -57,6 +57,8 @@ def parse():
                     choices=["step", "encode", "mod", "decode", "decode_compact", "propose", "train",
                              "tolerance", "splat", "ksvd", "precision", "restricted"],
                     help="time the whole step (default) or one leg alone, for profiling")
+    ap.add_argument("--tune", action="store_true",
+                    help="encode / decode legs: run the library's autotuner on the leg's inputs first")
     return ap.parse_args()
 
 
@@ -361,9 +363,10 @@ def multi_scenes(scale=1.0, n_scenes=13):
 
 def multi_leg(scale=1.0, steps=5, warmup=3):
     """13 scenes encoded by one graph-captured dlsh_encode_multi call (each
-    scene's (K, s) autotuned on a sample first), then decoded from one camera
-    per scene.  A step = the graph replay plus the decodes.  Returns the timing,
-    the per-scene RMSE and the launch count of one step."""
+    scene's (K, s) autotuned on a sample first: encoder kernel and ring stages,
+    then the decode's batch and warps on the sample's codes), then decoded from
+    one camera per scene.  A step = the graph replay plus the decodes.  Returns
+    the timing, the per-scene RMSE and the launch count of one step."""
     import torch
 
     from paper_2605_30396_gb300 import _lib, api
@@ -381,8 +384,14 @@ def multi_leg(scale=1.0, steps=5, warmup=3):
     total = sum(x["N"] for x in sc)
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        api.encode_multi(scenes)  # warm-up: workspaces and internal streams exist
+        warm = api.encode_multi(scenes)  # warm-up: workspaces and internal streams exist
     torch.cuda.synchronize()
+    tuned_dec = {}
+    for x, o, (mu, cam), sc_ in zip(sc, warm, decs, scenes):
+        key = (x["K"], x["s"])
+        if key not in tuned_dec:
+            S = min(x["N"], 1 << 20)
+            tuned_dec[key] = api.autotune_decode(sc_["D"], o[0][:S], o[1][:S], o[2][:S], means=mu[:S], cam=cam)
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=st):
         outs = api.encode_multi(scenes)
@@ -410,6 +419,7 @@ def multi_leg(scale=1.0, steps=5, warmup=3):
     return {"total_N": total, "ms_per_step": ms, "gaussians_per_s": total / (ms * 1e-3),
             "scenes": [[x["N"], x["K"], x["s"]] for x in sc], "rmse_per_scene": rm,
             "tuned_bn": {f"{k[0]},{k[1]}": v for k, v in tuned.items()},
+            "tuned_decode_batch_warps": {f"{k[0]},{k[1]}": list(v) for k, v in tuned_dec.items()},
             "decode_launches_per_step": (L.dlsh_kernel_launches() - launches0) // max(steps, 1)}
 
 
@@ -428,7 +438,8 @@ def run_multi(a):
         "config": {"workload": "multi-scene: 13 scenes, N log-uniform in [0.5M, 6M] x %g, "
                                "K in {512,1024,2048}, s in {4,8,16}; step = one graph replay of "
                                "the multi-scene encode + a decode per scene" % a.multi_scale,
-                   "total_N": r["total_N"], "scenes": r["scenes"], "tuned_bn": r["tuned_bn"]},
+                   "total_N": r["total_N"], "scenes": r["scenes"], "tuned_bn": r["tuned_bn"],
+                   "tuned_decode_batch_warps": r["tuned_decode_batch_warps"]},
         "clocks": cl, "detail": {"rmse_per_scene": r["rmse_per_scene"]},
     }))
 
@@ -547,6 +558,13 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
             N = B
     else:
         fn = lambda: api.encode(D, X, s, precision=a.precision, out=out)
+    tuned = None
+    if a.tune and a.leg == "decode":
+        tuned = api.autotune_decode(D, idx, coef, nnz, means=MU, cam=cam)
+    elif a.tune and a.leg == "decode_compact":
+        tuned = api.autotune_decode(D, idx_c, coef_c, nnz, means=MU, cam=cam)
+    elif a.tune and a.leg == "encode":
+        tuned = api.autotune_encode(D, X[:262144], s, precision=a.precision)
     for _ in range(a.warmup):
         fn()
     torch.cuda.synchronize()
@@ -560,6 +578,8 @@ def run_leg(a, api, L, X, MU, cam, D, out, rgb, stream):
     ms = e0.elapsed_time(e1) / max(a.steps, 1)
     line = {"leg": a.leg, "N": N, "K": K, "s": s, "precision": a.precision, "ms": ms,
             "gaussians_per_s": N / (ms * 1e-3)}
+    if tuned is not None:
+        line["tuned"] = tuned
     if a.leg == "decode":
         line["GBps"] = N * (12 + 6 * s + 1 + 12) / (ms * 1e-3) / 1e9
     if a.leg == "decode_compact":

@@ -256,8 +256,11 @@ int dlsh_learn_dictionary(const float* X, int64_t N, int d, int K, int s,
  * Each scene is encoded exactly as dlsh_encode would encode it (same plan, so
  * bitwise the same codes), on internal streams forked from `stream` and joined
  * back to it: scenes run concurrently, the most expensive (N*K*s) first.
- * precision: FP32, BF16 or FP8 for every scene; bn: 0 (tuned/default) or 64 /
- * 128 to force the atom-chunk width of FP32 scenes.  At most 32 scenes,
+ * precision: FP32, BF16 or FP8 for every scene; bn: 0 (tuned/default), a
+ * kernel variant of every scene (2..7 as dlsh_encode_variant numbers them;
+ * 64 / 128: one tile with that atom-chunk width), plus optionally 256 x a cap
+ * of 2..32 on the dictionary ring's stages (fewer stages than fit; the codes
+ * do not depend on it).  Invalid bn: DLSH_ERR_INVALID_ARG.  At most 32 scenes,
  * s <= 16; scenes with N = 0 are skipped.  The call enqueues only kernels and
  * event record/wait (no host copies), so it can be captured into a CUDA graph;
  * the scene table is read at enqueue time.  Workspace: see
@@ -278,11 +281,17 @@ size_t dlsh_encode_multi_workspace_size(const dlsh_scene* scenes, int n, int pre
 int dlsh_encode_multi(const dlsh_scene* scenes, int n, int precision, int bn, void* ws,
                       size_t ws_bytes, void* stream, int flags);
 
-/* Autotuner: times dlsh_encode on the caller's sample at every admissible
- * atom-chunk width (64 or 128 atoms per MMA) and records the fastest for
- * (K, s, precision); later plans use it.  With DLSH_AUTOTUNE_CACHE set to a file
- * path the table is kept there as JSON lines and read back at first use.
- * Outputs are scratch of the sample's size; *best_bn (host, may be NULL). */
+/* Autotuner: times dlsh_encode on the caller's sample with every encoder kernel
+ * whose plan fits (variants 2..7 of dlsh_encode_variant, and one tile with 64
+ * or 128 atoms per MMA), each with as many dictionary ring stages as fit; then,
+ * for the fastest, half that many stages and the kernel's minimum (2; 3 for
+ * variant 2).  It records the fastest (kernel, stages) for (K, s, precision),
+ * and later dlsh_encode / dlsh_encode_multi calls use it.  *best_bn (host, may
+ * be NULL) = the kernel (low byte) + 256 x the stage cap (0: as many as fit).
+ * With DLSH_AUTOTUNE_CACHE set to a file path the table of tuned choices
+ * (encoder and decode) is kept there as JSON lines and read back at first use.
+ * Outputs are scratch of the sample's size.  On an error no trial choice stays
+ * recorded. */
 int dlsh_autotune_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                          int precision, uint16_t* idx, float* coef, uint8_t* nnz,
                          float* resid_sq, void* ws, size_t ws_bytes, void* stream, int* best_bn);
@@ -385,6 +394,23 @@ int dlsh_decode_compact(const float* D, int K, int d, const void* idx, int idx_b
                         const uint16_t* coef_f16, const uint8_t* nnz, int s, int64_t N,
                         const float* dirs_or_means, const float* cam_pos, const float* dc,
                         float* rgb, void* stream, int flags);
+
+/* Decode autotuner: times the decode of the caller's codes with batches of 8
+ * and of 16 Gaussians per warp, each at three warp counts per CTA (as many as
+ * fit beside the shared-memory dictionary, three quarters and half of that;
+ * 32, 24 and 16 where rows are read through the read-only cache), and records
+ * the fastest for (format, K, s); later dlsh_decode / dlsh_decode_compact calls
+ * of that shape use it.  The colours do not depend on the choice.
+ *   format 0: dlsh_decode's codes (idx uint16, coef FP32);
+ *          1 / 2: compact codes with 8- / 16-bit indices and FP16 coef.
+ * rgb (N x 3, device) is scratch; the DC term is not applied.  *best_batch and
+ * *best_warps: host, may be NULL.  Errors: d != 45, s outside [1, 32] or K
+ * outside the format's range -> DLSH_ERR_UNSUPPORTED; format outside 0..2,
+ * N < 1 or a NULL array -> DLSH_ERR_INVALID_ARG (both before any GPU work). */
+int dlsh_autotune_decode(const float* D, int K, int d, const void* idx, const void* coef, int format,
+                         const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
+                         const float* cam_pos, float* rgb, void* stream, int* best_batch,
+                         int* best_warps);
 
 /*
  * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in

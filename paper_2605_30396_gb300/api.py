@@ -592,8 +592,10 @@ _KEEPALIVE = []
 
 
 def autotune_encode(D, X, s: int, precision="fp32") -> int:
-    """Times the encoder's admissible atom-chunk widths on this sample; returns the
-    winner (later encodes of the same K, s, precision use it)."""
+    """Times every encoder kernel whose plan fits on this sample, then shallower
+    dictionary rings for the fastest; returns the winner as dlsh_autotune_encode
+    codes it (kernel variant + 256 x ring-stage cap).  Later encodes of the same
+    K, s, precision use it."""
     D = _dev_f32(D)
     X = _dev_f32(X)
     N, K = X.shape[0], D.shape[0]
@@ -608,3 +610,32 @@ def autotune_encode(D, X, s: int, precision="fp32") -> int:
                                   _p(nnz), _p(resid), _p(ws), ws.numel(), _stream(),
                                   ctypes.byref(best)), "dlsh_autotune_encode")
     return int(best.value)
+
+
+def autotune_decode(D, idx, coef, nnz, dirs=None, means=None, cam=None):
+    """Times the decode of these codes at batches of 8 and 16 Gaussians per warp
+    and several warp counts per CTA; records the fastest for the codes' format
+    (FP32 coef: dlsh_decode; FP16 coef: compact codes), K and s, and returns it
+    as (batch, warps).  Later decodes of that shape use it."""
+    D = _dev_f32(D)
+    N, s = coef.shape
+    if coef.dtype == torch.float16:
+        fmt = 1 if idx.dtype == torch.uint8 else 2
+        coef = coef.contiguous()
+    else:
+        fmt = 0
+        coef = _dev_f32(coef)
+    idx = idx.contiguous()
+    nnz = nnz.contiguous()
+    if dirs is not None:
+        dm, cam_arr = _dev_f32(dirs), None
+    else:
+        dm = _dev_f32(means)
+        c = [float(v) for v in (cam.tolist() if hasattr(cam, "tolist") else cam)]
+        cam_arr = (ctypes.c_float * 3)(*c)
+    rgb = torch.empty((N, 3), dtype=torch.float32, device=coef.device)
+    gb, nw = ctypes.c_int(0), ctypes.c_int(0)
+    _check(_lib.lib().dlsh_autotune_decode(_p(D), D.shape[0], D.shape[1], _pd(idx), _pd(coef), fmt, _pd(nnz), s,
+                                           N, _p(dm), cam_arr, _p(rgb), _stream(), ctypes.byref(gb),
+                                           ctypes.byref(nw)), "dlsh_autotune_decode")
+    return int(gb.value), int(nw.value)

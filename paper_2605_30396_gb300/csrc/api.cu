@@ -1,8 +1,15 @@
 // C-ABI plumbing: error reporting, version, device queries and the status
 // word check shared by every entry point.
 #include <stdarg.h>
-#include <atomic>
 #include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "host.hpp"
 
@@ -65,6 +72,64 @@ int device_sm_count() {
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   return n;
+}
+
+// ---- launch choices recorded by the autotuners ----------------------------------
+static std::mutex g_tune_mu;
+static std::map<std::string, std::vector<int>> g_tune;
+static bool g_tune_loaded = false;
+
+// Reads DLSH_AUTOTUNE_CACHE once: lines {"key": "...", "values": [a, b, ...]},
+// and the older encoder lines {"K": k, "s": s, "precision": p, "bn": b}.
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    char key[128];
+    int v[4];
+    int K, s, prec, bn;
+    const int n = sscanf(line, " {\"key\": \"%127[^\"]\", \"values\": [%d, %d, %d, %d", key, &v[0], &v[1],
+                         &v[2], &v[3]);
+    if (n >= 2) {
+      g_tune[key] = std::vector<int>(v, v + (n - 1));
+    } else if (sscanf(line, " {\"K\": %d, \"s\": %d, \"precision\": %d, \"bn\": %d", &K, &s, &prec, &bn) == 4) {
+      char k2[128];
+      snprintf(k2, sizeof(k2), "encode K=%d s=%d p=%d", K, s, prec);
+      g_tune[k2] = std::vector<int>{bn};
+    }
+  }
+  fclose(f);
+}
+
+int tune_get(const char* key, int* vals, int n) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  auto it = g_tune.find(key);
+  if (it == g_tune.end()) return 0;
+  for (int i = 0; i < n; ++i) vals[i] = i < static_cast<int>(it->second.size()) ? it->second[i] : 0;
+  return 1;
+}
+
+void tune_put(const char* key, const int* vals, int n) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_locked();
+  if (n <= 0) g_tune.erase(key);
+  else g_tune[key] = std::vector<int>(vals, vals + (n < 4 ? n : 4));
+  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  for (const auto& kv : g_tune) {
+    fprintf(f, "{\"key\": \"%s\", \"values\": [", kv.first.c_str());
+    for (size_t i = 0; i < kv.second.size(); ++i) fprintf(f, i ? ", %d" : "%d", kv.second[i]);
+    fprintf(f, "]}\n");
+  }
+  fclose(f);
 }
 
 }  // namespace dlsh

@@ -23,6 +23,7 @@
 // the FP16 path's lane mapping.
 #include <cuda_fp16.h>
 #include <math.h>
+#include <stdio.h>
 
 #include "common.cuh"
 #include "host.hpp"
@@ -39,10 +40,11 @@ constexpr int YS = 16;          // basis values per Gaussian slot (15 and a zero
 // fall on different bank groups.  Returns the float offset of word k.
 __device__ __forceinline__ int ysw(int g, int k) { return (k ^ ((g >> 1) & 3)) * 4; }
 constexpr int SMEM_LIMIT = 232448;
-// Gaussians per warp batch: 8 beside the 192 KB FP32 table (small batches let
-// more warps fit in the shared memory left), 16 with the FP16 table (whose
-// warps already reach 32 per CTA, where the larger batch costs less per
-// Gaussian).
+// Gaussians per warp batch by default: 8 beside the 192 KB FP32 table (small
+// batches let more warps fit in the shared memory left), 16 with the FP16 table
+// (whose warps already reach 32 per CTA, where the larger batch costs less per
+// Gaussian).  dlsh_autotune_decode may record the other size (8 or 16) and a
+// warp count per (format, K, s).
 __host__ __device__ constexpr int batch_of(int fm) { return fm == 0 ? 8 : 16; }
 
 // Code slots staged per Gaussian: even (16-byte pair reads), and not a multiple
@@ -58,14 +60,14 @@ __host__ __device__ constexpr int dict_floats(int fm, int K) { return fm == FM_F
 
 __constant__ ShConst g_sh;
 
-template <int FM>
+template <int FM, int GB>
 __global__ void __launch_bounds__(1024) decode_kernel(
     const float* __restrict__ D, int K, const void* __restrict__ idxv, const void* __restrict__ coefv,
     const uint8_t* __restrict__ nnz, int s, int sp, uint32_t sdiv, int64_t N,
     const float* __restrict__ dm, int use_cam, float cx, float cy, float cz,
     const float* __restrict__ dc, float y00, float* __restrict__ rgb, uint32_t* status) {
   extern __shared__ __align__(16) float sm[];
-  constexpr int GB = batch_of(FM);
+  static_assert(GB == 8 || GB == 16, "batches of 8 or 16 Gaussians");
   const int nwarps = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
@@ -174,7 +176,6 @@ __global__ void __launch_bounds__(1024) decode_kernel(
       float Y[15];
       sh_basis(g_sh.c, vx, vy, vz, Y);
       if (lane < GB) {
-#pragma unroll
         float* ys = Ys + lane * YS;
         *reinterpret_cast<float4*>(ys + ysw(lane, 0)) = make_float4(Y[0], Y[1], Y[2], Y[3]);
         *reinterpret_cast<float4*>(ys + ysw(lane, 1)) = make_float4(Y[4], Y[5], Y[6], Y[7]);
@@ -340,20 +341,21 @@ static int upload_constants(cudaStream_t st) {
 // One decode launch with the dictionary format FM: shared-memory sizes from
 // the format, as many warps per CTA as shared memory allows (at most 32), and
 // a grid of (CTAs resident per SM) x SMs, capped by the work.
-template <int FM>
-static int launch_decode(const float* D, int K, const void* idx, const void* coef, const uint8_t* nnz,
-                         int s, int64_t N, const float* dm, const float* cam, const float* dc, float* rgb,
-                         uint32_t* status, int nwarps, cudaStream_t st, const char* call) {
+template <int FM, int GB>
+static int launch_decode_gb(const float* D, int K, const void* idx, const void* coef, const uint8_t* nnz,
+                            int s, int64_t N, const float* dm, const float* cam, const float* dc, float* rgb,
+                            uint32_t* status, int nwarps, cudaStream_t st, const char* call) {
   int sms = device_sm_count();
   if (sms <= 0) sms = 1;
   const int sp = staged_slots(s);
   const uint32_t sdiv = s >= 2 ? static_cast<uint32_t>((uint64_t(1) << 32) / static_cast<uint64_t>(s) + 1) : 0u;
-  constexpr int gb = batch_of(FM);
+  constexpr int gb = GB;
   const size_t smem = static_cast<size_t>(dict_floats(FM, K) + nwarps * warp_floats(sp, gb)) * 4;
-  DLSH_CUDA_TRY(cudaFuncSetAttribute(decode_kernel<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT),
-                call);
+  DLSH_CUDA_TRY(
+      cudaFuncSetAttribute(decode_kernel<FM, GB>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT), call);
   int per_sm = 0;
-  DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<FM>, nwarps * 32, smem), call);
+  DLSH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, decode_kernel<FM, GB>, nwarps * 32, smem),
+                call);
   if (per_sm < 1) per_sm = 1;
   const int64_t nbatch = (N + gb - 1) / gb;
   int64_t grid = static_cast<int64_t>(sms) * per_sm;
@@ -361,26 +363,59 @@ static int launch_decode(const float* D, int K, const void* idx, const void* coe
   if (grid > need) grid = need;
   const float cx = cam ? cam[0] : 0.f, cy = cam ? cam[1] : 0.f, cz = cam ? cam[2] : 0.f;
   const float y00 = static_cast<float>(0.5 / sqrt(M_PI));
-  decode_kernel<FM><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(D, K, idx, coef, nnz, s, sp, sdiv, N, dm,
-                                                                       cam != nullptr, cx, cy, cz, dc, y00, rgb,
-                                                                       status);
+  decode_kernel<FM, GB><<<static_cast<int>(grid), nwarps * 32, smem, st>>>(
+      D, K, idx, coef, nnz, s, sp, sdiv, N, dm, cam != nullptr, cx, cy, cz, dc, y00, rgb, status);
   count_launches(1);
   return check_launch(call);
 }
 
-// Warps per CTA that fit beside the dictionary of format fm (0 if none do).
-static int fit_warps(int fm, int K, int s) {
+// Warps per CTA that fit beside the dictionary of format fm with batches of gb
+// Gaussians (0 if none do).
+static int fit_warps(int fm, int K, int s, int gb) {
   const long long room = SMEM_LIMIT - 4LL * dict_floats(fm, K);
-  const long long wb = 4LL * warp_floats(staged_slots(s), batch_of(fm));
+  const long long wb = 4LL * warp_floats(staged_slots(s), gb);
   long long n = room > 0 ? room / wb : 0;
   return static_cast<int>(n > 32 ? 32 : n);
+}
+static int fit_warps(int fm, int K, int s) { return fit_warps(fm, K, s, batch_of(fm)); }
+
+// The batch size and warps per CTA for (fm, K, s): the autotuner's record if it
+// still fits, else the default batch with as many warps as fit (16 warps for
+// rows read through the read-only cache).
+static void decode_shape(int fm, int K, int s, int* gb, int* nw) {
+  char key[64];
+  snprintf(key, sizeof(key), "decode f=%d K=%d s=%d", fm, K, s);
+  int v[2] = {0, 0};
+  if (tune_get(key, v, 2) && (v[0] == 8 || v[0] == 16) && v[1] >= 1 &&
+      v[1] <= (fm == FM_GLOBAL ? 32 : fit_warps(fm, K, s, v[0]))) {
+    *gb = v[0];
+    *nw = v[1];
+    return;
+  }
+  *gb = batch_of(fm);
+  *nw = fm == FM_GLOBAL ? 16 : fit_warps(fm, K, s);
+}
+
+// One decode launch of format FM with a batch of gb Gaussians per warp.
+template <int FM>
+static int launch_decode(const float* D, int K, const void* idx, const void* coef, const uint8_t* nnz, int s,
+                         int64_t N, const float* dm, const float* cam, const float* dc, float* rgb,
+                         uint32_t* status, int gb, int nwarps, cudaStream_t st, const char* call) {
+  if (gb == 16)
+    return launch_decode_gb<FM, 16>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, nwarps, st, call);
+  return launch_decode_gb<FM, 8>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, nwarps, st, call);
 }
 
 }  // namespace dec
 
-// Shared with the bench / learn paths: enqueue one decode.  The FP32 table
-// stays in shared memory while at least six warps fit beside it; beyond that
-// (about 1150 atoms) the rows are read through the read-only cache.
+// The FP32 table stays in shared memory while at least six warps (batches of
+// 8) fit beside it; beyond that (about 1150 atoms) the rows are read through
+// the read-only cache.
+static int decode_format(int K, int s) {
+  return dec::fit_warps(dec::FM_F32, K, s) >= 6 ? dec::FM_F32 : dec::FM_GLOBAL;
+}
+
+// Shared with the bench / learn paths: enqueue one decode.
 int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef,
                    const uint8_t* nnz, int s, int64_t N, const float* dm, const float* cam,
                    const float* dc, float* rgb, uint32_t* status, cudaStream_t st) {
@@ -388,10 +423,13 @@ int decode_enqueue(const float* D, int K, const uint16_t* idx, const float* coef
   int rc = upload_constants(st);
   if (rc) return rc;
   if (N == 0) return DLSH_OK;
-  const int nw = fit_warps(FM_F32, K, s);
-  if (nw >= 6)
-    return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, nw, st, "dlsh_decode");
-  return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, 16, st, "dlsh_decode");
+  const int fm = decode_format(K, s);
+  int gb = 0, nw = 0;
+  decode_shape(fm, K, s, &gb, &nw);
+  if (fm == FM_F32)
+    return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, gb, nw, st, "dlsh_decode");
+  return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dm, cam, dc, rgb, status, gb, nw, st,
+                                  "dlsh_decode");
 }
 
 }  // namespace dlsh
@@ -471,12 +509,102 @@ extern "C" int dlsh_decode_compact(const float* D, int K, int d, const void* idx
   int rc = upload_constants(st);
   if (rc) return rc;
   if (N > 0) {
-    const int nw = fit_warps(FM_C8, K, s);
-    rc = idx_bytes == 1 ? launch_decode<FM_C8>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
-                                               nullptr, nw, st, "dlsh_decode_compact")
-                        : launch_decode<FM_C16>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
-                                                nullptr, nw, st, "dlsh_decode_compact");
+    const int fm = idx_bytes == 1 ? FM_C8 : FM_C16;
+    int gb = 0, nw = 0;
+    decode_shape(fm, K, s, &gb, &nw);
+    rc = fm == FM_C8 ? launch_decode<FM_C8>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
+                                            nullptr, gb, nw, st, "dlsh_decode_compact")
+                     : launch_decode<FM_C16>(D, K, idx, coef_f16, nnz, s, N, dirs_or_means, cam_pos, dc, rgb,
+                                             nullptr, gb, nw, st, "dlsh_decode_compact");
     if (rc) return rc;
   }
   return finish(st, nullptr, flags, "dlsh_decode_compact");
+}
+
+extern "C" int dlsh_autotune_decode(const float* D, int K, int d, const void* idx, const void* coef, int format,
+                                    const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
+                                    const float* cam_pos, float* rgb, void* stream, int* best_batch,
+                                    int* best_warps) {
+  using namespace dlsh;
+  using namespace dlsh::dec;
+  clear_error();
+  if (d != DLSH_D) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_decode: d must be 45, got %d", d);
+  if (format < 0 || format > 2)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_autotune_decode: format must be 0, 1 or 2, got %d", format);
+  if (s < 1 || s > DLSH_MAX_S)
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_decode: s must be in [1, 32], got %d", s);
+  if (K < 1 || K > DLSH_MAX_K || (format > 0 && static_cast<size_t>(K) > dlsh_decode_compact_max_k(s)) ||
+      (format == 1 && K > 256))
+    return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_decode: K=%d is out of range for format %d", K, format);
+  if (N < 1 || !D || !idx || !coef || !nnz || !dirs_or_means || !rgb)
+    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_autotune_decode: need a non-empty sample");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = upload_constants(st);
+  if (rc) return rc;
+  const int fm = format == 0 ? decode_format(K, s) : (format == 1 ? FM_C8 : FM_C16);
+  const char* call = "dlsh_autotune_decode";
+  auto run = [&](int gb, int nw) -> int {
+    switch (fm) {
+      case FM_F32:
+        return launch_decode<FM_F32>(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, nullptr, rgb, nullptr, gb,
+                                     nw, st, call);
+      case FM_GLOBAL:
+        return launch_decode<FM_GLOBAL>(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, nullptr, rgb, nullptr,
+                                        gb, nw, st, call);
+      case FM_C8:
+        return launch_decode<FM_C8>(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, nullptr, rgb, nullptr, gb,
+                                    nw, st, call);
+      default:
+        return launch_decode<FM_C16>(D, K, idx, coef, nnz, s, N, dirs_or_means, cam_pos, nullptr, rgb, nullptr,
+                                     gb, nw, st, call);
+    }
+  };
+  cudaEvent_t e0, e1;
+  DLSH_CUDA_TRY(cudaEventCreate(&e0), "dlsh_autotune_decode: event");
+  DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_decode: event");
+  int best_gb = 0, best_nw = 0;
+  float best_ms = 0.f;
+  for (int gb : {8, 16}) {
+    // as many warps as fit beside the dictionary, three quarters and half of that
+    const int maxw = fm == FM_GLOBAL ? 32 : fit_warps(fm, K, s, gb);
+    int cand[3], nc = 0;
+    for (int w : {maxw, maxw * 3 / 4, maxw / 2}) {
+      bool seen = false;
+      for (int i = 0; i < nc; ++i) seen |= cand[i] == w;
+      if (w >= 1 && !seen) cand[nc++] = w;
+    }
+    for (int i = 0; i < nc && !rc; ++i) {
+      float sum = 0.f;
+      for (int rep = 0; rep < 4 && !rc; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = run(gb, cand[i]);
+        cudaEventRecord(e1, st);
+        if (rc) break;
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(e, "dlsh_autotune_decode: event");
+          break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) sum += ms;  // the first run warms up
+      }
+      if (!rc && (best_gb == 0 || sum < best_ms)) {
+        best_gb = gb;
+        best_nw = cand[i];
+        best_ms = sum;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (best_gb == 0) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_decode: no shape fits");
+  char key[64];
+  snprintf(key, sizeof(key), "decode f=%d K=%d s=%d", fm, K, s);
+  const int v[2] = {best_gb, best_nw};
+  tune_put(key, v, 2);
+  if (best_batch) *best_batch = best_gb;
+  if (best_warps) *best_warps = best_nw;
+  return finish(st, nullptr, 0, call);
 }

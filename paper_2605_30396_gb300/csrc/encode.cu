@@ -94,8 +94,11 @@ inline int operand_precision(int code, int* top4) {
   return code == 0 ? 0 : ((code == 1 || code == 3) ? 1 : 2);
 }
 
-// Atom-chunk widths picked by dlsh_autotune_encode, keyed by (K, s, precision).
+// The choice recorded by dlsh_autotune_encode for (K, s, precision): kernel
+// variant (tuned_bn; 64 / 128 for the one-tile chunk widths) and, in
+// tuned_choice, 256 x the ring-stage cap (0 if none was recorded).
 int tuned_bn(int K, int s, int prec);
+int tuned_choice(int K, int s, int prec);
 
 // bn = 0: the tuned width if one was recorded, else the default.  BF16 and FP8
 // use 128 (the selection's key network packs 32 columns per thread).  f16: FP32
@@ -1444,6 +1447,22 @@ static int prepare(const float* D, const Plan& p, const Ws& w, bool gram, cudaSt
 
 }  // namespace enc
 
+// At most `cap` stages in a plan's dictionary ring (cap 0: as many as fit; a
+// cap below the kernel's minimum or above the fit changes nothing).  The shared
+// memory stays above half of an SM's, so that each SM holds one CTA and its
+// whole tensor memory.
+template <class P>
+static void cap_ring(P& p, int cap, int min_stages) {
+  if (cap < min_stages || cap >= p.stages) return;
+  p.stages = cap;
+  p.smem = p.off_ring + static_cast<uint32_t>(cap) * p.chunk_bytes;
+  if (p.smem < 120 * 1024) p.smem = 120 * 1024;
+}
+static void cap_ring(enc::Plan& p, int cap) {
+  cap_ring(p, cap, 2);
+  p.resident = p.stages >= p.nchunks;
+}
+
 // The built-in encoder choice among the kernels whose plans fit: 5 (FP32 on
 // selection and solver warps, FP16 parts), else 7 (FP32, one tile, FP16
 // parts), else 3 (FP32, two tiles in turn), else 2 (BF16/FP8 on two warp
@@ -1463,8 +1482,11 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   // the warps split into selection and solver groups (FP32 as three TF32 / three
   // FP16 products), 6 = the same with three tiles and FP16 products, 7 = one
   // tile with FP16 products (128-atom chunks); 64 / 128 = one tile with that
-  // atom-chunk width; 0 = the tuned choice, else the default below
-  int choice = bn != 0 ? bn : tuned_bn(K, s, prec);
+  // atom-chunk width; 0 = the tuned choice, else the default below.  Bits
+  // 8-15 of bn (or of the tuned choice) cap the dictionary ring's stages.
+  int choice = bn != 0 ? bn : tuned_choice(K, s, prec);
+  const int cap = (choice >> 8) & 255;
+  choice &= 255;
   PairPlan pp;
   AltPlan ap;
   SplitPlan sp, sp16, sp16x3;
@@ -1486,6 +1508,11 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   if (choice == 5 && !split16_ok) choice = 0;
   if (choice == 6 && !split16x3_ok) choice = 0;
   if (choice == 7 && !one16_ok) choice = 0;
+  cap_ring(pp, cap, 3);
+  cap_ring(ap, cap, 2);
+  cap_ring(sp, cap, 2);
+  cap_ring(sp16, cap, 2);
+  cap_ring(sp16x3, cap, 2);
   if (choice >= 3 && choice <= 6) {
     Plan p;  // the one-tile encoder's 128-atom FP32 operand image
     if (make_plan(K, s, prec, p, 128) != DLSH_OK || p.BN != 128)
@@ -1576,6 +1603,7 @@ int encode_enqueue(const float* D, int K, const float* X, int64_t N, int s, floa
   if (make_plan(K, s, prec, p, (choice >= 2 && choice <= 7) ? 0 : choice, SMEM_LIMIT, choice == 7) != DLSH_OK)
     return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode: K=%d s=%d precision=%d does not fit", K,
                      s, prec);
+  cap_ring(p, cap);
   Ws w;
   carve(ws, p, w);
   if (status_out) *status_out = w.status;
@@ -1764,52 +1792,32 @@ int dlsh_correlate(const float* D, int K, int d, const float* R, int64_t M, int 
 // caller's sample and records the fastest per (K, s, precision), in memory and,
 // if DLSH_AUTOTUNE_CACHE names a file, as JSON lines there (read at first use).
 // ===========================================================================
-#include <map>
-#include <mutex>
-#include <tuple>
-
 namespace dlsh {
 namespace enc {
 
-static std::mutex g_tune_mu;
-static std::map<std::tuple<int, int, int>, int> g_tuned;
-static bool g_tune_loaded = false;
-
-static void load_tune_cache_locked() {
-  if (g_tune_loaded) return;
-  g_tune_loaded = true;
-  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* f = fopen(path, "r");
-  if (!f) return;
-  char line[256];
-  while (fgets(line, sizeof(line), f)) {
-    int K, s, prec, bn;
-    if (sscanf(line, " {\"K\": %d, \"s\": %d, \"precision\": %d, \"bn\": %d", &K, &s, &prec, &bn) == 4)
-      g_tuned[std::make_tuple(K, s, prec)] = bn;
-  }
-  fclose(f);
+// The recorded choice for (K, s, precision): the kernel variant in the low
+// byte, the ring-stage cap above it (0: none recorded).
+int tuned_choice(int K, int s, int prec) {
+  char key[64];
+  snprintf(key, sizeof(key), "encode K=%d s=%d p=%d", K, s, prec);
+  int v[2] = {0, 0};
+  if (!tune_get(key, v, 2)) return 0;
+  return (v[0] & 255) | ((v[1] & 255) << 8);
 }
 
-int tuned_bn(int K, int s, int prec) {
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  load_tune_cache_locked();
-  auto it = g_tuned.find(std::make_tuple(K, s, prec));
-  return it == g_tuned.end() ? 0 : it->second;
+int tuned_bn(int K, int s, int prec) { return tuned_choice(K, s, prec) & 255; }
+
+static void record_tuned(int K, int s, int prec, int choice) {
+  char key[64];
+  snprintf(key, sizeof(key), "encode K=%d s=%d p=%d", K, s, prec);
+  const int v[2] = {choice & 255, (choice >> 8) & 255};
+  tune_put(key, v, 2);
 }
 
-static void record_tuned(int K, int s, int prec, int bn) {
-  std::lock_guard<std::mutex> lock(g_tune_mu);
-  load_tune_cache_locked();
-  g_tuned[std::make_tuple(K, s, prec)] = bn;
-  const char* path = getenv("DLSH_AUTOTUNE_CACHE");
-  if (!path) return;
-  FILE* f = fopen(path, "w");
-  if (!f) return;
-  for (const auto& kv : g_tuned)
-    fprintf(f, "{\"K\": %d, \"s\": %d, \"precision\": %d, \"bn\": %d}\n", std::get<0>(kv.first),
-            std::get<1>(kv.first), std::get<2>(kv.first), kv.second);
-  fclose(f);
+static void forget_tuned(int K, int s, int prec) {
+  char key[64];
+  snprintf(key, sizeof(key), "encode K=%d s=%d p=%d", K, s, prec);
+  tune_put(key, nullptr, 0);
 }
 
 }  // namespace enc
@@ -1832,7 +1840,27 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
   cudaEvent_t e0, e1;
   DLSH_CUDA_TRY(cudaEventCreate(&e0), "dlsh_autotune_encode: event");
   DLSH_CUDA_TRY(cudaEventCreate(&e1), "dlsh_autotune_encode: event");
-  int best = 0;
+  // the time of one choice: a warm-up run, then two timed runs
+  auto trial = [&](int choice, float* ms_out) -> int {
+    record_tuned(K, s, precision, choice);  // force this choice for the trial runs
+    uint32_t* status = nullptr;
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      const int r = encode_enqueue(D, K, X, N, s, 0.f, precision, idx, coef, nnz, resid_sq, ws, st, &status,
+                                   nullptr, nullptr);
+      cudaEventRecord(e1, st);
+      if (r) return r;
+      DLSH_CUDA_TRY(cudaEventSynchronize(e1), "dlsh_autotune_encode: event");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) ms_sum += ms;
+    }
+    *ms_out = ms_sum;
+    return DLSH_OK;
+  };
+  // first the kernel variant, each with as many ring stages as fit ...
+  int best = 0, best_stages = 0, min_stages = 2;
   float best_ms = 0.f;
   for (int bn : {64, 128, 2, 3, 4, 5, 6, 7}) {
     Plan p;
@@ -1845,30 +1873,40 @@ extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X
                 : bn == 7 ? (precision != 0 || make_plan(K, s, precision, p, 128, SMEM_LIMIT, true) != DLSH_OK)
                           : (make_plan(K, s, precision, p, bn) != DLSH_OK || p.BN != bn))
       continue;
-    // force this width for the trial runs
-    record_tuned(K, s, precision, bn);
-    uint32_t* status = nullptr;
-    float ms_sum = 0.f;
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(e0, st);
-      rc = encode_enqueue(D, K, X, N, s, 0.f, precision, idx, coef, nnz, resid_sq, ws, st, &status,
-                          nullptr, nullptr);
-      cudaEventRecord(e1, st);
-      if (rc) break;
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ms_sum += ms;  // the first run warms up
-    }
+    float ms = 0.f;
+    rc = trial(bn, &ms);
     if (rc) break;
-    if (best == 0 || ms_sum < best_ms) {
+    if (best == 0 || ms < best_ms) {
       best = bn;
-      best_ms = ms_sum;
+      best_ms = ms;
+      best_stages = bn == 2 ? pp.stages : bn == 3 ? ap.stages : (bn >= 4 && bn <= 6) ? sp.stages : p.stages;
+      min_stages = bn == 2 ? 3 : 2;
+    }
+  }
+  // ... then, for the fastest, a shallower dictionary ring (half the stages,
+  // and the kernel's minimum)
+  if (!rc && best != 0) {
+    const int v = best;
+    int caps[2] = {best_stages / 2, min_stages}, ncap = 0;
+    for (int c : {best_stages / 2, min_stages})
+      if (c >= min_stages && c < best_stages && (ncap == 0 || caps[0] != c)) caps[ncap++] = c;
+    for (int i = 0; i < ncap && !rc; ++i) {
+      float ms = 0.f;
+      rc = trial(v | (caps[i] << 8), &ms);
+      if (!rc && ms < best_ms) {
+        best = v | (caps[i] << 8);
+        best_ms = ms;
+      }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rc) return rc;
+  if (rc) {
+    // keep no trial choice: the best one timed so far, else none
+    if (best != 0) record_tuned(K, s, precision, best);
+    else forget_tuned(K, s, precision);
+    return rc;
+  }
   if (best == 0) return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_autotune_encode: no admissible width");
   record_tuned(K, s, precision, best);
   if (best_bn) *best_bn = best;
@@ -1929,8 +1967,10 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: 1..%d scenes", MAX_SCENES);
   if (prec < 0 || prec > 4)
     return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: unknown precision %d", prec);
-  if (bn != 0 && (bn < 2 || bn > 7) && bn != 64 && bn != 128)
-    return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: bn must be 0, 2..7, 64 or 128");
+  const int v = bn & 255, cap = bn >> 8;
+  if (bn < 0 || (v != 0 && (v < 2 || v > 7) && v != 64 && v != 128) || cap == 1 || cap > 32)
+    return set_error(DLSH_ERR_INVALID_ARG,
+                     "dlsh_encode_multi: bn must be 0, 2..7, 64 or 128, plus 256 x a ring cap of 2..32");
   for (int i = 0; i < n; ++i) {
     const dlsh_scene& x = sc[i];
     if (!x.D || x.K < 1 || x.K > DLSH_MAX_K || x.s < 1 || x.s > 16 || x.N < 0 || !(x.eps >= 0.f))
@@ -1938,7 +1978,7 @@ static int multi_validate(const dlsh_scene* sc, int n, int prec, int bn) {
     if (x.N > 0 && (!x.X || !x.idx || !x.coef || !x.nnz))
       return set_error(DLSH_ERR_INVALID_ARG, "dlsh_encode_multi: scene %d has a NULL array", i);
     Plan p;
-    if (make_plan(x.K, x.s, prec, p, (bn >= 2 && bn <= 7) ? 0 : bn) != DLSH_OK)
+    if (make_plan(x.K, x.s, prec, p, (v >= 2 && v <= 7) ? 0 : v) != DLSH_OK)
       return set_error(DLSH_ERR_UNSUPPORTED, "dlsh_encode_multi: scene %d (K=%d s=%d) does not fit",
                        i, x.K, x.s);
   }

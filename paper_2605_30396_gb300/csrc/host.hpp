@@ -94,4 +94,12 @@ class PerDevice {
 // Adds n to the process-wide count of kernels this library has enqueued.
 void count_launches(int n);
 
+// Launch choices recorded by the autotuners, keyed by text such as
+// "encode K=1024 s=8 p=0", with up to four integer values.  With
+// DLSH_AUTOTUNE_CACHE naming a file the table is kept there as JSON lines and
+// read back at first use.  tune_get fills vals[0..n) (missing values as 0) and
+// returns 1 if the key is known, else 0; tune_put with n <= 0 removes the key.
+int tune_get(const char* key, int* vals, int n);
+void tune_put(const char* key, const int* vals, int n);
+
 }  // namespace dlsh

@@ -353,10 +353,11 @@ __device__ __forceinline__ void ff_add(float& h, float& l, float p, float pl) {
 // SMAX >= s: the support slots of a lane's entry are loaded into registers at
 // the start of each step, next to its signal row, so no load waits inside the
 // slot loop.  Two lanes share an entry (half of its dimensions and slots each),
-// which halves the registers and doubles the warps an SM can hold.
+// which halves the registers and doubles the warps an SM can hold: five CTAs
+// per SM at s <= 8 (96 registers a thread), four at s <= 16.
 constexpr int DH = (DLSH_D + 1) / 2;  // dimensions per lane of a pair (23)
 template <int SMAX>
-__global__ void __launch_bounds__(128, SMAX <= 16 ? 4 : 3)
+__global__ void __launch_bounds__(128, SMAX <= 8 ? 5 : (SMAX <= 16 ? 4 : 3))
     accum_kernel(const float* __restrict__ X, const uint16_t* __restrict__ idx,
                  const float* __restrict__ coef, int s, int K, const int* __restrict__ atom_start,
                  const int* __restrict__ off, int T, int tpb, int PK,
@@ -519,15 +520,14 @@ __global__ void __launch_bounds__(128, SMAX <= 16 ? 4 : 3)
       glo[j] = l;
     }
     {
-      // lane (pe, sub) stores dimensions d0 + pe and d0 + pe + 16 of its half
-      double b0 = 0.0, b1 = 0.0;
+      // lanes 0 and 1 store the two halves.  Every index here is a constant:
+      // a lane-dependent pick of bh[d] would make the compiler keep bh and bl
+      // in local memory for the whole kernel.
+      if (pe == 0) {
 #pragma unroll
-      for (int d = 0; d < DH; ++d) {
-        if (pe == d) b0 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
-        if (pe + 16 == d) b1 = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
+        for (int d = 0; d < DH; ++d)
+          if (d0 + d < DLSH_D) bpart[d0 + d] = static_cast<double>(bh[d]) + static_cast<double>(bl[d]);
       }
-      if (d0 + pe < DLSH_D) bpart[d0 + pe] = b0;
-      if (pe + 16 < DH && d0 + pe + 16 < DLSH_D) bpart[d0 + pe + 16] = b1;
       if (lane < RW - DLSH_D) bpart[DLSH_D + lane] = 0.0;
     }
     // sum the warps' partials in order

@@ -139,3 +139,30 @@ def test_decode_full_colour_with_dc(lib, compact):
     assert (ref == 0).any() and (ref > 0).any()
     ok, worst = close_rel(rgb, ref)
     assert ok, worst
+
+
+@pytest.mark.parametrize("K,s,compact", [(1024, 8, False), (2048, 8, False), (1024, 8, True), (200, 4, True)])
+def test_decode_autotune_keeps_colours(lib, K, s, compact):
+    """The decode's batch size and warps per CTA change how Gaussians are dealt
+    to warps, not the arithmetic of one Gaussian: after tuning, the colours are
+    bitwise those of the default shape (K = 2048 reads the rows through the
+    read-only cache; K = 200 compact uses 8-bit indices)."""
+    rng = np.random.default_rng(K + s + int(compact))
+    N = 20011
+    D = synth.hidden_dictionary(K, 5).astype(np.float32)
+    idx, coef, nnz = _codes(rng, N, K, s)
+    dirs = synth.unit_directions(N, 6)
+    Dt = torch.from_numpy(D).cuda()
+    it = torch.from_numpy(idx.astype(np.int16)).cuda()
+    ct = torch.from_numpy(coef).cuda()
+    nt = torch.from_numpy(nnz).cuda()
+    dt = torch.from_numpy(dirs).cuda()
+    if compact:
+        it, ct = lib.compact_codes(it, ct, K, sync=True)
+        run = lambda: lib.decode_compact(Dt, it, ct, nt, dirs=dt, sync=True).cpu().numpy()
+    else:
+        run = lambda: lib.decode(Dt, it, ct, nt, dirs=dt, sync=True).cpu().numpy()
+    before = run()
+    gb, nw = lib.autotune_decode(Dt, it, ct, nt, dirs=dt)
+    assert gb in (8, 16) and 1 <= nw <= 32
+    np.testing.assert_array_equal(run(), before)

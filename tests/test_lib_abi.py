@@ -128,6 +128,31 @@ def test_host_side_errors_of_the_later_entries(L):
     assert rc == -2
 
 
+def test_autotuner_and_ring_cap_argument_errors(L):
+    """The decode autotuner and the multi-scene call's kernel / ring-cap code
+    reject bad arguments on the host, before any GPU work."""
+    from paper_2605_30396_gb300 import _lib
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    A = L.dlsh_autotune_decode
+    assert A(fake, 16, 44, fake, fake, 0, fake, 8, 10, fake, None, fake, None, None, None) == -2
+    assert A(fake, 16, 45, fake, fake, 3, fake, 8, 10, fake, None, fake, None, None, None) == -1
+    assert A(fake, 16, 45, fake, fake, 0, fake, 8, 0, fake, None, fake, None, None, None) == -1
+    assert A(fake, 16, 45, fake, fake, 0, fake, 40, 10, fake, None, fake, None, None, None) == -2
+    assert A(fake, 300, 45, fake, fake, 1, fake, 8, 10, fake, None, fake, None, None, None) == -2
+    assert A(fake, 16, 45, None, fake, 0, fake, 8, 10, fake, None, fake, None, None, None) == -1
+    sc = (_lib.Scene * 1)()
+    sc[0] = _lib.Scene(0x1000, 1024, 0x1000, 100, 8, 0.0, 0x1000, 0x1000, 0x1000, 0)
+    W = L.dlsh_encode_multi_workspace_size
+    assert W(ctypes.byref(sc), 1, 0, 0) > 0
+    assert W(ctypes.byref(sc), 1, 0, 5 + 256 * 2) > 0
+    assert W(ctypes.byref(sc), 1, 0, 2 * 256) > 0
+    for bad in (1, 8, 65, 5 + 256, 5 + 256 * 33, -5):
+        assert W(ctypes.byref(sc), 1, 0, bad) == 0, bad
+    rc = L.dlsh_encode_multi(ctypes.byref(sc), 1, 0, 5 + 256, fake, 1 << 30, None, 0)
+    assert rc == -1 and b"ring cap" in L.dlsh_last_error()
+
+
 def test_binding_refuses_host_tensors_for_device_arguments():
     import torch
 
