@@ -136,18 +136,20 @@ __global__ void count_kernel(const uint16_t* __restrict__ idx, const uint8_t* __
   for (int j = threadIdx.x; j < K; j += blockDim.x) hist[j] = 0;
   __syncthreads();
   const int64_t i0 = static_cast<int64_t>(blockIdx.x) * TS;
-  const int64_t i1 = i0 + TS < N ? i0 + TS : N;
+  const int nt = static_cast<int>(N - i0 < TS ? N - i0 : TS);  // signals in this tile
+  const uint16_t* tidx = idx + i0 * s;
   bool bad = false;
-  for (int64_t e = i0 * s + threadIdx.x; e < i1 * s; e += blockDim.x) {
-    const int64_t i = e / s;
-    const int t = static_cast<int>(e - i * s);
-    int nz = nnz[i];
+#pragma unroll 4
+  for (int e = threadIdx.x; e < nt * s; e += blockDim.x) {
+    const int q = e / s;
+    const int t = e - q * s;
+    int nz = nnz[i0 + q];
     if (nz > s) {
       bad = true;
       nz = s;
     }
     if (t < nz) {
-      const int j = idx[e];
+      const int j = tidx[e];
       if (j < K)
         atomicAdd(&hist[j], 1);
       else
@@ -226,25 +228,52 @@ __global__ void tile_offsets_kernel(const int* __restrict__ cnt, int T,
 }
 
 // ---- 3. counting-sort scatter, one CTA of 8 warps per tile, signal order ------
-// Warp w owns signals [64 w, 64 w + 64) of the tile and walks their code slots
-// in order, 32 at a time.  Pass 1 counts each atom per warp (lanes with the same
-// atom found by match-any); the counts become per-warp bases; pass 2 gives each
-// entry its rank among the earlier entries of its atom (warps in order, then
-// lanes in order) and writes it to the atom-major list.  A signal's atoms are
-// distinct, so within an atom the entries stay in signal order.
+// The tile's code indices and counts are first staged in shared memory with
+// coalesced loads, so that neither pass waits on a chain of dependent global
+// loads.  Warp w owns signals [64 w, 64 w + 64) of the tile and walks their code
+// slots in order, 32 at a time.  Pass 1 counts each atom per warp (lanes with
+// the same atom found by match-any); the counts become per-warp bases; pass 2
+// gives each entry its rank among the earlier entries of its atom (warps in
+// order, then lanes in order) and writes it to the atom-major list.  A signal's
+// atoms are distinct, so within an atom the entries stay in signal order.
 // SLOT: the record's upper 6 bits hold the entry's code slot t instead of nnz.
 constexpr int SC_T = 256;
+// Shared memory of a scatter CTA: staged indices (TS s uint16, a multiple of 16
+// bytes), counts (TS bytes), then per-warp counts [8][K] and tile offsets [K].
+inline size_t scatter_smem(int K, int s) {
+  return static_cast<size_t>(TS) * s * 2 + TS + static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
+}
 template <bool SLOT>
 __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restrict__ idx,
                                                       const float* __restrict__ coef,
                                                       const uint8_t* __restrict__ nnz, int s, int64_t N,
                                                       int K, int T, const int* __restrict__ off,
                                                       uint2* __restrict__ list) {
-  extern __shared__ int scs[];
-  int* wc = scs;                                   // [8][K] per-warp counts, then bases
-  int* toff = scs + static_cast<size_t>(SC_T / 32) * K;  // [K] this tile's list offsets
+  extern __shared__ __align__(16) uint8_t scb[];
+  uint16_t* sidx = reinterpret_cast<uint16_t*>(scb);                        // [TS * s]
+  uint8_t* snz = scb + static_cast<size_t>(TS) * s * 2;                     // [TS]
+  int* wc = reinterpret_cast<int*>(snz + TS);                               // [8][K] counts, then bases
+  int* toff = wc + static_cast<size_t>(SC_T / 32) * K;                      // [K] this tile's list offsets
   const int b = blockIdx.x;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t t0 = static_cast<int64_t>(b) * TS;
+  const int nt = static_cast<int>(N - t0 < TS ? N - t0 : TS);  // signals in this tile
+  {
+    // 16-byte loads where the tile's index rows are 16-byte aligned (the tile
+    // starts at a multiple of TS s, so only the array's base decides), the rest
+    // element by element
+    const uint16_t* src = idx + t0 * s;
+    const int ne = nt * s;
+    int done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+      const int nv = ne / 8;
+      for (int v = tid; v < nv; v += SC_T)
+        reinterpret_cast<uint4*>(sidx)[v] = __ldg(reinterpret_cast<const uint4*>(src) + v);
+      done = nv * 8;
+    }
+    for (int e = done + tid; e < ne; e += SC_T) sidx[e] = src[e];
+    for (int q = tid; q < nt; q += SC_T) snz[q] = nnz[t0 + q];
+  }
   for (int j = tid; j < K; j += SC_T) {
     toff[j] = off[static_cast<size_t>(j) * T + b];
 #pragma unroll
@@ -252,13 +281,15 @@ __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restric
   }
   __syncthreads();
   constexpr int SPW = TS / (SC_T / 32);  // signals per warp (64)
-  const int64_t i0 = static_cast<int64_t>(b) * TS + static_cast<int64_t>(warp) * SPW;
-  const int64_t i1w = i0 + SPW;
-  const int64_t iend = i1w < N ? i1w : N;
-  const int e_end = static_cast<int>(iend > i0 ? iend - i0 : 0) * s;  // <= 64 * 32
+  const int q0 = warp * SPW;              // the warp's first signal in the tile
+  const int64_t i0 = t0 + q0;
+  const int qn = nt - q0 < SPW ? nt - q0 : SPW;
+  const int e_end = (qn > 0 ? qn : 0) * s;  // <= 64 * 32
   int* mine = wc + static_cast<size_t>(warp) * K;
   const unsigned lt = (1u << lane) - 1u;
-  auto entry = [&](int e, int& j, float& c, int& nz, int64_t& sig) {
+  // entry e of the warp: its atom j (-1 if none), coefficient c (only when
+  // with_coef), count or slot field nz and signal
+  auto entry = [&](int e, bool with_coef, int& j, float& c, int& nz, int64_t& sig) {
     j = -1;
     c = 0.f;
     nz = 0;
@@ -267,15 +298,15 @@ __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restric
       const int q = e / s;
       sig = i0 + q;
       const int t = e - q * s;
-      nz = nnz[sig];
+      nz = snz[q0 + q];
       nz = nz > s ? s : nz;
       const bool live = t < nz;
       if (SLOT) nz = t;
       if (live) {
-        const int jj = idx[sig * s + t];
+        const int jj = sidx[(q0 + q) * s + t];
         if (jj < K) {
           j = jj;
-          c = coef[sig * s + t];
+          if (with_coef) c = coef[sig * s + t];
         }
       }
     }
@@ -285,7 +316,7 @@ __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restric
     int j, nz;
     float c;
     int64_t sig;
-    entry(e0 + lane, j, c, nz, sig);
+    entry(e0 + lane, false, j, c, nz, sig);
     const unsigned m = __match_any_sync(0xffffffffu, j);
     if (j >= 0 && (m & lt) == 0) mine[j] += __popc(m);
     __syncwarp();
@@ -307,7 +338,7 @@ __global__ void __launch_bounds__(SC_T) scatter_kernel(const uint16_t* __restric
     int j, nz;
     float c;
     int64_t sig;
-    entry(e0 + lane, j, c, nz, sig);
+    entry(e0 + lane, true, j, c, nz, sig);
     const unsigned m = __match_any_sync(0xffffffffu, j);
     if (j >= 0) {
       const int pos = mine[j] + __popc(m & lt);
@@ -1410,7 +1441,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
-    const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
+    const size_t sc_smem = scatter_smem(K, s);
     DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sc_smem)),
                   "dlsh_mod_update: attribute");
@@ -1524,7 +1555,7 @@ int ksvd_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, float* c
   tile_offsets_kernel<<<K, 256, 0, st>>>(w.cnt, T, w.atom_start, w.off);
   launches += (N > 0 ? 1 : 0) + 3;
   if (N > 0) {
-    const size_t sc_smem = static_cast<size_t>(SC_T / 32 + 1) * K * sizeof(int);
+    const size_t sc_smem = scatter_smem(K, s);
     DLSH_CUDA_TRY(cudaFuncSetAttribute(scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sc_smem)),
                   "dlsh_ksvd_update: attribute");
