@@ -31,7 +31,8 @@ TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 : BF16 ratio
 # variant), from one ncu capture at N = 1,000,000; the traffic grows with the
 # number of signals, so a launch over N signals moves N times it.  A kernel
 # without a capture of its current form reports null.
-ENCODE_TRAFFIC = {(1024, 8, 5): (185.01888e6 + 35.369472e6) / 1_000_000}
+ENCODE_TRAFFIC = {(1024, 8, 5): (185.01888e6 + 35.369472e6) / 1_000_000,
+                  (1024, 8, 6): (184.726272e6 + 35.841792e6) / 1_000_000}
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -59,6 +60,8 @@ def parse():
                     help="time the whole step (default) or one leg alone, for profiling")
     ap.add_argument("--tune", action="store_true",
                     help="encode / decode legs: run the library's autotuner on the leg's inputs first")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="step: skip the autotuning of the encoder and the decode before the warm-up")
     return ap.parse_args()
 
 
@@ -952,6 +955,17 @@ def main():
             ev["dec"].append((e2, e3))
         return Dn
 
+    # the library's autotuners, as a deployment would run them once per
+    # configuration: encoder kernel and ring depth on a 1M-signal sample, then
+    # the decode's batch and warps on that sample's codes (untimed)
+    tuned = None
+    if not a.no_tune:
+        S = min(N, 1 << 20)
+        t_enc = api.autotune_encode(D, X[:S], s, precision=a.precision)
+        api.encode(D, X[:S], s, precision=a.precision, out=tuple(t[:S] for t in out), sync=True)
+        t_dec = api.autotune_decode(D, idx[:S], coef[:S], nnz[:S], means=MU[:S], cam=cam)
+        tuned = {"encode": t_enc, "encode_kernel": t_enc & 255, "encode_ring_cap": t_enc >> 8,
+                 "decode_batch_warps": list(t_dec), "sample": S}
     Dcur = D
     for _ in range(a.warmup):
         Dcur = step(Dcur)
@@ -981,7 +995,7 @@ def main():
     # the kernel is timed per launch inside a 23 ms step, so the burst peak applies
     peaks, src = load_peaks()
     bf16 = float(peaks["bf16_tflops"])
-    variant = api.encode_variant(K, s, a.precision)
+    variant = tuned["encode_kernel"] if tuned else api.encode_variant(K, s, a.precision)
     if a.precision == "fp32" and variant in (5, 6, 7):
         peak = bf16 / 3.0
         peak_note = "FP16 dense (= bf16 burst) / 3 for the three-product FP16 split"
@@ -1041,7 +1055,7 @@ def main():
                                f"update + decode from a random camera",
                    "N": N, "K": K, "s": s, "precision": a.precision,
                    "l2": "inputs larger than L2 (X = %.0f MB)" % (N * 45 * 4 / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "autotuned": tuned},
         "omp": omp,
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
