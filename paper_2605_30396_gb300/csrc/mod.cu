@@ -561,15 +561,17 @@ __global__ void __launch_bounds__(128, SMAX <= 8 ? 5 : (SMAX <= 16 ? 4 : 3))
       }
       if (lane < RW - DLSH_D) bpart[DLSH_D + lane] = 0.0;
     }
-    // sum the warps' partials in order
+    // sum the warps' partials in order, in float-float (FP64 arithmetic is
+    // slow on this part: one conversion pair and one add per atom instead of
+    // four)
     __syncthreads();
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-      double acc = 0.0;
-      for (int w = 0; w < nw; ++w) {
+      float h = smf[k], l = smf[K + k];
+      for (int w = 1; w < nw; ++w) {
         const float* gh = smf + static_cast<size_t>(w) * 2 * K;
-        acc += static_cast<double>(gh[k]) + static_cast<double>(gh[K + k]);
+        ff_add(h, l, gh[k], gh[K + k]);
       }
-      Gp[static_cast<size_t>(seg) * K + k] = acc;
+      Gp[static_cast<size_t>(seg) * K + k] = static_cast<double>(h) + static_cast<double>(l);
     }
     for (int q = threadIdx.x; q < RW; q += blockDim.x) {
       double acc = 0.0;
