@@ -811,9 +811,10 @@ def e2e_leg(api, X, MU, Dcur, cam, s, out, rgb, precision, steps):
     step's inputs (signals, means, dictionary) go host -> device from pinned
     memory and its results (codes, residuals, the new dictionary, the decoded
     colours) come back to pinned host memory.  The copies run on a second
-    stream: the signals go in chunks, each chunk encoded as soon as it has
-    landed, and the codes go back while the MOD update and the decode run.
-    Events on the copy stream give the achieved copy bandwidths."""
+    stream: the signals go in growing chunks, each chunk encoded as soon as it
+    has landed; the codes go back while the MOD update and the decode run, and
+    the colours in two halves, the first while the second is decoded.  Events
+    on the copy stream give the achieved copy bandwidths."""
     import torch
     idx, coef, nnz, resid = out
     N = X.shape[0]
@@ -827,16 +828,17 @@ def e2e_leg(api, X, MU, Dcur, cam, s, out, rgb, precision, steps):
     MUd = torch.empty_like(MU)
     Dd = torch.empty_like(Dcur)
     copy = torch.cuda.Stream()
-    # chunk edges on whole waves of the encoder (one 128-signal tile per SM),
-    # the first chunk small so that the encode starts early
-    wave = 128 * torch.cuda.get_device_properties(0).multi_processor_count
-    if N >= 40 * wave:
-        first = 8 * wave
-        rest = (N - first) // (3 * wave) * wave
-        bnd = [0, first, first + rest, first + 2 * rest, N]
+    # chunk edges on whole waves of the encoder (three 128-signal tiles per SM);
+    # encoding a signal takes about 3.4x as long as copying it in, so the chunks
+    # grow 1, 4, 12 waves and then the rest: each chunk lands while the one
+    # before it is encoded, and only the first (11 MB) is exposed
+    wave = 3 * 128 * torch.cuda.get_device_properties(0).multi_processor_count
+    if N >= 24 * wave:
+        bnd = [0, wave, 5 * wave, 17 * wave, N]
     else:
         bnd = [0, N]
     nch = len(bnd) - 1
+    half = N // 2  # the colours go back in two halves, the first while the second decodes
     reps = max(1, min(3, steps))
     h2d_ms, d2h_ms = [], []
     for rep in range(reps + 1):  # the first repetition is an untimed warm-up
@@ -868,8 +870,12 @@ def e2e_leg(api, X, MU, Dcur, cam, s, out, rgb, precision, steps):
             ev[3].record(copy)
         Dn = api.mod_update(Xd, Dd, idx, coef, nnz, resid)
         stream.wait_event(mu_in)
-        api.decode(Dn, idx, coef, nnz, means=MUd, cam=cam, out=rgb)
-        oh[4].copy_(rgb, non_blocking=True)
+        for lo, hi in ((0, half), (half, N)):
+            api.decode(Dn, idx[lo:hi], coef[lo:hi], nnz[lo:hi], means=MUd[lo:hi], cam=cam, out=rgb[lo:hi])
+            part = stream.record_event()
+            with torch.cuda.stream(copy):
+                copy.wait_event(part)
+                oh[4][lo:hi].copy_(rgb[lo:hi], non_blocking=True)
         Dnh.copy_(Dn, non_blocking=True)
         torch.cuda.synchronize()
         if rep >= 1:
