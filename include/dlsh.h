@@ -296,6 +296,12 @@ int dlsh_autotune_encode(const float* D, int K, int d, const float* X, int64_t N
                          int precision, uint16_t* idx, float* coef, uint8_t* nnz,
                          float* resid_sq, void* ws, size_t ws_bytes, void* stream, int* best_bn);
 
+/* The encoder choice recorded for (K, s, precision) by dlsh_autotune_encode in
+ * this process or read from DLSH_AUTOTUNE_CACHE: the kernel (low byte) + 256 x
+ * the ring-stage cap, as *best_bn reports it; 0 if none is recorded or the
+ * arguments are out of range.  Host only (no GPU work). */
+int dlsh_tuned_encode(int K, int s, int precision);
+
 /* ---- learned support proposal ------------------------------------------
  * An extension of the paper's plain OMP (Sec. 2.1): a 45 -> 256 -> 256 -> K MLP
  *   xn = x/||x|| (0 if x = 0); h1 = gelu(W1 xn + b1); h2 = gelu(W2 h1 + b2);
@@ -411,6 +417,13 @@ int dlsh_autotune_decode(const float* D, int K, int d, const void* idx, const vo
                          const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
                          const float* cam_pos, float* rgb, void* stream, int* best_batch,
                          int* best_warps);
+
+/* The decode shape recorded for (format, K, s), format as in
+ * dlsh_autotune_decode: returns 1 and sets *batch and *warps (host, may be
+ * NULL) if one is recorded, else 0 (also for arguments out of range).  A
+ * record that no longer fits beside the dictionary is ignored by the decode.
+ * Host only (no GPU work). */
+int dlsh_tuned_decode(int format, int K, int s, int* batch, int* warps);
 
 /*
  * The paper's storage format (Sec. 2.2): the code matrix A (K x N) in

@@ -89,6 +89,8 @@ SIGNATURES = {
     "dlsh_autotune_encode": (c_int, [P, c_int, c_int, P, c_int64, c_int, c_int, P, P, P, P, P,
                                      c_size_t, P, P]),
     "dlsh_autotune_decode": (c_int, [P, c_int, c_int, P, P, c_int, P, c_int, c_int64, P, P, P, P, P, P]),
+    "dlsh_tuned_encode": (c_int, [c_int, c_int, c_int]),
+    "dlsh_tuned_decode": (c_int, [c_int, c_int, c_int, P, P]),
     "dlsh_csc_workspace_size": (c_size_t, [c_int64]),
     "dlsh_csc_from_ell": (c_int, [P, P, P, c_int64, c_int, P, P, P, P, c_size_t, P, c_int]),
     "dlsh_decode_compact_max_k": (c_size_t, [c_int]),

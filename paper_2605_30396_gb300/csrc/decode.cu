@@ -521,6 +521,20 @@ extern "C" int dlsh_decode_compact(const float* D, int K, int d, const void* idx
   return finish(st, nullptr, flags, "dlsh_decode_compact");
 }
 
+extern "C" int dlsh_tuned_decode(int format, int K, int s, int* batch, int* warps) {
+  using namespace dlsh;
+  using namespace dlsh::dec;
+  if (format < 0 || format > 2 || K < 1 || K > DLSH_MAX_K || s < 1 || s > DLSH_MAX_S) return 0;
+  const int fm = format == 0 ? decode_format(K, s) : (format == 1 ? FM_C8 : FM_C16);
+  char key[64];
+  snprintf(key, sizeof(key), "decode f=%d K=%d s=%d", fm, K, s);
+  int v[2] = {0, 0};
+  if (!tune_get(key, v, 2)) return 0;
+  if (batch) *batch = v[0];
+  if (warps) *warps = v[1];
+  return 1;
+}
+
 extern "C" int dlsh_autotune_decode(const float* D, int K, int d, const void* idx, const void* coef, int format,
                                     const uint8_t* nnz, int s, int64_t N, const float* dirs_or_means,
                                     const float* cam_pos, float* rgb, void* stream, int* best_batch,

@@ -1823,6 +1823,11 @@ static void forget_tuned(int K, int s, int prec) {
 }  // namespace enc
 }  // namespace dlsh
 
+extern "C" int dlsh_tuned_encode(int K, int s, int precision) {
+  if (K < 1 || K > DLSH_MAX_K || s < 1 || s > 16 || precision < 0 || precision > 4) return 0;
+  return dlsh::enc::tuned_choice(K, s, precision);
+}
+
 extern "C" int dlsh_autotune_encode(const float* D, int K, int d, const float* X, int64_t N, int s,
                                     int precision, uint16_t* idx, float* coef, uint8_t* nnz,
                                     float* resid_sq, void* ws, size_t ws_bytes, void* stream,

@@ -153,6 +153,42 @@ def test_autotuner_and_ring_cap_argument_errors(L):
     assert rc == -1 and b"ring cap" in L.dlsh_last_error()
 
 
+def test_tuning_table_read_from_the_cache_file(tmp_path):
+    """The autotuners' table as DLSH_AUTOTUNE_CACHE keeps it: JSON lines keyed by
+    configuration (and the older encoder-only lines), read back at first use.
+    Runs in a child process so that the file is the table's first source."""
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.jsonl"
+    cache.write_text('{"key": "encode K=1024 s=8 p=0", "values": [6, 2]}\n'
+                     '{"K": 512, "s": 4, "precision": 1, "bn": 2}\n'
+                     '{"key": "decode f=0 K=1024 s=8", "values": [16, 14]}\n'
+                     '{"key": "decode f=3 K=700 s=4", "values": [8, 21]}\n'
+                     'not a record\n')
+    code = (
+        "import ctypes, sys\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2605_30396_gb300 import _lib\n"
+        "L = _lib.lib()\n"
+        "b, w = ctypes.c_int(0), ctypes.c_int(0)\n"
+        "r = [L.dlsh_tuned_encode(1024, 8, 0), L.dlsh_tuned_encode(512, 4, 1), L.dlsh_tuned_encode(256, 8, 0),\n"
+        "     L.dlsh_tuned_encode(1024, 8, 9)]\n"
+        "d = L.dlsh_tuned_decode(0, 1024, 8, ctypes.byref(b), ctypes.byref(w))\n"
+        "r += [d, b.value, w.value]\n"
+        "d = L.dlsh_tuned_decode(2, 700, 4, ctypes.byref(b), ctypes.byref(w))\n"
+        "r += [d, b.value, w.value, L.dlsh_tuned_decode(1, 1024, 8, None, None), L.dlsh_tuned_decode(3, 1024, 8, None, None)]\n"
+        "print(r)\n" % ROOT)
+    env = dict(os.environ, DLSH_AUTOTUNE_CACHE=str(cache))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stderr
+    got = eval(out.stdout.strip().splitlines()[-1])
+    # encoder: kernel 6 with a ring cap of 2; the older line; nothing recorded; bad precision
+    assert got[:4] == [6 + 256 * 2, 2, 0, 0], got
+    # decode: FP32 codes at K = 1024 (the shared-memory table), compact 16-bit codes
+    # (internal format 3); nothing recorded for 8-bit codes; format out of range
+    assert got[4:] == [1, 16, 14, 1, 8, 21, 0, 0], got
+
+
 def test_binding_refuses_host_tensors_for_device_arguments():
     import torch
 
