@@ -10,8 +10,10 @@
 //   2. scan kernels     per-atom totals, atom offsets, per-(atom, tile) offsets
 //   3. scatter_kernel   one CTA per signal tile writes (signal, coef, nnz) into
 //                       the atom-major list in signal order (a counting sort)
-//   4. accum_kernel     one CTA per segment of an atom's list: row j of G and
-//                       column j of B.  Each warp owns a fixed slice, one list
+//   4. accum_kernel     one CTA per segment of an atom's list: row j of G
+//                       (entries k >= j; G is symmetric, and its lower
+//                       triangle is mirrored from the upper one after the
+//                       reduction) and column j of B.  Each warp owns a fixed slice, one list
 //                       entry per lane pair; sums are float-float (exact FMA
 //                       products, two-sum accumulation: about FP64 accuracy
 //                       on the FP32 pipe, since GB300's FP64 units are slow),
@@ -367,10 +369,12 @@ __device__ __forceinline__ void block_range(const int* __restrict__ off,
 //   B   each lane keeps float-float sums of its entries' a_ij x_i over half of
 //       the 45 dimensions in registers (the signal row is read straight from
 //       global memory); a butterfly of two-sums adds the lanes up at the end
-//   G   for each support slot t, the lanes add a_ij a_ik into the warp's row
-//       partial in shared memory; lanes that hit the same atom k are grouped
-//       (match) and their products summed in lane order by the group's first
-//       lane before its single update; the diagonal k = j stays in registers
+//   G   for each support slot t with atom k > j, the lanes add a_ij a_ik into
+//       the warp's row partial in shared memory (the entries k < j come from
+//       row k's segments, mirrored later); lanes that hit the same atom k are
+//       grouped (match) and their products summed in lane order by the group's
+//       first lane before its single update; the diagonal k = j stays in
+//       registers
 // Every sum runs in a fixed order, so the result does not depend on timing.
 __device__ __forceinline__ void ff_add(float& h, float& l, float p, float pl) {
   const float s = __fadd_rn(h, p);
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(128, SMAX <= 8 ? 5 : (SMAX <= 16 ? 4 : 3))
         const int k = kk[u];
         const float c = cc[u];
         if (on && k == j) ff_fma(dh, dl, a, c);
-        const bool upd = on && k != j && k < K;
+        const bool upd = on && k > j && k < K;
         const unsigned m = __ballot_sync(FULL, upd);
         if (upd) {
           const unsigned grp = __match_any_sync(m, k);
@@ -580,6 +584,28 @@ __global__ void __launch_bounds__(128, SMAX <= 8 ? 5 : (SMAX <= 16 ? 4 : 3))
       Bp[static_cast<size_t>(seg) * RW + q] = acc;
     }
     __syncthreads();  // shared partials are reused by the next segment
+  }
+}
+
+// M's lower triangle from its upper one: row j of G holds the entries k >= j,
+// so M[k][j] = M[j][k] for k > j (32 x 32 tiles through shared memory; only
+// the tiles on or above the diagonal are read).
+constexpr int MT = 32;
+__global__ void __launch_bounds__(MT * 8) mirror_kernel(double* __restrict__ M, int K) {
+  __shared__ double t[MT][MT + 1];
+  const int rb = blockIdx.y, cb = blockIdx.x;  // source tile: rows rb, columns cb >= rb
+  if (cb < rb) return;
+  const int x = threadIdx.x % MT, y0 = threadIdx.x / MT;
+  for (int y = y0; y < MT; y += 8) {
+    const int r = rb * MT + y, c = cb * MT + x;
+    t[y][x] = (r < K && c < K) ? M[static_cast<size_t>(r) * K + c] : 0.0;
+  }
+  __syncthreads();
+  // destination: row cb*MT + y, column rb*MT + x, written where it lies below
+  // the diagonal
+  for (int y = y0; y < MT; y += 8) {
+    const int r = cb * MT + y, c = rb * MT + x;
+    if (r < K && c < K && r > c) M[static_cast<size_t>(r) * K + c] = t[x][y];
   }
 }
 
@@ -1473,8 +1499,12 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
                                                                  P * K, w.seg_start, w.list, w.Gp, w.Bp);
   }
   seg_reduce_kernel<<<K, 256, 0, st>>>(w.seg_start, w.Gp, w.Bp, K, P, w.M, w.Z);
+  {
+    const int nb = (K + MT - 1) / MT;
+    mirror_kernel<<<dim3(nb, nb), MT * 8, 0, st>>>(w.M, K);
+  }
   ridge_kernel<<<1, 1024, 0, st>>>(w.M, K, w.lam);
-  launches += 4;
+  launches += 5;
   // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
   // kRefine FP32 solves with FP64 residuals in between
   scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, D_old, w.lam, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
