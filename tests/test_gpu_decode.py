@@ -166,3 +166,9 @@ def test_decode_autotune_keeps_colours(lib, K, s, compact):
     gb, nw = lib.autotune_decode(Dt, it, ct, nt, dirs=dt)
     assert gb in (8, 16) and 1 <= nw <= 32
     np.testing.assert_array_equal(run(), before)
+    import ctypes
+    from paper_2605_30396_gb300 import _lib as L
+    b, w = ctypes.c_int(0), ctypes.c_int(0)
+    fmt = 0 if not compact else (1 if K <= 256 else 2)
+    assert L.lib().dlsh_tuned_decode(fmt, K, s, ctypes.byref(b), ctypes.byref(w)) == 1
+    assert (b.value, w.value) == (gb, nw)

@@ -57,6 +57,8 @@ def test_autotune_keeps_results(lib):
     bn = lib.autotune_encode(sc["D"], sc["X"][:8192], 8)
     assert bn & 255 in (2, 3, 4, 5, 6, 7, 64, 128)
     assert bn >> 8 == 0 or 2 <= bn >> 8 <= 32
+    from paper_2605_30396_gb300 import _lib as L
+    assert L.lib().dlsh_tuned_encode(1024, 8, 0) == bn
     after = [t.cpu().numpy() for t in lib.encode(sc["D"], sc["X"], 8, sync=True)]
     (ia, ca, na, ra), (ib, cb, nb, rb) = before, after
     same = (ia == ib).all(axis=1) & (na == nb)
