@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 SO_PATH = os.path.join(PKG, "libdlsh.so")
 STAMP = os.path.join(PKG, "libdlsh.stamp")
-SOURCES = ["api.cu", "encode.cu", "decode.cu", "mod.cu", "learn.cu", "noalloc.cu", "mlp.cu", "propose.cu", "learned.cu", "selftest.cu", "splat.cu"]
+SOURCES = ["api.cu", "encode.cu", "enc_one_fp32.cu", "enc_one_lowp.cu", "enc_pair.cu", "enc_split.cu", "decode.cu", "mod.cu", "learn.cu", "noalloc.cu", "mlp.cu", "propose.cu", "learned.cu", "selftest.cu", "splat.cu"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

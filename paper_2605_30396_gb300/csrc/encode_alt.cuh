@@ -343,6 +343,9 @@ __device__ __forceinline__ void alt_issue(const AltSync& y, uint32_t tmem_base, 
   }
 }
 
+// (a template only so that the header can be included by several translation
+// units; instantiated in enc_split.cu)
+template <int V = 0>
 __global__ void __launch_bounds__(NTHREADS, 1) encode_alt_kernel(const __grid_constant__ AltArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t ACC0 = 128;
