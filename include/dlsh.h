@@ -162,12 +162,11 @@ int dlsh_encode_profile(const float* D, int K, int d, const float* X, int64_t N,
  * Scratch lives in one fixed device array of dlsh_encode_noalloc_max_bytes()
  * bytes (8 MiB), which every GPU that loads the library holds until the process
  * exits; that covers K <= 1024 at every precision and s.  A configuration that
- * needs more returns DLSH_ERR_UNSUPPORTED before anything is launched.  Each
- * call outside a stream capture looks up the array's device address on the
- * current device (so a context rebuilt after cudaDeviceReset is followed); a
- * call inside a capture uses the address its device last looked up, so make
- * the first call on a device before any stream capture (else
- * DLSH_ERR_INVALID_ARG).  All calls share
+ * needs more returns DLSH_ERR_UNSUPPORTED before anything is launched.  A call
+ * made while `stream` is not capturing looks up the array's device address on
+ * the current device (so a context rebuilt after cudaDeviceReset is followed);
+ * a call made while it is capturing uses the address from the device's last
+ * lookup, and returns DLSH_ERR_INVALID_ARG if there was none.  All calls share
  * the array: calls whose work overlaps on the GPU (different streams, or
  * different host threads) race on it and must be serialised by the caller.
  */

@@ -25,11 +25,11 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 static std::mutex g_mu;
 static void* g_addr[kMaxDevices] = {};
 
-// The device address of g_scratch on the current device.  Outside a stream
-// capture it is looked up with cudaGetSymbolAddress on every call (so a context
-// rebuilt after cudaDeviceReset is seen) and remembered per device; inside a
-// capture the remembered address is used, so the first call on a device must
-// come before any capture.
+// The device address of g_scratch on the current device: looked up with
+// cudaGetSymbolAddress on every call made while the stream is not capturing (so
+// a context rebuilt after cudaDeviceReset is seen) and remembered per device;
+// while the stream is capturing, the remembered address is used (an error if
+// there is none).
 static int scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   DLSH_CUDA_TRY(cudaGetDevice(&dev), "dlsh_encode_noalloc: cudaGetDevice");
