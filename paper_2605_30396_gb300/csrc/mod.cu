@@ -67,7 +67,7 @@ struct Ws {
   double* Zs;      // K x RW: S Z
   double* Xs;      // K x RW: solution of the scaled system (FP64 accumulation)
   float* R32;      // K x RW: current residual of the scaled system
-  double* Xb;      // K x RW: D~^T = S Xs
+  double* Xb;      // K x RW: D~^T = S Xs, kept up to date with Xs
   int* dead;       // K
   int* seg_start;  // P*K + 1: first accumulation segment of each (block p, atom j), p-major
   double* Gp;      // max_segs x K partial G rows
@@ -695,7 +695,7 @@ __global__ void scale_kernel(const double* __restrict__ M, const double* __restr
                              const float* __restrict__ D_old, const double* __restrict__ lamp, int K,
                              double* __restrict__ dsc, float* __restrict__ A,
                              double* __restrict__ Zs, float* __restrict__ R32,
-                             double* __restrict__ Xs) {
+                             double* __restrict__ Xs, double* __restrict__ Xb) {
   const int j = blockIdx.x;
   const double lam = *lamp;
   const double dj = 1.0 / sqrt(M[static_cast<size_t>(j) * K + j] + lam);
@@ -712,6 +712,7 @@ __global__ void scale_kernel(const double* __restrict__ M, const double* __restr
     Zs[static_cast<size_t>(j) * RW + c] = z;
     R32[static_cast<size_t>(j) * RW + c] = static_cast<float>(z);
     Xs[static_cast<size_t>(j) * RW + c] = 0.0;
+    Xb[static_cast<size_t>(j) * RW + c] = 0.0;
   }
 }
 
@@ -932,7 +933,8 @@ __global__ void __launch_bounds__(CH_T) chol_inv_kernel(float* __restrict__ A, f
 template <bool TRANS>
 __global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, int K,
                                                    const float* __restrict__ in, float* __restrict__ out,
-                                                   double* __restrict__ Xs) {
+                                                   double* __restrict__ Xs, const double* __restrict__ dsc,
+                                                   double* __restrict__ Xb) {
   const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= K) return;
@@ -965,8 +967,18 @@ __global__ void __launch_bounds__(256) trmm_kernel(const float* __restrict__ W, 
 #pragma unroll
   for (int c = 32; c < RW; ++c) v1 = lane == c - 32 ? acc[c] : v1;
   if (TRANS) {
-    Xs[static_cast<size_t>(row) * RW + lane] += static_cast<double>(v0);
-    if (lane < DLSH_D - 32) Xs[static_cast<size_t>(row) * RW + 32 + lane] += static_cast<double>(v1);
+    // the solution and its unscaled form D~^T = S Xs, which the FP64 residual
+    // and the normalisation read
+    const size_t o = static_cast<size_t>(row) * RW;
+    const double dr = dsc[row];
+    const double x0 = Xs[o + lane] + static_cast<double>(v0);
+    Xs[o + lane] = x0;
+    Xb[o + lane] = dr * x0;
+    if (lane < DLSH_D - 32) {
+      const double x1 = Xs[o + 32 + lane] + static_cast<double>(v1);
+      Xs[o + 32 + lane] = x1;
+      Xb[o + 32 + lane] = dr * x1;
+    }
   } else {
     out[static_cast<size_t>(row) * RW + lane] = v0;
     if (lane < RW - 32) out[static_cast<size_t>(row) * RW + 32 + lane] = v1;
@@ -982,7 +994,7 @@ __global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict
                                                         const double* __restrict__ lamp,
                                                         const double* __restrict__ dsc, int K,
                                                         const double* __restrict__ Zs,
-                                                        const double* __restrict__ Xs,
+                                                        const double* __restrict__ Xb,
                                                         float* __restrict__ R32) {
   __shared__ double Ms[RS_ROWS][33];
   __shared__ double Xt[32][RW + 1];
@@ -1001,7 +1013,7 @@ __global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict
     }
     for (int f = threadIdx.x; f < 32 * RW; f += RS_T) {
       const int r = f / RW, c = f % RW;
-      Xt[r][c] = k0 + r < K ? dsc[k0 + r] * Xs[static_cast<size_t>(k0 + r) * RW + c] : 0.0;
+      Xt[r][c] = k0 + r < K ? Xb[static_cast<size_t>(k0 + r) * RW + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -1034,12 +1046,6 @@ __global__ void __launch_bounds__(RS_T) residual_kernel(const double* __restrict
   }
 }
 
-// Unscaled solution D~^T = S X.
-__global__ void unscale_kernel(const double* __restrict__ dsc, const double* __restrict__ Xs, int K,
-                               double* __restrict__ Xb) {
-  const int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e < static_cast<int64_t>(K) * RW) Xb[e] = dsc[e / RW] * Xs[e];
-}
 
 // ---- 6a. normalise; mark dead atoms ----------------------------------------------
 __global__ void normalise_kernel(const double* __restrict__ Z, const int* __restrict__ atom_start,
@@ -1507,7 +1513,7 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   launches += 5;
   // mixed-precision solve: FP32 Cholesky of the Jacobi-scaled matrix, then
   // kRefine FP32 solves with FP64 residuals in between
-  scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, D_old, w.lam, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs);
+  scale_kernel<<<K, 256, 0, st>>>(w.M, w.Z, D_old, w.lam, K, w.dsc, w.A32, w.Zs, w.R32, w.Xs, w.Xb);
   ++launches;
   {
     static PerDevice<int> coop;
@@ -1539,16 +1545,13 @@ int mod_enqueue(const float* X, int64_t N, int K, const uint16_t* idx, const flo
   const int tr_grid = (K + 7) / 8;
   for (int it = 0; it < kRefine; ++it) {
     if (it > 0) {
-      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, RS_T, 0, st>>>(w.M, w.lam, w.dsc, K, w.Zs, w.Xs, w.R32);
+      residual_kernel<<<(K + RS_ROWS - 1) / RS_ROWS, RS_T, 0, st>>>(w.M, w.lam, w.dsc, K, w.Zs, w.Xb, w.R32);
       ++launches;
     }
-    trmm_kernel<false><<<tr_grid, 256, 0, st>>>(w.W32, K, w.R32, w.Y32, nullptr);
-    trmm_kernel<true><<<tr_grid, 256, 0, st>>>(w.W32, K, w.Y32, nullptr, w.Xs);
+    trmm_kernel<false><<<tr_grid, 256, 0, st>>>(w.W32, K, w.R32, w.Y32, nullptr, nullptr, nullptr);
+    trmm_kernel<true><<<tr_grid, 256, 0, st>>>(w.W32, K, w.Y32, nullptr, w.Xs, w.dsc, w.Xb);
     launches += 2;
   }
-  unscale_kernel<<<static_cast<int>((static_cast<int64_t>(K) * RW + 255) / 256), 256, 0, st>>>(
-      w.dsc, w.Xs, K, w.Xb);
-  ++launches;
   normalise_kernel<<<(K + 7) / 8, 256, 0, st>>>(w.Xb, w.atom_start, K, D_new, D_old, w.dead);
   ++launches;
   if (resid && N > 0) {
